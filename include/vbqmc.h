@@ -1,0 +1,156 @@
+/*
+ * vbqmc.h -- C ABI of the GB300 (sm_103a) Valence-Bond quantum Monte Carlo hot path.
+ *
+ * The library evaluates Jastrow-Valence-Bond (JVB) trial wave functions over a population
+ * of walkers and moves the walkers with VMC Metropolis sweeps, following Radenkovic,
+ * Domin, Toulouse and Braida, "The Valence-Bond Quantum Monte Carlo Method"
+ * (arXiv:2207.14715):
+ *
+ *   Psi(p) = J(alpha) exp(kappa_hat) sum_I c_I Phi_I          Sec. 2.1 Eq. PsiJVBSCF, Sec. 2.2 Eq. PsiJVBp
+ *   Phi_I  = HLSP structure (inactive pairs, singlet pairs,   Sec. 2.1 Eq. PhiI, expanded into
+ *            unpaired up electrons)                           2^Npairs determinants
+ *   J      = exp(f_en + f_ee + f_een), kappa = 0.8            Sec. 2.1, Jastrow expansions
+ *   E_L    = (H Psi)/Psi                                      Sec. 2.3.1
+ *   O_j    = Psi_j/Psi,  E_L,j = dE_L/dp_j                    Sec. 2.3.1, Eqs. Hi0..Sij
+ *
+ * Conventions
+ *   - Electrons 0..n_up-1 are spin up, n_up..N-1 spin down (spins fixed, Sec. 2.3.1).
+ *   - Basis: uncontracted normalised cartesian Gaussians; a shell of angular momentum l
+ *     (0, 1, 2) contributes 1, 3, 6 functions in the order s; x y z; xx yy zz xy xz yz.
+ *     zeta = 0 denotes the constant function 1.
+ *   - Walker positions R are walker-major: R[w][i][d] (double), w < W, i < N, d < 3.
+ *     Per-walker outputs are [W]; parameter derivatives are [W][P] (double).
+ *   - Parameters p, in this order: c_I for I in cparam; if jas_param: a_2..a_6 per
+ *     element, b_2..b_6, then (if een_on) 15 free e-e-n parameters theta per element;
+ *     then one kappa_kl per orbital excitation (k, l).
+ *   - All device pointers are borrowed for the duration of the call and must stay valid
+ *     until the work enqueued on 'stream' has completed.  Host arrays are copied.
+ *   - 'stream' is a cudaStream_t (NULL = legacy default stream).  Calls are asynchronous
+ *     with respect to the host unless stated otherwise.
+ *   - Return value: VBQMC_OK (0) or a negative error code; vbqmc_last_error() gives a
+ *     message for the calling thread.  No function aborts or traps.
+ */
+#ifndef VBQMC_H
+#define VBQMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VBQMC_OK 0
+#define VBQMC_ERR_ARG -1          /* invalid argument or inconsistent system description */
+#define VBQMC_ERR_CUDA -2         /* a CUDA runtime call failed */
+#define VBQMC_ERR_NOSYS -3        /* no system loaded under that id */
+#define VBQMC_ERR_CAPACITY -4     /* a size exceeds what the kernels support */
+#define VBQMC_ERR_UNSUPPORTED -5  /* option not implemented */
+
+#define VBQMC_FP64 0   /* every step in double precision */
+#define VBQMC_MIXED 1  /* basis, orbitals, Jastrow and bulk derivatives in float; Slater LU,
+                          inverses, ratios, structure sums and energy accumulation in double */
+
+#define VBQMC_MAX_SYSTEMS 64
+
+typedef struct vbqmc_ctx vbqmc_ctx;  /* opaque; owned by the library */
+
+/* System description: the inputs of Eqs. PsiJVBSCF, PhiI and PsiJVBp (Sec. 2.1-2.2).
+ * Every pointer is a host array, read during vbqmc_set_system only. */
+typedef struct vbqmc_system_desc {
+  int Nn, n_elem;
+  const double* nuc_xyz;   /* [Nn][3] bohr */
+  const double* nuc_Z;     /* [Nn] */
+  const int* nuc_elem;     /* [Nn] element index in [0, n_elem); Jastrow a and theta are per element */
+  int S;
+  const int* sh_center;    /* [S] nucleus of each shell; shells of one nucleus must be contiguous */
+  const int* sh_l;         /* [S] 0, 1 or 2 */
+  const double* sh_zeta;   /* [S] exponent >= 0 */
+  int Norb;
+  const double* orb_coef;  /* [Norb][M] lambda_{p,mu}, M = number of basis functions */
+  int Nup, Ndn;            /* electrons of each spin (Nup >= Ndn) */
+  int Nvb;
+  const double* c_vb;      /* [Nvb] structure coefficients c_I */
+  const int* inact_off;    /* [Nvb+1] offsets into inact */
+  const int* inact;        /* inactive (doubly occupied) orbitals of each structure */
+  const int* pair_off;     /* [Nvb+1] offsets into pairs */
+  const int* pairs;        /* [npairs][2] singlet-coupled active orbital pairs (i, j), i = j allowed */
+  const int* unp_off;      /* [Nvb+1] offsets into unp */
+  const int* unp;          /* unpaired (spin up) active orbitals */
+  double kappa;            /* Jastrow scaling parameter (0.8 in the paper) */
+  const double* jas_a;     /* [n_elem][6] a_1..a_6 of f_en */
+  const double* jas_b;     /* [6] b_1 (ignored) and b_2..b_6 of f_ee */
+  double b1_anti, b1_par;  /* b_1 for antiparallel and parallel pairs (1/2 and 1/4 give the cusps) */
+  int een_on;              /* include f_een */
+  const double* een_theta; /* [n_elem][15] free e-e-n parameters (cusp-preserving subspace) */
+  int n_cparam;
+  const int* cparam;       /* structure indices whose c_I are parameters */
+  int jas_param;           /* nonzero: Jastrow parameters are parameters */
+  int n_kappa;
+  const int* kappa_kl;     /* [n_kappa][2] orbital excitations (k, l): phi_l -> phi_l + kappa phi_k */
+} vbqmc_system_desc;
+
+/* Creates a context on CUDA device 'device' (the calling thread's current device is
+ * restored on return).  *out receives the handle; release with vbqmc_destroy. */
+int vbqmc_create(vbqmc_ctx** out, int device);
+
+/* Releases every device allocation of the context.  Waits for the device. */
+void vbqmc_destroy(vbqmc_ctx* ctx);
+
+/* Message of the last error raised on the calling thread (static storage, valid until the
+ * next failing call on this thread). */
+const char* vbqmc_last_error(void);
+
+/* Loads a system under sys_id (0 <= sys_id < VBQMC_MAX_SYSTEMS), replacing any previous one.
+ * Host-side set-up (Sec. 2.1-2.2): validates the description, expands every structure into
+ * signed determinants (Eq. PhiI and the expansion after it: 2^Npairs terms, self pairs
+ * i = j give one term), merges identical determinants, derives the cusp-preserving e-e-n
+ * coefficients c = B theta (the coefficients fixed "in order not to alter the cusp
+ * conditions", Sec. 2.1), builds the orbital-excitation tables (Sec. 2.2) and uploads
+ * everything to the device.  Synchronous.  Errors: VBQMC_ERR_ARG for inconsistent input,
+ * VBQMC_ERR_CAPACITY if a size exceeds the kernels' limits (N <= 64, n_up <= 32, M <= 1024). */
+int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc);
+
+/* Host-only variant of the set-up above for inspection: no device is touched.
+ * info[0..11] = N, P, M, Norb, number of determinant terms, unique up determinants,
+ * unique down determinants, structure terms, orbitals evaluated per walker, orbital
+ * excitation entries, n_up, n_dn.  If terms != NULL it receives up to max_terms rows of
+ * [n_up + n_dn + 2] ints: up orbitals (ascending), down orbitals (ascending), structure
+ * index, sign (+1/-1) of that structure's term.  If een_B != NULL it receives the 23x15
+ * e-e-n free-parameter basis (row-major).  Returns VBQMC_OK or an error code. */
+int vbqmc_inspect_system(const vbqmc_system_desc* desc, int* info, int* terms, int max_terms, double* een_B);
+
+/* Evaluates the trial wave function at W walker positions (Sec. 2.1; Sec. 2.3.1 for E_L,
+ * O_j and E_L,j).
+ *   R      [W][N][3] device, in
+ *   logpsi [W] device, out: ln|Psi|       sign [W] device, out: sign of Psi (0 if singular)
+ *   eloc   [W] device, out: E_L = (H Psi)/Psi, Hamiltonian with nucleus-nucleus repulsion
+ *   grad   [W][N][3] device or NULL, out: grad_i ln|Psi|
+ *   O      [W][P] device or NULL, out: Psi_j/Psi
+ *   dEL    [W][P] device or NULL, out: dE_L/dp_j (requires O != NULL)
+ * precision: VBQMC_FP64 or VBQMC_MIXED.  W may be 0. */
+int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const double* R, double* logpsi,
+                       double* sign, double* eloc, double* grad, double* O, double* dEL, void* stream);
+
+/* VMC (Sec. 2.3.1): nsweeps sweeps of single-electron Metropolis moves over every walker,
+ * electron i moved to r_i + step*(2u - 1) per coordinate and accepted when
+ * u_acc < |Psi(R')/Psi(R)|^2; inverses of every unique Slater matrix are refreshed by LU at
+ * the start of each sweep and updated by Sherman-Morrison after each accepted move.
+ * Random numbers: Philox4x32-10 keyed by seed, counter (walker_offset + w, step0 + sweep,
+ * electron, (system_tag << 8) | purpose) with purpose 0 -> (u_x, u_y) and 1 -> (u_z, u_acc),
+ * each uniform (x >> 11) * 2^-53 of one 64-bit half of the output.
+ *   R    [W][N][3] device, in/out
+ *   nacc [W] device int or NULL, out: accepted moves (accumulated over the sweeps)
+ * After the last sweep, if logpsi/sign/eloc/O/dEL are non-NULL, the walkers are evaluated as
+ * by vbqmc_eval_walkers (one walker-step = one sweep + that evaluation). */
+int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R, int nsweeps, double step,
+                    uint64_t seed, uint32_t step0, uint32_t system_tag, uint32_t walker_offset, int* nacc,
+                    double* logpsi, double* sign, double* eloc, double* O, double* dEL, void* stream);
+
+/* Number of kernel launches enqueued by the last successful call on this context. */
+int vbqmc_last_launch_count(vbqmc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VBQMC_H */

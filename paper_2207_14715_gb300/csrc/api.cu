@@ -1,0 +1,295 @@
+// C ABI of the VB-QMC library (declared in include/vbqmc.h): context, system upload and
+// the walker entry points.
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "vbqmc_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return VBQMC_ERR_CUDA;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+struct LoadedSystem {
+  bool loaded = false;
+  vbq::SysHost host;
+  vbq::SysDev dev{};
+  void* blob = nullptr;
+  size_t blob_bytes = 0;
+  vbq::EvalLayout lay_eval[2];
+  vbq::SweepLayout lay_sweep[2];
+  int lay_rc_eval[2] = {0, 0};
+  int lay_rc_sweep[2] = {0, 0};
+};
+
+// Packs host arrays into one 16-byte-aligned blob and records where each one went.
+struct BlobBuilder {
+  std::vector<unsigned char> bytes;
+  template <class T> size_t add(const std::vector<T>& v) {
+    size_t off = (bytes.size() + 15) & ~size_t(15);
+    bytes.resize(off + std::max<size_t>(v.size() * sizeof(T), 16), 0);
+    if (!v.empty()) std::memcpy(bytes.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+};
+
+}  // namespace
+
+struct vbqmc_ctx {
+  int device = 0;
+  int max_smem = 0;
+  int last_launches = 0;
+  LoadedSystem sys[VBQMC_MAX_SYSTEMS];
+};
+
+static void free_system(LoadedSystem& s) {
+  if (s.blob) cudaFree(s.blob);
+  s = LoadedSystem();
+}
+
+extern "C" {
+
+const char* vbqmc_last_error(void) { return g_err.c_str(); }
+
+int vbqmc_create(vbqmc_ctx** out, int device) {
+  if (!out) return fail(VBQMC_ERR_ARG, "null output handle");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(VBQMC_ERR_ARG, "device index out of range");
+  DeviceGuard g(device);
+  if (!g.ok) return fail(VBQMC_ERR_CUDA, "cudaSetDevice failed");
+  int smem = 0;
+  e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  vbqmc_ctx* c = new vbqmc_ctx();
+  c->device = device;
+  c->max_smem = smem;
+  *out = c;
+  return VBQMC_OK;
+}
+
+void vbqmc_destroy(vbqmc_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& s : ctx->sys) free_system(s);
+  delete ctx;
+}
+
+int vbqmc_inspect_system(const vbqmc_system_desc* desc, int* info, int* terms, int max_terms, double* een_B) {
+  vbq::SysHost h;
+  std::string err;
+  int rc = vbq::build_system(desc, h, err);
+  if (rc) return fail(rc, err);
+  if (info) {
+    int ent = (int)((h.kap_ent[0].size() + h.kap_ent[1].size()) / 4);
+    int v[12] = {h.N, h.P, h.M, h.Norb, (int)h.term_coef.size(), h.U[0], h.U[1], (int)h.sterm_d.size(),
+                 (int)h.ev_orb.size(), ent, h.Nup, h.Ndn};
+    std::memcpy(info, v, sizeof(v));
+  }
+  if (terms) {
+    const int row = h.Nup + h.Ndn + 2;
+    const int nst = (int)h.sterm_d.size();
+    for (int t = 0; t < nst && t < max_terms; ++t) {
+      const int k = h.sterm_k[t];
+      const int a = h.term_det[2 * k], b = h.term_det[2 * k + 1];
+      int* r = terms + (size_t)t * row;
+      for (int o = 0; o < h.Nup; ++o) r[o] = h.det_glob[0][a * h.Nup + o];
+      for (int o = 0; o < h.Ndn; ++o) r[h.Nup + o] = h.det_glob[1][b * h.Ndn + o];
+      r[h.Nup + h.Ndn] = h.sterm_I[t];
+      r[h.Nup + h.Ndn + 1] = (int)h.sterm_d[t];
+    }
+  }
+  if (een_B) std::memcpy(een_B, h.een_B.data(), h.een_B.size() * sizeof(double));
+  return VBQMC_OK;
+}
+
+int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) {
+  if (!ctx) return fail(VBQMC_ERR_ARG, "null context");
+  if (sys_id < 0 || sys_id >= VBQMC_MAX_SYSTEMS) return fail(VBQMC_ERR_ARG, "sys_id out of range");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(VBQMC_ERR_CUDA, "cudaSetDevice failed");
+  LoadedSystem ls;
+  std::string err;
+  int rc = vbq::build_system(desc, ls.host, err);
+  if (rc) return fail(rc, err);
+  const vbq::SysHost& h = ls.host;
+  BlobBuilder bb;
+  std::vector<float> coef_f(h.orb_coef.begin(), h.orb_coef.end());
+  std::vector<float> een_cf(h.een_c.begin(), h.een_c.end());
+  const size_t o_nuc4 = bb.add(h.nuc4), o_nuc_elem = bb.add(h.nuc_elem), o_sh_center = bb.add(h.sh_center),
+               o_sh_l = bb.add(h.sh_l), o_sh_first = bb.add(h.sh_first), o_sh_zeta = bb.add(h.sh_zeta),
+               o_sh_norm = bb.add(h.sh_norm), o_orb_lo = bb.add(h.orb_lo), o_orb_hi = bb.add(h.orb_hi),
+               o_orb_off = bb.add(h.orb_off), o_orb_coef = bb.add(h.orb_coef), o_orb_coef_f = bb.add(coef_f),
+               o_ev_orb = bb.add(h.ev_orb), o_occ0 = bb.add(h.occ_list[0]), o_occ1 = bb.add(h.occ_list[1]),
+               o_dl0 = bb.add(h.det_loc[0]), o_dl1 = bb.add(h.det_loc[1]), o_de0 = bb.add(h.det_ev[0]),
+               o_de1 = bb.add(h.det_ev[1]), o_term_det = bb.add(h.term_det), o_term_coef = bb.add(h.term_coef),
+               o_sI = bb.add(h.sterm_I), o_sk = bb.add(h.sterm_k), o_sd = bb.add(h.sterm_d),
+               o_cparam = bb.add(h.cparam), o_jas_a = bb.add(h.jas_a), o_jas_b = bb.add(h.jas_b),
+               o_een_c = bb.add(h.een_c), o_een_cf = bb.add(een_cf), o_een_B = bb.add(h.een_B),
+               o_ko0 = bb.add(h.kap_off[0]), o_ko1 = bb.add(h.kap_off[1]), o_ke0 = bb.add(h.kap_ent[0]),
+               o_ke1 = bb.add(h.kap_ent[1]);
+  cudaError_t e = cudaMalloc(&ls.blob, bb.bytes.size());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(system tables)");
+  ls.blob_bytes = bb.bytes.size();
+  e = cudaMemcpy(ls.blob, bb.bytes.data(), bb.bytes.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(ls.blob);
+    return cuda_fail(e, "cudaMemcpy(system tables)");
+  }
+  const unsigned char* B = static_cast<const unsigned char*>(ls.blob);
+  vbq::SysDev& d = ls.dev;
+  d.N = h.N; d.Nup = h.Nup; d.Ndn = h.Ndn; d.Nn = h.Nn; d.n_elem = h.n_elem; d.S = h.S; d.M = h.M;
+  d.Norb = h.Norb; d.Nvb = h.Nvb;
+  d.n_ev = (int)h.ev_orb.size(); d.n_ev_det = h.n_ev_det;
+  for (int sp = 0; sp < 2; ++sp) {
+    d.nocc[sp] = (int)h.occ_list[sp].size();
+    d.U[sp] = h.U[sp];
+    d.n[sp] = h.n[sp];
+  }
+  d.nterm = (int)h.term_coef.size();
+  d.nsterm = (int)h.sterm_d.size();
+  d.P = h.P; d.n_cparam = (int)h.cparam.size(); d.jas_param = h.jas_param; d.een_on = h.een_on;
+  d.n_kappa = h.n_kappa;
+  d.p_off_a = d.n_cparam;
+  d.p_off_b = d.p_off_a + (h.jas_param ? 5 * h.n_elem : 0);
+  d.p_off_theta = d.p_off_b + (h.jas_param ? 5 : 0);
+  d.p_off_kappa = d.p_off_theta + (h.jas_param && h.een_on ? vbq::kNfree * h.n_elem : 0);
+  d.kappa = h.kappa; d.b1_anti = h.b1_anti; d.b1_par = h.b1_par; d.vnn = h.vnn;
+  d.nuc4 = (const double*)(B + o_nuc4);
+  d.nuc_elem = (const int*)(B + o_nuc_elem);
+  d.sh_center = (const int*)(B + o_sh_center);
+  d.sh_l = (const int*)(B + o_sh_l);
+  d.sh_first = (const int*)(B + o_sh_first);
+  d.sh_zeta = (const double*)(B + o_sh_zeta);
+  d.sh_norm = (const double*)(B + o_sh_norm);
+  d.orb_lo = (const int*)(B + o_orb_lo);
+  d.orb_hi = (const int*)(B + o_orb_hi);
+  d.orb_off = (const int*)(B + o_orb_off);
+  d.orb_coef = (const double*)(B + o_orb_coef);
+  d.orb_coef_f = (const float*)(B + o_orb_coef_f);
+  d.ev_orb = (const int*)(B + o_ev_orb);
+  d.occ_list[0] = (const int*)(B + o_occ0);
+  d.occ_list[1] = (const int*)(B + o_occ1);
+  d.det_loc[0] = (const int*)(B + o_dl0);
+  d.det_loc[1] = (const int*)(B + o_dl1);
+  d.det_ev[0] = (const int*)(B + o_de0);
+  d.det_ev[1] = (const int*)(B + o_de1);
+  d.term_det = (const int*)(B + o_term_det);
+  d.term_coef = (const double*)(B + o_term_coef);
+  d.sterm_I = (const int*)(B + o_sI);
+  d.sterm_k = (const int*)(B + o_sk);
+  d.sterm_d = (const double*)(B + o_sd);
+  d.cparam = (const int*)(B + o_cparam);
+  d.jas_a = (const double*)(B + o_jas_a);
+  d.jas_b = (const double*)(B + o_jas_b);
+  d.een_c = (const double*)(B + o_een_c);
+  d.een_cf = (const float*)(B + o_een_cf);
+  d.een_B = (const double*)(B + o_een_B);
+  d.kap_off[0] = (const int*)(B + o_ko0);
+  d.kap_off[1] = (const int*)(B + o_ko1);
+  d.kap_ent[0] = (const int*)(B + o_ke0);
+  d.kap_ent[1] = (const int*)(B + o_ke1);
+  for (int p = 0; p < 2; ++p) {
+    const int tb = p == VBQMC_MIXED ? 4 : 8;
+    ls.lay_rc_eval[p] = vbq::make_eval_layout(d, tb, ctx->max_smem, ls.lay_eval[p]);
+    ls.lay_rc_sweep[p] = vbq::make_sweep_layout(d, tb, ctx->max_smem, ls.lay_sweep[p]);
+  }
+  ls.loaded = true;
+  free_system(ctx->sys[sys_id]);
+  ctx->sys[sys_id] = ls;
+  return VBQMC_OK;
+}
+
+int vbqmc_last_launch_count(vbqmc_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+static int check_call(vbqmc_ctx* ctx, int sys_id, int precision, int W) {
+  if (!ctx) return fail(VBQMC_ERR_ARG, "null context");
+  if (sys_id < 0 || sys_id >= VBQMC_MAX_SYSTEMS || !ctx->sys[sys_id].loaded)
+    return fail(VBQMC_ERR_NOSYS, "no system loaded under this id");
+  if (precision != VBQMC_FP64 && precision != VBQMC_MIXED) return fail(VBQMC_ERR_ARG, "bad precision mode");
+  if (W < 0) return fail(VBQMC_ERR_ARG, "negative walker count");
+  return VBQMC_OK;
+}
+
+int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const double* R, double* logpsi,
+                       double* sign, double* eloc, double* grad, double* O, double* dEL, void* stream) {
+  int rc = check_call(ctx, sys_id, precision, W);
+  if (rc) return rc;
+  ctx->last_launches = 0;
+  if (W == 0) return VBQMC_OK;
+  if (!R || !logpsi || !sign || !eloc) return fail(VBQMC_ERR_ARG, "null required pointer");
+  if (dEL && !O) return fail(VBQMC_ERR_ARG, "dEL requires O");
+  LoadedSystem& s = ctx->sys[sys_id];
+  if (s.lay_rc_eval[precision]) return fail(s.lay_rc_eval[precision], "per-walker state exceeds shared memory");
+  if ((O || dEL) && s.dev.P == 0) O = dEL = nullptr;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = vbq::launch_eval(precision, s.dev, s.lay_eval[precision], W, R, logpsi, sign, eloc, grad, O, dEL,
+                                   (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "eval kernel launch");
+  ctx->last_launches = 1;
+  return VBQMC_OK;
+}
+
+int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R, int nsweeps, double step,
+                    uint64_t seed, uint32_t step0, uint32_t system_tag, uint32_t walker_offset, int* nacc,
+                    double* logpsi, double* sign, double* eloc, double* O, double* dEL, void* stream) {
+  int rc = check_call(ctx, sys_id, precision, W);
+  if (rc) return rc;
+  ctx->last_launches = 0;
+  if (nsweeps < 0 || !(step > 0.0)) return fail(VBQMC_ERR_ARG, "bad sweep count or step");
+  if (system_tag > 0xffffffu) return fail(VBQMC_ERR_ARG, "system_tag must fit in 24 bits");
+  if (W == 0) return VBQMC_OK;
+  if (!R) return fail(VBQMC_ERR_ARG, "null R");
+  LoadedSystem& s = ctx->sys[sys_id];
+  if (s.lay_rc_sweep[precision]) return fail(s.lay_rc_sweep[precision], "per-walker state exceeds shared memory");
+  const bool do_eval = logpsi || sign || eloc || O || dEL;
+  if (do_eval && (!logpsi || !sign || !eloc)) return fail(VBQMC_ERR_ARG, "evaluation needs logpsi, sign and eloc");
+  if (dEL && !O) return fail(VBQMC_ERR_ARG, "dEL requires O");
+  DeviceGuard g(ctx->device);
+  int launches = 0;
+  if (nsweeps > 0) {
+    cudaError_t e = vbq::launch_sweep(precision, s.dev, s.lay_sweep[precision], W, R, nsweeps, step, seed, step0,
+                                      system_tag, walker_offset, nacc, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
+    ++launches;
+  }
+  if (do_eval) {
+    if (s.lay_rc_eval[precision]) return fail(s.lay_rc_eval[precision], "per-walker state exceeds shared memory");
+    if ((O || dEL) && s.dev.P == 0) O = dEL = nullptr;
+    cudaError_t e = vbq::launch_eval(precision, s.dev, s.lay_eval[precision], W, R, logpsi, sign, eloc, nullptr, O,
+                                     dEL, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "eval kernel launch");
+    ++launches;
+  }
+  ctx->last_launches = launches;
+  return VBQMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,861 @@
+// VB-QMC walker kernels for sm_103a: one warp per walker, per-walker state in shared memory.
+//
+//   eval_kernel   : ln|Psi|, sign, E_L, grad ln|Psi| and the parameter derivatives
+//                   O_j = Psi_j/Psi and E_L,j = dE_L/dp_j            (arXiv:2207.14715, Sec. 2.1-2.3.1)
+//   sweep_kernel  : VMC sweeps of single-electron Metropolis moves   (Sec. 2.3.1)
+//
+// Precision: template parameter Tb is the bulk type (basis functions, orbitals, Jastrow and
+// the excitation derivatives); the Slater LU, inverses, determinant ratios, structure sums
+// and energy accumulation are always double.
+#include <algorithm>
+#include <cfloat>
+
+#include "kernels.h"
+#include "wf_device.cuh"
+
+namespace vbq {
+
+namespace {
+
+inline int align16(int x) { return (x + 15) & ~15; }
+inline int group_size(int n) {
+  int g = 1;
+  while (g < n) g <<= 1;
+  return g;
+}
+
+template <class Tb> __device__ __forceinline__ const Tb* orb_coefs(const SysDev& s);
+template <> __device__ __forceinline__ const double* orb_coefs<double>(const SysDev& s) { return s.orb_coef; }
+template <> __device__ __forceinline__ const float* orb_coefs<float>(const SysDev& s) { return s.orb_coef_f; }
+template <class Tb> __device__ __forceinline__ const Tb* een_coefs(const SysDev& s);
+template <> __device__ __forceinline__ const double* een_coefs<double>(const SysDev& s) { return s.een_c; }
+template <> __device__ __forceinline__ const float* een_coefs<float>(const SysDev& s) { return s.een_cf; }
+
+// Basis functions (values, or values + gradient + Laplacian) of all shells at point r.
+// Lanes take shells round-robin.  Output arrays are indexed by basis function.
+template <class Tb, bool DERIV>
+__device__ __forceinline__ void basis_at(const SysDev& s, int lane, double x, double y, double z, Tb* bv, Tb* bx,
+                                         Tb* by, Tb* bz, Tb* bl) {
+  for (int sh = lane; sh < s.S; sh += 32) {
+    const double* nu = s.nuc4 + 4 * __ldg(s.sh_center + sh);
+    const int f = __ldg(s.sh_first + sh);
+    gto_shell<Tb, DERIV>(__ldg(s.sh_l + sh), (Tb)__ldg(s.sh_zeta + sh), s.sh_norm + 6 * sh, (Tb)(x - __ldg(nu)),
+                         (Tb)(y - __ldg(nu + 1)), (Tb)(z - __ldg(nu + 2)), bv + f, DERIV ? bx + f : nullptr,
+                         DERIV ? by + f : nullptr, DERIV ? bz + f : nullptr, DERIV ? bl + f : nullptr);
+  }
+}
+
+// e-n Jastrow/e-e Jastrow coefficient blocks as Tb
+struct PadeCoef {
+  double a1, a2, q[4];
+};
+__device__ __forceinline__ PadeCoef en_coef(const SysDev& s, int a) {
+  const double* p = s.jas_a + 6 * __ldg(s.nuc_elem + a);
+  PadeCoef c;
+  c.a1 = __ldg(p); c.a2 = __ldg(p + 1);
+  for (int q = 0; q < 4; ++q) c.q[q] = __ldg(p + 2 + q);
+  return c;
+}
+__device__ __forceinline__ PadeCoef ee_coef(const SysDev& s, bool same) {
+  PadeCoef c;
+  c.a1 = same ? s.b1_par : s.b1_anti;
+  c.a2 = __ldg(s.jas_b + 1);
+  for (int q = 0; q < 4; ++q) c.q[q] = __ldg(s.jas_b + 2 + q);
+  return c;
+}
+template <class Tb, bool DERIV>
+__device__ __forceinline__ void pade_eval(const PadeCoef& c, Tb r, Tb kap, Tb& f, Tb& df, Tb& d2f) {
+  const Tb q[4] = {(Tb)c.q[0], (Tb)c.q[1], (Tb)c.q[2], (Tb)c.q[3]};
+  pade_poly<Tb, DERIV>(r, kap, (Tb)c.a1, (Tb)c.a2, q, f, df, d2f);
+}
+
+__device__ __forceinline__ double dist3(const double* a, const double* b, double& dx, double& dy, double& dz) {
+  dx = a[0] - b[0];
+  dy = a[1] - b[1];
+  dz = a[2] - b[2];
+  return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+// Lane-group LU + inverse of every unique determinant of spin sp, from orbital values
+// Phi[(e0 + e) * ld + idx[u][o]].  Writes Binv[u], ldet[u], dsg[u] (and, if Lphi is given,
+// t[u] = tr(Binv L_occ) with L read like Phi).
+template <class Tb>
+__device__ __forceinline__ void lu_all(const SysDev& s, int sp, int lane, const Tb* Phi, const Tb* Lphi, int ld,
+                                       const int* idx, int G, double* Binv, double* scr, double* ldet, double* dsg,
+                                       double* tdet) {
+  const int n = s.n[sp], U = s.U[sp], e0 = sp ? s.Nup : 0;
+  if (n == 0) {
+    for (int u = lane; u < U; u += 32) {
+      ldet[u] = 0.0;
+      dsg[u] = 1.0;
+      if (tdet) tdet[u] = 0.0;
+    }
+    __syncwarp();
+    return;
+  }
+  const int ng = 32 / G, g = lane / G, gl = lane % G;
+  double* A = scr + g * n * n;
+  int* perm = reinterpret_cast<int*>(scr + ng * n * n) + g * n;
+  for (int u0 = 0; u0 < U; u0 += ng) {
+    const int u = u0 + g;
+    const bool act = u < U;
+    if (act)
+      for (int q = gl; q < n * n; q += G) {
+        const int e = q / n, o = q % n;
+        A[q] = (double)Phi[(e0 + e) * ld + __ldg(idx + u * n + o)];
+      }
+    __syncwarp();
+    double lg, sg;
+    double* B = Binv + (act ? u : 0) * n * n;
+    group_lu_inverse(A, B, perm, n, gl, G, act, lg, sg);
+    double t = 0.0;
+    if (tdet && act && gl < n) {
+      const int o = gl, col = __ldg(idx + u * n + o);
+      for (int e = 0; e < n; ++e) t = fma(B[o * n + e], (double)Lphi[(e0 + e) * ld + col], t);
+    }
+    t = group_sum(t, G);
+    if (act && gl == 0) {
+      ldet[u] = lg;
+      dsg[u] = sg;
+      if (tdet) tdet[u] = t;
+    }
+    __syncwarp();
+  }
+}
+
+// r_k = D_k/Phi for every determinant term and ln|Phi|, sign(Phi) (structure sum in the log
+// domain relative to the largest term, Sec. 2.1).
+__device__ __forceinline__ void term_ratios(const SysDev& s, int lane, const double* ldet, const double* dsg,
+                                            double* rk, double& lnPhi, double& sgnPhi) {
+  const int U0 = s.U[0];
+  double mx = -INFINITY;
+  for (int k = lane; k < s.nterm; k += 32) {
+    const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
+    if (dsg[a] * dsg[U0 + b] != 0.0) mx = fmax(mx, ldet[a] + ldet[U0 + b]);
+  }
+  mx = warp_max(mx);
+  double ph = 0.0;
+  for (int k = lane; k < s.nterm; k += 32) {
+    const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
+    const double sg = dsg[a] * dsg[U0 + b];
+    const double r = (sg != 0.0 && mx > -INFINITY) ? sg * exp(ldet[a] + ldet[U0 + b] - mx) : 0.0;
+    rk[k] = r;
+    ph = fma(__ldg(s.term_coef + k), r, ph);
+  }
+  ph = warp_sum(ph);
+  __syncwarp();
+  const double inv = (ph != 0.0) ? 1.0 / ph : 0.0;
+  for (int k = lane; k < s.nterm; k += 32) rk[k] *= inv;
+  __syncwarp();
+  lnPhi = (ph != 0.0) ? mx + log(fabs(ph)) : -INFINITY;
+  sgnPhi = ph > 0.0 ? 1.0 : (ph < 0.0 ? -1.0 : 0.0);
+}
+
+}  // namespace
+
+// =====================================================================================
+// Evaluation kernel
+// =====================================================================================
+template <class Tb>
+__global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLayout L, int W,
+                                                   const double* __restrict__ Rg, double* __restrict__ logpsi,
+                                                   double* __restrict__ sgn_out, double* __restrict__ eloc,
+                                                   double* __restrict__ grad, double* __restrict__ Og,
+                                                   double* __restrict__ dELg) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int wl = threadIdx.x >> 5;
+  const int w = blockIdx.x * L.wpb + wl;
+  if (w >= W) return;
+  unsigned char* base = smem + wl * L.warp_bytes;
+  double* R = reinterpret_cast<double*>(base + L.R);
+  double* vg = reinterpret_cast<double*>(base + L.vg);
+  Tb* G = reinterpret_cast<Tb*>(base + L.G);
+  Tb* LJ = reinterpret_cast<Tb*>(base + L.LJ);
+  Tb* Phi = reinterpret_cast<Tb*>(base + L.Phi);
+  Tb* Lphi = reinterpret_cast<Tb*>(base + L.Lphi);
+  Tb* Gphi = reinterpret_cast<Tb*>(base + L.Gphi);
+  double* Binv[2] = {reinterpret_cast<double*>(base + L.Binv0), reinterpret_cast<double*>(base + L.Binv1)};
+  double* ldet = reinterpret_cast<double*>(base + L.ldet);
+  double* dsg = reinterpret_cast<double*>(base + L.dsg);
+  double* tdet = reinterpret_cast<double*>(base + L.tdet);
+  double* Wdet = reinterpret_cast<double*>(base + L.Wdet);
+  double* Tdet = reinterpret_cast<double*>(base + L.Tdet);
+  double* rk = reinterpret_cast<double*>(base + L.rk);
+  unsigned char* scr = base + L.scratch;
+  double* kacc = reinterpret_cast<double*>(base + L.kacc);
+  double* red = reinterpret_cast<double*>(base + L.red);
+
+  const int N = s.N, Nn = s.Nn, Nup = s.Nup, U0 = s.U[0];
+  const Tb kap = (Tb)s.kappa;
+  for (int i = lane; i < 3 * N; i += 32) R[i] = Rg[(size_t)w * 3 * N + i];
+  __syncwarp();
+
+  // ---- A. Jastrow ln J, grad_i ln J, lap_i ln J and the potential (lane <-> electron) ----
+  double lnJ_loc = 0.0, V_loc = 0.0;
+  const Tb* cE = een_coefs<Tb>(s);
+  for (int i = lane; i < N; i += 32) {
+    const double* ri = R + 3 * i;
+    Tb g0 = 0, g1 = 0, g2 = 0, lap = 0, lnj = 0;
+    double v = 0.0;
+    for (int a = 0; a < Nn; ++a) {
+      double dx, dy, dz;
+      const double rd = dist3(ri, s.nuc4 + 4 * a, dx, dy, dz);
+      v -= __ldg(s.nuc4 + 4 * a + 3) / rd;
+      const Tb r = (Tb)rd, ir = (Tb)1 / r;
+      Tb f, df, d2f;
+      pade_eval<Tb, true>(en_coef(s, a), r, kap, f, df, d2f);
+      lnj += f;
+      g0 += df * (Tb)dx * ir; g1 += df * (Tb)dy * ir; g2 += df * (Tb)dz * ir;
+      lap += d2f + (Tb)2 * df * ir;
+    }
+    for (int j = 0; j < N; ++j) {
+      if (j == i) continue;
+      double dx, dy, dz;
+      const double rd = dist3(ri, R + 3 * j, dx, dy, dz);
+      v += 0.5 / rd;
+      const Tb r = (Tb)rd, ir = (Tb)1 / r;
+      const Tb ex = (Tb)dx * ir, ey = (Tb)dy * ir, ez = (Tb)dz * ir;
+      Tb f, df, d2f;
+      pade_eval<Tb, true>(ee_coef(s, (i < Nup) == (j < Nup)), r, kap, f, df, d2f);
+      lnj += (Tb)0.5 * f;
+      g0 += df * ex; g1 += df * ey; g2 += df * ez;
+      lap += d2f + (Tb)2 * df * ir;
+      if (s.een_on) {
+        const Tb u = (Tb)1 / ((Tb)1 + kap * r);
+        const Tb du = -kap * u * u, d2u = (Tb)2 * kap * kap * u * u * u;
+        for (int a = 0; a < Nn; ++a) {
+          double ax, ay, az, bx, by, bz;
+          const double ria = dist3(ri, s.nuc4 + 4 * a, ax, ay, az);
+          const double rja = dist3(R + 3 * j, s.nuc4 + 4 * a, bx, by, bz);
+          const Tb ira = (Tb)1 / (Tb)ria;
+          const Tb sv = (Tb)1 / ((Tb)1 + kap * (Tb)ria), tv = (Tb)1 / ((Tb)1 + kap * (Tb)rja);
+          const Tb ds = -kap * sv * sv, d2s = (Tb)2 * kap * kap * sv * sv * sv;
+          Tb F, Fu, Fs, Fuu, Fss, Fus;
+          een_partials_us<Tb>(cE + kNeen * __ldg(s.nuc_elem + a), u, sv, tv, F, Fu, Fs, Fuu, Fss, Fus);
+          const Tb fx = (Tb)ax * ira, fy = (Tb)ay * ira, fz = (Tb)az * ira;
+          const Tb A = Fu * du, B = Fs * ds;
+          lnj += (Tb)0.5 * F;
+          g0 += A * ex + B * fx; g1 += A * ey + B * fy; g2 += A * ez + B * fz;
+          lap += Fuu * du * du + Fu * (d2u + (Tb)2 * du * ir) + Fss * ds * ds + Fs * (d2s + (Tb)2 * ds * ira) +
+                 (Tb)2 * Fus * du * ds * (ex * fx + ey * fy + ez * fz);
+        }
+      }
+    }
+    G[3 * i] = g0; G[3 * i + 1] = g1; G[3 * i + 2] = g2;
+    LJ[i] = lap;
+    lnJ_loc += (double)lnj;
+    V_loc += v;
+  }
+  const double lnJ = warp_sum(lnJ_loc);
+  const double V = warp_sum(V_loc) + s.vnn;
+  __syncwarp();
+
+  // ---- B. orbitals phi, grad phi, dressed Laplacian L = lap phi + 2 grad lnJ . grad phi ----
+  const int nev = s.n_ev, nevd = s.n_ev_det, M = s.M;
+  {
+    Tb* bv = reinterpret_cast<Tb*>(scr);
+    Tb* bx = bv + M;
+    Tb* by = bx + M;
+    Tb* bz = by + M;
+    Tb* bl = bz + M;
+    const Tb* cf = orb_coefs<Tb>(s);
+    for (int e = 0; e < N; ++e) {
+      basis_at<Tb, true>(s, lane, R[3 * e], R[3 * e + 1], R[3 * e + 2], bv, bx, by, bz, bl);
+      __syncwarp();
+      const Tb G0 = G[3 * e], G1 = G[3 * e + 1], G2 = G[3 * e + 2];
+      for (int q = lane; q < nev; q += 32) {
+        const int k = __ldg(s.ev_orb + q);
+        const int lo = __ldg(s.orb_lo + k), hi = __ldg(s.orb_hi + k);
+        const Tb* c = cf + __ldg(s.orb_off + k) - lo;
+        Tb v = 0, x = 0, y = 0, z = 0, lp = 0;
+        for (int mu = lo; mu < hi; ++mu) {
+          const Tb cm = __ldg(c + mu);
+          v += cm * bv[mu]; x += cm * bx[mu]; y += cm * by[mu]; z += cm * bz[mu]; lp += cm * bl[mu];
+        }
+        Phi[e * nev + q] = v;
+        Lphi[e * nev + q] = lp + (Tb)2 * (G0 * x + G1 * y + G2 * z);
+        if (q < nevd) {
+          Gphi[(e * nevd + q) * 3] = x;
+          Gphi[(e * nevd + q) * 3 + 1] = y;
+          Gphi[(e * nevd + q) * 3 + 2] = z;
+        }
+      }
+      __syncwarp();
+    }
+  }
+
+  // ---- C. Slater matrices: LU, inverses, ln|det|, t_u = tr(A^-1 L) ----
+  lu_all<Tb>(s, 0, lane, Phi, Lphi, nev, s.det_ev[0], L.G0, Binv[0], reinterpret_cast<double*>(scr), ldet, dsg, tdet);
+  lu_all<Tb>(s, 1, lane, Phi, Lphi, nev, s.det_ev[1], L.G1, Binv[1], reinterpret_cast<double*>(scr), ldet + U0,
+             dsg + U0, tdet + U0);
+  double lnPhi, sgnPhi;
+  term_ratios(s, lane, ldet, dsg, rk, lnPhi, sgnPhi);
+  // marginal weights W_u = sum_{k contains u} w_k and T_u = sum_{k contains u} w_k t_k
+  double kphi = 0.0;
+  for (int k = lane; k < s.nterm; k += 32) {
+    const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
+    kphi += __ldg(s.term_coef + k) * rk[k] * (tdet[a] + tdet[U0 + b]);
+  }
+  kphi = warp_sum(kphi);
+  const int Utot = U0 + s.U[1];
+  for (int ud = lane; ud < Utot; ud += 32) {
+    const int sp = ud >= U0 ? 1 : 0, u = ud - (sp ? U0 : 0);
+    double Wv = 0.0, Tv = 0.0;
+    for (int k = 0; k < s.nterm; ++k) {
+      const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
+      if ((sp ? b : a) != u) continue;
+      const double wk = __ldg(s.term_coef + k) * rk[k];
+      Wv += wk;
+      Tv += wk * (tdet[a] + tdet[U0 + b]);
+    }
+    Wdet[ud] = Wv;
+    Tdet[ud] = Tv;
+  }
+  __syncwarp();
+  // grad_i ln|Psi| = grad_i lnJ + sum_u W_u sum_o Binv_u[o][i] grad phi_o(r_i)
+  double kin_loc = 0.0;
+  for (int e = lane; e < N; e += 32) {
+    const int sp = e >= Nup ? 1 : 0, ie = e - (sp ? Nup : 0), n = s.n[sp], uo = sp ? U0 : 0;
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int u = 0; u < s.U[sp]; ++u) {
+      const double* B = Binv[sp] + u * n * n;
+      double ax = 0.0, ay = 0.0, az = 0.0;
+      for (int o = 0; o < n; ++o) {
+        const double b = B[o * n + ie];
+        const Tb* gp = Gphi + (e * nevd + __ldg(s.det_ev[sp] + u * n + o)) * 3;
+        ax = fma(b, (double)gp[0], ax);
+        ay = fma(b, (double)gp[1], ay);
+        az = fma(b, (double)gp[2], az);
+      }
+      const double Wu = Wdet[uo + u];
+      gx = fma(Wu, ax, gx);
+      gy = fma(Wu, ay, gy);
+      gz = fma(Wu, az, gz);
+    }
+    const double G0 = (double)G[3 * e], G1 = (double)G[3 * e + 1], G2 = (double)G[3 * e + 2];
+    vg[3 * e] = G0 + gx;
+    vg[3 * e + 1] = G1 + gy;
+    vg[3 * e + 2] = G2 + gz;
+    kin_loc += (double)LJ[e] + G0 * G0 + G1 * G1 + G2 * G2;
+  }
+  const double kin = warp_sum(kin_loc) + kphi;
+  const double EL = -0.5 * kin + V;
+  __syncwarp();
+  if (lane == 0) {
+    logpsi[w] = lnJ + lnPhi;
+    sgn_out[w] = sgnPhi;
+    eloc[w] = EL;
+  }
+  if (grad)
+    for (int q = lane; q < 3 * N; q += 32) grad[(size_t)w * 3 * N + q] = vg[q];
+  if (!Og) return;
+
+  // ---- D. parameter derivatives ----
+  const int P = s.P;
+  double* Ow = Og + (size_t)w * P;
+  double* Ew = dELg ? dELg + (size_t)w * P : nullptr;
+  // D1. structure coefficients: O_I = Phi_I/Phi, E_L,I = -1/2 (K[Phi_I] - O_I K[Phi])
+  for (int q = lane; q < s.n_cparam; q += 32) {
+    const int I = __ldg(s.cparam + q);
+    double o = 0.0, kk = 0.0;
+    for (int t = 0; t < s.nsterm; ++t) {
+      if (__ldg(s.sterm_I + t) != I) continue;
+      const int k = __ldg(s.sterm_k + t);
+      const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
+      const double r = __ldg(s.sterm_d + t) * rk[k];
+      o += r;
+      kk += r * (tdet[a] + tdet[U0 + b]);
+    }
+    Ow[q] = o;
+    if (Ew) Ew[q] = -0.5 * (kk - o * kphi);
+  }
+  // D2. Jastrow parameters: O = d lnJ/d alpha, E_L,alpha = -1/2 sum_i (lap_i g + 2 grad_i g . grad_i ln|Psi|)
+  if (s.jas_param) {
+    // e-n: a_2..a_6 per element (lane <-> electron)
+    for (int E = 0; E < s.n_elem; ++E) {
+      double aO[5] = {0, 0, 0, 0, 0}, aE[5] = {0, 0, 0, 0, 0};
+      for (int i = lane; i < N; i += 32) {
+        for (int a = 0; a < Nn; ++a) {
+          if (__ldg(s.nuc_elem + a) != E) continue;
+          double dx, dy, dz;
+          const double r = dist3(R + 3 * i, s.nuc4 + 4 * a, dx, dy, dz);
+          const PadeCoef c = en_coef(s, a);
+          const double den = 1.0 / (1.0 + s.kappa * r), Rr = r * den, dR = den * den,
+                       d2R = -2.0 * s.kappa * dR * den;
+          const double cosv = (dx * vg[3 * i] + dy * vg[3 * i + 1] + dz * vg[3 * i + 2]) / r;
+          const double pd = 1.0 / (1.0 + c.a2 * Rr);
+          double h[5], hR[5], hRR[5];
+          h[0] = -c.a1 * Rr * Rr * pd * pd;
+          hR[0] = -2.0 * c.a1 * Rr * pd * pd * pd;
+          hRR[0] = -2.0 * c.a1 * (1.0 - 2.0 * c.a2 * Rr) * pd * pd * pd * pd;
+          double Rm2 = 1.0;  // R^(p-2)
+          for (int p = 2; p <= 5; ++p) {
+            h[p - 1] = Rm2 * Rr * Rr;
+            hR[p - 1] = p * Rm2 * Rr;
+            hRR[p - 1] = p * (p - 1) * Rm2;
+            Rm2 *= Rr;
+          }
+          for (int q = 0; q < 5; ++q) {
+            const double g1 = hR[q] * dR, g2 = hRR[q] * dR * dR + hR[q] * d2R;
+            aO[q] += h[q];
+            aE[q] += -0.5 * (g2 + 2.0 * g1 / r + 2.0 * g1 * cosv);
+          }
+        }
+      }
+      for (int q = 0; q < 5; ++q) {
+        const double o = warp_sum(aO[q]), e = warp_sum(aE[q]);
+        if (lane == 0) {
+          Ow[s.p_off_a + 5 * E + q] = o;
+          if (Ew) Ew[s.p_off_a + 5 * E + q] = e;
+        }
+      }
+    }
+    // e-e: b_2..b_6 (lane <-> pair)
+    {
+      double bO[5] = {0, 0, 0, 0, 0}, bE[5] = {0, 0, 0, 0, 0};
+      const int npair = N * (N - 1) / 2;
+      for (int pp = lane; pp < npair; pp += 32) {
+        int i = 0, rem = pp;
+        while (rem >= N - 1 - i) { rem -= N - 1 - i; ++i; }
+        const int j = i + 1 + rem;
+        double dx, dy, dz;
+        const double r = dist3(R + 3 * i, R + 3 * j, dx, dy, dz);
+        const PadeCoef c = ee_coef(s, (i < Nup) == (j < Nup));
+        const double den = 1.0 / (1.0 + s.kappa * r), Rr = r * den, dR = den * den, d2R = -2.0 * s.kappa * dR * den;
+        const double cosv = (dx * (vg[3 * i] - vg[3 * j]) + dy * (vg[3 * i + 1] - vg[3 * j + 1]) +
+                             dz * (vg[3 * i + 2] - vg[3 * j + 2])) / r;
+        const double pd = 1.0 / (1.0 + c.a2 * Rr);
+        double h[5], hR[5], hRR[5];
+        h[0] = -c.a1 * Rr * Rr * pd * pd;
+        hR[0] = -2.0 * c.a1 * Rr * pd * pd * pd;
+        hRR[0] = -2.0 * c.a1 * (1.0 - 2.0 * c.a2 * Rr) * pd * pd * pd * pd;
+        double Rm2 = 1.0;  // R^(p-2)
+        for (int p = 2; p <= 5; ++p) {
+          h[p - 1] = Rm2 * Rr * Rr;
+          hR[p - 1] = p * Rm2 * Rr;
+          hRR[p - 1] = p * (p - 1) * Rm2;
+          Rm2 *= Rr;
+        }
+        for (int q = 0; q < 5; ++q) {
+          const double g1 = hR[q] * dR, g2 = hRR[q] * dR * dR + hR[q] * d2R;
+          bO[q] += h[q];
+          bE[q] += -0.5 * (2.0 * (g2 + 2.0 * g1 / r) + 2.0 * g1 * cosv);
+        }
+      }
+      for (int q = 0; q < 5; ++q) {
+        const double o = warp_sum(bO[q]), e = warp_sum(bE[q]);
+        if (lane == 0) {
+          Ow[s.p_off_b + q] = o;
+          if (Ew) Ew[s.p_off_b + q] = e;
+        }
+      }
+    }
+    // e-e-n: raw terms per element (lane <-> pair), then theta = B^T raw
+    if (s.een_on) {
+      double* rawO = red;               // [23]
+      double* rawE = red + kNeen;       // [23]
+      const int npair = N * (N - 1) / 2;
+      for (int E = 0; E < s.n_elem; ++E) {
+        Tb accO[kNeen], accE[kNeen];
+#pragma unroll
+        for (int q = 0; q < kNeen; ++q) accO[q] = accE[q] = (Tb)0;
+        for (int pp = lane; pp < npair; pp += 32) {
+          int i = 0, rem = pp;
+          while (rem >= N - 1 - i) { rem -= N - 1 - i; ++i; }
+          const int j = i + 1 + rem;
+          double dx, dy, dz;
+          const double rij = dist3(R + 3 * i, R + 3 * j, dx, dy, dz);
+          const Tb irij = (Tb)(1.0 / rij);
+          const Tb ex = (Tb)dx * irij, ey = (Tb)dy * irij, ez = (Tb)dz * irij;
+          const Tb u = (Tb)1 / ((Tb)1 + kap * (Tb)rij), du = -kap * u * u, d2u = (Tb)2 * kap * kap * u * u * u;
+          const Tb vix = (Tb)vg[3 * i], viy = (Tb)vg[3 * i + 1], viz = (Tb)vg[3 * i + 2];
+          const Tb vjx = (Tb)vg[3 * j], vjy = (Tb)vg[3 * j + 1], vjz = (Tb)vg[3 * j + 2];
+          const Tb e_vi = ex * vix + ey * viy + ez * viz, e_vj = ex * vjx + ey * vjy + ez * vjz;
+          for (int a = 0; a < Nn; ++a) {
+            if (__ldg(s.nuc_elem + a) != E) continue;
+            double ax, ay, az, bx, by, bz;
+            const double ria = dist3(R + 3 * i, s.nuc4 + 4 * a, ax, ay, az);
+            const double rja = dist3(R + 3 * j, s.nuc4 + 4 * a, bx, by, bz);
+            const Tb iria = (Tb)(1.0 / ria), irja = (Tb)(1.0 / rja);
+            const Tb fx = (Tb)ax * iria, fy = (Tb)ay * iria, fz = (Tb)az * iria;
+            const Tb hx = (Tb)bx * irja, hy = (Tb)by * irja, hz = (Tb)bz * irja;
+            const Tb sv = (Tb)1 / ((Tb)1 + kap * (Tb)ria), tv = (Tb)1 / ((Tb)1 + kap * (Tb)rja);
+            const Tb ds = -kap * sv * sv, d2s = (Tb)2 * kap * kap * sv * sv * sv;
+            const Tb dt = -kap * tv * tv, d2t = (Tb)2 * kap * kap * tv * tv * tv;
+            const Tb f_vi = fx * vix + fy * viy + fz * viz, h_vj = hx * vjx + hy * vjy + hz * vjz;
+            const Tb e_f = ex * fx + ey * fy + ez * fz, e_h = ex * hx + ey * hy + ez * hz;
+            Pow6<Tb> Up, Sp, Tp;
+            Up.set(u); Sp.set(sv); Tp.set(tv);
+            een_for_each([&](int q, int k, int l, int m) {
+              const Tb f = Sp.p(l + m) * Tp.p(m) + Sp.p(m) * Tp.p(l + m);
+              const Tb fs = Sp.d(l + m) * Tp.p(m) + Sp.d(m) * Tp.p(l + m);
+              const Tb fss = Sp.dd(l + m) * Tp.p(m) + Sp.dd(m) * Tp.p(l + m);
+              const Tb ft = Sp.p(l + m) * Tp.d(m) + Sp.p(m) * Tp.d(l + m);
+              const Tb ftt = Sp.p(l + m) * Tp.dd(m) + Sp.p(m) * Tp.dd(l + m);
+              const Tb T0 = Up.p(k) * f, Tu = Up.d(k) * f, Tuu = Up.dd(k) * f;
+              const Tb Ts = Up.p(k) * fs, Tss = Up.p(k) * fss, Tus = Up.d(k) * fs;
+              const Tb Tt = Up.p(k) * ft, Ttt = Up.p(k) * ftt, Tut = Up.d(k) * ft;
+              const Tb radial_u = Tuu * du * du + Tu * (d2u + (Tb)2 * du * irij);
+              const Tb lap_i = radial_u + Tss * ds * ds + Ts * (d2s + (Tb)2 * ds * iria) + (Tb)2 * Tus * du * ds * e_f;
+              const Tb lap_j = radial_u + Ttt * dt * dt + Tt * (d2t + (Tb)2 * dt * irja) - (Tb)2 * Tut * du * dt * e_h;
+              const Tb gdot = Tu * du * (e_vi - e_vj) + Ts * ds * f_vi + Tt * dt * h_vj;
+              accO[q] += T0;
+              accE[q] += (Tb)-0.5 * (lap_i + lap_j + (Tb)2 * gdot);
+            });
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kNeen; ++q) {
+          const double o = warp_sum((double)accO[q]), e = warp_sum((double)accE[q]);
+          if (lane == 0) {
+            rawO[q] = o;
+            rawE[q] = e;
+          }
+        }
+        __syncwarp();
+        for (int f = lane; f < kNfree; f += 32) {
+          double o = 0.0, e = 0.0;
+          for (int q = 0; q < kNeen; ++q) {
+            const double b = __ldg(s.een_B + q * kNfree + f);
+            o = fma(b, rawO[q], o);
+            e = fma(b, rawE[q], e);
+          }
+          Ow[s.p_off_theta + kNfree * E + f] = o;
+          if (Ew) Ew[s.p_off_theta + kNfree * E + f] = e;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  // D3. orbital excitations kappa_kl (Sec. 2.2): for determinant u with l at slot o_l and
+  //   k unoccupied, x_u = (A^-1 Phi)[o_l][k] = d ln D_u, y_u = (A^-1 L)[o_l][k] -
+  //   sum_o' (A^-1 L)[o_l][occ o'] (A^-1 Phi)[o'][k] = d t_u; O = sum_u W_u x_u,
+  //   K[Phi_kappa] = sum_u (T_u x_u + W_u y_u), E_L,kappa = -1/2 (K[Phi_kappa] - O K[Phi]).
+  if (s.n_kappa > 0) {
+    const int nk = s.n_kappa;
+    for (int q = lane; q < 2 * nk; q += 32) kacc[q] = 0.0;
+    __syncwarp();
+    Tb* X = reinterpret_cast<Tb*>(scr);
+    for (int sp = 0; sp < 2; ++sp) {
+      const int n = s.n[sp], e0 = sp ? Nup : 0, uo = sp ? U0 : 0;
+      if (n == 0) continue;
+      Tb* Y = X + n * nev;
+      for (int u = 0; u < s.U[sp]; ++u) {
+        const int eb = __ldg(s.kap_off[sp] + u), ee = __ldg(s.kap_off[sp] + u + 1);
+        if (eb == ee) continue;
+        const double* B = Binv[sp] + u * n * n;
+        for (int q = lane; q < n * nev; q += 32) {
+          const int o = q / nev, c = q % nev;
+          Tb x = 0, y = 0;
+          for (int e = 0; e < n; ++e) {
+            const Tb b = (Tb)B[o * n + e];
+            x += b * Phi[(e0 + e) * nev + c];
+            y += b * Lphi[(e0 + e) * nev + c];
+          }
+          X[q] = x;
+          Y[q] = y;
+        }
+        __syncwarp();
+        const double Wu = Wdet[uo + u], Tu = Tdet[uo + u];
+        for (int t = eb + lane; t < ee; t += 32) {
+          const int j = __ldg(s.kap_ent[sp] + 4 * t), ol = __ldg(s.kap_ent[sp] + 4 * t + 1),
+                    kc = __ldg(s.kap_ent[sp] + 4 * t + 2);
+          const Tb x = X[ol * nev + kc];
+          Tb y = Y[ol * nev + kc];
+          for (int o2 = 0; o2 < n; ++o2) y -= Y[ol * nev + __ldg(s.det_ev[sp] + u * n + o2)] * X[o2 * nev + kc];
+          kacc[j] += Wu * (double)x;
+          kacc[nk + j] += Tu * (double)x + Wu * (double)y;
+        }
+        __syncwarp();
+      }
+    }
+    for (int j = lane; j < nk; j += 32) {
+      const double o = kacc[j];
+      Ow[s.p_off_kappa + j] = o;
+      if (Ew) Ew[s.p_off_kappa + j] = -0.5 * (kacc[nk + j] - o * kphi);
+    }
+  }
+}
+
+// =====================================================================================
+// VMC sweep kernel
+// =====================================================================================
+template <class Tb>
+__global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepLayout L, int W, double* __restrict__ Rg,
+                                                    int nsweeps, double step, uint64_t seed, uint32_t step0,
+                                                    uint32_t tag, uint32_t woff, int* __restrict__ nacc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int wl = threadIdx.x >> 5;
+  const int w = blockIdx.x * L.wpb + wl;
+  if (w >= W) return;
+  unsigned char* base = smem + wl * L.warp_bytes;
+  double* R = reinterpret_cast<double*>(base + L.R);
+  double* Binv[2] = {reinterpret_cast<double*>(base + L.Binv0), reinterpret_cast<double*>(base + L.Binv1)};
+  double* ldet = reinterpret_cast<double*>(base + L.ldet);
+  double* dsg = reinterpret_cast<double*>(base + L.dsg);
+  double* wk = reinterpret_cast<double*>(base + L.wk);
+  Tb* PhiO = reinterpret_cast<Tb*>(base + L.PhiO);
+  Tb* bas = reinterpret_cast<Tb*>(base + L.bas);
+  Tb* vrow = reinterpret_cast<Tb*>(base + L.vrow);
+  double* rho = reinterpret_cast<double*>(base + L.rho);
+  double* cvec = reinterpret_cast<double*>(base + L.cvec);
+  double* scr = reinterpret_cast<double*>(base + L.scratch);
+
+  const int N = s.N, Nn = s.Nn, Nup = s.Nup, U0 = s.U[0], ldo = L.nocc_max;
+  const Tb kap = (Tb)s.kappa;
+  const Tb* cf = orb_coefs<Tb>(s);
+  const Tb* cE = een_coefs<Tb>(s);
+  for (int i = lane; i < 3 * N; i += 32) R[i] = Rg[(size_t)w * 3 * N + i];
+  __syncwarp();
+  int accepted = 0;
+  const uint32_t wid = woff + (uint32_t)w;
+
+  for (int sw = 0; sw < nsweeps; ++sw) {
+    // orbital values of every electron, then LU of every unique determinant (refresh)
+    for (int e = 0; e < N; ++e) {
+      const int sp = e >= Nup ? 1 : 0;
+      basis_at<Tb, false>(s, lane, R[3 * e], R[3 * e + 1], R[3 * e + 2], bas, nullptr, nullptr, nullptr, nullptr);
+      __syncwarp();
+      for (int q = lane; q < s.nocc[sp]; q += 32) {
+        const int k = __ldg(s.occ_list[sp] + q);
+        const int lo = __ldg(s.orb_lo + k), hi = __ldg(s.orb_hi + k);
+        const Tb* c = cf + __ldg(s.orb_off + k) - lo;
+        Tb v = 0;
+        for (int mu = lo; mu < hi; ++mu) v += __ldg(c + mu) * bas[mu];
+        PhiO[e * ldo + q] = v;
+      }
+      __syncwarp();
+    }
+    lu_all<Tb>(s, 0, lane, PhiO, nullptr, ldo, s.det_loc[0], L.G0, Binv[0], scr, ldet, dsg, nullptr);
+    lu_all<Tb>(s, 1, lane, PhiO, nullptr, ldo, s.det_loc[1], L.G1, Binv[1], scr, ldet + U0, dsg + U0, nullptr);
+    {
+      double lnPhi, sgnPhi;
+      term_ratios(s, lane, ldet, dsg, wk, lnPhi, sgnPhi);
+      for (int k = lane; k < s.nterm; k += 32) wk[k] *= __ldg(s.term_coef + k);  // w_k = C_k D_k / Phi
+      __syncwarp();
+    }
+    const uint32_t st = step0 + (uint32_t)sw;
+    for (int e = 0; e < N; ++e) {
+      const int sp = e >= Nup ? 1 : 0, ie = e - (sp ? Nup : 0), n = s.n[sp], G = sp ? L.G1 : L.G0;
+      double u0, u1, u2, uacc;
+      uniforms2(seed, wid, st, (uint32_t)e, tag, 0, u0, u1);
+      uniforms2(seed, wid, st, (uint32_t)e, tag, 1, u2, uacc);
+      double rn[3];
+      rn[0] = __dadd_rn(R[3 * e], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u0), 1.0)));
+      rn[1] = __dadd_rn(R[3 * e + 1], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u1), 1.0)));
+      rn[2] = __dadd_rn(R[3 * e + 2], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u2), 1.0)));
+      // orbital row at the proposed position
+      basis_at<Tb, false>(s, lane, rn[0], rn[1], rn[2], bas, nullptr, nullptr, nullptr, nullptr);
+      __syncwarp();
+      for (int q = lane; q < s.nocc[sp]; q += 32) {
+        const int k = __ldg(s.occ_list[sp] + q);
+        const int lo = __ldg(s.orb_lo + k), hi = __ldg(s.orb_hi + k);
+        const Tb* c = cf + __ldg(s.orb_off + k) - lo;
+        Tb v = 0;
+        for (int mu = lo; mu < hi; ++mu) v += __ldg(c + mu) * bas[mu];
+        vrow[q] = v;
+      }
+      __syncwarp();
+      // determinant ratios rho_u = sum_o v_occ(o) Binv_u[o][ie]
+      const int U = s.U[sp], ng = 32 / G, g = lane / G, gl = lane % G;
+      const int* dl = s.det_loc[sp];
+      for (int ub = 0; ub < U; ub += ng) {
+        const int u = ub + g;
+        double r = 0.0;
+        if (u < U && gl < n) r = (double)vrow[__ldg(dl + u * n + gl)] * Binv[sp][u * n * n + gl * n + ie];
+        r = group_sum(r, G);
+        if (u < U && gl == 0) rho[u] = r;
+      }
+      __syncwarp();
+      double rphi = 0.0;
+      for (int k = lane; k < s.nterm; k += 32) rphi += wk[k] * rho[__ldg(s.term_det + 2 * k + sp)];
+      rphi = warp_sum(rphi);
+      // Jastrow change of the terms that involve electron e
+      Tb dj = 0;
+      const double* ro = R + 3 * e;
+      for (int j = lane; j < N; j += 32) {
+        if (j == e) continue;
+        double dx, dy, dz;
+        const double r_old = dist3(ro, R + 3 * j, dx, dy, dz);
+        const double r_new = dist3(rn, R + 3 * j, dx, dy, dz);
+        const PadeCoef c = ee_coef(s, (e < Nup) == (j < Nup));
+        Tb f1, f0, t0, t1;
+        pade_eval<Tb, false>(c, (Tb)r_new, kap, f1, t0, t1);
+        pade_eval<Tb, false>(c, (Tb)r_old, kap, f0, t0, t1);
+        dj += f1 - f0;
+        if (s.een_on) {
+          const Tb un = (Tb)1 / ((Tb)1 + kap * (Tb)r_new), uo = (Tb)1 / ((Tb)1 + kap * (Tb)r_old);
+          for (int a = 0; a < Nn; ++a) {
+            const double ran = dist3(rn, s.nuc4 + 4 * a, dx, dy, dz);
+            const double rao = dist3(ro, s.nuc4 + 4 * a, dx, dy, dz);
+            const double rja = dist3(R + 3 * j, s.nuc4 + 4 * a, dx, dy, dz);
+            const Tb tv = (Tb)1 / ((Tb)1 + kap * (Tb)rja);
+            const Tb* cc = cE + kNeen * __ldg(s.nuc_elem + a);
+            dj += een_value<Tb>(cc, un, (Tb)1 / ((Tb)1 + kap * (Tb)ran), tv) -
+                  een_value<Tb>(cc, uo, (Tb)1 / ((Tb)1 + kap * (Tb)rao), tv);
+          }
+        }
+      }
+      for (int a = lane; a < Nn; a += 32) {
+        double dx, dy, dz;
+        const double r_new = dist3(rn, s.nuc4 + 4 * a, dx, dy, dz);
+        const double r_old = dist3(ro, s.nuc4 + 4 * a, dx, dy, dz);
+        const PadeCoef c = en_coef(s, a);
+        Tb f1, f0, t0, t1;
+        pade_eval<Tb, false>(c, (Tb)r_new, kap, f1, t0, t1);
+        pade_eval<Tb, false>(c, (Tb)r_old, kap, f0, t0, t1);
+        dj += f1 - f0;
+      }
+      const double dJ = warp_sum((double)dj);
+      const double prob = rphi * rphi * exp(2.0 * dJ);
+      if (uacc < prob) {
+        // Sherman-Morrison: Binv <- Binv - Binv[:, ie] (v^T Binv - e_ie^T) / rho
+        for (int ub = 0; ub < U; ub += ng) {
+          const int u = ub + g;
+          const bool act = u < U;
+          double* B = Binv[sp] + (act ? u : 0) * n * n;
+          double* cv = cvec + g * n;
+          if (act && gl < n) cv[gl] = B[gl * n + ie];
+          __syncwarp();
+          if (act && gl < n) {
+            const int j = gl;
+            double wj = (j == ie) ? -1.0 : 0.0;
+            for (int o = 0; o < n; ++o) wj = fma((double)vrow[__ldg(dl + u * n + o)], B[o * n + j], wj);
+            const double f = wj / rho[u];
+            for (int o = 0; o < n; ++o) B[o * n + j] = fma(-cv[o], f, B[o * n + j]);
+          }
+          __syncwarp();
+        }
+        const double irphi = 1.0 / rphi;
+        for (int k = lane; k < s.nterm; k += 32) wk[k] *= rho[__ldg(s.term_det + 2 * k + sp)] * irphi;
+        if (lane < 3) R[3 * e + lane] = rn[lane];
+        ++accepted;
+      }
+      __syncwarp();
+    }
+  }
+  for (int i = lane; i < 3 * N; i += 32) Rg[(size_t)w * 3 * N + i] = R[i];
+  if (nacc && lane == 0) nacc[w] += accepted;
+}
+
+// =====================================================================================
+// layouts and launchers
+// =====================================================================================
+int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
+  int off = 0;
+  auto take = [&](int bytes) {
+    const int o = off;
+    off = align16(off + bytes);
+    return o;
+  };
+  const int N = s.N, Ut = s.U[0] + s.U[1];
+  L.G0 = group_size(s.n[0]);
+  L.G1 = group_size(s.n[1]);
+  L.R = take(8 * 3 * N);
+  L.vg = take(8 * 3 * N);
+  L.G = take(tb * 3 * N);
+  L.LJ = take(tb * N);
+  L.Phi = take(tb * N * s.n_ev);
+  L.Lphi = take(tb * N * s.n_ev);
+  L.Gphi = take(tb * N * s.n_ev_det * 3);
+  L.Binv0 = take(8 * s.U[0] * s.n[0] * s.n[0]);
+  L.Binv1 = take(8 * s.U[1] * s.n[1] * s.n[1]);
+  L.ldet = take(8 * Ut);
+  L.dsg = take(8 * Ut);
+  L.tdet = take(8 * Ut);
+  L.Wdet = take(8 * Ut);
+  L.Tdet = take(8 * Ut);
+  L.rk = take(8 * s.nterm);
+  int scr = 5 * s.M * tb;
+  for (int sp = 0; sp < 2; ++sp) {
+    const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
+    scr = std::max(scr, ng * (8 * n * n + 4 * n) + 16);
+    scr = std::max(scr, 2 * n * s.n_ev * tb);
+  }
+  L.scratch = take(scr);
+  L.kacc = take(8 * 2 * std::max(s.n_kappa, 1));
+  L.red = take(8 * 64);
+  L.warp_bytes = off;
+  int wpb = max_smem / off;
+  if (wpb > 16) wpb = 16;
+  if (wpb < 1) return VBQMC_ERR_CAPACITY;
+  L.wpb = wpb;
+  return VBQMC_OK;
+}
+
+int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
+  int off = 0;
+  auto take = [&](int bytes) {
+    const int o = off;
+    off = align16(off + bytes);
+    return o;
+  };
+  const int N = s.N, Ut = s.U[0] + s.U[1];
+  L.G0 = group_size(s.n[0]);
+  L.G1 = group_size(s.n[1]);
+  L.nocc_max = std::max(std::max(s.nocc[0], s.nocc[1]), 1);
+  L.R = take(8 * 3 * N);
+  L.Binv0 = take(8 * s.U[0] * s.n[0] * s.n[0]);
+  L.Binv1 = take(8 * s.U[1] * s.n[1] * s.n[1]);
+  L.ldet = take(8 * Ut);
+  L.dsg = take(8 * Ut);
+  L.wk = take(8 * s.nterm);
+  L.PhiO = take(tb * N * L.nocc_max);
+  L.bas = take(tb * s.M);
+  L.vrow = take(tb * L.nocc_max);
+  L.rho = take(8 * std::max(s.U[0], s.U[1]));
+  int cv = 0, scr = 0;
+  for (int sp = 0; sp < 2; ++sp) {
+    const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
+    cv = std::max(cv, 8 * ng * n);
+    scr = std::max(scr, ng * (8 * n * n + 4 * n) + 16);
+  }
+  L.cvec = take(std::max(cv, 8));
+  L.scratch = take(std::max(scr, 16));
+  L.warp_bytes = off;
+  int wpb = max_smem / off;
+  if (wpb > 16) wpb = 16;
+  if (wpb < 1) return VBQMC_ERR_CAPACITY;
+  L.wpb = wpb;
+  return VBQMC_OK;
+}
+
+template <class Tb>
+static cudaError_t launch_eval_t(const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
+                                 double* sign, double* eloc, double* grad, double* O, double* dEL, cudaStream_t st) {
+  const int smem = L.wpb * L.warp_bytes;
+  cudaError_t e = cudaFuncSetAttribute(eval_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int blocks = (W + L.wpb - 1) / L.wpb;
+  eval_kernel<Tb><<<blocks, 32 * L.wpb, smem, st>>>(s, L, W, R, logpsi, sign, eloc, grad, O, dEL);
+  return cudaGetLastError();
+}
+
+template <class Tb>
+static cudaError_t launch_sweep_t(const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps, double step,
+                                  uint64_t seed, uint32_t step0, uint32_t tag, uint32_t woff, int* nacc,
+                                  cudaStream_t st) {
+  const int smem = L.wpb * L.warp_bytes;
+  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int blocks = (W + L.wpb - 1) / L.wpb;
+  sweep_kernel<Tb><<<blocks, 32 * L.wpb, smem, st>>>(s, L, W, R, nsweeps, step, seed, step0, tag, woff, nacc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval(int precision, const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
+                        double* sign, double* eloc, double* grad, double* O, double* dEL, cudaStream_t st) {
+  if (precision == VBQMC_MIXED) return launch_eval_t<float>(s, L, W, R, logpsi, sign, eloc, grad, O, dEL, st);
+  return launch_eval_t<double>(s, L, W, R, logpsi, sign, eloc, grad, O, dEL, st);
+}
+
+cudaError_t launch_sweep(int precision, const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps,
+                         double step, uint64_t seed, uint32_t step0, uint32_t tag, uint32_t woff, int* nacc,
+                         cudaStream_t st) {
+  if (precision == VBQMC_MIXED) return launch_sweep_t<float>(s, L, W, R, nsweeps, step, seed, step0, tag, woff, nacc, st);
+  return launch_sweep_t<double>(s, L, W, R, nsweeps, step, seed, step0, tag, woff, nacc, st);
+}
+
+}  // namespace vbq

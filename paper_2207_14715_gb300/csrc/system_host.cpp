@@ -1,0 +1,381 @@
+// Host-side set-up of a JVB system: validation, basis normalisation, HLSP structure
+// expansion into determinants (arXiv:2207.14715, Sec. 2.1, Eq. PhiI and the expansion
+// after it), the cusp-preserving e-e-n parametrisation (Sec. 2.1, last paragraph) and the
+// orbital-excitation tables (Sec. 2.2).
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <sstream>
+
+#include "vbqmc_internal.h"
+
+namespace vbq {
+
+static const int kNcomp[3] = {1, 3, 6};
+static const int kCart[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                                 {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+static const int kCartOff[3] = {0, 1, 4};
+
+std::vector<EenTerm> een_term_list() {
+  std::vector<EenTerm> t;
+  for (int p = 2; p <= 5; ++p)
+    for (int k = 0; k < p; ++k) {
+      const int lmax = k ? p - k : p - k - 2;
+      for (int l = 0; l <= lmax; ++l)
+        if ((p - k - l) % 2 == 0) t.push_back({p, k, l, (p - k - l) / 2});
+    }
+  return t;
+}
+
+// Linear conditions on the raw e-e-n coefficients that keep both cusps of the Jastrow.
+// With u = Rbar(r_ij), s = Rbar(r_ia), t = Rbar(r_ja) and dRbar/dr(0) = -kappa:
+//  * r_ij -> 0 (then s = t): d term / d r_ij = -2 kappa k s^(p-k), so for every power q
+//    the coefficients with p - k = q satisfy sum k c = 0;
+//  * r_ia -> 0 (then s = 1 and u = t): d term / d s = (l+m) t^(k+m) + m t^(k+l+m), so for
+//    every power q of t the collected coefficients sum to zero.
+// The free coefficients span the null space; B holds the basis read off the reduced row
+// echelon form (free columns in ascending order), so c = B theta.
+static void een_free_basis(std::vector<double>& B) {
+  const std::vector<EenTerm> T = een_term_list();
+  const int nt = (int)T.size();
+  std::vector<std::vector<double>> rows;
+  for (int q = 1; q <= 5; ++q) {
+    std::vector<double> r(nt, 0.0);
+    bool used = false;
+    for (int i = 0; i < nt; ++i)
+      if (T[i].k >= 1 && T[i].p - T[i].k == q) { r[i] = T[i].k; used = true; }
+    if (used) rows.push_back(r);
+  }
+  for (int q = 0; q <= 6; ++q) {
+    std::vector<double> r(nt, 0.0);
+    bool used = false;
+    for (int i = 0; i < nt; ++i) {
+      double v = 0.0;
+      if (T[i].k + T[i].m == q) v += T[i].l + T[i].m;
+      if (T[i].k + T[i].l + T[i].m == q) v += T[i].m;
+      if (v != 0.0) { r[i] = v; used = true; }
+    }
+    if (used) rows.push_back(r);
+  }
+  const int nr = (int)rows.size();
+  std::vector<int> piv;
+  int r = 0;
+  for (int col = 0; col < nt && r < nr; ++col) {
+    int best = -1;
+    double bv = 1e-9;
+    for (int i = r; i < nr; ++i)
+      if (std::fabs(rows[i][col]) > bv) { bv = std::fabs(rows[i][col]); best = i; }
+    if (best < 0) continue;
+    std::swap(rows[r], rows[best]);
+    const double pv = rows[r][col];
+    for (double& x : rows[r]) x /= pv;
+    for (int i = 0; i < nr; ++i) {
+      if (i == r || rows[i][col] == 0.0) continue;
+      const double f = rows[i][col];
+      for (int j = 0; j < nt; ++j) rows[i][j] -= f * rows[r][j];
+    }
+    piv.push_back(col);
+    ++r;
+  }
+  std::vector<int> is_free(nt, 1);
+  for (int c : piv) is_free[c] = 0;
+  std::vector<int> freecols;
+  for (int j = 0; j < nt; ++j)
+    if (is_free[j]) freecols.push_back(j);
+  const int nf = (int)freecols.size();
+  B.assign((size_t)nt * kNfree, 0.0);
+  for (int f = 0; f < nf && f < kNfree; ++f) {
+    B[(size_t)freecols[f] * kNfree + f] = 1.0;
+    for (size_t i = 0; i < piv.size(); ++i) B[(size_t)piv[i] * kNfree + f] = -rows[i][freecols[f]];
+  }
+}
+
+static double double_factorial(int n) {
+  double r = 1.0;
+  for (int i = n; i > 1; i -= 2) r *= i;
+  return r;
+}
+
+// Parity of the permutation that sorts v ascending (v has distinct entries).
+static int sort_parity(std::vector<int>& v) {
+  int inv = 0;
+  for (size_t i = 0; i < v.size(); ++i)
+    for (size_t j = i + 1; j < v.size(); ++j)
+      if (v[i] > v[j]) ++inv;
+  std::sort(v.begin(), v.end());
+  return inv & 1;
+}
+
+struct RawDet {
+  std::vector<int> up, dn;
+  double sign;
+};
+
+// All signed determinants of one HLSP structure.  A pair (i, j), i != j, contributes
+// a+_{i up} a+_{j dn} - a+_{i dn} a+_{j up}; a self pair (i, i) contributes a+_{i up} a+_{i dn}
+// (the factor 2 is dropped: structures are unnormalised).  Each product of creation
+// operators is reordered to (up operators ascending)(down operators ascending); the
+// permutation parity multiplies the sign.  Strings with a repeated spin orbital vanish.
+static void expand_structure(const std::vector<int>& inact, const std::vector<std::pair<int, int>>& pairs,
+                             const std::vector<int>& unp, std::vector<RawDet>& out) {
+  const int np = (int)pairs.size();
+  std::vector<int> choice(np, 0);
+  for (;;) {
+    std::vector<std::pair<int, int>> ops;  // (orbital, spin)
+    double sgn = 1.0;
+    for (int p : inact) { ops.push_back({p, 0}); ops.push_back({p, 1}); }
+    for (int q = 0; q < np; ++q) {
+      if (choice[q] == 0) { ops.push_back({pairs[q].first, 0}); ops.push_back({pairs[q].second, 1}); }
+      else { ops.push_back({pairs[q].first, 1}); ops.push_back({pairs[q].second, 0}); sgn = -sgn; }
+    }
+    for (int q : unp) ops.push_back({q, 0});
+    int crossings = 0, downs = 0;
+    RawDet d;
+    for (auto& o : ops) {
+      if (o.second == 1) { ++downs; d.dn.push_back(o.first); }
+      else { crossings += downs; d.up.push_back(o.first); }
+    }
+    if (crossings & 1) sgn = -sgn;
+    if (sort_parity(d.up)) sgn = -sgn;
+    if (sort_parity(d.dn)) sgn = -sgn;
+    bool pauli = false;
+    for (auto* v : {&d.up, &d.dn})
+      for (size_t x = 1; x < v->size(); ++x)
+        if ((*v)[x] == (*v)[x - 1]) pauli = true;
+    d.sign = sgn;
+    if (!pauli) out.push_back(d);
+    int q = 0;
+    for (; q < np; ++q) {
+      const int nch = pairs[q].first == pairs[q].second ? 1 : 2;
+      if (++choice[q] < nch) break;
+      choice[q] = 0;
+    }
+    if (q == np) break;
+  }
+}
+
+#define VBQ_REQUIRE(cond, msg)                 \
+  do {                                         \
+    if (!(cond)) {                             \
+      std::ostringstream os_;                  \
+      os_ << msg;                              \
+      err = os_.str();                         \
+      return VBQMC_ERR_ARG;                    \
+    }                                          \
+  } while (0)
+
+int build_system(const vbqmc_system_desc* d, SysHost& s, std::string& err) {
+  VBQ_REQUIRE(d != nullptr, "null system description");
+  VBQ_REQUIRE(d->Nn >= 1 && d->n_elem >= 1 && d->S >= 1 && d->Norb >= 1 && d->Nvb >= 1, "empty system");
+  VBQ_REQUIRE(d->n_elem <= kMaxElem, "too many elements");
+  VBQ_REQUIRE(d->Nup >= 0 && d->Ndn >= 0 && d->Nup + d->Ndn >= 1, "bad electron counts");
+  if (d->Nup > kMaxSpinN || d->Ndn > kMaxSpinN || d->Nup + d->Ndn > kMaxN) {
+    err = "electron count beyond kernel limits (N <= 64, per spin <= 32)";
+    return VBQMC_ERR_CAPACITY;
+  }
+  VBQ_REQUIRE(d->nuc_xyz && d->nuc_Z && d->nuc_elem && d->sh_center && d->sh_l && d->sh_zeta && d->orb_coef &&
+                  d->c_vb && d->inact_off && d->pair_off && d->unp_off && d->jas_a && d->jas_b,
+              "missing array");
+  s = SysHost();
+  s.Nn = d->Nn; s.n_elem = d->n_elem; s.S = d->S; s.Norb = d->Norb; s.Nvb = d->Nvb;
+  s.Nup = d->Nup; s.Ndn = d->Ndn; s.N = d->Nup + d->Ndn;
+  s.nuc4.resize(4 * s.Nn);
+  for (int a = 0; a < s.Nn; ++a) {
+    for (int c = 0; c < 3; ++c) s.nuc4[4 * a + c] = d->nuc_xyz[3 * a + c];
+    s.nuc4[4 * a + 3] = d->nuc_Z[a];
+    VBQ_REQUIRE(d->nuc_elem[a] >= 0 && d->nuc_elem[a] < s.n_elem, "nucleus " << a << ": bad element id");
+    VBQ_REQUIRE(std::isfinite(d->nuc_Z[a]), "non-finite nuclear charge");
+  }
+  s.nuc_elem.assign(d->nuc_elem, d->nuc_elem + s.Nn);
+  // basis
+  s.sh_center.assign(d->sh_center, d->sh_center + s.S);
+  s.sh_l.assign(d->sh_l, d->sh_l + s.S);
+  s.sh_zeta.assign(d->sh_zeta, d->sh_zeta + s.S);
+  s.sh_first.resize(s.S);
+  s.sh_norm.assign((size_t)6 * s.S, 0.0);
+  int M = 0;
+  for (int i = 0; i < s.S; ++i) {
+    const int l = s.sh_l[i];
+    VBQ_REQUIRE(l >= 0 && l <= 2, "shell " << i << ": l must be 0, 1 or 2");
+    VBQ_REQUIRE(s.sh_center[i] >= 0 && s.sh_center[i] < s.Nn, "shell " << i << ": bad center");
+    VBQ_REQUIRE(s.sh_zeta[i] >= 0.0 && std::isfinite(s.sh_zeta[i]), "shell " << i << ": bad exponent");
+    s.sh_first[i] = M;
+    const double z = s.sh_zeta[i];
+    for (int c = 0; c < kNcomp[l]; ++c) {
+      const int* e = kCart[kCartOff[l] + c];
+      double nrm = 1.0;
+      if (z > 0.0)
+        nrm = std::pow(2.0 * z / M_PI, 0.75) * std::pow(4.0 * z, 0.5 * l) /
+              std::sqrt(double_factorial(2 * e[0] - 1) * double_factorial(2 * e[1] - 1) *
+                        double_factorial(2 * e[2] - 1));
+      s.sh_norm[(size_t)6 * i + c] = nrm;
+    }
+    M += kNcomp[l];
+  }
+  if (M > kMaxM) {
+    err = "basis larger than 1024 functions";
+    return VBQMC_ERR_CAPACITY;
+  }
+  s.M = M;
+  // orbital coefficient ranges
+  s.orb_lo.resize(s.Norb);
+  s.orb_hi.resize(s.Norb);
+  s.orb_off.resize(s.Norb);
+  for (int k = 0; k < s.Norb; ++k) {
+    const double* row = d->orb_coef + (size_t)k * M;
+    int lo = -1, hi = -1;
+    for (int mu = 0; mu < M; ++mu) {
+      VBQ_REQUIRE(std::isfinite(row[mu]), "orbital " << k << ": non-finite coefficient");
+      if (row[mu] != 0.0) {
+        if (lo < 0) lo = mu;
+        hi = mu + 1;
+      }
+    }
+    if (lo < 0) { lo = 0; hi = 0; }
+    s.orb_lo[k] = lo;
+    s.orb_hi[k] = hi;
+    s.orb_off[k] = (int)s.orb_coef.size();
+    for (int mu = lo; mu < hi; ++mu) s.orb_coef.push_back(row[mu]);
+  }
+  // structures -> determinants
+  std::map<std::vector<int>, int> up_id, dn_id;
+  std::vector<std::vector<int>> ups, dns;
+  std::map<std::pair<int, int>, int> term_id;
+  std::map<std::pair<int, int>, int> sterm_id;
+  for (int I = 0; I < s.Nvb; ++I) {
+    VBQ_REQUIRE(std::isfinite(d->c_vb[I]), "non-finite structure coefficient");
+    std::vector<int> ina, unp;
+    std::vector<std::pair<int, int>> prs;
+    for (int q = d->inact_off[I]; q < d->inact_off[I + 1]; ++q) ina.push_back(d->inact[q]);
+    for (int q = d->pair_off[I]; q < d->pair_off[I + 1]; ++q) prs.push_back({d->pairs[2 * q], d->pairs[2 * q + 1]});
+    for (int q = d->unp_off[I]; q < d->unp_off[I + 1]; ++q) unp.push_back(d->unp[q]);
+    for (int o : ina) VBQ_REQUIRE(o >= 0 && o < s.Norb, "structure " << I << ": bad orbital");
+    for (int o : unp) VBQ_REQUIRE(o >= 0 && o < s.Norb, "structure " << I << ": bad orbital");
+    for (auto& p : prs)
+      VBQ_REQUIRE(p.first >= 0 && p.first < s.Norb && p.second >= 0 && p.second < s.Norb,
+                  "structure " << I << ": bad orbital");
+    VBQ_REQUIRE((int)(2 * ina.size() + 2 * prs.size() + unp.size()) == s.N,
+                "structure " << I << ": electron count differs from Nup + Ndn");
+    VBQ_REQUIRE((int)(ina.size() + prs.size() + unp.size()) == s.Nup, "structure " << I << ": spin count mismatch");
+    std::vector<RawDet> raw;
+    expand_structure(ina, prs, unp, raw);
+    for (auto& r : raw) {
+      auto iu = up_id.find(r.up);
+      if (iu == up_id.end()) { iu = up_id.insert({r.up, (int)ups.size()}).first; ups.push_back(r.up); }
+      auto idn = dn_id.find(r.dn);
+      if (idn == dn_id.end()) { idn = dn_id.insert({r.dn, (int)dns.size()}).first; dns.push_back(r.dn); }
+      std::pair<int, int> key(iu->second, idn->second);
+      auto it = term_id.find(key);
+      if (it == term_id.end()) {
+        it = term_id.insert({key, (int)s.term_coef.size()}).first;
+        s.term_det.push_back(key.first);
+        s.term_det.push_back(key.second);
+        s.term_coef.push_back(0.0);
+      }
+      s.term_coef[it->second] += d->c_vb[I] * r.sign;
+      std::pair<int, int> sk(I, it->second);
+      auto st = sterm_id.find(sk);
+      if (st == sterm_id.end()) {
+        sterm_id.insert({sk, (int)s.sterm_d.size()});
+        s.sterm_I.push_back(I);
+        s.sterm_k.push_back(it->second);
+        s.sterm_d.push_back(r.sign);
+      } else {
+        s.sterm_d[st->second] += r.sign;
+      }
+    }
+  }
+  VBQ_REQUIRE(!s.term_coef.empty(), "every determinant vanishes");
+  s.U[0] = (int)ups.size();
+  s.U[1] = (int)dns.size();
+  s.n[0] = s.Nup;
+  s.n[1] = s.Ndn;
+  // orbitals used by each spin; eval orbital list = det orbitals, then excitation targets
+  std::vector<int> in_det(s.Norb, 0);
+  for (int sp = 0; sp < 2; ++sp) {
+    auto& sets = sp == 0 ? ups : dns;
+    std::vector<int> used(s.Norb, 0);
+    for (auto& v : sets)
+      for (int o : v) used[o] = 1, in_det[o] = 1;
+    for (int k = 0; k < s.Norb; ++k)
+      if (used[k]) s.occ_list[sp].push_back(k);
+  }
+  std::vector<int> ev_of(s.Norb, -1);
+  for (int k = 0; k < s.Norb; ++k)
+    if (in_det[k]) { ev_of[k] = (int)s.ev_orb.size(); s.ev_orb.push_back(k); }
+  s.n_ev_det = (int)s.ev_orb.size();
+  s.n_kappa = d->n_kappa;
+  for (int j = 0; j < s.n_kappa; ++j) {
+    const int k = d->kappa_kl[2 * j], l = d->kappa_kl[2 * j + 1];
+    VBQ_REQUIRE(k >= 0 && k < s.Norb && l >= 0 && l < s.Norb && k != l, "orbital excitation " << j << ": bad (k, l)");
+    if (ev_of[k] < 0) { ev_of[k] = (int)s.ev_orb.size(); s.ev_orb.push_back(k); }
+  }
+  for (int sp = 0; sp < 2; ++sp) {
+    auto& sets = sp == 0 ? ups : dns;
+    std::vector<int> loc(s.Norb, -1);
+    for (size_t q = 0; q < s.occ_list[sp].size(); ++q) loc[s.occ_list[sp][q]] = (int)q;
+    for (auto& v : sets)
+      for (int o : v) {
+        s.det_loc[sp].push_back(loc[o]);
+        s.det_ev[sp].push_back(ev_of[o]);
+        s.det_glob[sp].push_back(o);
+      }
+    // excitation entries: phi_l -> phi_l + eps phi_k changes a determinant only if l is
+    // occupied in it and k is not (otherwise two equal columns)
+    s.kap_off[sp].push_back(0);
+    for (size_t u = 0; u < sets.size(); ++u) {
+      for (int j = 0; j < s.n_kappa; ++j) {
+        const int k = d->kappa_kl[2 * j], l = d->kappa_kl[2 * j + 1];
+        int slot = -1;
+        bool has_k = false;
+        for (int o = 0; o < (int)sets[u].size(); ++o) {
+          if (sets[u][o] == l) slot = o;
+          if (sets[u][o] == k) has_k = true;
+        }
+        if (slot < 0 || has_k) continue;
+        s.kap_ent[sp].insert(s.kap_ent[sp].end(), {j, slot, ev_of[k], 0});
+      }
+      s.kap_off[sp].push_back((int)(s.kap_ent[sp].size() / 4));
+    }
+  }
+  // Jastrow
+  s.kappa = d->kappa;
+  s.b1_anti = d->b1_anti;
+  s.b1_par = d->b1_par;
+  s.een_on = d->een_on ? 1 : 0;
+  s.jas_a.assign(d->jas_a, d->jas_a + 6 * s.n_elem);
+  s.jas_b.assign(d->jas_b, d->jas_b + 6);
+  een_free_basis(s.een_B);
+  s.een_c.assign((size_t)s.n_elem * kNeen, 0.0);
+  if (s.een_on) {
+    VBQ_REQUIRE(d->een_theta != nullptr, "een_on without een_theta");
+    for (int e = 0; e < s.n_elem; ++e)
+      for (int t = 0; t < kNeen; ++t) {
+        double v = 0.0;
+        for (int f = 0; f < kNfree; ++f) v += s.een_B[(size_t)t * kNfree + f] * d->een_theta[e * kNfree + f];
+        s.een_c[(size_t)e * kNeen + t] = v;
+      }
+  }
+  // parameters
+  s.cparam.assign(d->cparam, d->cparam + d->n_cparam);
+  for (int I : s.cparam) VBQ_REQUIRE(I >= 0 && I < s.Nvb, "bad structure parameter index");
+  s.jas_param = d->jas_param ? 1 : 0;
+  s.P = (int)s.cparam.size() + (s.jas_param ? 5 * s.n_elem + 5 + (s.een_on ? kNfree * s.n_elem : 0) : 0) +
+        s.n_kappa;
+  // nucleus-nucleus repulsion
+  double vnn = 0.0;
+  for (int a = 0; a < s.Nn; ++a)
+    for (int b = a + 1; b < s.Nn; ++b) {
+      double r2 = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        const double x = s.nuc4[4 * a + c] - s.nuc4[4 * b + c];
+        r2 += x * x;
+      }
+      VBQ_REQUIRE(r2 > 0.0, "coincident nuclei");
+      vnn += s.nuc4[4 * a + 3] * s.nuc4[4 * b + 3] / std::sqrt(r2);
+    }
+  s.vnn = vnn;
+  return VBQMC_OK;
+}
+
+}  // namespace vbq

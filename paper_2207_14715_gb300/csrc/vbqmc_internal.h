@@ -1,0 +1,110 @@
+// Internal data layout of the VB-QMC library: the host-side system tables built by
+// vbqmc_set_system and the device image the kernels read.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/vbqmc.h"
+
+namespace vbq {
+
+constexpr int kMaxN = 64;        // electrons
+constexpr int kMaxSpinN = 32;    // electrons of one spin (Slater order <= one warp)
+constexpr int kMaxM = 1024;      // basis functions
+constexpr int kNeen = 23;        // e-e-n expansion terms per element (Sec. 2.1)
+constexpr int kNfree = 15;       // free e-e-n coefficients per element after the cusp conditions
+constexpr int kMaxElem = 16;
+
+// e-e-n terms (p, k, l, m): p = 2..5, k = 0..p-1, l = 0..lmax with lmax = p-k (k != 0) or
+// p-k-2 (k = 0), kept when m = (p-k-l)/2 is an integer (Sec. 2.1, f_een).
+struct EenTerm { int p, k, l, m; };
+std::vector<EenTerm> een_term_list();
+
+// Everything the kernels need, as host vectors (built by build_system).
+struct SysHost {
+  int N = 0, Nup = 0, Ndn = 0, Nn = 0, n_elem = 0, S = 0, M = 0, Norb = 0, Nvb = 0;
+  std::vector<double> nuc4;            // [Nn][4] x y z Z
+  std::vector<int> nuc_elem;
+  std::vector<int> sh_center, sh_l, sh_first;
+  std::vector<double> sh_zeta, sh_norm;  // norm [S][6]
+  // orbitals: nonzero range [lo, hi) per orbital, coefficients packed
+  std::vector<int> orb_lo, orb_hi, orb_off;
+  std::vector<double> orb_coef;
+  // orbitals evaluated in a full evaluation: det orbitals first, then excitation targets
+  std::vector<int> ev_orb;             // eval index -> global orbital
+  int n_ev_det = 0;                    // first n_ev_det eval orbitals appear in determinants
+  // per spin: orbitals appearing in its determinants (global ids, ascending)
+  std::vector<int> occ_list[2];
+  int U[2] = {0, 0};
+  int n[2] = {0, 0};
+  std::vector<int> det_loc[2];         // [U][n] index into occ_list[s]
+  std::vector<int> det_ev[2];          // [U][n] eval index
+  std::vector<int> det_glob[2];        // [U][n] global orbital id
+  // determinant terms: unique (up, dn) pairs with merged coefficients C_k = sum_I c_I d_{I,k}
+  std::vector<int> term_det;           // [nterm][2]
+  std::vector<double> term_coef;       // [nterm]
+  // structure terms (I, term, d) for the c_I derivatives
+  std::vector<int> sterm_I, sterm_k;
+  std::vector<double> sterm_d;
+  // Jastrow
+  double kappa = 0.8, b1_anti = 0.5, b1_par = 0.25, vnn = 0.0;
+  int een_on = 0;
+  std::vector<double> jas_a, jas_b;    // [n_elem][6], [6]
+  std::vector<double> een_c;           // [n_elem][23] raw coefficients
+  std::vector<double> een_B;           // [23][15] free-parameter basis
+  // parameters
+  int P = 0, jas_param = 0;
+  std::vector<int> cparam;
+  int n_kappa = 0;
+  std::vector<int> kap_off[2];         // [U_s + 1]
+  std::vector<int> kap_ent[2];         // [n_ent][4]: j, slot of l, eval index of k, 0
+};
+
+// Builds the tables; returns VBQMC_OK or an error code with a message in 'err'.
+int build_system(const vbqmc_system_desc* d, SysHost& s, std::string& err);
+
+// ---------------------------------------------------------------------------------------
+// Device image: one contiguous allocation, POD view passed to every kernel by value.
+// ---------------------------------------------------------------------------------------
+struct SysDev {
+  int N, Nup, Ndn, Nn, n_elem, S, M, Norb, Nvb;
+  int n_ev, n_ev_det;
+  int nocc[2], U[2], n[2];
+  int nterm, nsterm;
+  int P, n_cparam, jas_param, een_on, n_kappa;
+  int p_off_a, p_off_b, p_off_theta, p_off_kappa;
+  double kappa, b1_anti, b1_par, vnn;
+  const double* nuc4;
+  const int* nuc_elem;
+  const int* sh_center;
+  const int* sh_l;
+  const int* sh_first;
+  const double* sh_zeta;
+  const double* sh_norm;
+  const int* orb_lo;
+  const int* orb_hi;
+  const int* orb_off;
+  const double* orb_coef;
+  const float* orb_coef_f;
+  const int* ev_orb;
+  const int* occ_list[2];
+  const int* det_loc[2];
+  const int* det_ev[2];
+  const int* term_det;
+  const double* term_coef;
+  const int* sterm_I;
+  const int* sterm_k;
+  const double* sterm_d;
+  const int* cparam;
+  const double* jas_a;
+  const double* jas_b;
+  const double* een_c;
+  const float* een_cf;
+  const double* een_B;
+  const int* kap_off[2];
+  const int* kap_ent[2];               // [n_ent][4]: j, slot of l, eval index of k, 0
+};
+
+}  // namespace vbq

@@ -1,0 +1,302 @@
+// Device building blocks of the VB-QMC kernels: counter-based random numbers, warp and
+// lane-group reductions, the lane-group Slater LU/inverse, Gaussian basis functions and
+// the Jastrow pieces (arXiv:2207.14715, Sec. 2.1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vbqmc_internal.h"
+
+namespace vbq {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from the published round function.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1, uint32_t out[4]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Two uniforms in [0, 1): counter (walker, step, slot, (tag << 8) | purpose), key = seed.
+__device__ __forceinline__ void uniforms2(uint64_t seed, uint32_t walker, uint32_t step, uint32_t slot, uint32_t tag,
+                                          uint32_t purpose, double& u0, double& u1) {
+  uint32_t o[4];
+  philox4x32_10(walker, step, slot, (tag << 8) | (purpose & 0xffu), (uint32_t)seed, (uint32_t)(seed >> 32), o);
+  const uint64_t x0 = ((uint64_t)o[1] << 32) | o[0];
+  const uint64_t x1 = ((uint64_t)o[3] << 32) | o[2];
+  u0 = (double)(x0 >> 11) * 0x1.0p-53;
+  u1 = (double)(x1 >> 11) * 0x1.0p-53;
+}
+
+// ------------------------------------------------------------------------------------
+// reductions
+// ------------------------------------------------------------------------------------
+template <class T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+template <class T> __device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+template <class T> __device__ __forceinline__ T group_sum(T v, int G) {
+  for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o, G);
+  return v;
+}
+
+// ------------------------------------------------------------------------------------
+// Lane-group LU with partial pivoting and explicit inverse.
+// A (n x n, row-major, rows = electrons, columns = orbital slots) is overwritten with its
+// LU factors; Binv receives A^{-1} row-major ([slot][electron]).  A group of G lanes
+// (G = power of two >= n) handles one matrix; every lane of the warp must call this with
+// the same n and G (inactive groups pass active = false).  Pivot ties go to the lowest row.
+// Returns ln|det A| and sign(det A) in every lane of the group; a zero pivot gives
+// sign 0, ln|det| = -inf and a zero inverse.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void group_lu_inverse(double* A, double* Binv, int* perm, int n, int glane, int G,
+                                                 bool active, double& logdet, double& sgn) {
+  double s = 1.0;
+  bool singular = false;
+  if (active && glane < n) perm[glane] = glane;
+  __syncwarp();
+  for (int c = 0; c < n; ++c) {
+    double v = (active && glane >= c && glane < n) ? fabs(A[glane * n + c]) : -1.0;
+    int idx = glane;
+    for (int o = G >> 1; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(kFull, v, o, G);
+      const int oi = __shfl_xor_sync(kFull, idx, o, G);
+      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    if (v <= 0.0) singular = true;
+    if (idx != c) {
+      if (active && !singular)
+        for (int j = glane; j < n; j += G) {
+          const double t = A[c * n + j];
+          A[c * n + j] = A[idx * n + j];
+          A[idx * n + j] = t;
+        }
+      if (active && glane == 0) {
+        const int t = perm[c];
+        perm[c] = perm[idx];
+        perm[idx] = t;
+      }
+      s = -s;
+    }
+    __syncwarp();
+    if (active && !singular && glane > c && glane < n) {
+      const double l = A[glane * n + c] / A[c * n + c];
+      A[glane * n + c] = l;
+      for (int j = c + 1; j < n; ++j) A[glane * n + j] = fma(-l, A[c * n + j], A[glane * n + j]);
+    }
+    __syncwarp();
+  }
+  if (active && glane < n) {
+    const int j = glane;
+    if (!singular) {
+      for (int i = 0; i < n; ++i) {
+        double y = (perm[i] == j) ? 1.0 : 0.0;
+        for (int k = 0; k < i; ++k) y = fma(-A[i * n + k], Binv[k * n + j], y);
+        Binv[i * n + j] = y;
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        double x = Binv[i * n + j];
+        for (int k = i + 1; k < n; ++k) x = fma(-A[i * n + k], Binv[k * n + j], x);
+        Binv[i * n + j] = x / A[i * n + i];
+      }
+    } else {
+      for (int i = 0; i < n; ++i) Binv[i * n + j] = 0.0;
+    }
+  }
+  double ld = 0.0, neg = 0.0;
+  if (active && glane < n && !singular) {
+    const double d = A[glane * n + glane];
+    ld = log(fabs(d));
+    neg = d < 0.0 ? 1.0 : 0.0;
+  }
+  ld = group_sum(ld, G);
+  neg = group_sum(neg, G);
+  if (singular) {
+    logdet = -INFINITY;
+    sgn = 0.0;
+  } else {
+    logdet = ld;
+    sgn = (((int)neg) & 1) ? -s : s;
+  }
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------------------------
+// math helpers overloaded on the bulk type
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double vexp(double x) { return exp(x); }
+__device__ __forceinline__ float vexp(float x) { return expf(x); }
+__device__ __forceinline__ double vsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float vsqrt(float x) { return sqrtf(x); }
+
+template <class T> __device__ __forceinline__ T tload(const double* p) { return (T)__ldg(p); }
+
+// ------------------------------------------------------------------------------------
+// Cartesian Gaussian shell at displacement d = r - center: for every component
+//   chi = N P e^{-z r^2},  grad chi = N e (grad P - 2 z d P),
+//   lap chi = N e (lap P + P (4 z^2 r^2 - 6 z - 4 z l)),
+// P the cartesian monomial (s; x y z; xx yy zz xy xz yz).  Writes value (and if out_d is
+// non-null gradient and Laplacian) for component c at out[c * stride].
+// ------------------------------------------------------------------------------------
+template <class T, bool DERIV>
+__device__ __forceinline__ void gto_shell(int l, T z, const double* nrm, T dx, T dy, T dz, T* val, T* gx, T* gy, T* gz,
+                                          T* lap) {
+  const T r2 = dx * dx + dy * dy + dz * dz;
+  const T e = (z == (T)0) ? (T)1 : vexp(-z * r2);
+  const T tz = (T)2 * z;
+  const T base = (T)4 * z * z * r2 - (T)6 * z - (T)4 * z * (T)l;
+  if (l == 0) {
+    const T ne = (T)nrm[0] * e;
+    val[0] = ne;
+    if (DERIV) {
+      gx[0] = -tz * dx * ne; gy[0] = -tz * dy * ne; gz[0] = -tz * dz * ne;
+      lap[0] = base * ne;
+    }
+  } else if (l == 1) {
+    const T d[3] = {dx, dy, dz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T ne = (T)nrm[c] * e;
+      const T P = d[c];
+      val[c] = ne * P;
+      if (DERIV) {
+        gx[c] = ne * ((c == 0 ? (T)1 : (T)0) - tz * dx * P);
+        gy[c] = ne * ((c == 1 ? (T)1 : (T)0) - tz * dy * P);
+        gz[c] = ne * ((c == 2 ? (T)1 : (T)0) - tz * dz * P);
+        lap[c] = ne * P * base;
+      }
+    }
+  } else {
+    // xx yy zz xy xz yz
+    const int ia[6] = {0, 1, 2, 0, 0, 1};
+    const int ib[6] = {0, 1, 2, 1, 2, 2};
+    const T d[3] = {dx, dy, dz};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const T ne = (T)nrm[c] * e;
+      const T P = d[ia[c]] * d[ib[c]];
+      val[c] = ne * P;
+      if (DERIV) {
+        T g[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          T dP = (T)0;
+          if (ia[c] == q) dP += d[ib[c]];
+          if (ib[c] == q) dP += d[ia[c]];
+          g[q] = ne * (dP - tz * d[q] * P);
+        }
+        gx[c] = g[0]; gy[c] = g[1]; gz[c] = g[2];
+        const T lapP = (c < 3) ? (T)2 : (T)0;
+        lap[c] = ne * (lapP + P * base);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Jastrow radial pieces.  R(r) = r/(1 + kappa r); f(R) = a1 R/(1 + a2 R) + sum_{p=2..5} q_p R^p
+// with q_p = coef[p-2].  Returns f and, with DERIV, df/dr and d2f/dr2.
+// ------------------------------------------------------------------------------------
+template <class T, bool DERIV>
+__device__ __forceinline__ void pade_poly(T r, T kap, T a1, T a2, const T* q, T& f, T& df, T& d2f) {
+  const T den = (T)1 / ((T)1 + kap * r);
+  const T R = r * den;
+  const T pd = (T)1 / ((T)1 + a2 * R);
+  const T R2 = R * R, R3 = R2 * R, R4 = R3 * R, R5 = R4 * R;
+  f = a1 * R * pd + q[0] * R2 + q[1] * R3 + q[2] * R4 + q[3] * R5;
+  if (DERIV) {
+    const T dR = den * den;
+    const T d2R = (T)-2 * kap * dR * den;
+    const T fR = a1 * pd * pd + (T)2 * q[0] * R + (T)3 * q[1] * R2 + (T)4 * q[2] * R3 + (T)5 * q[3] * R4;
+    const T fRR = (T)-2 * a1 * a2 * pd * pd * pd + (T)2 * q[0] + (T)6 * q[1] * R + (T)12 * q[2] * R2 +
+                  (T)20 * q[3] * R3;
+    df = fR * dR;
+    d2f = fRR * dR * dR + fR * d2R;
+  }
+}
+
+// Calls f(q, k, l, m) for the e-e-n terms in the order of the sum of Sec. 2.1: p = 2..5,
+// k = 0..p-1, l = 0..lmax with lmax = p-k (k != 0) or p-k-2 (k = 0), kept when p-k-l is even
+// (m = (p-k-l)/2); q counts the kept terms.  All loops unroll at compile time.
+template <class F> __device__ __forceinline__ void een_for_each(F&& f) {
+  int q = 0;
+#pragma unroll
+  for (int p = 2; p <= 5; ++p) {
+#pragma unroll
+    for (int k = 0; k < p; ++k) {
+#pragma unroll
+      for (int l = 0; l <= (k ? p - k : p - k - 2); ++l) {
+        if (((p - k - l) & 1) == 0) {
+          f(q, k, l, (p - k - l) >> 1);
+          ++q;
+        }
+      }
+    }
+  }
+}
+
+template <class T> struct Pow6 {
+  T v[6];
+  __device__ __forceinline__ void set(T x) {
+    v[0] = (T)1; v[1] = x; v[2] = x * x; v[3] = v[2] * x; v[4] = v[3] * x; v[5] = v[4] * x;
+  }
+  __device__ __forceinline__ T p(int n) const { return v[n]; }
+  __device__ __forceinline__ T d(int n) const { return n >= 1 ? (T)n * v[n - 1] : (T)0; }
+  __device__ __forceinline__ T dd(int n) const { return n >= 2 ? (T)(n * (n - 1)) * v[n - 2] : (T)0; }
+};
+
+// Term t of the e-e-n expansion, T = u^k (s^l + t^l)(s t)^m = u^k (s^(l+m) t^m + s^m t^(l+m)).
+template <class T>
+__device__ __forceinline__ T een_term(const Pow6<T>& U, const Pow6<T>& S, const Pow6<T>& Tt, int k, int l, int m) {
+  return U.p(k) * (S.p(l + m) * Tt.p(m) + S.p(m) * Tt.p(l + m));
+}
+
+// Value of F = sum_t c_t T_t(u, s, t).
+template <class T> __device__ __forceinline__ T een_value(const T* c, T u, T s, T t) {
+  Pow6<T> U, S, Tt;
+  U.set(u); S.set(s); Tt.set(t);
+  T F = (T)0;
+  een_for_each([&](int q, int k, int l, int m) { F += c[q] * een_term(U, S, Tt, k, l, m); });
+  return F;
+}
+
+// F and its partial derivatives with respect to u and s (the electron-i side).
+template <class T>
+__device__ __forceinline__ void een_partials_us(const T* c, T u, T s, T t, T& F, T& Fu, T& Fs, T& Fuu, T& Fss,
+                                                T& Fus) {
+  Pow6<T> U, S, Tt;
+  U.set(u); S.set(s); Tt.set(t);
+  F = Fu = Fs = Fuu = Fss = Fus = (T)0;
+  een_for_each([&](int q, int k, int l, int m) {
+    const T f = S.p(l + m) * Tt.p(m) + S.p(m) * Tt.p(l + m);
+    const T fs = S.d(l + m) * Tt.p(m) + S.d(m) * Tt.p(l + m);
+    const T fss = S.dd(l + m) * Tt.p(m) + S.dd(m) * Tt.p(l + m);
+    const T cq = c[q];
+    F += cq * U.p(k) * f;
+    Fu += cq * U.d(k) * f;
+    Fuu += cq * U.dd(k) * f;
+    Fs += cq * U.p(k) * fs;
+    Fss += cq * U.p(k) * fss;
+    Fus += cq * U.d(k) * fs;
+  });
+}
+
+}  // namespace vbq

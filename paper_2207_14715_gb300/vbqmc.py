@@ -1,0 +1,192 @@
+"""Python binding of the VB-QMC C ABI (include/vbqmc.h): argument marshalling only.
+
+Every computation runs in the CUDA library paper_2207_14715_gb300/_lib/libvbqmc.so.  There is
+no fallback: if the library is missing or cannot be loaded, every call raises.  Device arrays
+are torch CUDA tensors (used only as device memory); streams are torch CUDA streams.
+
+Names follow the C ABI: create / set_system / inspect_system / eval_walkers / vmc_steps.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .systems import SystemSpec
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libvbqmc.so")
+
+FP64 = 0
+MIXED = 1
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_dbl_p = ctypes.POINTER(ctypes.c_double)
+
+
+class VbqmcError(RuntimeError):
+    pass
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [
+        ("Nn", ctypes.c_int), ("n_elem", ctypes.c_int),
+        ("nuc_xyz", _c_dbl_p), ("nuc_Z", _c_dbl_p), ("nuc_elem", _c_int_p),
+        ("S", ctypes.c_int), ("sh_center", _c_int_p), ("sh_l", _c_int_p), ("sh_zeta", _c_dbl_p),
+        ("Norb", ctypes.c_int), ("orb_coef", _c_dbl_p),
+        ("Nup", ctypes.c_int), ("Ndn", ctypes.c_int),
+        ("Nvb", ctypes.c_int), ("c_vb", _c_dbl_p),
+        ("inact_off", _c_int_p), ("inact", _c_int_p),
+        ("pair_off", _c_int_p), ("pairs", _c_int_p),
+        ("unp_off", _c_int_p), ("unp", _c_int_p),
+        ("kappa", ctypes.c_double), ("jas_a", _c_dbl_p), ("jas_b", _c_dbl_p),
+        ("b1_anti", ctypes.c_double), ("b1_par", ctypes.c_double),
+        ("een_on", ctypes.c_int), ("een_theta", _c_dbl_p),
+        ("n_cparam", ctypes.c_int), ("cparam", _c_int_p),
+        ("jas_param", ctypes.c_int),
+        ("n_kappa", ctypes.c_int), ("kappa_kl", _c_int_p),
+    ]
+
+
+EXPORTED = ["vbqmc_create", "vbqmc_destroy", "vbqmc_last_error", "vbqmc_set_system", "vbqmc_inspect_system",
+            "vbqmc_eval_walkers", "vbqmc_vmc_steps", "vbqmc_last_launch_count"]
+
+_LIB = None
+
+
+def lib():
+    """Loads libvbqmc.so (raises if it is missing: there is no CPU path)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise VbqmcError("CUDA library not built: %s (run __graft_entry__.build())" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        L.vbqmc_last_error.restype = ctypes.c_char_p
+        L.vbqmc_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
+        L.vbqmc_destroy.argtypes = [ctypes.c_void_p]
+        L.vbqmc_set_system.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(_Desc)]
+        L.vbqmc_inspect_system.argtypes = [ctypes.POINTER(_Desc), _c_int_p, _c_int_p, ctypes.c_int, _c_dbl_p]
+        vp = ctypes.c_void_p
+        L.vbqmc_eval_walkers.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.vbqmc_vmc_steps.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, vp, vp, vp,
+                                      vp, vp, vp, vp]
+        L.vbqmc_last_launch_count.argtypes = [vp]
+        _LIB = L
+    return _LIB
+
+
+def _check(rc):
+    if rc != 0:
+        raise VbqmcError("vbqmc error %d: %s" % (rc, lib().vbqmc_last_error().decode()))
+
+
+def _desc(spec: SystemSpec):
+    keep = []
+
+    def d(x):
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data_as(_c_dbl_p)
+
+    def i(x):
+        a = np.ascontiguousarray(x, dtype=np.int32)
+        if a.size == 0:
+            a = np.zeros(1, np.int32)
+        keep.append(a)
+        return a.ctypes.data_as(_c_int_p)
+
+    s = _Desc()
+    s.Nn, s.n_elem = spec.Nn, spec.n_elem
+    s.nuc_xyz, s.nuc_Z, s.nuc_elem = d(spec.nuc_xyz), d(spec.nuc_Z), i(spec.nuc_elem)
+    s.S = len(spec.sh_l)
+    s.sh_center, s.sh_l, s.sh_zeta = i(spec.sh_center), i(spec.sh_l), d(spec.sh_zeta)
+    s.Norb, s.orb_coef = spec.Norb, d(spec.orb_coef)
+    s.Nup, s.Ndn = spec.n_up, spec.n_dn
+    s.Nvb, s.c_vb = spec.Nvb, d(spec.c_vb)
+    s.inact_off, s.inact = i(spec.inact_off), i(spec.inact)
+    s.pair_off, s.pairs = i(spec.pair_off), i(spec.pairs)
+    s.unp_off, s.unp = i(spec.unp_off), i(spec.unp)
+    s.kappa, s.jas_a, s.jas_b = spec.kappa, d(spec.jas_a), d(spec.jas_b)
+    s.b1_anti, s.b1_par = spec.b1_anti, spec.b1_par
+    s.een_on, s.een_theta = int(spec.een_on), d(spec.theta())
+    s.n_cparam, s.cparam = len(spec.cparam), i(spec.cparam)
+    s.jas_param = int(spec.jas_param)
+    s.n_kappa, s.kappa_kl = len(spec.kappa_kl), i(spec.kappa_kl)
+    return s, keep
+
+
+def inspect_system(spec: SystemSpec, max_terms: int = 4096):
+    """Host-side set-up only (no device): sizes, the signed determinant terms per structure
+    (up orbitals, down orbitals, structure, sign) and the 23x15 e-e-n free-parameter basis."""
+    s, keep = _desc(spec)
+    info = np.zeros(12, np.int32)
+    row = spec.n_up + spec.n_dn + 2
+    terms = np.zeros((max_terms, row), np.int32)
+    B = np.zeros((23, 15))
+    _check(lib().vbqmc_inspect_system(ctypes.byref(s), info.ctypes.data_as(_c_int_p),
+                                      terms.ctypes.data_as(_c_int_p), max_terms, B.ctypes.data_as(_c_dbl_p)))
+    keys = ["N", "P", "M", "Norb", "nterm", "U_up", "U_dn", "nsterm", "n_ev", "n_kappa_entries", "n_up", "n_dn"]
+    d = dict(zip(keys, (int(x) for x in info)))
+    return d, terms[:d["nsterm"]], B
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """One library context on one CUDA device (vbqmc_create / vbqmc_destroy)."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib().vbqmc_create(ctypes.byref(h), int(device)))
+        self.h = h
+        self.device = device
+        self.specs = {}
+
+    def close(self):
+        if self.h:
+            lib().vbqmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_system(self, sys_id: int, spec: SystemSpec):
+        s, keep = _desc(spec)
+        _check(lib().vbqmc_set_system(self.h, int(sys_id), ctypes.byref(s)))
+        self.specs[sys_id] = spec
+
+    def last_launch_count(self) -> int:
+        return int(lib().vbqmc_last_launch_count(self.h))
+
+    def eval_walkers(self, sys_id, precision, R, logpsi, sign, eloc, grad=None, O=None, dEL=None, stream=None):
+        """R [W, N, 3] float64 CUDA tensor; outputs preallocated float64 CUDA tensors."""
+        W = R.shape[0]
+        _check(lib().vbqmc_eval_walkers(self.h, int(sys_id), int(precision), int(W), _ptr(R), _ptr(logpsi),
+                                        _ptr(sign), _ptr(eloc), _ptr(grad), _ptr(O), _ptr(dEL), _stream(stream)))
+
+    def vmc_steps(self, sys_id, precision, R, nsweeps, step, seed, step0=0, system_tag=0, walker_offset=0,
+                  nacc=None, logpsi=None, sign=None, eloc=None, O=None, dEL=None, stream=None):
+        W = R.shape[0]
+        _check(lib().vbqmc_vmc_steps(self.h, int(sys_id), int(precision), int(W), _ptr(R), int(nsweeps),
+                                     float(step), ctypes.c_uint64(seed), ctypes.c_uint32(step0),
+                                     ctypes.c_uint32(system_tag), ctypes.c_uint32(walker_offset), _ptr(nacc),
+                                     _ptr(logpsi), _ptr(sign), _ptr(eloc), _ptr(O), _ptr(dEL), _stream(stream)))
+
+
+def create(device: int = 0) -> Context:
+    return Context(device)

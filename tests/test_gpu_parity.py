@@ -1,0 +1,195 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances:
+  FP64 form  : ln|Psi| and E_L within 1e-10 relative (|d| <= 1e-10 max(1, |x|)); gradients
+               1e-9; parameter derivatives 1e-8 relative to max(1, |x|) (derivatives add one
+               more cancellation level than E_L).
+  mixed form : |d ln|Psi|| <= 1e-5 and |d E_L| <= 1e-4 max(1, |E_L|) per walker (worst walker
+               reported); derivatives 2e-3 relative to max(1, |x|) (float bulk arithmetic,
+               ~1e-7 relative rounding amplified by Slater conditioning).
+"""
+import numpy as np
+import pytest
+
+from paper_2207_14715_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_14715_gb300 import build, vbqmc
+    build.build()
+    ctx = vbqmc.create(0)
+    yield vbqmc, ctx
+    ctx.close()
+
+
+def gpu_eval(vb, spec, R, precision, derivs=False, grad=True):
+    mod, ctx = vb
+    ctx.set_system(0, spec)
+    W = R.shape[0]
+    P = spec.n_params
+    dev = "cuda"
+    Rt = torch.tensor(R, dtype=torch.float64, device=dev)
+    lp = torch.zeros(W, dtype=torch.float64, device=dev)
+    sg = torch.zeros_like(lp)
+    el = torch.zeros_like(lp)
+    g = torch.zeros_like(Rt) if grad else None
+    O = torch.zeros((W, P), dtype=torch.float64, device=dev) if derivs and P else None
+    dE = torch.zeros_like(O) if O is not None else None
+    ctx.eval_walkers(0, precision, Rt, lp, sg, el, g, O, dE)
+    torch.cuda.synchronize()
+    out = {"logpsi": lp.cpu().numpy(), "sign": sg.cpu().numpy(), "eloc": el.cpu().numpy()}
+    if grad:
+        out["grad"] = g.cpu().numpy()
+    if O is not None:
+        out["O"], out["dEL"] = O.cpu().numpy(), dE.cpu().numpy()
+    return out
+
+
+def rel_err(a, b):
+    return np.abs(a - b) / np.maximum(1.0, np.abs(b))
+
+
+SYSTEMS = {
+    "hydrogenic": (lambda: S.one_electron(3.0, 0.0, a1=-3.0, a2=-0.8), 10),
+    "gauss_h": (lambda: S.one_electron(1.0, 0.4), 9),
+    "two_electron": (lambda: S.two_electron_product(2.0, 0.9), 11),
+    "h2_vb": (S.h2_vb, 50),
+    "small_open_shell": (S.small_open_shell, 37),
+    "ethylene_vb": (S.ethylene_vb, 5),
+}
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_eval_fp64_matches_oracle(vb, orc, name):
+    maker, W = SYSTEMS[name]
+    spec = maker()
+    R = S.initial_walkers(spec, W, 100 + W)
+    ref = orc.evaluate(spec, R, grad=True)
+    got = gpu_eval(vb, spec, R, 0)
+    np.testing.assert_array_equal(got["sign"], ref["sign"])
+    assert rel_err(got["logpsi"], ref["logpsi"]).max() < 1e-10
+    assert rel_err(got["eloc"], ref["eloc"]).max() < 1e-10
+    assert rel_err(got["grad"], ref["grad"]).max() < 1e-9
+
+
+@pytest.mark.parametrize("name", ["small_open_shell", "ethylene_vb"])
+def test_eval_fp64_derivatives_match_oracle(vb, orc, name):
+    spec = SYSTEMS[name][0]()
+    W = 4 if name == "small_open_shell" else 2
+    R = S.initial_walkers(spec, W, 7)
+    ref = orc.evaluate(spec, R, derivs=True)
+    got = gpu_eval(vb, spec, R, 0, derivs=True)
+    assert rel_err(got["O"], ref["O"]).max() < 1e-8
+    scale = np.maximum(1.0, np.abs(ref["dEL"]))
+    assert (np.abs(got["dEL"] - ref["dEL"]) / scale).max() < 1e-8
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_eval_mixed_within_tolerance(vb, orc, name):
+    maker, W = SYSTEMS[name]
+    spec = maker()
+    R = S.initial_walkers(spec, W, 300 + W)
+    ref = orc.evaluate(spec, R, grad=True)
+    got = gpu_eval(vb, spec, R, 1)
+    dl = np.abs(got["logpsi"] - ref["logpsi"])
+    de = rel_err(got["eloc"], ref["eloc"])
+    print("%s mixed: worst |dlnPsi| %.2e (walker %d), worst rel dE_L %.2e (walker %d)"
+          % (name, dl.max(), dl.argmax(), de.max(), de.argmax()))
+    assert dl.max() <= 1e-5
+    assert de.max() <= 1e-4
+    np.testing.assert_array_equal(got["sign"], ref["sign"])
+
+
+@pytest.mark.parametrize("name", ["small_open_shell", "ethylene_vb"])
+def test_eval_mixed_derivatives(vb, orc, name):
+    spec = SYSTEMS[name][0]()
+    R = S.initial_walkers(spec, 2, 17)
+    ref = orc.evaluate(spec, R, derivs=True)
+    got = gpu_eval(vb, spec, R, 1, derivs=True)
+    eo = rel_err(got["O"], ref["O"]).max()
+    ee = (np.abs(got["dEL"] - ref["dEL"]) / np.maximum(1.0, np.abs(ref["dEL"]))).max()
+    print("%s mixed derivatives: worst rel dO %.2e, worst rel dE_L,j %.2e" % (name, eo, ee))
+    assert eo < 2e-3 and ee < 2e-3
+
+
+def gpu_vmc(vb, spec, R, nsweeps, seed, precision=0, step0=0):
+    mod, ctx = vb
+    ctx.set_system(0, spec)
+    Rt = torch.tensor(R, dtype=torch.float64, device="cuda")
+    nacc = torch.zeros(R.shape[0], dtype=torch.int32, device="cuda")
+    ctx.vmc_steps(0, precision, Rt, nsweeps, spec.step, seed, step0=step0, nacc=nacc)
+    torch.cuda.synchronize()
+    return Rt.cpu().numpy(), nacc.cpu().numpy()
+
+
+@pytest.mark.parametrize("name,W,nsw", [("h2_vb", 64, 6), ("small_open_shell", 33, 3), ("hydrogenic", 8, 5),
+                                        ("ethylene_vb", 3, 1)])
+def test_vmc_fp64_trajectory_matches_oracle(vb, orc, name, W, nsw):
+    """Same Philox streams, same proposals: FP64 trajectories agree move for move."""
+    spec = SYSTEMS[name][0]()
+    R0 = S.initial_walkers(spec, W, 5)
+    Rg, ng = gpu_vmc(vb, spec, R0, nsw, seed=2024, step0=11)
+    Ro, _, _, no = orc.vmc(spec, R0, nsw, spec.step, seed=2024, step0=11, eloc=False)
+    np.testing.assert_array_equal(ng, no)
+    np.testing.assert_allclose(Rg, Ro, rtol=0, atol=1e-12)
+
+
+def test_vmc_mixed_statistics_match_oracle(vb, orc):
+    """Mixed-form VMC of the H2 system: mean E_L agrees with the oracle's within 4 sigma."""
+    spec = S.h2_vb()
+    W = 512
+    R0 = S.initial_walkers(spec, W, 9)
+    mod, ctx = vb
+    ctx.set_system(0, spec)
+    Rt = torch.tensor(R0, device="cuda")
+    lp = torch.zeros(W, dtype=torch.float64, device="cuda")
+    sg, el = torch.zeros_like(lp), torch.zeros_like(lp)
+    ctx.vmc_steps(0, 1, Rt, 50, spec.step, 5, step0=0)
+    es = []
+    for k in range(60):
+        ctx.vmc_steps(0, 1, Rt, 1, spec.step, 5, step0=100 + k, logpsi=lp, sign=sg, eloc=el)
+        es.append(el.cpu().numpy().copy())
+    g_mean, g_err = orc.reblock(np.array(es).mean(axis=1))
+    Ro, _, _, _ = orc.vmc(spec, R0, 50, spec.step, seed=77, eloc=False)
+    _, hist, _, _ = orc.vmc(spec, Ro, 60, spec.step, seed=77, step0=500)
+    o_mean, o_err = orc.reblock(hist.mean(axis=1))
+    assert abs(g_mean - o_mean) < 4 * np.hypot(g_err, o_err), (g_mean, g_err, o_mean, o_err)
+
+
+def test_zero_walkers_and_ragged_tail(vb, orc):
+    mod, ctx = vb
+    spec = S.small_open_shell()
+    ctx.set_system(0, spec)
+    empty = torch.zeros((0, spec.N, 3), dtype=torch.float64, device="cuda")
+    z = torch.zeros(0, dtype=torch.float64, device="cuda")
+    ctx.eval_walkers(0, 0, empty, z, z, z)
+    assert ctx.last_launch_count() == 0
+    for W in (1, 17, 31, 33):
+        R = S.initial_walkers(spec, W, W)
+        got = gpu_eval(vb, spec, R, 0, grad=False)
+        ref = orc.evaluate(spec, R)
+        assert rel_err(got["eloc"], ref["eloc"]).max() < 1e-10
+
+
+def test_full_size_ethylene_sampled(vb, orc):
+    """16384 walkers in the benchmark's launch configuration; sampled walkers checked one by one."""
+    spec = S.ethylene_vb()
+    W = 16384
+    R = S.initial_walkers(spec, W, 1)
+    for precision, tol_l, tol_e in [(0, 1e-10, 1e-10), (1, 1e-5, 1e-4)]:
+        got = gpu_eval(vb, spec, R, precision, derivs=True, grad=False)
+        idx = np.array([0, 1, 4095, 8191, 12288, W - 1])
+        ref = orc.evaluate(spec, R[idx])
+        assert np.abs(got["logpsi"][idx] - ref["logpsi"]).max() <= tol_l * max(1.0, np.abs(ref["logpsi"]).max())
+        assert rel_err(got["eloc"][idx], ref["eloc"]).max() <= tol_e
+        assert np.all(np.isfinite(got["O"])) and np.all(np.isfinite(got["dEL"]))
+        ref_d = orc.evaluate(spec, R[[W - 1]], derivs=True)
+        tol_d = 1e-8 if precision == 0 else 2e-3
+        assert rel_err(got["O"][W - 1], ref_d["O"][0]).max() < tol_d
