@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""VMC walker-steps/s of the JVB hot path on GB300 (one JSON line on rank 0).
+
+Workload: ethylene-shaped JVB system (16 electrons 8 up / 8 down, 6 nuclei Z = 6,6,1,1,1,1,
+6 s + 3 p + 1 d Gaussians per center (M = 126), 6 VB structures / 24 determinants / 8 unique
+determinants per spin, e-n + e-e + e-e-n Jastrow, P = 216 parameters), 16384 walkers per GPU,
+synthetic seeded inputs.  One step = one VMC sweep of single-electron Metropolis moves over
+every walker followed by the evaluation of E_L, dln|Psi|/dp and dE_L/dp for every walker.
+The headline form is the mixed one (float bulk, double Slater/ratios/energies); the FP64 form
+is reported next to it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walker-steps/s (E_L + dlnPsi/dp + dE_L/dp), VMC sweep + evaluation"
+UNIT = "walker-steps/s"
+W_PER_GPU = 16384
+SEED = 20220728 + 1
+
+
+def workload_config(W, flush=True):
+    return {"workload": "ethylene-shaped JVB VMC: 16 e (8/8), 6 nuclei, M=126 Gaussians, 6 structures / "
+                        "24 determinants, e-n+e-e+e-e-n Jastrow, P=216, %d walkers per GPU" % W,
+            "walkers_per_gpu": W, "electrons": 16, "determinants": 24, "params": 216,
+            "l2": "flushed between timed steps (256 MiB write)" if flush else "not flushed"}
+
+
+# --------------------------------------------------------------------------------------
+# Algorithmic work per walker-step (documented in the design notes): counted per kernel,
+# split into the FP64 and FP32 pipes for each precision form.
+# --------------------------------------------------------------------------------------
+def work_model(spec, info):
+    import numpy as np
+    from paper_2207_14715_gb300.systems import NCOMP
+    N, Nn = spec.N, spec.Nn
+    ncomp = [NCOMP[int(l)] for l in spec.sh_l]
+    S = len(ncomp)
+    nnz = [(np.nonzero(spec.orb_coef[k])[0].max() - np.nonzero(spec.orb_coef[k])[0].min() + 1)
+           if np.any(spec.orb_coef[k]) else 0 for k in range(spec.Norb)]
+    det_orbs = sorted(set(int(x) for x in spec.inact) | set(int(x) for x in spec.pairs.ravel()) |
+                      set(int(x) for x in spec.unp))
+    ev_orbs = sorted(set(det_orbs) | set(int(k) for k in spec.kappa_kl[:, 0]))
+    nnz_det = sum(nnz[k] for k in det_orbs)
+    nnz_ev = sum(nnz[k] for k in ev_orbs)
+    n = spec.n_up
+    U = info["U_up"] + info["U_dn"]
+    basis_val = S * 6 + 2 * sum(ncomp)          # per point: r^2, exp, N P e per component
+    basis_full = S * 6 + 14 * sum(ncomp)        # + gradient and Laplacian per component
+    npair = N * (N - 1) // 2
+    een_terms = 23
+    # ---------------- sweep (N moves + one LU refresh) ----------------
+    sw64 = (N * (basis_val + 2 * nnz_det)                   # orbital values at all electrons (refresh)
+            + U * 2 * n ** 3                                 # LU + inverse
+            + N * (basis_val + 2 * nnz_det / 2)              # proposed orbital row (own spin's orbitals)
+            + N * (U / 2) * 2 * n                            # ratios
+            + N * 0.5 * (U / 2) * 4 * n * n)                 # Sherman-Morrison (acceptance ~ 1/2)
+    sw32 = N * ((N - 1) * (30 + Nn * een_terms * 2 * 4) + Nn * 30)   # Jastrow change, old and new
+    # ---------------- evaluation with derivatives ----------------
+    ev_basis = N * basis_full
+    ev_contr_val_det = 2 * N * nnz_det
+    ev_contr_rest = 2 * N * (4 * nnz_ev + (nnz_ev - nnz_det))
+    ev_lu = U * (2 * n ** 3 + 2 * n * n + 6 * n * n)
+    ev_jas = npair * (2 * 30) + N * Nn * 30 + 2 * npair * Nn * een_terms * 12
+    ev_jderiv = npair * Nn * een_terms * 45 + (npair + N * Nn) * 5 * 10
+    ev_kappa = U * 2 * 2 * n * n * len(ev_orbs) + info["n_kappa_entries"] * 2 * n
+    ev64_fp64 = ev_basis + ev_contr_val_det + ev_contr_rest + ev_lu + ev_jas + ev_jderiv + ev_kappa
+    ev64_mixed = N * basis_val + ev_contr_val_det + ev_lu
+    ev32_mixed = ev_basis + ev_contr_rest + ev_jas + ev_jderiv + ev_kappa
+    return {
+        "sweep": {"fp64": {"f64": sw64 + sw32, "f32": 0.0}, "mixed": {"f64": sw64, "f32": sw32}},
+        "eval": {"fp64": {"f64": ev64_fp64, "f32": 0.0}, "mixed": {"f64": ev64_mixed, "f32": ev32_mixed}},
+    }
+
+
+def peaks(sm_mhz):
+    """ALU peaks from unit counts and the SM clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA, and the
+    FP64 rate of 1.25 TFLOP/s at the 2070 MHz maximum clock, both scaled to the measured clock."""
+    f = sm_mhz * 1e6
+    return {"f32": 152 * 128 * 2 * f, "f64": 1.25e12 * (sm_mhz / 2070.0)}
+
+
+# --------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read-only query)."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(spec, R_host, seconds_hint=15.0):
+    """The oracle as it stands: one walker-step (sweep + E_L + derivatives) on a bounded sample."""
+    from oracle import oracle as orc
+    cores = os.cpu_count() or 1
+    Ws = max(2, min(R_host.shape[0], 2 * cores))
+    R = R_host[:Ws].copy()
+    t0 = time.perf_counter()
+    R, _, _, _ = orc.vmc(spec, R, 1, spec.step, seed=SEED, step0=999, eloc=False, nthreads=cores)
+    orc.evaluate(spec, R, derivs=True, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": Ws / dt, "unit": UNIT, "cores": min(cores, Ws), "kind": "oracle",
+            "sample": "%d walkers x 1 step (sweep + E_L + dlnPsi/dp + dE_L/dp), FP64 CPU oracle, %d threads"
+                      % (Ws, min(cores, Ws))}
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 CPU oracle, timed on this machine's host cores."""
+    if rank != 0:
+        return
+    from paper_2207_14715_gb300 import systems as S
+    spec = S.ethylene_vb()
+    cores = os.cpu_count() or 1
+    R = S.initial_walkers(spec, 2 * cores, SEED)
+    for _ in range(args.warmup):
+        cpu_baseline(spec, R)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(spec, R))
+    dt = time.perf_counter() - t0
+    value = sum(v["value"] for v in vals) / len(vals)
+    cb = dict(vals[0])
+    cb["value"] = value
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": workload_config(0, flush=False),
+                      "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                                  "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2207_14715_gb300 import systems as S
+    from paper_2207_14715_gb300 import vbqmc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = S.ethylene_vb()
+    info, _, _ = vbqmc.inspect_system(spec)
+    W = args.walkers
+    P = spec.n_params
+    ctx = vbqmc.create(local)
+    ctx.set_system(0, spec)
+    R = torch.tensor(S.initial_walkers(spec, W, SEED + 1000 * rank), device=dev)
+    lp = torch.zeros(W, dtype=torch.float64, device=dev)
+    sg, el = torch.zeros_like(lp), torch.zeros_like(lp)
+    O = torch.zeros((W, P), dtype=torch.float64, device=dev)
+    dE = torch.zeros_like(O)
+    nacc = torch.zeros(W, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    woff = rank * W
+    step_counter = [0]
+
+    def step(prec, ev=None):
+        k = step_counter[0]
+        step_counter[0] += 1
+        if ev is not None:
+            ev[0].record(stream)
+        ctx.vmc_steps(0, prec, R, 1, spec.step, SEED, step0=k, walker_offset=woff, nacc=nacc)
+        if ev is not None:
+            ev[1].record(stream)
+        ctx.eval_walkers(0, prec, R, lp, sg, el, None, O, dE)
+        if ev is not None:
+            ev[2].record(stream)
+
+    # equilibration (untimed)
+    ctx.vmc_steps(0, vbqmc.MIXED, R, 30, spec.step, SEED, step0=10 ** 6, walker_offset=woff, nacc=nacc)
+    torch.cuda.synchronize()
+    results = {}
+    for name, prec in (("mixed", vbqmc.MIXED), ("fp64", vbqmc.FP64)):
+        steps = args.steps if name == "mixed" else max(1, min(args.steps, args.fp64_steps))
+        for _ in range(args.warmup):
+            step(prec)
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        nacc.zero_()
+        barrier(ws)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if (rank == 0 and name == "mixed") else None
+        if sampler:
+            sampler.start()
+        t_wall = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()
+            step(prec, evs[k])
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        barrier(ws)
+        clocks = sampler.stop() if sampler else None
+        sweep_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
+        eval_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
+        tot_ms = allmax(sweep_ms + eval_ms, ws)
+        results[name] = {"steps": steps, "ms": tot_ms, "sweep_ms": sweep_ms / steps, "eval_ms": eval_ms / steps,
+                         "clocks": clocks, "wall_s": t_wall,
+                         "acc": float(nacc.double().mean().item()) / (spec.N * steps),
+                         "E_mean": float(el.mean().item())}
+    # end to end through the C ABI with host buffers (mixed form)
+    R_host = torch.empty((W, spec.N, 3), dtype=torch.float64, pin_memory=True)
+    R_host.copy_(R.cpu())
+    el_host = torch.empty(W, dtype=torch.float64, pin_memory=True)
+    e2e_steps = args.steps
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        R.copy_(R_host, non_blocking=True)
+        step(vbqmc.MIXED)
+        R_host.copy_(R, non_blocking=True)
+        el_host.copy_(el, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = allmax(time.perf_counter() - t0, ws)
+    barrier(ws)
+    if rank != 0:
+        return
+    model = work_model(spec, info)
+    m = results["mixed"]
+    value = ws * W * m["steps"] / (m["ms"] * 1e-3)
+    f64 = results["fp64"]
+    value64 = ws * W * f64["steps"] / (f64["ms"] * 1e-3)
+    clocks = m["clocks"] or {}
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    pk = peaks(sm_mhz)
+    # dominant kernel of the mixed step
+    dom = "eval" if m["eval_ms"] >= m["sweep_ms"] else "sweep"
+    dur = (m["eval_ms"] if dom == "eval" else m["sweep_ms"]) * 1e-3
+    w64 = model[dom]["mixed"]["f64"] * W
+    w32 = model[dom]["mixed"]["f32"] * W
+    frac64, frac32 = w64 / dur / pk["f64"], w32 / dur / pk["f32"]
+    if frac64 >= frac32:
+        roof = {"bound": "alu", "pipe": "fp64", "achieved": w64 / dur / 1e12, "peak": pk["f64"] / 1e12}
+    else:
+        roof = {"bound": "alu", "pipe": "fp32", "achieved": w32 / dur / 1e12, "peak": pk["f32"] / 1e12}
+    roof.update({"unit": "TFLOP/s", "frac": roof["achieved"] / roof["peak"], "traffic": None,
+                 "kernel": "%s_kernel<float>" % dom,
+                 "peak_source": "derived from unit counts at the measured median SM clock %.0f MHz" % sm_mhz,
+                 "other_pipe_frac": min(frac64, frac32)})
+    cb = cpu_baseline(spec, R_host.numpy()) if (ws == 1 and not args.no_cpu_baseline) else None
+    bi = W * spec.N * 3 * 8
+    bo = W * spec.N * 3 * 8 + W * 8
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": m["steps"], "warmup": args.warmup,
+        "ms_per_step": m["ms"] / m["steps"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64 (mixed: float bulk, double Slater LU/inverses/ratios/orbital values/energies)",
+        "data": "synthetic (seeded ethylene-shaped system, random-init parameters)",
+        "config": workload_config(W),
+        "fp64_form": {"value": value64, "unit": UNIT, "ms_per_step": f64["ms"] / f64["steps"],
+                      "steps": f64["steps"], "sweep_ms": f64["sweep_ms"], "eval_ms": f64["eval_ms"]},
+        "kernel_ms": {"sweep": m["sweep_ms"], "eval": m["eval_ms"]},
+        "acceptance": m["acc"], "E_L_mean": m["E_mean"],
+        "roofline": roof,
+        "cpu_baseline": cb,
+        "e2e": {"value": ws * W * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo},
+        "gpu_launches": 2 * m["steps"],
+        "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
+                   "reasons": clocks.get("reasons", [])},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--walkers", type=int, default=W_PER_GPU)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, ws, rank)
+        return
+    ws, rank, local = dist_setup()
+    run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

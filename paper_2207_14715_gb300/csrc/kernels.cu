@@ -17,7 +17,9 @@ namespace vbq {
 
 namespace {
 
-inline int align16(int x) { return (x + 15) & ~15; }
+__host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
+template <class A, class B> constexpr bool kSameType = false;
+template <class A> constexpr bool kSameType<A, A> = true;
 inline int group_size(int n) {
   int g = 1;
   while (g < n) g <<= 1;
@@ -78,11 +80,11 @@ __device__ __forceinline__ double dist3(const double* a, const double* b, double
 
 // Lane-group LU + inverse of every unique determinant of spin sp, from orbital values
 // Phi[(e0 + e) * ld + idx[u][o]].  Writes Binv[u], ldet[u], dsg[u] (and, if Lphi is given,
-// t[u] = tr(Binv L_occ) with L read like Phi).
-template <class Tb>
-__device__ __forceinline__ void lu_all(const SysDev& s, int sp, int lane, const Tb* Phi, const Tb* Lphi, int ld,
-                                       const int* idx, int G, double* Binv, double* scr, double* ldet, double* dsg,
-                                       double* tdet) {
+// t[u] = tr(Binv L_occ) with L read at Lphi[(e0 + e) * ldL + idx[u][o]]).
+template <class TP, class TL>
+__device__ __forceinline__ void lu_all(const SysDev& s, int sp, int lane, const TP* Phi, int ld, const TL* Lphi,
+                                       int ldL, const int* idx, int G, double* Binv, double* scr, double* ldet,
+                                       double* dsg, double* tdet) {
   const int n = s.n[sp], U = s.U[sp], e0 = sp ? s.Nup : 0;
   if (n == 0) {
     for (int u = lane; u < U; u += 32) {
@@ -111,7 +113,7 @@ __device__ __forceinline__ void lu_all(const SysDev& s, int sp, int lane, const 
     double t = 0.0;
     if (tdet && act && gl < n) {
       const int o = gl, col = __ldg(idx + u * n + o);
-      for (int e = 0; e < n; ++e) t = fma(B[o * n + e], (double)Lphi[(e0 + e) * ld + col], t);
+      for (int e = 0; e < n; ++e) t = fma(B[o * n + e], (double)Lphi[(e0 + e) * ldL + col], t);
     }
     t = group_sum(t, G);
     if (act && gl == 0) {
@@ -173,6 +175,7 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
   Tb* G = reinterpret_cast<Tb*>(base + L.G);
   Tb* LJ = reinterpret_cast<Tb*>(base + L.LJ);
   Tb* Phi = reinterpret_cast<Tb*>(base + L.Phi);
+  double* PhiD = reinterpret_cast<double*>(base + L.PhiD);
   Tb* Lphi = reinterpret_cast<Tb*>(base + L.Lphi);
   Tb* Gphi = reinterpret_cast<Tb*>(base + L.Gphi);
   double* Binv[2] = {reinterpret_cast<double*>(base + L.Binv0), reinterpret_cast<double*>(base + L.Binv1)};
@@ -196,8 +199,8 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
   const Tb* cE = een_coefs<Tb>(s);
   for (int i = lane; i < N; i += 32) {
     const double* ri = R + 3 * i;
-    Tb g0 = 0, g1 = 0, g2 = 0, lap = 0, lnj = 0;
-    double v = 0.0;
+    Tb g0 = 0, g1 = 0, g2 = 0, lap = 0;
+    double lnj = 0.0, v = 0.0;
     for (int a = 0; a < Nn; ++a) {
       double dx, dy, dz;
       const double rd = dist3(ri, s.nuc4 + 4 * a, dx, dy, dz);
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
       const Tb r = (Tb)rd, ir = (Tb)1 / r;
       Tb f, df, d2f;
       pade_eval<Tb, true>(en_coef(s, a), r, kap, f, df, d2f);
-      lnj += f;
+      lnj += (double)f;
       g0 += df * (Tb)dx * ir; g1 += df * (Tb)dy * ir; g2 += df * (Tb)dz * ir;
       lap += d2f + (Tb)2 * df * ir;
     }
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
       const Tb ex = (Tb)dx * ir, ey = (Tb)dy * ir, ez = (Tb)dz * ir;
       Tb f, df, d2f;
       pade_eval<Tb, true>(ee_coef(s, (i < Nup) == (j < Nup)), r, kap, f, df, d2f);
-      lnj += (Tb)0.5 * f;
+      lnj += 0.5 * (double)f;
       g0 += df * ex; g1 += df * ey; g2 += df * ez;
       lap += d2f + (Tb)2 * df * ir;
       if (s.een_on) {
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
           een_partials_us<Tb>(cE + kNeen * __ldg(s.nuc_elem + a), u, sv, tv, F, Fu, Fs, Fuu, Fss, Fus);
           const Tb fx = (Tb)ax * ira, fy = (Tb)ay * ira, fz = (Tb)az * ira;
           const Tb A = Fu * du, B = Fs * ds;
-          lnj += (Tb)0.5 * F;
+          lnj += 0.5 * (double)F;
           g0 += A * ex + B * fx; g1 += A * ey + B * fy; g2 += A * ez + B * fz;
           lap += Fuu * du * du + Fu * (d2u + (Tb)2 * du * ir) + Fss * ds * ds + Fs * (d2s + (Tb)2 * ds * ira) +
                  (Tb)2 * Fus * du * ds * (ex * fx + ey * fy + ez * fz);
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
     }
     G[3 * i] = g0; G[3 * i + 1] = g1; G[3 * i + 2] = g2;
     LJ[i] = lap;
-    lnJ_loc += (double)lnj;
+    lnJ_loc += lnj;
     V_loc += v;
   }
   const double lnJ = warp_sum(lnJ_loc);
@@ -252,6 +255,9 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
   __syncwarp();
 
   // ---- B. orbitals phi, grad phi, dressed Laplacian L = lap phi + 2 grad lnJ . grad phi ----
+  // Values of the basis functions and of the determinant orbitals are always double (they
+  // set ln|Phi| and the determinant ratios); gradients, Laplacians and the values of the
+  // other orbitals use the bulk type.
   const int nev = s.n_ev, nevd = s.n_ev_det, M = s.M;
   {
     Tb* bv = reinterpret_cast<Tb*>(scr);
@@ -259,36 +265,47 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
     Tb* by = bx + M;
     Tb* bz = by + M;
     Tb* bl = bz + M;
+    double* bvd = kSameType<Tb, double> ? reinterpret_cast<double*>(bv)
+                                        : reinterpret_cast<double*>(scr + align16(5 * M * (int)sizeof(Tb)));
     const Tb* cf = orb_coefs<Tb>(s);
     for (int e = 0; e < N; ++e) {
       basis_at<Tb, true>(s, lane, R[3 * e], R[3 * e + 1], R[3 * e + 2], bv, bx, by, bz, bl);
+      if (!kSameType<Tb, double>)
+        basis_at<double, false>(s, lane, R[3 * e], R[3 * e + 1], R[3 * e + 2], bvd, nullptr, nullptr, nullptr,
+                                nullptr);
       __syncwarp();
       const Tb G0 = G[3 * e], G1 = G[3 * e + 1], G2 = G[3 * e + 2];
       for (int q = lane; q < nev; q += 32) {
         const int k = __ldg(s.ev_orb + q);
-        const int lo = __ldg(s.orb_lo + k), hi = __ldg(s.orb_hi + k);
-        const Tb* c = cf + __ldg(s.orb_off + k) - lo;
+        const int lo = __ldg(s.orb_lo + k), hi = __ldg(s.orb_hi + k), off = __ldg(s.orb_off + k) - lo;
+        const Tb* c = cf + off;
         Tb v = 0, x = 0, y = 0, z = 0, lp = 0;
         for (int mu = lo; mu < hi; ++mu) {
           const Tb cm = __ldg(c + mu);
           v += cm * bv[mu]; x += cm * bx[mu]; y += cm * by[mu]; z += cm * bz[mu]; lp += cm * bl[mu];
         }
-        Phi[e * nev + q] = v;
         Lphi[e * nev + q] = lp + (Tb)2 * (G0 * x + G1 * y + G2 * z);
         if (q < nevd) {
+          double vd = 0.0;
+          const double* cd = s.orb_coef + off;
+          for (int mu = lo; mu < hi; ++mu) vd = fma(__ldg(cd + mu), bvd[mu], vd);
+          PhiD[e * nevd + q] = vd;
+          v = (Tb)vd;
           Gphi[(e * nevd + q) * 3] = x;
           Gphi[(e * nevd + q) * 3 + 1] = y;
           Gphi[(e * nevd + q) * 3 + 2] = z;
         }
+        Phi[e * nev + q] = v;
       }
       __syncwarp();
     }
   }
 
   // ---- C. Slater matrices: LU, inverses, ln|det|, t_u = tr(A^-1 L) ----
-  lu_all<Tb>(s, 0, lane, Phi, Lphi, nev, s.det_ev[0], L.G0, Binv[0], reinterpret_cast<double*>(scr), ldet, dsg, tdet);
-  lu_all<Tb>(s, 1, lane, Phi, Lphi, nev, s.det_ev[1], L.G1, Binv[1], reinterpret_cast<double*>(scr), ldet + U0,
-             dsg + U0, tdet + U0);
+  lu_all(s, 0, lane, PhiD, nevd, Lphi, nev, s.det_ev[0], L.G0, Binv[0], reinterpret_cast<double*>(scr), ldet, dsg,
+         tdet);
+  lu_all(s, 1, lane, PhiD, nevd, Lphi, nev, s.det_ev[1], L.G1, Binv[1], reinterpret_cast<double*>(scr), ldet + U0,
+         dsg + U0, tdet + U0);
   double lnPhi, sgnPhi;
   term_ratios(s, lane, ldet, dsg, rk, lnPhi, sgnPhi);
   // marginal weights W_u = sum_{k contains u} w_k and T_u = sum_{k contains u} w_k t_k
@@ -596,16 +613,16 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
   double* ldet = reinterpret_cast<double*>(base + L.ldet);
   double* dsg = reinterpret_cast<double*>(base + L.dsg);
   double* wk = reinterpret_cast<double*>(base + L.wk);
-  Tb* PhiO = reinterpret_cast<Tb*>(base + L.PhiO);
-  Tb* bas = reinterpret_cast<Tb*>(base + L.bas);
-  Tb* vrow = reinterpret_cast<Tb*>(base + L.vrow);
+  double* PhiO = reinterpret_cast<double*>(base + L.PhiO);
+  double* bas = reinterpret_cast<double*>(base + L.bas);
+  double* vrow = reinterpret_cast<double*>(base + L.vrow);
   double* rho = reinterpret_cast<double*>(base + L.rho);
   double* cvec = reinterpret_cast<double*>(base + L.cvec);
   double* scr = reinterpret_cast<double*>(base + L.scratch);
 
   const int N = s.N, Nn = s.Nn, Nup = s.Nup, U0 = s.U[0], ldo = L.nocc_max;
   const Tb kap = (Tb)s.kappa;
-  const Tb* cf = orb_coefs<Tb>(s);
+  const double* cf = s.orb_coef;
   const Tb* cE = een_coefs<Tb>(s);
   for (int i = lane; i < 3 * N; i += 32) R[i] = Rg[(size_t)w * 3 * N + i];
   __syncwarp();
@@ -616,20 +633,22 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
     // orbital values of every electron, then LU of every unique determinant (refresh)
     for (int e = 0; e < N; ++e) {
       const int sp = e >= Nup ? 1 : 0;
-      basis_at<Tb, false>(s, lane, R[3 * e], R[3 * e + 1], R[3 * e + 2], bas, nullptr, nullptr, nullptr, nullptr);
+      basis_at<double, false>(s, lane, R[3 * e], R[3 * e + 1], R[3 * e + 2], bas, nullptr, nullptr, nullptr,
+                              nullptr);
       __syncwarp();
       for (int q = lane; q < s.nocc[sp]; q += 32) {
         const int k = __ldg(s.occ_list[sp] + q);
         const int lo = __ldg(s.orb_lo + k), hi = __ldg(s.orb_hi + k);
-        const Tb* c = cf + __ldg(s.orb_off + k) - lo;
-        Tb v = 0;
-        for (int mu = lo; mu < hi; ++mu) v += __ldg(c + mu) * bas[mu];
+        const double* c = cf + __ldg(s.orb_off + k) - lo;
+        double v = 0.0;
+        for (int mu = lo; mu < hi; ++mu) v = fma(__ldg(c + mu), bas[mu], v);
         PhiO[e * ldo + q] = v;
       }
       __syncwarp();
     }
-    lu_all<Tb>(s, 0, lane, PhiO, nullptr, ldo, s.det_loc[0], L.G0, Binv[0], scr, ldet, dsg, nullptr);
-    lu_all<Tb>(s, 1, lane, PhiO, nullptr, ldo, s.det_loc[1], L.G1, Binv[1], scr, ldet + U0, dsg + U0, nullptr);
+    lu_all(s, 0, lane, PhiO, ldo, (const double*)nullptr, 0, s.det_loc[0], L.G0, Binv[0], scr, ldet, dsg, nullptr);
+    lu_all(s, 1, lane, PhiO, ldo, (const double*)nullptr, 0, s.det_loc[1], L.G1, Binv[1], scr, ldet + U0, dsg + U0,
+           nullptr);
     {
       double lnPhi, sgnPhi;
       term_ratios(s, lane, ldet, dsg, wk, lnPhi, sgnPhi);
@@ -647,14 +666,14 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
       rn[1] = __dadd_rn(R[3 * e + 1], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u1), 1.0)));
       rn[2] = __dadd_rn(R[3 * e + 2], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u2), 1.0)));
       // orbital row at the proposed position
-      basis_at<Tb, false>(s, lane, rn[0], rn[1], rn[2], bas, nullptr, nullptr, nullptr, nullptr);
+      basis_at<double, false>(s, lane, rn[0], rn[1], rn[2], bas, nullptr, nullptr, nullptr, nullptr);
       __syncwarp();
       for (int q = lane; q < s.nocc[sp]; q += 32) {
         const int k = __ldg(s.occ_list[sp] + q);
         const int lo = __ldg(s.orb_lo + k), hi = __ldg(s.orb_hi + k);
-        const Tb* c = cf + __ldg(s.orb_off + k) - lo;
-        Tb v = 0;
-        for (int mu = lo; mu < hi; ++mu) v += __ldg(c + mu) * bas[mu];
+        const double* c = cf + __ldg(s.orb_off + k) - lo;
+        double v = 0.0;
+        for (int mu = lo; mu < hi; ++mu) v = fma(__ldg(c + mu), bas[mu], v);
         vrow[q] = v;
       }
       __syncwarp();
@@ -664,7 +683,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
       for (int ub = 0; ub < U; ub += ng) {
         const int u = ub + g;
         double r = 0.0;
-        if (u < U && gl < n) r = (double)vrow[__ldg(dl + u * n + gl)] * Binv[sp][u * n * n + gl * n + ie];
+        if (u < U && gl < n) r = vrow[__ldg(dl + u * n + gl)] * Binv[sp][u * n * n + gl * n + ie];
         r = group_sum(r, G);
         if (u < U && gl == 0) rho[u] = r;
       }
@@ -722,7 +741,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
           if (act && gl < n) {
             const int j = gl;
             double wj = (j == ie) ? -1.0 : 0.0;
-            for (int o = 0; o < n; ++o) wj = fma((double)vrow[__ldg(dl + u * n + o)], B[o * n + j], wj);
+            for (int o = 0; o < n; ++o) wj = fma(vrow[__ldg(dl + u * n + o)], B[o * n + j], wj);
             const double f = wj / rho[u];
             for (int o = 0; o < n; ++o) B[o * n + j] = fma(-cv[o], f, B[o * n + j]);
           }
@@ -758,6 +777,7 @@ int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
   L.G = take(tb * 3 * N);
   L.LJ = take(tb * N);
   L.Phi = take(tb * N * s.n_ev);
+  L.PhiD = take(8 * N * std::max(s.n_ev_det, 1));
   L.Lphi = take(tb * N * s.n_ev);
   L.Gphi = take(tb * N * s.n_ev_det * 3);
   L.Binv0 = take(8 * s.U[0] * s.n[0] * s.n[0]);
@@ -768,7 +788,7 @@ int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
   L.Wdet = take(8 * Ut);
   L.Tdet = take(8 * Ut);
   L.rk = take(8 * s.nterm);
-  int scr = 5 * s.M * tb;
+  int scr = align16(5 * s.M * tb) + 8 * s.M;
   for (int sp = 0; sp < 2; ++sp) {
     const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
     scr = std::max(scr, ng * (8 * n * n + 4 * n) + 16);
@@ -802,9 +822,9 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.ldet = take(8 * Ut);
   L.dsg = take(8 * Ut);
   L.wk = take(8 * s.nterm);
-  L.PhiO = take(tb * N * L.nocc_max);
-  L.bas = take(tb * s.M);
-  L.vrow = take(tb * L.nocc_max);
+  L.PhiO = take(8 * N * L.nocc_max);
+  L.bas = take(8 * s.M);
+  L.vrow = take(8 * L.nocc_max);
   L.rho = take(8 * std::max(s.U[0], s.U[1]));
   int cv = 0, scr = 0;
   for (int sp = 0; sp < 2; ++sp) {

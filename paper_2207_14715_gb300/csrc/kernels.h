@@ -11,7 +11,7 @@ namespace vbq {
 // bytes from the start of the warp's region.
 struct EvalLayout {
   int wpb = 0, warp_bytes = 0;
-  int R, vg, G, LJ, Phi, Lphi, Gphi, Binv0, Binv1, ldet, dsg, tdet, Wdet, Tdet, rk, scratch, kacc, red;
+  int R, vg, G, LJ, Phi, PhiD, Lphi, Gphi, Binv0, Binv1, ldet, dsg, tdet, Wdet, Tdet, rk, scratch, kacc, red;
   int G0, G1;  // lane-group size per spin for the LU
 };
 
