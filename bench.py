@@ -232,6 +232,8 @@ def run_ours(args, ws, rank, local):
     O = torch.zeros((W, P), dtype=torch.float64, device=dev)
     dE = torch.zeros_like(O)
     nacc = torch.zeros(W, dtype=torch.int32, device=dev)
+    # persistent walker state (Slater inverses, ln|det|, signs) carried from one step to the next
+    state = torch.zeros((W, ctx.walker_state_size(0)), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     woff = rank * W
@@ -242,15 +244,17 @@ def run_ours(args, ws, rank, local):
         step_counter[0] += 1
         if ev is not None:
             ev[0].record(stream)
-        ctx.vmc_steps(0, prec, R, 1, spec.step, SEED, step0=k, walker_offset=woff, nacc=nacc)
+        ctx.vmc_steps(0, prec, R, 1, spec.step, SEED, step0=k, walker_offset=woff, refresh=0, state=state,
+                      state_valid=True, nacc=nacc)
         if ev is not None:
             ev[1].record(stream)
-        ctx.eval_walkers(0, prec, R, lp, sg, el, None, O, dE)
+        ctx.eval_walkers(0, prec, R, lp, sg, el, None, O, dE, state_out=state)
         if ev is not None:
             ev[2].record(stream)
 
-    # equilibration (untimed)
+    # equilibration (untimed), then one evaluation to initialise the walker state
     ctx.vmc_steps(0, vbqmc.MIXED, R, 30, spec.step, SEED, step0=10 ** 6, walker_offset=woff, nacc=nacc)
+    ctx.eval_walkers(0, vbqmc.MIXED, R, lp, sg, el, state_out=state)
     torch.cuda.synchronize()
     results = {}
     for name, prec in (("mixed", vbqmc.MIXED), ("fp64", vbqmc.FP64)):

@@ -119,32 +119,52 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc);
  * e-e-n free-parameter basis (row-major).  Returns VBQMC_OK or an error code. */
 int vbqmc_inspect_system(const vbqmc_system_desc* desc, int* info, int* terms, int max_terms, double* een_B);
 
+/* Per-walker persistent state: the inverse of every unique Slater matrix, its ln|det| and
+ * sign, as written by the evaluation and read by the next VMC sweep so that a sweep starts
+ * without a fresh LU.  *ndoubles receives the number of doubles per walker; a state buffer
+ * for W walkers holds W * ndoubles doubles, walker-major.  The layout is private to the
+ * library and valid only together with the positions it was computed at. */
+int vbqmc_walker_state_size(vbqmc_ctx* ctx, int sys_id, int* ndoubles);
+
 /* Evaluates the trial wave function at W walker positions (Sec. 2.1; Sec. 2.3.1 for E_L,
  * O_j and E_L,j).
- *   R      [W][N][3] device, in
- *   logpsi [W] device, out: ln|Psi|       sign [W] device, out: sign of Psi (0 if singular)
- *   eloc   [W] device, out: E_L = (H Psi)/Psi, Hamiltonian with nucleus-nucleus repulsion
- *   grad   [W][N][3] device or NULL, out: grad_i ln|Psi|
- *   O      [W][P] device or NULL, out: Psi_j/Psi
- *   dEL    [W][P] device or NULL, out: dE_L/dp_j (requires O != NULL)
+ *   R         [W][N][3] device, in
+ *   logpsi    [W] device, out: ln|Psi|       sign [W] device, out: sign of Psi (0 if singular)
+ *   eloc      [W] device, out: E_L = (H Psi)/Psi, Hamiltonian with nucleus-nucleus repulsion
+ *   grad      [W][N][3] device or NULL, out: grad_i ln|Psi|
+ *   O         [W][P] device or NULL, out: Psi_j/Psi
+ *   dEL       [W][P] device or NULL, out: dE_L/dp_j (requires O != NULL)
+ *   state_out [W][ndoubles] device or NULL, out: walker state at R (see above)
  * precision: VBQMC_FP64 or VBQMC_MIXED.  W may be 0. */
 int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const double* R, double* logpsi,
-                       double* sign, double* eloc, double* grad, double* O, double* dEL, void* stream);
+                       double* sign, double* eloc, double* grad, double* O, double* dEL, double* state_out,
+                       void* stream);
 
 /* VMC (Sec. 2.3.1): nsweeps sweeps of single-electron Metropolis moves over every walker,
  * electron i moved to r_i + step*(2u - 1) per coordinate and accepted when
- * u_acc < |Psi(R')/Psi(R)|^2; inverses of every unique Slater matrix are refreshed by LU at
- * the start of each sweep and updated by Sherman-Morrison after each accepted move.
+ * u_acc < |Psi(R')/Psi(R)|^2.  Determinant ratios and Sherman-Morrison updates of the
+ * inverses are double in both precision modes (the mixed mode forms the proposed orbital row
+ * in float).  The inverses at the start come from 'state' when state_valid != 0 (written by
+ * a previous evaluation at the current R), else from a fresh double-precision LU; within the
+ * call they are refreshed by LU every 'refresh' sweeps (0: never).
  * Random numbers: Philox4x32-10 keyed by seed, counter (walker_offset + w, step0 + sweep,
  * electron, (system_tag << 8) | purpose) with purpose 0 -> (u_x, u_y) and 1 -> (u_z, u_acc),
  * each uniform (x >> 11) * 2^-53 of one 64-bit half of the output.
- *   R    [W][N][3] device, in/out
- *   nacc [W] device int or NULL, out: accepted moves (accumulated over the sweeps)
+ *   R     [W][N][3] device, in/out
+ *   state [W][ndoubles] device or NULL, in (if state_valid) and out (if an evaluation runs)
+ *   nacc  [W] device int or NULL, out: accepted moves (accumulated over the sweeps)
  * After the last sweep, if logpsi/sign/eloc/O/dEL are non-NULL, the walkers are evaluated as
- * by vbqmc_eval_walkers (one walker-step = one sweep + that evaluation). */
+ * by vbqmc_eval_walkers and the state is rewritten (one walker-step = one sweep + that
+ * evaluation). */
 int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R, int nsweeps, double step,
-                    uint64_t seed, uint32_t step0, uint32_t system_tag, uint32_t walker_offset, int* nacc,
-                    double* logpsi, double* sign, double* eloc, double* O, double* dEL, void* stream);
+                    uint64_t seed, uint32_t step0, uint32_t system_tag, uint32_t walker_offset, int refresh,
+                    double* state, int state_valid, int* nacc, double* logpsi, double* sign, double* eloc,
+                    double* O, double* dEL, void* stream);
+
+/* Launch shape of the walker kernels for a loaded system: out[0..3] = walkers (warps) per
+ * thread block and shared-memory bytes per walker of the evaluation kernel, then the same two
+ * numbers for the sweep kernel, for the given precision mode. */
+int vbqmc_launch_info(vbqmc_ctx* ctx, int sys_id, int precision, int* out);
 
 /* Number of kernel launches enqueued by the last successful call on this context. */
 int vbqmc_last_launch_count(vbqmc_ctx* ctx);

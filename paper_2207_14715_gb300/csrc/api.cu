@@ -154,7 +154,9 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
                o_cparam = bb.add(h.cparam), o_jas_a = bb.add(h.jas_a), o_jas_b = bb.add(h.jas_b),
                o_een_c = bb.add(h.een_c), o_een_cf = bb.add(een_cf), o_een_B = bb.add(h.een_B),
                o_ko0 = bb.add(h.kap_off[0]), o_ko1 = bb.add(h.kap_off[1]), o_ke0 = bb.add(h.kap_ent[0]),
-               o_ke1 = bb.add(h.kap_ent[1]);
+               o_ke1 = bb.add(h.kap_ent[1]), o_oc0 = bb.add(h.occ_chunk[0]), o_oc1 = bb.add(h.occ_chunk[1]),
+               o_oco0 = bb.add(h.occ_chunk_off[0]), o_oco1 = bb.add(h.occ_chunk_off[1]), o_evc = bb.add(h.ev_chunk),
+               o_evco = bb.add(h.ev_chunk_off), o_dc = bb.add(h.det_chunk), o_dco = bb.add(h.det_chunk_off);
   cudaError_t e = cudaMalloc(&ls.blob, bb.bytes.size());
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(system tables)");
   ls.blob_bytes = bb.bytes.size();
@@ -216,6 +218,18 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.kap_off[1] = (const int*)(B + o_ko1);
   d.kap_ent[0] = (const int*)(B + o_ke0);
   d.kap_ent[1] = (const int*)(B + o_ke1);
+  for (int sp = 0; sp < 2; ++sp) d.n_occ_chunk[sp] = (int)(h.occ_chunk[sp].size() / 4);
+  d.n_ev_chunk = (int)(h.ev_chunk.size() / 4);
+  d.n_det_chunk = (int)(h.det_chunk.size() / 4);
+  d.occ_chunk[0] = (const int*)(B + o_oc0);
+  d.occ_chunk[1] = (const int*)(B + o_oc1);
+  d.occ_chunk_off[0] = (const int*)(B + o_oco0);
+  d.occ_chunk_off[1] = (const int*)(B + o_oco1);
+  d.ev_chunk = (const int*)(B + o_evc);
+  d.ev_chunk_off = (const int*)(B + o_evco);
+  d.det_chunk = (const int*)(B + o_dc);
+  d.det_chunk_off = (const int*)(B + o_dco);
+  d.state_doubles = h.U[0] * h.n[0] * h.n[0] + h.U[1] * h.n[1] * h.n[1] + 2 * (h.U[0] + h.U[1]);
   for (int p = 0; p < 2; ++p) {
     const int tb = p == VBQMC_MIXED ? 4 : 8;
     ls.lay_rc_eval[p] = vbq::make_eval_layout(d, tb, ctx->max_smem, ls.lay_eval[p]);
@@ -229,6 +243,19 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
 
 int vbqmc_last_launch_count(vbqmc_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
 
+int vbqmc_launch_info(vbqmc_ctx* ctx, int sys_id, int precision, int* out) {
+  if (!ctx || !out) return fail(VBQMC_ERR_ARG, "null argument");
+  if (sys_id < 0 || sys_id >= VBQMC_MAX_SYSTEMS || !ctx->sys[sys_id].loaded)
+    return fail(VBQMC_ERR_NOSYS, "no system loaded under this id");
+  if (precision != VBQMC_FP64 && precision != VBQMC_MIXED) return fail(VBQMC_ERR_ARG, "bad precision mode");
+  const LoadedSystem& s = ctx->sys[sys_id];
+  out[0] = s.lay_eval[precision].wpb;
+  out[1] = s.lay_eval[precision].warp_bytes;
+  out[2] = s.lay_sweep[precision].wpb;
+  out[3] = s.lay_sweep[precision].warp_bytes;
+  return VBQMC_OK;
+}
+
 static int check_call(vbqmc_ctx* ctx, int sys_id, int precision, int W) {
   if (!ctx) return fail(VBQMC_ERR_ARG, "null context");
   if (sys_id < 0 || sys_id >= VBQMC_MAX_SYSTEMS || !ctx->sys[sys_id].loaded)
@@ -238,8 +265,17 @@ static int check_call(vbqmc_ctx* ctx, int sys_id, int precision, int W) {
   return VBQMC_OK;
 }
 
+int vbqmc_walker_state_size(vbqmc_ctx* ctx, int sys_id, int* ndoubles) {
+  if (!ctx || !ndoubles) return fail(VBQMC_ERR_ARG, "null argument");
+  if (sys_id < 0 || sys_id >= VBQMC_MAX_SYSTEMS || !ctx->sys[sys_id].loaded)
+    return fail(VBQMC_ERR_NOSYS, "no system loaded under this id");
+  *ndoubles = ctx->sys[sys_id].dev.state_doubles;
+  return VBQMC_OK;
+}
+
 int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const double* R, double* logpsi,
-                       double* sign, double* eloc, double* grad, double* O, double* dEL, void* stream) {
+                       double* sign, double* eloc, double* grad, double* O, double* dEL, double* state_out,
+                       void* stream) {
   int rc = check_call(ctx, sys_id, precision, W);
   if (rc) return rc;
   ctx->last_launches = 0;
@@ -251,19 +287,21 @@ int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const d
   if ((O || dEL) && s.dev.P == 0) O = dEL = nullptr;
   DeviceGuard g(ctx->device);
   cudaError_t e = vbq::launch_eval(precision, s.dev, s.lay_eval[precision], W, R, logpsi, sign, eloc, grad, O, dEL,
-                                   (cudaStream_t)stream);
+                                   state_out, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "eval kernel launch");
   ctx->last_launches = 1;
   return VBQMC_OK;
 }
 
 int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R, int nsweeps, double step,
-                    uint64_t seed, uint32_t step0, uint32_t system_tag, uint32_t walker_offset, int* nacc,
-                    double* logpsi, double* sign, double* eloc, double* O, double* dEL, void* stream) {
+                    uint64_t seed, uint32_t step0, uint32_t system_tag, uint32_t walker_offset, int refresh,
+                    double* state, int state_valid, int* nacc, double* logpsi, double* sign, double* eloc, double* O,
+                    double* dEL, void* stream) {
   int rc = check_call(ctx, sys_id, precision, W);
   if (rc) return rc;
   ctx->last_launches = 0;
-  if (nsweeps < 0 || !(step > 0.0)) return fail(VBQMC_ERR_ARG, "bad sweep count or step");
+  if (nsweeps < 0 || !(step > 0.0) || refresh < 0) return fail(VBQMC_ERR_ARG, "bad sweep count, step or refresh");
+  if (state_valid && !state) return fail(VBQMC_ERR_ARG, "state_valid without state");
   if (system_tag > 0xffffffu) return fail(VBQMC_ERR_ARG, "system_tag must fit in 24 bits");
   if (W == 0) return VBQMC_OK;
   if (!R) return fail(VBQMC_ERR_ARG, "null R");
@@ -275,8 +313,9 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
   DeviceGuard g(ctx->device);
   int launches = 0;
   if (nsweeps > 0) {
-    cudaError_t e = vbq::launch_sweep(precision, s.dev, s.lay_sweep[precision], W, R, nsweeps, step, seed, step0,
-                                      system_tag, walker_offset, nacc, (cudaStream_t)stream);
+    cudaError_t e = vbq::launch_sweep(precision, s.dev, s.lay_sweep[precision], W, R, nsweeps, refresh,
+                                      state_valid ? state : nullptr, step, seed, step0, system_tag, walker_offset,
+                                      nacc, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
     ++launches;
   }
@@ -284,7 +323,7 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
     if (s.lay_rc_eval[precision]) return fail(s.lay_rc_eval[precision], "per-walker state exceeds shared memory");
     if ((O || dEL) && s.dev.P == 0) O = dEL = nullptr;
     cudaError_t e = vbq::launch_eval(precision, s.dev, s.lay_eval[precision], W, R, logpsi, sign, eloc, nullptr, O,
-                                     dEL, (cudaStream_t)stream);
+                                     dEL, state, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "eval kernel launch");
     ++launches;
   }

@@ -156,14 +156,21 @@ __device__ __forceinline__ void term_ratios(const SysDev& s, int lane, const dou
 }  // namespace
 
 // =====================================================================================
+// =====================================================================================
 // Evaluation kernel
 // =====================================================================================
+// Phases (one warp per walker):
+//   A  Jastrow ln J with grad_i ln J and lap_i ln J (lanes: electron x partner subset), potential
+//   B  orbitals at every electron: basis functions, then the contraction in balanced chunks
+//   C  Slater LU + inverses of every unique determinant, structure sum in the log domain,
+//      E_L and grad ln|Psi|; optionally the walker state (inverses, ln|det|, signs) is stored
+//   D  parameter derivatives (structure coefficients, Jastrow, orbital excitations)
 template <class Tb>
 __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLayout L, int W,
                                                    const double* __restrict__ Rg, double* __restrict__ logpsi,
                                                    double* __restrict__ sgn_out, double* __restrict__ eloc,
                                                    double* __restrict__ grad, double* __restrict__ Og,
-                                                   double* __restrict__ dELg) {
+                                                   double* __restrict__ dELg, double* __restrict__ state_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wl = threadIdx.x >> 5;
@@ -186,6 +193,8 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
   double* Tdet = reinterpret_cast<double*>(base + L.Tdet);
   double* rk = reinterpret_cast<double*>(base + L.rk);
   unsigned char* scr = base + L.scratch;
+  Tb* part = reinterpret_cast<Tb*>(base + L.part);
+  double* partd = reinterpret_cast<double*>(base + L.partd);
   double* kacc = reinterpret_cast<double*>(base + L.kacc);
   double* red = reinterpret_cast<double*>(base + L.red);
 
@@ -194,70 +203,83 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
   for (int i = lane; i < 3 * N; i += 32) R[i] = Rg[(size_t)w * 3 * N + i];
   __syncwarp();
 
-  // ---- A. Jastrow ln J, grad_i ln J, lap_i ln J and the potential (lane <-> electron) ----
+  // ---- A. Jastrow (S lanes per electron, partners split among them) ----
   double lnJ_loc = 0.0, V_loc = 0.0;
   const Tb* cE = een_coefs<Tb>(s);
-  for (int i = lane; i < N; i += 32) {
-    const double* ri = R + 3 * i;
-    Tb g0 = 0, g1 = 0, g2 = 0, lap = 0;
-    double lnj = 0.0, v = 0.0;
-    for (int a = 0; a < Nn; ++a) {
-      double dx, dy, dz;
-      const double rd = dist3(ri, s.nuc4 + 4 * a, dx, dy, dz);
-      v -= __ldg(s.nuc4 + 4 * a + 3) / rd;
-      const Tb r = (Tb)rd, ir = (Tb)1 / r;
-      Tb f, df, d2f;
-      pade_eval<Tb, true>(en_coef(s, a), r, kap, f, df, d2f);
-      lnj += (double)f;
-      g0 += df * (Tb)dx * ir; g1 += df * (Tb)dy * ir; g2 += df * (Tb)dz * ir;
-      lap += d2f + (Tb)2 * df * ir;
-    }
-    for (int j = 0; j < N; ++j) {
-      if (j == i) continue;
-      double dx, dy, dz;
-      const double rd = dist3(ri, R + 3 * j, dx, dy, dz);
-      v += 0.5 / rd;
-      const Tb r = (Tb)rd, ir = (Tb)1 / r;
-      const Tb ex = (Tb)dx * ir, ey = (Tb)dy * ir, ez = (Tb)dz * ir;
-      Tb f, df, d2f;
-      pade_eval<Tb, true>(ee_coef(s, (i < Nup) == (j < Nup)), r, kap, f, df, d2f);
-      lnj += 0.5 * (double)f;
-      g0 += df * ex; g1 += df * ey; g2 += df * ez;
-      lap += d2f + (Tb)2 * df * ir;
-      if (s.een_on) {
-        const Tb u = (Tb)1 / ((Tb)1 + kap * r);
-        const Tb du = -kap * u * u, d2u = (Tb)2 * kap * kap * u * u * u;
-        for (int a = 0; a < Nn; ++a) {
-          double ax, ay, az, bx, by, bz;
-          const double ria = dist3(ri, s.nuc4 + 4 * a, ax, ay, az);
-          const double rja = dist3(R + 3 * j, s.nuc4 + 4 * a, bx, by, bz);
-          const Tb ira = (Tb)1 / (Tb)ria;
-          const Tb sv = (Tb)1 / ((Tb)1 + kap * (Tb)ria), tv = (Tb)1 / ((Tb)1 + kap * (Tb)rja);
-          const Tb ds = -kap * sv * sv, d2s = (Tb)2 * kap * kap * sv * sv * sv;
-          Tb F, Fu, Fs, Fuu, Fss, Fus;
-          een_partials_us<Tb>(cE + kNeen * __ldg(s.nuc_elem + a), u, sv, tv, F, Fu, Fs, Fuu, Fss, Fus);
-          const Tb fx = (Tb)ax * ira, fy = (Tb)ay * ira, fz = (Tb)az * ira;
-          const Tb A = Fu * du, B = Fs * ds;
-          lnj += 0.5 * (double)F;
-          g0 += A * ex + B * fx; g1 += A * ey + B * fy; g2 += A * ez + B * fz;
-          lap += Fuu * du * du + Fu * (d2u + (Tb)2 * du * ir) + Fss * ds * ds + Fs * (d2s + (Tb)2 * ds * ira) +
-                 (Tb)2 * Fus * du * ds * (ex * fx + ey * fy + ez * fz);
+  {
+    const int S = L.lanes_per_e;
+    const int tot = N * S;
+    for (int b0 = 0; b0 < tot; b0 += 32) {
+      const int idx = b0 + lane, i = idx / S, h = idx % S;
+      const bool act = i < N;
+      Tb g0 = 0, g1 = 0, g2 = 0, lap = 0;
+      if (act) {
+        const double* ri = R + 3 * i;
+        double lnj = 0.0, v = 0.0;
+        for (int a = h; a < Nn; a += S) {
+          double dx, dy, dz;
+          const double rd = dist3(ri, s.nuc4 + 4 * a, dx, dy, dz);
+          v -= __ldg(s.nuc4 + 4 * a + 3) / rd;
+          const Tb r = (Tb)rd, ir = (Tb)1 / r;
+          Tb f, df, d2f;
+          pade_eval<Tb, true>(en_coef(s, a), r, kap, f, df, d2f);
+          lnj += (double)f;
+          g0 += df * (Tb)dx * ir; g1 += df * (Tb)dy * ir; g2 += df * (Tb)dz * ir;
+          lap += d2f + (Tb)2 * df * ir;
         }
+        for (int j = h; j < N; j += S) {
+          if (j == i) continue;
+          double dx, dy, dz;
+          const double rd = dist3(ri, R + 3 * j, dx, dy, dz);
+          v += 0.5 / rd;
+          const Tb r = (Tb)rd, ir = (Tb)1 / r;
+          const Tb ex = (Tb)dx * ir, ey = (Tb)dy * ir, ez = (Tb)dz * ir;
+          Tb f, df, d2f;
+          pade_eval<Tb, true>(ee_coef(s, (i < Nup) == (j < Nup)), r, kap, f, df, d2f);
+          lnj += 0.5 * (double)f;
+          g0 += df * ex; g1 += df * ey; g2 += df * ez;
+          lap += d2f + (Tb)2 * df * ir;
+          if (s.een_on) {
+            const Tb u = (Tb)1 / ((Tb)1 + kap * r);
+            const Tb du = -kap * u * u, d2u = (Tb)2 * kap * kap * u * u * u;
+            for (int a = 0; a < Nn; ++a) {
+              double ax, ay, az, bx, by, bz;
+              const double ria = dist3(ri, s.nuc4 + 4 * a, ax, ay, az);
+              const double rja = dist3(R + 3 * j, s.nuc4 + 4 * a, bx, by, bz);
+              const Tb ira = (Tb)1 / (Tb)ria;
+              const Tb sv = (Tb)1 / ((Tb)1 + kap * (Tb)ria), tv = (Tb)1 / ((Tb)1 + kap * (Tb)rja);
+              const Tb ds = -kap * sv * sv, d2s = (Tb)2 * kap * kap * sv * sv * sv;
+              Tb F, Fu, Fs, Fuu, Fss, Fus;
+              een_partials_us<Tb>(cE + kNeen * __ldg(s.nuc_elem + a), u, sv, tv, F, Fu, Fs, Fuu, Fss, Fus);
+              const Tb fx = (Tb)ax * ira, fy = (Tb)ay * ira, fz = (Tb)az * ira;
+              const Tb A = Fu * du, B = Fs * ds;
+              lnj += 0.5 * (double)F;
+              g0 += A * ex + B * fx; g1 += A * ey + B * fy; g2 += A * ez + B * fz;
+              lap += Fuu * du * du + Fu * (d2u + (Tb)2 * du * ir) + Fss * ds * ds + Fs * (d2s + (Tb)2 * ds * ira) +
+                     (Tb)2 * Fus * du * ds * (ex * fx + ey * fy + ez * fz);
+            }
+          }
+        }
+        lnJ_loc += lnj;
+        V_loc += v;
+      }
+      for (int o = S >> 1; o > 0; o >>= 1) {
+        g0 += __shfl_xor_sync(kFull, g0, o);
+        g1 += __shfl_xor_sync(kFull, g1, o);
+        g2 += __shfl_xor_sync(kFull, g2, o);
+        lap += __shfl_xor_sync(kFull, lap, o);
+      }
+      if (act && h == 0) {
+        G[3 * i] = g0; G[3 * i + 1] = g1; G[3 * i + 2] = g2;
+        LJ[i] = lap;
       }
     }
-    G[3 * i] = g0; G[3 * i + 1] = g1; G[3 * i + 2] = g2;
-    LJ[i] = lap;
-    lnJ_loc += lnj;
-    V_loc += v;
   }
   const double lnJ = warp_sum(lnJ_loc);
   const double V = warp_sum(V_loc) + s.vnn;
   __syncwarp();
 
-  // ---- B. orbitals phi, grad phi, dressed Laplacian L = lap phi + 2 grad lnJ . grad phi ----
-  // Values of the basis functions and of the determinant orbitals are always double (they
-  // set ln|Phi| and the determinant ratios); gradients, Laplacians and the values of the
-  // other orbitals use the bulk type.
+  // ---- B. orbitals: values (double for determinant orbitals), gradients, dressed Laplacian ----
   const int nev = s.n_ev, nevd = s.n_ev_det, M = s.M;
   {
     Tb* bv = reinterpret_cast<Tb*>(scr);
@@ -274,21 +296,43 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
         basis_at<double, false>(s, lane, R[3 * e], R[3 * e + 1], R[3 * e + 2], bvd, nullptr, nullptr, nullptr,
                                 nullptr);
       __syncwarp();
+      for (int c = lane; c < s.n_ev_chunk; c += 32) {
+        const int4 ch = __ldg(reinterpret_cast<const int4*>(s.ev_chunk) + c);
+        const Tb* cb = cf + ch.w;
+        Tb v = 0, x = 0, y = 0, z = 0, lp = 0;
+        for (int mu = ch.y; mu < ch.z; ++mu) {
+          const Tb cm = __ldg(cb + mu);
+          v += cm * bv[mu]; x += cm * bx[mu]; y += cm * by[mu]; z += cm * bz[mu]; lp += cm * bl[mu];
+        }
+        Tb* pp = part + 5 * c;
+        pp[0] = v; pp[1] = x; pp[2] = y; pp[3] = z; pp[4] = lp;
+      }
+      if (!kSameType<Tb, double>)
+        for (int c = lane; c < s.n_det_chunk; c += 32) {
+          const int4 ch = __ldg(reinterpret_cast<const int4*>(s.det_chunk) + c);
+          const double* cb = s.orb_coef + ch.w;
+          double vd = 0.0;
+          for (int mu = ch.y; mu < ch.z; ++mu) vd = fma(__ldg(cb + mu), bvd[mu], vd);
+          partd[c] = vd;
+        }
+      __syncwarp();
       const Tb G0 = G[3 * e], G1 = G[3 * e + 1], G2 = G[3 * e + 2];
       for (int q = lane; q < nev; q += 32) {
-        const int k = __ldg(s.ev_orb + q);
-        const int lo = __ldg(s.orb_lo + k), hi = __ldg(s.orb_hi + k), off = __ldg(s.orb_off + k) - lo;
-        const Tb* c = cf + off;
+        const int c0 = __ldg(s.ev_chunk_off + q), c1 = __ldg(s.ev_chunk_off + q + 1);
         Tb v = 0, x = 0, y = 0, z = 0, lp = 0;
-        for (int mu = lo; mu < hi; ++mu) {
-          const Tb cm = __ldg(c + mu);
-          v += cm * bv[mu]; x += cm * bx[mu]; y += cm * by[mu]; z += cm * bz[mu]; lp += cm * bl[mu];
+        for (int c = c0; c < c1; ++c) {
+          const Tb* pp = part + 5 * c;
+          v += pp[0]; x += pp[1]; y += pp[2]; z += pp[3]; lp += pp[4];
         }
         Lphi[e * nev + q] = lp + (Tb)2 * (G0 * x + G1 * y + G2 * z);
         if (q < nevd) {
           double vd = 0.0;
-          const double* cd = s.orb_coef + off;
-          for (int mu = lo; mu < hi; ++mu) vd = fma(__ldg(cd + mu), bvd[mu], vd);
+          if (kSameType<Tb, double>) {
+            vd = (double)v;
+          } else {
+            const int d0 = __ldg(s.det_chunk_off + q), d1 = __ldg(s.det_chunk_off + q + 1);
+            for (int c = d0; c < d1; ++c) vd += partd[c];
+          }
           PhiD[e * nevd + q] = vd;
           v = (Tb)vd;
           Gphi[(e * nevd + q) * 3] = x;
@@ -306,16 +350,27 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
          tdet);
   lu_all(s, 1, lane, PhiD, nevd, Lphi, nev, s.det_ev[1], L.G1, Binv[1], reinterpret_cast<double*>(scr), ldet + U0,
          dsg + U0, tdet + U0);
+  const int Utot = U0 + s.U[1];
+  if (state_out) {
+    // walker state: [Binv spin 0][Binv spin 1][ln|det| (U0+U1)][sign (U0+U1)]
+    double* st = state_out + (size_t)w * s.state_doubles;
+    const int nb0 = s.U[0] * s.n[0] * s.n[0], nb1 = s.U[1] * s.n[1] * s.n[1];
+    for (int q = lane; q < nb0; q += 32) st[q] = Binv[0][q];
+    for (int q = lane; q < nb1; q += 32) st[nb0 + q] = Binv[1][q];
+    for (int q = lane; q < Utot; q += 32) {
+      st[nb0 + nb1 + q] = ldet[q];
+      st[nb0 + nb1 + Utot + q] = dsg[q];
+    }
+  }
   double lnPhi, sgnPhi;
   term_ratios(s, lane, ldet, dsg, rk, lnPhi, sgnPhi);
-  // marginal weights W_u = sum_{k contains u} w_k and T_u = sum_{k contains u} w_k t_k
+  // K[Phi] and the marginal weights W_u = sum_{k contains u} w_k, T_u = sum_{k contains u} w_k t_k
   double kphi = 0.0;
   for (int k = lane; k < s.nterm; k += 32) {
     const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
     kphi += __ldg(s.term_coef + k) * rk[k] * (tdet[a] + tdet[U0 + b]);
   }
   kphi = warp_sum(kphi);
-  const int Utot = U0 + s.U[1];
   for (int ud = lane; ud < Utot; ud += 32) {
     const int sp = ud >= U0 ? 1 : 0, u = ud - (sp ? U0 : 0);
     double Wv = 0.0, Tv = 0.0;
@@ -389,35 +444,33 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
   }
   // D2. Jastrow parameters: O = d lnJ/d alpha, E_L,alpha = -1/2 sum_i (lap_i g + 2 grad_i g . grad_i ln|Psi|)
   if (s.jas_param) {
-    // e-n: a_2..a_6 per element (lane <-> electron)
+    // e-n: a_2..a_6 per element (lanes over electron-nucleus pairs)
     for (int E = 0; E < s.n_elem; ++E) {
       double aO[5] = {0, 0, 0, 0, 0}, aE[5] = {0, 0, 0, 0, 0};
-      for (int i = lane; i < N; i += 32) {
-        for (int a = 0; a < Nn; ++a) {
-          if (__ldg(s.nuc_elem + a) != E) continue;
-          double dx, dy, dz;
-          const double r = dist3(R + 3 * i, s.nuc4 + 4 * a, dx, dy, dz);
-          const PadeCoef c = en_coef(s, a);
-          const double den = 1.0 / (1.0 + s.kappa * r), Rr = r * den, dR = den * den,
-                       d2R = -2.0 * s.kappa * dR * den;
-          const double cosv = (dx * vg[3 * i] + dy * vg[3 * i + 1] + dz * vg[3 * i + 2]) / r;
-          const double pd = 1.0 / (1.0 + c.a2 * Rr);
-          double h[5], hR[5], hRR[5];
-          h[0] = -c.a1 * Rr * Rr * pd * pd;
-          hR[0] = -2.0 * c.a1 * Rr * pd * pd * pd;
-          hRR[0] = -2.0 * c.a1 * (1.0 - 2.0 * c.a2 * Rr) * pd * pd * pd * pd;
-          double Rm2 = 1.0;  // R^(p-2)
-          for (int p = 2; p <= 5; ++p) {
-            h[p - 1] = Rm2 * Rr * Rr;
-            hR[p - 1] = p * Rm2 * Rr;
-            hRR[p - 1] = p * (p - 1) * Rm2;
-            Rm2 *= Rr;
-          }
-          for (int q = 0; q < 5; ++q) {
-            const double g1 = hR[q] * dR, g2 = hRR[q] * dR * dR + hR[q] * d2R;
-            aO[q] += h[q];
-            aE[q] += -0.5 * (g2 + 2.0 * g1 / r + 2.0 * g1 * cosv);
-          }
+      for (int t = lane; t < N * Nn; t += 32) {
+        const int i = t / Nn, a = t % Nn;
+        if (__ldg(s.nuc_elem + a) != E) continue;
+        double dx, dy, dz;
+        const double r = dist3(R + 3 * i, s.nuc4 + 4 * a, dx, dy, dz);
+        const PadeCoef c = en_coef(s, a);
+        const double den = 1.0 / (1.0 + s.kappa * r), Rr = r * den, dR = den * den, d2R = -2.0 * s.kappa * dR * den;
+        const double cosv = (dx * vg[3 * i] + dy * vg[3 * i + 1] + dz * vg[3 * i + 2]) / r;
+        const double pd = 1.0 / (1.0 + c.a2 * Rr);
+        double h[5], hR[5], hRR[5];
+        h[0] = -c.a1 * Rr * Rr * pd * pd;
+        hR[0] = -2.0 * c.a1 * Rr * pd * pd * pd;
+        hRR[0] = -2.0 * c.a1 * (1.0 - 2.0 * c.a2 * Rr) * pd * pd * pd * pd;
+        double Rm2 = 1.0;  // R^(p-2)
+        for (int p = 2; p <= 5; ++p) {
+          h[p - 1] = Rm2 * Rr * Rr;
+          hR[p - 1] = p * Rm2 * Rr;
+          hRR[p - 1] = p * (p - 1) * Rm2;
+          Rm2 *= Rr;
+        }
+        for (int q = 0; q < 5; ++q) {
+          const double g1 = hR[q] * dR, g2 = hRR[q] * dR * dR + hR[q] * d2R;
+          aO[q] += h[q];
+          aE[q] += -0.5 * (g2 + 2.0 * g1 / r + 2.0 * g1 * cosv);
         }
       }
       for (int q = 0; q < 5; ++q) {
@@ -428,7 +481,7 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
         }
       }
     }
-    // e-e: b_2..b_6 (lane <-> pair)
+    // e-e: b_2..b_6 (lanes over pairs)
     {
       double bO[5] = {0, 0, 0, 0, 0}, bE[5] = {0, 0, 0, 0, 0};
       const int npair = N * (N - 1) / 2;
@@ -468,7 +521,7 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
         }
       }
     }
-    // e-e-n: raw terms per element (lane <-> pair), then theta = B^T raw
+    // e-e-n: raw terms per element (lanes over pairs), then theta = B^T raw
     if (s.een_on) {
       double* rawO = red;               // [23]
       double* rawE = red + kNeen;       // [23]
@@ -598,10 +651,15 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
 // =====================================================================================
 // VMC sweep kernel
 // =====================================================================================
+// Each sweep moves every electron once (Sec. 2.3.1).  The determinant inverses come from
+// the walker state written by the evaluation at the same positions, or from a fresh LU of
+// double-precision orbital values (first sweep without state, and every 'refresh' sweeps).
+// The proposed orbital row uses the bulk type; ratios and Sherman-Morrison updates are double.
 template <class Tb>
 __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepLayout L, int W, double* __restrict__ Rg,
-                                                    int nsweeps, double step, uint64_t seed, uint32_t step0,
-                                                    uint32_t tag, uint32_t woff, int* __restrict__ nacc) {
+                                                    int nsweeps, int refresh, const double* __restrict__ state_in,
+                                                    double step, uint64_t seed, uint32_t step0, uint32_t tag,
+                                                    uint32_t woff, int* __restrict__ nacc) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wl = threadIdx.x >> 5;
@@ -614,42 +672,64 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
   double* dsg = reinterpret_cast<double*>(base + L.dsg);
   double* wk = reinterpret_cast<double*>(base + L.wk);
   double* PhiO = reinterpret_cast<double*>(base + L.PhiO);
-  double* bas = reinterpret_cast<double*>(base + L.bas);
-  double* vrow = reinterpret_cast<double*>(base + L.vrow);
+  double* basd = reinterpret_cast<double*>(base + L.bas);
+  Tb* bas = reinterpret_cast<Tb*>(base + L.bas);
+  Tb* vrow = reinterpret_cast<Tb*>(base + L.vrow);
+  Tb* part = reinterpret_cast<Tb*>(base + L.part);
+  double* partd = reinterpret_cast<double*>(base + L.part);
   double* rho = reinterpret_cast<double*>(base + L.rho);
   double* cvec = reinterpret_cast<double*>(base + L.cvec);
   double* scr = reinterpret_cast<double*>(base + L.scratch);
 
   const int N = s.N, Nn = s.Nn, Nup = s.Nup, U0 = s.U[0], ldo = L.nocc_max;
   const Tb kap = (Tb)s.kappa;
-  const double* cf = s.orb_coef;
+  const Tb* cf = orb_coefs<Tb>(s);
   const Tb* cE = een_coefs<Tb>(s);
   for (int i = lane; i < 3 * N; i += 32) R[i] = Rg[(size_t)w * 3 * N + i];
+  if (state_in) {
+    const double* st = state_in + (size_t)w * s.state_doubles;
+    const int nb0 = s.U[0] * s.n[0] * s.n[0], nb1 = s.U[1] * s.n[1] * s.n[1], Ut = U0 + s.U[1];
+    for (int q = lane; q < nb0; q += 32) Binv[0][q] = st[q];
+    for (int q = lane; q < nb1; q += 32) Binv[1][q] = st[nb0 + q];
+    for (int q = lane; q < Ut; q += 32) {
+      ldet[q] = st[nb0 + nb1 + q];
+      dsg[q] = st[nb0 + nb1 + Ut + q];
+    }
+  }
   __syncwarp();
   int accepted = 0;
   const uint32_t wid = woff + (uint32_t)w;
 
   for (int sw = 0; sw < nsweeps; ++sw) {
-    // orbital values of every electron, then LU of every unique determinant (refresh)
-    for (int e = 0; e < N; ++e) {
-      const int sp = e >= Nup ? 1 : 0;
-      basis_at<double, false>(s, lane, R[3 * e], R[3 * e + 1], R[3 * e + 2], bas, nullptr, nullptr, nullptr,
-                              nullptr);
-      __syncwarp();
-      for (int q = lane; q < s.nocc[sp]; q += 32) {
-        const int k = __ldg(s.occ_list[sp] + q);
-        const int lo = __ldg(s.orb_lo + k), hi = __ldg(s.orb_hi + k);
-        const double* c = cf + __ldg(s.orb_off + k) - lo;
-        double v = 0.0;
-        for (int mu = lo; mu < hi; ++mu) v = fma(__ldg(c + mu), bas[mu], v);
-        PhiO[e * ldo + q] = v;
+    const bool do_refresh = (sw == 0) ? (state_in == nullptr) : (refresh > 0 && sw % refresh == 0);
+    if (do_refresh) {
+      // double-precision orbital values of every electron, then LU of every unique determinant
+      for (int e = 0; e < N; ++e) {
+        const int sp = e >= Nup ? 1 : 0;
+        basis_at<double, false>(s, lane, R[3 * e], R[3 * e + 1], R[3 * e + 2], basd, nullptr, nullptr, nullptr,
+                                nullptr);
+        __syncwarp();
+        for (int c = lane; c < s.n_occ_chunk[sp]; c += 32) {
+          const int4 ch = __ldg(reinterpret_cast<const int4*>(s.occ_chunk[sp]) + c);
+          const double* cb = s.orb_coef + ch.w;
+          double v = 0.0;
+          for (int mu = ch.y; mu < ch.z; ++mu) v = fma(__ldg(cb + mu), basd[mu], v);
+          partd[c] = v;
+        }
+        __syncwarp();
+        for (int q = lane; q < s.nocc[sp]; q += 32) {
+          const int c0 = __ldg(s.occ_chunk_off[sp] + q), c1 = __ldg(s.occ_chunk_off[sp] + q + 1);
+          double v = 0.0;
+          for (int c = c0; c < c1; ++c) v += partd[c];
+          PhiO[e * ldo + q] = v;
+        }
+        __syncwarp();
       }
-      __syncwarp();
+      lu_all(s, 0, lane, PhiO, ldo, (const double*)nullptr, 0, s.det_loc[0], L.G0, Binv[0], scr, ldet, dsg, nullptr);
+      lu_all(s, 1, lane, PhiO, ldo, (const double*)nullptr, 0, s.det_loc[1], L.G1, Binv[1], scr, ldet + U0, dsg + U0,
+             nullptr);
     }
-    lu_all(s, 0, lane, PhiO, ldo, (const double*)nullptr, 0, s.det_loc[0], L.G0, Binv[0], scr, ldet, dsg, nullptr);
-    lu_all(s, 1, lane, PhiO, ldo, (const double*)nullptr, 0, s.det_loc[1], L.G1, Binv[1], scr, ldet + U0, dsg + U0,
-           nullptr);
-    {
+    if (do_refresh || sw == 0) {
       double lnPhi, sgnPhi;
       term_ratios(s, lane, ldet, dsg, wk, lnPhi, sgnPhi);
       for (int k = lane; k < s.nterm; k += 32) wk[k] *= __ldg(s.term_coef + k);  // w_k = C_k D_k / Phi
@@ -665,15 +745,21 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
       rn[0] = __dadd_rn(R[3 * e], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u0), 1.0)));
       rn[1] = __dadd_rn(R[3 * e + 1], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u1), 1.0)));
       rn[2] = __dadd_rn(R[3 * e + 2], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u2), 1.0)));
-      // orbital row at the proposed position
-      basis_at<double, false>(s, lane, rn[0], rn[1], rn[2], bas, nullptr, nullptr, nullptr, nullptr);
+      // orbital row at the proposed position (bulk type), contraction in balanced chunks
+      basis_at<Tb, false>(s, lane, rn[0], rn[1], rn[2], bas, nullptr, nullptr, nullptr, nullptr);
+      __syncwarp();
+      for (int c = lane; c < s.n_occ_chunk[sp]; c += 32) {
+        const int4 ch = __ldg(reinterpret_cast<const int4*>(s.occ_chunk[sp]) + c);
+        const Tb* cb = cf + ch.w;
+        Tb v = 0;
+        for (int mu = ch.y; mu < ch.z; ++mu) v += __ldg(cb + mu) * bas[mu];
+        part[c] = v;
+      }
       __syncwarp();
       for (int q = lane; q < s.nocc[sp]; q += 32) {
-        const int k = __ldg(s.occ_list[sp] + q);
-        const int lo = __ldg(s.orb_lo + k), hi = __ldg(s.orb_hi + k);
-        const double* c = cf + __ldg(s.orb_off + k) - lo;
-        double v = 0.0;
-        for (int mu = lo; mu < hi; ++mu) v = fma(__ldg(c + mu), bas[mu], v);
+        const int c0 = __ldg(s.occ_chunk_off[sp] + q), c1 = __ldg(s.occ_chunk_off[sp] + q + 1);
+        Tb v = 0;
+        for (int c = c0; c < c1; ++c) v += part[c];
         vrow[q] = v;
       }
       __syncwarp();
@@ -683,7 +769,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
       for (int ub = 0; ub < U; ub += ng) {
         const int u = ub + g;
         double r = 0.0;
-        if (u < U && gl < n) r = vrow[__ldg(dl + u * n + gl)] * Binv[sp][u * n * n + gl * n + ie];
+        if (u < U && gl < n) r = (double)vrow[__ldg(dl + u * n + gl)] * Binv[sp][u * n * n + gl * n + ie];
         r = group_sum(r, G);
         if (u < U && gl == 0) rho[u] = r;
       }
@@ -691,41 +777,44 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
       double rphi = 0.0;
       for (int k = lane; k < s.nterm; k += 32) rphi += wk[k] * rho[__ldg(s.term_det + 2 * k + sp)];
       rphi = warp_sum(rphi);
-      // Jastrow change of the terms that involve electron e
+      // Jastrow change of the terms that involve electron e: items e-n (a), e-e (j), e-e-n (j, a)
       Tb dj = 0;
       const double* ro = R + 3 * e;
-      for (int j = lane; j < N; j += 32) {
-        if (j == e) continue;
+      const int nitem = Nn + (N - 1) * (1 + (s.een_on ? Nn : 0));
+      for (int t = lane; t < nitem; t += 32) {
         double dx, dy, dz;
-        const double r_old = dist3(ro, R + 3 * j, dx, dy, dz);
-        const double r_new = dist3(rn, R + 3 * j, dx, dy, dz);
-        const PadeCoef c = ee_coef(s, (e < Nup) == (j < Nup));
-        Tb f1, f0, t0, t1;
-        pade_eval<Tb, false>(c, (Tb)r_new, kap, f1, t0, t1);
-        pade_eval<Tb, false>(c, (Tb)r_old, kap, f0, t0, t1);
-        dj += f1 - f0;
-        if (s.een_on) {
-          const Tb un = (Tb)1 / ((Tb)1 + kap * (Tb)r_new), uo = (Tb)1 / ((Tb)1 + kap * (Tb)r_old);
-          for (int a = 0; a < Nn; ++a) {
-            const double ran = dist3(rn, s.nuc4 + 4 * a, dx, dy, dz);
-            const double rao = dist3(ro, s.nuc4 + 4 * a, dx, dy, dz);
-            const double rja = dist3(R + 3 * j, s.nuc4 + 4 * a, dx, dy, dz);
-            const Tb tv = (Tb)1 / ((Tb)1 + kap * (Tb)rja);
-            const Tb* cc = cE + kNeen * __ldg(s.nuc_elem + a);
-            dj += een_value<Tb>(cc, un, (Tb)1 / ((Tb)1 + kap * (Tb)ran), tv) -
-                  een_value<Tb>(cc, uo, (Tb)1 / ((Tb)1 + kap * (Tb)rao), tv);
-          }
+        if (t < Nn) {
+          const double r_new = dist3(rn, s.nuc4 + 4 * t, dx, dy, dz);
+          const double r_old = dist3(ro, s.nuc4 + 4 * t, dx, dy, dz);
+          const PadeCoef c = en_coef(s, t);
+          Tb f1, f0, t0, t1;
+          pade_eval<Tb, false>(c, (Tb)r_new, kap, f1, t0, t1);
+          pade_eval<Tb, false>(c, (Tb)r_old, kap, f0, t0, t1);
+          dj += f1 - f0;
+          continue;
         }
-      }
-      for (int a = lane; a < Nn; a += 32) {
-        double dx, dy, dz;
-        const double r_new = dist3(rn, s.nuc4 + 4 * a, dx, dy, dz);
-        const double r_old = dist3(ro, s.nuc4 + 4 * a, dx, dy, dz);
-        const PadeCoef c = en_coef(s, a);
-        Tb f1, f0, t0, t1;
-        pade_eval<Tb, false>(c, (Tb)r_new, kap, f1, t0, t1);
-        pade_eval<Tb, false>(c, (Tb)r_old, kap, f0, t0, t1);
-        dj += f1 - f0;
+        const int t2 = t - Nn, per = 1 + (s.een_on ? Nn : 0);
+        int j = t2 / per;
+        const int a = t2 % per - 1;  // -1: the e-e term itself
+        if (j >= e) ++j;
+        const double r_new = dist3(rn, R + 3 * j, dx, dy, dz);
+        const double r_old = dist3(ro, R + 3 * j, dx, dy, dz);
+        if (a < 0) {
+          const PadeCoef c = ee_coef(s, (e < Nup) == (j < Nup));
+          Tb f1, f0, t0, t1;
+          pade_eval<Tb, false>(c, (Tb)r_new, kap, f1, t0, t1);
+          pade_eval<Tb, false>(c, (Tb)r_old, kap, f0, t0, t1);
+          dj += f1 - f0;
+        } else {
+          const Tb un = (Tb)1 / ((Tb)1 + kap * (Tb)r_new), uo = (Tb)1 / ((Tb)1 + kap * (Tb)r_old);
+          const double ran = dist3(rn, s.nuc4 + 4 * a, dx, dy, dz);
+          const double rao = dist3(ro, s.nuc4 + 4 * a, dx, dy, dz);
+          const double rja = dist3(R + 3 * j, s.nuc4 + 4 * a, dx, dy, dz);
+          const Tb tv = (Tb)1 / ((Tb)1 + kap * (Tb)rja);
+          const Tb* cc = cE + kNeen * __ldg(s.nuc_elem + a);
+          dj += een_value<Tb>(cc, un, (Tb)1 / ((Tb)1 + kap * (Tb)ran), tv) -
+                een_value<Tb>(cc, uo, (Tb)1 / ((Tb)1 + kap * (Tb)rao), tv);
+        }
       }
       const double dJ = warp_sum((double)dj);
       const double prob = rphi * rphi * exp(2.0 * dJ);
@@ -741,7 +830,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
           if (act && gl < n) {
             const int j = gl;
             double wj = (j == ie) ? -1.0 : 0.0;
-            for (int o = 0; o < n; ++o) wj = fma(vrow[__ldg(dl + u * n + o)], B[o * n + j], wj);
+            for (int o = 0; o < n; ++o) wj = fma((double)vrow[__ldg(dl + u * n + o)], B[o * n + j], wj);
             const double f = wj / rho[u];
             for (int o = 0; o < n; ++o) B[o * n + j] = fma(-cv[o], f, B[o * n + j]);
           }
@@ -772,6 +861,9 @@ int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
   const int N = s.N, Ut = s.U[0] + s.U[1];
   L.G0 = group_size(s.n[0]);
   L.G1 = group_size(s.n[1]);
+  int S = 1;
+  while (2 * S * N <= 32) S *= 2;
+  L.lanes_per_e = S;
   L.R = take(8 * 3 * N);
   L.vg = take(8 * 3 * N);
   L.G = take(tb * 3 * N);
@@ -795,6 +887,8 @@ int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
     scr = std::max(scr, 2 * n * s.n_ev * tb);
   }
   L.scratch = take(scr);
+  L.part = take(5 * tb * std::max(s.n_ev_chunk, 1));
+  L.partd = take(8 * std::max(s.n_det_chunk, 1));
   L.kacc = take(8 * 2 * std::max(s.n_kappa, 1));
   L.red = take(8 * 64);
   L.warp_bytes = off;
@@ -825,6 +919,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.PhiO = take(8 * N * L.nocc_max);
   L.bas = take(8 * s.M);
   L.vrow = take(8 * L.nocc_max);
+  L.part = take(8 * std::max(std::max(s.n_occ_chunk[0], s.n_occ_chunk[1]), 1));
   L.rho = take(8 * std::max(s.U[0], s.U[1]));
   int cv = 0, scr = 0;
   for (int sp = 0; sp < 2; ++sp) {
@@ -844,38 +939,43 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
 
 template <class Tb>
 static cudaError_t launch_eval_t(const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
-                                 double* sign, double* eloc, double* grad, double* O, double* dEL, cudaStream_t st) {
+                                 double* sign, double* eloc, double* grad, double* O, double* dEL, double* state_out,
+                                 cudaStream_t st) {
   const int smem = L.wpb * L.warp_bytes;
   cudaError_t e = cudaFuncSetAttribute(eval_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int blocks = (W + L.wpb - 1) / L.wpb;
-  eval_kernel<Tb><<<blocks, 32 * L.wpb, smem, st>>>(s, L, W, R, logpsi, sign, eloc, grad, O, dEL);
+  eval_kernel<Tb><<<blocks, 32 * L.wpb, smem, st>>>(s, L, W, R, logpsi, sign, eloc, grad, O, dEL, state_out);
   return cudaGetLastError();
 }
 
 template <class Tb>
-static cudaError_t launch_sweep_t(const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps, double step,
-                                  uint64_t seed, uint32_t step0, uint32_t tag, uint32_t woff, int* nacc,
-                                  cudaStream_t st) {
+static cudaError_t launch_sweep_t(const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps, int refresh,
+                                  const double* state_in, double step, uint64_t seed, uint32_t step0, uint32_t tag,
+                                  uint32_t woff, int* nacc, cudaStream_t st) {
   const int smem = L.wpb * L.warp_bytes;
   cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int blocks = (W + L.wpb - 1) / L.wpb;
-  sweep_kernel<Tb><<<blocks, 32 * L.wpb, smem, st>>>(s, L, W, R, nsweeps, step, seed, step0, tag, woff, nacc);
+  sweep_kernel<Tb><<<blocks, 32 * L.wpb, smem, st>>>(s, L, W, R, nsweeps, refresh, state_in, step, seed, step0, tag,
+                                                     woff, nacc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_eval(int precision, const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
-                        double* sign, double* eloc, double* grad, double* O, double* dEL, cudaStream_t st) {
-  if (precision == VBQMC_MIXED) return launch_eval_t<float>(s, L, W, R, logpsi, sign, eloc, grad, O, dEL, st);
-  return launch_eval_t<double>(s, L, W, R, logpsi, sign, eloc, grad, O, dEL, st);
+                        double* sign, double* eloc, double* grad, double* O, double* dEL, double* state_out,
+                        cudaStream_t st) {
+  if (precision == VBQMC_MIXED)
+    return launch_eval_t<float>(s, L, W, R, logpsi, sign, eloc, grad, O, dEL, state_out, st);
+  return launch_eval_t<double>(s, L, W, R, logpsi, sign, eloc, grad, O, dEL, state_out, st);
 }
 
 cudaError_t launch_sweep(int precision, const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps,
-                         double step, uint64_t seed, uint32_t step0, uint32_t tag, uint32_t woff, int* nacc,
-                         cudaStream_t st) {
-  if (precision == VBQMC_MIXED) return launch_sweep_t<float>(s, L, W, R, nsweeps, step, seed, step0, tag, woff, nacc, st);
-  return launch_sweep_t<double>(s, L, W, R, nsweeps, step, seed, step0, tag, woff, nacc, st);
+                         int refresh, const double* state_in, double step, uint64_t seed, uint32_t step0, uint32_t tag,
+                         uint32_t woff, int* nacc, cudaStream_t st) {
+  if (precision == VBQMC_MIXED)
+    return launch_sweep_t<float>(s, L, W, R, nsweeps, refresh, state_in, step, seed, step0, tag, woff, nacc, st);
+  return launch_sweep_t<double>(s, L, W, R, nsweeps, refresh, state_in, step, seed, step0, tag, woff, nacc, st);
 }
 
 }  // namespace vbq

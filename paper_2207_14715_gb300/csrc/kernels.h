@@ -11,13 +11,15 @@ namespace vbq {
 // bytes from the start of the warp's region.
 struct EvalLayout {
   int wpb = 0, warp_bytes = 0;
-  int R, vg, G, LJ, Phi, PhiD, Lphi, Gphi, Binv0, Binv1, ldet, dsg, tdet, Wdet, Tdet, rk, scratch, kacc, red;
-  int G0, G1;  // lane-group size per spin for the LU
+  int R, vg, G, LJ, Phi, PhiD, Lphi, Gphi, Binv0, Binv1, ldet, dsg, tdet, Wdet, Tdet, rk, scratch, part, partd,
+      kacc, red;
+  int G0, G1;        // lane-group size per spin for the LU
+  int lanes_per_e;   // lanes sharing one electron in the Jastrow phase
 };
 
 struct SweepLayout {
   int wpb = 0, warp_bytes = 0;
-  int R, Binv0, Binv1, ldet, dsg, wk, PhiO, bas, vrow, rho, cvec, scratch;
+  int R, Binv0, Binv1, ldet, dsg, wk, PhiO, bas, vrow, part, rho, cvec, scratch;
   int nocc_max;
   int G0, G1;
 };
@@ -26,9 +28,10 @@ int make_eval_layout(const SysDev& s, int bulk_bytes, int max_smem, EvalLayout& 
 int make_sweep_layout(const SysDev& s, int bulk_bytes, int max_smem, SweepLayout& L);
 
 cudaError_t launch_eval(int precision, const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
-                        double* sign, double* eloc, double* grad, double* O, double* dEL, cudaStream_t st);
+                        double* sign, double* eloc, double* grad, double* O, double* dEL, double* state_out,
+                        cudaStream_t st);
 cudaError_t launch_sweep(int precision, const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps,
-                         double step, uint64_t seed, uint32_t step0, uint32_t tag, uint32_t woff, int* nacc,
-                         cudaStream_t st);
+                         int refresh, const double* state_in, double step, uint64_t seed, uint32_t step0, uint32_t tag,
+                         uint32_t woff, int* nacc, cudaStream_t st);
 
 }  // namespace vbq

@@ -154,6 +154,41 @@ static void expand_structure(const std::vector<int>& inact, const std::vector<st
   }
 }
 
+// Splits the nonzero coefficient ranges of the given orbitals into chunks so that 32 lanes
+// finish together.  The chunk length L minimises the critical path of one warp:
+//   ceil(chunks(L) / 32) * (L + 8)  [chunk loop, 8 ~ per-chunk overhead]
+//   + ceil(orbitals / 32) * max chunks of one orbital  [per-orbital sum of the partials],
+// with L >= 4.
+static void make_chunks(const SysHost& s, const std::vector<int>& orbs, std::vector<int>& chunks,
+                        std::vector<int>& off) {
+  chunks.clear();
+  off.assign(1, 0);
+  int maxlen = 1;
+  for (int k : orbs) maxlen = std::max(maxlen, s.orb_hi[k] - s.orb_lo[k]);
+  int bestL = maxlen;
+  long bestcost = -1;
+  const long norb = (long)orbs.size();
+  for (int L = std::min(4, maxlen); L <= maxlen; ++L) {
+    long nch = 0, maxc = 1;
+    for (int k : orbs) {
+      const long c = std::max(1, (s.orb_hi[k] - s.orb_lo[k] + L - 1) / L);
+      nch += c;
+      maxc = std::max(maxc, c);
+    }
+    const long cost = ((nch + 31) / 32) * (L + 8) + ((norb + 31) / 32) * maxc;
+    if (bestcost < 0 || cost < bestcost) { bestcost = cost; bestL = L; }
+  }
+  for (size_t q = 0; q < orbs.size(); ++q) {
+    const int k = orbs[q], lo = s.orb_lo[k], hi = s.orb_hi[k], len = hi - lo;
+    const int nc = std::max(1, (len + bestL - 1) / bestL);
+    for (int c = 0; c < nc; ++c) {
+      const int b = lo + (int)((long)len * c / nc), e = lo + (int)((long)len * (c + 1) / nc);
+      chunks.insert(chunks.end(), {(int)q, b, e, s.orb_off[k] - lo});
+    }
+    off.push_back((int)(chunks.size() / 4));
+  }
+}
+
 #define VBQ_REQUIRE(cond, msg)                 \
   do {                                         \
     if (!(cond)) {                             \
@@ -338,6 +373,10 @@ int build_system(const vbqmc_system_desc* d, SysHost& s, std::string& err) {
       s.kap_off[sp].push_back((int)(s.kap_ent[sp].size() / 4));
     }
   }
+  // contraction work chunks
+  for (int sp = 0; sp < 2; ++sp) make_chunks(s, s.occ_list[sp], s.occ_chunk[sp], s.occ_chunk_off[sp]);
+  make_chunks(s, s.ev_orb, s.ev_chunk, s.ev_chunk_off);
+  make_chunks(s, std::vector<int>(s.ev_orb.begin(), s.ev_orb.begin() + s.n_ev_det), s.det_chunk, s.det_chunk_off);
   // Jastrow
   s.kappa = d->kappa;
   s.b1_anti = d->b1_anti;

@@ -60,6 +60,12 @@ struct SysHost {
   int n_kappa = 0;
   std::vector<int> kap_off[2];         // [U_s + 1]
   std::vector<int> kap_ent[2];         // [n_ent][4]: j, slot of l, eval index of k, 0
+  // balanced work chunks of the orbital contraction phi_q = sum_mu lambda_{q,mu} chi_mu:
+  // [n_chunk][4] = (orbital slot q, first mu, one-past-last mu, coefficient base so that the
+  // coefficient of mu is orb_coef[base + mu]); chunk_off[q] .. chunk_off[q+1] are q's chunks.
+  std::vector<int> occ_chunk[2], occ_chunk_off[2];   // per spin, over occ_list[spin]
+  std::vector<int> ev_chunk, ev_chunk_off;            // over all evaluated orbitals
+  std::vector<int> det_chunk, det_chunk_off;          // over the first n_ev_det evaluated orbitals
 };
 
 // Builds the tables; returns VBQMC_OK or an error code with a message in 'err'.
@@ -105,6 +111,14 @@ struct SysDev {
   const double* een_B;
   const int* kap_off[2];
   const int* kap_ent[2];               // [n_ent][4]: j, slot of l, eval index of k, 0
+  int n_occ_chunk[2], n_ev_chunk, n_det_chunk;
+  const int* occ_chunk[2];
+  const int* occ_chunk_off[2];
+  const int* ev_chunk;
+  const int* ev_chunk_off;
+  const int* det_chunk;
+  const int* det_chunk_off;
+  int state_doubles;                   // persistent walker state: inverses, ln|det|, signs
 };
 
 }  // namespace vbq

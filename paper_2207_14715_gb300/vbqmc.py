@@ -50,7 +50,8 @@ class _Desc(ctypes.Structure):
 
 
 EXPORTED = ["vbqmc_create", "vbqmc_destroy", "vbqmc_last_error", "vbqmc_set_system", "vbqmc_inspect_system",
-            "vbqmc_eval_walkers", "vbqmc_vmc_steps", "vbqmc_last_launch_count"]
+            "vbqmc_walker_state_size", "vbqmc_eval_walkers", "vbqmc_vmc_steps", "vbqmc_launch_info",
+            "vbqmc_last_launch_count"]
 
 _LIB = None
 
@@ -68,11 +69,14 @@ def lib():
         L.vbqmc_set_system.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(_Desc)]
         L.vbqmc_inspect_system.argtypes = [ctypes.POINTER(_Desc), _c_int_p, _c_int_p, ctypes.c_int, _c_dbl_p]
         vp = ctypes.c_void_p
-        L.vbqmc_eval_walkers.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.vbqmc_walker_state_size.argtypes = [vp, ctypes.c_int, _c_int_p]
+        L.vbqmc_eval_walkers.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp,
+                                         vp]
         L.vbqmc_vmc_steps.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double,
-                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, vp, vp, vp,
-                                      vp, vp, vp, vp]
+                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
+                                      vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
         L.vbqmc_last_launch_count.argtypes = [vp]
+        L.vbqmc_launch_info.argtypes = [vp, ctypes.c_int, ctypes.c_int, _c_int_p]
         _LIB = L
     return _LIB
 
@@ -173,19 +177,34 @@ class Context:
     def last_launch_count(self) -> int:
         return int(lib().vbqmc_last_launch_count(self.h))
 
-    def eval_walkers(self, sys_id, precision, R, logpsi, sign, eloc, grad=None, O=None, dEL=None, stream=None):
+    def launch_info(self, sys_id, precision) -> dict:
+        out = np.zeros(4, np.int32)
+        _check(lib().vbqmc_launch_info(self.h, int(sys_id), int(precision), out.ctypes.data_as(_c_int_p)))
+        return {"eval_walkers_per_block": int(out[0]), "eval_smem_per_walker": int(out[1]),
+                "sweep_walkers_per_block": int(out[2]), "sweep_smem_per_walker": int(out[3])}
+
+    def walker_state_size(self, sys_id) -> int:
+        n = ctypes.c_int(0)
+        _check(lib().vbqmc_walker_state_size(self.h, int(sys_id), ctypes.byref(n)))
+        return int(n.value)
+
+    def eval_walkers(self, sys_id, precision, R, logpsi, sign, eloc, grad=None, O=None, dEL=None, state_out=None,
+                     stream=None):
         """R [W, N, 3] float64 CUDA tensor; outputs preallocated float64 CUDA tensors."""
         W = R.shape[0]
         _check(lib().vbqmc_eval_walkers(self.h, int(sys_id), int(precision), int(W), _ptr(R), _ptr(logpsi),
-                                        _ptr(sign), _ptr(eloc), _ptr(grad), _ptr(O), _ptr(dEL), _stream(stream)))
+                                        _ptr(sign), _ptr(eloc), _ptr(grad), _ptr(O), _ptr(dEL), _ptr(state_out),
+                                        _stream(stream)))
 
     def vmc_steps(self, sys_id, precision, R, nsweeps, step, seed, step0=0, system_tag=0, walker_offset=0,
-                  nacc=None, logpsi=None, sign=None, eloc=None, O=None, dEL=None, stream=None):
+                  refresh=1, state=None, state_valid=False, nacc=None, logpsi=None, sign=None, eloc=None, O=None,
+                  dEL=None, stream=None):
         W = R.shape[0]
         _check(lib().vbqmc_vmc_steps(self.h, int(sys_id), int(precision), int(W), _ptr(R), int(nsweeps),
                                      float(step), ctypes.c_uint64(seed), ctypes.c_uint32(step0),
-                                     ctypes.c_uint32(system_tag), ctypes.c_uint32(walker_offset), _ptr(nacc),
-                                     _ptr(logpsi), _ptr(sign), _ptr(eloc), _ptr(O), _ptr(dEL), _stream(stream)))
+                                     ctypes.c_uint32(system_tag), ctypes.c_uint32(walker_offset), int(refresh),
+                                     _ptr(state), int(bool(state_valid)), _ptr(nacc), _ptr(logpsi), _ptr(sign),
+                                     _ptr(eloc), _ptr(O), _ptr(dEL), _stream(stream)))
 
 
 def create(device: int = 0) -> Context:

@@ -141,6 +141,34 @@ def test_vmc_fp64_trajectory_matches_oracle(vb, orc, name, W, nsw):
     np.testing.assert_allclose(Rg, Ro, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("name,W,nsw", [("small_open_shell", 19, 3), ("ethylene_vb", 3, 1)])
+def test_vmc_fp64_from_saved_state_matches_oracle(vb, orc, name, W, nsw):
+    """Sweeps that start from the walker state written by an evaluation (no LU refresh inside
+    the call) follow the oracle's trajectory move for move, and the evaluation after them
+    rewrites a state equal to a fresh one."""
+    mod, ctx = vb
+    spec = SYSTEMS[name][0]()
+    ctx.set_system(0, spec)
+    R0 = S.initial_walkers(spec, W, 15)
+    Rt = torch.tensor(R0, device="cuda")
+    z = torch.zeros(W, dtype=torch.float64, device="cuda")
+    state = torch.zeros((W, ctx.walker_state_size(0)), dtype=torch.float64, device="cuda")
+    ctx.eval_walkers(0, 0, Rt, z.clone(), z.clone(), z.clone(), state_out=state)
+    nacc = torch.zeros(W, dtype=torch.int32, device="cuda")
+    lp, sg, el = z.clone(), z.clone(), z.clone()
+    ctx.vmc_steps(0, 0, Rt, nsw, spec.step, 99, step0=3, refresh=0, state=state, state_valid=True, nacc=nacc,
+                  logpsi=lp, sign=sg, eloc=el)
+    state2 = torch.zeros_like(state)
+    ctx.eval_walkers(0, 0, Rt, z.clone(), z.clone(), z.clone(), state_out=state2)
+    torch.cuda.synchronize()
+    Ro, _, _, no = orc.vmc(spec, R0, nsw, spec.step, seed=99, step0=3, eloc=False)
+    np.testing.assert_array_equal(nacc.cpu().numpy(), no)
+    np.testing.assert_allclose(Rt.cpu().numpy(), Ro, rtol=0, atol=1e-12)
+    ref = orc.evaluate(spec, Ro)
+    assert rel_err(el.cpu().numpy(), ref["eloc"]).max() < 1e-10
+    np.testing.assert_allclose(state.cpu().numpy(), state2.cpu().numpy(), rtol=1e-12, atol=1e-12)
+
+
 def test_vmc_mixed_statistics_match_oracle(vb, orc):
     """Mixed-form VMC of the H2 system: mean E_L agrees with the oracle's within 4 sigma."""
     spec = S.h2_vb()
@@ -176,6 +204,16 @@ def test_zero_walkers_and_ragged_tail(vb, orc):
         got = gpu_eval(vb, spec, R, 0, grad=False)
         ref = orc.evaluate(spec, R)
         assert rel_err(got["eloc"], ref["eloc"]).max() < 1e-10
+
+
+def test_ethylene_launch_shape(vb):
+    """The per-walker shared-memory footprint keeps several walkers per block."""
+    mod, ctx = vb
+    ctx.set_system(0, S.ethylene_vb())
+    for prec in (0, 1):
+        li = ctx.launch_info(0, prec)
+        assert li["eval_walkers_per_block"] >= 4 and li["sweep_walkers_per_block"] >= 8, li
+        assert li["eval_smem_per_walker"] * li["eval_walkers_per_block"] <= 232448
 
 
 def test_full_size_ethylene_sampled(vb, orc):
