@@ -18,6 +18,10 @@ namespace vbq {
 namespace {
 
 __host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
+// Threads per block the evaluation kernel is compiled for: the double instantiation keeps
+// more live values and runs few walkers per block, so it gets the larger register budget.
+template <class Tb> struct EvalBounds { static constexpr int threads = 512; };
+template <> struct EvalBounds<double> { static constexpr int threads = 256; };
 template <class A, class B> constexpr bool kSameType = false;
 template <class A> constexpr bool kSameType<A, A> = true;
 inline int group_size(int n) {
@@ -69,13 +73,6 @@ template <class Tb, bool DERIV>
 __device__ __forceinline__ void pade_eval(const PadeCoef& c, Tb r, Tb kap, Tb& f, Tb& df, Tb& d2f) {
   const Tb q[4] = {(Tb)c.q[0], (Tb)c.q[1], (Tb)c.q[2], (Tb)c.q[3]};
   pade_poly<Tb, DERIV>(r, kap, (Tb)c.a1, (Tb)c.a2, q, f, df, d2f);
-}
-
-__device__ __forceinline__ double dist3(const double* a, const double* b, double& dx, double& dy, double& dz) {
-  dx = a[0] - b[0];
-  dy = a[1] - b[1];
-  dz = a[2] - b[2];
-  return sqrt(dx * dx + dy * dy + dz * dz);
 }
 
 // Lane-group LU + inverse of every unique determinant of spin sp, from orbital values
@@ -166,7 +163,7 @@ __device__ __forceinline__ void term_ratios(const SysDev& s, int lane, const dou
 //      E_L and grad ln|Psi|; optionally the walker state (inverses, ln|det|, signs) is stored
 //   D  parameter derivatives (structure coefficients, Jastrow, orbital excitations)
 template <class Tb>
-__global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLayout L, int W,
+__global__ void __launch_bounds__(EvalBounds<Tb>::threads) eval_kernel(const SysDev s, const EvalLayout L, int W,
                                                    const double* __restrict__ Rg, double* __restrict__ logpsi,
                                                    double* __restrict__ sgn_out, double* __restrict__ eloc,
                                                    double* __restrict__ grad, double* __restrict__ Og,
@@ -197,79 +194,130 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
   double* partd = reinterpret_cast<double*>(base + L.partd);
   double* kacc = reinterpret_cast<double*>(base + L.kacc);
   double* red = reinterpret_cast<double*>(base + L.red);
+  Tb* rEE = reinterpret_cast<Tb*>(base + L.geo);       // [N][N] r_ij
+  Tb* uEE = rEE + s.N * s.N;                            // [N][N] Rbar(r_ij)
+  Tb* iEE = uEE + s.N * s.N;                            // [N][N] 1/r_ij
+  Tb* eEE = iEE + s.N * s.N;                            // [N][N][3] (r_i - r_j)/r_ij
+  Tb* rEN = eEE + 3 * s.N * s.N;                        // [N][Nn] r_ia
+  Tb* eEN = rEN + s.N * s.Nn;                           // [N][Nn][3] (r_i - r_a)/r_ia
+  Tb* Stab = eEN + 3 * s.N * s.Nn;                      // [Nn][N][6] Rbar(r_ia)^q
+  Tb* Ssum = Stab + 6 * s.N * s.Nn;                     // [Nn][6] sum_i Rbar(r_ia)^q
 
   const int N = s.N, Nn = s.Nn, Nup = s.Nup, U0 = s.U[0];
   const Tb kap = (Tb)s.kappa;
   for (int i = lane; i < 3 * N; i += 32) R[i] = Rg[(size_t)w * 3 * N + i];
   __syncwarp();
 
-  // ---- A. Jastrow (S lanes per electron, partners split among them) ----
+  // ---- A0. geometry tables: coordinate differences in double, the rest in the bulk type ----
   double lnJ_loc = 0.0, V_loc = 0.0;
   const Tb* cE = een_coefs<Tb>(s);
+  for (int p = lane; p < N * N; p += 32) {
+    const int i = p / N, j = p % N;
+    if (i == j) {
+      rEE[p] = (Tb)0; uEE[p] = (Tb)1; iEE[p] = (Tb)0;
+      eEE[3 * p] = eEE[3 * p + 1] = eEE[3 * p + 2] = (Tb)0;
+      continue;
+    }
+    const Tb dx = (Tb)(R[3 * i] - R[3 * j]), dy = (Tb)(R[3 * i + 1] - R[3 * j + 1]), dz = (Tb)(R[3 * i + 2] - R[3 * j + 2]);
+    const Tb r = vsqrt(dx * dx + dy * dy + dz * dz), ir = (Tb)1 / r;
+    rEE[p] = r; uEE[p] = (Tb)1 / ((Tb)1 + kap * r); iEE[p] = ir;
+    eEE[3 * p] = dx * ir; eEE[3 * p + 1] = dy * ir; eEE[3 * p + 2] = dz * ir;
+    if (i < j) V_loc += (double)ir;
+  }
+  for (int p = lane; p < N * Nn; p += 32) {
+    const int i = p / Nn, a = p % Nn;
+    const double* nu = s.nuc4 + 4 * a;
+    const Tb dx = (Tb)(R[3 * i] - __ldg(nu)), dy = (Tb)(R[3 * i + 1] - __ldg(nu + 1)), dz = (Tb)(R[3 * i + 2] - __ldg(nu + 2));
+    const Tb r = vsqrt(dx * dx + dy * dy + dz * dz), ir = (Tb)1 / r;
+    rEN[p] = r;
+    eEN[3 * p] = dx * ir; eEN[3 * p + 1] = dy * ir; eEN[3 * p + 2] = dz * ir;
+    V_loc -= __ldg(nu + 3) * (double)ir;
+    const Tb sv = (Tb)1 / ((Tb)1 + kap * r);
+    Tb* St = Stab + (a * N + i) * 6;
+    Tb pw = (Tb)1;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) { St[q] = pw; pw *= sv; }
+  }
+  __syncwarp();
+  for (int p = lane; p < Nn * 6; p += 32) {
+    const int a = p / 6, q = p % 6;
+    Tb t = 0;
+    for (int i = 0; i < N; ++i) t += Stab[(a * N + i) * 6 + q];
+    Ssum[p] = t;
+  }
+  __syncwarp();
+
+  // ---- A1. Jastrow ln J, grad_i ln J, lap_i ln J: lane -> (electron i, group g); group g takes
+  //      nuclei a = g, g + S, ... and partners j = g, g + S, ... ----
   {
-    const int S = L.lanes_per_e;
-    const int tot = N * S;
-    for (int b0 = 0; b0 < tot; b0 += 32) {
-      const int idx = b0 + lane, i = idx / S, h = idx % S;
+    const int Pp = L.jas_P, Sg = L.jas_S;
+    for (int b0 = 0; b0 < N; b0 += Pp) {
+      const int i = b0 + lane % Pp, g = lane / Pp;
       const bool act = i < N;
       Tb g0 = 0, g1 = 0, g2 = 0, lap = 0;
+      double lnj = 0.0;
       if (act) {
-        const double* ri = R + 3 * i;
-        double lnj = 0.0, v = 0.0;
-        for (int a = h; a < Nn; a += S) {
-          double dx, dy, dz;
-          const double rd = dist3(ri, s.nuc4 + 4 * a, dx, dy, dz);
-          v -= __ldg(s.nuc4 + 4 * a + 3) / rd;
-          const Tb r = (Tb)rd, ir = (Tb)1 / r;
+        for (int a = g; a < Nn; a += Sg) {
+          const int ia = i * Nn + a;
+          const Tb r = rEN[ia];
           Tb f, df, d2f;
           pade_eval<Tb, true>(en_coef(s, a), r, kap, f, df, d2f);
           lnj += (double)f;
-          g0 += df * (Tb)dx * ir; g1 += df * (Tb)dy * ir; g2 += df * (Tb)dz * ir;
-          lap += d2f + (Tb)2 * df * ir;
+          g0 += df * eEN[3 * ia]; g1 += df * eEN[3 * ia + 1]; g2 += df * eEN[3 * ia + 2];
+          lap += d2f + (Tb)2 * df / r;
         }
-        for (int j = h; j < N; j += S) {
+        for (int j = g; j < N; j += Sg) {
           if (j == i) continue;
-          double dx, dy, dz;
-          const double rd = dist3(ri, R + 3 * j, dx, dy, dz);
-          v += 0.5 / rd;
-          const Tb r = (Tb)rd, ir = (Tb)1 / r;
-          const Tb ex = (Tb)dx * ir, ey = (Tb)dy * ir, ez = (Tb)dz * ir;
+          const int ij = i * N + j;
           Tb f, df, d2f;
-          pade_eval<Tb, true>(ee_coef(s, (i < Nup) == (j < Nup)), r, kap, f, df, d2f);
+          pade_eval<Tb, true>(ee_coef(s, (i < Nup) == (j < Nup)), rEE[ij], kap, f, df, d2f);
           lnj += 0.5 * (double)f;
-          g0 += df * ex; g1 += df * ey; g2 += df * ez;
-          lap += d2f + (Tb)2 * df * ir;
-          if (s.een_on) {
-            const Tb u = (Tb)1 / ((Tb)1 + kap * r);
-            const Tb du = -kap * u * u, d2u = (Tb)2 * kap * kap * u * u * u;
-            for (int a = 0; a < Nn; ++a) {
-              double ax, ay, az, bx, by, bz;
-              const double ria = dist3(ri, s.nuc4 + 4 * a, ax, ay, az);
-              const double rja = dist3(R + 3 * j, s.nuc4 + 4 * a, bx, by, bz);
-              const Tb ira = (Tb)1 / (Tb)ria;
-              const Tb sv = (Tb)1 / ((Tb)1 + kap * (Tb)ria), tv = (Tb)1 / ((Tb)1 + kap * (Tb)rja);
-              const Tb ds = -kap * sv * sv, d2s = (Tb)2 * kap * kap * sv * sv * sv;
-              Tb F, Fu, Fs, Fuu, Fss, Fus;
-              een_partials_us<Tb>(cE + kNeen * __ldg(s.nuc_elem + a), u, sv, tv, F, Fu, Fs, Fuu, Fss, Fus);
-              const Tb fx = (Tb)ax * ira, fy = (Tb)ay * ira, fz = (Tb)az * ira;
-              const Tb A = Fu * du, B = Fs * ds;
-              lnj += 0.5 * (double)F;
-              g0 += A * ex + B * fx; g1 += A * ey + B * fy; g2 += A * ez + B * fz;
-              lap += Fuu * du * du + Fu * (d2u + (Tb)2 * du * ir) + Fss * ds * ds + Fs * (d2s + (Tb)2 * ds * ira) +
-                     (Tb)2 * Fus * du * ds * (ex * fx + ey * fy + ez * fz);
+          g0 += df * eEE[3 * ij]; g1 += df * eEE[3 * ij + 1]; g2 += df * eEE[3 * ij + 2];
+          lap += d2f + (Tb)2 * df * iEE[ij];
+        }
+        if (s.een_on)
+          for (int a = g; a < Nn; a += Sg) {
+            const int ia = i * Nn + a;
+            const Tb* c = cE + kNeen * __ldg(s.nuc_elem + a);
+            EenSide<Tb> si;
+            si.set(Stab[(a * N + i) * 6 + 1], rEN[ia], kap);
+            const Tb ex = eEN[3 * ia], ey = eEN[3 * ia + 1], ez = eEN[3 * ia + 2];
+            auto sink = [&](int t, Tb val, Tb gx, Tb gy, Tb gz, Tb lp) {
+              const Tb ct = c[t];
+              lnj += (double)(ct * val);
+              g0 += ct * gx; g1 += ct * gy; g2 += ct * gz;
+              lap += ct * lp;
+            };
+            {
+              EenAcc<Tb, 1, 2> acc;
+              acc.zero();
+              for (int j = 0; j < N; ++j)
+                if (j != i) {
+                  const int ij = i * N + j;
+                  acc.add(uEE[ij], iEE[ij], kap, eEE[3 * ij], eEE[3 * ij + 1], eEE[3 * ij + 2], Stab + (a * N + j) * 6);
+                }
+              een_terms(acc, si, ex, ey, ez, Ssum + 6 * a, sink);
+            }
+            {
+              EenAcc<Tb, 3, 4> acc;
+              acc.zero();
+              for (int j = 0; j < N; ++j)
+                if (j != i) {
+                  const int ij = i * N + j;
+                  acc.add(uEE[ij], iEE[ij], kap, eEE[3 * ij], eEE[3 * ij + 1], eEE[3 * ij + 2], Stab + (a * N + j) * 6);
+                }
+              een_terms(acc, si, ex, ey, ez, Ssum + 6 * a, sink);
             }
           }
-        }
         lnJ_loc += lnj;
-        V_loc += v;
       }
-      for (int o = S >> 1; o > 0; o >>= 1) {
+      for (int o = Pp; o < 32; o <<= 1) {
         g0 += __shfl_xor_sync(kFull, g0, o);
         g1 += __shfl_xor_sync(kFull, g1, o);
         g2 += __shfl_xor_sync(kFull, g2, o);
         lap += __shfl_xor_sync(kFull, lap, o);
       }
-      if (act && h == 0) {
+      if (act && g == 0) {
         G[3 * i] = g0; G[3 * i + 1] = g1; G[3 * i + 2] = g2;
         LJ[i] = lap;
       }
@@ -444,135 +492,136 @@ __global__ void __launch_bounds__(512) eval_kernel(const SysDev s, const EvalLay
   }
   // D2. Jastrow parameters: O = d lnJ/d alpha, E_L,alpha = -1/2 sum_i (lap_i g + 2 grad_i g . grad_i ln|Psi|)
   if (s.jas_param) {
-    // e-n: a_2..a_6 per element (lanes over electron-nucleus pairs)
+    // e-n: a_2..a_6 per element (lanes over electron-nucleus pairs).  With h(R) the derivative
+    // of f(R) = a1 R/(1 + a2 R) + sum_p a_{p+1} R^p with respect to the parameter:
+    //   a_2: h = -a1 R^2/(1+a2 R)^2, h' = -2 a1 R/(1+a2 R)^3, h'' = -2 a1 (1-2 a2 R)/(1+a2 R)^4
+    //   a_{p+1}: h = R^p; chain rule to r with R' = 1/(1+kappa r)^2, R'' = -2 kappa/(1+kappa r)^3.
     for (int E = 0; E < s.n_elem; ++E) {
-      double aO[5] = {0, 0, 0, 0, 0}, aE[5] = {0, 0, 0, 0, 0};
+      Tb aO[5] = {0, 0, 0, 0, 0}, aE[5] = {0, 0, 0, 0, 0};
       for (int t = lane; t < N * Nn; t += 32) {
         const int i = t / Nn, a = t % Nn;
         if (__ldg(s.nuc_elem + a) != E) continue;
-        double dx, dy, dz;
-        const double r = dist3(R + 3 * i, s.nuc4 + 4 * a, dx, dy, dz);
+        const Tb r = rEN[t];
         const PadeCoef c = en_coef(s, a);
-        const double den = 1.0 / (1.0 + s.kappa * r), Rr = r * den, dR = den * den, d2R = -2.0 * s.kappa * dR * den;
-        const double cosv = (dx * vg[3 * i] + dy * vg[3 * i + 1] + dz * vg[3 * i + 2]) / r;
-        const double pd = 1.0 / (1.0 + c.a2 * Rr);
-        double h[5], hR[5], hRR[5];
-        h[0] = -c.a1 * Rr * Rr * pd * pd;
-        hR[0] = -2.0 * c.a1 * Rr * pd * pd * pd;
-        hRR[0] = -2.0 * c.a1 * (1.0 - 2.0 * c.a2 * Rr) * pd * pd * pd * pd;
-        double Rm2 = 1.0;  // R^(p-2)
+        const Tb a1 = (Tb)c.a1, a2 = (Tb)c.a2;
+        const Tb den = (Tb)1 / ((Tb)1 + kap * r), Rr = r * den, dR = den * den, d2R = (Tb)-2 * kap * dR * den;
+        const Tb cosv = eEN[3 * t] * (Tb)vg[3 * i] + eEN[3 * t + 1] * (Tb)vg[3 * i + 1] + eEN[3 * t + 2] * (Tb)vg[3 * i + 2];
+        const Tb pd = (Tb)1 / ((Tb)1 + a2 * Rr);
+        Tb h[5], hR[5], hRR[5];
+        h[0] = -a1 * Rr * Rr * pd * pd;
+        hR[0] = (Tb)-2 * a1 * Rr * pd * pd * pd;
+        hRR[0] = (Tb)-2 * a1 * ((Tb)1 - (Tb)2 * a2 * Rr) * pd * pd * pd * pd;
+        Tb Rm2 = 1;  // R^(p-2)
+#pragma unroll
         for (int p = 2; p <= 5; ++p) {
           h[p - 1] = Rm2 * Rr * Rr;
-          hR[p - 1] = p * Rm2 * Rr;
-          hRR[p - 1] = p * (p - 1) * Rm2;
+          hR[p - 1] = (Tb)p * Rm2 * Rr;
+          hRR[p - 1] = (Tb)(p * (p - 1)) * Rm2;
           Rm2 *= Rr;
         }
+#pragma unroll
         for (int q = 0; q < 5; ++q) {
-          const double g1 = hR[q] * dR, g2 = hRR[q] * dR * dR + hR[q] * d2R;
+          const Tb g1 = hR[q] * dR, g2 = hRR[q] * dR * dR + hR[q] * d2R;
           aO[q] += h[q];
-          aE[q] += -0.5 * (g2 + 2.0 * g1 / r + 2.0 * g1 * cosv);
+          aE[q] += (Tb)-0.5 * (g2 + (Tb)2 * g1 / r + (Tb)2 * g1 * cosv);
         }
       }
+#pragma unroll
       for (int q = 0; q < 5; ++q) {
-        const double o = warp_sum(aO[q]), e = warp_sum(aE[q]);
+        const double o = warp_sum((double)aO[q]), e = warp_sum((double)aE[q]);
         if (lane == 0) {
           Ow[s.p_off_a + 5 * E + q] = o;
           if (Ew) Ew[s.p_off_a + 5 * E + q] = e;
         }
       }
     }
-    // e-e: b_2..b_6 (lanes over pairs)
+    // e-e: b_2..b_6 (lanes over pairs), same radial forms with b1 (by spins) and b2
     {
-      double bO[5] = {0, 0, 0, 0, 0}, bE[5] = {0, 0, 0, 0, 0};
+      Tb bO[5] = {0, 0, 0, 0, 0}, bE[5] = {0, 0, 0, 0, 0};
       const int npair = N * (N - 1) / 2;
       for (int pp = lane; pp < npair; pp += 32) {
         int i = 0, rem = pp;
         while (rem >= N - 1 - i) { rem -= N - 1 - i; ++i; }
-        const int j = i + 1 + rem;
-        double dx, dy, dz;
-        const double r = dist3(R + 3 * i, R + 3 * j, dx, dy, dz);
+        const int j = i + 1 + rem, ij = i * N + j;
+        const Tb r = rEE[ij];
         const PadeCoef c = ee_coef(s, (i < Nup) == (j < Nup));
-        const double den = 1.0 / (1.0 + s.kappa * r), Rr = r * den, dR = den * den, d2R = -2.0 * s.kappa * dR * den;
-        const double cosv = (dx * (vg[3 * i] - vg[3 * j]) + dy * (vg[3 * i + 1] - vg[3 * j + 1]) +
-                             dz * (vg[3 * i + 2] - vg[3 * j + 2])) / r;
-        const double pd = 1.0 / (1.0 + c.a2 * Rr);
-        double h[5], hR[5], hRR[5];
-        h[0] = -c.a1 * Rr * Rr * pd * pd;
-        hR[0] = -2.0 * c.a1 * Rr * pd * pd * pd;
-        hRR[0] = -2.0 * c.a1 * (1.0 - 2.0 * c.a2 * Rr) * pd * pd * pd * pd;
-        double Rm2 = 1.0;  // R^(p-2)
+        const Tb a1 = (Tb)c.a1, a2 = (Tb)c.a2;
+        const Tb den = (Tb)1 / ((Tb)1 + kap * r), Rr = r * den, dR = den * den, d2R = (Tb)-2 * kap * dR * den;
+        const Tb cosv = eEE[3 * ij] * (Tb)(vg[3 * i] - vg[3 * j]) + eEE[3 * ij + 1] * (Tb)(vg[3 * i + 1] - vg[3 * j + 1]) +
+                        eEE[3 * ij + 2] * (Tb)(vg[3 * i + 2] - vg[3 * j + 2]);
+        const Tb pd = (Tb)1 / ((Tb)1 + a2 * Rr);
+        Tb h[5], hR[5], hRR[5];
+        h[0] = -a1 * Rr * Rr * pd * pd;
+        hR[0] = (Tb)-2 * a1 * Rr * pd * pd * pd;
+        hRR[0] = (Tb)-2 * a1 * ((Tb)1 - (Tb)2 * a2 * Rr) * pd * pd * pd * pd;
+        Tb Rm2 = 1;  // R^(p-2)
+#pragma unroll
         for (int p = 2; p <= 5; ++p) {
           h[p - 1] = Rm2 * Rr * Rr;
-          hR[p - 1] = p * Rm2 * Rr;
-          hRR[p - 1] = p * (p - 1) * Rm2;
+          hR[p - 1] = (Tb)p * Rm2 * Rr;
+          hRR[p - 1] = (Tb)(p * (p - 1)) * Rm2;
           Rm2 *= Rr;
         }
+#pragma unroll
         for (int q = 0; q < 5; ++q) {
-          const double g1 = hR[q] * dR, g2 = hRR[q] * dR * dR + hR[q] * d2R;
+          const Tb g1 = hR[q] * dR, g2 = hRR[q] * dR * dR + hR[q] * d2R;
           bO[q] += h[q];
-          bE[q] += -0.5 * (2.0 * (g2 + 2.0 * g1 / r) + 2.0 * g1 * cosv);
+          bE[q] += (Tb)-0.5 * ((Tb)2 * (g2 + (Tb)2 * g1 * iEE[ij]) + (Tb)2 * g1 * cosv);
         }
       }
+#pragma unroll
       for (int q = 0; q < 5; ++q) {
-        const double o = warp_sum(bO[q]), e = warp_sum(bE[q]);
+        const double o = warp_sum((double)bO[q]), e = warp_sum((double)bE[q]);
         if (lane == 0) {
           Ow[s.p_off_b + q] = o;
           if (Ew) Ew[s.p_off_b + q] = e;
         }
       }
     }
-    // e-e-n: raw terms per element (lanes over pairs), then theta = B^T raw
+    // e-e-n: per element, the raw-term derivatives from the pair sums (lane -> (electron i,
+    // group g), nuclei of the element split among groups), then theta = B^T raw
     if (s.een_on) {
       double* rawO = red;               // [23]
       double* rawE = red + kNeen;       // [23]
-      const int npair = N * (N - 1) / 2;
+      const int Pp = L.jas_P, Sg = L.jas_S;
       for (int E = 0; E < s.n_elem; ++E) {
         Tb accO[kNeen], accE[kNeen];
 #pragma unroll
         for (int q = 0; q < kNeen; ++q) accO[q] = accE[q] = (Tb)0;
-        for (int pp = lane; pp < npair; pp += 32) {
-          int i = 0, rem = pp;
-          while (rem >= N - 1 - i) { rem -= N - 1 - i; ++i; }
-          const int j = i + 1 + rem;
-          double dx, dy, dz;
-          const double rij = dist3(R + 3 * i, R + 3 * j, dx, dy, dz);
-          const Tb irij = (Tb)(1.0 / rij);
-          const Tb ex = (Tb)dx * irij, ey = (Tb)dy * irij, ez = (Tb)dz * irij;
-          const Tb u = (Tb)1 / ((Tb)1 + kap * (Tb)rij), du = -kap * u * u, d2u = (Tb)2 * kap * kap * u * u * u;
-          const Tb vix = (Tb)vg[3 * i], viy = (Tb)vg[3 * i + 1], viz = (Tb)vg[3 * i + 2];
-          const Tb vjx = (Tb)vg[3 * j], vjy = (Tb)vg[3 * j + 1], vjz = (Tb)vg[3 * j + 2];
-          const Tb e_vi = ex * vix + ey * viy + ez * viz, e_vj = ex * vjx + ey * vjy + ez * vjz;
-          for (int a = 0; a < Nn; ++a) {
+        for (int b0 = 0; b0 < N; b0 += Pp) {
+          const int i = b0 + lane % Pp, g = lane / Pp;
+          if (i >= N) continue;
+          const Tb vx = (Tb)vg[3 * i], vy = (Tb)vg[3 * i + 1], vz = (Tb)vg[3 * i + 2];
+          for (int a = g; a < Nn; a += Sg) {
             if (__ldg(s.nuc_elem + a) != E) continue;
-            double ax, ay, az, bx, by, bz;
-            const double ria = dist3(R + 3 * i, s.nuc4 + 4 * a, ax, ay, az);
-            const double rja = dist3(R + 3 * j, s.nuc4 + 4 * a, bx, by, bz);
-            const Tb iria = (Tb)(1.0 / ria), irja = (Tb)(1.0 / rja);
-            const Tb fx = (Tb)ax * iria, fy = (Tb)ay * iria, fz = (Tb)az * iria;
-            const Tb hx = (Tb)bx * irja, hy = (Tb)by * irja, hz = (Tb)bz * irja;
-            const Tb sv = (Tb)1 / ((Tb)1 + kap * (Tb)ria), tv = (Tb)1 / ((Tb)1 + kap * (Tb)rja);
-            const Tb ds = -kap * sv * sv, d2s = (Tb)2 * kap * kap * sv * sv * sv;
-            const Tb dt = -kap * tv * tv, d2t = (Tb)2 * kap * kap * tv * tv * tv;
-            const Tb f_vi = fx * vix + fy * viy + fz * viz, h_vj = hx * vjx + hy * vjy + hz * vjz;
-            const Tb e_f = ex * fx + ey * fy + ez * fz, e_h = ex * hx + ey * hy + ez * hz;
-            Pow6<Tb> Up, Sp, Tp;
-            Up.set(u); Sp.set(sv); Tp.set(tv);
-            een_for_each([&](int q, int k, int l, int m) {
-              const Tb f = Sp.p(l + m) * Tp.p(m) + Sp.p(m) * Tp.p(l + m);
-              const Tb fs = Sp.d(l + m) * Tp.p(m) + Sp.d(m) * Tp.p(l + m);
-              const Tb fss = Sp.dd(l + m) * Tp.p(m) + Sp.dd(m) * Tp.p(l + m);
-              const Tb ft = Sp.p(l + m) * Tp.d(m) + Sp.p(m) * Tp.d(l + m);
-              const Tb ftt = Sp.p(l + m) * Tp.dd(m) + Sp.p(m) * Tp.dd(l + m);
-              const Tb T0 = Up.p(k) * f, Tu = Up.d(k) * f, Tuu = Up.dd(k) * f;
-              const Tb Ts = Up.p(k) * fs, Tss = Up.p(k) * fss, Tus = Up.d(k) * fs;
-              const Tb Tt = Up.p(k) * ft, Ttt = Up.p(k) * ftt, Tut = Up.d(k) * ft;
-              const Tb radial_u = Tuu * du * du + Tu * (d2u + (Tb)2 * du * irij);
-              const Tb lap_i = radial_u + Tss * ds * ds + Ts * (d2s + (Tb)2 * ds * iria) + (Tb)2 * Tus * du * ds * e_f;
-              const Tb lap_j = radial_u + Ttt * dt * dt + Tt * (d2t + (Tb)2 * dt * irja) - (Tb)2 * Tut * du * dt * e_h;
-              const Tb gdot = Tu * du * (e_vi - e_vj) + Ts * ds * f_vi + Tt * dt * h_vj;
-              accO[q] += T0;
-              accE[q] += (Tb)-0.5 * (lap_i + lap_j + (Tb)2 * gdot);
-            });
+            const int ia = i * Nn + a;
+            EenSide<Tb> si;
+            si.set(Stab[(a * N + i) * 6 + 1], rEN[ia], kap);
+            const Tb ex = eEN[3 * ia], ey = eEN[3 * ia + 1], ez = eEN[3 * ia + 2];
+            auto sink = [&](int t, Tb val, Tb gx, Tb gy, Tb gz, Tb lp) {
+              accO[t] += val;
+              accE[t] += (Tb)-0.5 * (lp + (Tb)2 * (gx * vx + gy * vy + gz * vz));
+            };
+            {
+              EenAcc<Tb, 1, 2> acc;
+              acc.zero();
+              for (int j = 0; j < N; ++j)
+                if (j != i) {
+                  const int ij = i * N + j;
+                  acc.add(uEE[ij], iEE[ij], kap, eEE[3 * ij], eEE[3 * ij + 1], eEE[3 * ij + 2], Stab + (a * N + j) * 6);
+                }
+              een_terms(acc, si, ex, ey, ez, Ssum + 6 * a, sink);
+            }
+            {
+              EenAcc<Tb, 3, 4> acc;
+              acc.zero();
+              for (int j = 0; j < N; ++j)
+                if (j != i) {
+                  const int ij = i * N + j;
+                  acc.add(uEE[ij], iEE[ij], kap, eEE[3 * ij], eEE[3 * ij + 1], eEE[3 * ij + 2], Stab + (a * N + j) * 6);
+                }
+              een_terms(acc, si, ex, ey, ez, Ssum + 6 * a, sink);
+            }
           }
         }
 #pragma unroll
@@ -680,12 +729,36 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
   double* rho = reinterpret_cast<double*>(base + L.rho);
   double* cvec = reinterpret_cast<double*>(base + L.cvec);
   double* scr = reinterpret_cast<double*>(base + L.scratch);
+  Tb* rEE = reinterpret_cast<Tb*>(base + L.geo);       // [N][N] r_ij
+  Tb* rEN = rEE + s.N * s.N;                            // [N][Nn] r_ia
+  Tb* Stab = rEN + s.N * s.Nn;                          // [Nn][N][6] Rbar(r_ia)^q
+  Tb* rnE = Stab + 6 * s.N * s.Nn;                      // [N] r from the proposed position
+  Tb* rnN = rnE + s.N;                                  // [Nn]
+  Tb* Snew = rnN + s.Nn;                                // [Nn][6]
 
   const int N = s.N, Nn = s.Nn, Nup = s.Nup, U0 = s.U[0], ldo = L.nocc_max;
   const Tb kap = (Tb)s.kappa;
   const Tb* cf = orb_coefs<Tb>(s);
   const Tb* cE = een_coefs<Tb>(s);
   for (int i = lane; i < 3 * N; i += 32) R[i] = Rg[(size_t)w * 3 * N + i];
+  __syncwarp();
+  // geometry tables (coordinate differences in double, the rest in the bulk type)
+  for (int p = lane; p < N * N; p += 32) {
+    const int i = p / N, j = p % N;
+    const Tb dx = (Tb)(R[3 * i] - R[3 * j]), dy = (Tb)(R[3 * i + 1] - R[3 * j + 1]), dz = (Tb)(R[3 * i + 2] - R[3 * j + 2]);
+    rEE[p] = i == j ? (Tb)0 : vsqrt(dx * dx + dy * dy + dz * dz);
+  }
+  for (int p = lane; p < N * Nn; p += 32) {
+    const int i = p / Nn, a = p % Nn;
+    const double* nu = s.nuc4 + 4 * a;
+    const Tb dx = (Tb)(R[3 * i] - __ldg(nu)), dy = (Tb)(R[3 * i + 1] - __ldg(nu + 1)), dz = (Tb)(R[3 * i + 2] - __ldg(nu + 2));
+    const Tb r = vsqrt(dx * dx + dy * dy + dz * dz);
+    rEN[p] = r;
+    const Tb sv = (Tb)1 / ((Tb)1 + kap * r);
+    Tb pw = (Tb)1;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) { Stab[(a * N + i) * 6 + q] = pw; pw *= sv; }
+  }
   if (state_in) {
     const double* st = state_in + (size_t)w * s.state_doubles;
     const int nb0 = s.U[0] * s.n[0] * s.n[0], nb1 = s.U[1] * s.n[1] * s.n[1], Ut = U0 + s.U[1];
@@ -777,43 +850,68 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
       double rphi = 0.0;
       for (int k = lane; k < s.nterm; k += 32) rphi += wk[k] * rho[__ldg(s.term_det + 2 * k + sp)];
       rphi = warp_sum(rphi);
-      // Jastrow change of the terms that involve electron e: items e-n (a), e-e (j), e-e-n (j, a)
+      // Jastrow change of the terms that involve electron e (Sec. 2.1): distances from the
+      // proposed position, then items e-n (a), e-e (j) and e-e-n (a, k), the last through the
+      // pair sums Y^{k,q} = sum_{j != e} u_ej^k s_j^q (the terms of e are s_e^A Y^{k,B} + s_e^B Y^{k,A}).
+      for (int j = lane; j < N; j += 32) {
+        const Tb dx = (Tb)(rn[0] - R[3 * j]), dy = (Tb)(rn[1] - R[3 * j + 1]), dz = (Tb)(rn[2] - R[3 * j + 2]);
+        rnE[j] = j == e ? (Tb)0 : vsqrt(dx * dx + dy * dy + dz * dz);
+      }
+      for (int a = lane; a < Nn; a += 32) {
+        const double* nu = s.nuc4 + 4 * a;
+        const Tb dx = (Tb)(rn[0] - __ldg(nu)), dy = (Tb)(rn[1] - __ldg(nu + 1)), dz = (Tb)(rn[2] - __ldg(nu + 2));
+        const Tb r = vsqrt(dx * dx + dy * dy + dz * dz);
+        rnN[a] = r;
+        const Tb sv = (Tb)1 / ((Tb)1 + kap * r);
+        Tb pw = (Tb)1;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) { Snew[a * 6 + q] = pw; pw *= sv; }
+      }
+      __syncwarp();
       Tb dj = 0;
-      const double* ro = R + 3 * e;
-      const int nitem = Nn + (N - 1) * (1 + (s.een_on ? Nn : 0));
+      const int nitem = Nn + N + (s.een_on ? 5 * Nn : 0);
       for (int t = lane; t < nitem; t += 32) {
-        double dx, dy, dz;
         if (t < Nn) {
-          const double r_new = dist3(rn, s.nuc4 + 4 * t, dx, dy, dz);
-          const double r_old = dist3(ro, s.nuc4 + 4 * t, dx, dy, dz);
           const PadeCoef c = en_coef(s, t);
           Tb f1, f0, t0, t1;
-          pade_eval<Tb, false>(c, (Tb)r_new, kap, f1, t0, t1);
-          pade_eval<Tb, false>(c, (Tb)r_old, kap, f0, t0, t1);
+          pade_eval<Tb, false>(c, rnN[t], kap, f1, t0, t1);
+          pade_eval<Tb, false>(c, rEN[e * Nn + t], kap, f0, t0, t1);
           dj += f1 - f0;
-          continue;
-        }
-        const int t2 = t - Nn, per = 1 + (s.een_on ? Nn : 0);
-        int j = t2 / per;
-        const int a = t2 % per - 1;  // -1: the e-e term itself
-        if (j >= e) ++j;
-        const double r_new = dist3(rn, R + 3 * j, dx, dy, dz);
-        const double r_old = dist3(ro, R + 3 * j, dx, dy, dz);
-        if (a < 0) {
+        } else if (t < Nn + N) {
+          const int j = t - Nn;
+          if (j == e) continue;
           const PadeCoef c = ee_coef(s, (e < Nup) == (j < Nup));
           Tb f1, f0, t0, t1;
-          pade_eval<Tb, false>(c, (Tb)r_new, kap, f1, t0, t1);
-          pade_eval<Tb, false>(c, (Tb)r_old, kap, f0, t0, t1);
+          pade_eval<Tb, false>(c, rnE[j], kap, f1, t0, t1);
+          pade_eval<Tb, false>(c, rEE[e * N + j], kap, f0, t0, t1);
           dj += f1 - f0;
         } else {
-          const Tb un = (Tb)1 / ((Tb)1 + kap * (Tb)r_new), uo = (Tb)1 / ((Tb)1 + kap * (Tb)r_old);
-          const double ran = dist3(rn, s.nuc4 + 4 * a, dx, dy, dz);
-          const double rao = dist3(ro, s.nuc4 + 4 * a, dx, dy, dz);
-          const double rja = dist3(R + 3 * j, s.nuc4 + 4 * a, dx, dy, dz);
-          const Tb tv = (Tb)1 / ((Tb)1 + kap * (Tb)rja);
-          const Tb* cc = cE + kNeen * __ldg(s.nuc_elem + a);
-          dj += een_value<Tb>(cc, un, (Tb)1 / ((Tb)1 + kap * (Tb)ran), tv) -
-                een_value<Tb>(cc, uo, (Tb)1 / ((Tb)1 + kap * (Tb)rao), tv);
+          const int tt = t - Nn - N, a = tt / 5, k = tt % 5;
+          Tb Yo[6], Yn[6];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) Yo[q] = Yn[q] = (Tb)0;
+          for (int j = 0; j < N; ++j) {
+            if (j == e) continue;
+            const Tb uo = (Tb)1 / ((Tb)1 + kap * rEE[e * N + j]), un = (Tb)1 / ((Tb)1 + kap * rnE[j]);
+            Tb po = (Tb)1, pn = (Tb)1;
+            for (int kk = 0; kk < k; ++kk) { po *= uo; pn *= un; }
+            const Tb* Sj = Stab + (a * N + j) * 6;
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+              if (q <= 5 - k) {
+                Yo[q] += po * Sj[q];
+                Yn[q] += pn * Sj[q];
+              }
+          }
+          const Tb* So = Stab + (a * N + e) * 6;
+          const Tb* Sn = Snew + a * 6;
+          const Tb* c = cE + kNeen * __ldg(s.nuc_elem + a);
+          een_for_each([&](auto tc) {
+            constexpr int q = decltype(tc)::value;
+            constexpr int tk = een_klm(q).k, A = een_klm(q).l + een_klm(q).m, B = een_klm(q).m;
+            if (tk != k) return;
+            dj += c[q] * ((Sn[A] * Yn[B] + Sn[B] * Yn[A]) - (So[A] * Yo[B] + So[B] * Yo[A]));
+          });
         }
       }
       const double dJ = warp_sum((double)dj);
@@ -839,6 +937,12 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
         const double irphi = 1.0 / rphi;
         for (int k = lane; k < s.nterm; k += 32) wk[k] *= rho[__ldg(s.term_det + 2 * k + sp)] * irphi;
         if (lane < 3) R[3 * e + lane] = rn[lane];
+        for (int j = lane; j < N; j += 32) rEE[e * N + j] = rEE[j * N + e] = rnE[j];
+        for (int a = lane; a < Nn; a += 32) {
+          rEN[e * Nn + a] = rnN[a];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) Stab[(a * N + e) * 6 + q] = Snew[a * 6 + q];
+        }
         ++accepted;
       }
       __syncwarp();
@@ -861,9 +965,6 @@ int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
   const int N = s.N, Ut = s.U[0] + s.U[1];
   L.G0 = group_size(s.n[0]);
   L.G1 = group_size(s.n[1]);
-  int S = 1;
-  while (2 * S * N <= 32) S *= 2;
-  L.lanes_per_e = S;
   L.R = take(8 * 3 * N);
   L.vg = take(8 * 3 * N);
   L.G = take(tb * 3 * N);
@@ -891,9 +992,17 @@ int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
   L.partd = take(8 * std::max(s.n_det_chunk, 1));
   L.kacc = take(8 * 2 * std::max(s.n_kappa, 1));
   L.red = take(8 * 64);
+  L.geo = take(tb * (6 * N * N + 4 * N * s.Nn + 6 * N * s.Nn + 6 * s.Nn));
+  {
+    int P = 1;
+    while (P < N && P < 32) P <<= 1;
+    L.jas_P = P;
+    L.jas_S = 32 / P;
+  }
   L.warp_bytes = off;
   int wpb = max_smem / off;
-  if (wpb > 16) wpb = 16;
+  const int cap = (tb == 8 ? EvalBounds<double>::threads : EvalBounds<float>::threads) / 32;
+  if (wpb > cap) wpb = cap;
   if (wpb < 1) return VBQMC_ERR_CAPACITY;
   L.wpb = wpb;
   return VBQMC_OK;
@@ -929,6 +1038,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   }
   L.cvec = take(std::max(cv, 8));
   L.scratch = take(std::max(scr, 16));
+  L.geo = take(tb * (N * N + N * s.Nn + 6 * N * s.Nn + N + s.Nn + 6 * s.Nn));
   L.warp_bytes = off;
   int wpb = max_smem / off;
   if (wpb > 16) wpb = 16;

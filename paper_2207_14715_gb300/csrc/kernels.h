@@ -12,14 +12,14 @@ namespace vbq {
 struct EvalLayout {
   int wpb = 0, warp_bytes = 0;
   int R, vg, G, LJ, Phi, PhiD, Lphi, Gphi, Binv0, Binv1, ldet, dsg, tdet, Wdet, Tdet, rk, scratch, part, partd,
-      kacc, red;
-  int G0, G1;        // lane-group size per spin for the LU
-  int lanes_per_e;   // lanes sharing one electron in the Jastrow phase
+      kacc, red, geo;
+  int G0, G1;          // lane-group size per spin for the LU
+  int jas_P, jas_S;    // Jastrow lanes: electron = lane % jas_P, group = lane / jas_P (jas_S groups)
 };
 
 struct SweepLayout {
   int wpb = 0, warp_bytes = 0;
-  int R, Binv0, Binv1, ldet, dsg, wk, PhiO, bas, vrow, part, rho, cvec, scratch;
+  int R, Binv0, Binv1, ldet, dsg, wk, PhiO, bas, vrow, part, rho, cvec, scratch, geo;
   int nocc_max;
   int G0, G1;
 };

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "vbqmc_internal.h"
 
 namespace vbq {
@@ -233,24 +235,30 @@ __device__ __forceinline__ void pade_poly(T r, T kap, T a1, T a2, const T* q, T&
   }
 }
 
-// Calls f(q, k, l, m) for the e-e-n terms in the order of the sum of Sec. 2.1: p = 2..5,
-// k = 0..p-1, l = 0..lmax with lmax = p-k (k != 0) or p-k-2 (k = 0), kept when p-k-l is even
-// (m = (p-k-l)/2); q counts the kept terms.  All loops unroll at compile time.
-template <class F> __device__ __forceinline__ void een_for_each(F&& f) {
+// e-e-n terms in the order of the sum of Sec. 2.1: p = 2..5, k = 0..p-1, l = 0..lmax with
+// lmax = p-k (k != 0) or p-k-2 (k = 0), kept when p-k-l is even (m = (p-k-l)/2).
+struct EenKLM { int k, l, m; };
+__host__ __device__ constexpr EenKLM een_klm(int t) {
   int q = 0;
-#pragma unroll
-  for (int p = 2; p <= 5; ++p) {
-#pragma unroll
-    for (int k = 0; k < p; ++k) {
-#pragma unroll
-      for (int l = 0; l <= (k ? p - k : p - k - 2); ++l) {
-        if (((p - k - l) & 1) == 0) {
-          f(q, k, l, (p - k - l) >> 1);
+  for (int p = 2; p <= 5; ++p)
+    for (int k = 0; k < p; ++k)
+      for (int l = 0; l <= (k ? p - k : p - k - 2); ++l)
+        if ((p - k - l) % 2 == 0) {
+          if (q == t) return EenKLM{k, l, (p - k - l) / 2};
           ++q;
         }
-      }
-    }
-  }
+  return EenKLM{-1, -1, -1};
+}
+static_assert(een_klm(kNeen - 1).k == 4 && een_klm(kNeen).k == -1, "23 e-e-n terms");
+
+template <class F, int... T>
+__device__ __forceinline__ void een_for_each_impl(F& f, std::integer_sequence<int, T...>) {
+  (f(std::integral_constant<int, T>{}), ...);
+}
+// Calls f(std::integral_constant<int, t>) for t = 0..22; inside, een_klm(t) is a constant
+// expression, so register arrays indexed by the term's powers stay in registers.
+template <class F> __device__ __forceinline__ void een_for_each(F&& f) {
+  een_for_each_impl(f, std::make_integer_sequence<int, kNeen>{});
 }
 
 template <class T> struct Pow6 {
@@ -274,7 +282,11 @@ template <class T> __device__ __forceinline__ T een_value(const T* c, T u, T s, 
   Pow6<T> U, S, Tt;
   U.set(u); S.set(s); Tt.set(t);
   T F = (T)0;
-  een_for_each([&](int q, int k, int l, int m) { F += c[q] * een_term(U, S, Tt, k, l, m); });
+  een_for_each([&](auto tc) {
+    constexpr int q = decltype(tc)::value;
+    constexpr EenKLM x = een_klm(q);
+    F += c[q] * een_term(U, S, Tt, x.k, x.l, x.m);
+  });
   return F;
 }
 
@@ -285,7 +297,9 @@ __device__ __forceinline__ void een_partials_us(const T* c, T u, T s, T t, T& F,
   Pow6<T> U, S, Tt;
   U.set(u); S.set(s); Tt.set(t);
   F = Fu = Fs = Fuu = Fss = Fus = (T)0;
-  een_for_each([&](int q, int k, int l, int m) {
+  een_for_each([&](auto tc) {
+    constexpr int q = decltype(tc)::value;
+    constexpr int k = een_klm(q).k, l = een_klm(q).l, m = een_klm(q).m;
     const T f = S.p(l + m) * Tt.p(m) + S.p(m) * Tt.p(l + m);
     const T fs = S.d(l + m) * Tt.p(m) + S.d(m) * Tt.p(l + m);
     const T fss = S.dd(l + m) * Tt.p(m) + S.dd(m) * Tt.p(l + m);
@@ -296,6 +310,116 @@ __device__ __forceinline__ void een_partials_us(const T* c, T u, T s, T t, T& F,
     Fs += cq * U.p(k) * fs;
     Fss += cq * U.p(k) * fss;
     Fus += cq * U.d(k) * fs;
+  });
+}
+
+}  // namespace vbq
+
+namespace vbq {
+
+// ------------------------------------------------------------------------------------
+// e-e-n Jastrow through pair sums.  For one nucleus with s_i = Rbar(r_ia) and u_ij = Rbar(r_ij),
+// every term c u^k (s_i^l + s_j^l)(s_i s_j)^m summed over pairs i < j equals
+//   c sum_{i != j} u_ij^k s_i^A s_j^B  with A = l + m, B = m,
+// so f_een = sum_t c_t sum_i S_i^A Y_i^{k,B} with Y_i^{k,q} = sum_{j != i} u_ij^k s_j^q.
+// Gradient and Laplacian with respect to r_i follow from the product rule with
+//   Z_i^{k,q} = sum_{j != i} grad_i(u_ij^k) s_j^q,  Q_i^{k,q} = sum_{j != i} lap_i(u_ij^k) s_j^q:
+//   grad_i = S^A Z^{k,B} + S^B Z^{k,A} + D^A Y^{k,B} + D^B Y^{k,A}
+//   lap_i  = S^A Q^{k,B} + S^B Q^{k,A} + 2 D^A.Z^{k,B} + 2 D^B.Z^{k,A} + L^A Y^{k,B} + L^B Y^{k,A}
+// with D^q = grad_i s_i^q and L^q = lap_i s_i^q.  For k = 0, Y^{0,q}_i = sum_j s_j^q - s_i^q and
+// Z = Q = 0.  Accumulators exist for k in [K0, K1] and q <= 5 - k (the powers the terms use).
+// ------------------------------------------------------------------------------------
+template <int K0, int K1> struct EenK {
+  __host__ __device__ static constexpr int count() {
+    int c = 0;
+    for (int k = K0; k <= K1; ++k) c += 6 - k;
+    return c;
+  }
+  __host__ __device__ static constexpr int idx(int k, int q) {
+    int c = 0;
+    for (int kk = K0; kk < k; ++kk) c += 6 - kk;
+    return c + q;
+  }
+};
+
+template <class T, int K0, int K1> struct EenAcc {
+  static constexpr int C = EenK<K0, K1>::count();
+  T Y[C], Zx[C], Zy[C], Zz[C], Q[C];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int c = 0; c < C; ++c) Y[c] = Zx[c] = Zy[c] = Zz[c] = Q[c] = (T)0;
+  }
+  // adds partner j: u = Rbar(r_ij), ir = 1/r_ij, (ex, ey, ez) = (r_i - r_j)/r_ij, S = s_j^0..5
+  __device__ __forceinline__ void add(T u, T ir, T kap, T ex, T ey, T ez, const T* S) {
+    const T du = -kap * u * u, d2u = (T)2 * kap * kap * u * u * u;
+    T up[5];
+    up[0] = (T)1; up[1] = u; up[2] = u * u; up[3] = up[2] * u; up[4] = up[3] * u;
+#pragma unroll
+    for (int k = K0; k <= K1; ++k) {
+      const T Uk = up[k];
+      const T dUk = (T)k * up[k - 1] * du;
+      const T d2Uk = (k >= 2 ? (T)(k * (k - 1)) * up[k >= 2 ? k - 2 : 0] * du * du : (T)0) + (T)k * up[k - 1] * d2u;
+      const T Hk = d2Uk + (T)2 * dUk * ir;
+#pragma unroll
+      for (int q = 0; q <= 5 - k; ++q) {
+        const int c = EenK<K0, K1>::idx(k, q);
+        const T sq = S[q];
+        Y[c] += Uk * sq;
+        const T g = dUk * sq;
+        Zx[c] += g * ex; Zy[c] += g * ey; Zz[c] += g * ez;
+        Q[c] += Hk * sq;
+      }
+    }
+  }
+};
+
+// Per electron-nucleus data: S^q, dS^q/dr and the radial Laplacian of s^q for q = 0..5.
+template <class T> struct EenSide {
+  T S[6], dS[6], L[6];
+  __device__ __forceinline__ void set(T s, T r, T kap) {
+    const T ds = -kap * s * s, d2s = (T)2 * kap * kap * s * s * s, ir = (T)1 / r;
+    S[0] = (T)1; dS[0] = (T)0; L[0] = (T)0;
+#pragma unroll
+    for (int q = 1; q <= 5; ++q) {
+      S[q] = S[q - 1] * s;
+      dS[q] = (T)q * S[q - 1] * ds;
+      const T d2 = (q >= 2 ? (T)(q * (q - 1)) * S[q >= 2 ? q - 2 : 0] * ds * ds : (T)0) + (T)q * S[q - 1] * d2s;
+      L[q] = d2 + (T)2 * dS[q] * ir;
+    }
+  }
+};
+
+// Calls f(t, val, gx, gy, gz, lap) for every term t with k in [K0, K1] (k = 0 terms when
+// K0 == 1): val = s_i^A Y^{k,B}, (gx, gy, gz) = grad_i and lap = lap_i of the term's part
+// that involves electron i, as written above.  (ex, ey, ez) = (r_i - r_a)/r_ia; Ssum[q] = sum_j s_j^q.
+template <class T, int K0, int K1, class F>
+__device__ __forceinline__ void een_terms(const EenAcc<T, K0, K1>& acc, const EenSide<T>& si, T ex, T ey, T ez,
+                                          const T* Ssum, F&& f) {
+  een_for_each([&](auto tc) {
+    constexpr int t = decltype(tc)::value;
+    constexpr int k = een_klm(t).k, A = een_klm(t).l + een_klm(t).m, B = een_klm(t).m;
+    constexpr bool mine = (k >= K0 && k <= K1) || (k == 0 && K0 == 1);
+    if (!mine) return;
+    T Ya, Yb, Zax = 0, Zay = 0, Zaz = 0, Zbx = 0, Zby = 0, Zbz = 0, Qa = 0, Qb = 0;
+    if (k == 0) {
+      Ya = Ssum[A] - si.S[A];
+      Yb = Ssum[B] - si.S[B];
+    } else {
+      constexpr int ca = EenK<K0, K1>::idx(k >= K0 ? k : K0, A <= 5 - k ? A : 0);
+      constexpr int cb = EenK<K0, K1>::idx(k >= K0 ? k : K0, B <= 5 - k ? B : 0);
+      Ya = acc.Y[ca]; Yb = acc.Y[cb];
+      Zax = acc.Zx[ca]; Zay = acc.Zy[ca]; Zaz = acc.Zz[ca];
+      Zbx = acc.Zx[cb]; Zby = acc.Zy[cb]; Zbz = acc.Zz[cb];
+      Qa = acc.Q[ca]; Qb = acc.Q[cb];
+    }
+    const T SA = si.S[A], SB = si.S[B], dA = si.dS[A], dB = si.dS[B];
+    const T val = SA * Yb;
+    const T gx = SA * Zbx + SB * Zax + (dA * Yb + dB * Ya) * ex;
+    const T gy = SA * Zby + SB * Zay + (dA * Yb + dB * Ya) * ey;
+    const T gz = SA * Zbz + SB * Zaz + (dA * Yb + dB * Ya) * ez;
+    const T lap = SA * Qb + SB * Qa + (T)2 * (dA * (ex * Zbx + ey * Zby + ez * Zbz) + dB * (ex * Zax + ey * Zay + ez * Zaz)) +
+                  si.L[A] * Yb + si.L[B] * Ya;
+    f(t, val, gx, gy, gz, lap);
   });
 }
 
