@@ -660,15 +660,18 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads) eval_kernel(const Sys
       const int n = s.n[sp], e0 = sp ? Nup : 0, uo = sp ? U0 : 0;
       if (n == 0) continue;
       Tb* Y = X + n * nev;
+      Tb* Bt = Y + n * nev;  // bulk-type copy of the inverse
       for (int u = 0; u < s.U[sp]; ++u) {
         const int eb = __ldg(s.kap_off[sp] + u), ee = __ldg(s.kap_off[sp] + u + 1);
         if (eb == ee) continue;
         const double* B = Binv[sp] + u * n * n;
+        for (int q = lane; q < n * n; q += 32) Bt[q] = (Tb)B[q];
+        __syncwarp();
         for (int q = lane; q < n * nev; q += 32) {
           const int o = q / nev, c = q % nev;
           Tb x = 0, y = 0;
           for (int e = 0; e < n; ++e) {
-            const Tb b = (Tb)B[o * n + e];
+            const Tb b = Bt[o * n + e];
             x += b * Phi[(e0 + e) * nev + c];
             y += b * Lphi[(e0 + e) * nev + c];
           }
@@ -735,6 +738,8 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
   Tb* rnE = Stab + 6 * s.N * s.Nn;                      // [N] r from the proposed position
   Tb* rnN = rnE + s.N;                                  // [Nn]
   Tb* Snew = rnN + s.Nn;                                // [Nn][6]
+  Tb* Upo = Snew + 6 * s.Nn;                            // [5][N] Rbar(r_ej)^k, current position of e
+  Tb* Upn = Upo + 5 * s.N;                              // [5][N] Rbar(r_ej)^k, proposed position
 
   const int N = s.N, Nn = s.Nn, Nup = s.Nup, U0 = s.U[0], ldo = L.nocc_max;
   const Tb kap = (Tb)s.kappa;
@@ -855,7 +860,17 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
       // pair sums Y^{k,q} = sum_{j != e} u_ej^k s_j^q (the terms of e are s_e^A Y^{k,B} + s_e^B Y^{k,A}).
       for (int j = lane; j < N; j += 32) {
         const Tb dx = (Tb)(rn[0] - R[3 * j]), dy = (Tb)(rn[1] - R[3 * j + 1]), dz = (Tb)(rn[2] - R[3 * j + 2]);
-        rnE[j] = j == e ? (Tb)0 : vsqrt(dx * dx + dy * dy + dz * dz);
+        const Tb rnew = j == e ? (Tb)0 : vsqrt(dx * dx + dy * dy + dz * dz);
+        rnE[j] = rnew;
+        const Tb uo = (Tb)1 / ((Tb)1 + kap * rEE[e * N + j]), un = (Tb)1 / ((Tb)1 + kap * rnew);
+        Tb po = (Tb)1, pn = (Tb)1;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          Upo[k * N + j] = po;
+          Upn[k * N + j] = pn;
+          po *= uo;
+          pn *= un;
+        }
       }
       for (int a = lane; a < Nn; a += 32) {
         const double* nu = s.nuc4 + 4 * a;
@@ -892,9 +907,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
           for (int q = 0; q < 6; ++q) Yo[q] = Yn[q] = (Tb)0;
           for (int j = 0; j < N; ++j) {
             if (j == e) continue;
-            const Tb uo = (Tb)1 / ((Tb)1 + kap * rEE[e * N + j]), un = (Tb)1 / ((Tb)1 + kap * rnE[j]);
-            Tb po = (Tb)1, pn = (Tb)1;
-            for (int kk = 0; kk < k; ++kk) { po *= uo; pn *= un; }
+            const Tb po = Upo[k * N + j], pn = Upn[k * N + j];
             const Tb* Sj = Stab + (a * N + j) * 6;
 #pragma unroll
             for (int q = 0; q < 6; ++q)
@@ -985,7 +998,7 @@ int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
   for (int sp = 0; sp < 2; ++sp) {
     const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
     scr = std::max(scr, ng * (8 * n * n + 4 * n) + 16);
-    scr = std::max(scr, 2 * n * s.n_ev * tb);
+    scr = std::max(scr, (2 * n * s.n_ev + n * n) * tb);
   }
   L.scratch = take(scr);
   L.part = take(5 * tb * std::max(s.n_ev_chunk, 1));
@@ -1038,7 +1051,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   }
   L.cvec = take(std::max(cv, 8));
   L.scratch = take(std::max(scr, 16));
-  L.geo = take(tb * (N * N + N * s.Nn + 6 * N * s.Nn + N + s.Nn + 6 * s.Nn));
+  L.geo = take(tb * (N * N + N * s.Nn + 6 * N * s.Nn + N + s.Nn + 6 * s.Nn + 10 * N));
   L.warp_bytes = off;
   int wpb = max_smem / off;
   if (wpb > 16) wpb = 16;
