@@ -143,6 +143,16 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   BlobBuilder bb;
   std::vector<float> coef_f(h.orb_coef.begin(), h.orb_coef.end());
   std::vector<float> een_cf(h.een_c.begin(), h.een_c.end());
+  auto split = [](const std::vector<double>& v) {
+    std::vector<float> o(2 * v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      const float hi = (float)v[i];
+      o[2 * i] = hi;
+      o[2 * i + 1] = (float)(v[i] - (double)hi);
+    }
+    return o;
+  };
+  const std::vector<float> zeta_ds = split(h.sh_zeta), norm_ds = split(h.sh_norm), coef_ds = split(h.orb_coef);
   const size_t o_nuc4 = bb.add(h.nuc4), o_nuc_elem = bb.add(h.nuc_elem), o_sh_center = bb.add(h.sh_center),
                o_sh_l = bb.add(h.sh_l), o_sh_first = bb.add(h.sh_first), o_sh_zeta = bb.add(h.sh_zeta),
                o_sh_norm = bb.add(h.sh_norm), o_orb_lo = bb.add(h.orb_lo), o_orb_hi = bb.add(h.orb_hi),
@@ -156,7 +166,8 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
                o_ko0 = bb.add(h.kap_off[0]), o_ko1 = bb.add(h.kap_off[1]), o_ke0 = bb.add(h.kap_ent[0]),
                o_ke1 = bb.add(h.kap_ent[1]), o_oc0 = bb.add(h.occ_chunk[0]), o_oc1 = bb.add(h.occ_chunk[1]),
                o_oco0 = bb.add(h.occ_chunk_off[0]), o_oco1 = bb.add(h.occ_chunk_off[1]), o_evc = bb.add(h.ev_chunk),
-               o_evco = bb.add(h.ev_chunk_off), o_dc = bb.add(h.det_chunk), o_dco = bb.add(h.det_chunk_off);
+               o_evco = bb.add(h.ev_chunk_off), o_dc = bb.add(h.det_chunk), o_dco = bb.add(h.det_chunk_off),
+               o_zds = bb.add(zeta_ds), o_nds = bb.add(norm_ds), o_cds = bb.add(coef_ds);
   cudaError_t e = cudaMalloc(&ls.blob, bb.bytes.size());
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(system tables)");
   ls.blob_bytes = bb.bytes.size();
@@ -230,6 +241,9 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.det_chunk = (const int*)(B + o_dc);
   d.det_chunk_off = (const int*)(B + o_dco);
   d.state_doubles = h.U[0] * h.n[0] * h.n[0] + h.U[1] * h.n[1] * h.n[1] + 2 * (h.U[0] + h.U[1]);
+  d.sh_zeta_ds = (const float*)(B + o_zds);
+  d.sh_norm_ds = (const float*)(B + o_nds);
+  d.orb_coef_ds = (const float*)(B + o_cds);
   for (int p = 0; p < 2; ++p) {
     const int tb = p == VBQMC_MIXED ? 4 : 8;
     ls.lay_rc_eval[p] = vbq::make_eval_layout(d, tb, ctx->max_smem, ls.lay_eval[p]);

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cfloat>
 
+#include "dsfloat.cuh"
 #include "kernels.h"
 #include "wf_device.cuh"
 
@@ -51,10 +52,58 @@ __device__ __forceinline__ void basis_at(const SysDev& s, int lane, double x, do
   }
 }
 
+// Values of all basis functions at point r in float-float (mixed form).  Per center the
+// displacement and r^2 are formed in double and split once; per shell exp(-zeta r^2) and the
+// cartesian factors are float-float.  ctab: [Nn][4] scratch (dx, dy, dz, r^2).
+__device__ __forceinline__ void basis_values_ds(const SysDev& s, int lane, double x, double y, double z, dsf* ctab,
+                                                dsf* out) {
+  for (int c = lane; c < s.Nn; c += 32) {
+    const double* nu = s.nuc4 + 4 * c;
+    const double dx = x - __ldg(nu), dy = y - __ldg(nu + 1), dz = z - __ldg(nu + 2);
+    ctab[4 * c] = ds_from_double(dx);
+    ctab[4 * c + 1] = ds_from_double(dy);
+    ctab[4 * c + 2] = ds_from_double(dz);
+    ctab[4 * c + 3] = ds_from_double(fma(dx, dx, fma(dy, dy, dz * dz)));
+  }
+  __syncwarp();
+  for (int sh = lane; sh < s.S; sh += 32) {
+    const int c = __ldg(s.sh_center + sh), l = __ldg(s.sh_l + sh), f = __ldg(s.sh_first + sh);
+    const float2 zt = __ldg(reinterpret_cast<const float2*>(s.sh_zeta_ds) + sh);
+    dsf e = {1.0f, 0.0f};
+    if (zt.x != 0.0f) e = ds_exp_neg(ds_mul(ctab[4 * c + 3], dsf{zt.x, zt.y}));
+    const float2* nr = reinterpret_cast<const float2*>(s.sh_norm_ds) + 6 * sh;
+    if (l == 0) {
+      const float2 n0 = __ldg(nr);
+      out[f] = ds_mul(dsf{n0.x, n0.y}, e);
+    } else if (l == 1) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float2 nq = __ldg(nr + q);
+        out[f + q] = ds_mul(ds_mul(dsf{nq.x, nq.y}, ctab[4 * c + q]), e);
+      }
+    } else {
+      const int ia[6] = {0, 1, 2, 0, 0, 1};
+      const int ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const float2 nq = __ldg(nr + q);
+        out[f + q] = ds_mul(ds_mul(dsf{nq.x, nq.y}, ds_mul(ctab[4 * c + ia[q]], ctab[4 * c + ib[q]])), e);
+      }
+    }
+  }
+}
+
 // e-n Jastrow/e-e Jastrow coefficient blocks as Tb
 struct PadeCoef {
   double a1, a2, q[4];
 };
+// 1/x to about 47 bits: float reciprocal refined by one Newton step in double (one division's
+// worth of FP64 work is ~20 instructions on this part; this is 3).
+__device__ __forceinline__ double recip(double x) {
+  double y = (double)__frcp_rn((float)x);
+  return y * fma(-x, y, 2.0);
+}
+
 __device__ __forceinline__ PadeCoef en_coef(const SysDev& s, int a) {
   const double* p = s.jas_a + 6 * __ldg(s.nuc_elem + a);
   PadeCoef c;
@@ -163,7 +212,7 @@ __device__ __forceinline__ void term_ratios(const SysDev& s, int lane, const dou
 //      E_L and grad ln|Psi|; optionally the walker state (inverses, ln|det|, signs) is stored
 //   D  parameter derivatives (structure coefficients, Jastrow, orbital excitations)
 template <class Tb>
-__global__ void __launch_bounds__(EvalBounds<Tb>::threads) eval_kernel(const SysDev s, const EvalLayout L, int W,
+__global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1) eval_kernel(const SysDev s, const EvalLayout L, int W,
                                                    const double* __restrict__ Rg, double* __restrict__ logpsi,
                                                    double* __restrict__ sgn_out, double* __restrict__ eloc,
                                                    double* __restrict__ grad, double* __restrict__ Og,
@@ -335,14 +384,14 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads) eval_kernel(const Sys
     Tb* by = bx + M;
     Tb* bz = by + M;
     Tb* bl = bz + M;
-    double* bvd = kSameType<Tb, double> ? reinterpret_cast<double*>(bv)
-                                        : reinterpret_cast<double*>(scr + align16(5 * M * (int)sizeof(Tb)));
+    // mixed form: float-float values of the basis functions for the determinant orbitals
+    dsf* bds = reinterpret_cast<dsf*>(scr + align16(5 * M * (int)sizeof(Tb)));
+    dsf* ctab = bds + M;
+    dsf* partds = reinterpret_cast<dsf*>(partd);
     const Tb* cf = orb_coefs<Tb>(s);
     for (int e = 0; e < N; ++e) {
       basis_at<Tb, true>(s, lane, R[3 * e], R[3 * e + 1], R[3 * e + 2], bv, bx, by, bz, bl);
-      if (!kSameType<Tb, double>)
-        basis_at<double, false>(s, lane, R[3 * e], R[3 * e + 1], R[3 * e + 2], bvd, nullptr, nullptr, nullptr,
-                                nullptr);
+      if (!kSameType<Tb, double>) basis_values_ds(s, lane, R[3 * e], R[3 * e + 1], R[3 * e + 2], ctab, bds);
       __syncwarp();
       for (int c = lane; c < s.n_ev_chunk; c += 32) {
         const int4 ch = __ldg(reinterpret_cast<const int4*>(s.ev_chunk) + c);
@@ -358,10 +407,13 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads) eval_kernel(const Sys
       if (!kSameType<Tb, double>)
         for (int c = lane; c < s.n_det_chunk; c += 32) {
           const int4 ch = __ldg(reinterpret_cast<const int4*>(s.det_chunk) + c);
-          const double* cb = s.orb_coef + ch.w;
-          double vd = 0.0;
-          for (int mu = ch.y; mu < ch.z; ++mu) vd = fma(__ldg(cb + mu), bvd[mu], vd);
-          partd[c] = vd;
+          const float2* cb = reinterpret_cast<const float2*>(s.orb_coef_ds) + ch.w;
+          dsf acc = {0.0f, 0.0f};
+          for (int mu = ch.y; mu < ch.z; ++mu) {
+            const float2 lm = __ldg(cb + mu);
+            acc = ds_add(acc, ds_mul(dsf{lm.x, lm.y}, bds[mu]));
+          }
+          partds[c] = acc;
         }
       __syncwarp();
       const Tb G0 = G[3 * e], G1 = G[3 * e + 1], G2 = G[3 * e + 2];
@@ -379,7 +431,9 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads) eval_kernel(const Sys
             vd = (double)v;
           } else {
             const int d0 = __ldg(s.det_chunk_off + q), d1 = __ldg(s.det_chunk_off + q + 1);
-            for (int c = d0; c < d1; ++c) vd += partd[c];
+            dsf acc = {0.0f, 0.0f};
+            for (int c = d0; c < d1; ++c) acc = ds_add(acc, partds[c]);
+            vd = ds_to_double(acc);
           }
           PhiD[e * nevd + q] = vd;
           v = (Tb)vd;
@@ -433,30 +487,39 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads) eval_kernel(const Sys
     Tdet[ud] = Tv;
   }
   __syncwarp();
-  // grad_i ln|Psi| = grad_i lnJ + sum_u W_u sum_o Binv_u[o][i] grad phi_o(r_i)
+  // grad_i ln|Psi| = grad_i lnJ + sum_u W_u sum_o Binv_u[o][i] grad phi_o(r_i), in the bulk type
+  // (it feeds the Jastrow-parameter derivatives and the drift, not E_L)
+  Tb* Bt = reinterpret_cast<Tb*>(scr);
+  {
+    const int nb0 = s.U[0] * s.n[0] * s.n[0], nb1 = s.U[1] * s.n[1] * s.n[1];
+    for (int q = lane; q < nb0; q += 32) Bt[q] = (Tb)Binv[0][q];
+    for (int q = lane; q < nb1; q += 32) Bt[nb0 + q] = (Tb)Binv[1][q];
+  }
+  __syncwarp();
   double kin_loc = 0.0;
   for (int e = lane; e < N; e += 32) {
     const int sp = e >= Nup ? 1 : 0, ie = e - (sp ? Nup : 0), n = s.n[sp], uo = sp ? U0 : 0;
-    double gx = 0.0, gy = 0.0, gz = 0.0;
+    const Tb* Bs = Bt + (sp ? s.U[0] * s.n[0] * s.n[0] : 0);
+    Tb gx = 0, gy = 0, gz = 0;
     for (int u = 0; u < s.U[sp]; ++u) {
-      const double* B = Binv[sp] + u * n * n;
-      double ax = 0.0, ay = 0.0, az = 0.0;
+      const Tb* B = Bs + u * n * n;
+      Tb ax = 0, ay = 0, az = 0;
       for (int o = 0; o < n; ++o) {
-        const double b = B[o * n + ie];
+        const Tb b = B[o * n + ie];
         const Tb* gp = Gphi + (e * nevd + __ldg(s.det_ev[sp] + u * n + o)) * 3;
-        ax = fma(b, (double)gp[0], ax);
-        ay = fma(b, (double)gp[1], ay);
-        az = fma(b, (double)gp[2], az);
+        ax += b * gp[0];
+        ay += b * gp[1];
+        az += b * gp[2];
       }
-      const double Wu = Wdet[uo + u];
-      gx = fma(Wu, ax, gx);
-      gy = fma(Wu, ay, gy);
-      gz = fma(Wu, az, gz);
+      const Tb Wu = (Tb)Wdet[uo + u];
+      gx += Wu * ax;
+      gy += Wu * ay;
+      gz += Wu * az;
     }
     const double G0 = (double)G[3 * e], G1 = (double)G[3 * e + 1], G2 = (double)G[3 * e + 2];
-    vg[3 * e] = G0 + gx;
-    vg[3 * e + 1] = G1 + gy;
-    vg[3 * e + 2] = G2 + gz;
+    vg[3 * e] = G0 + (double)gx;
+    vg[3 * e + 1] = G1 + (double)gy;
+    vg[3 * e + 2] = G2 + (double)gz;
     kin_loc += (double)LJ[e] + G0 * G0 + G1 * G1 + G2 * G2;
   }
   const double kin = warp_sum(kin_loc) + kphi;
@@ -708,7 +771,7 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads) eval_kernel(const Sys
 // double-precision orbital values (first sweep without state, and every 'refresh' sweeps).
 // The proposed orbital row uses the bulk type; ratios and Sherman-Morrison updates are double.
 template <class Tb>
-__global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepLayout L, int W, double* __restrict__ Rg,
+__global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const SweepLayout L, int W, double* __restrict__ Rg,
                                                     int nsweeps, int refresh, const double* __restrict__ state_in,
                                                     double step, uint64_t seed, uint32_t step0, uint32_t tag,
                                                     uint32_t woff, int* __restrict__ nacc) {
@@ -726,7 +789,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
   double* PhiO = reinterpret_cast<double*>(base + L.PhiO);
   double* basd = reinterpret_cast<double*>(base + L.bas);
   Tb* bas = reinterpret_cast<Tb*>(base + L.bas);
-  Tb* vrow = reinterpret_cast<Tb*>(base + L.vrow);
+  double* vrowd = reinterpret_cast<double*>(base + L.vrow);
   Tb* part = reinterpret_cast<Tb*>(base + L.part);
   double* partd = reinterpret_cast<double*>(base + L.part);
   double* rho = reinterpret_cast<double*>(base + L.rho);
@@ -838,7 +901,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
         const int c0 = __ldg(s.occ_chunk_off[sp] + q), c1 = __ldg(s.occ_chunk_off[sp] + q + 1);
         Tb v = 0;
         for (int c = c0; c < c1; ++c) v += part[c];
-        vrow[q] = v;
+        vrowd[q] = (double)v;
       }
       __syncwarp();
       // determinant ratios rho_u = sum_o v_occ(o) Binv_u[o][ie]
@@ -847,7 +910,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
       for (int ub = 0; ub < U; ub += ng) {
         const int u = ub + g;
         double r = 0.0;
-        if (u < U && gl < n) r = (double)vrow[__ldg(dl + u * n + gl)] * Binv[sp][u * n * n + gl * n + ie];
+        if (u < U && gl < n) r = vrowd[__ldg(dl + u * n + gl)] * Binv[sp][u * n * n + gl * n + ie];
         r = group_sum(r, G);
         if (u < U && gl == 0) rho[u] = r;
       }
@@ -927,8 +990,8 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
           });
         }
       }
-      const double dJ = warp_sum((double)dj);
-      const double prob = rphi * rphi * exp(2.0 * dJ);
+      const Tb dJ = warp_sum(dj);
+      const double prob = rphi * rphi * (double)vexp((Tb)2 * dJ);
       if (uacc < prob) {
         // Sherman-Morrison: Binv <- Binv - Binv[:, ie] (v^T Binv - e_ie^T) / rho
         for (int ub = 0; ub < U; ub += ng) {
@@ -941,13 +1004,13 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SysDev s, const SweepL
           if (act && gl < n) {
             const int j = gl;
             double wj = (j == ie) ? -1.0 : 0.0;
-            for (int o = 0; o < n; ++o) wj = fma((double)vrow[__ldg(dl + u * n + o)], B[o * n + j], wj);
-            const double f = wj / rho[u];
+            for (int o = 0; o < n; ++o) wj = fma(vrowd[__ldg(dl + u * n + o)], B[o * n + j], wj);
+            const double f = wj * recip(rho[u]);
             for (int o = 0; o < n; ++o) B[o * n + j] = fma(-cv[o], f, B[o * n + j]);
           }
           __syncwarp();
         }
-        const double irphi = 1.0 / rphi;
+        const double irphi = recip(rphi);
         for (int k = lane; k < s.nterm; k += 32) wk[k] *= rho[__ldg(s.term_det + 2 * k + sp)] * irphi;
         if (lane < 3) R[3 * e + lane] = rn[lane];
         for (int j = lane; j < N; j += 32) rEE[e * N + j] = rEE[j * N + e] = rnE[j];
@@ -994,7 +1057,8 @@ int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
   L.Wdet = take(8 * Ut);
   L.Tdet = take(8 * Ut);
   L.rk = take(8 * s.nterm);
-  int scr = align16(5 * s.M * tb) + 8 * s.M;
+  int scr = align16(5 * s.M * tb) + 8 * s.M + 32 * s.Nn;
+  scr = std::max(scr, tb * (s.U[0] * s.n[0] * s.n[0] + s.U[1] * s.n[1] * s.n[1]));
   for (int sp = 0; sp < 2; ++sp) {
     const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
     scr = std::max(scr, ng * (8 * n * n + 4 * n) + 16);

@@ -119,6 +119,10 @@ struct SysDev {
   const int* det_chunk;
   const int* det_chunk_off;
   int state_doubles;                   // persistent walker state: inverses, ln|det|, signs
+  // float-float copies (hi, lo) for the mixed form's double-accurate values
+  const float* sh_zeta_ds;             // [S][2]
+  const float* sh_norm_ds;             // [S][6][2]
+  const float* orb_coef_ds;            // like orb_coef, [.][2]
 };
 
 }  // namespace vbq

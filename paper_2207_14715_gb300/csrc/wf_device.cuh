@@ -14,6 +14,8 @@ namespace vbq {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+__device__ __forceinline__ int lane_id() { return (int)(threadIdx.x & 31); }
+
 // ------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from the published round function.
 // ------------------------------------------------------------------------------------
@@ -106,6 +108,9 @@ __device__ __forceinline__ void group_lu_inverse(double* A, double* Binv, int* p
     }
     __syncwarp();
   }
+  // reciprocal of the U diagonal: lane i of the group holds 1/U_ii; the back substitution
+  // multiplies by it (broadcast by shuffle) instead of dividing in every lane
+  const double dinv = (active && glane < n && !singular) ? 1.0 / A[glane * n + glane] : 0.0;
   if (active && glane < n) {
     const int j = glane;
     if (!singular) {
@@ -114,15 +119,20 @@ __device__ __forceinline__ void group_lu_inverse(double* A, double* Binv, int* p
         for (int k = 0; k < i; ++k) y = fma(-A[i * n + k], Binv[k * n + j], y);
         Binv[i * n + j] = y;
       }
-      for (int i = n - 1; i >= 0; --i) {
-        double x = Binv[i * n + j];
-        for (int k = i + 1; k < n; ++k) x = fma(-A[i * n + k], Binv[k * n + j], x);
-        Binv[i * n + j] = x / A[i * n + i];
-      }
     } else {
       for (int i = 0; i < n; ++i) Binv[i * n + j] = 0.0;
     }
   }
+  for (int i = n - 1; i >= 0; --i) {
+    const double di = __shfl_sync(kFull, dinv, (lane_id() & ~(G - 1)) + i);
+    if (active && glane < n && !singular) {
+      const int j = glane;
+      double x = Binv[i * n + j];
+      for (int k = i + 1; k < n; ++k) x = fma(-A[i * n + k], Binv[k * n + j], x);
+      Binv[i * n + j] = x * di;
+    }
+  }
+
   double ld = 0.0, neg = 0.0;
   if (active && glane < n && !singular) {
     const double d = A[glane * n + glane];
