@@ -229,8 +229,9 @@ def run_ours(args, ws, rank, local):
     R = torch.tensor(S.initial_walkers(spec, W, SEED + 1000 * rank), device=dev)
     lp = torch.zeros(W, dtype=torch.float64, device=dev)
     sg, el = torch.zeros_like(lp), torch.zeros_like(lp)
-    O = torch.zeros((W, P), dtype=torch.float64, device=dev)
-    dE = torch.zeros_like(O)
+    # derivative arrays in each form's bulk type
+    Ods = {p: torch.zeros((W, P), dtype=vbqmc.deriv_dtype(p), device=dev) for p in (vbqmc.MIXED, vbqmc.FP64)}
+    dEs = {p: torch.zeros_like(Ods[p]) for p in Ods}
     nacc = torch.zeros(W, dtype=torch.int32, device=dev)
     # persistent walker state (Slater inverses, ln|det|, signs) carried from one step to the next
     state = torch.zeros((W, ctx.walker_state_size(0)), dtype=torch.float64, device=dev)
@@ -248,7 +249,7 @@ def run_ours(args, ws, rank, local):
                       state_valid=True, nacc=nacc)
         if ev is not None:
             ev[1].record(stream)
-        ctx.eval_walkers(0, prec, R, lp, sg, el, None, O, dE, state_out=state)
+        ctx.eval_walkers(0, prec, R, lp, sg, el, None, Ods[prec], dEs[prec], state_out=state)
         if ev is not None:
             ev[2].record(stream)
 
@@ -300,6 +301,8 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
     t_e2e = allmax(time.perf_counter() - t0, ws)
     barrier(ws)
+    lin = lin_method_timing(ctx, vbqmc, dev, args.steps) if not args.no_lin else None
+    barrier(ws)
     if rank != 0:
         return
     model = work_model(spec, info)
@@ -341,11 +344,37 @@ def run_ours(args, ws, rank, local):
         "cpu_baseline": cb,
         "e2e": {"value": ws * W * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
+        "linear_method": lin,
         "gpu_launches": 2 * m["steps"],
         "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
                    "reasons": clocks.get("reasons", [])},
     }
     print(json.dumps(line), flush=True)
+
+
+def lin_method_timing(ctx, vbqmc, dev, steps):
+    """Linear-method estimators for 2^20 samples x 400 parameters (mixed form, float inputs):
+    time per accumulation with CUDA events, inputs resident in HBM (larger than L2)."""
+    import torch
+    M, P = 1 << 20, 400
+    g = torch.Generator(device=dev)
+    g.manual_seed(SEED)
+    O = torch.randn((M, P), generator=g, device=dev, dtype=torch.float32)
+    dE = 0.3 * torch.randn((M, P), generator=g, device=dev, dtype=torch.float32)
+    E = -10.0 + torch.randn(M, generator=g, device=dev, dtype=torch.float64)
+    ctx.accumulate_lin_matrices(vbqmc.MIXED, O, dE, E)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(3, steps)
+    e0.record()
+    for _ in range(n):
+        ctx.accumulate_lin_matrices(vbqmc.MIXED, O, dE, E)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    flops = 2 * 2.0 * M * P * P  # S and H products
+    return {"samples": M, "params": P, "ms": ms, "tflops_fp32_products": flops / (ms * 1e-3) / 1e12,
+            "input_bytes": 2 * M * P * 4 + M * 8}
 
 
 def main():
@@ -357,6 +386,7 @@ def main():
     ap.add_argument("--walkers", type=int, default=W_PER_GPU)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-lin", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

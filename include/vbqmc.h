@@ -127,7 +127,8 @@ int vbqmc_inspect_system(const vbqmc_system_desc* desc, int* info, int* terms, i
 int vbqmc_walker_state_size(vbqmc_ctx* ctx, int sys_id, int* ndoubles);
 
 /* Evaluates the trial wave function at W walker positions (Sec. 2.1; Sec. 2.3.1 for E_L,
- * O_j and E_L,j).
+ * O_j and E_L,j).  The element type of O and dEL is double for VBQMC_FP64 and float for
+ * VBQMC_MIXED (the form's bulk type).
  *   R         [W][N][3] device, in
  *   logpsi    [W] device, out: ln|Psi|       sign [W] device, out: sign of Psi (0 if singular)
  *   eloc      [W] device, out: E_L = (H Psi)/Psi, Hamiltonian with nucleus-nucleus repulsion
@@ -137,7 +138,7 @@ int vbqmc_walker_state_size(vbqmc_ctx* ctx, int sys_id, int* ndoubles);
  *   state_out [W][ndoubles] device or NULL, out: walker state at R (see above)
  * precision: VBQMC_FP64 or VBQMC_MIXED.  W may be 0. */
 int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const double* R, double* logpsi,
-                       double* sign, double* eloc, double* grad, double* O, double* dEL, double* state_out,
+                       double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out,
                        void* stream);
 
 /* VMC (Sec. 2.3.1): nsweeps sweeps of single-electron Metropolis moves over every walker,
@@ -159,7 +160,23 @@ int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const d
 int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R, int nsweeps, double step,
                     uint64_t seed, uint32_t step0, uint32_t system_tag, uint32_t walker_offset, int refresh,
                     double* state, int state_valid, int* nacc, double* logpsi, double* sign, double* eloc,
-                    double* O, double* dEL, void* stream);
+                    void* O, void* dEL, void* stream);
+
+/* Linear-method estimators from M samples (Sec. 2.3.1, Eqs. Hi0, H0j, Hij, Sij, feeding the
+ * generalized eigenproblem Eq. geneigeqM).  With weights w (NULL: all 1), averages
+ * <x> = sum w x / sum w and Ot = O - <O>, the outputs are
+ *   E0 = <E_L>,  gL_i = 2 <Ot_i E_L>,  gR_j = 2 (<Ot_j E_L> + <E_L,j>),
+ *   S[i][j] = <Ot_i Ot_j>,  H[i][j] = <Ot_i (E_L Ot_j + E_L,j)>,
+ * which equal the printed sums of averages term by term.
+ *   O, dEL  [M][P] device, element type double (VBQMC_FP64) or float (VBQMC_MIXED)
+ *   eloc    [M] device double;  weights [M] device double or NULL
+ *   E0 [1], gL [P], gR [P], S [P][P], H [P][P]: device double, out
+ * Column sums are double; centred values are float; products are accumulated on the FP32
+ * pipe in chunks of up to 16384 samples and the chunk partials summed in double.  The
+ * context keeps a device workspace (grown on demand, synchronizing 'stream' when it grows). */
+int vbqmc_accumulate_lin_matrices(vbqmc_ctx* ctx, int precision, int P, int64_t M, const void* O, const void* dEL,
+                                  const double* eloc, const double* weights, double* E0, double* gL, double* gR,
+                                  double* S, double* H, void* stream);
 
 /* Launch shape of the walker kernels for a loaded system: out[0..3] = walkers (warps) per
  * thread block and shared-memory bytes per walker of the evaluation kernel, then the same two

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "linmethod.h"
 #include "vbqmc_internal.h"
 
 namespace {
@@ -64,6 +65,8 @@ struct vbqmc_ctx {
   int max_smem = 0;
   int last_launches = 0;
   LoadedSystem sys[VBQMC_MAX_SYSTEMS];
+  void* work = nullptr;      // grow-only device workspace of the linear-method accumulation
+  size_t work_bytes = 0;
 };
 
 static void free_system(LoadedSystem& s) {
@@ -99,6 +102,7 @@ void vbqmc_destroy(vbqmc_ctx* ctx) {
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
   for (auto& s : ctx->sys) free_system(s);
+  if (ctx->work) cudaFree(ctx->work);
   delete ctx;
 }
 
@@ -288,7 +292,7 @@ int vbqmc_walker_state_size(vbqmc_ctx* ctx, int sys_id, int* ndoubles) {
 }
 
 int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const double* R, double* logpsi,
-                       double* sign, double* eloc, double* grad, double* O, double* dEL, double* state_out,
+                       double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out,
                        void* stream) {
   int rc = check_call(ctx, sys_id, precision, W);
   if (rc) return rc;
@@ -309,8 +313,8 @@ int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const d
 
 int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R, int nsweeps, double step,
                     uint64_t seed, uint32_t step0, uint32_t system_tag, uint32_t walker_offset, int refresh,
-                    double* state, int state_valid, int* nacc, double* logpsi, double* sign, double* eloc, double* O,
-                    double* dEL, void* stream) {
+                    double* state, int state_valid, int* nacc, double* logpsi, double* sign, double* eloc, void* O,
+                    void* dEL, void* stream) {
   int rc = check_call(ctx, sys_id, precision, W);
   if (rc) return rc;
   ctx->last_launches = 0;
@@ -342,6 +346,34 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
     ++launches;
   }
   ctx->last_launches = launches;
+  return VBQMC_OK;
+}
+
+int vbqmc_accumulate_lin_matrices(vbqmc_ctx* ctx, int precision, int P, int64_t M, const void* O, const void* dEL,
+                                  const double* eloc, const double* weights, double* E0, double* gL, double* gR,
+                                  double* S, double* H, void* stream) {
+  if (!ctx) return fail(VBQMC_ERR_ARG, "null context");
+  if (precision != VBQMC_FP64 && precision != VBQMC_MIXED) return fail(VBQMC_ERR_ARG, "bad precision mode");
+  if (P < 1 || M < 1) return fail(VBQMC_ERR_ARG, "need P >= 1 and M >= 1");
+  if (!O || !dEL || !eloc || !E0 || !gL || !gR || !S || !H) return fail(VBQMC_ERR_ARG, "null required pointer");
+  DeviceGuard g(ctx->device);
+  ctx->last_launches = 0;
+  const size_t need = vbq::lin_workspace_bytes(P, M);
+  if (need > ctx->work_bytes) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (ctx->work) cudaFree(ctx->work);
+    ctx->work = nullptr;
+    ctx->work_bytes = 0;
+    e = cudaMalloc(&ctx->work, need);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(linear-method workspace)");
+    ctx->work_bytes = need;
+  }
+  int nl = 0;
+  cudaError_t e = vbq::launch_lin(precision == VBQMC_MIXED, P, (long long)M, O, dEL, eloc, weights, ctx->work, E0, gL,
+                                  gR, S, H, (cudaStream_t)stream, &nl);
+  if (e != cudaSuccess) return cuda_fail(e, "linear-method kernels");
+  ctx->last_launches = nl;
   return VBQMC_OK;
 }
 

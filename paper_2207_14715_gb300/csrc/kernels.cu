@@ -215,8 +215,8 @@ template <class Tb>
 __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1) eval_kernel(const SysDev s, const EvalLayout L, int W,
                                                    const double* __restrict__ Rg, double* __restrict__ logpsi,
                                                    double* __restrict__ sgn_out, double* __restrict__ eloc,
-                                                   double* __restrict__ grad, double* __restrict__ Og,
-                                                   double* __restrict__ dELg, double* __restrict__ state_out) {
+                                                   double* __restrict__ grad, Tb* __restrict__ Og,
+                                                   Tb* __restrict__ dELg, double* __restrict__ state_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wl = threadIdx.x >> 5;
@@ -536,8 +536,8 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1) eval_kernel(const 
 
   // ---- D. parameter derivatives ----
   const int P = s.P;
-  double* Ow = Og + (size_t)w * P;
-  double* Ew = dELg ? dELg + (size_t)w * P : nullptr;
+  Tb* Ow = Og + (size_t)w * P;
+  Tb* Ew = dELg ? dELg + (size_t)w * P : nullptr;
   // D1. structure coefficients: O_I = Phi_I/Phi, E_L,I = -1/2 (K[Phi_I] - O_I K[Phi])
   for (int q = lane; q < s.n_cparam; q += 32) {
     const int I = __ldg(s.cparam + q);
@@ -550,8 +550,8 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1) eval_kernel(const 
       o += r;
       kk += r * (tdet[a] + tdet[U0 + b]);
     }
-    Ow[q] = o;
-    if (Ew) Ew[q] = -0.5 * (kk - o * kphi);
+    Ow[q] = (Tb)(o);
+    if (Ew) Ew[q] = (Tb)(-0.5 * (kk - o * kphi));
   }
   // D2. Jastrow parameters: O = d lnJ/d alpha, E_L,alpha = -1/2 sum_i (lap_i g + 2 grad_i g . grad_i ln|Psi|)
   if (s.jas_param) {
@@ -593,8 +593,8 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1) eval_kernel(const 
       for (int q = 0; q < 5; ++q) {
         const double o = warp_sum((double)aO[q]), e = warp_sum((double)aE[q]);
         if (lane == 0) {
-          Ow[s.p_off_a + 5 * E + q] = o;
-          if (Ew) Ew[s.p_off_a + 5 * E + q] = e;
+          Ow[s.p_off_a + 5 * E + q] = (Tb)(o);
+          if (Ew) Ew[s.p_off_a + 5 * E + q] = (Tb)(e);
         }
       }
     }
@@ -636,8 +636,8 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1) eval_kernel(const 
       for (int q = 0; q < 5; ++q) {
         const double o = warp_sum((double)bO[q]), e = warp_sum((double)bE[q]);
         if (lane == 0) {
-          Ow[s.p_off_b + q] = o;
-          if (Ew) Ew[s.p_off_b + q] = e;
+          Ow[s.p_off_b + q] = (Tb)(o);
+          if (Ew) Ew[s.p_off_b + q] = (Tb)(e);
         }
       }
     }
@@ -703,8 +703,8 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1) eval_kernel(const 
             o = fma(b, rawO[q], o);
             e = fma(b, rawE[q], e);
           }
-          Ow[s.p_off_theta + kNfree * E + f] = o;
-          if (Ew) Ew[s.p_off_theta + kNfree * E + f] = e;
+          Ow[s.p_off_theta + kNfree * E + f] = (Tb)(o);
+          if (Ew) Ew[s.p_off_theta + kNfree * E + f] = (Tb)(e);
         }
         __syncwarp();
       }
@@ -757,8 +757,8 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1) eval_kernel(const 
     }
     for (int j = lane; j < nk; j += 32) {
       const double o = kacc[j];
-      Ow[s.p_off_kappa + j] = o;
-      if (Ew) Ew[s.p_off_kappa + j] = -0.5 * (kacc[nk + j] - o * kphi);
+      Ow[s.p_off_kappa + j] = (Tb)(o);
+      if (Ew) Ew[s.p_off_kappa + j] = (Tb)(-0.5 * (kacc[nk + j] - o * kphi));
     }
   }
 }
@@ -1126,7 +1126,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
 
 template <class Tb>
 static cudaError_t launch_eval_t(const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
-                                 double* sign, double* eloc, double* grad, double* O, double* dEL, double* state_out,
+                                 double* sign, double* eloc, double* grad, Tb* O, Tb* dEL, double* state_out,
                                  cudaStream_t st) {
   const int smem = L.wpb * L.warp_bytes;
   cudaError_t e = cudaFuncSetAttribute(eval_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1150,11 +1150,13 @@ static cudaError_t launch_sweep_t(const SysDev& s, const SweepLayout& L, int W, 
 }
 
 cudaError_t launch_eval(int precision, const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
-                        double* sign, double* eloc, double* grad, double* O, double* dEL, double* state_out,
+                        double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out,
                         cudaStream_t st) {
   if (precision == VBQMC_MIXED)
-    return launch_eval_t<float>(s, L, W, R, logpsi, sign, eloc, grad, O, dEL, state_out, st);
-  return launch_eval_t<double>(s, L, W, R, logpsi, sign, eloc, grad, O, dEL, state_out, st);
+    return launch_eval_t<float>(s, L, W, R, logpsi, sign, eloc, grad, static_cast<float*>(O),
+                                static_cast<float*>(dEL), state_out, st);
+  return launch_eval_t<double>(s, L, W, R, logpsi, sign, eloc, grad, static_cast<double*>(O),
+                               static_cast<double*>(dEL), state_out, st);
 }
 
 cudaError_t launch_sweep(int precision, const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps,

@@ -28,7 +28,7 @@ int make_eval_layout(const SysDev& s, int bulk_bytes, int max_smem, EvalLayout& 
 int make_sweep_layout(const SysDev& s, int bulk_bytes, int max_smem, SweepLayout& L);
 
 cudaError_t launch_eval(int precision, const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
-                        double* sign, double* eloc, double* grad, double* O, double* dEL, double* state_out,
+                        double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out,
                         cudaStream_t st);
 cudaError_t launch_sweep(int precision, const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps,
                          int refresh, const double* state_in, double step, uint64_t seed, uint32_t step0, uint32_t tag,

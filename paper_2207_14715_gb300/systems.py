@@ -319,6 +319,13 @@ def ethylene_vb(seed: int = 20220728 + 1, n_virt_center: int = 15, n_virt_deloc:
         jas_param=params, kappa_kl=kap, step=0.3)
 
 
+def ethylene_vb_p400(seed: int = 20220728 + 4) -> SystemSpec:
+    """The ethylene-shaped system with enough virtual orbitals for exactly 400 parameters
+    (5 structure coefficients, 45 Jastrow, 350 orbital excitations), for the linear-method
+    accumulation at scale."""
+    return ethylene_vb(seed=seed, n_virt_center=30, n_virt_deloc=24, params=True)
+
+
 def small_open_shell(seed: int = 11, params: bool = True, een: bool = True) -> SystemSpec:
     """Small test system: 3 nuclei (Z = 3, 1, 1), 5 electrons (3 up, 2 down, one unpaired),
     s/s/p/d shells per center, one localised core, four active orbitals, three virtuals; four

@@ -50,8 +50,8 @@ class _Desc(ctypes.Structure):
 
 
 EXPORTED = ["vbqmc_create", "vbqmc_destroy", "vbqmc_last_error", "vbqmc_set_system", "vbqmc_inspect_system",
-            "vbqmc_walker_state_size", "vbqmc_eval_walkers", "vbqmc_vmc_steps", "vbqmc_launch_info",
-            "vbqmc_last_launch_count"]
+            "vbqmc_walker_state_size", "vbqmc_eval_walkers", "vbqmc_vmc_steps", "vbqmc_accumulate_lin_matrices",
+            "vbqmc_launch_info", "vbqmc_last_launch_count"]
 
 _LIB = None
 
@@ -77,6 +77,8 @@ def lib():
                                       vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
         L.vbqmc_last_launch_count.argtypes = [vp]
         L.vbqmc_launch_info.argtypes = [vp, ctypes.c_int, ctypes.c_int, _c_int_p]
+        L.vbqmc_accumulate_lin_matrices.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp, vp, vp,
+                                                    vp, vp, vp, vp, vp, vp]
         _LIB = L
     return _LIB
 
@@ -142,6 +144,19 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def deriv_dtype(precision):
+    """Element type of O and dE_L/dp for a precision mode (the mode's bulk type)."""
+    import torch
+    return torch.float32 if precision == MIXED else torch.float64
+
+
+def _check_deriv(precision, *ts):
+    want = deriv_dtype(precision)
+    for t in ts:
+        if t is not None and t.dtype != want:
+            raise VbqmcError("derivative arrays must be %s in this precision mode" % want)
+
+
 def _stream(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -192,6 +207,7 @@ class Context:
                      stream=None):
         """R [W, N, 3] float64 CUDA tensor; outputs preallocated float64 CUDA tensors."""
         W = R.shape[0]
+        _check_deriv(precision, O, dEL)
         _check(lib().vbqmc_eval_walkers(self.h, int(sys_id), int(precision), int(W), _ptr(R), _ptr(logpsi),
                                         _ptr(sign), _ptr(eloc), _ptr(grad), _ptr(O), _ptr(dEL), _ptr(state_out),
                                         _stream(stream)))
@@ -200,6 +216,7 @@ class Context:
                   refresh=1, state=None, state_valid=False, nacc=None, logpsi=None, sign=None, eloc=None, O=None,
                   dEL=None, stream=None):
         W = R.shape[0]
+        _check_deriv(precision, O, dEL)
         _check(lib().vbqmc_vmc_steps(self.h, int(sys_id), int(precision), int(W), _ptr(R), int(nsweeps),
                                      float(step), ctypes.c_uint64(seed), ctypes.c_uint32(step0),
                                      ctypes.c_uint32(system_tag), ctypes.c_uint32(walker_offset), int(refresh),
@@ -207,5 +224,53 @@ class Context:
                                      _ptr(eloc), _ptr(O), _ptr(dEL), _stream(stream)))
 
 
+    def accumulate_lin_matrices(self, precision, O, dEL, eloc, weights=None, stream=None):
+        """Linear-method estimators (E0, gL, gR, S, H) from O, dEL [M, P] (mode's bulk type) and
+        eloc [M] float64 CUDA tensors; returns float64 CUDA tensors."""
+        import torch
+        _check_deriv(precision, O, dEL)
+        M, P = O.shape
+        dev = O.device
+        E0 = torch.empty(1, dtype=torch.float64, device=dev)
+        gL = torch.empty(P, dtype=torch.float64, device=dev)
+        gR = torch.empty(P, dtype=torch.float64, device=dev)
+        S = torch.empty((P, P), dtype=torch.float64, device=dev)
+        H = torch.empty((P, P), dtype=torch.float64, device=dev)
+        _check(lib().vbqmc_accumulate_lin_matrices(self.h, int(precision), int(P), int(M), _ptr(O), _ptr(dEL),
+                                                   _ptr(eloc), _ptr(weights), _ptr(E0), _ptr(gL), _ptr(gR), _ptr(S),
+                                                   _ptr(H), _stream(stream)))
+        return {"E0": E0, "gL": gL, "gR": gR, "S": S, "H": H}
+
+
 def create(device: int = 0) -> Context:
     return Context(device)
+
+
+def lin_solve(E0, gL, gR, H, S, shift=0.0):
+    """Host-side FP64 generalized eigenproblem of Eq. geneigeqM for the parameter update: the
+    lowest real eigenvalue whose eigenvector has a first component >= 1e-3 of its norm, scaled
+    to first component 1.  (Host library routine on a (P+1)^2 matrix, not a GPU step.)"""
+    import scipy.linalg
+    P = len(gL)
+    A = np.zeros((P + 1, P + 1))
+    B = np.zeros((P + 1, P + 1))
+    A[0, 0] = float(E0)
+    A[0, 1:] = 0.5 * np.asarray(gR)
+    A[1:, 0] = 0.5 * np.asarray(gL)
+    A[1:, 1:] = np.asarray(H) + shift * np.eye(P)
+    B[0, 0] = 1.0
+    B[1:, 1:] = np.asarray(S)
+    ev, vec = scipy.linalg.eig(A, B)
+    best = None
+    for k in range(P + 1):
+        lam = ev[k]
+        if not np.isfinite(lam) or abs(lam.imag) > 1e-8 * max(1.0, abs(lam.real)):
+            continue
+        v = vec[:, k].real
+        if abs(v[0]) < 1e-3 * np.linalg.norm(v):
+            continue
+        if best is None or lam.real < best[0]:
+            best = (lam.real, v / v[0])
+    if best is None:
+        raise VbqmcError("no admissible eigenvector")
+    return best[1][1:], best[0]

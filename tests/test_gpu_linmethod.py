@@ -1,0 +1,132 @@
+"""Linear-method estimators on the GPU (Sec. 2.3.1, Eqs. Hi0, H0j, Hij, Sij) against the oracle.
+
+Tolerance: products of float-rounded centred values accumulated in float over chunks of at
+most 16384 samples and summed in double: each entry within 1e-5 of the matrix scale
+(max |entry|) for float inputs and 2e-6 for double inputs."""
+import numpy as np
+import pytest
+
+from paper_2207_14715_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_14715_gb300 import build, vbqmc
+    build.build()
+    ctx = vbqmc.create(0)
+    yield vbqmc, ctx
+    ctx.close()
+
+
+def synthetic(M, P, seed, weights=False):
+    rng = np.random.default_rng(seed)
+    mix = rng.normal(size=(P, P)) / np.sqrt(P)
+    O = rng.normal(size=(M, P)) @ mix + rng.normal(size=P)           # correlated, nonzero means
+    dE = rng.normal(size=(M, P)) * 0.3
+    E = -10.0 + rng.normal(size=M) + 0.5 * O[:, 0]
+    w = rng.uniform(0.2, 1.8, M) if weights else None
+    return O, dE, E, w
+
+
+def run_gpu(vb, precision, O, dE, E, w):
+    mod, ctx = vb
+    dt = mod.deriv_dtype(precision)
+    t = lambda x, d=torch.float64: None if x is None else torch.tensor(x, dtype=d, device="cuda")
+    out = ctx.accumulate_lin_matrices(precision, t(O, dt), t(dE, dt), t(E), t(w))
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def check(got, ref, tol):
+    for k in ("S", "H", "gL", "gR"):
+        scale = max(1.0, np.abs(ref[k]).max())
+        err = np.abs(got[k] - ref[k]).max() / scale
+        assert err < tol, (k, err)
+    assert abs(got["E0"][0] - ref["E0"]) < 1e-12 * max(1.0, abs(ref["E0"]))
+
+
+@pytest.mark.parametrize("M,P,weights", [(1, 1, False), (300, 7, False), (5000, 37, True), (40000, 130, False)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lin_matrices_match_oracle(vb, orc, M, P, weights, precision):
+    O, dE, E, w = synthetic(M, P, M + P, weights)
+    if precision == 1:  # the oracle sees the same float-rounded inputs
+        O, dE = O.astype(np.float32).astype(np.float64), dE.astype(np.float32).astype(np.float64)
+    ref = orc.lin_matrices(O, dE, E, w)
+    got = run_gpu(vb, precision, O, dE, E, w)
+    check(got, ref, 2e-6 if precision == 0 else 1e-5)
+
+
+def test_lin_matrices_full_size_sampled(vb):
+    """2^20 samples x 400 parameters in the benchmark's configuration: sampled entries against
+    direct FP64 sums."""
+    M, P = 1 << 20, 400
+    rng = np.random.default_rng(3)
+    O = (rng.standard_normal((M, P), dtype=np.float32) + rng.standard_normal(P).astype(np.float32))
+    dE = rng.standard_normal((M, P), dtype=np.float32) * np.float32(0.3)
+    E = -10.0 + rng.standard_normal(M) + 0.5 * O[:, 0]
+    got = run_gpu(vb, 1, O, dE, E, None)
+    Od, dEd = O.astype(np.float64), dE.astype(np.float64)
+    mO, mE = Od.mean(axis=0), E.mean()
+    for (i, j) in [(0, 0), (1, 399), (250, 3), (399, 399), (128, 127)]:
+        xi, xj = Od[:, i] - mO[i], Od[:, j] - mO[j]
+        s_ref = np.mean(xi * xj)
+        h_ref = np.mean(xi * (E * xj + dEd[:, j]))
+        assert abs(got["S"][i, j] - s_ref) < 1e-5 * max(1.0, abs(got["S"]).max())
+        assert abs(got["H"][i, j] - h_ref) < 1e-5 * max(1.0, abs(got["H"]).max())
+    assert abs(got["E0"][0] - mE) < 1e-12 * abs(mE)
+
+
+def test_strong_zero_variance_through_gpu(vb, orc):
+    """GPU evaluation + GPU accumulation + host solve recover the exact state of the
+    two-structure 1s system from a small sample (Sec. 2.3.1, strong zero variance), to the
+    precision of the float products of the accumulation (~1e-7 relative)."""
+    mod, ctx = vb
+    for Z, c2 in [(1.0, 0.7), (3.0, -0.4)]:
+        spec = S.two_structure_1s(Z, 0.9, c2)
+        ctx.set_system(0, spec)
+        W = 40
+        R = torch.tensor(np.random.default_rng(3).normal(scale=1.0 / Z, size=(W, 1, 3)), device="cuda")
+        lp, sg, el = (torch.zeros(W, dtype=torch.float64, device="cuda") for _ in range(3))
+        O = torch.zeros((W, 1), dtype=torch.float64, device="cuda")
+        dE = torch.zeros_like(O)
+        ctx.eval_walkers(0, 0, R, lp, sg, el, None, O, dE)
+        m = ctx.accumulate_lin_matrices(0, O, dE, el)
+        m = {k: v.cpu().numpy() for k, v in m.items()}
+        dp, Elin = mod.lin_solve(m["E0"][0], m["gL"], m["gR"], m["H"], m["S"])
+        obar = O.cpu().numpy()[:, 0].mean()
+        assert dp[0] / (1.0 - dp[0] * obar) == pytest.approx(-c2, rel=1e-6, abs=1e-7)
+        assert Elin == pytest.approx(-0.5 * Z * Z, rel=1e-6)
+
+
+def test_linear_method_update_matches_oracle(vb, orc):
+    """Walkers of the small open-shell system: parameter update from the GPU pipeline (FP64
+    form) equals the oracle's (same walkers, oracle derivatives, oracle matrices, same solve)."""
+    mod, ctx = vb
+    spec = S.small_open_shell()
+    ctx.set_system(0, spec)
+    W = 64
+    R0 = S.initial_walkers(spec, W, 12)
+    R = torch.tensor(R0, device="cuda")
+    ctx.vmc_steps(0, 0, R, 20, spec.step, 4)
+    Rn = R.cpu().numpy()
+    P = spec.n_params
+    lp, sg, el = (torch.zeros(W, dtype=torch.float64, device="cuda") for _ in range(3))
+    O = torch.zeros((W, P), dtype=torch.float64, device="cuda")
+    dE = torch.zeros_like(O)
+    ctx.eval_walkers(0, 0, R, lp, sg, el, None, O, dE)
+    m = {k: v.cpu().numpy() for k, v in ctx.accumulate_lin_matrices(0, O, dE, el).items()}
+    ref_ev = orc.evaluate(spec, Rn, derivs=True)
+    ref = orc.lin_matrices(ref_ev["O"], ref_ev["dEL"], ref_ev["eloc"])
+    check(m, ref, 1e-6)
+    shift = 0.5
+    dp, E = mod.lin_solve(m["E0"][0], m["gL"], m["gR"], m["H"], m["S"], shift=shift)
+    dpo, Eo = orc.lin_solve(ref["E0"], ref["gL"], ref["gR"], ref["H"], ref["S"], shift=shift)
+    # the solve amplifies the float-product rounding of the matrices (1e-6 of their scale) by the
+    # conditioning of S (near-redundant parameters): compare against the update's own scale
+    np.testing.assert_allclose(dp, dpo, rtol=0, atol=1e-5 * max(1.0, np.abs(dpo).max()))
+    assert E == pytest.approx(Eo, rel=1e-6)

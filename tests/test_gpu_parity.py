@@ -40,7 +40,7 @@ def gpu_eval(vb, spec, R, precision, derivs=False, grad=True):
     sg = torch.zeros_like(lp)
     el = torch.zeros_like(lp)
     g = torch.zeros_like(Rt) if grad else None
-    O = torch.zeros((W, P), dtype=torch.float64, device=dev) if derivs and P else None
+    O = torch.zeros((W, P), dtype=mod.deriv_dtype(precision), device=dev) if derivs and P else None
     dE = torch.zeros_like(O) if O is not None else None
     ctx.eval_walkers(0, precision, Rt, lp, sg, el, g, O, dE)
     torch.cuda.synchronize()
@@ -48,7 +48,7 @@ def gpu_eval(vb, spec, R, precision, derivs=False, grad=True):
     if grad:
         out["grad"] = g.cpu().numpy()
     if O is not None:
-        out["O"], out["dEL"] = O.cpu().numpy(), dE.cpu().numpy()
+        out["O"], out["dEL"] = O.double().cpu().numpy(), dE.double().cpu().numpy()
     return out
 
 

@@ -97,3 +97,14 @@ def test_invalid_inputs_are_rejected(vb):
     bad.kappa_kl = np.array([[1, 1]], np.int32)
     with pytest.raises(vb.VbqmcError, match="excitation"):
         vb.inspect_system(bad)
+
+
+def test_binding_exposes_the_entry_points(vb):
+    """The Python binding has one method per C entry point (argument marshalling only)."""
+    for name in ("set_system", "eval_walkers", "vmc_steps", "accumulate_lin_matrices", "walker_state_size",
+                 "launch_info", "last_launch_count", "close"):
+        assert callable(getattr(vb.Context, name)), name
+    for name in ("create", "inspect_system", "lin_solve", "deriv_dtype"):
+        assert callable(getattr(vb, name)), name
+    for sym in vb.EXPORTED:
+        assert hasattr(vb.lib(), sym)
