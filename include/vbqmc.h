@@ -178,6 +178,30 @@ int vbqmc_accumulate_lin_matrices(vbqmc_ctx* ctx, int precision, int P, int64_t 
                                   const double* eloc, const double* weights, double* E0, double* gL, double* gR,
                                   double* S, double* H, void* stream);
 
+/* Scratch size of vbqmc_accumulate_lin_matrices_noalloc, bytes per device (64 MiB). */
+#define VBQMC_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* The same estimators as vbqmc_accumulate_lin_matrices, computed by the same kernels, without
+ * any device memory allocation (the paper has no counterpart: this is a library service).
+ * For callers that must not have the library allocate: applications that give the whole
+ * device to their own allocator or a fixed budget, or latency-critical paths where an
+ * allocation's implicit synchronization or failure is unacceptable.  Arguments, layouts and
+ * outputs are those of vbqmc_accumulate_lin_matrices, without a context: the call works on
+ * the calling thread's current device, and 'stream' must belong to it.
+ * Workspace: one fixed device array of VBQMC_NOALLOC_SCRATCH_BYTES per device, created when
+ * the library's module is loaded.  The first call with a device current looks up its address
+ * (set-up work; make that call before any stream capture begins).  Each call clears, on
+ * 'stream', the parts of the array that must start at zero; the array keeps the last call's
+ * contents otherwise.  Calls on one device whose executions overlap (other streams, other
+ * threads) race on the array and give wrong results: order them on one stream.
+ * Errors: VBQMC_ERR_CAPACITY when (P, M) needs more scratch than the fixed size (about
+ * 8 bytes x M x P rounded up to 128, plus chunk partials; a 16384 x 216 call needs 40 MiB);
+ * VBQMC_ERR_ARG for bad precision, P < 1, M < 1 or a NULL required pointer;
+ * VBQMC_ERR_CUDA when a CUDA call or launch fails.  Message in vbqmc_last_error(). */
+int vbqmc_accumulate_lin_matrices_noalloc(int precision, int P, int64_t M, const void* O, const void* dEL,
+                                          const double* eloc, const double* weights, double* E0, double* gL,
+                                          double* gR, double* S, double* H, void* stream);
+
 /* Launch shape of the walker kernels for a loaded system: out[0..3] = walkers (warps) per
  * thread block and shared-memory bytes per walker of the evaluation kernel, then the same two
  * numbers for the sweep kernel, for the given precision mode. */

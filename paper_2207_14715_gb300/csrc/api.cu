@@ -60,6 +60,11 @@ struct BlobBuilder {
 
 }  // namespace
 
+namespace vbq {
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+int set_cuda_error(int cuda_error, const char* what) { return cuda_fail((cudaError_t)cuda_error, what); }
+}  // namespace vbq
+
 struct vbqmc_ctx {
   int device = 0;
   int max_smem = 0;

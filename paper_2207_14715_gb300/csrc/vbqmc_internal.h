@@ -125,4 +125,10 @@ struct SysDev {
   const float* orb_coef_ds;            // like orb_coef, [.][2]
 };
 
+// Records the calling thread's error message (read by vbqmc_last_error) and returns 'code';
+// the CUDA form takes a cudaError_t value and returns VBQMC_ERR_CUDA.  Defined with the
+// other entry points.
+int set_error(int code, const std::string& msg);
+int set_cuda_error(int cuda_error, const char* what);
+
 }  // namespace vbq

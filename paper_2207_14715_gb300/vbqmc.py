@@ -51,7 +51,7 @@ class _Desc(ctypes.Structure):
 
 EXPORTED = ["vbqmc_create", "vbqmc_destroy", "vbqmc_last_error", "vbqmc_set_system", "vbqmc_inspect_system",
             "vbqmc_walker_state_size", "vbqmc_eval_walkers", "vbqmc_vmc_steps", "vbqmc_accumulate_lin_matrices",
-            "vbqmc_launch_info", "vbqmc_last_launch_count"]
+            "vbqmc_launch_info", "vbqmc_last_launch_count", "vbqmc_accumulate_lin_matrices_noalloc"]
 
 _LIB = None
 
@@ -79,6 +79,8 @@ def lib():
         L.vbqmc_launch_info.argtypes = [vp, ctypes.c_int, ctypes.c_int, _c_int_p]
         L.vbqmc_accumulate_lin_matrices.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp, vp, vp,
                                                     vp, vp, vp, vp, vp, vp]
+        L.vbqmc_accumulate_lin_matrices_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp, vp,
+                                                            vp, vp, vp, vp, vp, vp, vp]
         _LIB = L
     return _LIB
 
@@ -240,6 +242,23 @@ class Context:
                                                    _ptr(eloc), _ptr(weights), _ptr(E0), _ptr(gL), _ptr(gR), _ptr(S),
                                                    _ptr(H), _stream(stream)))
         return {"E0": E0, "gL": gL, "gR": gR, "S": S, "H": H}
+
+
+def accumulate_lin_matrices_noalloc(precision, O, dEL, eloc, weights, E0, gL, gR, S, H, stream=None):
+    """vbqmc_accumulate_lin_matrices_noalloc: the linear-method estimators into caller-owned
+    float64 CUDA tensors E0 [1], gL [P], gR [P], S [P, P], H [P, P], with no device allocation
+    by the library or by this wrapper.  Runs on O's device (made current for the call)."""
+    import torch
+    _check_deriv(precision, O, dEL)
+    M, P = O.shape
+    for t, shape in ((E0, (1,)), (gL, (P,)), (gR, (P,)), (S, (P, P)), (H, (P, P))):
+        if t.dtype != torch.float64 or tuple(t.shape) != shape or not t.is_contiguous() or t.device != O.device:
+            raise VbqmcError("outputs must be contiguous float64 tensors on O's device with shapes "
+                             "E0 [1], gL [P], gR [P], S [P, P], H [P, P]")
+    with torch.cuda.device(O.device):
+        _check(lib().vbqmc_accumulate_lin_matrices_noalloc(int(precision), int(P), int(M), _ptr(O), _ptr(dEL),
+                                                           _ptr(eloc), _ptr(weights), _ptr(E0), _ptr(gL), _ptr(gR),
+                                                           _ptr(S), _ptr(H), _stream(stream)))
 
 
 def create(device: int = 0) -> Context:

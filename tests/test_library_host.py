@@ -104,7 +104,7 @@ def test_binding_exposes_the_entry_points(vb):
     for name in ("set_system", "eval_walkers", "vmc_steps", "accumulate_lin_matrices", "walker_state_size",
                  "launch_info", "last_launch_count", "close"):
         assert callable(getattr(vb.Context, name)), name
-    for name in ("create", "inspect_system", "lin_solve", "deriv_dtype"):
+    for name in ("create", "inspect_system", "lin_solve", "deriv_dtype", "accumulate_lin_matrices_noalloc"):
         assert callable(getattr(vb, name)), name
     for sym in vb.EXPORTED:
         assert hasattr(vb.lib(), sym)
