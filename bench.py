@@ -28,6 +28,26 @@ UNIT = "walker-steps/s"
 W_PER_GPU = 16384
 SEED = 20220728 + 1
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per walker of the walker kernels
+# from one ncu capture (8192 walkers of the same workload; traffic scales with walkers), valid
+# only while the kernel sources hash to the recorded value (else the bench reports null).
+WALKER_KERNEL_SOURCES = ["kernels.cu", "kernels.h", "wf_device.cuh", "dsfloat.cuh", "vbqmc_internal.h"]
+PROFILED_TRAFFIC = {
+    "sources_sha256": "12ffb96a168db7931266778f5208ad73ebc0b2780baa5380854084405d36a0b1",
+    "bytes_per_walker": {"eval": (3489024 + 26889728) / 8192, "sweep": (72515072 + 1231360) / 8192},
+}
+
+
+def walker_kernel_traffic(kernel, W):
+    import hashlib
+    h = hashlib.sha256()
+    for f in WALKER_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2207_14715_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != PROFILED_TRAFFIC["sources_sha256"]:
+        return None
+    return PROFILED_TRAFFIC["bytes_per_walker"][kernel] * W
+
 
 def workload_config(W, flush=True):
     return {"workload": "ethylene-shaped JVB VMC: 16 e (8/8), 6 nuclei, M=126 Gaussians, 6 structures / "
@@ -301,7 +321,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
     t_e2e = allmax(time.perf_counter() - t0, ws)
     barrier(ws)
-    lin = lin_method_timing(ctx, vbqmc, dev, args.steps) if not args.no_lin else None
+    lin = lin_method_timing(ctx, vbqmc, dev, args.steps, args.lin_samples) if not args.no_lin else None
     barrier(ws)
     if rank != 0:
         return
@@ -323,7 +343,7 @@ def run_ours(args, ws, rank, local):
         roof = {"bound": "alu", "pipe": "fp64", "achieved": w64 / dur / 1e12, "peak": pk["f64"] / 1e12}
     else:
         roof = {"bound": "alu", "pipe": "fp32", "achieved": w32 / dur / 1e12, "peak": pk["f32"] / 1e12}
-    roof.update({"unit": "TFLOP/s", "frac": roof["achieved"] / roof["peak"], "traffic": None,
+    roof.update({"unit": "TFLOP/s", "frac": roof["achieved"] / roof["peak"], "traffic": walker_kernel_traffic(dom, W),
                  "kernel": "%s_kernel<float>" % dom,
                  "peak_source": "derived from unit counts at the measured median SM clock %.0f MHz" % sm_mhz,
                  "other_pipe_frac": min(frac64, frac32)})
@@ -352,11 +372,12 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def lin_method_timing(ctx, vbqmc, dev, steps):
-    """Linear-method estimators for 2^20 samples x 400 parameters (mixed form, float inputs):
-    time per accumulation with CUDA events, inputs resident in HBM (larger than L2)."""
+def lin_method_timing(ctx, vbqmc, dev, steps, M=1 << 20):
+    """Linear-method estimators for M (default 2^20) samples x 400 parameters (mixed form,
+    float inputs): time per accumulation with CUDA events, inputs resident in HBM (larger than
+    L2)."""
     import torch
-    M, P = 1 << 20, 400
+    P = 400
     g = torch.Generator(device=dev)
     g.manual_seed(SEED)
     O = torch.randn((M, P), generator=g, device=dev, dtype=torch.float32)
@@ -387,6 +408,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lin", action="store_true")
+    ap.add_argument("--lin-samples", type=int, default=1 << 20, help="samples of the linear-method timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
