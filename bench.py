@@ -321,6 +321,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
     t_e2e = allmax(time.perf_counter() - t0, ws)
     barrier(ws)
+    dmc = dmc_timing(ctx, vbqmc, R, el, args.dmc_steps) if args.dmc_steps > 0 else None
     lin = lin_method_timing(ctx, vbqmc, dev, args.steps, args.lin_samples) if not args.no_lin else None
     barrier(ws)
     if rank != 0:
@@ -365,11 +366,35 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": ws * W * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
         "linear_method": lin,
+        "dmc": dmc,
         "gpu_launches": 2 * m["steps"],
         "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
                    "reasons": clocks.get("reasons", [])},
     }
     print(json.dumps(line), flush=True)
+
+
+def dmc_timing(ctx, vbqmc, R, el, steps, tau=0.005):
+    """Fixed-node DMC steps of the mixed form from the equilibrated walkers (population target =
+    walker count, capacity 2x): walker-steps/s over the timed steps, CUDA events around the call
+    (which synchronizes once per step to read the population)."""
+    import torch
+    W = R.shape[0]
+    buf = torch.zeros((2 * W,) + tuple(R.shape[1:]), dtype=torch.float64, device=R.device)
+    buf[:W] = R
+    e_t = float(el.mean().item())
+    Wc, e_t, _ = ctx.dmc_steps(0, vbqmc.MIXED, buf, W, 3, tau, e_t, W, SEED, step0=1 << 20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    W1, _, hist = ctx.dmc_steps(0, vbqmc.MIXED, buf, Wc, steps, tau, e_t, W, SEED, step0=(1 << 20) + 3)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    moved = Wc + int(hist["pop"][:-1].sum())
+    return {"walker_steps_per_s": moved / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps, "tau": tau,
+            "target": W, "population": [int(x) for x in hist["pop"]],
+            "acceptance": hist["accepted"] / max(moved, 1), "launches_per_step": 5}
 
 
 def lin_method_timing(ctx, vbqmc, dev, steps, M=1 << 20):
@@ -409,6 +434,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lin", action="store_true")
     ap.add_argument("--lin-samples", type=int, default=1 << 20, help="samples of the linear-method timing")
+    ap.add_argument("--dmc-steps", type=int, default=5, help="timed DMC steps (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -162,6 +162,36 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
                     double* state, int state_valid, int* nacc, double* logpsi, double* sign, double* eloc,
                     void* O, void* dEL, void* stream);
 
+/* Fixed-node diffusion Monte Carlo steps (Sec. 2.3.2; mixed estimator Eq. E0DMCweights).  The
+ * paper names its step algorithm without giving it; the step here, per walker, is
+ *   R' = R + tau v(R) + sqrt(tau) z  (v = grad ln|Psi|, z standard normal per coordinate);
+ *   rejected if sign Psi(R') != sign Psi(R), else accepted with probability
+ *   min(1, exp(2 (ln|Psi(R')| - ln|Psi(R)|)) G(R <- R') / G(R' <- R)),
+ *   G(R' <- R) = exp(-|R' - R - tau v(R)|^2 / (2 tau));
+ *   weight w = exp(-tau ((E_L(R) + E_L(R_kept)) / 2 - E_T)); copies = min(floor(w + u), 3),
+ *   children in parent order (weights are 1 after branching);
+ *   then E_T = sum(w E_L) / sum(w) - (0.1 / tau) ln(population / target).
+ * Random numbers: Philox4x32-10 keyed by seed, counter (walker index in the current population,
+ * step0 + step, slot, (system_tag << 8) | purpose): slot e < N, purpose 2 -> (u0, u1) giving
+ * z_x = r cos(2 pi u1), z_y = r sin(2 pi u1) with r = sqrt(-2 ln(1 - u0)); purpose 3 -> z_z from
+ * the cosine branch of its pair; slot N, purpose 4 -> (u_acc, u_branch).  Uniforms as in
+ * vbqmc_vmc_steps.  The evaluation at R' computes E_L and grad ln|Psi| in the given precision
+ * mode; acceptance, weights and sums are double in both modes.
+ *   W_io     host, in/out: population (0 <= W <= cap)
+ *   R        [cap][N][3] device, in/out: walkers (the first W rows are the population)
+ *   E_T_io   host, in/out: trial energy
+ *   sum_wE, sum_w [nsteps] host double or NULL: per step, sums of the pre-branching weights
+ *            times E_L and of the weights (the estimator is sum_wE / sum_w)
+ *   pop [nsteps] host int or NULL: population after branching; e_trial [nsteps] host or NULL:
+ *            E_T after its update;  accepted: host or NULL, accepted moves over the call.
+ * The call synchronizes 'stream' once per step (to read the population and the sums) and keeps
+ * a device workspace for 'cap' walkers in the context (grown on demand).  A population of 0
+ * ends the call early.  Returns VBQMC_ERR_CAPACITY if branching would exceed 'cap': the moves of
+ * that step are applied, its branching is not, and W_io holds the population before it. */
+int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int cap, double* R, int nsteps, double tau,
+                    double* E_T_io, int target, uint64_t seed, uint32_t step0, uint32_t system_tag, double* sum_wE,
+                    double* sum_w, int* pop, double* e_trial, int64_t* accepted, void* stream);
+
 /* Linear-method estimators from M samples (Sec. 2.3.1, Eqs. Hi0, H0j, Hij, Sij, feeding the
  * generalized eigenproblem Eq. geneigeqM).  With weights w (NULL: all 1), averages
  * <x> = sum w x / sum w and Ot = O - <O>, the outputs are

@@ -17,7 +17,7 @@ LIB = os.path.join(LIBDIR, "libvbqmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
-CU_SOURCES = ["kernels.cu", "linmethod.cu", "linmethod_noalloc.cu", "api.cu"]
+CU_SOURCES = ["kernels.cu", "dmc.cu", "linmethod.cu", "linmethod_noalloc.cu", "api.cu"]
 CPP_SOURCES = ["system_host.cpp"]
 
 

@@ -2,8 +2,12 @@
 // the walker entry points.
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
+#include <cmath>
+
+#include "dmc.h"
 #include "kernels.h"
 #include "linmethod.h"
 #include "vbqmc_internal.h"
@@ -72,6 +76,8 @@ struct vbqmc_ctx {
   LoadedSystem sys[VBQMC_MAX_SYSTEMS];
   void* work = nullptr;      // grow-only device workspace of the linear-method accumulation
   size_t work_bytes = 0;
+  void* dmc_work = nullptr;  // grow-only device workspace of the DMC steps
+  size_t dmc_bytes = 0;
 };
 
 static void free_system(LoadedSystem& s) {
@@ -108,6 +114,7 @@ void vbqmc_destroy(vbqmc_ctx* ctx) {
   cudaDeviceSynchronize();
   for (auto& s : ctx->sys) free_system(s);
   if (ctx->work) cudaFree(ctx->work);
+  if (ctx->dmc_work) cudaFree(ctx->dmc_work);
   delete ctx;
 }
 
@@ -352,6 +359,131 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
   }
   ctx->last_launches = launches;
   return VBQMC_OK;
+}
+
+int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int cap, double* R, int nsteps, double tau,
+                    double* E_T_io, int target, uint64_t seed, uint32_t step0, uint32_t system_tag, double* sum_wE,
+                    double* sum_w, int* pop, double* e_trial, int64_t* accepted, void* stream) {
+  if (!W_io || !E_T_io) return fail(VBQMC_ERR_ARG, "null W_io or E_T_io");
+  int rc = check_call(ctx, sys_id, precision, *W_io);
+  if (rc) return rc;
+  ctx->last_launches = 0;
+  int W = *W_io;
+  if (cap < 1 || W > cap) return fail(VBQMC_ERR_ARG, "need 1 <= cap and W <= cap");
+  if (nsteps < 0 || !(tau > 0.0) || target < 1) return fail(VBQMC_ERR_ARG, "bad step count, tau or target");
+  if (system_tag > 0xffffffu) return fail(VBQMC_ERR_ARG, "system_tag must fit in 24 bits");
+  if (accepted) *accepted = 0;
+  if (W == 0 || nsteps == 0) return VBQMC_OK;
+  if (!R) return fail(VBQMC_ERR_ARG, "null R");
+  LoadedSystem& s = ctx->sys[sys_id];
+  if (s.lay_rc_eval[precision]) return fail(s.lay_rc_eval[precision], "per-walker state exceeds shared memory");
+  DeviceGuard g(ctx->device);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int N = s.dev.N, n3 = 3 * N;
+  // workspace: Rp, grad A, grad1, R B, grad B ([cap][3N] each), 11 per-walker doubles, 3 ints, totals
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t vec = al(sizeof(double) * (size_t)cap * n3), sca = al(sizeof(double) * (size_t)cap),
+               ints = al(sizeof(int) * (size_t)cap);
+  const size_t need = 5 * vec + 11 * sca + 3 * ints + al(sizeof(vbq::DmcTotals));
+  if (need > ctx->dmc_bytes) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (ctx->dmc_work) cudaFree(ctx->dmc_work);
+    ctx->dmc_work = nullptr;
+    ctx->dmc_bytes = 0;
+    e = cudaMalloc(&ctx->dmc_work, need);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(DMC workspace)");
+    ctx->dmc_bytes = need;
+  }
+  unsigned char* p = static_cast<unsigned char*>(ctx->dmc_work);
+  auto take = [&](size_t b) {
+    unsigned char* r = p;
+    p += b;
+    return r;
+  };
+  struct Set {
+    double *R, *lp, *sg, *el, *grad;
+  };
+  double* Rp = reinterpret_cast<double*>(take(vec));
+  double* grad1 = reinterpret_cast<double*>(take(vec));
+  Set cur, nxt;
+  cur.R = R;
+  cur.grad = reinterpret_cast<double*>(take(vec));
+  nxt.R = reinterpret_cast<double*>(take(vec));
+  nxt.grad = reinterpret_cast<double*>(take(vec));
+  cur.lp = reinterpret_cast<double*>(take(sca));
+  cur.sg = reinterpret_cast<double*>(take(sca));
+  cur.el = reinterpret_cast<double*>(take(sca));
+  nxt.lp = reinterpret_cast<double*>(take(sca));
+  nxt.sg = reinterpret_cast<double*>(take(sca));
+  nxt.el = reinterpret_cast<double*>(take(sca));
+  double* lp1 = reinterpret_cast<double*>(take(sca));
+  double* sg1 = reinterpret_cast<double*>(take(sca));
+  double* el1 = reinterpret_cast<double*>(take(sca));
+  double* wt = reinterpret_cast<double*>(take(sca));
+  double* wE = reinterpret_cast<double*>(take(sca));
+  int* copies = reinterpret_cast<int*>(take(ints));
+  int* offsets = reinterpret_cast<int*>(take(ints));
+  int* acc = reinterpret_cast<int*>(take(ints));
+  vbq::DmcTotals* tot = reinterpret_cast<vbq::DmcTotals*>(take(al(sizeof(vbq::DmcTotals))));
+  int launches = 0;
+  double E_T = *E_T_io;
+  int64_t nacc = 0;
+  // the walkers' values at R, carried from step to step
+  cudaError_t e = vbq::launch_eval(precision, s.dev, s.lay_eval[precision], W, cur.R, cur.lp, cur.sg, cur.el, cur.grad,
+                                   nullptr, nullptr, nullptr, st);
+  if (e != cudaSuccess) return cuda_fail(e, "eval kernel launch");
+  ++launches;
+  int rcode = VBQMC_OK;
+  for (int k = 0; k < nsteps; ++k) {
+    const uint32_t stp = step0 + (uint32_t)k;
+    e = vbq::launch_dmc_propose(W, N, cur.R, cur.grad, tau, seed, stp, system_tag, Rp, st);
+    if (e == cudaSuccess)
+      e = vbq::launch_eval(precision, s.dev, s.lay_eval[precision], W, Rp, lp1, sg1, el1, grad1, nullptr, nullptr,
+                           nullptr, st);
+    if (e == cudaSuccess)
+      e = vbq::launch_dmc_accept(W, N, cur.R, cur.lp, cur.sg, cur.el, cur.grad, Rp, lp1, sg1, el1, grad1, tau, E_T,
+                                 seed, stp, system_tag, wt, wE, copies, acc, st);
+    if (e == cudaSuccess) e = vbq::launch_dmc_scan(W, copies, wt, wE, acc, offsets, tot, st);
+    if (e == cudaSuccess)
+      e = vbq::launch_dmc_branch(W, N, cap, copies, offsets, tot, cur.R, cur.lp, cur.sg, cur.el, cur.grad, nxt.R,
+                                 nxt.lp, nxt.sg, nxt.el, nxt.grad, st);
+    vbq::DmcTotals h{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, tot, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      rcode = cuda_fail(e, "DMC step");
+      break;
+    }
+    launches += 5;
+    nacc += h.accepted;
+    if (h.total > cap) {
+      rcode = fail(VBQMC_ERR_CAPACITY, "DMC population " + std::to_string(h.total) + " exceeds capacity " +
+                                           std::to_string(cap) + " at step " + std::to_string(k) +
+                                           " (moves of that step applied, branching not done)");
+      break;
+    }
+    std::swap(cur, nxt);
+    W = (int)h.total;
+    const double Emean = h.sum_w > 0.0 ? h.sum_wE / h.sum_w : E_T;
+    if (W > 0) E_T = Emean - (0.1 / tau) * std::log((double)W / (double)target);
+    if (sum_wE) sum_wE[k] = h.sum_wE;
+    if (sum_w) sum_w[k] = h.sum_w;
+    if (pop) pop[k] = W;
+    if (e_trial) e_trial[k] = E_T;
+    if (W == 0) break;
+  }
+  // the population lives in the caller's R at return
+  if (cur.R != R && W > 0) {
+    e = cudaMemcpyAsync(R, cur.R, sizeof(double) * (size_t)W * n3, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess && rcode == VBQMC_OK) rcode = cuda_fail(e, "DMC population copy");
+  }
+  *W_io = W;
+  *E_T_io = E_T;
+  if (accepted) *accepted = nacc;
+  ctx->last_launches = launches;
+  return rcode;
 }
 
 int vbqmc_accumulate_lin_matrices(vbqmc_ctx* ctx, int precision, int P, int64_t M, const void* O, const void* dEL,

@@ -1,0 +1,237 @@
+// Fixed-node diffusion Monte Carlo step (arXiv:2207.14715, Sec. 2.3.2, Eq. E0DMCweights).
+//
+// The paper names the algorithm it uses but does not spell out its step, so the step here is
+// a plain all-electron drift-diffusion move with Metropolis acceptance:
+//   R' = R + tau v(R) + sqrt(tau) z,   v = grad ln|Psi|,   z ~ N(0, 1) per coordinate;
+//   rejected when sign Psi(R') != sign Psi(R) (fixed node), else accepted with probability
+//   min(1, Psi(R')^2 G(R <- R') / (Psi(R)^2 G(R' <- R))), G(R' <- R) = exp(-|R' - R - tau v(R)|^2 / 2 tau);
+//   weight w = exp(-tau [ (E_L(R) + E_L(R_new)) / 2 - E_T ]) with R_new the position kept;
+//   copies = min(floor(w + u), 3), children stored in parent order (exclusive prefix sum);
+//   E_T <- <E_L>_w - (0.1 / tau) ln(population / target) after branching.
+// Random numbers: Philox4x32-10 with counter (walker index in the current population, step,
+// slot, (system << 8) | purpose): slot e < N, purposes 2 and 3 -> Box-Muller normals of
+// electron e (purpose 2: z_x, z_y from the cosine and sine branches; purpose 3: z_z from the
+// cosine branch); slot N, purpose 4 -> (u_acc, u_branch).
+//
+// Kernels per step: dmc_propose (thread per electron), the evaluation kernel at R' with the
+// gradient, dmc_accept (warp per walker), dmc_scan (one block: prefix sum of the copies and
+// the weight sums in a fixed order, so results do not depend on scheduling) and dmc_branch
+// (warp per parent).
+#include "dmc.h"
+#include "wf_device.cuh"
+
+namespace vbq {
+
+namespace {
+
+__global__ void dmc_propose_kernel(int W, int N, const double* __restrict__ R, const double* __restrict__ grad,
+                                   double tau, double sqtau, uint64_t seed, uint32_t step, uint32_t tag,
+                                   double* __restrict__ Rp) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)W * N) return;
+  const int w = (int)(t / N), e = (int)(t % N);
+  double ua0, ua1, ub0, ub1;
+  uniforms2(seed, (uint32_t)w, step, (uint32_t)e, tag, 2, ua0, ua1);
+  uniforms2(seed, (uint32_t)w, step, (uint32_t)e, tag, 3, ub0, ub1);
+  const double ra = sqrt(-2.0 * log(1.0 - ua0));
+  const double rb = sqrt(-2.0 * log(1.0 - ub0));
+  double sa, ca;
+  sincospi(2.0 * ua1, &sa, &ca);
+  const double z[3] = {ra * ca, ra * sa, rb * cospi(2.0 * ub1)};
+  const size_t o = (size_t)t * 3;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) Rp[o + d] = R[o + d] + tau * grad[o + d] + sqtau * z[d];
+}
+
+// Acceptance, weight and copy count per walker; the accepted move is written into the carried
+// walker (R, ln|Psi|, sign, E_L, grad) in place.
+__global__ void dmc_accept_kernel(int W, int N, double* __restrict__ R, double* __restrict__ lp,
+                                  double* __restrict__ sg, double* __restrict__ el, double* __restrict__ grad,
+                                  const double* __restrict__ Rp, const double* __restrict__ lp1,
+                                  const double* __restrict__ sg1, const double* __restrict__ el1,
+                                  const double* __restrict__ grad1, double tau, double E_T, uint64_t seed,
+                                  uint32_t step, uint32_t tag, double* __restrict__ wt, double* __restrict__ wE,
+                                  int* __restrict__ copies, int* __restrict__ acc) {
+  const int w = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = lane_id();
+  if (w >= W) return;
+  const int n3 = 3 * N;
+  const size_t base = (size_t)w * n3;
+  double f = 0.0, b = 0.0;
+  for (int q = lane; q < n3; q += 32) {
+    const double r = R[base + q], p = Rp[base + q];
+    const double fq = p - r - tau * grad[base + q];
+    const double bq = r - p - tau * grad1[base + q];
+    f = fma(fq, fq, f);
+    b = fma(bq, bq, b);
+  }
+  f = warp_sum(f);
+  b = warp_sum(b);
+  int accept = 0;
+  if (lane == 0) {
+    double uacc, ubr;
+    uniforms2(seed, (uint32_t)w, step, (uint32_t)N, tag, 4, uacc, ubr);
+    const double s0 = sg[w], s1 = sg1[w];
+    if (s1 == s0 && s1 != 0.0) {
+      const double lnr = 2.0 * (lp1[w] - lp[w]) - b / (2.0 * tau) + f / (2.0 * tau);
+      accept = uacc < exp(lnr);
+    }
+    const double e0 = el[w];
+    const double en = accept ? el1[w] : e0;
+    const double ww = exp(-tau * (0.5 * (e0 + en) - E_T));
+    const double x = ww + ubr;
+    const int c = (x >= 3.0) ? 3 : (x >= 0.0 ? (int)floor(x) : 0);  // NaN weights die
+    wt[w] = ww;
+    wE[w] = ww * en;
+    copies[w] = c;
+    acc[w] = accept;
+    if (accept) {
+      lp[w] = lp1[w];
+      sg[w] = s1;
+      el[w] = en;
+    }
+  }
+  accept = __shfl_sync(kFull, accept, 0);
+  if (accept)
+    for (int q = lane; q < n3; q += 32) {
+      R[base + q] = Rp[base + q];
+      grad[base + q] = grad1[base + q];
+    }
+}
+
+constexpr int kScanThreads = 1024;
+
+// One block: exclusive prefix sum of the copies (children offsets), population after
+// branching, and the weight sums, each thread summing a fixed stride of walkers, then a fixed
+// reduction tree.
+__global__ void __launch_bounds__(kScanThreads) dmc_scan_kernel(int W, const int* __restrict__ copies,
+                                                                const double* __restrict__ wt,
+                                                                const double* __restrict__ wE,
+                                                                const int* __restrict__ acc,
+                                                                int* __restrict__ offsets, DmcTotals* out) {
+  __shared__ int wsum[32];
+  __shared__ double rs[2][32];
+  __shared__ int ra[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  long long running = 0;
+  double sw = 0.0, swe = 0.0;
+  int na = 0;
+  for (int base = 0; base < W; base += kScanThreads) {
+    const int i = base + tid;
+    const int c = i < W ? copies[i] : 0;
+    if (i < W) {
+      sw += wt[i];
+      swe += wE[i];
+      na += acc[i];
+    }
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int v = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += u;
+      }
+      wsum[lane] = v;  // inclusive over warps
+    }
+    __syncthreads();
+    const int warp_off = wid ? wsum[wid - 1] : 0;
+    if (i < W) offsets[i] = (int)(running + warp_off + incl - c);
+    running += wsum[31];
+    __syncthreads();
+  }
+  sw = warp_sum(sw);
+  swe = warp_sum(swe);
+  na = warp_sum(na);
+  if (lane == 0) {
+    rs[0][wid] = sw;
+    rs[1][wid] = swe;
+    ra[wid] = na;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    double a = rs[0][lane], e = rs[1][lane];
+    int n = ra[lane];
+    a = warp_sum(a);
+    e = warp_sum(e);
+    n = warp_sum(n);
+    if (lane == 0) {
+      out->total = running;
+      out->sum_w = a;
+      out->sum_wE = e;
+      out->accepted = n;
+    }
+  }
+}
+
+// Children of each parent, in parent order, into the second buffer set (skipped when the new
+// population would exceed the capacity; the host reports that).
+__global__ void dmc_branch_kernel(int W, int N, int cap, const int* __restrict__ copies,
+                                  const int* __restrict__ offsets, const DmcTotals* __restrict__ tot,
+                                  const double* __restrict__ R, const double* __restrict__ lp,
+                                  const double* __restrict__ sg, const double* __restrict__ el,
+                                  const double* __restrict__ grad, double* __restrict__ Rb, double* __restrict__ lpb,
+                                  double* __restrict__ sgb, double* __restrict__ elb, double* __restrict__ gradb) {
+  const int w = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = lane_id();
+  if (w >= W || tot->total > cap) return;
+  const int c = copies[w], o = offsets[w], n3 = 3 * N;
+  for (int k = 0; k < c; ++k) {
+    const size_t src = (size_t)w * n3, dst = (size_t)(o + k) * n3;
+    for (int q = lane; q < n3; q += 32) {
+      Rb[dst + q] = R[src + q];
+      gradb[dst + q] = grad[src + q];
+    }
+    if (lane == 0) {
+      lpb[o + k] = lp[w];
+      sgb[o + k] = sg[w];
+      elb[o + k] = el[w];
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_dmc_propose(int W, int N, const double* R, const double* grad, double tau, uint64_t seed,
+                               uint32_t step, uint32_t tag, double* Rp, cudaStream_t st) {
+  const long long n = (long long)W * N;
+  dmc_propose_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, N, R, grad, tau, sqrt(tau), seed, step, tag,
+                                                                    Rp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dmc_accept(int W, int N, double* R, double* lp, double* sg, double* el, double* grad,
+                              const double* Rp, const double* lp1, const double* sg1, const double* el1,
+                              const double* grad1, double tau, double E_T, uint64_t seed, uint32_t step, uint32_t tag,
+                              double* wt, double* wE, int* copies, int* acc, cudaStream_t st) {
+  const long long threads = (long long)W * 32;
+  dmc_accept_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(W, N, R, lp, sg, el, grad, Rp, lp1, sg1, el1,
+                                                                        grad1, tau, E_T, seed, step, tag, wt, wE,
+                                                                        copies, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dmc_scan(int W, const int* copies, const double* wt, const double* wE, const int* acc,
+                            int* offsets, DmcTotals* out, cudaStream_t st) {
+  dmc_scan_kernel<<<1, kScanThreads, 0, st>>>(W, copies, wt, wE, acc, offsets, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dmc_branch(int W, int N, int cap, const int* copies, const int* offsets, const DmcTotals* tot,
+                              const double* R, const double* lp, const double* sg, const double* el,
+                              const double* grad, double* Rb, double* lpb, double* sgb, double* elb, double* gradb,
+                              cudaStream_t st) {
+  const long long threads = (long long)W * 32;
+  dmc_branch_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(W, N, cap, copies, offsets, tot, R, lp, sg,
+                                                                        el, grad, Rb, lpb, sgb, elb, gradb);
+  return cudaGetLastError();
+}
+
+}  // namespace vbq

@@ -51,7 +51,8 @@ class _Desc(ctypes.Structure):
 
 EXPORTED = ["vbqmc_create", "vbqmc_destroy", "vbqmc_last_error", "vbqmc_set_system", "vbqmc_inspect_system",
             "vbqmc_walker_state_size", "vbqmc_eval_walkers", "vbqmc_vmc_steps", "vbqmc_accumulate_lin_matrices",
-            "vbqmc_launch_info", "vbqmc_last_launch_count", "vbqmc_accumulate_lin_matrices_noalloc"]
+            "vbqmc_launch_info", "vbqmc_last_launch_count", "vbqmc_accumulate_lin_matrices_noalloc",
+            "vbqmc_dmc_steps"]
 
 _LIB = None
 
@@ -79,6 +80,10 @@ def lib():
         L.vbqmc_launch_info.argtypes = [vp, ctypes.c_int, ctypes.c_int, _c_int_p]
         L.vbqmc_accumulate_lin_matrices.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp, vp, vp,
                                                     vp, vp, vp, vp, vp, vp]
+        L.vbqmc_dmc_steps.argtypes = [vp, ctypes.c_int, ctypes.c_int, _c_int_p, ctypes.c_int, vp, ctypes.c_int,
+                                      ctypes.c_double, _c_dbl_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                      ctypes.c_uint32, _c_dbl_p, _c_dbl_p, _c_int_p, _c_dbl_p,
+                                      ctypes.POINTER(ctypes.c_int64), vp]
         L.vbqmc_accumulate_lin_matrices_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp, vp,
                                                             vp, vp, vp, vp, vp, vp, vp]
         _LIB = L
@@ -138,6 +143,14 @@ def inspect_system(spec: SystemSpec, max_terms: int = 4096):
     keys = ["N", "P", "M", "Norb", "nterm", "U_up", "U_dn", "nsterm", "n_ev", "n_kappa_entries", "n_up", "n_dn"]
     d = dict(zip(keys, (int(x) for x in info)))
     return d, terms[:d["nsterm"]], B
+
+
+def _dp(a):
+    return a.ctypes.data_as(_c_dbl_p)
+
+
+def _ip(a):
+    return a.ctypes.data_as(_c_int_p)
 
 
 def _ptr(t):
@@ -225,6 +238,28 @@ class Context:
                                      _ptr(state), int(bool(state_valid)), _ptr(nacc), _ptr(logpsi), _ptr(sign),
                                      _ptr(eloc), _ptr(O), _ptr(dEL), _stream(stream)))
 
+
+    def dmc_steps(self, sys_id, precision, R, W, nsteps, tau, E_T, target, seed, step0=0, system_tag=0,
+                  stream=None):
+        """vbqmc_dmc_steps on the population R[:W] of a float64 CUDA tensor R [cap, N, 3] (updated
+        in place).  Returns (W, E_T, history) with history the per-step host arrays sum_wE,
+        sum_w, pop, e_trial (truncated to the steps run) and the accepted-move count."""
+        cap = R.shape[0]
+        W_c = ctypes.c_int(int(W))
+        et = ctypes.c_double(float(E_T))
+        swe = np.zeros(max(nsteps, 1))
+        sw = np.zeros(max(nsteps, 1))
+        pop = np.full(max(nsteps, 1), -1, np.int32)
+        etr = np.zeros(max(nsteps, 1))
+        nacc = ctypes.c_int64(0)
+        _check(lib().vbqmc_dmc_steps(self.h, int(sys_id), int(precision), ctypes.byref(W_c), int(cap), _ptr(R),
+                                     int(nsteps), float(tau), ctypes.byref(et), int(target), int(seed) & (2**64 - 1),
+                                     int(step0) & 0xffffffff, int(system_tag), _dp(swe), _dp(sw), _ip(pop), _dp(etr),
+                                     ctypes.byref(nacc), _stream(stream)))
+        ran = int((pop >= 0).sum()) if nsteps > 0 else 0
+        hist = {"sum_wE": swe[:ran], "sum_w": sw[:ran], "pop": pop[:ran], "e_trial": etr[:ran],
+                "accepted": int(nacc.value)}
+        return W_c.value, et.value, hist
 
     def accumulate_lin_matrices(self, precision, O, dEL, eloc, weights=None, stream=None):
         """Linear-method estimators (E0, gL, gR, S, H) from O, dEL [M, P] (mode's bulk type) and
