@@ -31,10 +31,11 @@ SEED = 20220728 + 1
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per walker of the walker kernels
 # from one ncu capture (8192 walkers of the same workload; traffic scales with walkers), valid
 # only while the kernel sources hash to the recorded value (else the bench reports null).
-WALKER_KERNEL_SOURCES = ["kernels.cu", "kernels.h", "wf_device.cuh", "dsfloat.cuh", "vbqmc_internal.h"]
+WALKER_KERNEL_SOURCES = ["kernels.cu", "eval_jastrow.cu", "eval_orbitals.cu", "eval_det.cu", "walker_common.cuh",
+                         "kernels.h", "wf_device.cuh", "dsfloat.cuh", "vbqmc_internal.h"]
 PROFILED_TRAFFIC = {
-    "sources_sha256": "12ffb96a168db7931266778f5208ad73ebc0b2780baa5380854084405d36a0b1",
-    "bytes_per_walker": {"eval": (3489024 + 26889728) / 8192, "sweep": (72515072 + 1231360) / 8192},
+    "sources_sha256": None,
+    "bytes_per_walker": {},
 }
 
 
@@ -44,7 +45,7 @@ def walker_kernel_traffic(kernel, W):
     for f in WALKER_KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2207_14715_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != PROFILED_TRAFFIC["sources_sha256"]:
+    if h.hexdigest() != PROFILED_TRAFFIC["sources_sha256"] or kernel not in PROFILED_TRAFFIC["bytes_per_walker"]:
         return None
     return PROFILED_TRAFFIC["bytes_per_walker"][kernel] * W
 
@@ -94,12 +95,14 @@ def work_model(spec, info):
     ev_jas = npair * (2 * 30) + N * Nn * 30 + 2 * npair * Nn * een_terms * 12
     ev_jderiv = npair * Nn * een_terms * 45 + (npair + N * Nn) * 5 * 10
     ev_kappa = U * 2 * 2 * n * n * len(ev_orbs) + info["n_kappa_entries"] * 2 * n
-    ev64_fp64 = ev_basis + ev_contr_val_det + ev_contr_rest + ev_lu + ev_jas + ev_jderiv + ev_kappa
-    ev64_mixed = N * basis_val + ev_contr_val_det + ev_lu
-    ev32_mixed = ev_basis + ev_contr_rest + ev_jas + ev_jderiv + ev_kappa
+    ev_orb = ev_basis + ev_contr_val_det + ev_contr_rest
+    # per kernel and form: algorithmic flops per walker on the pipe each part runs on
     return {
         "sweep": {"fp64": {"f64": sw64 + sw32, "f32": 0.0}, "mixed": {"f64": sw64, "f32": sw32}},
-        "eval": {"fp64": {"f64": ev64_fp64, "f32": 0.0}, "mixed": {"f64": ev64_mixed, "f32": ev32_mixed}},
+        "jastrow": {"fp64": {"f64": ev_jas, "f32": 0.0}, "mixed": {"f64": 0.0, "f32": ev_jas}},
+        "orbitals": {"fp64": {"f64": ev_orb, "f32": 0.0}, "mixed": {"f64": 0.0, "f32": ev_orb}},
+        "det": {"fp64": {"f64": ev_lu + ev_kappa, "f32": 0.0}, "mixed": {"f64": ev_lu, "f32": ev_kappa}},
+        "jastrow_deriv": {"fp64": {"f64": ev_jderiv, "f32": 0.0}, "mixed": {"f64": 0.0, "f32": ev_jderiv}},
     }
 
 
@@ -290,18 +293,29 @@ def run_ours(args, ws, rank, local):
         sampler = ClockSampler(local) if (rank == 0 and name == "mixed") else None
         if sampler:
             sampler.start()
+        # events around each evaluation kernel (read back after every step, outside the
+        # device-timed intervals)
+        ctx.set_kernel_timing(True)
+        ktimes = {key: 0.0 for key in ctx.EVAL_KERNELS}
         t_wall = time.perf_counter()
         for k in range(steps):
             flush.zero_()
             step(prec, evs[k])
+            for key, v in ctx.kernel_times().items():
+                ktimes[key] += v
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+        ctx.set_kernel_timing(False)
+        launches = 1 + ctx.last_launch_count()
         barrier(ws)
         clocks = sampler.stop() if sampler else None
         sweep_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
         eval_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
         tot_ms = allmax(sweep_ms + eval_ms, ws)
+        kernel_ms = {"sweep": sweep_ms / steps}
+        kernel_ms.update({key: v / steps for key, v in ktimes.items()})
         results[name] = {"steps": steps, "ms": tot_ms, "sweep_ms": sweep_ms / steps, "eval_ms": eval_ms / steps,
+                         "kernel_ms": kernel_ms, "launches_per_step": launches,
                          "clocks": clocks, "wall_s": t_wall,
                          "acc": float(nacc.double().mean().item()) / (spec.N * steps),
                          "E_mean": float(el.mean().item())}
@@ -335,8 +349,9 @@ def run_ours(args, ws, rank, local):
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     pk = peaks(sm_mhz)
     # dominant kernel of the mixed step
-    dom = "eval" if m["eval_ms"] >= m["sweep_ms"] else "sweep"
-    dur = (m["eval_ms"] if dom == "eval" else m["sweep_ms"]) * 1e-3
+    km = m["kernel_ms"]
+    dom = max(km, key=km.get)
+    dur = km[dom] * 1e-3
     w64 = model[dom]["mixed"]["f64"] * W
     w32 = model[dom]["mixed"]["f32"] * W
     frac64, frac32 = w64 / dur / pk["f64"], w32 / dur / pk["f32"]
@@ -358,8 +373,9 @@ def run_ours(args, ws, rank, local):
         "data": "synthetic (seeded ethylene-shaped system, random-init parameters)",
         "config": workload_config(W),
         "fp64_form": {"value": value64, "unit": UNIT, "ms_per_step": f64["ms"] / f64["steps"],
-                      "steps": f64["steps"], "sweep_ms": f64["sweep_ms"], "eval_ms": f64["eval_ms"]},
-        "kernel_ms": {"sweep": m["sweep_ms"], "eval": m["eval_ms"]},
+                      "steps": f64["steps"], "sweep_ms": f64["sweep_ms"], "eval_ms": f64["eval_ms"],
+                      "kernel_ms": {k: round(v, 4) for k, v in f64["kernel_ms"].items()}},
+        "kernel_ms": {k: round(v, 4) for k, v in km.items()},
         "acceptance": m["acc"], "E_L_mean": m["E_mean"],
         "roofline": roof,
         "cpu_baseline": cb,
@@ -367,7 +383,7 @@ def run_ours(args, ws, rank, local):
                 "d2h_bytes_per_step": bo},
         "linear_method": lin,
         "dmc": dmc,
-        "gpu_launches": 2 * m["steps"],
+        "gpu_launches": m["launches_per_step"] * m["steps"],
         "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
                    "reasons": clocks.get("reasons", [])},
     }
@@ -394,7 +410,8 @@ def dmc_timing(ctx, vbqmc, R, el, steps, tau=0.005):
     moved = Wc + int(hist["pop"][:-1].sum())
     return {"walker_steps_per_s": moved / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps, "tau": tau,
             "target": W, "population": [int(x) for x in hist["pop"]],
-            "acceptance": hist["accepted"] / max(moved, 1), "launches_per_step": 5}
+            "acceptance": hist["accepted"] / max(moved, 1),
+            "launches_per_step": (ctx.last_launch_count() - 3) / steps}
 
 
 def lin_method_timing(ctx, vbqmc, dev, steps, M=1 << 20):

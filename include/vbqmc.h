@@ -90,7 +90,9 @@ typedef struct vbqmc_system_desc {
 } vbqmc_system_desc;
 
 /* Creates a context on CUDA device 'device' (the calling thread's current device is
- * restored on return).  *out receives the handle; release with vbqmc_destroy. */
+ * restored on return).  *out receives the handle; release with vbqmc_destroy.  A context
+ * owns device workspaces that its calls share (grown on demand): calls on one context must
+ * not overlap in time (use one stream per context, or order the streams). */
 int vbqmc_create(vbqmc_ctx** out, int device);
 
 /* Releases every device allocation of the context.  Waits for the device. */
@@ -232,9 +234,21 @@ int vbqmc_accumulate_lin_matrices_noalloc(int precision, int P, int64_t M, const
                                           const double* eloc, const double* weights, double* E0, double* gL,
                                           double* gR, double* S, double* H, void* stream);
 
+/* Per-kernel timing of the evaluation (diagnostics; the paper has no counterpart).  With
+ * timing on, every evaluation (vbqmc_eval_walkers, and the evaluation at the end of
+ * vbqmc_vmc_steps) records CUDA events on its stream around each of its kernels; the
+ * evaluation runs as four kernels in this order: Jastrow factor, orbitals, determinants
+ * (with E_L, structure and excitation derivatives), Jastrow-parameter derivatives (skipped
+ * when no derivatives are asked for: time 0). */
+int vbqmc_set_kernel_timing(vbqmc_ctx* ctx, int on);
+/* Durations in ms of the four evaluation kernels of the last timed evaluation, in the order
+ * above: ms[0..min(max, 4) - 1]; *n = 4.  Waits for that evaluation to finish.  Error if no
+ * timed evaluation has been recorded since timing was switched on. */
+int vbqmc_kernel_times(vbqmc_ctx* ctx, double* ms, int max, int* n);
+
 /* Launch shape of the walker kernels for a loaded system: out[0..3] = walkers (warps) per
- * thread block and shared-memory bytes per walker of the evaluation kernel, then the same two
- * numbers for the sweep kernel, for the given precision mode. */
+ * thread block and shared-memory bytes per walker of the evaluation's determinant kernel, then
+ * the same two numbers for the sweep kernel, for the given precision mode. */
 int vbqmc_launch_info(vbqmc_ctx* ctx, int sys_id, int precision, int* out);
 
 /* Number of kernel launches enqueued by the last successful call on this context. */

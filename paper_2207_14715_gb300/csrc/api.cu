@@ -78,6 +78,11 @@ struct vbqmc_ctx {
   size_t work_bytes = 0;
   void* dmc_work = nullptr;  // grow-only device workspace of the DMC steps
   size_t dmc_bytes = 0;
+  void* eval_work = nullptr;  // grow-only device workspace of the evaluation kernels
+  size_t eval_bytes = 0;
+  int timing = 0;                               // record events around the evaluation kernels
+  cudaEvent_t tev[vbq::kEvalKernels + 1] = {};  // created on first use
+  bool tev_valid = false;                       // events of the last timed evaluation are recorded
 };
 
 static void free_system(LoadedSystem& s) {
@@ -115,6 +120,9 @@ void vbqmc_destroy(vbqmc_ctx* ctx) {
   for (auto& s : ctx->sys) free_system(s);
   if (ctx->work) cudaFree(ctx->work);
   if (ctx->dmc_work) cudaFree(ctx->dmc_work);
+  if (ctx->eval_work) cudaFree(ctx->eval_work);
+  for (auto& ev : ctx->tev)
+    if (ev) cudaEventDestroy(ev);
   delete ctx;
 }
 
@@ -279,8 +287,8 @@ int vbqmc_launch_info(vbqmc_ctx* ctx, int sys_id, int precision, int* out) {
     return fail(VBQMC_ERR_NOSYS, "no system loaded under this id");
   if (precision != VBQMC_FP64 && precision != VBQMC_MIXED) return fail(VBQMC_ERR_ARG, "bad precision mode");
   const LoadedSystem& s = ctx->sys[sys_id];
-  out[0] = s.lay_eval[precision].wpb;
-  out[1] = s.lay_eval[precision].warp_bytes;
+  out[0] = s.lay_eval[precision].det.wpb;
+  out[1] = s.lay_eval[precision].det.warp_bytes;
   out[2] = s.lay_sweep[precision].wpb;
   out[3] = s.lay_sweep[precision].warp_bytes;
   return VBQMC_OK;
@@ -303,6 +311,31 @@ int vbqmc_walker_state_size(vbqmc_ctx* ctx, int sys_id, int* ndoubles) {
   return VBQMC_OK;
 }
 
+// Events for a timed evaluation (null when timing is off; creates them on first use).
+static cudaEvent_t* timing_events(vbqmc_ctx* ctx) {
+  if (!ctx->timing) return nullptr;
+  for (auto& ev : ctx->tev)
+    if (!ev && cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+  ctx->tev_valid = true;
+  return ctx->tev;
+}
+
+// Grows the context's evaluation workspace to hold W walkers of the system (synchronizing
+// 'stream' first when it grows, since earlier work on it may still use the old buffer).
+static int ensure_eval_ws(vbqmc_ctx* ctx, const LoadedSystem& s, int precision, int W, cudaStream_t st) {
+  const size_t need = vbq::eval_workspace_bytes(s.dev, precision == VBQMC_MIXED ? 4 : 8, W);
+  if (need <= ctx->eval_bytes) return VBQMC_OK;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  if (ctx->eval_work) cudaFree(ctx->eval_work);
+  ctx->eval_work = nullptr;
+  ctx->eval_bytes = 0;
+  e = cudaMalloc(&ctx->eval_work, need);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(evaluation workspace)");
+  ctx->eval_bytes = need;
+  return VBQMC_OK;
+}
+
 int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const double* R, double* logpsi,
                        double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out,
                        void* stream) {
@@ -316,10 +349,13 @@ int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const d
   if (s.lay_rc_eval[precision]) return fail(s.lay_rc_eval[precision], "per-walker state exceeds shared memory");
   if ((O || dEL) && s.dev.P == 0) O = dEL = nullptr;
   DeviceGuard g(ctx->device);
+  rc = ensure_eval_ws(ctx, s, precision, W, (cudaStream_t)stream);
+  if (rc) return rc;
+  int nl = 0;
   cudaError_t e = vbq::launch_eval(precision, s.dev, s.lay_eval[precision], W, R, logpsi, sign, eloc, grad, O, dEL,
-                                   state_out, (cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(e, "eval kernel launch");
-  ctx->last_launches = 1;
+                                   state_out, ctx->eval_work, (cudaStream_t)stream, &nl, timing_events(ctx));
+  ctx->last_launches = nl;
+  if (e != cudaSuccess) return cuda_fail(e, "evaluation kernel launch");
   return VBQMC_OK;
 }
 
@@ -352,10 +388,16 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
   if (do_eval) {
     if (s.lay_rc_eval[precision]) return fail(s.lay_rc_eval[precision], "per-walker state exceeds shared memory");
     if ((O || dEL) && s.dev.P == 0) O = dEL = nullptr;
+    rc = ensure_eval_ws(ctx, s, precision, W, (cudaStream_t)stream);
+    if (rc) return rc;
+    int nl = 0;
     cudaError_t e = vbq::launch_eval(precision, s.dev, s.lay_eval[precision], W, R, logpsi, sign, eloc, nullptr, O,
-                                     dEL, state, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "eval kernel launch");
-    ++launches;
+                                     dEL, state, ctx->eval_work, (cudaStream_t)stream, &nl, timing_events(ctx));
+    launches += nl;
+    if (e != cudaSuccess) {
+      ctx->last_launches = launches;
+      return cuda_fail(e, "evaluation kernel launch");
+    }
   }
   ctx->last_launches = launches;
   return VBQMC_OK;
@@ -429,18 +471,21 @@ int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int ca
   int launches = 0;
   double E_T = *E_T_io;
   int64_t nacc = 0;
+  rc = ensure_eval_ws(ctx, s, precision, cap, st);
+  if (rc) return rc;
   // the walkers' values at R, carried from step to step
+  int nl = 0;
   cudaError_t e = vbq::launch_eval(precision, s.dev, s.lay_eval[precision], W, cur.R, cur.lp, cur.sg, cur.el, cur.grad,
-                                   nullptr, nullptr, nullptr, st);
-  if (e != cudaSuccess) return cuda_fail(e, "eval kernel launch");
-  ++launches;
+                                   nullptr, nullptr, nullptr, ctx->eval_work, st, &nl);
+  if (e != cudaSuccess) return cuda_fail(e, "evaluation kernel launch");
+  launches += nl;
   int rcode = VBQMC_OK;
   for (int k = 0; k < nsteps; ++k) {
     const uint32_t stp = step0 + (uint32_t)k;
     e = vbq::launch_dmc_propose(W, N, cur.R, cur.grad, tau, seed, stp, system_tag, Rp, st);
     if (e == cudaSuccess)
       e = vbq::launch_eval(precision, s.dev, s.lay_eval[precision], W, Rp, lp1, sg1, el1, grad1, nullptr, nullptr,
-                           nullptr, st);
+                           nullptr, ctx->eval_work, st, &nl);
     if (e == cudaSuccess)
       e = vbq::launch_dmc_accept(W, N, cur.R, cur.lp, cur.sg, cur.el, cur.grad, Rp, lp1, sg1, el1, grad1, tau, E_T,
                                  seed, stp, system_tag, wt, wE, copies, acc, st);
@@ -455,7 +500,7 @@ int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int ca
       rcode = cuda_fail(e, "DMC step");
       break;
     }
-    launches += 5;
+    launches += 4 + nl;
     nacc += h.accepted;
     if (h.total > cap) {
       rcode = fail(VBQMC_ERR_CAPACITY, "DMC population " + std::to_string(h.total) + " exceeds capacity " +
@@ -484,6 +529,29 @@ int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int ca
   if (accepted) *accepted = nacc;
   ctx->last_launches = launches;
   return rcode;
+}
+
+int vbqmc_set_kernel_timing(vbqmc_ctx* ctx, int on) {
+  if (!ctx) return fail(VBQMC_ERR_ARG, "null context");
+  ctx->timing = on ? 1 : 0;
+  ctx->tev_valid = false;
+  return VBQMC_OK;
+}
+
+int vbqmc_kernel_times(vbqmc_ctx* ctx, double* ms, int max, int* n) {
+  if (!ctx || !ms || !n) return fail(VBQMC_ERR_ARG, "null argument");
+  if (!ctx->tev_valid) return fail(VBQMC_ERR_ARG, "no timed evaluation recorded");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaEventSynchronize(ctx->tev[vbq::kEvalKernels]);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+  *n = vbq::kEvalKernels;
+  for (int k = 0; k < vbq::kEvalKernels && k < max; ++k) {
+    float t = 0.0f;
+    e = cudaEventElapsedTime(&t, ctx->tev[k], ctx->tev[k + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    ms[k] = t;
+  }
+  return VBQMC_OK;
 }
 
 int vbqmc_accumulate_lin_matrices(vbqmc_ctx* ctx, int precision, int P, int64_t M, const void* O, const void* dEL,

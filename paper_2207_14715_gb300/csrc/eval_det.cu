@@ -1,0 +1,400 @@
+// Determinant part of the evaluation and the evaluation driver (arXiv:2207.14715, Sec. 2.1,
+// Sec. 2.2, Sec. 2.3.1).  One warp per walker:
+//   C  Slater LU + inverses of every unique determinant (double), structure sum in the log
+//      domain, E_L and grad ln|Psi|; optionally the walker state (inverses, ln|det|, signs)
+//   D1 structure-coefficient derivatives; D3 orbital-excitation derivatives
+// from the Jastrow and orbital results in the evaluation workspace.  The inverses are kept in
+// shared memory in the bulk type only (the double inverses go straight to the walker state).
+#include "walker_common.cuh"
+
+namespace vbq {
+
+namespace {
+
+// Lane-group LU + inverse of every unique determinant of spin sp from the double orbital
+// values PhiD[(e0 + e) * ld + idx[u][o]]: Bt[u] = A^-1 in the bulk type, ln|det|, sign,
+// t_u = tr(A^-1 L) with L read at Lphi[(e0 + e) * ldL + idx[u][o]]; the double inverse is
+// also written to st_binv[u] when st_binv is not null.
+template <class Tb>
+__device__ __forceinline__ void lu_det_all(const SysDev& s, int sp, int lane, const double* PhiD, int ld,
+                                           const Tb* Lphi, int ldL, const int* idx, int G, Tb* Bt, double* scr,
+                                           double* ldet, double* dsg, double* tdet, double* st_binv) {
+  const int n = s.n[sp], U = s.U[sp], e0 = sp ? s.Nup : 0;
+  if (n == 0) {
+    for (int u = lane; u < U; u += 32) {
+      ldet[u] = 0.0;
+      dsg[u] = 1.0;
+      tdet[u] = 0.0;
+    }
+    __syncwarp();
+    return;
+  }
+  const int ng = 32 / G, g = lane / G, gl = lane % G;
+  double* A = scr + g * n * n;
+  double* B = scr + ng * n * n + g * n * n;
+  int* perm = reinterpret_cast<int*>(scr + 2 * ng * n * n) + g * n;
+  for (int u0 = 0; u0 < U; u0 += ng) {
+    const int u = u0 + g;
+    const bool act = u < U;
+    if (act)
+      for (int q = gl; q < n * n; q += G) {
+        const int e = q / n, o = q % n;
+        A[q] = PhiD[(e0 + e) * ld + __ldg(idx + u * n + o)];
+      }
+    __syncwarp();
+    double lg, sg;
+    group_lu_inverse(A, B, perm, n, gl, G, act, lg, sg);
+    __syncwarp();
+    double t = 0.0;
+    if (act && gl < n) {
+      const int o = gl, col = __ldg(idx + u * n + o);
+      for (int e = 0; e < n; ++e) t = fma(B[o * n + e], (double)Lphi[(e0 + e) * ldL + col], t);
+    }
+    t = group_sum(t, G);
+    if (act) {
+      for (int q = gl; q < n * n; q += G) {
+        Bt[u * n * n + q] = (Tb)B[q];
+        if (st_binv) st_binv[u * n * n + q] = B[q];
+      }
+      if (gl == 0) {
+        ldet[u] = lg;
+        dsg[u] = sg;
+        tdet[u] = t;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <class Tb>
+__global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
+    det_kernel(const SysDev s, const DetLayout L, int W, const Tb* __restrict__ JG, const Tb* __restrict__ JL,
+               const double* __restrict__ JS, const Tb* __restrict__ OB, const double* __restrict__ OD,
+               double* __restrict__ logpsi, double* __restrict__ sgn_out, double* __restrict__ eloc,
+               double* __restrict__ vg_ws, double* __restrict__ grad, Tb* __restrict__ Og, Tb* __restrict__ dELg,
+               double* __restrict__ state_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int wl = threadIdx.x >> 5;
+  const int w = blockIdx.x * L.wpb + wl;
+  if (w >= W) return;
+  unsigned char* base = smem + wl * L.warp_bytes;
+  double* vg = reinterpret_cast<double*>(base + L.vg);
+  Tb* G = reinterpret_cast<Tb*>(base + L.G);
+  Tb* LJ = reinterpret_cast<Tb*>(base + L.LJ);
+  Tb* Phi = reinterpret_cast<Tb*>(base + L.Phi);
+  double* PhiD = reinterpret_cast<double*>(base + L.PhiD);
+  Tb* Lphi = reinterpret_cast<Tb*>(base + L.Lphi);
+  Tb* Gphi = reinterpret_cast<Tb*>(base + L.Gphi);
+  Tb* Bt[2] = {reinterpret_cast<Tb*>(base + L.Bt0), reinterpret_cast<Tb*>(base + L.Bt1)};
+  double* ldet = reinterpret_cast<double*>(base + L.ldet);
+  double* dsg = reinterpret_cast<double*>(base + L.dsg);
+  double* tdet = reinterpret_cast<double*>(base + L.tdet);
+  double* Wdet = reinterpret_cast<double*>(base + L.Wdet);
+  double* Tdet = reinterpret_cast<double*>(base + L.Tdet);
+  double* rk = reinterpret_cast<double*>(base + L.rk);
+  unsigned char* scr = base + L.scratch;
+  double* kacc = reinterpret_cast<double*>(base + L.kacc);
+
+  const int N = s.N, Nup = s.Nup, U0 = s.U[0];
+  const int nev = s.n_ev, nevd = s.n_ev_det;
+  // Jastrow results and orbitals from the workspace; dressed Laplacian L = lap phi + 2 grad lnJ . grad phi
+  for (int q = lane; q < 3 * N; q += 32) G[q] = JG[(size_t)w * 3 * N + q];
+  for (int q = lane; q < N; q += 32) LJ[q] = JL[(size_t)w * N + q];
+  const double lnJ = JS[2 * (size_t)w], V = JS[2 * (size_t)w + 1];
+  __syncwarp();
+  for (int e = 0; e < N; ++e) {
+    const Tb* ob = OB + ((size_t)w * N + e) * 5 * nev;
+    const double* od = OD + ((size_t)w * N + e) * nevd;
+    const Tb G0 = G[3 * e], G1 = G[3 * e + 1], G2 = G[3 * e + 2];
+    for (int q = lane; q < nev; q += 32) {
+      const Tb v = ob[q], x = ob[nev + q], y = ob[2 * nev + q], z = ob[3 * nev + q], lp = ob[4 * nev + q];
+      Lphi[e * nev + q] = lp + (Tb)2 * (G0 * x + G1 * y + G2 * z);
+      if (q < nevd) {
+        PhiD[e * nevd + q] = od[q];
+        Gphi[(e * nevd + q) * 3] = x;
+        Gphi[(e * nevd + q) * 3 + 1] = y;
+        Gphi[(e * nevd + q) * 3 + 2] = z;
+      }
+      Phi[e * nev + q] = v;
+    }
+  }
+  __syncwarp();
+
+  // ---- C. Slater matrices: LU, inverses, ln|det|, t_u = tr(A^-1 L) ----
+  double* st = state_out ? state_out + (size_t)w * s.state_doubles : nullptr;
+  const int nb0 = s.U[0] * s.n[0] * s.n[0], nb1 = s.U[1] * s.n[1] * s.n[1];
+  lu_det_all<Tb>(s, 0, lane, PhiD, nevd, Lphi, nev, s.det_ev[0], L.G0, Bt[0], reinterpret_cast<double*>(scr), ldet,
+                 dsg, tdet, st);
+  lu_det_all<Tb>(s, 1, lane, PhiD, nevd, Lphi, nev, s.det_ev[1], L.G1, Bt[1], reinterpret_cast<double*>(scr),
+                 ldet + U0, dsg + U0, tdet + U0, st ? st + nb0 : nullptr);
+  const int Utot = U0 + s.U[1];
+  if (st)
+    // walker state: [Binv spin 0][Binv spin 1][ln|det| (U0+U1)][sign (U0+U1)]
+    for (int q = lane; q < Utot; q += 32) {
+      st[nb0 + nb1 + q] = ldet[q];
+      st[nb0 + nb1 + Utot + q] = dsg[q];
+    }
+  double lnPhi, sgnPhi;
+  term_ratios(s, lane, ldet, dsg, rk, lnPhi, sgnPhi);
+  // K[Phi] and the marginal weights W_u = sum_{k contains u} w_k, T_u = sum_{k contains u} w_k t_k
+  double kphi = 0.0;
+  for (int k = lane; k < s.nterm; k += 32) {
+    const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
+    kphi += __ldg(s.term_coef + k) * rk[k] * (tdet[a] + tdet[U0 + b]);
+  }
+  kphi = warp_sum(kphi);
+  for (int ud = lane; ud < Utot; ud += 32) {
+    const int sp = ud >= U0 ? 1 : 0, u = ud - (sp ? U0 : 0);
+    double Wv = 0.0, Tv = 0.0;
+    for (int k = 0; k < s.nterm; ++k) {
+      const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
+      if ((sp ? b : a) != u) continue;
+      const double wk = __ldg(s.term_coef + k) * rk[k];
+      Wv += wk;
+      Tv += wk * (tdet[a] + tdet[U0 + b]);
+    }
+    Wdet[ud] = Wv;
+    Tdet[ud] = Tv;
+  }
+  __syncwarp();
+  // grad_i ln|Psi| = grad_i lnJ + sum_u W_u sum_o Binv_u[o][i] grad phi_o(r_i), in the bulk type
+  // (it feeds the Jastrow-parameter derivatives and the drift, not E_L)
+  double kin_loc = 0.0;
+  for (int e = lane; e < N; e += 32) {
+    const int sp = e >= Nup ? 1 : 0, ie = e - (sp ? Nup : 0), n = s.n[sp], uo = sp ? U0 : 0;
+    const Tb* Bs = Bt[sp];
+    Tb gx = 0, gy = 0, gz = 0;
+    for (int u = 0; u < s.U[sp]; ++u) {
+      const Tb* B = Bs + u * n * n;
+      Tb ax = 0, ay = 0, az = 0;
+      for (int o = 0; o < n; ++o) {
+        const Tb b = B[o * n + ie];
+        const Tb* gp = Gphi + (e * nevd + __ldg(s.det_ev[sp] + u * n + o)) * 3;
+        ax += b * gp[0];
+        ay += b * gp[1];
+        az += b * gp[2];
+      }
+      const Tb Wu = (Tb)Wdet[uo + u];
+      gx += Wu * ax;
+      gy += Wu * ay;
+      gz += Wu * az;
+    }
+    const double G0 = (double)G[3 * e], G1 = (double)G[3 * e + 1], G2 = (double)G[3 * e + 2];
+    vg[3 * e] = G0 + (double)gx;
+    vg[3 * e + 1] = G1 + (double)gy;
+    vg[3 * e + 2] = G2 + (double)gz;
+    kin_loc += (double)LJ[e] + G0 * G0 + G1 * G1 + G2 * G2;
+  }
+  const double kin = warp_sum(kin_loc) + kphi;
+  const double EL = -0.5 * kin + V;
+  __syncwarp();
+  if (lane == 0) {
+    logpsi[w] = lnJ + lnPhi;
+    sgn_out[w] = sgnPhi;
+    eloc[w] = EL;
+  }
+  for (int q = lane; q < 3 * N; q += 32) {
+    vg_ws[(size_t)w * 3 * N + q] = vg[q];
+    if (grad) grad[(size_t)w * 3 * N + q] = vg[q];
+  }
+  if (!Og) return;
+
+  // ---- D. parameter derivatives (the Jastrow parameters are done by the Jastrow kernel) ----
+  const int P = s.P;
+  Tb* Ow = Og + (size_t)w * P;
+  Tb* Ew = dELg ? dELg + (size_t)w * P : nullptr;
+  // D1. structure coefficients: O_I = Phi_I/Phi, E_L,I = -1/2 (K[Phi_I] - O_I K[Phi])
+  for (int q = lane; q < s.n_cparam; q += 32) {
+    const int I = __ldg(s.cparam + q);
+    double o = 0.0, kk = 0.0;
+    for (int t = 0; t < s.nsterm; ++t) {
+      if (__ldg(s.sterm_I + t) != I) continue;
+      const int k = __ldg(s.sterm_k + t);
+      const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
+      const double r = __ldg(s.sterm_d + t) * rk[k];
+      o += r;
+      kk += r * (tdet[a] + tdet[U0 + b]);
+    }
+    Ow[q] = (Tb)(o);
+    if (Ew) Ew[q] = (Tb)(-0.5 * (kk - o * kphi));
+  }
+  // D3. orbital excitations kappa_kl (Sec. 2.2): for determinant u with l at slot o_l and
+  //   k unoccupied, x_u = (A^-1 Phi)[o_l][k] = d ln D_u, y_u = (A^-1 L)[o_l][k] -
+  //   sum_o' (A^-1 L)[o_l][occ o'] (A^-1 Phi)[o'][k] = d t_u; O = sum_u W_u x_u,
+  //   K[Phi_kappa] = sum_u (T_u x_u + W_u y_u), E_L,kappa = -1/2 (K[Phi_kappa] - O K[Phi]).
+  if (s.n_kappa > 0) {
+    const int nk = s.n_kappa;
+    for (int q = lane; q < 2 * nk; q += 32) kacc[q] = 0.0;
+    __syncwarp();
+    Tb* X = reinterpret_cast<Tb*>(scr);
+    for (int sp = 0; sp < 2; ++sp) {
+      const int n = s.n[sp], e0 = sp ? Nup : 0, uo = sp ? U0 : 0;
+      if (n == 0) continue;
+      Tb* Y = X + n * nev;
+      for (int u = 0; u < s.U[sp]; ++u) {
+        const int eb = __ldg(s.kap_off[sp] + u), ee = __ldg(s.kap_off[sp] + u + 1);
+        if (eb == ee) continue;
+        const Tb* B = Bt[sp] + u * n * n;
+        for (int q = lane; q < n * nev; q += 32) {
+          const int o = q / nev, c = q % nev;
+          Tb x = 0, y = 0;
+          for (int e = 0; e < n; ++e) {
+            const Tb b = B[o * n + e];
+            x += b * Phi[(e0 + e) * nev + c];
+            y += b * Lphi[(e0 + e) * nev + c];
+          }
+          X[q] = x;
+          Y[q] = y;
+        }
+        __syncwarp();
+        const double Wu = Wdet[uo + u], Tu = Tdet[uo + u];
+        for (int t = eb + lane; t < ee; t += 32) {
+          const int j = __ldg(s.kap_ent[sp] + 4 * t), ol = __ldg(s.kap_ent[sp] + 4 * t + 1),
+                    kc = __ldg(s.kap_ent[sp] + 4 * t + 2);
+          const Tb x = X[ol * nev + kc];
+          Tb y = Y[ol * nev + kc];
+          for (int o2 = 0; o2 < n; ++o2) y -= Y[ol * nev + __ldg(s.det_ev[sp] + u * n + o2)] * X[o2 * nev + kc];
+          kacc[j] += Wu * (double)x;
+          kacc[nk + j] += Tu * (double)x + Wu * (double)y;
+        }
+        __syncwarp();
+      }
+    }
+    for (int j = lane; j < nk; j += 32) {
+      const double o = kacc[j];
+      Ow[s.p_off_kappa + j] = (Tb)(o);
+      if (Ew) Ew[s.p_off_kappa + j] = (Tb)(-0.5 * (kacc[nk + j] - o * kphi));
+    }
+  }
+}
+
+int make_det_layout(const SysDev& s, int tb, int max_smem, DetLayout& L) {
+  int off = 0;
+  auto take = [&](int bytes) {
+    const int o = off;
+    off = align16(off + bytes);
+    return o;
+  };
+  const int N = s.N, Ut = s.U[0] + s.U[1];
+  L.G0 = group_size(s.n[0]);
+  L.G1 = group_size(s.n[1]);
+  L.vg = take(8 * 3 * N);
+  L.G = take(tb * 3 * N);
+  L.LJ = take(tb * N);
+  L.Phi = take(tb * N * s.n_ev);
+  L.PhiD = take(8 * N * std::max(s.n_ev_det, 1));
+  L.Lphi = take(tb * N * s.n_ev);
+  L.Gphi = take(tb * N * s.n_ev_det * 3);
+  L.Bt0 = take(tb * s.U[0] * s.n[0] * s.n[0]);
+  L.Bt1 = take(tb * s.U[1] * s.n[1] * s.n[1]);
+  L.ldet = take(8 * Ut);
+  L.dsg = take(8 * Ut);
+  L.tdet = take(8 * Ut);
+  L.Wdet = take(8 * Ut);
+  L.Tdet = take(8 * Ut);
+  L.rk = take(8 * s.nterm);
+  int scr = 16;
+  for (int sp = 0; sp < 2; ++sp) {
+    const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
+    scr = std::max(scr, ng * (16 * n * n + 4 * n) + 16);  // LU: A, inverse, pivots per group
+    scr = std::max(scr, 2 * n * s.n_ev * tb);              // excitations: X, Y
+  }
+  L.scratch = take(scr);
+  L.kacc = take(8 * 2 * std::max(s.n_kappa, 1));
+  L.warp_bytes = off;
+  int wpb = max_smem / off;
+  const int cap = (tb == 8 ? EvalBounds<double>::threads : EvalBounds<float>::threads) / 32;
+  if (wpb > cap) wpb = cap;
+  if (wpb < 1) return VBQMC_ERR_CAPACITY;
+  L.wpb = wpb;
+  return VBQMC_OK;
+}
+
+inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct EvalWs {
+  void *JG, *JL, *OB;
+  double *JS, *OD, *VG;
+};
+
+EvalWs carve(const SysDev& s, int tb, int W, void* ws) {
+  const size_t N = s.N, Wz = W;
+  unsigned char* p = static_cast<unsigned char*>(ws);
+  EvalWs r;
+  auto take = [&](size_t b) {
+    unsigned char* q = p;
+    p += al256(b);
+    return q;
+  };
+  r.JG = take(Wz * 3 * N * tb);
+  r.JL = take(Wz * N * tb);
+  r.JS = reinterpret_cast<double*>(take(Wz * 2 * 8));
+  r.OB = take(Wz * N * 5 * s.n_ev * tb);
+  r.OD = reinterpret_cast<double*>(take(Wz * N * std::max(s.n_ev_det, 1) * 8));
+  r.VG = reinterpret_cast<double*>(take(Wz * 3 * N * 8));
+  return r;
+}
+
+template <class Tb>
+cudaError_t launch_eval_t(const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi, double* sign,
+                          double* eloc, double* grad, Tb* O, Tb* dEL, double* state_out, void* ws, cudaStream_t st,
+                          int* nlaunch, cudaEvent_t* ev) {
+  const EvalWs b = carve(s, (int)sizeof(Tb), W, ws);
+  *nlaunch = 0;
+  auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], st) : cudaSuccess; };
+  cudaError_t e = mark(0);
+  if (e != cudaSuccess) return e;
+  e = launch_jastrow<Tb>(s, L.jas, W, R, static_cast<Tb*>(b.JG), static_cast<Tb*>(b.JL), b.JS, st);
+  if (e != cudaSuccess) return e;
+  ++*nlaunch;
+  if ((e = mark(1)) != cudaSuccess) return e;
+  e = launch_orbitals<Tb>(s, L.orb, W, R, static_cast<Tb*>(b.OB), b.OD, st);
+  if (e != cudaSuccess) return e;
+  ++*nlaunch;
+  if ((e = mark(2)) != cudaSuccess) return e;
+  const DetLayout& D = L.det;
+  const int smem = D.wpb * D.warp_bytes;
+  e = cudaFuncSetAttribute(det_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  det_kernel<Tb><<<(W + D.wpb - 1) / D.wpb, 32 * D.wpb, smem, st>>>(
+      s, D, W, static_cast<const Tb*>(b.JG), static_cast<const Tb*>(b.JL), b.JS, static_cast<const Tb*>(b.OB), b.OD,
+      logpsi, sign, eloc, b.VG, grad, O, dEL, state_out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ++*nlaunch;
+  if ((e = mark(3)) != cudaSuccess) return e;
+  if (O && s.jas_param) {
+    e = launch_jastrow_deriv<Tb>(s, L.jas, W, R, b.VG, O, dEL, st);
+    if (e != cudaSuccess) return e;
+    ++*nlaunch;
+  }
+  return mark(4);
+}
+
+}  // namespace
+
+int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
+  int rc = make_jas_layout(s, tb, max_smem, L.jas);
+  if (rc == VBQMC_OK) rc = make_orb_layout(s, tb, max_smem, L.orb);
+  if (rc == VBQMC_OK) rc = make_det_layout(s, tb, max_smem, L.det);
+  return rc;
+}
+
+size_t eval_workspace_bytes(const SysDev& s, int tb, int W) {
+  const size_t N = s.N, Wz = std::max(W, 1);
+  return al256(Wz * 3 * N * tb) + al256(Wz * N * tb) + al256(Wz * 2 * 8) + al256(Wz * N * 5 * s.n_ev * tb) +
+         al256(Wz * N * std::max(s.n_ev_det, 1) * 8) + al256(Wz * 3 * N * 8);
+}
+
+cudaError_t launch_eval(int precision, const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
+                        double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out, void* ws,
+                        cudaStream_t st, int* nlaunch, cudaEvent_t* ev) {
+  if (precision == VBQMC_MIXED)
+    return launch_eval_t<float>(s, L, W, R, logpsi, sign, eloc, grad, static_cast<float*>(O),
+                                static_cast<float*>(dEL), state_out, ws, st, nlaunch, ev);
+  return launch_eval_t<double>(s, L, W, R, logpsi, sign, eloc, grad, static_cast<double*>(O),
+                               static_cast<double*>(dEL), state_out, ws, st, nlaunch, ev);
+}
+
+}  // namespace vbq

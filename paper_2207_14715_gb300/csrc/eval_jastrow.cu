@@ -1,0 +1,364 @@
+// Jastrow part of the evaluation (arXiv:2207.14715, Sec. 2.1, Jastrow factor; Sec. 2.3.1):
+//   jastrow_kernel        ln J, grad_i ln J, lap_i ln J and the Coulomb potential per walker
+//   jastrow_deriv_kernel  O_alpha = d ln J/d alpha and E_L,alpha = -1/2 sum_i (lap_i g_alpha +
+//                         2 grad_i g_alpha . grad_i ln|Psi|) for every Jastrow parameter alpha
+// One warp per walker; the geometry tables of the walker live in shared memory.
+#include "walker_common.cuh"
+
+namespace vbq {
+
+namespace {
+
+// Blocks per SM the Jastrow kernels are compiled for (the double instantiation keeps more
+// live values, so it gets the whole register file of one block).
+template <class Tb> struct JasBounds { static constexpr int min_blocks = 2; };
+template <> struct JasBounds<double> { static constexpr int min_blocks = 1; };
+
+// lanes -> (electron i, group g); group g takes nuclei a = g, g + S, ... and partners
+// j = g, g + S, ...
+template <class Tb>
+__global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_kernel(const SysDev s, const JasLayout L, int W,
+                                                         const double* __restrict__ Rg, Tb* __restrict__ JG,
+                                                         Tb* __restrict__ JL, double* __restrict__ JS) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int wl = threadIdx.x >> 5;
+  const int w = blockIdx.x * L.wpb + wl;
+  if (w >= W) return;
+  unsigned char* base = smem + wl * L.warp_bytes;
+  double* R = reinterpret_cast<double*>(base + L.R);
+  const int N = s.N, Nn = s.Nn, Nup = s.Nup;
+  const GeoTables<Tb> g(reinterpret_cast<Tb*>(base + L.geo), N, Nn);
+  const Tb kap = (Tb)s.kappa;
+  for (int i = lane; i < 3 * N; i += 32) R[i] = Rg[(size_t)w * 3 * N + i];
+  __syncwarp();
+  double V_loc = build_geometry<Tb>(s, lane, R, g);
+  double lnJ_loc = 0.0;
+  const Tb* cE = een_coefs<Tb>(s);
+  const int Pp = L.jas_P, Sg = L.jas_S;
+  for (int b0 = 0; b0 < N; b0 += Pp) {
+    const int i = b0 + lane % Pp, gr = lane / Pp;
+    const bool act = i < N;
+    Tb g0 = 0, g1 = 0, g2 = 0, lap = 0;
+    double lnj = 0.0;
+    if (act) {
+      for (int a = gr; a < Nn; a += Sg) {
+        const int ia = i * Nn + a;
+        const Tb r = g.rEN[ia];
+        Tb f, df, d2f;
+        pade_eval<Tb, true>(en_coef(s, a), r, kap, f, df, d2f);
+        lnj += (double)f;
+        g0 += df * g.eEN[3 * ia]; g1 += df * g.eEN[3 * ia + 1]; g2 += df * g.eEN[3 * ia + 2];
+        lap += d2f + (Tb)2 * df / r;
+      }
+      for (int j = gr; j < N; j += Sg) {
+        if (j == i) continue;
+        const int ij = i * N + j;
+        Tb f, df, d2f;
+        pade_eval<Tb, true>(ee_coef(s, (i < Nup) == (j < Nup)), g.rEE[ij], kap, f, df, d2f);
+        lnj += 0.5 * (double)f;
+        g0 += df * g.eEE[3 * ij]; g1 += df * g.eEE[3 * ij + 1]; g2 += df * g.eEE[3 * ij + 2];
+        lap += d2f + (Tb)2 * df * g.iEE[ij];
+      }
+      if (s.een_on)
+        for (int a = gr; a < Nn; a += Sg) {
+          const int ia = i * Nn + a;
+          const Tb* c = cE + kNeen * __ldg(s.nuc_elem + a);
+          EenSide<Tb> si;
+          si.set(g.Stab[(a * N + i) * 6 + 1], g.rEN[ia], kap);
+          const Tb ex = g.eEN[3 * ia], ey = g.eEN[3 * ia + 1], ez = g.eEN[3 * ia + 2];
+          auto sink = [&](int t, Tb val, Tb gx, Tb gy, Tb gz, Tb lp) {
+            const Tb ct = c[t];
+            lnj += (double)(ct * val);
+            g0 += ct * gx; g1 += ct * gy; g2 += ct * gz;
+            lap += ct * lp;
+          };
+          {
+            EenAcc<Tb, 1, 2> acc;
+            acc.zero();
+            for (int j = 0; j < N; ++j)
+              if (j != i) {
+                const int ij = i * N + j;
+                acc.add(g.uEE[ij], g.iEE[ij], kap, g.eEE[3 * ij], g.eEE[3 * ij + 1], g.eEE[3 * ij + 2],
+                        g.Stab + (a * N + j) * 6);
+              }
+            een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, sink);
+          }
+          {
+            EenAcc<Tb, 3, 4> acc;
+            acc.zero();
+            for (int j = 0; j < N; ++j)
+              if (j != i) {
+                const int ij = i * N + j;
+                acc.add(g.uEE[ij], g.iEE[ij], kap, g.eEE[3 * ij], g.eEE[3 * ij + 1], g.eEE[3 * ij + 2],
+                        g.Stab + (a * N + j) * 6);
+              }
+            een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, sink);
+          }
+        }
+      lnJ_loc += lnj;
+    }
+    for (int o = Pp; o < 32; o <<= 1) {
+      g0 += __shfl_xor_sync(kFull, g0, o);
+      g1 += __shfl_xor_sync(kFull, g1, o);
+      g2 += __shfl_xor_sync(kFull, g2, o);
+      lap += __shfl_xor_sync(kFull, lap, o);
+    }
+    if (act && gr == 0) {
+      Tb* Gw = JG + (size_t)w * 3 * N;
+      Gw[3 * i] = g0; Gw[3 * i + 1] = g1; Gw[3 * i + 2] = g2;
+      JL[(size_t)w * N + i] = lap;
+    }
+  }
+  const double lnJ = warp_sum(lnJ_loc);
+  const double V = warp_sum(V_loc) + s.vnn;
+  if (lane == 0) {
+    JS[2 * (size_t)w] = lnJ;
+    JS[2 * (size_t)w + 1] = V;
+  }
+}
+
+// Radial parameter derivatives of the Pade + polynomial form f(R) = a1 R/(1 + a2 R) +
+// sum_p a_{p+1} R^p, R = r/(1 + kappa r): with h the derivative of f with respect to the
+// parameter,
+//   a_2: h = -a1 R^2/(1+a2 R)^2, h' = -2 a1 R/(1+a2 R)^3, h'' = -2 a1 (1-2 a2 R)/(1+a2 R)^4
+//   a_{p+1}: h = R^p; chain rule to r with R' = 1/(1+kappa r)^2, R'' = -2 kappa/(1+kappa r)^3.
+template <class Tb>
+__device__ __forceinline__ void pade_param_derivs(Tb r, Tb kap, Tb a1, Tb a2, Tb h[5], Tb g1[5], Tb g2[5]) {
+  const Tb den = (Tb)1 / ((Tb)1 + kap * r), Rr = r * den, dR = den * den, d2R = (Tb)-2 * kap * dR * den;
+  const Tb pd = (Tb)1 / ((Tb)1 + a2 * Rr);
+  Tb hR[5], hRR[5];
+  h[0] = -a1 * Rr * Rr * pd * pd;
+  hR[0] = (Tb)-2 * a1 * Rr * pd * pd * pd;
+  hRR[0] = (Tb)-2 * a1 * ((Tb)1 - (Tb)2 * a2 * Rr) * pd * pd * pd * pd;
+  Tb Rm2 = 1;  // R^(p-2)
+#pragma unroll
+  for (int p = 2; p <= 5; ++p) {
+    h[p - 1] = Rm2 * Rr * Rr;
+    hR[p - 1] = (Tb)p * Rm2 * Rr;
+    hRR[p - 1] = (Tb)(p * (p - 1)) * Rm2;
+    Rm2 *= Rr;
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    g1[q] = hR[q] * dR;
+    g2[q] = hRR[q] * dR * dR + hR[q] * d2R;
+  }
+}
+
+template <class Tb>
+__global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_deriv_kernel(const SysDev s, const JasLayout L, int W,
+                                                               const double* __restrict__ Rg,
+                                                               const double* __restrict__ vgg, Tb* __restrict__ Og,
+                                                               Tb* __restrict__ dELg) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int wl = threadIdx.x >> 5;
+  const int w = blockIdx.x * L.wpb + wl;
+  if (w >= W) return;
+  unsigned char* base = smem + wl * L.warp_bytes;
+  double* R = reinterpret_cast<double*>(base + L.R);
+  double* vg = reinterpret_cast<double*>(base + L.vg);
+  double* red = reinterpret_cast<double*>(base + L.red);
+  const int N = s.N, Nn = s.Nn, Nup = s.Nup;
+  const GeoTables<Tb> g(reinterpret_cast<Tb*>(base + L.geo), N, Nn);
+  const Tb kap = (Tb)s.kappa;
+  for (int i = lane; i < 3 * N; i += 32) {
+    R[i] = Rg[(size_t)w * 3 * N + i];
+    vg[i] = vgg[(size_t)w * 3 * N + i];
+  }
+  __syncwarp();
+  build_geometry<Tb>(s, lane, R, g);
+  const int P = s.P;
+  Tb* Ow = Og + (size_t)w * P;
+  Tb* Ew = dELg ? dELg + (size_t)w * P : nullptr;
+  // e-n: a_2..a_6 per element (lanes over electron-nucleus pairs)
+  for (int E = 0; E < s.n_elem; ++E) {
+    Tb aO[5] = {0, 0, 0, 0, 0}, aE[5] = {0, 0, 0, 0, 0};
+    for (int t = lane; t < N * Nn; t += 32) {
+      const int i = t / Nn, a = t % Nn;
+      if (__ldg(s.nuc_elem + a) != E) continue;
+      const Tb r = g.rEN[t];
+      const PadeCoef c = en_coef(s, a);
+      const Tb cosv = g.eEN[3 * t] * (Tb)vg[3 * i] + g.eEN[3 * t + 1] * (Tb)vg[3 * i + 1] +
+                      g.eEN[3 * t + 2] * (Tb)vg[3 * i + 2];
+      Tb h[5], g1[5], g2[5];
+      pade_param_derivs<Tb>(r, kap, (Tb)c.a1, (Tb)c.a2, h, g1, g2);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        aO[q] += h[q];
+        aE[q] += (Tb)-0.5 * (g2[q] + (Tb)2 * g1[q] / r + (Tb)2 * g1[q] * cosv);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const double o = warp_sum((double)aO[q]), e = warp_sum((double)aE[q]);
+      if (lane == 0) {
+        Ow[s.p_off_a + 5 * E + q] = (Tb)(o);
+        if (Ew) Ew[s.p_off_a + 5 * E + q] = (Tb)(e);
+      }
+    }
+  }
+  // e-e: b_2..b_6 (lanes over pairs), same radial forms with b1 (by spins) and b2
+  {
+    Tb bO[5] = {0, 0, 0, 0, 0}, bE[5] = {0, 0, 0, 0, 0};
+    const int npair = N * (N - 1) / 2;
+    for (int pp = lane; pp < npair; pp += 32) {
+      int i = 0, rem = pp;
+      while (rem >= N - 1 - i) { rem -= N - 1 - i; ++i; }
+      const int j = i + 1 + rem, ij = i * N + j;
+      const Tb r = g.rEE[ij];
+      const PadeCoef c = ee_coef(s, (i < Nup) == (j < Nup));
+      const Tb cosv = g.eEE[3 * ij] * (Tb)(vg[3 * i] - vg[3 * j]) + g.eEE[3 * ij + 1] * (Tb)(vg[3 * i + 1] - vg[3 * j + 1]) +
+                      g.eEE[3 * ij + 2] * (Tb)(vg[3 * i + 2] - vg[3 * j + 2]);
+      Tb h[5], g1[5], g2[5];
+      pade_param_derivs<Tb>(r, kap, (Tb)c.a1, (Tb)c.a2, h, g1, g2);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        bO[q] += h[q];
+        bE[q] += (Tb)-0.5 * ((Tb)2 * (g2[q] + (Tb)2 * g1[q] * g.iEE[ij]) + (Tb)2 * g1[q] * cosv);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const double o = warp_sum((double)bO[q]), e = warp_sum((double)bE[q]);
+      if (lane == 0) {
+        Ow[s.p_off_b + q] = (Tb)(o);
+        if (Ew) Ew[s.p_off_b + q] = (Tb)(e);
+      }
+    }
+  }
+  // e-e-n: per element, the raw-term derivatives from the pair sums (lane -> (electron i,
+  // group g), nuclei of the element split among groups), then theta = B^T raw
+  if (s.een_on) {
+    double* rawO = red;          // [23]
+    double* rawE = red + kNeen;  // [23]
+    const int Pp = L.jas_P, Sg = L.jas_S;
+    for (int E = 0; E < s.n_elem; ++E) {
+      Tb accO[kNeen], accE[kNeen];
+#pragma unroll
+      for (int q = 0; q < kNeen; ++q) accO[q] = accE[q] = (Tb)0;
+      for (int b0 = 0; b0 < N; b0 += Pp) {
+        const int i = b0 + lane % Pp, gr = lane / Pp;
+        if (i >= N) continue;
+        const Tb vx = (Tb)vg[3 * i], vy = (Tb)vg[3 * i + 1], vz = (Tb)vg[3 * i + 2];
+        for (int a = gr; a < Nn; a += Sg) {
+          if (__ldg(s.nuc_elem + a) != E) continue;
+          const int ia = i * Nn + a;
+          EenSide<Tb> si;
+          si.set(g.Stab[(a * N + i) * 6 + 1], g.rEN[ia], kap);
+          const Tb ex = g.eEN[3 * ia], ey = g.eEN[3 * ia + 1], ez = g.eEN[3 * ia + 2];
+          auto sink = [&](int t, Tb val, Tb gx, Tb gy, Tb gz, Tb lp) {
+            accO[t] += val;
+            accE[t] += (Tb)-0.5 * (lp + (Tb)2 * (gx * vx + gy * vy + gz * vz));
+          };
+          {
+            EenAcc<Tb, 1, 2> acc;
+            acc.zero();
+            for (int j = 0; j < N; ++j)
+              if (j != i) {
+                const int ij = i * N + j;
+                acc.add(g.uEE[ij], g.iEE[ij], kap, g.eEE[3 * ij], g.eEE[3 * ij + 1], g.eEE[3 * ij + 2],
+                        g.Stab + (a * N + j) * 6);
+              }
+            een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, sink);
+          }
+          {
+            EenAcc<Tb, 3, 4> acc;
+            acc.zero();
+            for (int j = 0; j < N; ++j)
+              if (j != i) {
+                const int ij = i * N + j;
+                acc.add(g.uEE[ij], g.iEE[ij], kap, g.eEE[3 * ij], g.eEE[3 * ij + 1], g.eEE[3 * ij + 2],
+                        g.Stab + (a * N + j) * 6);
+              }
+            een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, sink);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kNeen; ++q) {
+        const double o = warp_sum((double)accO[q]), e = warp_sum((double)accE[q]);
+        if (lane == 0) {
+          rawO[q] = o;
+          rawE[q] = e;
+        }
+      }
+      __syncwarp();
+      for (int f = lane; f < kNfree; f += 32) {
+        double o = 0.0, e = 0.0;
+        for (int q = 0; q < kNeen; ++q) {
+          const double b = __ldg(s.een_B + q * kNfree + f);
+          o = fma(b, rawO[q], o);
+          e = fma(b, rawE[q], e);
+        }
+        Ow[s.p_off_theta + kNfree * E + f] = (Tb)(o);
+        if (Ew) Ew[s.p_off_theta + kNfree * E + f] = (Tb)(e);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+}  // namespace
+
+int make_jas_layout(const SysDev& s, int tb, int max_smem, JasLayout& L) {
+  int off = 0;
+  auto take = [&](int bytes) {
+    const int o = off;
+    off = align16(off + bytes);
+    return o;
+  };
+  const int N = s.N;
+  L.R = take(8 * 3 * N);
+  L.vg = take(8 * 3 * N);
+  L.red = take(8 * 2 * kNeen);
+  L.geo = take(tb * geo_elems<float>(N, s.Nn));
+  {
+    int P = 1;
+    while (P < N && P < 32) P <<= 1;
+    L.jas_P = P;
+    L.jas_S = 32 / P;
+  }
+  L.warp_bytes = off;
+  int wpb = std::min(8, max_smem / off);
+  if (wpb < 1) return VBQMC_ERR_CAPACITY;
+  L.wpb = wpb;
+  return VBQMC_OK;
+}
+
+template <class K>
+static cudaError_t set_smem(K kernel, int smem) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+template <class Tb>
+cudaError_t launch_jastrow(const SysDev& s, const JasLayout& L, int W, const double* R, Tb* JG, Tb* JL, double* JS,
+                           cudaStream_t st) {
+  const int smem = L.wpb * L.warp_bytes;
+  cudaError_t e = set_smem(jastrow_kernel<Tb>, smem);
+  if (e != cudaSuccess) return e;
+  jastrow_kernel<Tb><<<(W + L.wpb - 1) / L.wpb, 32 * L.wpb, smem, st>>>(s, L, W, R, JG, JL, JS);
+  return cudaGetLastError();
+}
+
+template <class Tb>
+cudaError_t launch_jastrow_deriv(const SysDev& s, const JasLayout& L, int W, const double* R, const double* vg, Tb* O,
+                                 Tb* dEL, cudaStream_t st) {
+  const int smem = L.wpb * L.warp_bytes;
+  cudaError_t e = set_smem(jastrow_deriv_kernel<Tb>, smem);
+  if (e != cudaSuccess) return e;
+  jastrow_deriv_kernel<Tb><<<(W + L.wpb - 1) / L.wpb, 32 * L.wpb, smem, st>>>(s, L, W, R, vg, O, dEL);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_jastrow<float>(const SysDev&, const JasLayout&, int, const double*, float*, float*,
+                                           double*, cudaStream_t);
+template cudaError_t launch_jastrow<double>(const SysDev&, const JasLayout&, int, const double*, double*, double*,
+                                            double*, cudaStream_t);
+template cudaError_t launch_jastrow_deriv<float>(const SysDev&, const JasLayout&, int, const double*, const double*,
+                                                 float*, float*, cudaStream_t);
+template cudaError_t launch_jastrow_deriv<double>(const SysDev&, const JasLayout&, int, const double*, const double*,
+                                                  double*, double*, cudaStream_t);
+
+}  // namespace vbq

@@ -1,0 +1,134 @@
+// Orbitals at every electron (arXiv:2207.14715, Sec. 2.1: phi_p = sum_mu lambda_{p mu} chi_mu):
+// basis functions with gradients and Laplacians, then the contraction in balanced chunks of
+// the nonzero coefficients.  One warp per (walker, electron), so that many warps share each
+// SM; results go to the evaluation workspace:
+//   OB [W][N][5][n_ev] bulk type: phi, d/dx, d/dy, d/dz, lap phi of the evaluated orbitals
+//   OD [W][N][n_det_ev] double: values of the orbitals that enter determinants; in the mixed
+//      form these come from float-float basis values and coefficients, and OB holds them
+//      rounded to float.
+#include "walker_common.cuh"
+
+namespace vbq {
+
+namespace {
+
+constexpr int kOrbWarps = 8;
+
+template <class Tb>
+__global__ void __launch_bounds__(32 * kOrbWarps, 4) orbital_kernel(const SysDev s, const OrbLayout L, int W,
+                                                                     const double* __restrict__ Rg,
+                                                                     Tb* __restrict__ OB, double* __restrict__ OD) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int wl = threadIdx.x >> 5;
+  const int N = s.N;
+  const long long gw = (long long)blockIdx.x * kOrbWarps + wl;
+  if (gw >= (long long)W * N) return;  // warp gw: walker gw / N, electron gw % N
+  unsigned char* base = smem + wl * L.warp_bytes;
+  const int nev = s.n_ev, nevd = s.n_ev_det, M = s.M;
+  Tb* bv = reinterpret_cast<Tb*>(base + L.bas);
+  Tb* bx = bv + M;
+  Tb* by = bx + M;
+  Tb* bz = by + M;
+  Tb* bl = bz + M;
+  dsf* bds = reinterpret_cast<dsf*>(base + L.bds);
+  dsf* ctab = reinterpret_cast<dsf*>(base + L.ctab);
+  Tb* part = reinterpret_cast<Tb*>(base + L.part);
+  dsf* partds = reinterpret_cast<dsf*>(base + L.partd);
+  const double* r = Rg + (size_t)gw * 3;
+  const double x = r[0], y = r[1], z = r[2];
+  const Tb* cf = orb_coefs<Tb>(s);
+  basis_at<Tb, true>(s, lane, x, y, z, bv, bx, by, bz, bl);
+  if (!kSameType<Tb, double>) basis_values_ds(s, lane, x, y, z, ctab, bds);
+  __syncwarp();
+  for (int c = lane; c < s.n_ev_chunk; c += 32) {
+    const int4 ch = __ldg(reinterpret_cast<const int4*>(s.ev_chunk) + c);
+    const Tb* cb = cf + ch.w;
+    Tb v = 0, gx = 0, gy = 0, gz = 0, lp = 0;
+    for (int mu = ch.y; mu < ch.z; ++mu) {
+      const Tb cm = __ldg(cb + mu);
+      v += cm * bv[mu]; gx += cm * bx[mu]; gy += cm * by[mu]; gz += cm * bz[mu]; lp += cm * bl[mu];
+    }
+    Tb* pp = part + 5 * c;
+    pp[0] = v; pp[1] = gx; pp[2] = gy; pp[3] = gz; pp[4] = lp;
+  }
+  if (!kSameType<Tb, double>)
+    for (int c = lane; c < s.n_det_chunk; c += 32) {
+      const int4 ch = __ldg(reinterpret_cast<const int4*>(s.det_chunk) + c);
+      const float2* cb = reinterpret_cast<const float2*>(s.orb_coef_ds) + ch.w;
+      dsf acc = {0.0f, 0.0f};
+      for (int mu = ch.y; mu < ch.z; ++mu) {
+        const float2 lm = __ldg(cb + mu);
+        acc = ds_add(acc, ds_mul(dsf{lm.x, lm.y}, bds[mu]));
+      }
+      partds[c] = acc;
+    }
+  __syncwarp();
+  Tb* out = OB + (size_t)gw * 5 * nev;
+  for (int q = lane; q < nev; q += 32) {
+    const int c0 = __ldg(s.ev_chunk_off + q), c1 = __ldg(s.ev_chunk_off + q + 1);
+    Tb v = 0, gx = 0, gy = 0, gz = 0, lp = 0;
+    for (int c = c0; c < c1; ++c) {
+      const Tb* pp = part + 5 * c;
+      v += pp[0]; gx += pp[1]; gy += pp[2]; gz += pp[3]; lp += pp[4];
+    }
+    if (q < nevd) {
+      double vd = 0.0;
+      if (kSameType<Tb, double>) {
+        vd = (double)v;
+      } else {
+        const int d0 = __ldg(s.det_chunk_off + q), d1 = __ldg(s.det_chunk_off + q + 1);
+        dsf acc = {0.0f, 0.0f};
+        for (int c = d0; c < d1; ++c) acc = ds_add(acc, partds[c]);
+        vd = ds_to_double(acc);
+      }
+      OD[(size_t)gw * nevd + q] = vd;
+      v = (Tb)vd;
+    }
+    out[q] = v;
+    out[nev + q] = gx;
+    out[2 * nev + q] = gy;
+    out[3 * nev + q] = gz;
+    out[4 * nev + q] = lp;
+  }
+}
+
+}  // namespace
+
+int make_orb_layout(const SysDev& s, int tb, int max_smem, OrbLayout& L) {
+  int off = 0;
+  auto take = [&](int bytes) {
+    const int o = off;
+    off = align16(off + bytes);
+    return o;
+  };
+  const int M = s.M;
+  L.bas = take(5 * M * tb);
+  L.bds = take(tb == 4 ? 8 * M : 16);
+  L.ctab = take(tb == 4 ? 8 * 4 * s.Nn : 16);
+  L.part = take(5 * tb * std::max(s.n_ev_chunk, 1));
+  L.partd = take(tb == 4 ? 8 * std::max(s.n_det_chunk, 1) : 16);
+  L.warp_bytes = off;
+  L.wpb = kOrbWarps;
+  if (kOrbWarps * off > max_smem) return VBQMC_ERR_CAPACITY;
+  return VBQMC_OK;
+}
+
+template <class Tb>
+cudaError_t launch_orbitals(const SysDev& s, const OrbLayout& L, int W, const double* R, Tb* OB, double* OD,
+                            cudaStream_t st) {
+  const int smem = kOrbWarps * L.warp_bytes;
+  cudaError_t e = cudaFuncSetAttribute(orbital_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const long long warps = (long long)W * s.N;
+  orbital_kernel<Tb><<<(unsigned)((warps + kOrbWarps - 1) / kOrbWarps), 32 * kOrbWarps, smem, st>>>(s, L, W, R, OB,
+                                                                                                    OD);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_orbitals<float>(const SysDev&, const OrbLayout&, int, const double*, float*, double*,
+                                            cudaStream_t);
+template cudaError_t launch_orbitals<double>(const SysDev&, const OrbLayout&, int, const double*, double*, double*,
+                                             cudaStream_t);
+
+}  // namespace vbq

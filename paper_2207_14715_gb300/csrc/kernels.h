@@ -7,14 +7,35 @@
 
 namespace vbq {
 
-// One warp evaluates one walker; all per-walker state lives in shared memory.  Offsets are
-// bytes from the start of the warp's region.
-struct EvalLayout {
+// The evaluation runs as four kernels, each with the occupancy its own working set allows:
+//   jastrow     warp per walker: geometry tables, ln J, grad_i ln J, lap_i ln J, potential
+//   orbitals    warp per (walker, electron): basis functions and orbital values/derivatives
+//   det         warp per walker: Slater LU + inverses, structure sum, E_L, grad ln|Psi|,
+//               structure-coefficient and orbital-excitation derivatives, walker state
+//   jastrow_d   warp per walker: Jastrow-parameter derivatives (needs grad ln|Psi|)
+// connected through a device workspace (eval_workspace_bytes).  Offsets are bytes from the
+// start of a warp's shared-memory region.
+struct JasLayout {
   int wpb = 0, warp_bytes = 0;
-  int R, vg, G, LJ, Phi, PhiD, Lphi, Gphi, Binv0, Binv1, ldet, dsg, tdet, Wdet, Tdet, rk, scratch, part, partd,
-      kacc, red, geo;
-  int G0, G1;          // lane-group size per spin for the LU
-  int jas_P, jas_S;    // Jastrow lanes: electron = lane % jas_P, group = lane / jas_P (jas_S groups)
+  int R, vg, red, geo;
+  int jas_P, jas_S;  // lanes: electron = lane % jas_P, group = lane / jas_P (jas_S groups)
+};
+
+struct OrbLayout {
+  int wpb = 0, warp_bytes = 0;
+  int bas, bds, ctab, part, partd;
+};
+
+struct DetLayout {
+  int wpb = 0, warp_bytes = 0;
+  int vg, G, LJ, Phi, PhiD, Lphi, Gphi, Bt0, Bt1, ldet, dsg, tdet, Wdet, Tdet, rk, scratch, kacc;
+  int G0, G1;  // lane-group size per spin for the LU
+};
+
+struct EvalLayout {
+  JasLayout jas;
+  OrbLayout orb;
+  DetLayout det;
 };
 
 struct SweepLayout {
@@ -27,11 +48,32 @@ struct SweepLayout {
 int make_eval_layout(const SysDev& s, int bulk_bytes, int max_smem, EvalLayout& L);
 int make_sweep_layout(const SysDev& s, int bulk_bytes, int max_smem, SweepLayout& L);
 
+// Device workspace of one evaluation of W walkers (bytes, 256-aligned pieces).
+size_t eval_workspace_bytes(const SysDev& s, int bulk_bytes, int W);
+
+// Evaluation of W walkers; ws: eval_workspace_bytes(s, bulk, W) bytes of device memory.
+// *nlaunch receives the number of kernels launched.  If ev is not null, ev[0..4] are recorded
+// on st before the Jastrow kernel and after the Jastrow, orbital, determinant and
+// Jastrow-derivative kernels (the last right after the determinant kernel when it is skipped).
+constexpr int kEvalKernels = 4;
 cudaError_t launch_eval(int precision, const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
-                        double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out,
-                        cudaStream_t st);
+                        double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out, void* ws,
+                        cudaStream_t st, int* nlaunch, cudaEvent_t* ev = nullptr);
 cudaError_t launch_sweep(int precision, const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps,
                          int refresh, const double* state_in, double step, uint64_t seed, uint32_t step0, uint32_t tag,
                          uint32_t woff, int* nacc, cudaStream_t st);
+
+// Per-kernel launchers of the evaluation (eval_jastrow.cu, eval_orbitals.cu, eval_det.cu).
+template <class Tb>
+cudaError_t launch_jastrow(const SysDev& s, const JasLayout& L, int W, const double* R, Tb* JG, Tb* JL, double* JS,
+                           cudaStream_t st);
+template <class Tb>
+cudaError_t launch_jastrow_deriv(const SysDev& s, const JasLayout& L, int W, const double* R, const double* vg, Tb* O,
+                                 Tb* dEL, cudaStream_t st);
+template <class Tb>
+cudaError_t launch_orbitals(const SysDev& s, const OrbLayout& L, int W, const double* R, Tb* OB, double* OD,
+                            cudaStream_t st);
+int make_jas_layout(const SysDev& s, int bulk_bytes, int max_smem, JasLayout& L);
+int make_orb_layout(const SysDev& s, int bulk_bytes, int max_smem, OrbLayout& L);
 
 }  // namespace vbq

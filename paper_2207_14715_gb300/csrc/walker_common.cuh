@@ -1,0 +1,269 @@
+// Device helpers shared by the walker kernels (evaluation kernels and the sweep kernel):
+// basis functions in the bulk type and in float-float, Jastrow radial coefficients, the
+// Slater LU of every unique determinant and the structure sum in the log domain
+// (arXiv:2207.14715, Sec. 2.1).
+#pragma once
+
+#include <algorithm>
+#include <cfloat>
+
+#include "dsfloat.cuh"
+#include "kernels.h"
+#include "wf_device.cuh"
+
+namespace vbq {
+
+namespace {
+
+
+__host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
+// Threads per block the evaluation kernel is compiled for: the double instantiation keeps
+// more live values and runs few walkers per block, so it gets the larger register budget.
+template <class Tb> struct EvalBounds { static constexpr int threads = 512; };
+template <> struct EvalBounds<double> { static constexpr int threads = 256; };
+template <class A, class B> constexpr bool kSameType = false;
+template <class A> constexpr bool kSameType<A, A> = true;
+inline int group_size(int n) {
+  int g = 1;
+  while (g < n) g <<= 1;
+  return g;
+}
+
+template <class Tb> __device__ __forceinline__ const Tb* orb_coefs(const SysDev& s);
+template <> __device__ __forceinline__ const double* orb_coefs<double>(const SysDev& s) { return s.orb_coef; }
+template <> __device__ __forceinline__ const float* orb_coefs<float>(const SysDev& s) { return s.orb_coef_f; }
+template <class Tb> __device__ __forceinline__ const Tb* een_coefs(const SysDev& s);
+template <> __device__ __forceinline__ const double* een_coefs<double>(const SysDev& s) { return s.een_c; }
+template <> __device__ __forceinline__ const float* een_coefs<float>(const SysDev& s) { return s.een_cf; }
+
+// Basis functions (values, or values + gradient + Laplacian) of all shells at point r.
+// Lanes take shells round-robin.  Output arrays are indexed by basis function.
+template <class Tb, bool DERIV>
+__device__ __forceinline__ void basis_at(const SysDev& s, int lane, double x, double y, double z, Tb* bv, Tb* bx,
+                                         Tb* by, Tb* bz, Tb* bl) {
+  for (int sh = lane; sh < s.S; sh += 32) {
+    const double* nu = s.nuc4 + 4 * __ldg(s.sh_center + sh);
+    const int f = __ldg(s.sh_first + sh);
+    gto_shell<Tb, DERIV>(__ldg(s.sh_l + sh), (Tb)__ldg(s.sh_zeta + sh), s.sh_norm + 6 * sh, (Tb)(x - __ldg(nu)),
+                         (Tb)(y - __ldg(nu + 1)), (Tb)(z - __ldg(nu + 2)), bv + f, DERIV ? bx + f : nullptr,
+                         DERIV ? by + f : nullptr, DERIV ? bz + f : nullptr, DERIV ? bl + f : nullptr);
+  }
+}
+
+// Values of all basis functions at point r in float-float (mixed form).  Per center the
+// displacement and r^2 are formed in double and split once; per shell exp(-zeta r^2) and the
+// cartesian factors are float-float.  ctab: [Nn][4] scratch (dx, dy, dz, r^2).
+__device__ __forceinline__ void basis_values_ds(const SysDev& s, int lane, double x, double y, double z, dsf* ctab,
+                                                dsf* out) {
+  for (int c = lane; c < s.Nn; c += 32) {
+    const double* nu = s.nuc4 + 4 * c;
+    const double dx = x - __ldg(nu), dy = y - __ldg(nu + 1), dz = z - __ldg(nu + 2);
+    ctab[4 * c] = ds_from_double(dx);
+    ctab[4 * c + 1] = ds_from_double(dy);
+    ctab[4 * c + 2] = ds_from_double(dz);
+    ctab[4 * c + 3] = ds_from_double(fma(dx, dx, fma(dy, dy, dz * dz)));
+  }
+  __syncwarp();
+  for (int sh = lane; sh < s.S; sh += 32) {
+    const int c = __ldg(s.sh_center + sh), l = __ldg(s.sh_l + sh), f = __ldg(s.sh_first + sh);
+    const float2 zt = __ldg(reinterpret_cast<const float2*>(s.sh_zeta_ds) + sh);
+    dsf e = {1.0f, 0.0f};
+    if (zt.x != 0.0f) e = ds_exp_neg(ds_mul(ctab[4 * c + 3], dsf{zt.x, zt.y}));
+    const float2* nr = reinterpret_cast<const float2*>(s.sh_norm_ds) + 6 * sh;
+    if (l == 0) {
+      const float2 n0 = __ldg(nr);
+      out[f] = ds_mul(dsf{n0.x, n0.y}, e);
+    } else if (l == 1) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float2 nq = __ldg(nr + q);
+        out[f + q] = ds_mul(ds_mul(dsf{nq.x, nq.y}, ctab[4 * c + q]), e);
+      }
+    } else {
+      const int ia[6] = {0, 1, 2, 0, 0, 1};
+      const int ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const float2 nq = __ldg(nr + q);
+        out[f + q] = ds_mul(ds_mul(dsf{nq.x, nq.y}, ds_mul(ctab[4 * c + ia[q]], ctab[4 * c + ib[q]])), e);
+      }
+    }
+  }
+}
+
+// e-n Jastrow/e-e Jastrow coefficient blocks as Tb
+struct PadeCoef {
+  double a1, a2, q[4];
+};
+// 1/x to about 47 bits: float reciprocal refined by one Newton step in double (one division's
+// worth of FP64 work is ~20 instructions on this part; this is 3).
+__device__ __forceinline__ double recip(double x) {
+  double y = (double)__frcp_rn((float)x);
+  return y * fma(-x, y, 2.0);
+}
+
+__device__ __forceinline__ PadeCoef en_coef(const SysDev& s, int a) {
+  const double* p = s.jas_a + 6 * __ldg(s.nuc_elem + a);
+  PadeCoef c;
+  c.a1 = __ldg(p); c.a2 = __ldg(p + 1);
+  for (int q = 0; q < 4; ++q) c.q[q] = __ldg(p + 2 + q);
+  return c;
+}
+__device__ __forceinline__ PadeCoef ee_coef(const SysDev& s, bool same) {
+  PadeCoef c;
+  c.a1 = same ? s.b1_par : s.b1_anti;
+  c.a2 = __ldg(s.jas_b + 1);
+  for (int q = 0; q < 4; ++q) c.q[q] = __ldg(s.jas_b + 2 + q);
+  return c;
+}
+template <class Tb, bool DERIV>
+__device__ __forceinline__ void pade_eval(const PadeCoef& c, Tb r, Tb kap, Tb& f, Tb& df, Tb& d2f) {
+  const Tb q[4] = {(Tb)c.q[0], (Tb)c.q[1], (Tb)c.q[2], (Tb)c.q[3]};
+  pade_poly<Tb, DERIV>(r, kap, (Tb)c.a1, (Tb)c.a2, q, f, df, d2f);
+}
+
+// Lane-group LU + inverse of every unique determinant of spin sp, from orbital values
+// Phi[(e0 + e) * ld + idx[u][o]].  Writes Binv[u], ldet[u], dsg[u] (and, if Lphi is given,
+// t[u] = tr(Binv L_occ) with L read at Lphi[(e0 + e) * ldL + idx[u][o]]).
+template <class TP, class TL>
+__device__ __forceinline__ void lu_all(const SysDev& s, int sp, int lane, const TP* Phi, int ld, const TL* Lphi,
+                                       int ldL, const int* idx, int G, double* Binv, double* scr, double* ldet,
+                                       double* dsg, double* tdet) {
+  const int n = s.n[sp], U = s.U[sp], e0 = sp ? s.Nup : 0;
+  if (n == 0) {
+    for (int u = lane; u < U; u += 32) {
+      ldet[u] = 0.0;
+      dsg[u] = 1.0;
+      if (tdet) tdet[u] = 0.0;
+    }
+    __syncwarp();
+    return;
+  }
+  const int ng = 32 / G, g = lane / G, gl = lane % G;
+  double* A = scr + g * n * n;
+  int* perm = reinterpret_cast<int*>(scr + ng * n * n) + g * n;
+  for (int u0 = 0; u0 < U; u0 += ng) {
+    const int u = u0 + g;
+    const bool act = u < U;
+    if (act)
+      for (int q = gl; q < n * n; q += G) {
+        const int e = q / n, o = q % n;
+        A[q] = (double)Phi[(e0 + e) * ld + __ldg(idx + u * n + o)];
+      }
+    __syncwarp();
+    double lg, sg;
+    double* B = Binv + (act ? u : 0) * n * n;
+    group_lu_inverse(A, B, perm, n, gl, G, act, lg, sg);
+    double t = 0.0;
+    if (tdet && act && gl < n) {
+      const int o = gl, col = __ldg(idx + u * n + o);
+      for (int e = 0; e < n; ++e) t = fma(B[o * n + e], (double)Lphi[(e0 + e) * ldL + col], t);
+    }
+    t = group_sum(t, G);
+    if (act && gl == 0) {
+      ldet[u] = lg;
+      dsg[u] = sg;
+      if (tdet) tdet[u] = t;
+    }
+    __syncwarp();
+  }
+}
+
+// r_k = D_k/Phi for every determinant term and ln|Phi|, sign(Phi) (structure sum in the log
+// domain relative to the largest term, Sec. 2.1).
+__device__ __forceinline__ void term_ratios(const SysDev& s, int lane, const double* ldet, const double* dsg,
+                                            double* rk, double& lnPhi, double& sgnPhi) {
+  const int U0 = s.U[0];
+  double mx = -INFINITY;
+  for (int k = lane; k < s.nterm; k += 32) {
+    const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
+    if (dsg[a] * dsg[U0 + b] != 0.0) mx = fmax(mx, ldet[a] + ldet[U0 + b]);
+  }
+  mx = warp_max(mx);
+  double ph = 0.0;
+  for (int k = lane; k < s.nterm; k += 32) {
+    const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
+    const double sg = dsg[a] * dsg[U0 + b];
+    const double r = (sg != 0.0 && mx > -INFINITY) ? sg * exp(ldet[a] + ldet[U0 + b] - mx) : 0.0;
+    rk[k] = r;
+    ph = fma(__ldg(s.term_coef + k), r, ph);
+  }
+  ph = warp_sum(ph);
+  __syncwarp();
+  const double inv = (ph != 0.0) ? 1.0 / ph : 0.0;
+  for (int k = lane; k < s.nterm; k += 32) rk[k] *= inv;
+  __syncwarp();
+  lnPhi = (ph != 0.0) ? mx + log(fabs(ph)) : -INFINITY;
+  sgnPhi = ph > 0.0 ? 1.0 : (ph < 0.0 ? -1.0 : 0.0);
+}
+
+
+// Per-walker geometry tables for the Jastrow factor (coordinate differences in double, the
+// rest in the bulk type).  Layout of geo (bulk type):
+//   rEE [N][N] r_ij, uEE [N][N] Rbar(r_ij), iEE [N][N] 1/r_ij, eEE [N][N][3] (r_i - r_j)/r_ij,
+//   rEN [N][Nn] r_ia, eEN [N][Nn][3] (r_i - r_a)/r_ia, Stab [Nn][N][6] Rbar(r_ia)^q,
+//   Ssum [Nn][6] sum_i Rbar(r_ia)^q.
+// Returns this lane's share of the Coulomb potential V_ee + V_en.
+template <class Tb> struct GeoTables {
+  Tb *rEE, *uEE, *iEE, *eEE, *rEN, *eEN, *Stab, *Ssum;
+  __device__ __forceinline__ GeoTables(Tb* geo, int N, int Nn) {
+    rEE = geo;
+    uEE = rEE + N * N;
+    iEE = uEE + N * N;
+    eEE = iEE + N * N;
+    rEN = eEE + 3 * N * N;
+    eEN = rEN + N * Nn;
+    Stab = eEN + 3 * N * Nn;
+    Ssum = Stab + 6 * N * Nn;
+  }
+};
+template <class Tb> __host__ __device__ constexpr int geo_elems(int N, int Nn) {
+  return 6 * N * N + 4 * N * Nn + 6 * N * Nn + 6 * Nn;
+}
+
+template <class Tb>
+__device__ __forceinline__ double build_geometry(const SysDev& s, int lane, const double* R, const GeoTables<Tb>& g) {
+  const int N = s.N, Nn = s.Nn;
+  const Tb kap = (Tb)s.kappa;
+  double V_loc = 0.0;
+  for (int p = lane; p < N * N; p += 32) {
+    const int i = p / N, j = p % N;
+    if (i == j) {
+      g.rEE[p] = (Tb)0; g.uEE[p] = (Tb)1; g.iEE[p] = (Tb)0;
+      g.eEE[3 * p] = g.eEE[3 * p + 1] = g.eEE[3 * p + 2] = (Tb)0;
+      continue;
+    }
+    const Tb dx = (Tb)(R[3 * i] - R[3 * j]), dy = (Tb)(R[3 * i + 1] - R[3 * j + 1]), dz = (Tb)(R[3 * i + 2] - R[3 * j + 2]);
+    const Tb r = vsqrt(dx * dx + dy * dy + dz * dz), ir = (Tb)1 / r;
+    g.rEE[p] = r; g.uEE[p] = (Tb)1 / ((Tb)1 + kap * r); g.iEE[p] = ir;
+    g.eEE[3 * p] = dx * ir; g.eEE[3 * p + 1] = dy * ir; g.eEE[3 * p + 2] = dz * ir;
+    if (i < j) V_loc += (double)ir;
+  }
+  for (int p = lane; p < N * Nn; p += 32) {
+    const int i = p / Nn, a = p % Nn;
+    const double* nu = s.nuc4 + 4 * a;
+    const Tb dx = (Tb)(R[3 * i] - __ldg(nu)), dy = (Tb)(R[3 * i + 1] - __ldg(nu + 1)), dz = (Tb)(R[3 * i + 2] - __ldg(nu + 2));
+    const Tb r = vsqrt(dx * dx + dy * dy + dz * dz), ir = (Tb)1 / r;
+    g.rEN[p] = r;
+    g.eEN[3 * p] = dx * ir; g.eEN[3 * p + 1] = dy * ir; g.eEN[3 * p + 2] = dz * ir;
+    V_loc -= __ldg(nu + 3) * (double)ir;
+    const Tb sv = (Tb)1 / ((Tb)1 + kap * r);
+    Tb* St = g.Stab + (a * N + i) * 6;
+    Tb pw = (Tb)1;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) { St[q] = pw; pw *= sv; }
+  }
+  __syncwarp();
+  for (int p = lane; p < Nn * 6; p += 32) {
+    const int a = p / 6, q = p % 6;
+    Tb t = 0;
+    for (int i = 0; i < N; ++i) t += g.Stab[(a * N + i) * 6 + q];
+    g.Ssum[p] = t;
+  }
+  __syncwarp();
+  return V_loc;
+}
+
+}  // namespace
+
+}  // namespace vbq

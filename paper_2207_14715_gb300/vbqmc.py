@@ -52,7 +52,7 @@ class _Desc(ctypes.Structure):
 EXPORTED = ["vbqmc_create", "vbqmc_destroy", "vbqmc_last_error", "vbqmc_set_system", "vbqmc_inspect_system",
             "vbqmc_walker_state_size", "vbqmc_eval_walkers", "vbqmc_vmc_steps", "vbqmc_accumulate_lin_matrices",
             "vbqmc_launch_info", "vbqmc_last_launch_count", "vbqmc_accumulate_lin_matrices_noalloc",
-            "vbqmc_dmc_steps"]
+            "vbqmc_dmc_steps", "vbqmc_set_kernel_timing", "vbqmc_kernel_times"]
 
 _LIB = None
 
@@ -84,6 +84,8 @@ def lib():
                                       ctypes.c_double, _c_dbl_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
                                       ctypes.c_uint32, _c_dbl_p, _c_dbl_p, _c_int_p, _c_dbl_p,
                                       ctypes.POINTER(ctypes.c_int64), vp]
+        L.vbqmc_set_kernel_timing.argtypes = [vp, ctypes.c_int]
+        L.vbqmc_kernel_times.argtypes = [vp, _c_dbl_p, ctypes.c_int, _c_int_p]
         L.vbqmc_accumulate_lin_matrices_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp, vp,
                                                             vp, vp, vp, vp, vp, vp, vp]
         _LIB = L
@@ -260,6 +262,19 @@ class Context:
         hist = {"sum_wE": swe[:ran], "sum_w": sw[:ran], "pop": pop[:ran], "e_trial": etr[:ran],
                 "accepted": int(nacc.value)}
         return W_c.value, et.value, hist
+
+    EVAL_KERNELS = ("jastrow", "orbitals", "det", "jastrow_deriv")
+
+    def set_kernel_timing(self, on=True):
+        """Record CUDA events around each evaluation kernel (vbqmc_set_kernel_timing)."""
+        _check(lib().vbqmc_set_kernel_timing(self.h, 1 if on else 0))
+
+    def kernel_times(self):
+        """ms per evaluation kernel of the last timed evaluation, keyed by EVAL_KERNELS."""
+        ms = np.zeros(len(self.EVAL_KERNELS))
+        n = ctypes.c_int(0)
+        _check(lib().vbqmc_kernel_times(self.h, _dp(ms), len(ms), ctypes.byref(n)))
+        return dict(zip(self.EVAL_KERNELS, ms.tolist()))
 
     def accumulate_lin_matrices(self, precision, O, dEL, eloc, weights=None, stream=None):
         """Linear-method estimators (E0, gL, gR, S, H) from O, dEL [M, P] (mode's bulk type) and
