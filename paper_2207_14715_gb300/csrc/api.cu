@@ -177,6 +177,15 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
     return o;
   };
   const std::vector<float> zeta_ds = split(h.sh_zeta), norm_ds = split(h.sh_norm), coef_ds = split(h.orb_coef);
+  std::vector<double> nuc_xyz;
+  for (size_t a = 0; a < h.nuc4.size() / 4; ++a)
+    for (int d = 0; d < 3; ++d) nuc_xyz.push_back(h.nuc4[4 * a + d]);
+  const std::vector<float> nuc_ds = split(nuc_xyz);
+  std::vector<float> nuc_zf;
+  for (size_t a = 0; a < h.nuc4.size() / 4; ++a) nuc_zf.push_back((float)h.nuc4[4 * a + 3]);
+  const std::vector<float> zeta_f(h.sh_zeta.begin(), h.sh_zeta.end()), norm_f(h.sh_norm.begin(), h.sh_norm.end()),
+      jas_af(h.jas_a.begin(), h.jas_a.end()), jas_bf(h.jas_b.begin(), h.jas_b.end()),
+      een_Bf(h.een_B.begin(), h.een_B.end());
   const size_t o_nuc4 = bb.add(h.nuc4), o_nuc_elem = bb.add(h.nuc_elem), o_sh_center = bb.add(h.sh_center),
                o_sh_l = bb.add(h.sh_l), o_sh_first = bb.add(h.sh_first), o_sh_zeta = bb.add(h.sh_zeta),
                o_sh_norm = bb.add(h.sh_norm), o_orb_lo = bb.add(h.orb_lo), o_orb_hi = bb.add(h.orb_hi),
@@ -191,7 +200,9 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
                o_ke1 = bb.add(h.kap_ent[1]), o_oc0 = bb.add(h.occ_chunk[0]), o_oc1 = bb.add(h.occ_chunk[1]),
                o_oco0 = bb.add(h.occ_chunk_off[0]), o_oco1 = bb.add(h.occ_chunk_off[1]), o_evc = bb.add(h.ev_chunk),
                o_evco = bb.add(h.ev_chunk_off), o_dc = bb.add(h.det_chunk), o_dco = bb.add(h.det_chunk_off),
-               o_zds = bb.add(zeta_ds), o_nds = bb.add(norm_ds), o_cds = bb.add(coef_ds);
+               o_zds = bb.add(zeta_ds), o_nds = bb.add(norm_ds), o_cds = bb.add(coef_ds), o_nucds = bb.add(nuc_ds),
+               o_zf = bb.add(zeta_f), o_nf = bb.add(norm_f), o_jaf = bb.add(jas_af), o_jbf = bb.add(jas_bf),
+               o_ebf = bb.add(een_Bf), o_nzf = bb.add(nuc_zf);
   cudaError_t e = cudaMalloc(&ls.blob, bb.bytes.size());
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(system tables)");
   ls.blob_bytes = bb.bytes.size();
@@ -268,6 +279,16 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.sh_zeta_ds = (const float*)(B + o_zds);
   d.sh_norm_ds = (const float*)(B + o_nds);
   d.orb_coef_ds = (const float*)(B + o_cds);
+  d.nuc_ds = (const float*)(B + o_nucds);
+  d.nuc_zf = (const float*)(B + o_nzf);
+  d.sh_zeta_f = (const float*)(B + o_zf);
+  d.sh_norm_f = (const float*)(B + o_nf);
+  d.jas_af = (const float*)(B + o_jaf);
+  d.jas_bf = (const float*)(B + o_jbf);
+  d.een_Bf = (const float*)(B + o_ebf);
+  d.kappa_f = (float)d.kappa;
+  d.b1_anti_f = (float)d.b1_anti;
+  d.b1_par_f = (float)d.b1_par;
   for (int p = 0; p < 2; ++p) {
     const int tb = p == VBQMC_MIXED ? 4 : 8;
     ls.lay_rc_eval[p] = vbq::make_eval_layout(d, tb, ctx->max_smem, ls.lay_eval[p]);

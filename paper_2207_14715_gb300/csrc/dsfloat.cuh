@@ -51,6 +51,19 @@ __device__ __forceinline__ dsf ds_mul(dsf a, dsf b) {
   p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
   return ds_fast_two_sum(p.hi, p.lo);
 }
+// a + b for a float b (cancellation-safe)
+__device__ __forceinline__ dsf ds_add_f(dsf a, float b) {
+  dsf s = ds_two_sum(a.hi, b);
+  s.lo += a.lo;
+  return ds_fast_two_sum(s.hi, s.lo);
+}
+// a - b rounded to float (within one rounding of the exact difference): the difference of the
+// high parts is exact through TwoSum, the low parts only add a small correction.
+__device__ __forceinline__ float ds_diff_f(dsf a, dsf b) {
+  const dsf d = ds_two_sum(a.hi, -b.hi);
+  return d.hi + (d.lo + (a.lo - b.lo));
+}
+__device__ __forceinline__ dsf ds_neg(dsf a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ dsf ds_from_double(double x) {
   const float h = (float)x;
   return {h, (float)(x - (double)h)};

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
   double* Tdet = reinterpret_cast<double*>(base + L.Tdet);
   double* rk = reinterpret_cast<double*>(base + L.rk);
   unsigned char* scr = base + L.scratch;
-  double* kacc = reinterpret_cast<double*>(base + L.kacc);
+  Tb* kacc = reinterpret_cast<Tb*>(base + L.kacc);
 
   const int N = s.N, Nup = s.Nup, U0 = s.U[0];
   const int nev = s.n_ev, nevd = s.n_ev_det;
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
   //   K[Phi_kappa] = sum_u (T_u x_u + W_u y_u), E_L,kappa = -1/2 (K[Phi_kappa] - O K[Phi]).
   if (s.n_kappa > 0) {
     const int nk = s.n_kappa;
-    for (int q = lane; q < 2 * nk; q += 32) kacc[q] = 0.0;
+    for (int q = lane; q < 2 * nk; q += 32) kacc[q] = (Tb)0;
     __syncwarp();
     Tb* X = reinterpret_cast<Tb*>(scr);
     for (int sp = 0; sp < 2; ++sp) {
@@ -248,23 +248,23 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
           Y[q] = y;
         }
         __syncwarp();
-        const double Wu = Wdet[uo + u], Tu = Tdet[uo + u];
+        const Tb Wu = (Tb)Wdet[uo + u], Tu = (Tb)Tdet[uo + u];
         for (int t = eb + lane; t < ee; t += 32) {
           const int j = __ldg(s.kap_ent[sp] + 4 * t), ol = __ldg(s.kap_ent[sp] + 4 * t + 1),
                     kc = __ldg(s.kap_ent[sp] + 4 * t + 2);
           const Tb x = X[ol * nev + kc];
           Tb y = Y[ol * nev + kc];
           for (int o2 = 0; o2 < n; ++o2) y -= Y[ol * nev + __ldg(s.det_ev[sp] + u * n + o2)] * X[o2 * nev + kc];
-          kacc[j] += Wu * (double)x;
-          kacc[nk + j] += Tu * (double)x + Wu * (double)y;
+          kacc[j] += Wu * x;
+          kacc[nk + j] += Tu * x + Wu * y;
         }
         __syncwarp();
       }
     }
     for (int j = lane; j < nk; j += 32) {
-      const double o = kacc[j];
-      Ow[s.p_off_kappa + j] = (Tb)(o);
-      if (Ew) Ew[s.p_off_kappa + j] = (Tb)(-0.5 * (kacc[nk + j] - o * kphi));
+      const Tb o = kacc[j];
+      Ow[s.p_off_kappa + j] = o;
+      if (Ew) Ew[s.p_off_kappa + j] = (Tb)-0.5 * (kacc[nk + j] - o * (Tb)kphi);
     }
   }
 }

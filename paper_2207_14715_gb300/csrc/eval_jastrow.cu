@@ -14,6 +14,21 @@ namespace {
 template <class Tb> struct JasBounds { static constexpr int min_blocks = 2; };
 template <> struct JasBounds<double> { static constexpr int min_blocks = 1; };
 
+// Per-lane sum of ln J terms: double in the FP64 form, float-float in the mixed form (the
+// value enters ln|Psi|, so it keeps about double accuracy without double instructions).
+template <class Tb> struct LnSum {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add(const LnSum& o) { v += o.v; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <> struct LnSum<float> {
+  dsf v = {0.0f, 0.0f};
+  __device__ __forceinline__ void add(float x) { v = ds_add_f(v, x); }
+  __device__ __forceinline__ void add(const LnSum& o) { v = ds_add(v, o.v); }
+  __device__ __forceinline__ double value() const { return ds_to_double(v); }
+};
+
 // lanes -> (electron i, group g); group g takes nuclei a = g, g + S, ... and partners
 // j = g, g + S, ...
 template <class Tb>
@@ -26,28 +41,26 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_kernel
   const int w = blockIdx.x * L.wpb + wl;
   if (w >= W) return;
   unsigned char* base = smem + wl * L.warp_bytes;
-  double* R = reinterpret_cast<double*>(base + L.R);
   const int N = s.N, Nn = s.Nn, Nup = s.Nup;
   const GeoTables<Tb> g(reinterpret_cast<Tb*>(base + L.geo), N, Nn);
   const Tb kap = (Tb)s.kappa;
-  for (int i = lane; i < 3 * N; i += 32) R[i] = Rg[(size_t)w * 3 * N + i];
-  __syncwarp();
-  double V_loc = build_geometry<Tb>(s, lane, R, g);
-  double lnJ_loc = 0.0;
+  const Coords<Tb> C = load_coords<Tb>(Rg + (size_t)w * 3 * N, N, lane, base + L.R);
+  const double V_loc = build_geometry<Tb>(s, lane, C, g);
+  LnSum<Tb> lnJ_loc;
   const Tb* cE = een_coefs<Tb>(s);
   const int Pp = L.jas_P, Sg = L.jas_S;
   for (int b0 = 0; b0 < N; b0 += Pp) {
     const int i = b0 + lane % Pp, gr = lane / Pp;
     const bool act = i < N;
     Tb g0 = 0, g1 = 0, g2 = 0, lap = 0;
-    double lnj = 0.0;
+    LnSum<Tb> lnj;
     if (act) {
       for (int a = gr; a < Nn; a += Sg) {
         const int ia = i * Nn + a;
         const Tb r = g.rEN[ia];
         Tb f, df, d2f;
-        pade_eval<Tb, true>(en_coef(s, a), r, kap, f, df, d2f);
-        lnj += (double)f;
+        pade_eval<Tb, true>(en_coef_t<Tb>(s, a), r, kap, f, df, d2f);
+        lnj.add(f);
         g0 += df * g.eEN[3 * ia]; g1 += df * g.eEN[3 * ia + 1]; g2 += df * g.eEN[3 * ia + 2];
         lap += d2f + (Tb)2 * df / r;
       }
@@ -55,8 +68,8 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_kernel
         if (j == i) continue;
         const int ij = i * N + j;
         Tb f, df, d2f;
-        pade_eval<Tb, true>(ee_coef(s, (i < Nup) == (j < Nup)), g.rEE[ij], kap, f, df, d2f);
-        lnj += 0.5 * (double)f;
+        pade_eval<Tb, true>(ee_coef_t<Tb>(s, (i < Nup) == (j < Nup)), g.rEE[ij], kap, f, df, d2f);
+        lnj.add((Tb)0.5 * f);
         g0 += df * g.eEE[3 * ij]; g1 += df * g.eEE[3 * ij + 1]; g2 += df * g.eEE[3 * ij + 2];
         lap += d2f + (Tb)2 * df * g.iEE[ij];
       }
@@ -69,7 +82,7 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_kernel
           const Tb ex = g.eEN[3 * ia], ey = g.eEN[3 * ia + 1], ez = g.eEN[3 * ia + 2];
           auto sink = [&](int t, Tb val, Tb gx, Tb gy, Tb gz, Tb lp) {
             const Tb ct = c[t];
-            lnj += (double)(ct * val);
+            lnj.add(ct * val);
             g0 += ct * gx; g1 += ct * gy; g2 += ct * gz;
             lap += ct * lp;
           };
@@ -96,7 +109,7 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_kernel
             een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, sink);
           }
         }
-      lnJ_loc += lnj;
+      lnJ_loc.add(lnj);
     }
     for (int o = Pp; o < 32; o <<= 1) {
       g0 += __shfl_xor_sync(kFull, g0, o);
@@ -110,7 +123,7 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_kernel
       JL[(size_t)w * N + i] = lap;
     }
   }
-  const double lnJ = warp_sum(lnJ_loc);
+  const double lnJ = warp_sum(lnJ_loc.value());
   const double V = warp_sum(V_loc) + s.vnn;
   if (lane == 0) {
     JS[2 * (size_t)w] = lnJ;
@@ -157,18 +170,14 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_deriv_
   const int w = blockIdx.x * L.wpb + wl;
   if (w >= W) return;
   unsigned char* base = smem + wl * L.warp_bytes;
-  double* R = reinterpret_cast<double*>(base + L.R);
-  double* vg = reinterpret_cast<double*>(base + L.vg);
-  double* red = reinterpret_cast<double*>(base + L.red);
+  Tb* vg = reinterpret_cast<Tb*>(base + L.vg);  // grad ln|Psi| in the bulk type
+  Tb* red = reinterpret_cast<Tb*>(base + L.red);
   const int N = s.N, Nn = s.Nn, Nup = s.Nup;
   const GeoTables<Tb> g(reinterpret_cast<Tb*>(base + L.geo), N, Nn);
   const Tb kap = (Tb)s.kappa;
-  for (int i = lane; i < 3 * N; i += 32) {
-    R[i] = Rg[(size_t)w * 3 * N + i];
-    vg[i] = vgg[(size_t)w * 3 * N + i];
-  }
-  __syncwarp();
-  build_geometry<Tb>(s, lane, R, g);
+  for (int i = lane; i < 3 * N; i += 32) vg[i] = (Tb)vgg[(size_t)w * 3 * N + i];
+  const Coords<Tb> C = load_coords<Tb>(Rg + (size_t)w * 3 * N, N, lane, base + L.R);
+  build_geometry<Tb>(s, lane, C, g);
   const int P = s.P;
   Tb* Ow = Og + (size_t)w * P;
   Tb* Ew = dELg ? dELg + (size_t)w * P : nullptr;
@@ -179,11 +188,10 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_deriv_
       const int i = t / Nn, a = t % Nn;
       if (__ldg(s.nuc_elem + a) != E) continue;
       const Tb r = g.rEN[t];
-      const PadeCoef c = en_coef(s, a);
-      const Tb cosv = g.eEN[3 * t] * (Tb)vg[3 * i] + g.eEN[3 * t + 1] * (Tb)vg[3 * i + 1] +
-                      g.eEN[3 * t + 2] * (Tb)vg[3 * i + 2];
+      const PadeT<Tb> c = en_coef_t<Tb>(s, a);
+      const Tb cosv = g.eEN[3 * t] * vg[3 * i] + g.eEN[3 * t + 1] * vg[3 * i + 1] + g.eEN[3 * t + 2] * vg[3 * i + 2];
       Tb h[5], g1[5], g2[5];
-      pade_param_derivs<Tb>(r, kap, (Tb)c.a1, (Tb)c.a2, h, g1, g2);
+      pade_param_derivs<Tb>(r, kap, c.a1, c.a2, h, g1, g2);
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
         aO[q] += h[q];
@@ -192,10 +200,10 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_deriv_
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      const double o = warp_sum((double)aO[q]), e = warp_sum((double)aE[q]);
+      const Tb o = warp_sum(aO[q]), e = warp_sum(aE[q]);
       if (lane == 0) {
-        Ow[s.p_off_a + 5 * E + q] = (Tb)(o);
-        if (Ew) Ew[s.p_off_a + 5 * E + q] = (Tb)(e);
+        Ow[s.p_off_a + 5 * E + q] = o;
+        if (Ew) Ew[s.p_off_a + 5 * E + q] = e;
       }
     }
   }
@@ -208,11 +216,11 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_deriv_
       while (rem >= N - 1 - i) { rem -= N - 1 - i; ++i; }
       const int j = i + 1 + rem, ij = i * N + j;
       const Tb r = g.rEE[ij];
-      const PadeCoef c = ee_coef(s, (i < Nup) == (j < Nup));
-      const Tb cosv = g.eEE[3 * ij] * (Tb)(vg[3 * i] - vg[3 * j]) + g.eEE[3 * ij + 1] * (Tb)(vg[3 * i + 1] - vg[3 * j + 1]) +
-                      g.eEE[3 * ij + 2] * (Tb)(vg[3 * i + 2] - vg[3 * j + 2]);
+      const PadeT<Tb> c = ee_coef_t<Tb>(s, (i < Nup) == (j < Nup));
+      const Tb cosv = g.eEE[3 * ij] * (vg[3 * i] - vg[3 * j]) + g.eEE[3 * ij + 1] * (vg[3 * i + 1] - vg[3 * j + 1]) +
+                      g.eEE[3 * ij + 2] * (vg[3 * i + 2] - vg[3 * j + 2]);
       Tb h[5], g1[5], g2[5];
-      pade_param_derivs<Tb>(r, kap, (Tb)c.a1, (Tb)c.a2, h, g1, g2);
+      pade_param_derivs<Tb>(r, kap, c.a1, c.a2, h, g1, g2);
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
         bO[q] += h[q];
@@ -221,18 +229,18 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_deriv_
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      const double o = warp_sum((double)bO[q]), e = warp_sum((double)bE[q]);
+      const Tb o = warp_sum(bO[q]), e = warp_sum(bE[q]);
       if (lane == 0) {
-        Ow[s.p_off_b + q] = (Tb)(o);
-        if (Ew) Ew[s.p_off_b + q] = (Tb)(e);
+        Ow[s.p_off_b + q] = o;
+        if (Ew) Ew[s.p_off_b + q] = e;
       }
     }
   }
   // e-e-n: per element, the raw-term derivatives from the pair sums (lane -> (electron i,
   // group g), nuclei of the element split among groups), then theta = B^T raw
   if (s.een_on) {
-    double* rawO = red;          // [23]
-    double* rawE = red + kNeen;  // [23]
+    Tb* rawO = red;          // [23]
+    Tb* rawE = red + kNeen;  // [23]
     const int Pp = L.jas_P, Sg = L.jas_S;
     for (int E = 0; E < s.n_elem; ++E) {
       Tb accO[kNeen], accE[kNeen];
@@ -241,7 +249,7 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_deriv_
       for (int b0 = 0; b0 < N; b0 += Pp) {
         const int i = b0 + lane % Pp, gr = lane / Pp;
         if (i >= N) continue;
-        const Tb vx = (Tb)vg[3 * i], vy = (Tb)vg[3 * i + 1], vz = (Tb)vg[3 * i + 2];
+        const Tb vx = vg[3 * i], vy = vg[3 * i + 1], vz = vg[3 * i + 2];
         for (int a = gr; a < Nn; a += Sg) {
           if (__ldg(s.nuc_elem + a) != E) continue;
           const int ia = i * Nn + a;
@@ -278,22 +286,23 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_deriv_
       }
 #pragma unroll
       for (int q = 0; q < kNeen; ++q) {
-        const double o = warp_sum((double)accO[q]), e = warp_sum((double)accE[q]);
+        const Tb o = warp_sum(accO[q]), e = warp_sum(accE[q]);
         if (lane == 0) {
           rawO[q] = o;
           rawE[q] = e;
         }
       }
       __syncwarp();
+      const Tb* Bmat = een_basis_t<Tb>(s);
       for (int f = lane; f < kNfree; f += 32) {
-        double o = 0.0, e = 0.0;
+        Tb o = 0, e = 0;
         for (int q = 0; q < kNeen; ++q) {
-          const double b = __ldg(s.een_B + q * kNfree + f);
-          o = fma(b, rawO[q], o);
-          e = fma(b, rawE[q], e);
+          const Tb b = __ldg(Bmat + q * kNfree + f);
+          o += b * rawO[q];
+          e += b * rawE[q];
         }
-        Ow[s.p_off_theta + kNfree * E + f] = (Tb)(o);
-        if (Ew) Ew[s.p_off_theta + kNfree * E + f] = (Tb)(e);
+        Ow[s.p_off_theta + kNfree * E + f] = o;
+        if (Ew) Ew[s.p_off_theta + kNfree * E + f] = e;
       }
       __syncwarp();
     }

@@ -36,10 +36,14 @@ __global__ void __launch_bounds__(32 * kOrbWarps, 4) orbital_kernel(const SysDev
   Tb* part = reinterpret_cast<Tb*>(base + L.part);
   dsf* partds = reinterpret_cast<dsf*>(base + L.partd);
   const double* r = Rg + (size_t)gw * 3;
-  const double x = r[0], y = r[1], z = r[2];
   const Tb* cf = orb_coefs<Tb>(s);
-  basis_at<Tb, true>(s, lane, x, y, z, bv, bx, by, bz, bl);
-  if (!kSameType<Tb, double>) basis_values_ds(s, lane, x, y, z, ctab, bds);
+  if constexpr (kSameType<Tb, double>) {
+    basis_at<double, true>(s, lane, r[0], r[1], r[2], bv, bx, by, bz, bl);
+  } else {
+    const dsf r3[3] = {ds_from_double(r[0]), ds_from_double(r[1]), ds_from_double(r[2])};
+    basis_at_f<true>(s, lane, r3, bv, bx, by, bz, bl);
+    basis_values_ds(s, lane, r3, ctab, bds);
+  }
   __syncwarp();
   for (int c = lane; c < s.n_ev_chunk; c += 32) {
     const int4 ch = __ldg(reinterpret_cast<const int4*>(s.ev_chunk) + c);

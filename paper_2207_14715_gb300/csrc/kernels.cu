@@ -54,17 +54,25 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const Swe
   const Tb* cf = orb_coefs<Tb>(s);
   const Tb* cE = een_coefs<Tb>(s);
   for (int i = lane; i < 3 * N; i += 32) R[i] = Rg[(size_t)w * 3 * N + i];
+  // positions as the bulk-type arithmetic reads them (float-float copies in the mixed form)
+  dsf* Rds = reinterpret_cast<dsf*>(base + L.Rds);
+  Coords<Tb> C;
+  if constexpr (kSameType<Tb, double>) {
+    C.R = R;
+  } else {
+    for (int i = lane; i < 3 * N; i += 32) Rds[i] = ds_from_double(Rg[(size_t)w * 3 * N + i]);
+    C.R = Rds;
+  }
   __syncwarp();
-  // geometry tables (coordinate differences in double, the rest in the bulk type)
+  // geometry tables
   for (int p = lane; p < N * N; p += 32) {
     const int i = p / N, j = p % N;
-    const Tb dx = (Tb)(R[3 * i] - R[3 * j]), dy = (Tb)(R[3 * i + 1] - R[3 * j + 1]), dz = (Tb)(R[3 * i + 2] - R[3 * j + 2]);
+    const Tb dx = C.ee(i, j, 0), dy = C.ee(i, j, 1), dz = C.ee(i, j, 2);
     rEE[p] = i == j ? (Tb)0 : vsqrt(dx * dx + dy * dy + dz * dz);
   }
   for (int p = lane; p < N * Nn; p += 32) {
     const int i = p / Nn, a = p % Nn;
-    const double* nu = s.nuc4 + 4 * a;
-    const Tb dx = (Tb)(R[3 * i] - __ldg(nu)), dy = (Tb)(R[3 * i + 1] - __ldg(nu + 1)), dz = (Tb)(R[3 * i + 2] - __ldg(nu + 2));
+    const Tb dx = C.en(s, i, a, 0), dy = C.en(s, i, a, 1), dz = C.en(s, i, a, 2);
     const Tb r = vsqrt(dx * dx + dy * dy + dz * dz);
     rEN[p] = r;
     const Tb sv = (Tb)1 / ((Tb)1 + kap * r);
@@ -131,8 +139,26 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const Swe
       rn[0] = __dadd_rn(R[3 * e], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u0), 1.0)));
       rn[1] = __dadd_rn(R[3 * e + 1], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u1), 1.0)));
       rn[2] = __dadd_rn(R[3 * e + 2], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u2), 1.0)));
+      // the proposed position as the bulk-type arithmetic reads it
+      dsf rnd[3];
+      if constexpr (!kSameType<Tb, double>) {
+        rnd[0] = ds_from_double(rn[0]);
+        rnd[1] = ds_from_double(rn[1]);
+        rnd[2] = ds_from_double(rn[2]);
+      }
+      auto dnew_e = [&](int j, int d) -> Tb {  // proposed position minus electron j
+        if constexpr (kSameType<Tb, double>) return (Tb)(rn[d] - R[3 * j + d]);
+        else return ds_diff_f(rnd[d], Rds[3 * j + d]);
+      };
+      auto dnew_n = [&](int a, int d) -> Tb {  // proposed position minus nucleus a
+        if constexpr (kSameType<Tb, double>) return (Tb)(rn[d] - __ldg(s.nuc4 + 4 * a + d));
+        else return ds_diff_f(rnd[d], nuc_coord_ds(s, a, d));
+      };
       // orbital row at the proposed position (bulk type), contraction in balanced chunks
-      basis_at<Tb, false>(s, lane, rn[0], rn[1], rn[2], bas, nullptr, nullptr, nullptr, nullptr);
+      if constexpr (kSameType<Tb, double>)
+        basis_at<double, false>(s, lane, rn[0], rn[1], rn[2], bas, nullptr, nullptr, nullptr, nullptr);
+      else
+        basis_at_f<false>(s, lane, rnd, bas, nullptr, nullptr, nullptr, nullptr);
       __syncwarp();
       for (int c = lane; c < s.n_occ_chunk[sp]; c += 32) {
         const int4 ch = __ldg(reinterpret_cast<const int4*>(s.occ_chunk[sp]) + c);
@@ -167,7 +193,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const Swe
       // proposed position, then items e-n (a), e-e (j) and e-e-n (a, k), the last through the
       // pair sums Y^{k,q} = sum_{j != e} u_ej^k s_j^q (the terms of e are s_e^A Y^{k,B} + s_e^B Y^{k,A}).
       for (int j = lane; j < N; j += 32) {
-        const Tb dx = (Tb)(rn[0] - R[3 * j]), dy = (Tb)(rn[1] - R[3 * j + 1]), dz = (Tb)(rn[2] - R[3 * j + 2]);
+        const Tb dx = dnew_e(j, 0), dy = dnew_e(j, 1), dz = dnew_e(j, 2);
         const Tb rnew = j == e ? (Tb)0 : vsqrt(dx * dx + dy * dy + dz * dz);
         rnE[j] = rnew;
         const Tb uo = (Tb)1 / ((Tb)1 + kap * rEE[e * N + j]), un = (Tb)1 / ((Tb)1 + kap * rnew);
@@ -181,8 +207,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const Swe
         }
       }
       for (int a = lane; a < Nn; a += 32) {
-        const double* nu = s.nuc4 + 4 * a;
-        const Tb dx = (Tb)(rn[0] - __ldg(nu)), dy = (Tb)(rn[1] - __ldg(nu + 1)), dz = (Tb)(rn[2] - __ldg(nu + 2));
+        const Tb dx = dnew_n(a, 0), dy = dnew_n(a, 1), dz = dnew_n(a, 2);
         const Tb r = vsqrt(dx * dx + dy * dy + dz * dz);
         rnN[a] = r;
         const Tb sv = (Tb)1 / ((Tb)1 + kap * r);
@@ -195,7 +220,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const Swe
       const int nitem = Nn + N + (s.een_on ? 5 * Nn : 0);
       for (int t = lane; t < nitem; t += 32) {
         if (t < Nn) {
-          const PadeCoef c = en_coef(s, t);
+          const PadeT<Tb> c = en_coef_t<Tb>(s, t);
           Tb f1, f0, t0, t1;
           pade_eval<Tb, false>(c, rnN[t], kap, f1, t0, t1);
           pade_eval<Tb, false>(c, rEN[e * Nn + t], kap, f0, t0, t1);
@@ -203,7 +228,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const Swe
         } else if (t < Nn + N) {
           const int j = t - Nn;
           if (j == e) continue;
-          const PadeCoef c = ee_coef(s, (e < Nup) == (j < Nup));
+          const PadeT<Tb> c = ee_coef_t<Tb>(s, (e < Nup) == (j < Nup));
           Tb f1, f0, t0, t1;
           pade_eval<Tb, false>(c, rnE[j], kap, f1, t0, t1);
           pade_eval<Tb, false>(c, rEE[e * N + j], kap, f0, t0, t1);
@@ -257,7 +282,10 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const Swe
         }
         const double irphi = recip(rphi);
         for (int k = lane; k < s.nterm; k += 32) wk[k] *= rho[__ldg(s.term_det + 2 * k + sp)] * irphi;
-        if (lane < 3) R[3 * e + lane] = rn[lane];
+        if (lane < 3) {
+          R[3 * e + lane] = lane == 0 ? rn[0] : (lane == 1 ? rn[1] : rn[2]);
+          if constexpr (!kSameType<Tb, double>) Rds[3 * e + lane] = lane == 0 ? rnd[0] : (lane == 1 ? rnd[1] : rnd[2]);
+        }
         for (int j = lane; j < N; j += 32) rEE[e * N + j] = rEE[j * N + e] = rnE[j];
         for (int a = lane; a < Nn; a += 32) {
           rEN[e * Nn + a] = rnN[a];
@@ -288,6 +316,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.G1 = group_size(s.n[1]);
   L.nocc_max = std::max(std::max(s.nocc[0], s.nocc[1]), 1);
   L.R = take(8 * 3 * N);
+  L.Rds = take(tb == 4 ? 8 * 3 * N : 16);
   L.Binv0 = take(8 * s.U[0] * s.n[0] * s.n[0]);
   L.Binv1 = take(8 * s.U[1] * s.n[1] * s.n[1]);
   L.ldet = take(8 * Ut);

@@ -123,6 +123,15 @@ struct SysDev {
   const float* sh_zeta_ds;             // [S][2]
   const float* sh_norm_ds;             // [S][6][2]
   const float* orb_coef_ds;            // like orb_coef, [.][2]
+  const float* nuc_ds;                 // [Nn][3][2] nucleus coordinates
+  const float* nuc_zf;                 // [Nn] nuclear charges
+  // float copies for the mixed form's bulk arithmetic
+  const float* sh_zeta_f;              // [S]
+  const float* sh_norm_f;              // [S][6]
+  const float* jas_af;                 // like jas_a
+  const float* jas_bf;                 // like jas_b
+  const float* een_Bf;                 // like een_B
+  float kappa_f, b1_anti_f, b1_par_f;
 };
 
 // Records the calling thread's error message (read by vbqmc_last_error) and returns 'code';

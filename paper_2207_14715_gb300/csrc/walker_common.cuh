@@ -32,6 +32,9 @@ inline int group_size(int n) {
 template <class Tb> __device__ __forceinline__ const Tb* orb_coefs(const SysDev& s);
 template <> __device__ __forceinline__ const double* orb_coefs<double>(const SysDev& s) { return s.orb_coef; }
 template <> __device__ __forceinline__ const float* orb_coefs<float>(const SysDev& s) { return s.orb_coef_f; }
+template <class Tb> __device__ __forceinline__ const Tb* een_basis_t(const SysDev& s);
+template <> __device__ __forceinline__ const double* een_basis_t<double>(const SysDev& s) { return s.een_B; }
+template <> __device__ __forceinline__ const float* een_basis_t<float>(const SysDev& s) { return s.een_Bf; }
 template <class Tb> __device__ __forceinline__ const Tb* een_coefs(const SysDev& s);
 template <> __device__ __forceinline__ const double* een_coefs<double>(const SysDev& s) { return s.een_c; }
 template <> __device__ __forceinline__ const float* een_coefs<float>(const SysDev& s) { return s.een_cf; }
@@ -50,18 +53,39 @@ __device__ __forceinline__ void basis_at(const SysDev& s, int lane, double x, do
   }
 }
 
-// Values of all basis functions at point r in float-float (mixed form).  Per center the
-// displacement and r^2 are formed in double and split once; per shell exp(-zeta r^2) and the
+// The same in the mixed form from a point given in float-float (r3[0..2]): the displacement
+// from each center is rounded to float from its float-float value, and shell exponents and
+// normalisations are float, so no double-precision instruction is issued per shell.
+__device__ __forceinline__ dsf nuc_coord_ds(const SysDev& s, int a, int d) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(s.nuc_ds) + 3 * a + d);
+  return dsf{v.x, v.y};
+}
+template <bool DERIV>
+__device__ __forceinline__ void basis_at_f(const SysDev& s, int lane, const dsf* r3, float* bv, float* bx, float* by,
+                                           float* bz, float* bl) {
+  for (int sh = lane; sh < s.S; sh += 32) {
+    const int c = __ldg(s.sh_center + sh);
+    const int f = __ldg(s.sh_first + sh);
+    const float dx = ds_diff_f(r3[0], nuc_coord_ds(s, c, 0)), dy = ds_diff_f(r3[1], nuc_coord_ds(s, c, 1)),
+                dz = ds_diff_f(r3[2], nuc_coord_ds(s, c, 2));
+    gto_shell<float, DERIV>(__ldg(s.sh_l + sh), __ldg(s.sh_zeta_f + sh), s.sh_norm_f + 6 * sh, dx, dy, dz, bv + f,
+                            DERIV ? bx + f : nullptr, DERIV ? by + f : nullptr, DERIV ? bz + f : nullptr,
+                            DERIV ? bl + f : nullptr);
+  }
+}
+
+// Values of all basis functions at the point r3 (float-float) in float-float (mixed form).
+// Per center the displacement and r^2 are float-float; per shell exp(-zeta r^2) and the
 // cartesian factors are float-float.  ctab: [Nn][4] scratch (dx, dy, dz, r^2).
-__device__ __forceinline__ void basis_values_ds(const SysDev& s, int lane, double x, double y, double z, dsf* ctab,
-                                                dsf* out) {
+__device__ __forceinline__ void basis_values_ds(const SysDev& s, int lane, const dsf* r3, dsf* ctab, dsf* out) {
   for (int c = lane; c < s.Nn; c += 32) {
-    const double* nu = s.nuc4 + 4 * c;
-    const double dx = x - __ldg(nu), dy = y - __ldg(nu + 1), dz = z - __ldg(nu + 2);
-    ctab[4 * c] = ds_from_double(dx);
-    ctab[4 * c + 1] = ds_from_double(dy);
-    ctab[4 * c + 2] = ds_from_double(dz);
-    ctab[4 * c + 3] = ds_from_double(fma(dx, dx, fma(dy, dy, dz * dz)));
+    const dsf dx = ds_add(r3[0], ds_neg(nuc_coord_ds(s, c, 0)));
+    const dsf dy = ds_add(r3[1], ds_neg(nuc_coord_ds(s, c, 1)));
+    const dsf dz = ds_add(r3[2], ds_neg(nuc_coord_ds(s, c, 2)));
+    ctab[4 * c] = dx;
+    ctab[4 * c + 1] = dy;
+    ctab[4 * c + 2] = dz;
+    ctab[4 * c + 3] = ds_add_nc(ds_add_nc(ds_mul(dx, dx), ds_mul(dy, dy)), ds_mul(dz, dz));
   }
   __syncwarp();
   for (int sh = lane; sh < s.S; sh += 32) {
@@ -95,6 +119,32 @@ __device__ __forceinline__ void basis_values_ds(const SysDev& s, int lane, doubl
 struct PadeCoef {
   double a1, a2, q[4];
 };
+// the same in the bulk type, loaded from the bulk-type tables (no conversion per use)
+template <class Tb> struct PadeT {
+  Tb a1, a2, q[4];
+};
+template <class Tb> __device__ __forceinline__ PadeT<Tb> en_coef_t(const SysDev& s, int a);
+template <class Tb> __device__ __forceinline__ PadeT<Tb> ee_coef_t(const SysDev& s, bool same);
+template <class Tb> __device__ __forceinline__ PadeT<Tb> load_pade(const Tb* p, Tb a1) {
+  PadeT<Tb> c;
+  c.a1 = a1; c.a2 = __ldg(p + 1);
+  for (int q = 0; q < 4; ++q) c.q[q] = __ldg(p + 2 + q);
+  return c;
+}
+template <> __device__ __forceinline__ PadeT<double> en_coef_t<double>(const SysDev& s, int a) {
+  const double* p = s.jas_a + 6 * __ldg(s.nuc_elem + a);
+  return load_pade<double>(p, __ldg(p));
+}
+template <> __device__ __forceinline__ PadeT<float> en_coef_t<float>(const SysDev& s, int a) {
+  const float* p = s.jas_af + 6 * __ldg(s.nuc_elem + a);
+  return load_pade<float>(p, __ldg(p));
+}
+template <> __device__ __forceinline__ PadeT<double> ee_coef_t<double>(const SysDev& s, bool same) {
+  return load_pade<double>(s.jas_b, same ? s.b1_par : s.b1_anti);
+}
+template <> __device__ __forceinline__ PadeT<float> ee_coef_t<float>(const SysDev& s, bool same) {
+  return load_pade<float>(s.jas_bf, same ? s.b1_par_f : s.b1_anti_f);
+}
 // 1/x to about 47 bits: float reciprocal refined by one Newton step in double (one division's
 // worth of FP64 work is ~20 instructions on this part; this is 3).
 __device__ __forceinline__ double recip(double x) {
@@ -115,6 +165,10 @@ __device__ __forceinline__ PadeCoef ee_coef(const SysDev& s, bool same) {
   c.a2 = __ldg(s.jas_b + 1);
   for (int q = 0; q < 4; ++q) c.q[q] = __ldg(s.jas_b + 2 + q);
   return c;
+}
+template <class Tb, bool DERIV>
+__device__ __forceinline__ void pade_eval(const PadeT<Tb>& c, Tb r, Tb kap, Tb& f, Tb& df, Tb& d2f) {
+  pade_poly<Tb, DERIV>(r, kap, c.a1, c.a2, c.q, f, df, d2f);
 }
 template <class Tb, bool DERIV>
 __device__ __forceinline__ void pade_eval(const PadeCoef& c, Tb r, Tb kap, Tb& f, Tb& df, Tb& d2f) {
@@ -221,11 +275,47 @@ template <class Tb> __host__ __device__ constexpr int geo_elems(int N, int Nn) {
   return 6 * N * N + 4 * N * Nn + 6 * N * Nn + 6 * Nn;
 }
 
+// Electron coordinates of one walker as the kernels read them: double in the FP64 form;
+// float-float in the mixed form, so that differences come out rounded to float without a
+// double-precision instruction per pair.
+template <class Tb> struct Coords {
+  const double* R;  // [N][3]
+  __device__ __forceinline__ Tb ee(int i, int j, int d) const { return (Tb)(R[3 * i + d] - R[3 * j + d]); }
+  __device__ __forceinline__ Tb en(const SysDev& s, int i, int a, int d) const {
+    return (Tb)(R[3 * i + d] - __ldg(s.nuc4 + 4 * a + d));
+  }
+  __device__ __forceinline__ Tb charge(const SysDev& s, int a) const { return (Tb)__ldg(s.nuc4 + 4 * a + 3); }
+};
+template <> struct Coords<float> {
+  const dsf* R;  // [N][3]
+  __device__ __forceinline__ float ee(int i, int j, int d) const { return ds_diff_f(R[3 * i + d], R[3 * j + d]); }
+  __device__ __forceinline__ float en(const SysDev& s, int i, int a, int d) const {
+    return ds_diff_f(R[3 * i + d], nuc_coord_ds(s, a, d));
+  }
+  __device__ __forceinline__ float charge(const SysDev& s, int a) const { return __ldg(s.nuc_zf + a); }
+};
+// Loads a walker's coordinates from global memory (double [N][3]) into the form of Coords<Tb>
+// at dst (shared memory, 3N doubles or 3N float pairs).
+template <class Tb> __device__ __forceinline__ Coords<Tb> load_coords(const double* Rg, int N, int lane, void* dst) {
+  Coords<Tb> c;
+  if constexpr (kSameType<Tb, double>) {
+    double* R = static_cast<double*>(dst);
+    for (int i = lane; i < 3 * N; i += 32) R[i] = Rg[i];
+    c.R = R;
+  } else {
+    dsf* R = static_cast<dsf*>(dst);
+    for (int i = lane; i < 3 * N; i += 32) R[i] = ds_from_double(Rg[i]);
+    c.R = R;
+  }
+  __syncwarp();
+  return c;
+}
+
 template <class Tb>
-__device__ __forceinline__ double build_geometry(const SysDev& s, int lane, const double* R, const GeoTables<Tb>& g) {
+__device__ __forceinline__ double build_geometry(const SysDev& s, int lane, const Coords<Tb>& C, const GeoTables<Tb>& g) {
   const int N = s.N, Nn = s.Nn;
   const Tb kap = (Tb)s.kappa;
-  double V_loc = 0.0;
+  Tb V_loc = 0;
   for (int p = lane; p < N * N; p += 32) {
     const int i = p / N, j = p % N;
     if (i == j) {
@@ -233,20 +323,19 @@ __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, cons
       g.eEE[3 * p] = g.eEE[3 * p + 1] = g.eEE[3 * p + 2] = (Tb)0;
       continue;
     }
-    const Tb dx = (Tb)(R[3 * i] - R[3 * j]), dy = (Tb)(R[3 * i + 1] - R[3 * j + 1]), dz = (Tb)(R[3 * i + 2] - R[3 * j + 2]);
+    const Tb dx = C.ee(i, j, 0), dy = C.ee(i, j, 1), dz = C.ee(i, j, 2);
     const Tb r = vsqrt(dx * dx + dy * dy + dz * dz), ir = (Tb)1 / r;
     g.rEE[p] = r; g.uEE[p] = (Tb)1 / ((Tb)1 + kap * r); g.iEE[p] = ir;
     g.eEE[3 * p] = dx * ir; g.eEE[3 * p + 1] = dy * ir; g.eEE[3 * p + 2] = dz * ir;
-    if (i < j) V_loc += (double)ir;
+    if (i < j) V_loc += ir;
   }
   for (int p = lane; p < N * Nn; p += 32) {
     const int i = p / Nn, a = p % Nn;
-    const double* nu = s.nuc4 + 4 * a;
-    const Tb dx = (Tb)(R[3 * i] - __ldg(nu)), dy = (Tb)(R[3 * i + 1] - __ldg(nu + 1)), dz = (Tb)(R[3 * i + 2] - __ldg(nu + 2));
+    const Tb dx = C.en(s, i, a, 0), dy = C.en(s, i, a, 1), dz = C.en(s, i, a, 2);
     const Tb r = vsqrt(dx * dx + dy * dy + dz * dz), ir = (Tb)1 / r;
     g.rEN[p] = r;
     g.eEN[3 * p] = dx * ir; g.eEN[3 * p + 1] = dy * ir; g.eEN[3 * p + 2] = dz * ir;
-    V_loc -= __ldg(nu + 3) * (double)ir;
+    V_loc -= C.charge(s, a) * ir;
     const Tb sv = (Tb)1 / ((Tb)1 + kap * r);
     Tb* St = g.Stab + (a * N + i) * 6;
     Tb pw = (Tb)1;
@@ -261,7 +350,7 @@ __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, cons
     g.Ssum[p] = t;
   }
   __syncwarp();
-  return V_loc;
+  return (double)V_loc;
 }
 
 }  // namespace

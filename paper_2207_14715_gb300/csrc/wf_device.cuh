@@ -168,8 +168,8 @@ template <class T> __device__ __forceinline__ T tload(const double* p) { return 
 // P the cartesian monomial (s; x y z; xx yy zz xy xz yz).  Writes value (and if out_d is
 // non-null gradient and Laplacian) for component c at out[c * stride].
 // ------------------------------------------------------------------------------------
-template <class T, bool DERIV>
-__device__ __forceinline__ void gto_shell(int l, T z, const double* nrm, T dx, T dy, T dz, T* val, T* gx, T* gy, T* gz,
+template <class T, bool DERIV, class NT>
+__device__ __forceinline__ void gto_shell(int l, T z, const NT* nrm, T dx, T dy, T dz, T* val, T* gx, T* gy, T* gz,
                                           T* lap) {
   const T r2 = dx * dx + dy * dy + dz * dz;
   const T e = (z == (T)0) ? (T)1 : vexp(-z * r2);
