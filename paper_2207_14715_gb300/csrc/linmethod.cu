@@ -8,20 +8,21 @@
 // (expanding the products recovers the printed sums of averages term by term).
 //
 // Passes: (1) column sums in double; (2) centring and conversion to float, X = Ot and
-// Y = E Ot + dE; (3) split-K products over sample chunks on the FP32 pipe, 128x128 output
-// tiles per block, each thread an 8x8 block of S and of H, partial tiles written per chunk;
-// (4) deterministic reduction of the chunk partials in double and scaling.
+// Y = E Ot + dE; (3) the products X^T W X and X^T W Y on the tensor cores (tcgen05, TF32
+// operands split into high and low parts so that the products keep float accuracy, FP32
+// accumulators in tensor memory) per 128 x 128 output tile and chunk of samples, the chunk
+// partials written in double; (4) deterministic reduction of the chunk partials in double
+// and scaling.
 #include <algorithm>
 
 #include "linmethod.h"
+#include "tc_ptx.cuh"
 
 namespace vbq {
 
 namespace {
 
 constexpr int kTile = 128;     // output tile edge
-constexpr int kKStep = 16;     // samples staged in shared memory per step
-constexpr int kThreads = 256;  // 16 x 16 threads, 8 x 8 outputs each
 
 // Column sums: acc = [sum w, sum w E, sum w O_c (P), sum w dE_c (P)]; also float copies of w
 // and E per sample.  Each block covers 256 samples; per-thread partial sums in the input type.
@@ -68,101 +69,230 @@ __global__ void lin_colsum_kernel(int P, long long M, const Tin* __restrict__ O,
   }
 }
 
-// X = O - <O>, Y = E X + dE (floats, rows padded to Pp columns with zeros); sxe += sum w X E.
+// Centred values, transposed (parameter-major, Mp samples per row) and scaled by sqrt(w_s) so
+// that the products need no weights: Xt[c][s] = sqrt(w_s) X_sc, Yt[c][s] = sqrt(w_s) Y_sc with
+// X = O - <O>, Y = E X + dE (floats; rows c >= P are zero).  sxe[c] += sum_s w_s X_sc E_s.
+// A block transposes a 64-sample x 64-parameter tile through shared memory so that both the
+// reads (along parameters) and the writes (along samples) are coalesced.
 template <class Tin>
-__global__ void lin_center_kernel(int P, int Pp, long long M, const Tin* __restrict__ O,
+__global__ void lin_center_kernel(int P, long long M, long long Mp, const Tin* __restrict__ O,
                                   const Tin* __restrict__ dEL, const double* __restrict__ acc,
-                                  const float* __restrict__ wf, const float* __restrict__ Ef, float* __restrict__ X,
-                                  float* __restrict__ Y, double* __restrict__ sxe /* [P] */) {
-  const long long s0 = (long long)blockIdx.x * 256, s1 = min(M, s0 + 256);
+                                  const float* __restrict__ wf, const float* __restrict__ Ef, float* __restrict__ Xt,
+                                  float* __restrict__ Yt, double* __restrict__ sxe) {
+  __shared__ float tx[64][65], ty[64][65];
+  __shared__ float red[4][64];
+  const long long s0 = (long long)blockIdx.x * 64;
+  const int c0 = blockIdx.y * 64;
   const double isw = 1.0 / acc[0];
-  for (int c = threadIdx.x; c < Pp; c += blockDim.x) {
+  {
+    const int cl = threadIdx.x & 63, sq = threadIdx.x >> 6;
+    const int c = c0 + cl;
     const Tin mo = c < P ? (Tin)(acc[2 + c] * isw) : (Tin)0;
     float sx = 0.0f;
-    for (long long s = s0; s < s1; ++s) {
-      const float x = c < P ? (float)(O[s * P + c] - mo) : 0.0f;
-      const float y = c < P ? fmaf(Ef[s], x, (float)dEL[s * P + c]) : 0.0f;
-      X[s * Pp + c] = x;
-      Y[s * Pp + c] = y;
-      sx = fmaf(wf[s] * x, Ef[s], sx);
+    for (int k = 0; k < 16; ++k) {
+      const int sl = sq + 4 * k;
+      const long long sm = s0 + sl;
+      float xs = 0.0f, ys = 0.0f;
+      if (sm < M && c < P) {
+        const float x = (float)(O[sm * P + c] - mo);
+        const float y = fmaf(Ef[sm], x, (float)dEL[sm * P + c]);
+        const float sw = sqrtf(wf[sm]);
+        xs = sw * x;
+        ys = sw * y;
+        sx = fmaf(wf[sm] * x, Ef[sm], sx);
+      }
+      tx[cl][sl] = xs;
+      ty[cl][sl] = ys;
     }
-    if (c < P) atomicAdd(sxe + c, (double)sx);
+    red[sq][cl] = sx;
   }
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int c = c0 + threadIdx.x;
+    if (c < P) atomicAdd(sxe + c, (double)(red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] +
+                                           red[3][threadIdx.x]));
+  }
+  const int sl = threadIdx.x & 63, cq = threadIdx.x >> 6;
+  const long long sm = s0 + sl;
+  if (sm < M)
+    for (int k = 0; k < 16; ++k) {
+      const int cc = cq + 4 * k;
+      Xt[(size_t)(c0 + cc) * Mp + sm] = tx[cc][sl];
+      Yt[(size_t)(c0 + cc) * Mp + sm] = ty[cc][sl];
+    }
 }
 
 // Partial tiles: part[chunk][0][i][j] = sum_{s in chunk} w_s X_si X_sj,
-//                part[chunk][1][i][j] = sum_{s in chunk} w_s X_si Y_sj.
-__global__ void __launch_bounds__(kThreads, 1)
-    lin_tile_kernel(int Pp, long long M, long long chunk, const float* __restrict__ X, const float* __restrict__ Y,
-                    const float* __restrict__ wf, double* __restrict__ part) {
-  __shared__ __align__(16) float As[kKStep][kTile];
-  __shared__ __align__(16) float Bx[kKStep][kTile];
-  __shared__ __align__(16) float By[kKStep][kTile];
+//                part[chunk][1][i][j] = sum_{s in chunk} w_s X_si Y_sj,
+// one CTA per (128 x 128 output tile, chunk).  Per step of 32 samples, TMA brings the tiles
+// A = Xt[i0..i0+127][s..s+31], Bx = Xt[j0..][s..], By = Yt[j0..][s..] into shared memory,
+// K-major with the 128-byte swizzle (the layout the MMA reads).  The threads split each value
+// into TF32 parts x = hi + lo (hi: low 13 mantissa bits cleared, written back in place; lo in a
+// second tile at the same offsets), and one thread issues the 8-sample MMAs A_hi B_lo and
+// A_lo B_hi (first, while the accumulator is small) and A_hi B_hi into two 128 x 128 FP32
+// accumulators in tensor memory, starting from zero every step.  The tensor core's
+// accumulation rounds at the accumulator's magnitude, so each step's result is moved to
+// registers and summed there in FP32 (round to nearest) instead of accumulating the whole
+// chunk in tensor memory.  Two stages (shared memory and tensor-memory sets) alternate: the
+// TMA of step k+1 and the draining of step k-1 overlap the MMAs of step k.  Barrier waits are
+// bounded (about a second); on a timeout the CTA raises *err and stops.
+constexpr int kTcThreads = 256;
+constexpr int kTcK = 32;                              // samples per step (128 bytes of TF32)
+constexpr int kTileBytes = kTile * kTcK * 4;          // one 128 x 32 TF32 tile: 16 KB
+constexpr int kStageBytes = 6 * kTileBytes;           // A hi/lo, Bx hi/lo, By hi/lo
+constexpr int kTcSmem = 2 * kStageBytes + 1024 + 64;  // two stages, alignment, barriers
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+// adds this thread's 128 accumulator columns of TMEM set 'set' to acc (warp w: lanes
+// 32 (w % 4) + lane; warps 0-3 the S tile, warps 4-7 the H tile)
+__device__ __forceinline__ void drain(uint32_t tmem, int set, int warp, float acc[kTile]) {
+  const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * set) + (warp < 4 ? 0u : 128u);
+#pragma unroll
+  for (int c = 0; c < kTile; c += 16) {
+    float v[16];
+    tmem_ld16(base + c, v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[c + q] += v[q];
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    lin_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int Pp,
+                  long long M, long long chunk, double* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  // 1024-byte aligned stage buffers (required by the swizzle), barriers after them
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + 2 * kStageBytes);  // [2] TMA arrivals
+  uint64_t* done = full + 2;                                            // [2] MMA completions
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int ntj = Pp / kTile;
   const int ti = blockIdx.x / ntj, tj = blockIdx.x % ntj;
   const int i0 = ti * kTile, j0 = tj * kTile;
   const long long s0 = (long long)blockIdx.y * chunk, s1 = min(M, s0 + chunk);
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  float cs[8][8], ch[8][8];
-#pragma unroll
-  for (int a = 0; a < 8; ++a)
-#pragma unroll
-    for (int b = 0; b < 8; ++b) cs[a][b] = ch[a][b] = 0.0f;
-  for (long long sb = s0; sb < s1; sb += kKStep) {
-    // stage kKStep samples: 16 x 128 floats per operand, 8 per thread
-    for (int q = threadIdx.x; q < kKStep * kTile; q += kThreads) {
-      const int k = q / kTile, c = q % kTile;
-      const long long s = sb + k;
-      float a = 0.0f, bx = 0.0f, by = 0.0f;
-      if (s < s1) {
-        const float ws = wf[s];
-        a = X[s * (long long)Pp + i0 + c];
-        bx = ws * X[s * (long long)Pp + j0 + c];
-        by = ws * Y[s * (long long)Pp + j0 + c];
-      }
-      As[k][c] = a;
-      Bx[k][c] = bx;
-      By[k][c] = by;
+  const int nsteps = (int)((s1 - s0 + kTcK - 1) / kTcK);
+  // tiles of a stage: 0 A_hi, 1 A_lo, 2 Bx_hi, 3 Bx_lo, 4 By_hi, 5 By_lo
+  auto tile = [&](int st, int t) { return sm + st * kStageBytes + t * kTileBytes; };
+  int loaded = 0;  // (thread 0) steps whose TMA was issued
+  auto load = [&](int ks) {  // thread 0: TMA of step ks into stage ks & 1
+    const int st = ks & 1, x = (int)(s0 + (long long)ks * kTcK);
+    loaded = ks + 1;
+    mbar_arrive_expect_tx(&full[st], 3 * kTileBytes);
+    tma_load_2d(tile(st, 0), &tmX, x, i0, &full[st]);
+    tma_load_2d(tile(st, 2), &tmX, x, j0, &full[st]);
+    tma_load_2d(tile(st, 4), &tmY, x, j0, &full[st]);
+  };
+
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&done[b], 1);
     }
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < kKStep; ++k) {
-      float a[8], bx[8], by[8];
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[k][ty * 8]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[k][ty * 8 + 4]);
-      const float4 x0 = *reinterpret_cast<const float4*>(&Bx[k][tx * 8]);
-      const float4 x1 = *reinterpret_cast<const float4*>(&Bx[k][tx * 8 + 4]);
-      const float4 y0 = *reinterpret_cast<const float4*>(&By[k][tx * 8]);
-      const float4 y1 = *reinterpret_cast<const float4*>(&By[k][tx * 8 + 4]);
-      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
-      bx[0] = x0.x; bx[1] = x0.y; bx[2] = x0.z; bx[3] = x0.w; bx[4] = x1.x; bx[5] = x1.y; bx[6] = x1.z; bx[7] = x1.w;
-      by[0] = y0.x; by[1] = y0.y; by[2] = y0.z; by[3] = y0.w; by[4] = y1.x; by[5] = y1.y; by[6] = y1.z; by[7] = y1.w;
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          cs[r][c] = fmaf(a[r], bx[c], cs[r][c]);
-          ch[r][c] = fmaf(a[r], by[c], ch[r][c]);
-        }
-    }
-    __syncthreads();
+    fence_async_smem();
   }
-  double* ps = part + (size_t)blockIdx.y * 2 * Pp * Pp;
-  double* ph = ps + (size_t)Pp * Pp;
+  if (warp == 0) tmem_alloc(tmem_holder, 512);  // set b at columns 256 b: S tile (+0), H tile (+128)
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  if (tid == 0 && nsteps > 0) load(0);
+  constexpr uint32_t idesc = idesc_tf32(128, 128);
+  float acc[kTile];
 #pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const size_t o = (size_t)(i0 + ty * 8 + r) * Pp + j0 + tx * 8 + c;
-      ps[o] = (double)cs[r][c];
-      ph[o] = (double)ch[r][c];
+  for (int c = 0; c < kTile; ++c) acc[c] = 0.0f;
+  bool ok = true;
+  int issued = 0;                   // steps whose MMAs were issued
+  int drained = 0;                  // steps whose results were added to acc
+
+  for (int ks = 0; ks < nsteps; ++ks) {
+    const int st = ks & 1;
+    ok = __syncthreads_and(mbar_wait(&full[st], (uint32_t)((ks >> 1) & 1), kWaitNs)) != 0;
+    if (!ok) break;
+    // split into TF32 high and low parts (elementwise: the swizzled layout is kept)
+    for (int t = 0; t < 3; ++t) {
+      float4* hi = reinterpret_cast<float4*>(tile(st, 2 * t));
+      float4* lo = reinterpret_cast<float4*>(tile(st, 2 * t + 1));
+      for (int q = tid; q < kTileBytes / 16; q += kTcThreads) {
+        const float4 x = hi[q];
+        const float4 h = make_float4(__uint_as_float(__float_as_uint(x.x) & 0xffffe000u),
+                                     __uint_as_float(__float_as_uint(x.y) & 0xffffe000u),
+                                     __uint_as_float(__float_as_uint(x.z) & 0xffffe000u),
+                                     __uint_as_float(__float_as_uint(x.w) & 0xffffe000u));
+        hi[q] = h;
+        lo[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
     }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a_hi = smem_addr(tile(st, 0)), a_lo = a_hi + kTileBytes;
+      const uint32_t bx_hi = a_hi + 2 * kTileBytes, bx_lo = a_hi + 3 * kTileBytes;
+      const uint32_t by_hi = a_hi + 4 * kTileBytes, by_lo = a_hi + 5 * kTileBytes;
+      const uint32_t dS = tmem + 256 * st, dH = dS + 128;
+#pragma unroll
+      for (int kk = 0; kk < kTcK / 8; ++kk) {
+        const uint32_t ko = kk * 32;  // 8 TF32 = 32 bytes along the swizzled row
+        mma_tf32(dS, smem_desc_k128(a_hi + ko), smem_desc_k128(bx_lo + ko), idesc, kk > 0 ? 1u : 0u);
+        mma_tf32(dS, smem_desc_k128(a_lo + ko), smem_desc_k128(bx_hi + ko), idesc, 1u);
+        mma_tf32(dH, smem_desc_k128(a_hi + ko), smem_desc_k128(by_lo + ko), idesc, kk > 0 ? 1u : 0u);
+        mma_tf32(dH, smem_desc_k128(a_lo + ko), smem_desc_k128(by_hi + ko), idesc, 1u);
+      }
+#pragma unroll
+      for (int kk = 0; kk < kTcK / 8; ++kk) {
+        const uint32_t ko = kk * 32;
+        mma_tf32(dS, smem_desc_k128(a_hi + ko), smem_desc_k128(bx_hi + ko), idesc, 1u);
+        mma_tf32(dH, smem_desc_k128(a_hi + ko), smem_desc_k128(by_hi + ko), idesc, 1u);
+      }
+      mma_commit(&done[st]);
+    }
+    issued = ks + 1;
+    if (ks >= 1) {
+      // MMAs of step ks-1 done: their stage can be refilled and their accumulators drained
+      ok = __syncthreads_and(mbar_wait(&done[st ^ 1], (uint32_t)(((ks - 1) >> 1) & 1), kWaitNs)) != 0;
+      if (!ok) break;
+      if (tid == 0 && ks + 1 < nsteps) load(ks + 1);
+      tc_fence_after();
+      drain(tmem, st ^ 1, warp, acc);
+      drained = ks;
+      tc_fence_before();
+    } else if (tid == 0 && nsteps > 1) {
+      load(1);
+    }
+  }
+  // the last issued step: wait and drain; on a timeout, still give the copies and MMAs in
+  // flight a bounded wait before the shared and tensor memory are released
+  if (issued > 0 && drained < issued) {
+    const int ks = issued - 1;
+    const bool d = mbar_wait(&done[ks & 1], (uint32_t)((ks >> 1) & 1), kWaitNs);
+    ok = __syncthreads_and(ok && d) != 0;
+    if (ok) {
+      tc_fence_after();
+      drain(tmem, ks & 1, warp, acc);
+      drained = issued;
+    }
+  }
+  if (!ok && tid == 0)
+    for (int ks = issued; ks < loaded; ++ks) mbar_wait(&full[ks & 1], (uint32_t)((ks >> 1) & 1), kWaitNs);
+  if (ok && drained == nsteps) {
+    const int row = i0 + 32 * (warp & 3) + (tid & 31);
+    double* out = part + (size_t)blockIdx.y * 2 * Pp * Pp + (warp < 4 ? 0 : (size_t)Pp * Pp) + (size_t)row * Pp + j0;
+#pragma unroll
+    for (int c = 0; c < kTile; ++c) out[c] = (double)acc[c];
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 __global__ void lin_reduce_kernel(int P, int Pp, int nchunk, const double* __restrict__ part,
                                   const double* __restrict__ acc, const double* __restrict__ sxe, double* E0,
-                                  double* gL, double* gR, double* S, double* H) {
-  const double isw = 1.0 / acc[0];
+                                  double* gL, double* gR, double* S, double* H, const int* __restrict__ err) {
+  // a timed-out tensor-core stage leaves NaN outputs
+  const double isw = *err ? __longlong_as_double(0x7ff8000000000000ll) : 1.0 / acc[0];
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q < (long long)P * P) {
     const int i = (int)(q / P), j = (int)(q % P);
@@ -192,9 +322,11 @@ size_t lin_workspace_bytes(int P, long long M) {
   size_t b = 0;
   b += sizeof(double) * (2 + 2 * (size_t)P) + 256;        // acc
   b += sizeof(double) * (size_t)P + 256;                  // sxe
-  b += sizeof(float) * (size_t)M * Pp * 2 + 256;          // X, Y
+  const long long Mp = (M + 31) / 32 * 32;
+  b += 2 * (sizeof(float) * (size_t)Mp * Pp + 256);       // Xt, Yt
   b += 2 * (sizeof(float) * (size_t)M + 256);             // wf, Ef
   b += sizeof(double) * (size_t)nchunk * 2 * Pp * Pp + 256;  // partial tiles
+  b += 256;                                                  // error flag
   return b;
 }
 
@@ -203,6 +335,33 @@ long long lin_chunk(long long M) {
   long long c = 16384;
   while (c > 2048 && (M + c - 1) / c < 32) c /= 2;
   return c;
+}
+
+// Tensor map of a [rows][Mp] float array read as M samples per row in 32-sample x 128-row
+// boxes with the 128-byte swizzle (samples past M read as zero).  The encoder comes from the
+// driver through the runtime, so the library does not link the driver library itself.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static cudaError_t encode_tile_map(CUtensorMap* map, const float* base, int rows, long long M, long long Mp) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorSymbolNotFound;
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Mp * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTile};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <class Tin>
@@ -220,21 +379,31 @@ static cudaError_t launch_lin_t(int P, long long M, const Tin* O, const Tin* dEL
   };
   double* acc = reinterpret_cast<double*>(take(sizeof(double) * (2 + 2 * (size_t)P)));
   double* sxe = reinterpret_cast<double*>(take(sizeof(double) * (size_t)P));
-  float* X = reinterpret_cast<float*>(take(sizeof(float) * (size_t)M * Pp));
-  float* Y = reinterpret_cast<float*>(take(sizeof(float) * (size_t)M * Pp));
+  const long long Mp = (M + 31) / 32 * 32;
+  float* Xt = reinterpret_cast<float*>(take(sizeof(float) * (size_t)Mp * Pp));
+  float* Yt = reinterpret_cast<float*>(take(sizeof(float) * (size_t)Mp * Pp));
   float* wf = reinterpret_cast<float*>(take(sizeof(float) * (size_t)M));
   float* Ef = reinterpret_cast<float*>(take(sizeof(float) * (size_t)M));
   double* part = reinterpret_cast<double*>(take(sizeof(double) * (size_t)nchunk * 2 * Pp * Pp));
+  int* err = reinterpret_cast<int*>(take(sizeof(int)));
   cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * (2 + 2 * (size_t)P), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(sxe, 0, sizeof(double) * (size_t)P, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   const int nb = (int)((M + 255) / 256);
   lin_colsum_kernel<Tin><<<nb, 256, 0, st>>>(P, M, O, dEL, E, w, acc, wf, Ef);
-  lin_center_kernel<Tin><<<nb, 256, 0, st>>>(P, Pp, M, O, dEL, acc, wf, Ef, X, Y, sxe);
+  lin_center_kernel<Tin><<<dim3((unsigned)((M + 63) / 64), Pp / 64), 256, 0, st>>>(P, M, Mp, O, dEL, acc, wf, Ef, Xt,
+                                                                                    Yt, sxe);
+  CUtensorMap tmX, tmY;
+  e = encode_tile_map(&tmX, Xt, Pp, M, Mp);
+  if (e == cudaSuccess) e = encode_tile_map(&tmY, Yt, Pp, M, Mp);
+  if (e != cudaSuccess) return e;
   const int ntile = (Pp / kTile) * (Pp / kTile);
-  lin_tile_kernel<<<dim3(ntile, nchunk), kThreads, 0, st>>>(Pp, M, chunk, X, Y, wf, part);
+  e = cudaFuncSetAttribute(lin_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  if (e != cudaSuccess) return e;
+  lin_tc_kernel<<<dim3(ntile, nchunk), kTcThreads, kTcSmem, st>>>(tmX, tmY, Pp, M, chunk, part, err);
   const long long nq = std::max<long long>((long long)P * P, 1);
-  lin_reduce_kernel<<<(int)((nq + 255) / 256), 256, 0, st>>>(P, Pp, nchunk, part, acc, sxe, E0, gL, gR, S, H);
+  lin_reduce_kernel<<<(int)((nq + 255) / 256), 256, 0, st>>>(P, Pp, nchunk, part, acc, sxe, E0, gL, gR, S, H, err);
   *nlaunch = 4;
   return cudaGetLastError();
 }
