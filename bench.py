@@ -336,6 +336,7 @@ def run_ours(args, ws, rank, local):
     t_e2e = allmax(time.perf_counter() - t0, ws)
     barrier(ws)
     dmc = dmc_timing(ctx, vbqmc, R, el, args.dmc_steps) if args.dmc_steps > 0 else None
+    batched = batched_timing(vbqmc, dev, args.steps) if args.batch_steps > 0 else None
     lin = lin_method_timing(ctx, vbqmc, dev, args.steps, args.lin_samples) if not args.no_lin else None
     barrier(ws)
     if rank != 0:
@@ -383,6 +384,7 @@ def run_ours(args, ws, rank, local):
                 "d2h_bytes_per_step": bo},
         "linear_method": lin,
         "dmc": dmc,
+        "batched": batched,
         "gpu_launches": m["launches_per_step"] * m["steps"],
         "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
                    "reasons": clocks.get("reasons", [])},
@@ -412,6 +414,48 @@ def dmc_timing(ctx, vbqmc, R, el, steps, tau=0.005):
             "target": W, "population": [int(x) for x in hist["pop"]],
             "acceptance": hist["accepted"] / max(moved, 1),
             "launches_per_step": (ctx.last_launch_count() - 3) / steps}
+
+
+def batched_timing(vbqmc, dev, steps):
+    """The batched workload (64 random molecules of 2-32 electrons, 256-4096 walkers each) as
+    one batch in the mixed form: tuned launch shapes, then steps of one sweep + evaluation with
+    derivatives of every system, replayed from the captured graph; walker-steps/s over all
+    systems (CUDA events around the timed steps)."""
+    import torch
+    from paper_2207_14715_gb300 import systems as S
+    specs, W = S.batched_workload(64)
+    ctx = vbqmc.create(dev.index or 0)
+    for k, sp in enumerate(specs):
+        ctx.set_system(k, sp)
+    R = [torch.tensor(S.initial_walkers(sp, w, SEED + k), device=dev) for k, (sp, w) in enumerate(zip(specs, W))]
+    z = lambda: [torch.zeros(w, dtype=torch.float64, device=dev) for w in W]
+    lp, sg, el = z(), z(), z()
+    O = [torch.zeros((w, sp.n_params), dtype=torch.float32, device=dev) for sp, w in zip(specs, W)]
+    dE = [torch.zeros_like(o) for o in O]
+    st = [torch.zeros((w, ctx.walker_state_size(k)), dtype=torch.float64, device=dev) for k, w in enumerate(W)]
+    batch = vbqmc.Batch(ctx, list(range(len(specs))), W, vbqmc.MIXED)
+    batch.tune(R, lp, sg, el)
+    args = dict(logpsi=lp, sign=sg, eloc=el, O=O, dEL=dE, state=st)
+    batch.vmc_steps(R, 10, 0.3, SEED, step0=1 << 22, refresh=0, **args)   # equilibration, then warm-up
+    for k in range(3):
+        batch.vmc_steps(R, 1, 0.3, SEED, step0=(1 << 22) + 1 + k, refresh=0, state_valid=True, **args)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(3, steps)
+    e0.record()
+    for k in range(n):
+        batch.vmc_steps(R, 1, 0.3, SEED, step0=(1 << 23) + k, refresh=0, state_valid=True, **args)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    launches = ctx.last_launch_count()
+    info = batch.info()
+    batch.close()
+    ctx.close()
+    return {"systems": len(specs), "walkers": int(sum(W)), "electrons": [min(sp.N for sp in specs),
+                                                                       max(sp.N for sp in specs)],
+            "walker_steps_per_s": sum(W) / (ms * 1e-3), "ms_per_step": ms, "launches_per_step": launches,
+            "launch_shapes": {k: [v["grid"], v["warps"], v["persist"], v["cap"]] for k, v in info.items()}}
 
 
 def lin_method_timing(ctx, vbqmc, dev, steps, M=1 << 20):
@@ -452,6 +496,7 @@ def main():
     ap.add_argument("--no-lin", action="store_true")
     ap.add_argument("--lin-samples", type=int, default=1 << 20, help="samples of the linear-method timing")
     ap.add_argument("--dmc-steps", type=int, default=5, help="timed DMC steps (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=3, help="batched-workload timing (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

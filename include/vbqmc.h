@@ -234,6 +234,42 @@ int vbqmc_accumulate_lin_matrices_noalloc(int precision, int P, int64_t M, const
                                           const double* eloc, const double* weights, double* E0, double* gL,
                                           double* gR, double* S, double* H, void* stream);
 
+/* ---- Batched systems (many small molecules of uneven size in one set of launches) ----
+ * A batch holds several systems already loaded in the context (each with its own walker
+ * count W[k]) in one precision mode.  Every kernel type runs once per step for all systems,
+ * through a table of (system, walker range) work items ordered by estimated cost; the
+ * launches of a step are captured in a CUDA graph on first use (per call shape: with or
+ * without sweeps, evaluation and derivatives) and replayed.  Results equal those of the
+ * per-system calls with system_tag = the system id and walker_offset = 0.  A batch keeps a
+ * copy of the systems' tables: recreate it after reloading one of its systems.  The paper has
+ * no counterpart (it runs one molecule per calculation); this serves many small systems at
+ * once. */
+typedef struct vbqmc_batch vbqmc_batch;
+/* Creates a batch of nsys distinct loaded systems sys_ids[k] with W[k] >= 1 walkers each;
+ * allocates the evaluation workspace of all of them.  Errors: VBQMC_ERR_NOSYS,
+ * VBQMC_ERR_CAPACITY (a system's per-walker state does not fit in shared memory),
+ * VBQMC_ERR_ARG, VBQMC_ERR_CUDA. */
+int vbqmc_batch_create(vbqmc_ctx* ctx, int nsys, const int* sys_ids, const int* W, int precision, vbqmc_batch** out);
+void vbqmc_batch_destroy(vbqmc_batch* batch);
+/* vbqmc_vmc_steps for every system of the batch; every pointer argument is a host array of
+ * nsys device pointers (R, and state/nacc/logpsi/sign/eloc/O/dEL when not NULL), each laid out
+ * as in vbqmc_vmc_steps for its own system.  The call copies its arguments through pinned
+ * staging buffers: it waits until the previous call's graph has read them. */
+int vbqmc_batch_vmc_steps(vbqmc_batch* batch, double* const* R, int nsweeps, double step, uint64_t seed,
+                          uint32_t step0, int refresh, double* const* state, int state_valid, int* const* nacc,
+                          double* const* logpsi, double* const* sign, double* const* eloc, void* const* O,
+                          void* const* dEL, void* stream);
+/* Launch-shape tuner: times the evaluation kernels of the batch on the walkers R (outputs
+ * written to logpsi/sign/eloc) for one-block-per-item and persistent grids, with and without a
+ * cap on walkers per block, keeps the fastest for each kernel and drops captured graphs.
+ * Synchronizes 'stream'. */
+int vbqmc_batch_tune(vbqmc_batch* batch, double* const* R, double* const* logpsi, double* const* sign,
+                     double* const* eloc, void* stream);
+/* Launch shapes: out[5 k + 0..4] = work items, grid, warps per block, persistence (0: one
+ * block per item, p: p x resident blocks), walkers-per-block cap (0: none) for kernel k in
+ * the order sweep, Jastrow, Jastrow derivatives, orbitals, determinants. */
+int vbqmc_batch_info(vbqmc_batch* batch, int* out);
+
 /* Per-kernel timing of the evaluation (diagnostics; the paper has no counterpart).  With
  * timing on, every evaluation (vbqmc_eval_walkers, and the evaluation at the end of
  * vbqmc_vmc_steps) records CUDA events on its stream around each of its kernels; the

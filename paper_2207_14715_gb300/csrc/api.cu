@@ -10,6 +10,7 @@
 #include "dmc.h"
 #include "kernels.h"
 #include "linmethod.h"
+#include "ctx_internal.h"
 #include "vbqmc_internal.h"
 
 namespace {
@@ -26,31 +27,6 @@ int cuda_fail(cudaError_t e, const char* what) {
   return VBQMC_ERR_CUDA;
 }
 
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = false;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
-struct LoadedSystem {
-  bool loaded = false;
-  vbq::SysHost host;
-  vbq::SysDev dev{};
-  void* blob = nullptr;
-  size_t blob_bytes = 0;
-  vbq::EvalLayout lay_eval[2];
-  vbq::SweepLayout lay_sweep[2];
-  int lay_rc_eval[2] = {0, 0};
-  int lay_rc_sweep[2] = {0, 0};
-};
-
 // Packs host arrays into one 16-byte-aligned blob and records where each one went.
 struct BlobBuilder {
   std::vector<unsigned char> bytes;
@@ -64,26 +40,13 @@ struct BlobBuilder {
 
 }  // namespace
 
+using vbq::DeviceGuard;
+using vbq::LoadedSystem;
+
 namespace vbq {
 int set_error(int code, const std::string& msg) { return fail(code, msg); }
 int set_cuda_error(int cuda_error, const char* what) { return cuda_fail((cudaError_t)cuda_error, what); }
 }  // namespace vbq
-
-struct vbqmc_ctx {
-  int device = 0;
-  int max_smem = 0;
-  int last_launches = 0;
-  LoadedSystem sys[VBQMC_MAX_SYSTEMS];
-  void* work = nullptr;      // grow-only device workspace of the linear-method accumulation
-  size_t work_bytes = 0;
-  void* dmc_work = nullptr;  // grow-only device workspace of the DMC steps
-  size_t dmc_bytes = 0;
-  void* eval_work = nullptr;  // grow-only device workspace of the evaluation kernels
-  size_t eval_bytes = 0;
-  int timing = 0;                               // record events around the evaluation kernels
-  cudaEvent_t tev[vbq::kEvalKernels + 1] = {};  // created on first use
-  bool tev_valid = false;                       // events of the last timed evaluation are recorded
-};
 
 static void free_system(LoadedSystem& s) {
   if (s.blob) cudaFree(s.blob);

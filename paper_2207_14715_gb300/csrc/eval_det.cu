@@ -5,6 +5,7 @@
 //   D1 structure-coefficient derivatives; D3 orbital-excitation derivatives
 // from the Jastrow and orbital results in the evaluation workspace.  The inverses are kept in
 // shared memory in the bulk type only (the double inverses go straight to the walker state).
+#include "batch.h"
 #include "walker_common.cuh"
 
 namespace vbq {
@@ -67,18 +68,14 @@ __device__ __forceinline__ void lu_det_all(const SysDev& s, int sp, int lane, co
 }
 
 template <class Tb>
-__global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
-    det_kernel(const SysDev s, const DetLayout L, int W, const Tb* __restrict__ JG, const Tb* __restrict__ JL,
-               const double* __restrict__ JS, const Tb* __restrict__ OB, const double* __restrict__ OD,
-               double* __restrict__ logpsi, double* __restrict__ sgn_out, double* __restrict__ eloc,
-               double* __restrict__ vg_ws, double* __restrict__ grad, Tb* __restrict__ Og, Tb* __restrict__ dELg,
-               double* __restrict__ state_out) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, int w, unsigned char* base,
+                                         const Tb* __restrict__ JG, const Tb* __restrict__ JL,
+                                         const double* __restrict__ JS, const Tb* __restrict__ OB,
+                                         const double* __restrict__ OD, double* __restrict__ logpsi,
+                                         double* __restrict__ sgn_out, double* __restrict__ eloc,
+                                         double* __restrict__ vg_ws, double* __restrict__ grad, Tb* __restrict__ Og,
+                                         Tb* __restrict__ dELg, double* __restrict__ state_out) {
   const int lane = threadIdx.x & 31;
-  const int wl = threadIdx.x >> 5;
-  const int w = blockIdx.x * L.wpb + wl;
-  if (w >= W) return;
-  unsigned char* base = smem + wl * L.warp_bytes;
   double* vg = reinterpret_cast<double*>(base + L.vg);
   Tb* G = reinterpret_cast<Tb*>(base + L.G);
   Tb* LJ = reinterpret_cast<Tb*>(base + L.LJ);
@@ -269,6 +266,40 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
   }
 }
 
+template <class Tb>
+__global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
+    det_kernel(const SysDev s, const DetLayout L, int W, const Tb* __restrict__ JG, const Tb* __restrict__ JL,
+               const double* __restrict__ JS, const Tb* __restrict__ OB, const double* __restrict__ OD,
+               double* __restrict__ logpsi, double* __restrict__ sgn_out, double* __restrict__ eloc,
+               double* __restrict__ vg_ws, double* __restrict__ grad, Tb* __restrict__ Og, Tb* __restrict__ dELg,
+               double* __restrict__ state_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wl = threadIdx.x >> 5;
+  const int w = blockIdx.x * L.wpb + wl;
+  if (w >= W) return;
+  det_body<Tb>(s, L, w, smem + wl * L.warp_bytes, JG, JL, JS, OB, OD, logpsi, sgn_out, eloc, vg_ws, grad, Og, dELg,
+               state_out);
+}
+
+template <class Tb>
+__global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
+    det_batch_kernel(const BatchSys* __restrict__ sys, const BatchItem* __restrict__ items, int nitems,
+                     const BatchCall* __restrict__ call) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wl = threadIdx.x >> 5;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    // the warps' shared-memory regions depend on the item's system: start together
+    __syncthreads();
+    const BatchItem item = items[it];
+    if (wl >= item.count) continue;
+    const BatchSys& b = sys[item.sys];
+    const bool d = call->derivs && b.O && b.dev.P > 0;
+    det_body<Tb>(b.dev, b.lay.det, item.first + wl, smem + wl * b.lay.det.warp_bytes, static_cast<const Tb*>(b.JG),
+                 static_cast<const Tb*>(b.JL), b.JS, static_cast<const Tb*>(b.OB), b.OD, b.logpsi, b.sign, b.eloc, b.VG,
+                 nullptr, d ? static_cast<Tb*>(b.O) : nullptr, d ? static_cast<Tb*>(b.dEL) : nullptr, b.state);
+  }
+}
+
 int make_det_layout(const SysDev& s, int tb, int max_smem, DetLayout& L) {
   int off = 0;
   auto take = [&](int bytes) {
@@ -373,6 +404,21 @@ cudaError_t launch_eval_t(const SysDev& s, const EvalLayout& L, int W, const dou
 }
 
 }  // namespace
+
+template <class Tb>
+cudaError_t launch_det_batch(const BatchSys* sys, const BatchItem* items, int nitems, const BatchCall* call, int grid,
+                             int warps, int smem, cudaStream_t st) {
+  det_batch_kernel<Tb><<<grid, 32 * warps, smem, st>>>(sys, items, nitems, call);
+  return cudaGetLastError();
+}
+int det_batch_grid(int is_float, int nitems, int warps, int smem, int persist) {
+  return batch_grid(is_float ? (const void*)det_batch_kernel<float> : (const void*)det_batch_kernel<double>, nitems,
+                    warps, smem, persist);
+}
+template cudaError_t launch_det_batch<float>(const BatchSys*, const BatchItem*, int, const BatchCall*, int, int, int,
+                                             cudaStream_t);
+template cudaError_t launch_det_batch<double>(const BatchSys*, const BatchItem*, int, const BatchCall*, int, int, int,
+                                              cudaStream_t);
 
 int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
   int rc = make_jas_layout(s, tb, max_smem, L.jas);

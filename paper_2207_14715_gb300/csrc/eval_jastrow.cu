@@ -3,6 +3,7 @@
 //   jastrow_deriv_kernel  O_alpha = d ln J/d alpha and E_L,alpha = -1/2 sum_i (lap_i g_alpha +
 //                         2 grad_i g_alpha . grad_i ln|Psi|) for every Jastrow parameter alpha
 // One warp per walker; the geometry tables of the walker live in shared memory.
+#include "batch.h"
 #include "walker_common.cuh"
 
 namespace vbq {
@@ -32,15 +33,10 @@ template <> struct LnSum<float> {
 // lanes -> (electron i, group g); group g takes nuclei a = g, g + S, ... and partners
 // j = g, g + S, ...
 template <class Tb>
-__global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_kernel(const SysDev s, const JasLayout L, int W,
-                                                         const double* __restrict__ Rg, Tb* __restrict__ JG,
-                                                         Tb* __restrict__ JL, double* __restrict__ JS) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L, int w, unsigned char* base,
+                                             const double* __restrict__ Rg, Tb* __restrict__ JG, Tb* __restrict__ JL,
+                                             double* __restrict__ JS) {
   const int lane = threadIdx.x & 31;
-  const int wl = threadIdx.x >> 5;
-  const int w = blockIdx.x * L.wpb + wl;
-  if (w >= W) return;
-  unsigned char* base = smem + wl * L.warp_bytes;
   const int N = s.N, Nn = s.Nn, Nup = s.Nup;
   const GeoTables<Tb> g(reinterpret_cast<Tb*>(base + L.geo), N, Nn);
   const Tb kap = (Tb)s.kappa;
@@ -131,6 +127,33 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_kernel
   }
 }
 
+template <class Tb>
+__global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks)
+    jastrow_kernel(const SysDev s, const JasLayout L, int W, const double* __restrict__ Rg, Tb* __restrict__ JG,
+                   Tb* __restrict__ JL, double* __restrict__ JS) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wl = threadIdx.x >> 5;
+  const int w = blockIdx.x * L.wpb + wl;
+  if (w >= W) return;
+  jastrow_body<Tb>(s, L, w, smem + wl * L.warp_bytes, Rg, JG, JL, JS);
+}
+
+template <class Tb>
+__global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks)
+    jastrow_batch_kernel(const BatchSys* __restrict__ sys, const BatchItem* __restrict__ items, int nitems) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wl = threadIdx.x >> 5;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    // the warps' shared-memory regions depend on the item's system: start together
+    __syncthreads();
+    const BatchItem item = items[it];
+    if (wl >= item.count) continue;
+    const BatchSys& b = sys[item.sys];
+    jastrow_body<Tb>(b.dev, b.lay.jas, item.first + wl, smem + wl * b.lay.jas.warp_bytes, b.R,
+                     static_cast<Tb*>(b.JG), static_cast<Tb*>(b.JL), b.JS);
+  }
+}
+
 // Radial parameter derivatives of the Pade + polynomial form f(R) = a1 R/(1 + a2 R) +
 // sum_p a_{p+1} R^p, R = r/(1 + kappa r): with h the derivative of f with respect to the
 // parameter,
@@ -160,16 +183,10 @@ __device__ __forceinline__ void pade_param_derivs(Tb r, Tb kap, Tb a1, Tb a2, Tb
 }
 
 template <class Tb>
-__global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_deriv_kernel(const SysDev s, const JasLayout L, int W,
-                                                               const double* __restrict__ Rg,
-                                                               const double* __restrict__ vgg, Tb* __restrict__ Og,
-                                                               Tb* __restrict__ dELg) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void jastrow_deriv_body(const SysDev& s, const JasLayout& L, int w, unsigned char* base,
+                                                   const double* __restrict__ Rg, const double* __restrict__ vgg,
+                                                   Tb* __restrict__ Og, Tb* __restrict__ dELg) {
   const int lane = threadIdx.x & 31;
-  const int wl = threadIdx.x >> 5;
-  const int w = blockIdx.x * L.wpb + wl;
-  if (w >= W) return;
-  unsigned char* base = smem + wl * L.warp_bytes;
   Tb* vg = reinterpret_cast<Tb*>(base + L.vg);  // grad ln|Psi| in the bulk type
   Tb* red = reinterpret_cast<Tb*>(base + L.red);
   const int N = s.N, Nn = s.Nn, Nup = s.Nup;
@@ -309,6 +326,34 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks) jastrow_deriv_
   }
 }
 
+template <class Tb>
+__global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks)
+    jastrow_deriv_kernel(const SysDev s, const JasLayout L, int W, const double* __restrict__ Rg,
+                         const double* __restrict__ vgg, Tb* __restrict__ Og, Tb* __restrict__ dELg) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wl = threadIdx.x >> 5;
+  const int w = blockIdx.x * L.wpb + wl;
+  if (w >= W) return;
+  jastrow_deriv_body<Tb>(s, L, w, smem + wl * L.warp_bytes, Rg, vgg, Og, dELg);
+}
+
+template <class Tb>
+__global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks)
+    jastrow_deriv_batch_kernel(const BatchSys* __restrict__ sys, const BatchItem* __restrict__ items, int nitems) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wl = threadIdx.x >> 5;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    // the warps' shared-memory regions depend on the item's system: start together
+    __syncthreads();
+    const BatchItem item = items[it];
+    if (wl >= item.count) continue;
+    const BatchSys& b = sys[item.sys];
+    if (!b.O || !b.dev.jas_param) continue;
+    jastrow_deriv_body<Tb>(b.dev, b.lay.jas, item.first + wl, smem + wl * b.lay.jas.warp_bytes, b.R, b.VG,
+                           static_cast<Tb*>(b.O), static_cast<Tb*>(b.dEL));
+  }
+}
+
 }  // namespace
 
 int make_jas_layout(const SysDev& s, int tb, int max_smem, JasLayout& L) {
@@ -360,6 +405,32 @@ cudaError_t launch_jastrow_deriv(const SysDev& s, const JasLayout& L, int W, con
   jastrow_deriv_kernel<Tb><<<(W + L.wpb - 1) / L.wpb, 32 * L.wpb, smem, st>>>(s, L, W, R, vg, O, dEL);
   return cudaGetLastError();
 }
+
+template <class Tb>
+cudaError_t launch_jastrow_batch(const BatchSys* sys, const BatchItem* items, int nitems, int grid, int warps, int smem,
+                                 cudaStream_t st) {
+  jastrow_batch_kernel<Tb><<<grid, 32 * warps, smem, st>>>(sys, items, nitems);
+  return cudaGetLastError();
+}
+template <class Tb>
+cudaError_t launch_jastrow_deriv_batch(const BatchSys* sys, const BatchItem* items, int nitems, int grid, int warps,
+                                       int smem, cudaStream_t st) {
+  jastrow_deriv_batch_kernel<Tb><<<grid, 32 * warps, smem, st>>>(sys, items, nitems);
+  return cudaGetLastError();
+}
+int jastrow_batch_grid(int is_float, int deriv, int nitems, int warps, int smem, int persist) {
+  const void* fn = deriv ? (is_float ? (const void*)jastrow_deriv_batch_kernel<float>
+                                     : (const void*)jastrow_deriv_batch_kernel<double>)
+                         : (is_float ? (const void*)jastrow_batch_kernel<float> : (const void*)jastrow_batch_kernel<double>);
+  return batch_grid(fn, nitems, warps, smem, persist);
+}
+#define VBQ_INST(T)                                                                                                  \
+  template cudaError_t launch_jastrow_batch<T>(const BatchSys*, const BatchItem*, int, int, int, int, cudaStream_t); \
+  template cudaError_t launch_jastrow_deriv_batch<T>(const BatchSys*, const BatchItem*, int, int, int, int,         \
+                                                     cudaStream_t);
+VBQ_INST(float)
+VBQ_INST(double)
+#undef VBQ_INST
 
 template cudaError_t launch_jastrow<float>(const SysDev&, const JasLayout&, int, const double*, float*, float*,
                                            double*, cudaStream_t);

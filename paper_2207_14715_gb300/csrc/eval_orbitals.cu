@@ -6,6 +6,7 @@
 //   OD [W][N][n_det_ev] double: values of the orbitals that enter determinants; in the mixed
 //      form these come from float-float basis values and coefficients, and OB holds them
 //      rounded to float.
+#include "batch.h"
 #include "walker_common.cuh"
 
 namespace vbq {
@@ -14,17 +15,12 @@ namespace {
 
 constexpr int kOrbWarps = 8;
 
+// One warp, (walker, electron) pair gw (walker gw / N, electron gw % N).
 template <class Tb>
-__global__ void __launch_bounds__(32 * kOrbWarps, 4) orbital_kernel(const SysDev s, const OrbLayout L, int W,
-                                                                     const double* __restrict__ Rg,
-                                                                     Tb* __restrict__ OB, double* __restrict__ OD) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L, long long gw, unsigned char* base,
+                                             const double* __restrict__ Rg, Tb* __restrict__ OB,
+                                             double* __restrict__ OD) {
   const int lane = threadIdx.x & 31;
-  const int wl = threadIdx.x >> 5;
-  const int N = s.N;
-  const long long gw = (long long)blockIdx.x * kOrbWarps + wl;
-  if (gw >= (long long)W * N) return;  // warp gw: walker gw / N, electron gw % N
-  unsigned char* base = smem + wl * L.warp_bytes;
   const int nev = s.n_ev, nevd = s.n_ev_det, M = s.M;
   Tb* bv = reinterpret_cast<Tb*>(base + L.bas);
   Tb* bx = bv + M;
@@ -97,6 +93,33 @@ __global__ void __launch_bounds__(32 * kOrbWarps, 4) orbital_kernel(const SysDev
   }
 }
 
+template <class Tb>
+__global__ void __launch_bounds__(32 * kOrbWarps, 4) orbital_kernel(const SysDev s, const OrbLayout L, int W,
+                                                                     const double* __restrict__ Rg,
+                                                                     Tb* __restrict__ OB, double* __restrict__ OD) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wl = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * kOrbWarps + wl;
+  if (gw >= (long long)W * s.N) return;
+  orbital_body<Tb>(s, L, gw, smem + wl * L.warp_bytes, Rg, OB, OD);
+}
+
+template <class Tb>
+__global__ void __launch_bounds__(32 * kOrbWarps, 4)
+    orbital_batch_kernel(const BatchSys* __restrict__ sys, const BatchItem* __restrict__ items, int nitems) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wl = threadIdx.x >> 5;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    // the warps' shared-memory regions depend on the item's system: start together
+    __syncthreads();
+    const BatchItem item = items[it];
+    if (wl >= item.count) continue;
+    const BatchSys& b = sys[item.sys];
+    orbital_body<Tb>(b.dev, b.lay.orb, (long long)item.first + wl, smem + wl * b.lay.orb.warp_bytes, b.R,
+                     static_cast<Tb*>(b.OB), b.OD);
+  }
+}
+
 }  // namespace
 
 int make_orb_layout(const SysDev& s, int tb, int max_smem, OrbLayout& L) {
@@ -129,6 +152,19 @@ cudaError_t launch_orbitals(const SysDev& s, const OrbLayout& L, int W, const do
                                                                                                     OD);
   return cudaGetLastError();
 }
+
+template <class Tb>
+cudaError_t launch_orbitals_batch(const BatchSys* sys, const BatchItem* items, int nitems, int grid, int warps,
+                                  int smem, cudaStream_t st) {
+  orbital_batch_kernel<Tb><<<grid, 32 * warps, smem, st>>>(sys, items, nitems);
+  return cudaGetLastError();
+}
+int orbital_batch_grid(int is_float, int nitems, int warps, int smem, int persist) {
+  return batch_grid(is_float ? (const void*)orbital_batch_kernel<float> : (const void*)orbital_batch_kernel<double>,
+                    nitems, warps, smem, persist);
+}
+template cudaError_t launch_orbitals_batch<float>(const BatchSys*, const BatchItem*, int, int, int, int, cudaStream_t);
+template cudaError_t launch_orbitals_batch<double>(const BatchSys*, const BatchItem*, int, int, int, int, cudaStream_t);
 
 template cudaError_t launch_orbitals<float>(const SysDev&, const OrbLayout&, int, const double*, float*, double*,
                                             cudaStream_t);

@@ -4,6 +4,7 @@
 //
 // Precision: template parameter Tb is the bulk type (proposal rows and Jastrow changes); the
 // determinant ratios and Sherman-Morrison updates of the inverses are always double.
+#include "batch.h"
 #include "walker_common.cuh"
 
 namespace vbq {
@@ -15,17 +16,13 @@ namespace vbq {
 // the walker state written by the evaluation at the same positions, or from a fresh LU of
 // double-precision orbital values (first sweep without state, and every 'refresh' sweeps).
 // The proposed orbital row uses the bulk type; ratios and Sherman-Morrison updates are double.
+// One warp, walker w, shared-memory region 'base' of L.warp_bytes bytes.
 template <class Tb>
-__global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const SweepLayout L, int W, double* __restrict__ Rg,
-                                                    int nsweeps, int refresh, const double* __restrict__ state_in,
-                                                    double step, uint64_t seed, uint32_t step0, uint32_t tag,
-                                                    uint32_t woff, int* __restrict__ nacc) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L, int w, unsigned char* base,
+                                           double* __restrict__ Rg, int nsweeps, int refresh,
+                                           const double* __restrict__ state_in, double step, uint64_t seed,
+                                           uint32_t step0, uint32_t tag, uint32_t woff, int* __restrict__ nacc) {
   const int lane = threadIdx.x & 31;
-  const int wl = threadIdx.x >> 5;
-  const int w = blockIdx.x * L.wpb + wl;
-  if (w >= W) return;
-  unsigned char* base = smem + wl * L.warp_bytes;
   double* R = reinterpret_cast<double*>(base + L.R);
   double* Binv[2] = {reinterpret_cast<double*>(base + L.Binv0), reinterpret_cast<double*>(base + L.Binv1)};
   double* ldet = reinterpret_cast<double*>(base + L.ldet);
@@ -301,6 +298,36 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const Swe
   if (nacc && lane == 0) nacc[w] += accepted;
 }
 
+template <class Tb>
+__global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const SweepLayout L, int W, double* __restrict__ Rg,
+                                                    int nsweeps, int refresh, const double* __restrict__ state_in,
+                                                    double step, uint64_t seed, uint32_t step0, uint32_t tag,
+                                                    uint32_t woff, int* __restrict__ nacc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wl = threadIdx.x >> 5;
+  const int w = blockIdx.x * L.wpb + wl;
+  if (w >= W) return;
+  sweep_body<Tb>(s, L, w, smem + wl * L.warp_bytes, Rg, nsweeps, refresh, state_in, step, seed, step0, tag, woff, nacc);
+}
+
+// All systems of a batch: blocks loop over work items; warp wl takes walker first + wl.
+template <class Tb>
+__global__ void __launch_bounds__(512, 1) sweep_batch_kernel(const BatchSys* __restrict__ sys,
+                                                          const BatchItem* __restrict__ items, int nitems,
+                                                          const BatchCall* __restrict__ call) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wl = threadIdx.x >> 5;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    // the warps' shared-memory regions depend on the item's system: start together
+    __syncthreads();
+    const BatchItem item = items[it];
+    if (wl >= item.count) continue;
+    const BatchSys& b = sys[item.sys];
+    sweep_body<Tb>(b.dev, b.sweep, item.first + wl, smem + wl * b.sweep.warp_bytes, b.R, call->nsweeps, call->refresh,
+                   call->state_valid ? b.state : nullptr, call->step, call->seed, call->step0, b.tag, 0u, b.nacc);
+  }
+}
+
 // =====================================================================================
 // layouts and launchers
 // =====================================================================================
@@ -356,6 +383,32 @@ static cudaError_t launch_sweep_t(const SysDev& s, const SweepLayout& L, int W, 
                                                      woff, nacc);
   return cudaGetLastError();
 }
+
+template <class Tb>
+cudaError_t launch_sweep_batch(const BatchSys* sys, const BatchItem* items, int nitems, const BatchCall* call,
+                               int grid, int warps, int smem, cudaStream_t st) {
+  sweep_batch_kernel<Tb><<<grid, 32 * warps, smem, st>>>(sys, items, nitems, call);
+  return cudaGetLastError();
+}
+int batch_grid(const void* fn, int nitems, int warps, int smem, int persist) {
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return -1;
+  if (persist <= 0) return nitems;
+  int bps = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 32 * warps, smem) != cudaSuccess) return -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return -1;
+  const long long g = (long long)persist * std::max(bps, 1) * sms;
+  return (int)std::max<long long>(1, std::min<long long>(g, nitems));
+}
+int sweep_batch_grid(int is_float, int nitems, int warps, int smem, int persist) {
+  return batch_grid(is_float ? (const void*)sweep_batch_kernel<float> : (const void*)sweep_batch_kernel<double>, nitems,
+                    warps, smem, persist);
+}
+
+template cudaError_t launch_sweep_batch<float>(const BatchSys*, const BatchItem*, int, const BatchCall*, int, int, int,
+                                               cudaStream_t);
+template cudaError_t launch_sweep_batch<double>(const BatchSys*, const BatchItem*, int, const BatchCall*, int, int, int,
+                                                cudaStream_t);
 
 cudaError_t launch_sweep(int precision, const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps,
                          int refresh, const double* state_in, double step, uint64_t seed, uint32_t step0, uint32_t tag,

@@ -362,6 +362,120 @@ def small_open_shell(seed: int = 11, params: bool = True, een: bool = True) -> S
         kappa_kl=kap if params else np.zeros((0, 2), np.int32), step=0.4)
 
 
+def random_molecule(seed: int, max_electrons: int = 32) -> SystemSpec:
+    """One system of the batched workload of many small uneven molecules: 2-10 nuclei with Z in
+    {1, 3, 6, 7, 8, 9} at random positions at least 1.8 bohr apart, N = sum Z rounded up to
+    even and clamped to [2, max_electrons] (resampled while sum Z > max_electrons + 2), Sz = 0.
+    Per center 4-12 Gaussian shells split s:p:d about 5:3:2 (at least one s), exponents per
+    element log-uniform in [0.1, 20].  Orbitals: N/2 - k doubly occupied and 2k active
+    localised orbitals, placed on the nuclei in proportion to their charges, k = 0..4 distinct pairs per structure (fewer for
+    large N so that the unique determinants per spin stay within C(2k, k) <= 20 at n > 8);
+    2-16 structures drawn as random pairings of the active orbitals (covalent or ionic, duplicates
+    removed).  Jastrow e-n, e-e and e-e-n with small random polynomial parts; parameters: the
+    structure coefficients after the first and the Jastrow."""
+    rng = np.random.default_rng(seed)
+    zs = [1, 3, 6, 7, 8, 9]
+    while True:
+        Nn = int(rng.integers(2, 11))
+        Z = rng.choice(zs, size=Nn)
+        if Z.sum() <= max_electrons + 2:
+            break
+    N = int(min(max(2, Z.sum() + (Z.sum() % 2)), max_electrons))
+    n = N // 2
+    # positions: rejection sampling in a box that grows with the number of nuclei
+    box = 1.8 * (Nn ** (1.0 / 3.0)) + 1.0
+    xyz = []
+    while len(xyz) < Nn:
+        p = rng.uniform(-box, box, 3)
+        if all(np.linalg.norm(p - q) >= 1.8 for q in xyz):
+            xyz.append(p)
+    xyz = np.array(xyz, np.float64)
+    elems = sorted(set(int(z) for z in Z))
+    elem = np.array([elems.index(int(z)) for z in Z], np.int32)
+    # shells per element: 4-12 primitives, s:p:d about 5:3:2
+    shell_ls_elem = {}
+    for e in range(len(elems)):
+        nsh = int(rng.integers(4, 13))
+        nd = int(round(0.2 * nsh))
+        npp = int(round(0.3 * nsh))
+        ns = max(1, nsh - nd - npp)
+        shell_ls_elem[e] = [0] * ns + [1] * npp + [2] * nd
+    zeta_elem = {e: np.exp(rng.uniform(math.log(0.1), math.log(20.0), size=len(v))) for e, v in shell_ls_elem.items()}
+    sc, sl, sz = [], [], []
+    for c in range(Nn):
+        e = int(elem[c])
+        for l, z in zip(shell_ls_elem[e], zeta_elem[e]):
+            sc.append(c); sl.append(l); sz.append(z)
+    sc, sl, sz = np.array(sc, np.int32), np.array(sl, np.int32), np.array(sz, np.float64)
+    M = int(sum(NCOMP[l] for l in sl))
+    lo, hi = _basis_ranges(sc, sl, Nn)
+    # pairs per structure, limited by the size of the unique-determinant set
+    k = int(rng.integers(0, 5))
+    while k > 0 and (math.comb(2 * k, k) > (70 if n <= 8 else 20) or k > n):
+        k -= 1
+    n_inact = n - k
+    # orbital q sits on the nucleus that initial_walkers() places electrons 2q and 2q + 1 near
+    # (nuclei listed round(Z) times each), so that starting configurations are well conditioned
+    slots = []
+    for a, z in enumerate(Z):
+        slots += [a] * max(1, int(round(z)))
+    orbs, ocls, okind = [], [], []
+    for q in range(n_inact):
+        c = slots[(2 * q) % len(slots)]
+        orbs.append(_local_orbital(rng, M, lo, hi, sc, sl, c)); ocls.append(c); okind.append(0)
+    act = []
+    for q in range(2 * k):
+        c = slots[(2 * n_inact + q) % len(slots)]
+        act.append(len(orbs))
+        orbs.append(_local_orbital(rng, M, lo, hi, sc, sl, c)); ocls.append(c); okind.append(1)
+    orb = np.stack(orbs)
+    inactive = list(range(n_inact))
+    target = int(rng.integers(2, 17))
+    strs, seen = [], set()
+    for _ in range(200):
+        if len(strs) >= target:
+            break
+        perm = list(rng.permutation(act)) if k else []
+        prs = []
+        for q in range(k):
+            a, b = int(perm[2 * q]), int(perm[2 * q + 1])
+            if rng.uniform() < 0.2:   # ionic: both electrons of the pair on one orbital
+                b = a
+            prs.append((min(a, b), max(a, b)))
+        key = tuple(sorted(prs))
+        if key in seen:
+            continue
+        seen.add(key)
+        strs.append((inactive, prs, []))
+    io, ina, po, prs_arr, uo, un = _structures(strs)
+    nvb = len(strs)
+    c_vb = np.concatenate([[1.0], rng.uniform(0.1, 0.6, nvb - 1)])
+    n_elem = len(elems)
+    jas_a = np.zeros((n_elem, 6))
+    jas_a[:, 0] = -np.array(elems, np.float64)
+    jas_a[:, 1] = 1.0
+    jas_a[:, 2:] = rng.uniform(-0.05, 0.05, (n_elem, 4))
+    jas_b = np.zeros(6)
+    jas_b[1] = 1.0
+    jas_b[2:] = rng.uniform(-0.05, 0.05, 4)
+    return SystemSpec(
+        name="random_molecule_%d" % seed, nuc_xyz=xyz, nuc_Z=Z.astype(np.float64), nuc_elem=elem, n_elem=n_elem,
+        sh_center=sc, sh_l=sl, sh_zeta=sz, orb_coef=orb, orb_class=np.array(ocls, np.int32),
+        orb_kind=np.array(okind, np.int32), n_up=n, n_dn=n, c_vb=c_vb, inact_off=io, inact=ina, pair_off=po,
+        pairs=prs_arr, unp_off=uo, unp=un, jas_a=jas_a, jas_b=jas_b, een_on=True,
+        een_theta=rng.uniform(-0.02, 0.02, (n_elem, EEN_NFREE)),
+        cparam=np.arange(1, nvb, dtype=np.int32), jas_param=True, step=0.3)
+
+
+def batched_workload(n_systems: int = 64, seed: int = 20220728 + 2, w_lo: int = 256, w_hi: int = 4096):
+    """The batched workload: n_systems random molecules with walker counts drawn log-uniform
+    in [w_lo, w_hi] (rounded to multiples of 32).  Returns (specs, walker counts)."""
+    rng = np.random.default_rng(seed)
+    specs = [random_molecule(seed * 1000 + i) for i in range(n_systems)]
+    W = [int(round(math.exp(rng.uniform(math.log(w_lo), math.log(w_hi))) / 32.0)) * 32 for _ in range(n_systems)]
+    return specs, [max(32, w) for w in W]
+
+
 def initial_walkers(spec: SystemSpec, W: int, seed: int, sigma: float = 1.0) -> np.ndarray:
     """Walker positions (W, N, 3): electron e placed Gaussian(sigma) around a nucleus chosen
     round-robin over a list holding each nucleus round(Z) times; up and down electrons

@@ -52,7 +52,8 @@ class _Desc(ctypes.Structure):
 EXPORTED = ["vbqmc_create", "vbqmc_destroy", "vbqmc_last_error", "vbqmc_set_system", "vbqmc_inspect_system",
             "vbqmc_walker_state_size", "vbqmc_eval_walkers", "vbqmc_vmc_steps", "vbqmc_accumulate_lin_matrices",
             "vbqmc_launch_info", "vbqmc_last_launch_count", "vbqmc_accumulate_lin_matrices_noalloc",
-            "vbqmc_dmc_steps", "vbqmc_set_kernel_timing", "vbqmc_kernel_times"]
+            "vbqmc_dmc_steps", "vbqmc_set_kernel_timing", "vbqmc_kernel_times", "vbqmc_batch_create",
+            "vbqmc_batch_destroy", "vbqmc_batch_vmc_steps", "vbqmc_batch_tune", "vbqmc_batch_info"]
 
 _LIB = None
 
@@ -84,6 +85,13 @@ def lib():
                                       ctypes.c_double, _c_dbl_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
                                       ctypes.c_uint32, _c_dbl_p, _c_dbl_p, _c_int_p, _c_dbl_p,
                                       ctypes.POINTER(ctypes.c_int64), vp]
+        L.vbqmc_batch_create.argtypes = [vp, ctypes.c_int, _c_int_p, _c_int_p, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_void_p)]
+        L.vbqmc_batch_destroy.argtypes = [vp]
+        L.vbqmc_batch_vmc_steps.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                            ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
+        L.vbqmc_batch_tune.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.vbqmc_batch_info.argtypes = [vp, _c_int_p]
         L.vbqmc_set_kernel_timing.argtypes = [vp, ctypes.c_int]
         L.vbqmc_kernel_times.argtypes = [vp, _c_dbl_p, ctypes.c_int, _c_int_p]
         L.vbqmc_accumulate_lin_matrices_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp, vp,
@@ -309,6 +317,59 @@ def accumulate_lin_matrices_noalloc(precision, O, dEL, eloc, weights, E0, gL, gR
         _check(lib().vbqmc_accumulate_lin_matrices_noalloc(int(precision), int(P), int(M), _ptr(O), _ptr(dEL),
                                                            _ptr(eloc), _ptr(weights), _ptr(E0), _ptr(gL), _ptr(gR),
                                                            _ptr(S), _ptr(H), _stream(stream)))
+
+
+def _ptr_array(ts):
+    """Host array of device pointers (None -> NULL array)."""
+    if ts is None:
+        return None
+    arr = (ctypes.c_void_p * len(ts))(*[t.data_ptr() if t is not None else None for t in ts])
+    return arr
+
+
+class Batch:
+    """Several loaded systems run as one set of launches (vbqmc_batch_*).  Per-system arguments
+    are lists of CUDA tensors in the order of sys_ids."""
+
+    KINDS = ("sweep", "jastrow", "jastrow_deriv", "orbitals", "det")
+
+    def __init__(self, ctx: "Context", sys_ids, walkers, precision):
+        self.ctx = ctx
+        self.n = len(sys_ids)
+        ids = np.ascontiguousarray(sys_ids, np.int32)
+        W = np.ascontiguousarray(walkers, np.int32)
+        h = ctypes.c_void_p()
+        _check(lib().vbqmc_batch_create(ctx.h, self.n, _ip(ids), _ip(W), int(precision), ctypes.byref(h)))
+        self.h = h
+        self.precision = precision
+
+    def close(self):
+        if self.h:
+            lib().vbqmc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vmc_steps(self, R, nsweeps, step, seed, step0=0, refresh=1, state=None, state_valid=False, nacc=None,
+                  logpsi=None, sign=None, eloc=None, O=None, dEL=None, stream=None):
+        keep = [_ptr_array(x) for x in (R, state, nacc, logpsi, sign, eloc, O, dEL)]
+        _check(lib().vbqmc_batch_vmc_steps(self.h, keep[0], int(nsweeps), float(step), int(seed) & (2**64 - 1),
+                                           int(step0) & 0xffffffff, int(refresh), keep[1], 1 if state_valid else 0,
+                                           keep[2], keep[3], keep[4], keep[5], keep[6], keep[7], _stream(stream)))
+
+    def tune(self, R, logpsi, sign, eloc, stream=None):
+        keep = [_ptr_array(x) for x in (R, logpsi, sign, eloc)]
+        _check(lib().vbqmc_batch_tune(self.h, keep[0], keep[1], keep[2], keep[3], _stream(stream)))
+
+    def info(self):
+        out = np.zeros(25, np.int32)
+        _check(lib().vbqmc_batch_info(self.h, _ip(out)))
+        return {k: dict(zip(("items", "grid", "warps", "persist", "cap"), out[5 * i:5 * i + 5].tolist()))
+                for i, k in enumerate(self.KINDS)}
 
 
 def create(device: int = 0) -> Context:

@@ -1,0 +1,155 @@
+"""Batched systems: many small molecules of uneven size in one set of launches.
+
+The batch runs the per-system kernels' arithmetic on every system through work-item tables,
+so a batched step must reproduce the per-system calls (same Philox streams with the system id
+as tag) to rounding; random molecules are also checked against the oracle directly."""
+import numpy as np
+import pytest
+
+from paper_2207_14715_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_14715_gb300 import build, vbqmc
+    build.build()
+    ctx = vbqmc.create(0)
+    yield vbqmc, ctx
+    ctx.close()
+
+
+def load(vb, specs):
+    mod, ctx = vb
+    for k, sp in enumerate(specs):
+        ctx.set_system(k, sp)
+    return list(range(len(specs)))
+
+
+def buffers(mod, ctx, specs, W, prec, seed):
+    dev = "cuda"
+    out = {"R": [], "lp": [], "sg": [], "el": [], "O": [], "dE": [], "st": [], "na": []}
+    for k, (sp, w) in enumerate(zip(specs, W)):
+        out["R"].append(torch.tensor(S.initial_walkers(sp, w, seed + k), device=dev))
+        out["lp"].append(torch.zeros(w, dtype=torch.float64, device=dev))
+        out["sg"].append(torch.zeros(w, dtype=torch.float64, device=dev))
+        out["el"].append(torch.zeros(w, dtype=torch.float64, device=dev))
+        out["O"].append(torch.zeros((w, sp.n_params), dtype=mod.deriv_dtype(prec), device=dev))
+        out["dE"].append(torch.zeros_like(out["O"][-1]))
+        out["st"].append(torch.zeros((w, ctx.walker_state_size(k)), dtype=torch.float64, device=dev))
+        out["na"].append(torch.zeros(w, dtype=torch.int32, device=dev))
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_per_system_calls(vb, precision):
+    mod, ctx = vb
+    specs, _ = S.batched_workload(10, w_lo=32, w_hi=160)
+    ids = load(vb, specs)
+    W = [32 + 16 * k for k in range(len(specs))]
+    a = buffers(mod, ctx, specs, W, precision, 5)
+    b = buffers(mod, ctx, specs, W, precision, 5)
+    for step in range(2):
+        for k in ids:
+            ctx.vmc_steps(k, precision, a["R"][k], 2, specs[k].step, 77, step0=10 * step, system_tag=k, refresh=1,
+                          state=a["st"][k], state_valid=step > 0, nacc=a["na"][k], logpsi=a["lp"][k],
+                          sign=a["sg"][k], eloc=a["el"][k], O=a["O"][k], dEL=a["dE"][k])
+    batch = mod.Batch(ctx, ids, W, precision)
+    for step in range(2):
+        batch.vmc_steps(b["R"], 2, 0.3, 77, step0=10 * step, refresh=1, state=b["st"], state_valid=step > 0,
+                        nacc=b["na"], logpsi=b["lp"], sign=b["sg"], eloc=b["el"], O=b["O"], dEL=b["dE"])
+    torch.cuda.synchronize()
+    assert all(sp.step == 0.3 for sp in specs)
+    # positions and acceptances: identical (the same moves from the same random numbers);
+    # evaluated quantities: the same arithmetic inlined into another kernel, where the compiler
+    # may contract a few operations differently, so they agree to rounding amplified by the
+    # conditioning of the Slater matrices of these random molecules (relative to each array's
+    # scale; the float form to float rounding; the stored inverses of nearly singular matrices
+    # reach 1e10 here, hence their looser bound)
+    if precision == 0:
+        tol = {"lp": 1e-9, "sg": 0.0, "el": 1e-8, "st": 1e-6, "O": 1e-8, "dE": 1e-7}
+    else:
+        tol = {"lp": 1e-6, "sg": 0.0, "el": 1e-5, "st": 1e-4, "O": 1e-4, "dE": 1e-3}
+    for k in ids:
+        assert torch.equal(a["R"][k], b["R"][k]), k
+        assert torch.equal(a["na"][k], b["na"][k]), k
+        for key, t in tol.items():
+            x, y = a[key][k].double().cpu().numpy(), b[key][k].double().cpu().numpy()
+            scale = max(1.0, np.abs(x).max())
+            assert np.abs(x - y).max() <= t * scale, (key, k, np.abs(x - y).max() / scale)
+    batch.close()
+
+
+def test_batch_tune_and_replay(vb):
+    """The tuner picks launch shapes; replays of the captured graph agree with fresh per-system
+    evaluations of the walkers it moved."""
+    mod, ctx = vb
+    specs, _ = S.batched_workload(12, w_lo=64, w_hi=512)
+    ids = load(vb, specs)
+    W = [64 * (1 + k % 4) for k in range(len(specs))]
+    b = buffers(mod, ctx, specs, W, 1, 9)
+    batch = mod.Batch(ctx, ids, W, 1)
+    batch.tune(b["R"], b["lp"], b["sg"], b["el"])
+    info = batch.info()
+    assert all(info[k]["items"] > 0 for k in info)
+    for step in range(3):
+        batch.vmc_steps(b["R"], 1, 0.3, 5, step0=step, logpsi=b["lp"], sign=b["sg"], eloc=b["el"])
+    torch.cuda.synchronize()
+    for k in ids:
+        lp, sg, el = (torch.zeros_like(b["lp"][k]) for _ in range(3))
+        ctx.eval_walkers(k, 1, b["R"][k], lp, sg, el)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(lp.cpu().numpy(), b["lp"][k].cpu().numpy(), rtol=1e-6, atol=1e-6)
+        np.testing.assert_allclose(el.cpu().numpy(), b["el"][k].cpu().numpy(), rtol=1e-5, atol=1e-5)
+    batch.close()
+
+
+def test_random_molecules_match_oracle(vb, orc):
+    """FP64 evaluation of random molecules of the batched workload (2-32 electrons) against the
+    oracle, derivatives included."""
+    mod, ctx = vb
+    specs, _ = S.batched_workload(64)
+    picks = [sp for sp in specs if sp.N <= 12][:3] + [max(specs, key=lambda sp: sp.N)]
+    for k, sp in enumerate(picks):
+        ctx.set_system(k, sp)
+        R = S.initial_walkers(sp, 3, 40 + k)
+        Rt = torch.tensor(R, device="cuda")
+        lp, sg, el = (torch.zeros(3, dtype=torch.float64, device="cuda") for _ in range(3))
+        O = torch.zeros((3, sp.n_params), dtype=torch.float64, device="cuda")
+        dE = torch.zeros_like(O)
+        ctx.eval_walkers(k, 0, Rt, lp, sg, el, O=O, dEL=dE)
+        torch.cuda.synchronize()
+        ref = orc.evaluate(sp, R, derivs=True)
+        scale = max(1.0, np.abs(ref["logpsi"]).max())
+        assert np.abs(lp.cpu().numpy() - ref["logpsi"]).max() <= 1e-10 * scale, sp.name
+        np.testing.assert_array_equal(sg.cpu().numpy(), ref["sign"])
+        assert (np.abs(el.cpu().numpy() - ref["eloc"]) / np.maximum(1.0, np.abs(ref["eloc"]))).max() <= 1e-10, sp.name
+        np.testing.assert_allclose(O.cpu().numpy(), ref["O"], rtol=1e-8, atol=1e-8 * max(1.0, np.abs(ref["O"]).max()))
+        np.testing.assert_allclose(dE.cpu().numpy(), ref["dEL"], rtol=1e-7,
+                                   atol=1e-8 * max(1.0, np.abs(ref["dEL"]).max()))
+
+
+def test_full_batched_workload(vb):
+    """64 random molecules with 256-4096 walkers each, mixed form, one batch: a tuned step with
+    derivatives gives finite results and reproduces a per-system evaluation on a sample."""
+    mod, ctx = vb
+    specs, W = S.batched_workload(64)
+    ids = load(vb, specs)
+    b = buffers(mod, ctx, specs, W, 1, 3)
+    batch = mod.Batch(ctx, ids, W, 1)
+    batch.tune(b["R"], b["lp"], b["sg"], b["el"])
+    batch.vmc_steps(b["R"], 1, 0.3, 11, logpsi=b["lp"], sign=b["sg"], eloc=b["el"], O=b["O"], dEL=b["dE"],
+                    state=b["st"])
+    torch.cuda.synchronize()
+    for k in ids:
+        assert torch.isfinite(b["el"][k]).all() and torch.isfinite(b["O"][k]).all(), k
+    for k in (0, 17, 63):
+        lp, sg, el = (torch.zeros_like(b["lp"][k]) for _ in range(3))
+        ctx.eval_walkers(k, 1, b["R"][k], lp, sg, el)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(el.cpu().numpy(), b["el"][k].cpu().numpy(), rtol=1e-5, atol=1e-5)
+    batch.close()
