@@ -30,18 +30,18 @@ __device__ __forceinline__ void lu_det_all(const SysDev& s, int sp, int lane, co
     __syncwarp();
     return;
   }
-  const int ng = 32 / G, g = lane / G, gl = lane % G;
+  const LaneGroup lgp(lane, G);
+  const int ng = lgp.ng, g = lgp.g, gl = lgp.gl;
   double* A = scr + g * n * n;
   double* B = scr + ng * n * n + g * n * n;
   int* perm = reinterpret_cast<int*>(scr + 2 * ng * n * n) + g * n;
   for (int u0 = 0; u0 < U; u0 += ng) {
     const int u = u0 + g;
     const bool act = u < U;
-    if (act)
-      for (int q = gl; q < n * n; q += G) {
-        const int e = q / n, o = q % n;
-        A[q] = PhiD[(e0 + e) * ld + __ldg(idx + u * n + o)];
-      }
+    if (act && gl < n) {  // lane gl fills column (orbital slot) gl
+      const int col = __ldg(idx + u * n + gl);
+      for (int e = 0; e < n; ++e) A[e * n + gl] = PhiD[(e0 + e) * ld + col];
+    }
     __syncwarp();
     double lg, sg;
     group_lu_inverse(A, B, perm, n, gl, G, act, lg, sg);
@@ -233,8 +233,8 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
         const int eb = __ldg(s.kap_off[sp] + u), ee = __ldg(s.kap_off[sp] + u + 1);
         if (eb == ee) continue;
         const Tb* B = Bt[sp] + u * n * n;
-        for (int q = lane; q < n * nev; q += 32) {
-          const int o = q / nev, c = q % nev;
+        for (DivStep oc(lane, nev); oc.hi < n; oc.next(nev)) {
+          const int o = oc.hi, c = oc.lo, q = o * nev + c;
           Tb x = 0, y = 0;
           for (int e = 0; e < n; ++e) {
             const Tb b = B[o * n + e];

@@ -46,7 +46,7 @@ __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L
   const Tb* cE = een_coefs<Tb>(s);
   const int Pp = L.jas_P, Sg = L.jas_S;
   for (int b0 = 0; b0 < N; b0 += Pp) {
-    const int i = b0 + lane % Pp, gr = lane / Pp;
+    const int i = b0 + (lane & (Pp - 1)), gr = lane >> (__ffs(Pp) - 1);
     const bool act = i < N;
     Tb g0 = 0, g1 = 0, g2 = 0, lap = 0;
     LnSum<Tb> lnj;
@@ -201,8 +201,8 @@ __device__ __forceinline__ void jastrow_deriv_body(const SysDev& s, const JasLay
   // e-n: a_2..a_6 per element (lanes over electron-nucleus pairs)
   for (int E = 0; E < s.n_elem; ++E) {
     Tb aO[5] = {0, 0, 0, 0, 0}, aE[5] = {0, 0, 0, 0, 0};
-    for (int t = lane; t < N * Nn; t += 32) {
-      const int i = t / Nn, a = t % Nn;
+    for (DivStep ia(lane, Nn); ia.hi < N; ia.next(Nn)) {
+      const int i = ia.hi, a = ia.lo, t = i * Nn + a;
       if (__ldg(s.nuc_elem + a) != E) continue;
       const Tb r = g.rEN[t];
       const PadeT<Tb> c = en_coef_t<Tb>(s, a);
@@ -264,7 +264,7 @@ __device__ __forceinline__ void jastrow_deriv_body(const SysDev& s, const JasLay
 #pragma unroll
       for (int q = 0; q < kNeen; ++q) accO[q] = accE[q] = (Tb)0;
       for (int b0 = 0; b0 < N; b0 += Pp) {
-        const int i = b0 + lane % Pp, gr = lane / Pp;
+        const int i = b0 + (lane & (Pp - 1)), gr = lane >> (__ffs(Pp) - 1);
         if (i >= N) continue;
         const Tb vx = vg[3 * i], vy = vg[3 * i + 1], vz = vg[3 * i + 2];
         for (int a = gr; a < Nn; a += Sg) {

@@ -62,13 +62,13 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   }
   __syncwarp();
   // geometry tables
-  for (int p = lane; p < N * N; p += 32) {
-    const int i = p / N, j = p % N;
+  for (DivStep ij(lane, N); ij.hi < N; ij.next(N)) {
+    const int i = ij.hi, j = ij.lo, p = i * N + j;
     const Tb dx = C.ee(i, j, 0), dy = C.ee(i, j, 1), dz = C.ee(i, j, 2);
     rEE[p] = i == j ? (Tb)0 : vsqrt(dx * dx + dy * dy + dz * dz);
   }
-  for (int p = lane; p < N * Nn; p += 32) {
-    const int i = p / Nn, a = p % Nn;
+  for (DivStep ia(lane, Nn); ia.hi < N; ia.next(Nn)) {
+    const int i = ia.hi, a = ia.lo, p = i * Nn + a;
     const Tb dx = C.en(s, i, a, 0), dy = C.en(s, i, a, 1), dz = C.en(s, i, a, 2);
     const Tb r = vsqrt(dx * dx + dy * dy + dz * dz);
     rEN[p] = r;
@@ -173,7 +173,8 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
       }
       __syncwarp();
       // determinant ratios rho_u = sum_o v_occ(o) Binv_u[o][ie]
-      const int U = s.U[sp], ng = 32 / G, g = lane / G, gl = lane % G;
+      const LaneGroup lgp(lane, G);
+      const int U = s.U[sp], ng = lgp.ng, g = lgp.g, gl = lgp.gl;
       const int* dl = s.det_loc[sp];
       for (int ub = 0; ub < U; ub += ng) {
         const int u = ub + g;
@@ -267,17 +268,20 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           double* B = Binv[sp] + (act ? u : 0) * n * n;
           double* cv = cvec + g * n;
           if (act && gl < n) cv[gl] = B[gl * n + ie];
+          // 1/rho_u once per determinant (lane 0 of the group), broadcast in the group
+          double irho = (act && gl == 0) ? recip(rho[u]) : 0.0;
+          irho = __shfl_sync(kFull, irho, lane & ~(G - 1));
           __syncwarp();
           if (act && gl < n) {
             const int j = gl;
             double wj = (j == ie) ? -1.0 : 0.0;
             for (int o = 0; o < n; ++o) wj = fma(vrowd[__ldg(dl + u * n + o)], B[o * n + j], wj);
-            const double f = wj * recip(rho[u]);
+            const double f = wj * irho;
             for (int o = 0; o < n; ++o) B[o * n + j] = fma(-cv[o], f, B[o * n + j]);
           }
           __syncwarp();
         }
-        const double irphi = recip(rphi);
+        const double irphi = __shfl_sync(kFull, lane == 0 ? recip(rphi) : 0.0, 0);
         for (int k = lane; k < s.nterm; k += 32) wk[k] *= rho[__ldg(s.term_det + 2 * k + sp)] * irphi;
         if (lane < 3) {
           R[3 * e + lane] = lane == 0 ? rn[0] : (lane == 1 ? rn[1] : rn[2]);

@@ -145,12 +145,8 @@ template <> __device__ __forceinline__ PadeT<double> ee_coef_t<double>(const Sys
 template <> __device__ __forceinline__ PadeT<float> ee_coef_t<float>(const SysDev& s, bool same) {
   return load_pade<float>(s.jas_bf, same ? s.b1_par_f : s.b1_anti_f);
 }
-// 1/x to about 47 bits: float reciprocal refined by one Newton step in double (one division's
-// worth of FP64 work is ~20 instructions on this part; this is 3).
-__device__ __forceinline__ double recip(double x) {
-  double y = (double)__frcp_rn((float)x);
-  return y * fma(-x, y, 2.0);
-}
+// 1/x in double (the determinant-ratio updates); see recip_dd.
+__device__ __forceinline__ double recip(double x) { return recip_dd(x); }
 
 __device__ __forceinline__ PadeCoef en_coef(const SysDev& s, int a) {
   const double* p = s.jas_a + 6 * __ldg(s.nuc_elem + a);
@@ -193,17 +189,17 @@ __device__ __forceinline__ void lu_all(const SysDev& s, int sp, int lane, const 
     __syncwarp();
     return;
   }
-  const int ng = 32 / G, g = lane / G, gl = lane % G;
+  const LaneGroup lgp(lane, G);
+  const int ng = lgp.ng, g = lgp.g, gl = lgp.gl;
   double* A = scr + g * n * n;
   int* perm = reinterpret_cast<int*>(scr + ng * n * n) + g * n;
   for (int u0 = 0; u0 < U; u0 += ng) {
     const int u = u0 + g;
     const bool act = u < U;
-    if (act)
-      for (int q = gl; q < n * n; q += G) {
-        const int e = q / n, o = q % n;
-        A[q] = (double)Phi[(e0 + e) * ld + __ldg(idx + u * n + o)];
-      }
+    if (act && gl < n) {  // lane gl fills column (orbital slot) gl
+      const int col = __ldg(idx + u * n + gl);
+      for (int e = 0; e < n; ++e) A[e * n + gl] = (double)Phi[(e0 + e) * ld + col];
+    }
     __syncwarp();
     double lg, sg;
     double* B = Binv + (act ? u : 0) * n * n;
@@ -316,8 +312,8 @@ __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, cons
   const int N = s.N, Nn = s.Nn;
   const Tb kap = (Tb)s.kappa;
   Tb V_loc = 0;
-  for (int p = lane; p < N * N; p += 32) {
-    const int i = p / N, j = p % N;
+  for (DivStep ij(lane, N); ij.hi < N; ij.next(N)) {
+    const int i = ij.hi, j = ij.lo, p = i * N + j;
     if (i == j) {
       g.rEE[p] = (Tb)0; g.uEE[p] = (Tb)1; g.iEE[p] = (Tb)0;
       g.eEE[3 * p] = g.eEE[3 * p + 1] = g.eEE[3 * p + 2] = (Tb)0;
@@ -329,8 +325,8 @@ __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, cons
     g.eEE[3 * p] = dx * ir; g.eEE[3 * p + 1] = dy * ir; g.eEE[3 * p + 2] = dz * ir;
     if (i < j) V_loc += ir;
   }
-  for (int p = lane; p < N * Nn; p += 32) {
-    const int i = p / Nn, a = p % Nn;
+  for (DivStep ia(lane, Nn); ia.hi < N; ia.next(Nn)) {
+    const int i = ia.hi, a = ia.lo, p = i * Nn + a;
     const Tb dx = C.en(s, i, a, 0), dy = C.en(s, i, a, 1), dz = C.en(s, i, a, 2);
     const Tb r = vsqrt(dx * dx + dy * dy + dz * dz), ir = (Tb)1 / r;
     g.rEN[p] = r;
@@ -344,7 +340,7 @@ __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, cons
   }
   __syncwarp();
   for (int p = lane; p < Nn * 6; p += 32) {
-    const int a = p / 6, q = p % 6;
+    const int a = p / 6, q = p - 6 * a;
     Tb t = 0;
     for (int i = 0; i < N; ++i) t += g.Stab[(a * N + i) * 6 + q];
     g.Ssum[p] = t;

@@ -16,6 +16,30 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ int lane_id() { return (int)(threadIdx.x & 31); }
 
+// (q / d, q % d) along q = q0, q0 + 32, q0 + 64, ... without integer division (which this
+// part executes through conversions on its slow double-precision pipe): divide once by
+// subtraction (q0 < 32), then step.
+struct DivStep {
+  int hi, lo;
+  __device__ __forceinline__ DivStep(int q0, int d) : hi(0), lo(q0) {
+    while (lo >= d) { lo -= d; ++hi; }
+  }
+  __device__ __forceinline__ void next(int d) {
+    lo += 32;
+    while (lo >= d) { lo -= d; ++hi; }
+  }
+};
+// lane-group coordinates for a power-of-two group size G
+struct LaneGroup {
+  int ng, g, gl;
+  __device__ __forceinline__ LaneGroup(int lane, int G) {
+    const int lg = __ffs(G) - 1;
+    ng = 32 >> lg;
+    g = lane >> lg;
+    gl = lane & (G - 1);
+  }
+};
+
 // ------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from the published round function.
 // ------------------------------------------------------------------------------------
@@ -62,6 +86,21 @@ template <class T> __device__ __forceinline__ T group_sum(T v, int G) {
   return v;
 }
 
+// 1/x in double, a few FP64 instructions instead of a division: x = m 2^k with m in [1, 2)
+// (read from the bit pattern), the float reciprocal of m refined by two Newton steps (each
+// doubles the correct bits: 2^-23 -> 2^-46 -> below double rounding), scaled by 2^-k.  Zero,
+// subnormal, huge and non-finite x take the division.
+__device__ __forceinline__ double recip_dd(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e <= 1 || e >= 2045) return 1.0 / x;
+  const double m = __longlong_as_double((b & (long long)0x800fffffffffffffull) | 0x3ff0000000000000ll);
+  double y = (double)__frcp_rn((float)m);
+  y = y * fma(-m, y, 2.0);
+  y = y * fma(-m, y, 2.0);
+  return y * __longlong_as_double((long long)(2046 - e) << 52);
+}
+
 // ------------------------------------------------------------------------------------
 // Lane-group LU with partial pivoting and explicit inverse.
 // A (n x n, row-major, rows = electrons, columns = orbital slots) is overwritten with its
@@ -101,8 +140,12 @@ __device__ __forceinline__ void group_lu_inverse(double* A, double* Binv, int* p
       s = -s;
     }
     __syncwarp();
+    // pivot reciprocal: computed by the pivot lane and broadcast (one reciprocal per column)
+    double ip = 0.0;
+    if (active && !singular && glane == c) ip = recip_dd(A[c * n + c]);
+    ip = __shfl_sync(kFull, ip, (lane_id() & ~(G - 1)) + c);
     if (active && !singular && glane > c && glane < n) {
-      const double l = A[glane * n + c] / A[c * n + c];
+      const double l = A[glane * n + c] * ip;
       A[glane * n + c] = l;
       for (int j = c + 1; j < n; ++j) A[glane * n + j] = fma(-l, A[c * n + j], A[glane * n + j]);
     }
@@ -110,7 +153,7 @@ __device__ __forceinline__ void group_lu_inverse(double* A, double* Binv, int* p
   }
   // reciprocal of the U diagonal: lane i of the group holds 1/U_ii; the back substitution
   // multiplies by it (broadcast by shuffle) instead of dividing in every lane
-  const double dinv = (active && glane < n && !singular) ? 1.0 / A[glane * n + glane] : 0.0;
+  const double dinv = (active && glane < n && !singular) ? recip_dd(A[glane * n + glane]) : 0.0;
   if (active && glane < n) {
     const int j = glane;
     if (!singular) {
@@ -133,20 +176,28 @@ __device__ __forceinline__ void group_lu_inverse(double* A, double* Binv, int* p
     }
   }
 
-  double ld = 0.0, neg = 0.0;
+  // ln|det| = ln prod |U_ii|: the product of the mantissas (each in [1, 2)) and the sum of the
+  // binary exponents over the group, then one logarithm (no overflow for n <= 32)
+  double mant = 1.0;
+  int ex = 0, neg = 0;
   if (active && glane < n && !singular) {
     const double d = A[glane * n + glane];
-    ld = log(fabs(d));
-    neg = d < 0.0 ? 1.0 : 0.0;
+    const long long bits = __double_as_longlong(fabs(d));
+    ex = (int)((bits >> 52) & 0x7ff) - 1023;
+    mant = __longlong_as_double((bits & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
+    neg = d < 0.0 ? 1 : 0;
   }
-  ld = group_sum(ld, G);
-  neg = group_sum(neg, G);
+  for (int o = G >> 1; o > 0; o >>= 1) {
+    mant *= __shfl_xor_sync(kFull, mant, o, G);
+    ex += __shfl_xor_sync(kFull, ex, o, G);
+    neg += __shfl_xor_sync(kFull, neg, o, G);
+  }
   if (singular) {
     logdet = -INFINITY;
     sgn = 0.0;
   } else {
-    logdet = ld;
-    sgn = (((int)neg) & 1) ? -s : s;
+    logdet = log(mant) + (double)ex * 0.6931471805599453;
+    sgn = (neg & 1) ? -s : s;
   }
   __syncwarp();
 }
