@@ -36,8 +36,10 @@ __device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L
   if constexpr (kSameType<Tb, double>) {
     basis_at<double, true>(s, lane, r[0], r[1], r[2], bv, bx, by, bz, bl);
   } else {
+    // float form: value and gradient of a basis function interleaved as one float4 (one
+    // shared-memory load per function and coefficient), Laplacians after them
     const dsf r3[3] = {ds_from_double(r[0]), ds_from_double(r[1]), ds_from_double(r[2])};
-    basis_at_f<true>(s, lane, r3, bv, bx, by, bz, bl);
+    basis_at_f<true>(s, lane, r3, bv, bv + 1, bv + 2, bv + 3, bv + 4 * M, 4);
     basis_values_ds(s, lane, r3, ctab, bds);
   }
   __syncwarp();
@@ -45,9 +47,19 @@ __device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L
     const int4 ch = __ldg(reinterpret_cast<const int4*>(s.ev_chunk) + c);
     const Tb* cb = cf + ch.w;
     Tb v = 0, gx = 0, gy = 0, gz = 0, lp = 0;
-    for (int mu = ch.y; mu < ch.z; ++mu) {
-      const Tb cm = __ldg(cb + mu);
-      v += cm * bv[mu]; gx += cm * bx[mu]; gy += cm * by[mu]; gz += cm * bz[mu]; lp += cm * bl[mu];
+    if constexpr (kSameType<Tb, double>) {
+      for (int mu = ch.y; mu < ch.z; ++mu) {
+        const Tb cm = __ldg(cb + mu);
+        v += cm * bv[mu]; gx += cm * bx[mu]; gy += cm * by[mu]; gz += cm * bz[mu]; lp += cm * bl[mu];
+      }
+    } else {
+      const float4* b4 = reinterpret_cast<const float4*>(bv);
+      const float* blf = reinterpret_cast<const float*>(bv) + 4 * M;
+      for (int mu = ch.y; mu < ch.z; ++mu) {
+        const float cm = __ldg(cb + mu);
+        const float4 b = b4[mu];
+        v += cm * b.x; gx += cm * b.y; gy += cm * b.z; gz += cm * b.w; lp += cm * blf[mu];
+      }
     }
     Tb* pp = part + 5 * c;
     pp[0] = v; pp[1] = gx; pp[2] = gy; pp[3] = gz; pp[4] = lp;

@@ -127,15 +127,26 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
       __syncwarp();
     }
     const uint32_t st = step0 + (uint32_t)sw;
+    // the sweep's random numbers, one electron per lane: displacement step (2u - 1) per
+    // coordinate and the acceptance uniform
+    double* rtab = reinterpret_cast<double*>(base + L.rtab);
+    for (int e = lane; e < N; e += 32) {
+      double u0, u1, u2, ua;
+      uniforms2(seed, wid, st, (uint32_t)e, tag, 0, u0, u1);
+      uniforms2(seed, wid, st, (uint32_t)e, tag, 1, u2, ua);
+      rtab[4 * e] = __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u0), 1.0));
+      rtab[4 * e + 1] = __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u1), 1.0));
+      rtab[4 * e + 2] = __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u2), 1.0));
+      rtab[4 * e + 3] = ua;
+    }
+    __syncwarp();
     for (int e = 0; e < N; ++e) {
       const int sp = e >= Nup ? 1 : 0, ie = e - (sp ? Nup : 0), n = s.n[sp], G = sp ? L.G1 : L.G0;
-      double u0, u1, u2, uacc;
-      uniforms2(seed, wid, st, (uint32_t)e, tag, 0, u0, u1);
-      uniforms2(seed, wid, st, (uint32_t)e, tag, 1, u2, uacc);
+      const double uacc = rtab[4 * e + 3];
       double rn[3];
-      rn[0] = __dadd_rn(R[3 * e], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u0), 1.0)));
-      rn[1] = __dadd_rn(R[3 * e + 1], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u1), 1.0)));
-      rn[2] = __dadd_rn(R[3 * e + 2], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u2), 1.0)));
+      rn[0] = __dadd_rn(R[3 * e], rtab[4 * e]);
+      rn[1] = __dadd_rn(R[3 * e + 1], rtab[4 * e + 1]);
+      rn[2] = __dadd_rn(R[3 * e + 2], rtab[4 * e + 2]);
       // the proposed position as the bulk-type arithmetic reads it
       dsf rnd[3];
       if constexpr (!kSameType<Tb, double>) {
@@ -348,6 +359,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.nocc_max = std::max(std::max(s.nocc[0], s.nocc[1]), 1);
   L.R = take(8 * 3 * N);
   L.Rds = take(tb == 4 ? 8 * 3 * N : 16);
+  L.rtab = take(8 * 4 * N);
   L.Binv0 = take(8 * s.U[0] * s.n[0] * s.n[0]);
   L.Binv1 = take(8 * s.U[1] * s.n[1] * s.n[1]);
   L.ldet = take(8 * Ut);

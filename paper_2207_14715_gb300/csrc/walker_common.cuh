@@ -62,15 +62,15 @@ __device__ __forceinline__ dsf nuc_coord_ds(const SysDev& s, int a, int d) {
 }
 template <bool DERIV>
 __device__ __forceinline__ void basis_at_f(const SysDev& s, int lane, const dsf* r3, float* bv, float* bx, float* by,
-                                           float* bz, float* bl) {
+                                           float* bz, float* bl, int cs = 1) {
   for (int sh = lane; sh < s.S; sh += 32) {
     const int c = __ldg(s.sh_center + sh);
     const int f = __ldg(s.sh_first + sh);
     const float dx = ds_diff_f(r3[0], nuc_coord_ds(s, c, 0)), dy = ds_diff_f(r3[1], nuc_coord_ds(s, c, 1)),
                 dz = ds_diff_f(r3[2], nuc_coord_ds(s, c, 2));
-    gto_shell<float, DERIV>(__ldg(s.sh_l + sh), __ldg(s.sh_zeta_f + sh), s.sh_norm_f + 6 * sh, dx, dy, dz, bv + f,
-                            DERIV ? bx + f : nullptr, DERIV ? by + f : nullptr, DERIV ? bz + f : nullptr,
-                            DERIV ? bl + f : nullptr);
+    gto_shell<float, DERIV>(__ldg(s.sh_l + sh), __ldg(s.sh_zeta_f + sh), s.sh_norm_f + 6 * sh, dx, dy, dz,
+                            bv + f * cs, DERIV ? bx + f * cs : nullptr, DERIV ? by + f * cs : nullptr,
+                            DERIV ? bz + f * cs : nullptr, DERIV ? bl + f : nullptr, cs);
   }
 }
 

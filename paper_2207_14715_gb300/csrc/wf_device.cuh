@@ -221,7 +221,7 @@ template <class T> __device__ __forceinline__ T tload(const double* p) { return 
 // ------------------------------------------------------------------------------------
 template <class T, bool DERIV, class NT>
 __device__ __forceinline__ void gto_shell(int l, T z, const NT* nrm, T dx, T dy, T dz, T* val, T* gx, T* gy, T* gz,
-                                          T* lap) {
+                                          T* lap, int cs = 1) {
   const T r2 = dx * dx + dy * dy + dz * dz;
   const T e = (z == (T)0) ? (T)1 : vexp(-z * r2);
   const T tz = (T)2 * z;
@@ -239,11 +239,11 @@ __device__ __forceinline__ void gto_shell(int l, T z, const NT* nrm, T dx, T dy,
     for (int c = 0; c < 3; ++c) {
       const T ne = (T)nrm[c] * e;
       const T P = d[c];
-      val[c] = ne * P;
+      val[c * cs] = ne * P;
       if (DERIV) {
-        gx[c] = ne * ((c == 0 ? (T)1 : (T)0) - tz * dx * P);
-        gy[c] = ne * ((c == 1 ? (T)1 : (T)0) - tz * dy * P);
-        gz[c] = ne * ((c == 2 ? (T)1 : (T)0) - tz * dz * P);
+        gx[c * cs] = ne * ((c == 0 ? (T)1 : (T)0) - tz * dx * P);
+        gy[c * cs] = ne * ((c == 1 ? (T)1 : (T)0) - tz * dy * P);
+        gz[c * cs] = ne * ((c == 2 ? (T)1 : (T)0) - tz * dz * P);
         lap[c] = ne * P * base;
       }
     }
@@ -256,7 +256,7 @@ __device__ __forceinline__ void gto_shell(int l, T z, const NT* nrm, T dx, T dy,
     for (int c = 0; c < 6; ++c) {
       const T ne = (T)nrm[c] * e;
       const T P = d[ia[c]] * d[ib[c]];
-      val[c] = ne * P;
+      val[c * cs] = ne * P;
       if (DERIV) {
         T g[3];
 #pragma unroll
@@ -266,7 +266,7 @@ __device__ __forceinline__ void gto_shell(int l, T z, const NT* nrm, T dx, T dy,
           if (ib[c] == q) dP += d[ia[c]];
           g[q] = ne * (dP - tz * d[q] * P);
         }
-        gx[c] = g[0]; gy[c] = g[1]; gz[c] = g[2];
+        gx[c * cs] = g[0]; gy[c * cs] = g[1]; gz[c * cs] = g[2];
         const T lapP = (c < 3) ? (T)2 : (T)0;
         lap[c] = ne * (lapP + P * base);
       }
