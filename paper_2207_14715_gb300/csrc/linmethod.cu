@@ -124,23 +124,25 @@ __global__ void lin_center_kernel(int P, long long M, long long Mp, const Tin* _
 
 // Partial tiles: part[chunk][0][i][j] = sum_{s in chunk} w_s X_si X_sj,
 //                part[chunk][1][i][j] = sum_{s in chunk} w_s X_si Y_sj,
-// one CTA per (128 x 128 output tile, chunk).  Per step of 32 samples, TMA brings the tiles
-// A = Xt[i0..i0+127][s..s+31], Bx = Xt[j0..][s..], By = Yt[j0..][s..] into shared memory,
-// K-major with the 128-byte swizzle (the layout the MMA reads).  The threads split each value
-// into TF32 parts x = hi + lo (hi: low 13 mantissa bits cleared, written back in place; lo in a
-// second tile at the same offsets), and one thread issues the 8-sample MMAs A_hi B_lo and
-// A_lo B_hi (first, while the accumulator is small) and A_hi B_hi into two 128 x 128 FP32
-// accumulators in tensor memory, starting from zero every step.  The tensor core's
-// accumulation rounds at the accumulator's magnitude, so each step's result is moved to
-// registers and summed there in FP32 (round to nearest) instead of accumulating the whole
-// chunk in tensor memory.  Two stages (shared memory and tensor-memory sets) alternate: the
-// TMA of step k+1 and the draining of step k-1 overlap the MMAs of step k.  Barrier waits are
-// bounded (about a second); on a timeout the CTA raises *err and stops.
+// one CTA per (128 x 128 output tile, chunk).  Per step of 16 samples, TMA brings the tiles
+// A = Xt[i0..i0+127][s..s+15], Bx = Xt[j0..][s..], By = Yt[j0..][s..] into shared memory,
+// K-major with the 64-byte swizzle (the layout the MMA reads), four steps in flight.  Each
+// value is x = hi + lo with hi = x with its low 13 mantissa bits cleared, which is what the
+// tensor core reads of the raw tile as TF32; the threads write lo = x - hi to a second tile
+// at the same offsets.  One thread issues the 8-sample MMAs A_hi B_lo and A_lo B_hi (first,
+// while the accumulator is small) and A_hi B_hi, B = [w X_j; w Y_j] (256 rows), into one
+// 128 x 256 FP32 accumulator in tensor memory (S and H side by side), starting from zero every
+// second step.  The tensor core's accumulation rounds at the accumulator's magnitude, so every
+// 32 samples the result is moved to registers and summed there in FP32 (round to nearest)
+// instead of accumulating the whole chunk in tensor memory.  Two tensor-memory sets alternate
+// so that draining overlaps the MMAs.  Barrier waits are bounded (about a second); on a
+// timeout the CTA raises *err and stops.
 constexpr int kTcThreads = 256;
-constexpr int kTcK = 32;                              // samples per step (128 bytes of TF32)
-constexpr int kTileBytes = kTile * kTcK * 4;          // one 128 x 32 TF32 tile: 16 KB
-constexpr int kStageBytes = 6 * kTileBytes;           // A hi/lo, Bx hi/lo, By hi/lo
-constexpr int kTcSmem = 2 * kStageBytes + 1024 + 64;  // two stages, alignment, barriers
+constexpr int kTcK = 16;                               // samples per step (64 bytes of TF32)
+constexpr int kStages = 4;                             // steps in flight
+constexpr int kTileBytes = kTile * kTcK * 4;           // one 128 x 16 TF32 tile: 8 KB
+constexpr int kStageBytes = 6 * kTileBytes;            // A hi/lo, Bx hi/lo, By hi/lo
+constexpr int kTcSmem = kStages * kStageBytes + 1024 + 128;  // stages, alignment, barriers
 constexpr uint64_t kWaitNs = 1000000000ull;
 
 // adds this thread's 128 accumulator columns of TMEM set 'set' to acc (warp w: lanes
@@ -160,31 +162,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     lin_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int Pp,
                   long long M, long long chunk, double* __restrict__ part, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
-  // 1024-byte aligned stage buffers (required by the swizzle), barriers after them
+  // 1024-byte aligned stage buffers (the swizzle needs 512), barriers after them
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + 2 * kStageBytes);  // [2] TMA arrivals
-  uint64_t* done = full + 2;                                            // [2] MMA completions
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 2);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kStages * kStageBytes);  // [kStages] TMA arrivals
+  uint64_t* done = full + kStages;                                            // [kStages] MMA completions
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + kStages);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int ntj = Pp / kTile;
   const int ti = blockIdx.x / ntj, tj = blockIdx.x % ntj;
   const int i0 = ti * kTile, j0 = tj * kTile;
   const long long s0 = (long long)blockIdx.y * chunk, s1 = min(M, s0 + chunk);
   const int nsteps = (int)((s1 - s0 + kTcK - 1) / kTcK);
-  // tiles of a stage: 0 A_hi, 1 A_lo, 2 Bx_hi, 3 Bx_lo, 4 By_hi, 5 By_lo
+  // tiles of a stage: 0 A_hi, 1 A_lo, 2 Bx_hi, 3 By_hi, 4 Bx_lo, 5 By_lo; Bx and By of one part
+  // are adjacent, so that they form one 256-row B operand [w X_j; w Y_j]
   auto tile = [&](int st, int t) { return sm + st * kStageBytes + t * kTileBytes; };
   int loaded = 0;  // (thread 0) steps whose TMA was issued
-  auto load = [&](int ks) {  // thread 0: TMA of step ks into stage ks & 1
-    const int st = ks & 1, x = (int)(s0 + (long long)ks * kTcK);
+  auto load = [&](int ks) {  // thread 0: TMA of step ks into stage ks % kStages
+    const int st = ks % kStages, x = (int)(s0 + (long long)ks * kTcK);
     loaded = ks + 1;
     mbar_arrive_expect_tx(&full[st], 3 * kTileBytes);
     tma_load_2d(tile(st, 0), &tmX, x, i0, &full[st]);
     tma_load_2d(tile(st, 2), &tmX, x, j0, &full[st]);
-    tma_load_2d(tile(st, 4), &tmY, x, j0, &full[st]);
+    tma_load_2d(tile(st, 3), &tmY, x, j0, &full[st]);
   };
 
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kStages; ++b) {
       mbar_init(&full[b], 1);
       mbar_init(&done[b], 1);
     }
@@ -195,31 +198,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
-  if (tid == 0 && nsteps > 0) load(0);
-  constexpr uint32_t idesc = idesc_tf32(128, 128);
+  if (tid == 0)
+    for (int ks = 0; ks < kStages && ks < nsteps; ++ks) load(ks);
+  constexpr uint32_t idesc = idesc_tf32(128, 256);
   float acc[kTile];
 #pragma unroll
   for (int c = 0; c < kTile; ++c) acc[c] = 0.0f;
   bool ok = true;
-  int issued = 0;                   // steps whose MMAs were issued
-  int drained = 0;                  // steps whose results were added to acc
+  int issued = 0;   // steps whose MMAs were issued
+  int drained = 0;  // steps whose results were added to acc
 
   for (int ks = 0; ks < nsteps; ++ks) {
-    const int st = ks & 1;
-    ok = __syncthreads_and(mbar_wait(&full[st], (uint32_t)((ks >> 1) & 1), kWaitNs)) != 0;
+    // steps 2p and 2p + 1 accumulate into tensor-memory set p & 1
+    const int st = ks % kStages, set = (ks >> 1) & 1;
+    ok = __syncthreads_and(mbar_wait(&full[st], (uint32_t)((ks / kStages) & 1), kWaitNs)) != 0;
     if (!ok) break;
-    // split into TF32 high and low parts (elementwise: the swizzled layout is kept)
+    // low TF32 parts lo = x - hi (hi: x with its low 13 mantissa bits cleared, which is what
+    // the tensor core reads of x) in a second tile at the same (swizzled) offsets
     for (int t = 0; t < 3; ++t) {
-      float4* hi = reinterpret_cast<float4*>(tile(st, 2 * t));
-      float4* lo = reinterpret_cast<float4*>(tile(st, 2 * t + 1));
+      const int th = t == 0 ? 0 : 1 + t, tl = t == 0 ? 1 : 3 + t;  // (0, 1), (2, 4), (3, 5)
+      const float4* hi = reinterpret_cast<const float4*>(tile(st, th));
+      float4* lo = reinterpret_cast<float4*>(tile(st, tl));
       for (int q = tid; q < kTileBytes / 16; q += kTcThreads) {
         const float4 x = hi[q];
-        const float4 h = make_float4(__uint_as_float(__float_as_uint(x.x) & 0xffffe000u),
-                                     __uint_as_float(__float_as_uint(x.y) & 0xffffe000u),
-                                     __uint_as_float(__float_as_uint(x.z) & 0xffffe000u),
-                                     __uint_as_float(__float_as_uint(x.w) & 0xffffe000u));
-        hi[q] = h;
-        lo[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        lo[q] = make_float4(x.x - __uint_as_float(__float_as_uint(x.x) & 0xffffe000u),
+                            x.y - __uint_as_float(__float_as_uint(x.y) & 0xffffe000u),
+                            x.z - __uint_as_float(__float_as_uint(x.z) & 0xffffe000u),
+                            x.w - __uint_as_float(__float_as_uint(x.w) & 0xffffe000u));
       }
     }
     fence_async_smem();
@@ -228,53 +233,51 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (tid == 0) {
       tc_fence_after();
       const uint32_t a_hi = smem_addr(tile(st, 0)), a_lo = a_hi + kTileBytes;
-      const uint32_t bx_hi = a_hi + 2 * kTileBytes, bx_lo = a_hi + 3 * kTileBytes;
-      const uint32_t by_hi = a_hi + 4 * kTileBytes, by_lo = a_hi + 5 * kTileBytes;
-      const uint32_t dS = tmem + 256 * st, dH = dS + 128;
+      const uint32_t b_hi = a_hi + 2 * kTileBytes, b_lo = a_hi + 4 * kTileBytes;
+      const uint32_t d = tmem + 256 * set;  // S in columns 0..127, H in 128..255
+      const bool fresh = (ks & 1) == 0;
 #pragma unroll
       for (int kk = 0; kk < kTcK / 8; ++kk) {
         const uint32_t ko = kk * 32;  // 8 TF32 = 32 bytes along the swizzled row
-        mma_tf32(dS, smem_desc_k128(a_hi + ko), smem_desc_k128(bx_lo + ko), idesc, kk > 0 ? 1u : 0u);
-        mma_tf32(dS, smem_desc_k128(a_lo + ko), smem_desc_k128(bx_hi + ko), idesc, 1u);
-        mma_tf32(dH, smem_desc_k128(a_hi + ko), smem_desc_k128(by_lo + ko), idesc, kk > 0 ? 1u : 0u);
-        mma_tf32(dH, smem_desc_k128(a_lo + ko), smem_desc_k128(by_hi + ko), idesc, 1u);
+        mma_tf32(d, smem_desc_k64(a_hi + ko), smem_desc_k64(b_lo + ko), idesc, (fresh && kk == 0) ? 0u : 1u);
+        mma_tf32(d, smem_desc_k64(a_lo + ko), smem_desc_k64(b_hi + ko), idesc, 1u);
       }
 #pragma unroll
-      for (int kk = 0; kk < kTcK / 8; ++kk) {
-        const uint32_t ko = kk * 32;
-        mma_tf32(dS, smem_desc_k128(a_hi + ko), smem_desc_k128(bx_hi + ko), idesc, 1u);
-        mma_tf32(dH, smem_desc_k128(a_hi + ko), smem_desc_k128(by_hi + ko), idesc, 1u);
-      }
+      for (int kk = 0; kk < kTcK / 8; ++kk)
+        mma_tf32(d, smem_desc_k64(a_hi + kk * 32), smem_desc_k64(b_hi + kk * 32), idesc, 1u);
       mma_commit(&done[st]);
     }
     issued = ks + 1;
     if (ks >= 1) {
-      // MMAs of step ks-1 done: their stage can be refilled and their accumulators drained
-      ok = __syncthreads_and(mbar_wait(&done[st ^ 1], (uint32_t)(((ks - 1) >> 1) & 1), kWaitNs)) != 0;
+      // MMAs of step ks-1 done: refill its stage with step ks+3; after the second step of a
+      // pair, drain the pair's accumulators
+      const int pk = ks - 1, pst = pk % kStages;
+      ok = __syncthreads_and(mbar_wait(&done[pst], (uint32_t)((pk / kStages) & 1), kWaitNs)) != 0;
       if (!ok) break;
-      if (tid == 0 && ks + 1 < nsteps) load(ks + 1);
-      tc_fence_after();
-      drain(tmem, st ^ 1, warp, acc);
-      drained = ks;
-      tc_fence_before();
-    } else if (tid == 0 && nsteps > 1) {
-      load(1);
+      if (tid == 0 && pk + kStages < nsteps) load(pk + kStages);
+      if (pk & 1) {
+        tc_fence_after();
+        drain(tmem, (pk >> 1) & 1, warp, acc);
+        drained = pk + 1;
+        tc_fence_before();
+      }
     }
   }
-  // the last issued step: wait and drain; on a timeout, still give the copies and MMAs in
-  // flight a bounded wait before the shared and tensor memory are released
+  // the steps not yet drained (the last pair): wait for the last MMAs and drain; on a
+  // timeout, still give the copies and MMAs in flight a bounded wait before the shared and
+  // tensor memory are released
   if (issued > 0 && drained < issued) {
     const int ks = issued - 1;
-    const bool d = mbar_wait(&done[ks & 1], (uint32_t)((ks >> 1) & 1), kWaitNs);
+    const bool d = mbar_wait(&done[ks % kStages], (uint32_t)((ks / kStages) & 1), kWaitNs);
     ok = __syncthreads_and(ok && d) != 0;
     if (ok) {
       tc_fence_after();
-      drain(tmem, ks & 1, warp, acc);
+      drain(tmem, (ks >> 1) & 1, warp, acc);
       drained = issued;
     }
   }
   if (!ok && tid == 0)
-    for (int ks = issued; ks < loaded; ++ks) mbar_wait(&full[ks & 1], (uint32_t)((ks >> 1) & 1), kWaitNs);
+    for (int ks = issued; ks < loaded; ++ks) mbar_wait(&full[ks % kStages], (uint32_t)((ks / kStages) & 1), kWaitNs);
   if (ok && drained == nsteps) {
     const int row = i0 + 32 * (warp & 3) + (tid & 31);
     double* out = part + (size_t)blockIdx.y * 2 * Pp * Pp + (warp < 4 ? 0 : (size_t)Pp * Pp) + (size_t)row * Pp + j0;
@@ -337,8 +340,8 @@ long long lin_chunk(long long M) {
   return c;
 }
 
-// Tensor map of a [rows][Mp] float array read as M samples per row in 32-sample x 128-row
-// boxes with the 128-byte swizzle (samples past M read as zero).  The encoder comes from the
+// Tensor map of a [rows][Mp] float array read as M samples per row in 16-sample x 128-row
+// boxes with the 64-byte swizzle (samples past M read as zero).  The encoder comes from the
 // driver through the runtime, so the library does not link the driver library itself.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -358,8 +361,9 @@ static cudaError_t encode_tile_map(CUtensorMap* map, const float* base, int rows
   const cuuint64_t strides[1] = {(cuuint64_t)Mp * sizeof(float)};
   const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTile};
   const cuuint32_t estr[2] = {1, 1};
+  static_assert(kTcK * 4 == 64, "the tile rows are 64 bytes (64-byte swizzle)");
   const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }

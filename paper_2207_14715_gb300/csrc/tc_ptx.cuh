@@ -100,6 +100,17 @@ __device__ __forceinline__ uint64_t smem_desc_k128(uint32_t saddr) {
   d |= (uint64_t)2 << 61;                         // 128-byte swizzle
   return d;
 }
+// The same for rows of 64 bytes with the 64-byte swizzle: 8-row groups 512 bytes apart (tile
+// base 512-byte aligned).
+__device__ __forceinline__ uint64_t smem_desc_k64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);         // start address
+  d |= (uint64_t)1 << 16;                         // leading-dimension byte offset (unused here)
+  d |= (uint64_t)(512 >> 4) << 32;                // stride-dimension byte offset: 8 rows
+  d |= (uint64_t)1 << 46;                         // descriptor version
+  d |= (uint64_t)4 << 61;                         // 64-byte swizzle
+  return d;
+}
 // Instruction descriptor: D f32, A and B tf32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
