@@ -140,6 +140,19 @@ def evaluate(spec, R, derivs: bool = False, grad: bool = False, nthreads: int | 
     return out
 
 
+def nuclear_derivs(spec, R, eloc: bool = True, nthreads: int | None = None):
+    """d ln|Psi| / dR_alpha and d E_L / dR_alpha, each (W, Nn, 3), at electron positions R."""
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    W = R.shape[0]
+    s, keep = _pack(spec)
+    dlp = np.zeros((W, spec.Nn, 3))
+    dE = np.zeros((W, spec.Nn, 3)) if eloc else None
+    rc = lib().orc_nuclear_derivs(ctypes.byref(s), W, _dp(R), _dp(dlp), _dp(dE), nthreads or default_threads())
+    if rc:
+        raise RuntimeError("oracle nuclear derivatives failed: %d" % rc)
+    return {"dlogpsi": dlp, "dEL": dE}
+
+
 def lnJ(spec, R):
     R = np.ascontiguousarray(R, dtype=np.float64)
     s, keep = _pack(spec)

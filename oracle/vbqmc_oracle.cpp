@@ -42,7 +42,9 @@
 //     derivative row (fresh LU each time);
 //   * electron gradients/Laplacians of ln J: hyper-dual numbers (exact second derivatives);
 //   * parameter derivatives: forward-mode dual numbers, one tangent per parameter, pushed
-//     through the whole evaluation above.
+//     through the whole evaluation above;
+//   * nucleus-position derivatives of ln|Psi| and E_L (the ingredients of forces): the same,
+//     one tangent per nucleus coordinate (basis centres, Jastrow e-n/e-e-n terms and V move).
 //
 // Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) written from its
 // published definition; uniforms are (x >> 11) * 2^-53 of a 64-bit word.
@@ -468,9 +470,11 @@ static int build_sys(const orc_system* in, Sys& s) {
   return 0;
 }
 
-// Parameter values in scalar type T; 'dir' >= 0 puts a unit tangent on parameter dir.
+// Parameter values and nucleus positions in scalar type T; 'dir' >= 0 puts a unit tangent on
+// parameter dir (dir < P) or on nucleus coordinate dir - P.
 template <class T> struct Params {
   std::vector<T> c, a, b, craw, lam;
+  std::vector<T> nuc;  // [Nn][3] nucleus positions (basis centres, Jastrow e-n and e-e-n, V)
 };
 
 template <class T> static void set_tangent(T&, double) {}
@@ -494,7 +498,11 @@ template <class T> static Params<T> make_params(const Sys& s, int dir) {
     }
   P.lam.resize(s.lam.size());
   for (size_t i = 0; i < s.lam.size(); ++i) P.lam[i] = T(s.lam[i]);
+  P.nuc.resize(3 * (size_t)s.Nn);
+  for (int i = 0; i < 3 * s.Nn; ++i) P.nuc[i] = T(s.nuc_xyz[i]);
   if (dir < 0) return P;
+  // directions past the parameters: nucleus coordinate (dir - P) = 3 alpha + d
+  if (dir >= s.P) { set_tangent(P.nuc[dir - s.P], 1.0); return P; }
   int j = dir;
   if (j < (int)s.cparam.size()) { set_tangent(P.c[s.cparam[j]], 1.0); return P; }
   j -= (int)s.cparam.size();
@@ -521,39 +529,41 @@ template <class T> static Params<T> make_params(const Sys& s, int dir) {
 // Cartesian Gaussian values, gradients and Laplacians at point r (closed form):
 // chi = N P(x) e^{-z r^2};  grad chi = N e (grad P - 2 z x P);
 // lap chi = N e (lap P + P (4 z^2 r^2 - 6 z - 4 z l)).
-static void basis_at(const Sys& s, const double* r, double* chi, double* dchi, double* lchi) {
+// The centres are nuc (type T, so that a tangent on a nucleus position carries through).
+template <class T>
+static void basis_at(const Sys& s, const std::vector<T>& nuc, const double* r, T* chi, T* dchi, T* lchi) {
   for (int sh = 0; sh < s.S; ++sh) {
     int c = s.sh_center[sh], l = s.sh_l[sh];
-    double x[3] = {r[0] - s.nuc_xyz[3 * c], r[1] - s.nuc_xyz[3 * c + 1], r[2] - s.nuc_xyz[3 * c + 2]};
-    double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    T x[3] = {r[0] - nuc[3 * c], r[1] - nuc[3 * c + 1], r[2] - nuc[3 * c + 2]};
+    T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     double z = s.sh_zeta[sh];
-    double e = std::exp(-z * r2);
+    T e = vexp(r2 * (-z));
     for (int q = 0; q < NCOMP[l]; ++q) {
       const int* ex = CART[CART_OFF[l] + q];
       double nrm = s.sh_norm[(size_t)sh * 6 + q];
-      double P = 1.0;
-      for (int d = 0; d < 3; ++d) P *= std::pow(x[d], ex[d]);
+      T P(1.0);
+      for (int d = 0; d < 3; ++d) P = P * ipow(x[d], ex[d]);
       int mu = s.sh_first[sh] + q;
-      chi[mu] = nrm * P * e;
+      chi[mu] = P * e * nrm;
       if (dchi) {
         for (int d = 0; d < 3; ++d) {
-          double dP = 0.0;
+          T dP(0.0);
           if (ex[d] > 0) {
-            dP = ex[d] * std::pow(x[d], ex[d] - 1);
+            dP = ipow(x[d], ex[d] - 1) * (double)ex[d];
             for (int o = 0; o < 3; ++o)
-              if (o != d) dP *= std::pow(x[o], ex[o]);
+              if (o != d) dP = dP * ipow(x[o], ex[o]);
           }
-          dchi[3 * mu + d] = nrm * e * (dP - 2.0 * z * x[d] * P);
+          dchi[3 * mu + d] = e * (dP - x[d] * P * (2.0 * z)) * nrm;
         }
-        double lapP = 0.0;
+        T lapP(0.0);
         for (int d = 0; d < 3; ++d)
           if (ex[d] >= 2) {
-            double t = ex[d] * (ex[d] - 1) * std::pow(x[d], ex[d] - 2);
+            T t = ipow(x[d], ex[d] - 2) * (double)(ex[d] * (ex[d] - 1));
             for (int o = 0; o < 3; ++o)
-              if (o != d) t *= std::pow(x[o], ex[o]);
-            lapP += t;
+              if (o != d) t = t * ipow(x[o], ex[o]);
+            lapP = lapP + t;
           }
-        lchi[mu] = nrm * e * (lapP + P * (4.0 * z * z * r2 - 6.0 * z - 4.0 * z * l));
+        lchi[mu] = e * (lapP + P * (r2 * (4.0 * z * z) - (6.0 * z + 4.0 * z * l))) * nrm;
       }
     }
   }
@@ -586,7 +596,7 @@ template <class T> static T det_lu(int n, std::vector<T> A) {
 
 // Jastrow pieces (Sec. 2.1).  Positions of type S, parameters promoted from T.
 template <class S, class T> static S f_en(const Sys& s, const Params<T>& P, const S* ri, int al) {
-  S dx = ri[0] - s.nuc_xyz[3 * al], dy = ri[1] - s.nuc_xyz[3 * al + 1], dz = ri[2] - s.nuc_xyz[3 * al + 2];
+  S dx = ri[0] - S(P.nuc[3 * al]), dy = ri[1] - S(P.nuc[3 * al + 1]), dz = ri[2] - S(P.nuc[3 * al + 2]);
   S r = vsqrt(dx * dx + dy * dy + dz * dz);
   S R = r / (1.0 + s.kappa * r);
   const T* a = &P.a[(size_t)s.nuc_elem[al] * 6];
@@ -606,7 +616,7 @@ template <class S, class T> static S f_ee(const Sys& s, const Params<T>& P, cons
   return v;
 }
 template <class S, class T> static S f_een(const Sys& s, const Params<T>& P, const S* ri, const S* rj, int al) {
-  const double* A = &s.nuc_xyz[3 * al];
+  const S A[3] = {S(P.nuc[3 * al]), S(P.nuc[3 * al + 1]), S(P.nuc[3 * al + 2])};
   S dij[3] = {ri[0] - rj[0], ri[1] - rj[1], ri[2] - rj[2]};
   S dia[3] = {ri[0] - A[0], ri[1] - A[1], ri[2] - A[2]};
   S dja[3] = {rj[0] - A[0], rj[1] - A[1], rj[2] - A[2]};
@@ -654,23 +664,23 @@ template <class S, class T> static S lnJ_of(const Sys& s, const Params<T>& P, co
   return v;
 }
 
-static double potential(const Sys& s, const double* R) {
-  double V = 0.0;
+// V = V_en + V_ee + V_nn at electron positions R [N][3], nuclei at P.nuc.
+template <class T> static T potential(const Sys& s, const Params<T>& P, const double* R) {
+  T V(0.0);
   for (int i = 0; i < s.N; ++i)
     for (int al = 0; al < s.Nn; ++al) {
-      double d[3] = {R[3 * i] - s.nuc_xyz[3 * al], R[3 * i + 1] - s.nuc_xyz[3 * al + 1], R[3 * i + 2] - s.nuc_xyz[3 * al + 2]};
-      V -= s.nuc_Z[al] / std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      T d[3] = {R[3 * i] - P.nuc[3 * al], R[3 * i + 1] - P.nuc[3 * al + 1], R[3 * i + 2] - P.nuc[3 * al + 2]};
+      V = V - s.nuc_Z[al] / vsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     }
   for (int i = 0; i < s.N; ++i)
     for (int j = i + 1; j < s.N; ++j) {
       double d[3] = {R[3 * i] - R[3 * j], R[3 * i + 1] - R[3 * j + 1], R[3 * i + 2] - R[3 * j + 2]};
-      V += 1.0 / std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      V = V + 1.0 / std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     }
   for (int a = 0; a < s.Nn; ++a)
     for (int b = a + 1; b < s.Nn; ++b) {
-      double d[3] = {s.nuc_xyz[3 * a] - s.nuc_xyz[3 * b], s.nuc_xyz[3 * a + 1] - s.nuc_xyz[3 * b + 1],
-                     s.nuc_xyz[3 * a + 2] - s.nuc_xyz[3 * b + 2]};
-      V += s.nuc_Z[a] * s.nuc_Z[b] / std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      T d[3] = {P.nuc[3 * a] - P.nuc[3 * b], P.nuc[3 * a + 1] - P.nuc[3 * b + 1], P.nuc[3 * a + 2] - P.nuc[3 * b + 2]};
+      V = V + s.nuc_Z[a] * s.nuc_Z[b] / vsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     }
   return V;
 }
@@ -685,10 +695,10 @@ template <class T> struct Eval {
 // Evaluate ln|Psi|, sign and, if full, E_L and grad ln|Psi| at configuration R [N][3].
 template <class T> static Eval<T> evaluate(const Sys& s, const Params<T>& P, const double* R, bool full) {
   const int N = s.N, M = s.M, No = s.Norb;
-  std::vector<double> chi(M), dchi(3 * M), lchi(M);
+  std::vector<T> chi(M), dchi(3 * M), lchi(M);
   std::vector<T> phi((size_t)N * No), dphi(full ? (size_t)N * No * 3 : 0), lphi(full ? (size_t)N * No : 0);
   for (int e = 0; e < N; ++e) {
-    basis_at(s, R + 3 * e, chi.data(), full ? dchi.data() : nullptr, full ? lchi.data() : nullptr);
+    basis_at(s, P.nuc, R + 3 * e, chi.data(), full ? dchi.data() : nullptr, full ? lchi.data() : nullptr);
     for (int k = 0; k < No; ++k) {
       T v(0.0), g0(0.0), g1(0.0), g2(0.0), lp(0.0);
       for (int mu = 0; mu < M; ++mu) {
@@ -785,7 +795,7 @@ template <class T> static Eval<T> evaluate(const Sys& s, const Params<T>& P, con
     }
     kin = kin + lPhi[i] / Phi + 2.0 * dot + LJ[i] + gg;
   }
-  out.eloc = -0.5 * kin + potential(s, R);
+  out.eloc = -0.5 * kin + potential(s, P, R);
   return out;
 }
 
@@ -867,7 +877,7 @@ int orc_expand(const orc_system* in, int maxterms, int* str, double* d, int* up,
 int orc_basis_eval(const orc_system* in, const double* r, double* chi, double* dchi, double* lchi) {
   Sys s;
   if (build_sys(in, s)) return -1;
-  basis_at(s, r, chi, dchi, lchi);
+  basis_at(s, s.nuc_xyz, r, chi, dchi, lchi);
   return s.M;
 }
 
@@ -923,6 +933,28 @@ int orc_eval(const orc_system* in, int W, const double* R, double* logpsi, doubl
         if (O) O[(size_t)w * P + j] = ed.logpsi.d;
         if (dEL) dEL[(size_t)w * P + j] = ed.eloc.d;
       }
+    }
+  });
+  return 0;
+}
+
+// Nucleus-position derivatives at fixed electron positions R [W][N][3]: dlogpsi [W][Nn][3] =
+// d ln|Psi| / dR_alpha and dEL [W][Nn][3] = d E_L / dR_alpha (either may be NULL).  The
+// nucleus positions enter the basis centres, the e-n and e-e-n Jastrow terms and V; each of
+// the 3 Nn coordinates gets one forward-mode tangent through the whole evaluation, as the
+// parameters do for E_L,j (Sec. 2.3.1, the definition after Eq. H0j).
+int orc_nuclear_derivs(const orc_system* in, int W, const double* R, double* dlogpsi, double* dEL, int nthreads) {
+  Sys s;
+  int rc = build_sys(in, s);
+  if (rc) return rc;
+  const int N = s.N, K = 3 * s.Nn;
+  parallel_for(W, nthreads, [&](int w) {
+    const double* Rw = R + (size_t)w * 3 * N;
+    for (int q = 0; q < K; ++q) {
+      Params<Dual<double>> Pq = make_params<Dual<double>>(s, s.P + q);
+      Eval<Dual<double>> ed = evaluate(s, Pq, Rw, dEL != nullptr);
+      if (dlogpsi) dlogpsi[(size_t)w * K + q] = ed.logpsi.d;
+      if (dEL) dEL[(size_t)w * K + q] = ed.eloc.d;
     }
   });
   return 0;

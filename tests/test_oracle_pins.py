@@ -472,6 +472,108 @@ def test_structure_coefficient_sum_rule(orc):
     np.testing.assert_allclose(O @ spec.c_vb, 1.0, rtol=1e-13)
 
 
+# ----------------------------------------------------------------------------- nucleus-position derivatives
+def _moved(spec, q, h):
+    """Copy of spec with nucleus coordinate q = 3 alpha + d moved by h (its shells move with it)."""
+    import copy
+    s = copy.deepcopy(spec)
+    s.nuc_xyz = spec.nuc_xyz.copy()
+    s.nuc_xyz[q // 3, q % 3] += h
+    return s
+
+
+def _fd_nuclei(orc, spec, R, qs, h=1e-3):
+    outL, outE = [], []
+    for q in qs:
+        def f(hh):
+            o = orc.evaluate(_moved(spec, q, hh), R)
+            return o["logpsi"], o["eloc"]
+        a1, b1 = f(h); a2, b2 = f(-h); a3, b3 = f(h / 2); a4, b4 = f(-h / 2)
+        outL.append((4 * (a3 - a4) / h - (a1 - a2) / (2 * h)) / 3)
+        outE.append((4 * (b3 - b4) / h - (b1 - b2) / (2 * h)) / 3)
+    return np.array(outL).T, np.array(outE).T
+
+
+def test_nuclear_derivatives_finite_difference(orc):
+    """d ln|Psi|/dR_alpha and dE_L/dR_alpha against Richardson central differences of the
+    oracle moved to displaced nuclei (basis centres, e-n and e-e-n Jastrow and V all move)."""
+    spec = S.small_open_shell()
+    R = S.initial_walkers(spec, 3, 8)
+    out = orc.nuclear_derivs(spec, R)
+    L_fd, E_fd = _fd_nuclei(orc, spec, R, range(3 * spec.Nn))
+    W = R.shape[0]
+    np.testing.assert_allclose(out["dlogpsi"].reshape(W, -1), L_fd, rtol=1e-7, atol=1e-8)
+    scale = 1.0 + np.abs(E_fd).max()
+    np.testing.assert_allclose(out["dEL"].reshape(W, -1), E_fd, rtol=1e-6, atol=1e-7 * scale)
+
+
+def test_nuclear_derivatives_finite_difference_ethylene_subset(orc):
+    spec = S.ethylene_vb()
+    R = S.initial_walkers(spec, 1, 3)
+    out = orc.nuclear_derivs(spec, R)
+    qs = [0, 4, 8, 10, 17]
+    L_fd, E_fd = _fd_nuclei(orc, spec, R, qs)
+    np.testing.assert_allclose(out["dlogpsi"].reshape(1, -1)[:, qs], L_fd, rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(out["dEL"].reshape(1, -1)[:, qs], E_fd, rtol=1e-5,
+                               atol=1e-6 * (1 + np.abs(E_fd).max()))
+
+
+@pytest.mark.parametrize("Z", [1, 3, 6])
+def test_nuclear_derivatives_hydrogen_like(orc, Z):
+    """Psi = exp(-Z |r - R_a|): d ln Psi/dR_a = Z (r - R_a)/|r - R_a| and E_L = -Z^2/2 wherever
+    the nucleus sits, so dE_L/dR_a = 0."""
+    spec = S.one_electron(Z, 0.0, a1=-Z, a2=-0.8)
+    spec.nuc_xyz = np.array([[0.3, -0.2, 0.5]])
+    R = spec.nuc_xyz[None] + np.random.default_rng(Z).normal(scale=2.0 / Z, size=(12, 1, 3))
+    out = orc.nuclear_derivs(spec, R)
+    d = R[:, 0] - spec.nuc_xyz[0]
+    np.testing.assert_allclose(out["dlogpsi"][:, 0], Z * d / np.linalg.norm(d, axis=1)[:, None], rtol=1e-12)
+    assert np.abs(out["dEL"]).max() <= 1e-11 * Z * Z
+
+
+def test_nuclear_derivatives_coulomb(orc):
+    """A wave function that does not depend on the nuclei (constant orbital, no Jastrow):
+    d ln Psi/dR = 0 and dE_L/dR_a = dV/dR_a, Coulomb's law for the electrons and the other
+    nuclei: -Z_a sum_i (r_i - R_a)/|r_i - R_a|^3 - Z_a sum_b Z_b (R_a - R_b)/|R_a - R_b|^3."""
+    spec = S.two_electron_product(2.0, 0.0)
+    spec.nuc_xyz = np.array([[0.0, 0.0, 0.0], [1.3, -0.4, 0.2], [-0.7, 0.9, 1.1]])
+    spec.nuc_Z = np.array([2.0, 1.0, 3.0])
+    spec.nuc_elem = np.zeros(3, np.int32)
+    R = np.random.default_rng(4).normal(scale=1.5, size=(6, 2, 3))
+    out = orc.nuclear_derivs(spec, R)
+    assert np.abs(out["dlogpsi"]).max() == 0.0
+    X, Zs = spec.nuc_xyz, spec.nuc_Z
+    want = np.zeros((6, 3, 3))
+    for a in range(3):
+        for i in range(2):
+            d = R[:, i] - X[a]
+            want[:, a] -= Zs[a] * d / (np.linalg.norm(d, axis=1) ** 3)[:, None]
+        for b in range(3):
+            if b != a:
+                d = X[a] - X[b]
+                want[:, a] -= Zs[a] * Zs[b] * d / np.linalg.norm(d) ** 3
+    np.testing.assert_allclose(out["dEL"], want, rtol=1e-12, atol=1e-12)
+
+
+def test_nuclear_derivatives_translation_sum(orc):
+    """Moving every nucleus and every electron together changes nothing, so
+    sum_a d/dR_a = -sum_i d/dr_i: against the electron gradient of ln|Psi|, and against a
+    Richardson difference of E_L under a common shift of the electrons."""
+    spec = S.small_open_shell()
+    R = S.initial_walkers(spec, 3, 5)
+    out = orc.nuclear_derivs(spec, R)
+    g = orc.evaluate(spec, R, grad=True)["grad"]
+    np.testing.assert_allclose(out["dlogpsi"].sum(1), -g.sum(1), rtol=1e-10, atol=1e-10)
+    h = 1e-3
+    for d in range(3):
+        def el(hh):
+            Rs = R.copy()
+            Rs[:, :, d] += hh
+            return orc.evaluate(spec, Rs)["eloc"]
+        fd = (4 * (el(h / 2) - el(-h / 2)) / h - (el(h) - el(-h)) / (2 * h)) / 3
+        np.testing.assert_allclose(out["dEL"][:, :, d].sum(1), -fd, rtol=1e-6, atol=1e-6 * (1 + np.abs(fd).max()))
+
+
 # ----------------------------------------------------------------------------- linear method
 def test_linear_method_strong_zero_variance(orc):
     """Psi = J (Phi_1 + c2 Phi_2) with J = exp(-Z r): the exact state exp(-Z r) = Psi - c2 Psi_c2 is
