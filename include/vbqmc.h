@@ -143,6 +143,24 @@ int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const d
                        double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out,
                        void* stream);
 
+/* Derivatives with respect to the nucleus positions R_a at fixed electron positions: the
+ * derivative of E_L defined after Eq. H0j (Sec. 2.3.1), E_L,j = dE_L/dp_j, taken with p_j a
+ * nucleus coordinate, and the matching O_j = d ln|Psi|/dp_j.  Moving a nucleus moves the
+ * basis functions centred on it (Sec. 2.1, orbital expansion), its e-n and e-e-n Jastrow
+ * terms and the potential.  These give the usual force estimate
+ *   F_a = -<dE_L/dR_a> - 2 <(E_L - <E_L>) d ln|Psi|/dR_a>.
+ * The walkers are evaluated as by vbqmc_eval_walkers (no parameter derivatives), then one
+ * more kernel forms the derivatives.
+ *   R           [W][N][3] device, in
+ *   logpsi, sign, eloc  [W] device, out (as vbqmc_eval_walkers)
+ *   dlogpsi_dR  [W][Nn][3] device double, out: d ln|Psi| / dR_a
+ *   dEL_dR      [W][Nn][3] device double or NULL, out: dE_L / dR_a
+ * precision: VBQMC_FP64, or VBQMC_MIXED (bulk arithmetic in float as in the evaluation, the
+ * sums over determinants and the potential term in double).  W may be 0.  Errors:
+ * VBQMC_ERR_CAPACITY if the per-walker tables do not fit in shared memory. */
+int vbqmc_eval_nuclear_derivs(vbqmc_ctx* ctx, int sys_id, int precision, int W, const double* R, double* logpsi,
+                              double* sign, double* eloc, double* dlogpsi_dR, double* dEL_dR, void* stream);
+
 /* VMC (Sec. 2.3.1): nsweeps sweeps of single-electron Metropolis moves over every walker,
  * electron i moved to r_i + step*(2u - 1) per coordinate and accepted when
  * u_acc < |Psi(R')/Psi(R)|^2.  Determinant ratios and Sherman-Morrison updates of the

@@ -84,6 +84,7 @@ void vbqmc_destroy(vbqmc_ctx* ctx) {
   if (ctx->work) cudaFree(ctx->work);
   if (ctx->dmc_work) cudaFree(ctx->dmc_work);
   if (ctx->eval_work) cudaFree(ctx->eval_work);
+  if (ctx->force_work) cudaFree(ctx->force_work);
   for (auto& ev : ctx->tev)
     if (ev) cudaEventDestroy(ev);
   delete ctx;
@@ -165,7 +166,7 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
                o_evco = bb.add(h.ev_chunk_off), o_dc = bb.add(h.det_chunk), o_dco = bb.add(h.det_chunk_off),
                o_zds = bb.add(zeta_ds), o_nds = bb.add(norm_ds), o_cds = bb.add(coef_ds), o_nucds = bb.add(nuc_ds),
                o_zf = bb.add(zeta_f), o_nf = bb.add(norm_f), o_jaf = bb.add(jas_af), o_jbf = bb.add(jas_bf),
-               o_ebf = bb.add(een_Bf), o_nzf = bb.add(nuc_zf);
+               o_ebf = bb.add(een_Bf), o_nzf = bb.add(nuc_zf), o_nsh = bb.add(h.nuc_sh);
   cudaError_t e = cudaMalloc(&ls.blob, bb.bytes.size());
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(system tables)");
   ls.blob_bytes = bb.bytes.size();
@@ -198,6 +199,8 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.sh_center = (const int*)(B + o_sh_center);
   d.sh_l = (const int*)(B + o_sh_l);
   d.sh_first = (const int*)(B + o_sh_first);
+  d.nuc_sh = (const int*)(B + o_nsh);
+  d.max_nuc_mu = h.max_nuc_mu;
   d.sh_zeta = (const double*)(B + o_sh_zeta);
   d.sh_norm = (const double*)(B + o_sh_norm);
   d.orb_lo = (const int*)(B + o_orb_lo);
@@ -256,6 +259,7 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
     const int tb = p == VBQMC_MIXED ? 4 : 8;
     ls.lay_rc_eval[p] = vbq::make_eval_layout(d, tb, ctx->max_smem, ls.lay_eval[p]);
     ls.lay_rc_sweep[p] = vbq::make_sweep_layout(d, tb, ctx->max_smem, ls.lay_sweep[p]);
+    ls.lay_rc_force[p] = vbq::make_force_layout(d, tb, ctx->max_smem, ls.lay_force[p]);
   }
   ls.loaded = true;
   free_system(ctx->sys[sys_id]);
@@ -340,6 +344,41 @@ int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const d
                                    state_out, ctx->eval_work, (cudaStream_t)stream, &nl, timing_events(ctx));
   ctx->last_launches = nl;
   if (e != cudaSuccess) return cuda_fail(e, "evaluation kernel launch");
+  return VBQMC_OK;
+}
+
+int vbqmc_eval_nuclear_derivs(vbqmc_ctx* ctx, int sys_id, int precision, int W, const double* R, double* logpsi,
+                              double* sign, double* eloc, double* dlogpsi_dR, double* dEL_dR, void* stream) {
+  int rc = check_call(ctx, sys_id, precision, W);
+  if (rc) return rc;
+  ctx->last_launches = 0;
+  if (W == 0) return VBQMC_OK;
+  if (!R || !logpsi || !sign || !eloc || !dlogpsi_dR) return fail(VBQMC_ERR_ARG, "null required pointer");
+  LoadedSystem& s = ctx->sys[sys_id];
+  if (s.lay_rc_eval[precision]) return fail(s.lay_rc_eval[precision], "per-walker state exceeds shared memory");
+  if (s.lay_rc_force[precision])
+    return fail(s.lay_rc_force[precision], "nucleus-derivative tables exceed shared memory");
+  DeviceGuard g(ctx->device);
+  const cudaStream_t st = (cudaStream_t)stream;
+  rc = ensure_eval_ws(ctx, s, precision, W, st);
+  if (rc) return rc;
+  const size_t need = vbq::force_workspace_bytes(s.dev, W);
+  if (need > ctx->force_bytes) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (ctx->force_work) cudaFree(ctx->force_work);
+    ctx->force_work = nullptr;
+    ctx->force_bytes = 0;
+    e = cudaMalloc(&ctx->force_work, need);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(nucleus-derivative workspace)");
+    ctx->force_bytes = need;
+  }
+  int nl = 0;
+  cudaError_t e = vbq::launch_nuclear_derivs(precision, s.dev, s.lay_eval[precision], s.lay_force[precision], W, R,
+                                             logpsi, sign, eloc, dlogpsi_dR, dEL_dR, ctx->eval_work,
+                                             ctx->force_work, st, &nl);
+  ctx->last_launches = nl;
+  if (e != cudaSuccess) return cuda_fail(e, "nucleus-derivative kernel launch");
   return VBQMC_OK;
 }
 

@@ -29,8 +29,10 @@ struct LoadedSystem {
   size_t blob_bytes = 0;
   vbq::EvalLayout lay_eval[2];
   vbq::SweepLayout lay_sweep[2];
+  vbq::ForceLayout lay_force[2];
   int lay_rc_eval[2] = {0, 0};
   int lay_rc_sweep[2] = {0, 0};
+  int lay_rc_force[2] = {0, 0};
 };
 
 }  // namespace vbq
@@ -46,6 +48,8 @@ struct vbqmc_ctx {
   size_t dmc_bytes = 0;
   void* eval_work = nullptr;  // grow-only device workspace of the evaluation kernels
   size_t eval_bytes = 0;
+  void* force_work = nullptr;  // grow-only device workspace of the nucleus derivatives
+  size_t force_bytes = 0;
   int timing = 0;                               // record events around the evaluation kernels
   cudaEvent_t tev[vbq::kEvalKernels + 1] = {};  // created on first use
   bool tev_valid = false;                       // events of the last timed evaluation are recorded

@@ -74,7 +74,8 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
                                          const double* __restrict__ OD, double* __restrict__ logpsi,
                                          double* __restrict__ sgn_out, double* __restrict__ eloc,
                                          double* __restrict__ vg_ws, double* __restrict__ grad, Tb* __restrict__ Og,
-                                         Tb* __restrict__ dELg, double* __restrict__ state_out) {
+                                         Tb* __restrict__ dELg, double* __restrict__ state_out,
+                                         double* __restrict__ aux) {
   const int lane = threadIdx.x & 31;
   double* vg = reinterpret_cast<double*>(base + L.vg);
   Tb* G = reinterpret_cast<Tb*>(base + L.G);
@@ -153,7 +154,12 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
     }
     Wdet[ud] = Wv;
     Tdet[ud] = Tv;
+    if (aux) {
+      aux[(size_t)w * (2 * Utot + 1) + ud] = Wv;
+      aux[(size_t)w * (2 * Utot + 1) + Utot + ud] = Tv;
+    }
   }
+  if (aux && lane == 0) aux[(size_t)w * (2 * Utot + 1) + 2 * Utot] = kphi;
   __syncwarp();
   // grad_i ln|Psi| = grad_i lnJ + sum_u W_u sum_o Binv_u[o][i] grad phi_o(r_i), in the bulk type
   // (it feeds the Jastrow-parameter derivatives and the drift, not E_L)
@@ -272,13 +278,13 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
                const double* __restrict__ JS, const Tb* __restrict__ OB, const double* __restrict__ OD,
                double* __restrict__ logpsi, double* __restrict__ sgn_out, double* __restrict__ eloc,
                double* __restrict__ vg_ws, double* __restrict__ grad, Tb* __restrict__ Og, Tb* __restrict__ dELg,
-               double* __restrict__ state_out) {
+               double* __restrict__ state_out, double* __restrict__ aux) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int wl = threadIdx.x >> 5;
   const int w = blockIdx.x * L.wpb + wl;
   if (w >= W) return;
   det_body<Tb>(s, L, w, smem + wl * L.warp_bytes, JG, JL, JS, OB, OD, logpsi, sgn_out, eloc, vg_ws, grad, Og, dELg,
-               state_out);
+               state_out, aux);
 }
 
 template <class Tb>
@@ -296,7 +302,8 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
     const bool d = call->derivs && b.O && b.dev.P > 0;
     det_body<Tb>(b.dev, b.lay.det, item.first + wl, smem + wl * b.lay.det.warp_bytes, static_cast<const Tb*>(b.JG),
                  static_cast<const Tb*>(b.JL), b.JS, static_cast<const Tb*>(b.OB), b.OD, b.logpsi, b.sign, b.eloc, b.VG,
-                 nullptr, d ? static_cast<Tb*>(b.O) : nullptr, d ? static_cast<Tb*>(b.dEL) : nullptr, b.state);
+                 nullptr, d ? static_cast<Tb*>(b.O) : nullptr, d ? static_cast<Tb*>(b.dEL) : nullptr, b.state,
+                 nullptr);
   }
 }
 
@@ -344,12 +351,9 @@ int make_det_layout(const SysDev& s, int tb, int max_smem, DetLayout& L) {
 
 inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
-struct EvalWs {
-  void *JG, *JL, *OB;
-  double *JS, *OD, *VG;
-};
+}  // namespace
 
-EvalWs carve(const SysDev& s, int tb, int W, void* ws) {
+EvalWs carve_eval_ws(const SysDev& s, int tb, int W, void* ws) {
   const size_t N = s.N, Wz = W;
   unsigned char* p = static_cast<unsigned char*>(ws);
   EvalWs r;
@@ -367,11 +371,13 @@ EvalWs carve(const SysDev& s, int tb, int W, void* ws) {
   return r;
 }
 
+namespace {
+
 template <class Tb>
 cudaError_t launch_eval_t(const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi, double* sign,
                           double* eloc, double* grad, Tb* O, Tb* dEL, double* state_out, void* ws, cudaStream_t st,
-                          int* nlaunch, cudaEvent_t* ev) {
-  const EvalWs b = carve(s, (int)sizeof(Tb), W, ws);
+                          int* nlaunch, cudaEvent_t* ev, double* aux) {
+  const EvalWs b = carve_eval_ws(s, (int)sizeof(Tb), W, ws);
   *nlaunch = 0;
   auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], st) : cudaSuccess; };
   cudaError_t e = mark(0);
@@ -390,7 +396,7 @@ cudaError_t launch_eval_t(const SysDev& s, const EvalLayout& L, int W, const dou
   if (e != cudaSuccess) return e;
   det_kernel<Tb><<<(W + D.wpb - 1) / D.wpb, 32 * D.wpb, smem, st>>>(
       s, D, W, static_cast<const Tb*>(b.JG), static_cast<const Tb*>(b.JL), b.JS, static_cast<const Tb*>(b.OB), b.OD,
-      logpsi, sign, eloc, b.VG, grad, O, dEL, state_out);
+      logpsi, sign, eloc, b.VG, grad, O, dEL, state_out, aux);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ++*nlaunch;
@@ -435,12 +441,12 @@ size_t eval_workspace_bytes(const SysDev& s, int tb, int W) {
 
 cudaError_t launch_eval(int precision, const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
                         double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out, void* ws,
-                        cudaStream_t st, int* nlaunch, cudaEvent_t* ev) {
+                        cudaStream_t st, int* nlaunch, cudaEvent_t* ev, double* aux) {
   if (precision == VBQMC_MIXED)
     return launch_eval_t<float>(s, L, W, R, logpsi, sign, eloc, grad, static_cast<float*>(O),
-                                static_cast<float*>(dEL), state_out, ws, st, nlaunch, ev);
+                                static_cast<float*>(dEL), state_out, ws, st, nlaunch, ev, aux);
   return launch_eval_t<double>(s, L, W, R, logpsi, sign, eloc, grad, static_cast<double*>(O),
-                               static_cast<double*>(dEL), state_out, ws, st, nlaunch, ev);
+                               static_cast<double*>(dEL), state_out, ws, st, nlaunch, ev, aux);
 }
 
 }  // namespace vbq

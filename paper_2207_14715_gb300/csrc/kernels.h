@@ -45,20 +45,51 @@ struct SweepLayout {
   int G0, G1;
 };
 
+// Nucleus-derivative kernel (eval_forces.cu), warp per walker: positions, weights, grad ln J,
+// orbital gradients, inverses B_u and Z_u = B_u L_u B_u, the orbital tangents of one nucleus
+// D [N][n_ev_det][12], basis derivatives of Ec electrons at a time bd [Ec][max_mu][12], and
+// the Jastrow tangents dG [N][3][3], dLJ [N][3].
+struct ForceLayout {
+  int wpb = 0, warp_bytes = 0;
+  int R, wt, G, Gphi, B, Z, D, bd, dG, dLJ;
+  int Ec, max_mu;
+};
+
 int make_eval_layout(const SysDev& s, int bulk_bytes, int max_smem, EvalLayout& L);
+int make_force_layout(const SysDev& s, int bulk_bytes, int max_smem, ForceLayout& L);
 int make_sweep_layout(const SysDev& s, int bulk_bytes, int max_smem, SweepLayout& L);
 
 // Device workspace of one evaluation of W walkers (bytes, 256-aligned pieces).
 size_t eval_workspace_bytes(const SysDev& s, int bulk_bytes, int W);
 
+// Pieces of the evaluation workspace (carve_eval_ws): JG [W][N][3] and JL [W][N] grad and
+// Laplacian of ln J (bulk type), JS [W][2] ln J and V, OB [W][N][5][n_ev] orbital values,
+// gradients and Laplacians (bulk type), OD [W][N][n_ev_det] double orbital values, VG
+// [W][N][3] grad ln|Psi|.
+struct EvalWs {
+  void *JG, *JL, *OB;
+  double *JS, *OD, *VG;
+};
+EvalWs carve_eval_ws(const SysDev& s, int bulk_bytes, int W, void* ws);
+
 // Evaluation of W walkers; ws: eval_workspace_bytes(s, bulk, W) bytes of device memory.
 // *nlaunch receives the number of kernels launched.  If ev is not null, ev[0..4] are recorded
 // on st before the Jastrow kernel and after the Jastrow, orbital, determinant and
 // Jastrow-derivative kernels (the last right after the determinant kernel when it is skipped).
+// If aux is not null, the determinant kernel writes per walker [2 U + 1] doubles: the
+// marginal weights W_u and T_u of every unique determinant (both spins, U = U_up + U_dn)
+// and K[Phi]/Phi (see eval_det.cu), which the nucleus-derivative kernel reads.
 constexpr int kEvalKernels = 4;
 cudaError_t launch_eval(int precision, const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
                         double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out, void* ws,
-                        cudaStream_t st, int* nlaunch, cudaEvent_t* ev = nullptr);
+                        cudaStream_t st, int* nlaunch, cudaEvent_t* ev = nullptr, double* aux = nullptr);
+// Evaluation followed by the nucleus-derivative kernel: logpsi, sign, eloc as launch_eval,
+// dlp [W][Nn][3] = d ln|Psi|/dR_a, dEL [W][Nn][3] = dE_L/dR_a (may be null).  ws: evaluation
+// workspace; fws: force_workspace_bytes(s, W) bytes (walker state and determinant weights).
+size_t force_workspace_bytes(const SysDev& s, int W);
+cudaError_t launch_nuclear_derivs(int precision, const SysDev& s, const EvalLayout& LE, const ForceLayout& LF, int W,
+                                  const double* R, double* logpsi, double* sign, double* eloc, double* dlp,
+                                  double* dEL, void* ws, void* fws, cudaStream_t st, int* nlaunch);
 cudaError_t launch_sweep(int precision, const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps,
                          int refresh, const double* state_in, double step, uint64_t seed, uint32_t step0, uint32_t tag,
                          uint32_t woff, int* nacc, cudaStream_t st);

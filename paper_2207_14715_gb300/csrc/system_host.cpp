@@ -252,6 +252,22 @@ int build_system(const vbqmc_system_desc* d, SysHost& s, std::string& err) {
     return VBQMC_ERR_CAPACITY;
   }
   s.M = M;
+  // shells and basis functions of each nucleus: one contiguous run per nucleus
+  s.nuc_sh.assign((size_t)4 * s.Nn, 0);
+  s.max_nuc_mu = 0;
+  for (int i = 0; i < s.S;) {
+    const int a = s.sh_center[i];
+    VBQ_REQUIRE(s.nuc_sh[4 * a + 1] == 0, "shells of nucleus " << a << " are not contiguous");
+    int j = i;
+    while (j < s.S && s.sh_center[j] == a) ++j;
+    const int mu1 = j < s.S ? s.sh_first[j] : M;
+    s.nuc_sh[4 * a] = i;
+    s.nuc_sh[4 * a + 1] = j;
+    s.nuc_sh[4 * a + 2] = s.sh_first[i];
+    s.nuc_sh[4 * a + 3] = mu1;
+    s.max_nuc_mu = std::max(s.max_nuc_mu, mu1 - s.sh_first[i]);
+    i = j;
+  }
   // orbital coefficient ranges
   s.orb_lo.resize(s.Norb);
   s.orb_hi.resize(s.Norb);

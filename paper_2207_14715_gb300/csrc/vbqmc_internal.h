@@ -29,6 +29,8 @@ struct SysHost {
   std::vector<int> nuc_elem;
   std::vector<int> sh_center, sh_l, sh_first;
   std::vector<double> sh_zeta, sh_norm;  // norm [S][6]
+  std::vector<int> nuc_sh;             // [Nn][4]: first shell, end shell, first and end basis function
+  int max_nuc_mu = 0;                  // most basis functions on one nucleus
   // orbitals: nonzero range [lo, hi) per orbital, coefficients packed
   std::vector<int> orb_lo, orb_hi, orb_off;
   std::vector<double> orb_coef;
@@ -87,6 +89,8 @@ struct SysDev {
   const int* sh_center;
   const int* sh_l;
   const int* sh_first;
+  const int* nuc_sh;                   // [Nn][4], see SysHost
+  int max_nuc_mu;
   const double* sh_zeta;
   const double* sh_norm;
   const int* orb_lo;

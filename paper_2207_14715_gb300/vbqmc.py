@@ -53,7 +53,8 @@ EXPORTED = ["vbqmc_create", "vbqmc_destroy", "vbqmc_last_error", "vbqmc_set_syst
             "vbqmc_walker_state_size", "vbqmc_eval_walkers", "vbqmc_vmc_steps", "vbqmc_accumulate_lin_matrices",
             "vbqmc_launch_info", "vbqmc_last_launch_count", "vbqmc_accumulate_lin_matrices_noalloc",
             "vbqmc_dmc_steps", "vbqmc_set_kernel_timing", "vbqmc_kernel_times", "vbqmc_batch_create",
-            "vbqmc_batch_destroy", "vbqmc_batch_vmc_steps", "vbqmc_batch_tune", "vbqmc_batch_info"]
+            "vbqmc_batch_destroy", "vbqmc_batch_vmc_steps", "vbqmc_batch_tune", "vbqmc_batch_info",
+            "vbqmc_eval_nuclear_derivs"]
 
 _LIB = None
 
@@ -74,6 +75,8 @@ def lib():
         L.vbqmc_walker_state_size.argtypes = [vp, ctypes.c_int, _c_int_p]
         L.vbqmc_eval_walkers.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp,
                                          vp]
+        L.vbqmc_eval_nuclear_derivs.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp,
+                                                vp]
         L.vbqmc_vmc_steps.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
                                       vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
@@ -236,6 +239,13 @@ class Context:
         _check(lib().vbqmc_eval_walkers(self.h, int(sys_id), int(precision), int(W), _ptr(R), _ptr(logpsi),
                                         _ptr(sign), _ptr(eloc), _ptr(grad), _ptr(O), _ptr(dEL), _ptr(state_out),
                                         _stream(stream)))
+
+    def eval_nuclear_derivs(self, sys_id, precision, R, logpsi, sign, eloc, dlogpsi_dR, dEL_dR=None, stream=None):
+        """Evaluation plus d ln|Psi|/dR_a and dE_L/dR_a ([W, Nn, 3] float64 CUDA tensors)."""
+        W = R.shape[0]
+        _check(lib().vbqmc_eval_nuclear_derivs(self.h, int(sys_id), int(precision), int(W), _ptr(R), _ptr(logpsi),
+                                               _ptr(sign), _ptr(eloc), _ptr(dlogpsi_dR), _ptr(dEL_dR),
+                                               _stream(stream)))
 
     def vmc_steps(self, sys_id, precision, R, nsweeps, step, seed, step0=0, system_tag=0, walker_offset=0,
                   refresh=1, state=None, state_valid=False, nacc=None, logpsi=None, sign=None, eloc=None, O=None,

@@ -101,8 +101,8 @@ def test_invalid_inputs_are_rejected(vb):
 
 def test_binding_exposes_the_entry_points(vb):
     """The Python binding has one method per C entry point (argument marshalling only)."""
-    for name in ("set_system", "eval_walkers", "vmc_steps", "dmc_steps", "accumulate_lin_matrices", "walker_state_size",
-                 "launch_info", "last_launch_count", "close"):
+    for name in ("set_system", "eval_walkers", "eval_nuclear_derivs", "vmc_steps", "dmc_steps",
+                 "accumulate_lin_matrices", "walker_state_size", "launch_info", "last_launch_count", "close"):
         assert callable(getattr(vb.Context, name)), name
     for name in ("create", "inspect_system", "lin_solve", "deriv_dtype", "accumulate_lin_matrices_noalloc"):
         assert callable(getattr(vb, name)), name
