@@ -335,6 +335,8 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
     t_e2e = allmax(time.perf_counter() - t0, ws)
     barrier(ws)
+    mhz = (results["mixed"]["clocks"] or {}).get("sm_mhz") or 2070.0
+    forces = force_timing(ctx, vbqmc, spec, info, R, args.force_steps, mhz) if args.force_steps > 0 else None
     dmc = dmc_timing(ctx, vbqmc, R, el, args.dmc_steps) if args.dmc_steps > 0 else None
     batched = batched_timing(vbqmc, dev, args.steps) if args.batch_steps > 0 else None
     lin = lin_method_timing(ctx, vbqmc, dev, args.steps, args.lin_samples) if not args.no_lin else None
@@ -383,6 +385,7 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": ws * W * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
         "linear_method": lin,
+        "nuclear_derivs": forces,
         "dmc": dmc,
         "batched": batched,
         "gpu_launches": m["launches_per_step"] * m["steps"],
@@ -390,6 +393,64 @@ def run_ours(args, ws, rank, local):
                    "reasons": clocks.get("reasons", [])},
     }
     print(json.dumps(line), flush=True)
+
+
+def force_work(spec, info):
+    """Algorithmic flops per walker of the nucleus-derivative kernel (documented in the design
+    notes): e-e-n partial derivatives to third order and their assembly per ordered triple
+    (i, j, a), e-n terms per (i, a), Gaussian derivatives to third order per (electron, basis
+    function), the contraction of 12 derivative values per nonzero coefficient of the
+    determinant orbitals, Z_u = B L B once and x_u, y_u per (nucleus, direction)."""
+    import numpy as np
+    N, Nn, n = spec.N, spec.Nn, spec.n_up
+    U = info["U_up"] + info["U_dn"]
+    det_orbs = sorted(set(int(x) for x in spec.inact) | set(int(x) for x in spec.pairs.ravel()) |
+                      set(int(x) for x in spec.unp))
+    nnz_det = sum(int(np.count_nonzero(spec.orb_coef[k])) for k in det_orbs)
+    triples = N * (N - 1) * Nn if spec.een_on else 0
+    jas = triples * (23 * 6 * 2 * 2 + 12 * 5 * 2 + 3 * 40) + N * Nn * 3 * 40
+    basis = N * spec.M * (12 * 3 + 12) + N * len(spec.sh_l) * 3 * 3 * 4 * 4
+    contr = N * nnz_det * 12 * 2
+    det = U * 2 * 2 * n ** 3 + Nn * U * n * n * 3 * 3 * 2
+    return jas + basis + contr + det
+
+
+def force_timing(ctx, vbqmc, spec, info, R, steps, sm_mhz=2070.0):
+    """d ln|Psi|/dR_a and dE_L/dR_a of every walker (one evaluation + the nucleus-derivative
+    kernel) in both forms: CUDA events around the call and around a plain evaluation at the
+    same positions; the difference is the derivative kernel."""
+    import torch
+    W = R.shape[0]
+    dev = R.device
+    lp, sg, el = (torch.zeros(W, dtype=torch.float64, device=dev) for _ in range(3))
+    dlp = torch.zeros((W, spec.Nn, 3), dtype=torch.float64, device=dev)
+    dE = torch.zeros_like(dlp)
+    out = {}
+    for name, prec in (("mixed", vbqmc.MIXED), ("fp64", vbqmc.FP64)):
+        n = max(3, steps)
+        ms = {}
+        for what in ("forces", "eval"):
+            call = ((lambda: ctx.eval_nuclear_derivs(0, prec, R, lp, sg, el, dlp, dE)) if what == "forces" else
+                    (lambda: ctx.eval_walkers(0, prec, R, lp, sg, el)))
+            for _ in range(3):
+                call()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(n):
+                call()
+            e1.record()
+            torch.cuda.synchronize()
+            ms[what] = e0.elapsed_time(e1) / n
+        kms = max(ms["forces"] - ms["eval"], 1e-6)
+        flops = force_work(spec, info) * W
+        pk = peaks(sm_mhz)["f32" if prec == vbqmc.MIXED else "f64"]
+        out[name] = {"walkers_per_s": W / (ms["forces"] * 1e-3), "ms_per_call": ms["forces"],
+                     "eval_ms": ms["eval"], "kernel_ms": kms,
+                     "kernel_roofline": {"bound": "alu", "pipe": "fp32" if prec == vbqmc.MIXED else "fp64",
+                                         "achieved": flops / (kms * 1e-3) / 1e12, "peak": pk / 1e12,
+                                         "unit": "TFLOP/s", "frac": flops / (kms * 1e-3) / pk}}
+    return {"walkers": W, "nuclei": spec.Nn, **out}
 
 
 def dmc_timing(ctx, vbqmc, R, el, steps, tau=0.005):
@@ -497,6 +558,7 @@ def main():
     ap.add_argument("--lin-samples", type=int, default=1 << 20, help="samples of the linear-method timing")
     ap.add_argument("--dmc-steps", type=int, default=5, help="timed DMC steps (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3, help="batched-workload timing (0: skip)")
+    ap.add_argument("--force-steps", type=int, default=3, help="nucleus-derivative timing (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

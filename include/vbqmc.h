@@ -161,6 +161,20 @@ int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const d
 int vbqmc_eval_nuclear_derivs(vbqmc_ctx* ctx, int sys_id, int precision, int W, const double* R, double* logpsi,
                               double* sign, double* eloc, double* dlogpsi_dR, double* dEL_dR, void* stream);
 
+/* Weighted sums over walkers of derivative rows, in double with a fixed summation order:
+ *   out[k] = sum_w (ga[w] Ja[w][k] + gb[w] Jb[w][k]),  k < K.
+ * With Ja = O, Jb = dEL (vbqmc_eval_walkers), ga = 2 (E_L - <E_L>)/W and gb = 1/W this is the
+ * energy gradient of Eq. H0j (Sec. 2.3.1) up to its factor 2 convention; with the walkers'
+ * upstream gradients as ga, gb it is the vector-Jacobian product of (ln|Psi|, E_L), and with
+ * the [W][Nn*3] nucleus derivatives (vbqmc_eval_nuclear_derivs) it gives forces.
+ *   Ja, Jb  [W][K] device, element type double (jtype 0) or float (jtype 1); gb and Jb are
+ *           both NULL or both given
+ *   ga, gb  [W] device double
+ *   out     [K] device double (zero when W = 0)
+ * The context's calls must not overlap (a grow-only workspace of the context is used). */
+int vbqmc_weighted_colsum(vbqmc_ctx* ctx, int W, int K, int jtype, const double* ga, const void* Ja,
+                          const double* gb, const void* Jb, double* out, void* stream);
+
 /* VMC (Sec. 2.3.1): nsweeps sweeps of single-electron Metropolis moves over every walker,
  * electron i moved to r_i + step*(2u - 1) per coordinate and accepted when
  * u_acc < |Psi(R')/Psi(R)|^2.  Determinant ratios and Sherman-Morrison updates of the

@@ -18,7 +18,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
 CU_SOURCES = ["kernels.cu", "eval_jastrow.cu", "eval_orbitals.cu", "eval_det.cu", "eval_forces.cu", "dmc.cu",
-              "linmethod.cu", "linmethod_noalloc.cu", "api.cu", "batch_api.cu"]
+              "gradient.cu", "linmethod.cu", "linmethod_noalloc.cu", "api.cu", "batch_api.cu"]
 CPP_SOURCES = ["system_host.cpp"]
 
 

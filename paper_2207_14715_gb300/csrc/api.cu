@@ -85,6 +85,7 @@ void vbqmc_destroy(vbqmc_ctx* ctx) {
   if (ctx->dmc_work) cudaFree(ctx->dmc_work);
   if (ctx->eval_work) cudaFree(ctx->eval_work);
   if (ctx->force_work) cudaFree(ctx->force_work);
+  if (ctx->red_work) cudaFree(ctx->red_work);
   for (auto& ev : ctx->tev)
     if (ev) cudaEventDestroy(ev);
   delete ctx;
@@ -379,6 +380,40 @@ int vbqmc_eval_nuclear_derivs(vbqmc_ctx* ctx, int sys_id, int precision, int W, 
                                              ctx->force_work, st, &nl);
   ctx->last_launches = nl;
   if (e != cudaSuccess) return cuda_fail(e, "nucleus-derivative kernel launch");
+  return VBQMC_OK;
+}
+
+int vbqmc_weighted_colsum(vbqmc_ctx* ctx, int W, int K, int jtype, const double* ga, const void* Ja,
+                          const double* gb, const void* Jb, double* out, void* stream) {
+  if (!ctx) return fail(VBQMC_ERR_ARG, "null context");
+  ctx->last_launches = 0;
+  if (W < 0 || K < 0) return fail(VBQMC_ERR_ARG, "negative size");
+  if (jtype != 0 && jtype != 1) return fail(VBQMC_ERR_ARG, "jtype must be 0 (double) or 1 (float)");
+  if (K == 0) return VBQMC_OK;
+  if (!out) return fail(VBQMC_ERR_ARG, "null out");
+  if ((gb == nullptr) != (Jb == nullptr)) return fail(VBQMC_ERR_ARG, "gb and Jb must both be given or both NULL");
+  DeviceGuard g(ctx->device);
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (W == 0) {
+    cudaError_t e = cudaMemsetAsync(out, 0, (size_t)K * sizeof(double), st);
+    return e == cudaSuccess ? VBQMC_OK : cuda_fail(e, "cudaMemsetAsync");
+  }
+  if (!ga || !Ja) return fail(VBQMC_ERR_ARG, "null ga or Ja");
+  const size_t need = (size_t)vbq::colsum_slices(W) * K * sizeof(double);
+  if (need > ctx->red_bytes) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (ctx->red_work) cudaFree(ctx->red_work);
+    ctx->red_work = nullptr;
+    ctx->red_bytes = 0;
+    e = cudaMalloc(&ctx->red_work, need);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(column-sum workspace)");
+    ctx->red_bytes = need;
+  }
+  cudaError_t e =
+      vbq::launch_weighted_colsum(W, K, jtype, ga, Ja, gb, Jb, out, static_cast<double*>(ctx->red_work), st);
+  if (e != cudaSuccess) return cuda_fail(e, "column-sum kernel launch");
+  ctx->last_launches = 2;
   return VBQMC_OK;
 }
 

@@ -50,6 +50,8 @@ struct vbqmc_ctx {
   size_t eval_bytes = 0;
   void* force_work = nullptr;  // grow-only device workspace of the nucleus derivatives
   size_t force_bytes = 0;
+  void* red_work = nullptr;    // grow-only device workspace of the weighted column sums
+  size_t red_bytes = 0;
   int timing = 0;                               // record events around the evaluation kernels
   cudaEvent_t tev[vbq::kEvalKernels + 1] = {};  // created on first use
   bool tev_valid = false;                       // events of the last timed evaluation are recorded

@@ -90,6 +90,11 @@ size_t force_workspace_bytes(const SysDev& s, int W);
 cudaError_t launch_nuclear_derivs(int precision, const SysDev& s, const EvalLayout& LE, const ForceLayout& LF, int W,
                                   const double* R, double* logpsi, double* sign, double* eloc, double* dlp,
                                   double* dEL, void* ws, void* fws, cudaStream_t st, int* nlaunch);
+// out[k] = sum_w (ga[w] Ja[w][k] + gb[w] Jb[w][k]) (gradient.cu); J element type double
+// (jtype 0) or float (jtype 1), gb/Jb may be null; part: colsum_slices(W) * K doubles.
+int colsum_slices(int W);
+cudaError_t launch_weighted_colsum(int W, int K, int jtype, const double* ga, const void* Ja, const double* gb,
+                                   const void* Jb, double* out, double* part, cudaStream_t st);
 cudaError_t launch_sweep(int precision, const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps,
                          int refresh, const double* state_in, double step, uint64_t seed, uint32_t step0, uint32_t tag,
                          uint32_t woff, int* nacc, cudaStream_t st);

@@ -54,7 +54,7 @@ EXPORTED = ["vbqmc_create", "vbqmc_destroy", "vbqmc_last_error", "vbqmc_set_syst
             "vbqmc_launch_info", "vbqmc_last_launch_count", "vbqmc_accumulate_lin_matrices_noalloc",
             "vbqmc_dmc_steps", "vbqmc_set_kernel_timing", "vbqmc_kernel_times", "vbqmc_batch_create",
             "vbqmc_batch_destroy", "vbqmc_batch_vmc_steps", "vbqmc_batch_tune", "vbqmc_batch_info",
-            "vbqmc_eval_nuclear_derivs"]
+            "vbqmc_eval_nuclear_derivs", "vbqmc_weighted_colsum"]
 
 _LIB = None
 
@@ -77,6 +77,7 @@ def lib():
                                          vp]
         L.vbqmc_eval_nuclear_derivs.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp,
                                                 vp]
+        L.vbqmc_weighted_colsum.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]
         L.vbqmc_vmc_steps.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
                                       vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
@@ -239,6 +240,20 @@ class Context:
         _check(lib().vbqmc_eval_walkers(self.h, int(sys_id), int(precision), int(W), _ptr(R), _ptr(logpsi),
                                         _ptr(sign), _ptr(eloc), _ptr(grad), _ptr(O), _ptr(dEL), _ptr(state_out),
                                         _stream(stream)))
+
+    def weighted_colsum(self, ga, Ja, out, gb=None, Jb=None, stream=None):
+        """out[k] = sum_w ga[w] Ja[w, k] (+ gb[w] Jb[w, k]); Ja, Jb [W, K] float64 or float32 CUDA
+        tensors of one dtype, ga, gb [W] float64, out [K] float64."""
+        W = int(Ja.shape[0])
+        K = int(np.prod(Ja.shape[1:])) if Ja.dim() > 1 else 1
+        for t in (Ja, Jb, ga, gb, out):
+            if t is not None and not t.is_contiguous():
+                raise ValueError("weighted_colsum needs contiguous tensors")
+        jtype = 1 if str(Ja.dtype) == "torch.float32" else 0
+        if Jb is not None and Jb.dtype != Ja.dtype:
+            raise ValueError("Ja and Jb must have one dtype")
+        _check(lib().vbqmc_weighted_colsum(self.h, W, K, jtype, _ptr(ga), _ptr(Ja), _ptr(gb), _ptr(Jb), _ptr(out),
+                                           _stream(stream)))
 
     def eval_nuclear_derivs(self, sys_id, precision, R, logpsi, sign, eloc, dlogpsi_dR, dEL_dR=None, stream=None):
         """Evaluation plus d ln|Psi|/dR_a and dE_L/dR_a ([W, Nn, 3] float64 CUDA tensors)."""
