@@ -45,13 +45,17 @@ struct SweepLayout {
   int G0, G1;
 };
 
-// Nucleus-derivative kernel (eval_forces.cu), warp per walker: positions, weights, grad ln J,
-// orbital gradients, inverses B_u and Z_u = B_u L_u B_u, the orbital tangents of one nucleus
-// D [N][n_ev_det][12], basis derivatives of Ec electrons at a time bd [Ec][max_mu][12], and
-// the Jastrow tangents dG [N][3][3], dLJ [N][3].
+// Nucleus-derivative kernel (eval_forces.cu), one block per walker with one warp per nucleus.
+// Block-shared (offsets from the block's base): positions, determinant weights, grad ln J,
+// pair distances and unit vectors, orbital gradients, dressed Laplacians, inverses B_u and
+// Z_u = B_u L_u B_u.  Per warp (offsets from shared_bytes + warp * warp_bytes): the orbital
+// tangents D [N][n_ev_det][6], basis derivatives of Ec electrons at a time bd
+// [Ec][max_mu][12], the Jastrow tangents dG [N][3][3] and dLJ [N][3], distances to the
+// warp's nucleus sN [N][4] and the scratch Y of Z_u.
 struct ForceLayout {
-  int wpb = 0, warp_bytes = 0;
-  int R, wt, G, Gphi, B, Z, D, bd, dG, dLJ;
+  int nwarps = 0, shared_bytes = 0, warp_bytes = 0, block_bytes = 0;
+  int R, wt, G, uE, uH, Gphi, Ld, B, Z;
+  int D, bd, dG, dLJ, sN, Y;
   int Ec, max_mu;
 };
 
