@@ -167,7 +167,9 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
                o_evco = bb.add(h.ev_chunk_off), o_dc = bb.add(h.det_chunk), o_dco = bb.add(h.det_chunk_off),
                o_zds = bb.add(zeta_ds), o_nds = bb.add(norm_ds), o_cds = bb.add(coef_ds), o_nucds = bb.add(nuc_ds),
                o_zf = bb.add(zeta_f), o_nf = bb.add(norm_f), o_jaf = bb.add(jas_af), o_jbf = bb.add(jas_bf),
-               o_ebf = bb.add(een_Bf), o_nzf = bb.add(nuc_zf), o_nsh = bb.add(h.nuc_sh);
+               o_ebf = bb.add(een_Bf), o_nzf = bb.add(nuc_zf), o_nsh = bb.add(h.nuc_sh),
+               o_jads = bb.add(split(h.jas_a)), o_jbds = bb.add(split(h.jas_b)), o_ecds = bb.add(split(h.een_c)), o_tx0 = bb.add(h.tab_x[0]),
+               o_tx1 = bb.add(h.tab_x[1]), o_td0 = bb.add(h.tab_det[0]), o_td1 = bb.add(h.tab_det[1]);
   cudaError_t e = cudaMalloc(&ls.blob, bb.bytes.size());
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(system tables)");
   ls.blob_bytes = bb.bytes.size();
@@ -216,6 +218,12 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.det_loc[1] = (const int*)(B + o_dl1);
   d.det_ev[0] = (const int*)(B + o_de0);
   d.det_ev[1] = (const int*)(B + o_de1);
+  d.tab_x[0] = (const int*)(B + o_tx0);
+  d.tab_x[1] = (const int*)(B + o_tx1);
+  d.tab_det[0] = (const int*)(B + o_td0);
+  d.tab_det[1] = (const int*)(B + o_td1);
+  d.n_x[0] = (int)h.tab_x[0].size();
+  d.n_x[1] = (int)h.tab_x[1].size();
   d.term_det = (const int*)(B + o_term_det);
   d.term_coef = (const double*)(B + o_term_coef);
   d.sterm_I = (const int*)(B + o_sI);
@@ -256,6 +264,22 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.kappa_f = (float)d.kappa;
   d.b1_anti_f = (float)d.b1_anti;
   d.b1_par_f = (float)d.b1_par;
+  d.jas_a_ds = (const float*)(B + o_jads);
+  d.jas_b_ds = (const float*)(B + o_jbds);
+  d.een_c_ds = (const float*)(B + o_ecds);
+  {
+    const std::vector<float> sc = split(std::vector<double>{d.kappa, d.b1_anti, d.b1_par});
+    d.kappa_ds[0] = sc[0]; d.kappa_ds[1] = sc[1];
+    d.b1_anti_ds[0] = sc[2]; d.b1_anti_ds[1] = sc[3];
+    d.b1_par_ds[0] = sc[4]; d.b1_par_ds[1] = sc[5];
+  }
+  // determinants through the reference-determinant tables when the per-determinant inverses of
+  // one walker do not fit in shared memory
+  d.msd = 0;
+  {
+    vbq::DetLayout probe;
+    if (h.tab_ok && vbq::make_det_layout(d, 8, ctx->max_smem, probe) != VBQMC_OK) d.msd = 1;
+  }
   for (int p = 0; p < 2; ++p) {
     const int tb = p == VBQMC_MIXED ? 4 : 8;
     ls.lay_rc_eval[p] = vbq::make_eval_layout(d, tb, ctx->max_smem, ls.lay_eval[p]);
@@ -276,8 +300,8 @@ int vbqmc_launch_info(vbqmc_ctx* ctx, int sys_id, int precision, int* out) {
     return fail(VBQMC_ERR_NOSYS, "no system loaded under this id");
   if (precision != VBQMC_FP64 && precision != VBQMC_MIXED) return fail(VBQMC_ERR_ARG, "bad precision mode");
   const LoadedSystem& s = ctx->sys[sys_id];
-  out[0] = s.lay_eval[precision].det.wpb;
-  out[1] = s.lay_eval[precision].det.warp_bytes;
+  out[0] = s.dev.msd ? s.lay_eval[precision].tab.wpb : s.lay_eval[precision].det.wpb;
+  out[1] = s.dev.msd ? s.lay_eval[precision].tab.warp_bytes : s.lay_eval[precision].det.warp_bytes;
   out[2] = s.lay_sweep[precision].wpb;
   out[3] = s.lay_sweep[precision].warp_bytes;
   return VBQMC_OK;
@@ -337,6 +361,10 @@ int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const d
   LoadedSystem& s = ctx->sys[sys_id];
   if (s.lay_rc_eval[precision]) return fail(s.lay_rc_eval[precision], "per-walker state exceeds shared memory");
   if ((O || dEL) && s.dev.P == 0) O = dEL = nullptr;
+  if (s.dev.msd && state_out)
+    return fail(VBQMC_ERR_UNSUPPORTED, "walker state: this system's determinants go through reference tables");
+  if (s.dev.msd && O && s.dev.n_kappa > 0)
+    return fail(VBQMC_ERR_UNSUPPORTED, "orbital-excitation derivatives with reference-determinant tables");
   DeviceGuard g(ctx->device);
   rc = ensure_eval_ws(ctx, s, precision, W, (cudaStream_t)stream);
   if (rc) return rc;
@@ -357,6 +385,7 @@ int vbqmc_eval_nuclear_derivs(vbqmc_ctx* ctx, int sys_id, int precision, int W, 
   if (!R || !logpsi || !sign || !eloc || !dlogpsi_dR) return fail(VBQMC_ERR_ARG, "null required pointer");
   LoadedSystem& s = ctx->sys[sys_id];
   if (s.lay_rc_eval[precision]) return fail(s.lay_rc_eval[precision], "per-walker state exceeds shared memory");
+  if (s.dev.msd) return fail(VBQMC_ERR_UNSUPPORTED, "nucleus derivatives with reference-determinant tables");
   if (s.lay_rc_force[precision])
     return fail(s.lay_rc_force[precision], "nucleus-derivative tables exceed shared memory");
   DeviceGuard g(ctx->device);
@@ -430,6 +459,7 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
   if (W == 0) return VBQMC_OK;
   if (!R) return fail(VBQMC_ERR_ARG, "null R");
   LoadedSystem& s = ctx->sys[sys_id];
+  if (s.dev.msd) return fail(VBQMC_ERR_UNSUPPORTED, "VMC sweeps need per-determinant inverses (use DMC steps)");
   if (s.lay_rc_sweep[precision]) return fail(s.lay_rc_sweep[precision], "per-walker state exceeds shared memory");
   const bool do_eval = logpsi || sign || eloc || O || dEL;
   if (do_eval && (!logpsi || !sign || !eloc)) return fail(VBQMC_ERR_ARG, "evaluation needs logpsi, sign and eloc");

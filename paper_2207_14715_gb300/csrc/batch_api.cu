@@ -240,6 +240,8 @@ int vbqmc_batch_create(vbqmc_ctx* ctx, int nsys, const int* sys_ids, const int* 
     if (id < 0 || id >= VBQMC_MAX_SYSTEMS || !ctx->sys[id].loaded)
       return fail(VBQMC_ERR_NOSYS, "no system loaded under id " + std::to_string(id));
     if (W[k] < 1) return fail(VBQMC_ERR_ARG, "every system needs at least one walker");
+    if (ctx->sys[id].dev.msd)
+      return fail(VBQMC_ERR_UNSUPPORTED, "system " + std::to_string(id) + " needs reference-determinant tables");
     if (ctx->sys[id].lay_rc_eval[precision] || ctx->sys[id].lay_rc_sweep[precision])
       return fail(VBQMC_ERR_CAPACITY, "per-walker state of system " + std::to_string(id) + " exceeds shared memory");
     for (int q = 0; q < k; ++q)

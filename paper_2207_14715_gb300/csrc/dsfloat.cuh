@@ -64,6 +64,28 @@ __device__ __forceinline__ float ds_diff_f(dsf a, dsf b) {
   return d.hi + (d.lo + (a.lo - b.lo));
 }
 __device__ __forceinline__ dsf ds_neg(dsf a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dsf ds_sub(dsf a, dsf b) { return ds_add(a, ds_neg(b)); }
+// 1/a: float reciprocal y0 of a.hi, then one Newton step y0 + y0 (1 - a y0) with the residual
+// 1 - a y0 formed in float-float (its error is second order in the float error of y0).
+__device__ __forceinline__ dsf ds_recip(dsf a) {
+  const float y0 = 1.0f / a.hi;
+  const dsf e = ds_add_f(ds_neg(ds_mul(a, dsf{y0, 0.0f})), 1.0f);
+  return ds_add_f(ds_two_prod(y0, e.hi), y0);
+}
+// a/b: float quotient q0 = a.hi/b.hi, then one correction (a - b q0)/b.hi
+__device__ __forceinline__ dsf ds_div(dsf a, dsf b) {
+  const float q0 = a.hi / b.hi;
+  const dsf r = ds_sub(a, ds_mul(b, dsf{q0, 0.0f}));
+  return ds_add_f(dsf{r.hi / b.hi, 0.0f}, q0);
+}
+// sqrt(a), a >= 0: s0 = sqrt(a.hi) in float, then s0 + (a - s0^2)/(2 s0) (Newton's step on
+// s^2 = a, residual exact through TwoProduct).
+__device__ __forceinline__ dsf ds_sqrt(dsf a) {
+  if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
+  const float s0 = sqrtf(a.hi);
+  const dsf r = ds_sub(a, ds_two_prod(s0, s0));
+  return ds_add_f(dsf{r.hi / (2.0f * s0), 0.0f}, s0);
+}
 __device__ __forceinline__ dsf ds_from_double(double x) {
   const float h = (float)x;
   return {h, (float)(x - (double)h)};

@@ -307,6 +307,8 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
   }
 }
 
+}  // namespace
+
 int make_det_layout(const SysDev& s, int tb, int max_smem, DetLayout& L) {
   int off = 0;
   auto take = [&](int bytes) {
@@ -349,8 +351,8 @@ int make_det_layout(const SysDev& s, int tb, int max_smem, DetLayout& L) {
   return VBQMC_OK;
 }
 
+namespace {
 inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
-
 }  // namespace
 
 EvalWs carve_eval_ws(const SysDev& s, int tb, int W, void* ws) {
@@ -390,14 +392,19 @@ cudaError_t launch_eval_t(const SysDev& s, const EvalLayout& L, int W, const dou
   if (e != cudaSuccess) return e;
   ++*nlaunch;
   if ((e = mark(2)) != cudaSuccess) return e;
-  const DetLayout& D = L.det;
-  const int smem = D.wpb * D.warp_bytes;
-  e = cudaFuncSetAttribute(det_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  det_kernel<Tb><<<(W + D.wpb - 1) / D.wpb, 32 * D.wpb, smem, st>>>(
-      s, D, W, static_cast<const Tb*>(b.JG), static_cast<const Tb*>(b.JL), b.JS, static_cast<const Tb*>(b.OB), b.OD,
-      logpsi, sign, eloc, b.VG, grad, O, dEL, state_out, aux);
-  e = cudaGetLastError();
+  if (s.msd) {
+    e = launch_dettab<Tb>(s, L.tab, W, static_cast<const Tb*>(b.JG), static_cast<const Tb*>(b.JL), b.JS,
+                          static_cast<const Tb*>(b.OB), b.OD, logpsi, sign, eloc, b.VG, grad, O, dEL, st);
+  } else {
+    const DetLayout& D = L.det;
+    const int smem = D.wpb * D.warp_bytes;
+    e = cudaFuncSetAttribute(det_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    det_kernel<Tb><<<(W + D.wpb - 1) / D.wpb, 32 * D.wpb, smem, st>>>(
+        s, D, W, static_cast<const Tb*>(b.JG), static_cast<const Tb*>(b.JL), b.JS, static_cast<const Tb*>(b.OB), b.OD,
+        logpsi, sign, eloc, b.VG, grad, O, dEL, state_out, aux);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   ++*nlaunch;
   if ((e = mark(3)) != cudaSuccess) return e;
@@ -429,7 +436,8 @@ template cudaError_t launch_det_batch<double>(const BatchSys*, const BatchItem*,
 int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
   int rc = make_jas_layout(s, tb, max_smem, L.jas);
   if (rc == VBQMC_OK) rc = make_orb_layout(s, tb, max_smem, L.orb);
-  if (rc == VBQMC_OK) rc = make_det_layout(s, tb, max_smem, L.det);
+  if (rc == VBQMC_OK)
+    rc = s.msd ? make_dettab_layout(s, tb, max_smem, L.tab) : make_det_layout(s, tb, max_smem, L.det);
   return rc;
 }
 

@@ -26,6 +26,7 @@ template <class Tb> struct LnSum {
 template <> struct LnSum<float> {
   dsf v = {0.0f, 0.0f};
   __device__ __forceinline__ void add(float x) { v = ds_add_f(v, x); }
+  __device__ __forceinline__ void add(dsf x) { v = ds_add(v, x); }
   __device__ __forceinline__ void add(const LnSum& o) { v = ds_add(v, o.v); }
   __device__ __forceinline__ double value() const { return ds_to_double(v); }
 };
@@ -56,7 +57,13 @@ __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L
         const Tb r = g.rEN[ia];
         Tb f, df, d2f;
         pade_eval<Tb, true>(en_coef_t<Tb>(s, a), r, kap, f, df, d2f);
-        lnj.add(f);
+        if constexpr (kSameType<Tb, double>) {
+          lnj.add(f);
+        } else {  // the value in float-float from float-float coordinates
+          const dsf na[3] = {nuc_coord_ds(s, a, 0), nuc_coord_ds(s, a, 1), nuc_coord_ds(s, a, 2)};
+          lnj.add(pade_value_ds(ds_dist(C.R + 3 * i, na), s.jas_a_ds + 12 * __ldg(s.nuc_elem + a), nullptr,
+                                s.kappa_ds));
+        }
         g0 += df * g.eEN[3 * ia]; g1 += df * g.eEN[3 * ia + 1]; g2 += df * g.eEN[3 * ia + 2];
         lap += d2f + (Tb)2 * df / r;
       }
@@ -65,7 +72,13 @@ __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L
         const int ij = i * N + j;
         Tb f, df, d2f;
         pade_eval<Tb, true>(ee_coef_t<Tb>(s, (i < Nup) == (j < Nup)), g.rEE[ij], kap, f, df, d2f);
-        lnj.add((Tb)0.5 * f);
+        if constexpr (kSameType<Tb, double>) {
+          lnj.add((Tb)0.5 * f);
+        } else {
+          const dsf v = pade_value_ds(ds_dist(C.R + 3 * i, C.R + 3 * j), s.jas_b_ds,
+                                      (i < Nup) == (j < Nup) ? s.b1_par_ds : s.b1_anti_ds, s.kappa_ds);
+          lnj.add(dsf{0.5f * v.hi, 0.5f * v.lo});
+        }
         g0 += df * g.eEE[3 * ij]; g1 += df * g.eEE[3 * ij + 1]; g2 += df * g.eEE[3 * ij + 2];
         lap += d2f + (Tb)2 * df * g.iEE[ij];
       }
@@ -76,9 +89,13 @@ __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L
           EenSide<Tb> si;
           si.set(g.Stab[(a * N + i) * 6 + 1], g.rEN[ia], kap);
           const Tb ex = g.eEN[3 * ia], ey = g.eEN[3 * ia + 1], ez = g.eEN[3 * ia + 2];
+          const float* cds = s.een_c_ds + 2 * kNeen * __ldg(s.nuc_elem + a);
           auto sink = [&](int t, Tb val, Tb gx, Tb gy, Tb gz, Tb lp) {
             const Tb ct = c[t];
-            lnj.add(ct * val);
+            if constexpr (kSameType<Tb, double>)
+              lnj.add(ct * val);
+            else  // coefficient as a float-float pair: its rounding would shift every triple alike
+              lnj.add(ds_mul(dsf{__ldg(cds + 2 * t), __ldg(cds + 2 * t + 1)}, dsf{val, 0.0f}));
             g0 += ct * gx; g1 += ct * gy; g2 += ct * gz;
             lap += ct * lp;
           };
@@ -91,7 +108,7 @@ __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L
                 acc.add(g.uEE[ij], g.iEE[ij], kap, g.eEE[3 * ij], g.eEE[3 * ij + 1], g.eEE[3 * ij + 2],
                         g.Stab + (a * N + j) * 6);
               }
-            een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, sink);
+            een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, g.SsumLo + 6 * a, sink);
           }
           {
             EenAcc<Tb, 3, 4> acc;
@@ -102,7 +119,7 @@ __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L
                 acc.add(g.uEE[ij], g.iEE[ij], kap, g.eEE[3 * ij], g.eEE[3 * ij + 1], g.eEE[3 * ij + 2],
                         g.Stab + (a * N + j) * 6);
               }
-            een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, sink);
+            een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, g.SsumLo + 6 * a, sink);
           }
         }
       lnJ_loc.add(lnj);
@@ -286,7 +303,7 @@ __device__ __forceinline__ void jastrow_deriv_body(const SysDev& s, const JasLay
                 acc.add(g.uEE[ij], g.iEE[ij], kap, g.eEE[3 * ij], g.eEE[3 * ij + 1], g.eEE[3 * ij + 2],
                         g.Stab + (a * N + j) * 6);
               }
-            een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, sink);
+            een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, g.SsumLo + 6 * a, sink);
           }
           {
             EenAcc<Tb, 3, 4> acc;
@@ -297,7 +314,7 @@ __device__ __forceinline__ void jastrow_deriv_body(const SysDev& s, const JasLay
                 acc.add(g.uEE[ij], g.iEE[ij], kap, g.eEE[3 * ij], g.eEE[3 * ij + 1], g.eEE[3 * ij + 2],
                         g.Stab + (a * N + j) * 6);
               }
-            een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, sink);
+            een_terms(acc, si, ex, ey, ez, g.Ssum + 6 * a, g.SsumLo + 6 * a, sink);
           }
         }
       }

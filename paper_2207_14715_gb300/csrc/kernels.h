@@ -32,10 +32,17 @@ struct DetLayout {
   int G0, G1;  // lane-group size per spin for the LU
 };
 
+// Determinant part through the reference-determinant tables (eval_dettab.cu), warp per walker.
+struct DetTabLayout {
+  int wpb = 0, warp_bytes = 0;
+  int vg, G, B0, B1, T0, T1, Y0, Y1, A, Bs, perm, Ls, ldet, dsg, tdet, Wdet, rk, Minv, Gam;
+};
+
 struct EvalLayout {
   JasLayout jas;
   OrbLayout orb;
   DetLayout det;
+  DetTabLayout tab;  // used instead of det when the system's msd flag is set
 };
 
 struct SweepLayout {
@@ -60,6 +67,12 @@ struct ForceLayout {
 };
 
 int make_eval_layout(const SysDev& s, int bulk_bytes, int max_smem, EvalLayout& L);
+int make_det_layout(const SysDev& s, int bulk_bytes, int max_smem, DetLayout& L);
+int make_dettab_layout(const SysDev& s, int bulk_bytes, int max_smem, DetTabLayout& L);
+template <class Tb>
+cudaError_t launch_dettab(const SysDev& s, const DetTabLayout& L, int W, const Tb* JG, const Tb* JL, const double* JS,
+                          const Tb* OB, const double* OD, double* logpsi, double* sign, double* eloc, double* vg_ws,
+                          double* grad, Tb* O, Tb* dEL, cudaStream_t st);
 int make_force_layout(const SysDev& s, int bulk_bytes, int max_smem, ForceLayout& L);
 int make_sweep_layout(const SysDev& s, int bulk_bytes, int max_smem, SweepLayout& L);
 

@@ -389,6 +389,56 @@ int build_system(const vbqmc_system_desc* d, SysHost& s, std::string& err) {
       s.kap_off[sp].push_back((int)(s.kap_ent[sp].size() / 4));
     }
   }
+  // reference-determinant tables: determinant u of a spin is the reference (u = 0) with the
+  // slots S_u replaced by the orbitals Q_u (k_u <= kMaxExc each, ascending, paired in order),
+  // up to the parity of the column permutation from that replaced column list to u's own
+  // column order: D_u = sgn_u D_0 det(T[S_u, Q_u]) with T = A_0^-1 Phi.
+  s.tab_ok = 1;
+  for (int sp = 0; sp < 2; ++sp) {
+    const int n = s.n[sp], U = s.U[sp];
+    s.tab_x[sp].clear();
+    s.tab_det[sp].assign((size_t)U * kTabStride, 0);
+    if (n == 0) continue;
+    const int* ref = s.det_ev[sp].data();
+    std::vector<char> in_ref(s.ev_orb.size(), 0);
+    for (int o = 0; o < n; ++o) in_ref[ref[o]] = 1;
+    std::vector<int> xpos(s.ev_orb.size(), -1);
+    for (int u = 0; u < U; ++u)
+      for (int o = 0; o < n; ++o) {
+        const int q = s.det_ev[sp][(size_t)u * n + o];
+        if (!in_ref[q] && xpos[q] < 0) xpos[q] = 0;
+      }
+    for (size_t q = 0; q < xpos.size(); ++q)
+      if (xpos[q] == 0) { xpos[q] = (int)s.tab_x[sp].size(); s.tab_x[sp].push_back((int)q); }
+    for (int u = 0; u < U; ++u) {
+      const int* cols = s.det_ev[sp].data() + (size_t)u * n;
+      std::vector<char> in_u(s.ev_orb.size(), 0);
+      for (int o = 0; o < n; ++o) in_u[cols[o]] = 1;
+      std::vector<int> S, Q;
+      for (int o = 0; o < n; ++o)
+        if (!in_u[ref[o]]) S.push_back(o);
+      for (int o = 0; o < n; ++o)
+        if (!in_ref[cols[o]]) Q.push_back(cols[o]);
+      std::sort(Q.begin(), Q.end());
+      if ((int)S.size() > kMaxExc) { s.tab_ok = 0; continue; }
+      // replaced column list and the parity of the permutation to u's order
+      std::vector<int> rep(ref, ref + n);
+      for (size_t j = 0; j < S.size(); ++j) rep[S[j]] = Q[j];
+      std::vector<int> pos(n);
+      for (int o = 0; o < n; ++o) pos[o] = (int)(std::find(rep.begin(), rep.end(), cols[o]) - rep.begin());
+      int par = 0;
+      for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+          if (pos[i] > pos[j]) ++par;
+      int* t = s.tab_det[sp].data() + (size_t)u * kTabStride;
+      t[0] = (int)S.size();
+      t[1] = (par & 1) ? -1 : 1;
+      for (size_t j = 0; j < S.size(); ++j) {
+        t[2 + j] = S[j];
+        t[2 + kMaxExc + j] = xpos[Q[j]];
+      }
+    }
+  }
   // contraction work chunks
   for (int sp = 0; sp < 2; ++sp) make_chunks(s, s.occ_list[sp], s.occ_chunk[sp], s.occ_chunk_off[sp]);
   make_chunks(s, s.ev_orb, s.ev_chunk, s.ev_chunk_off);

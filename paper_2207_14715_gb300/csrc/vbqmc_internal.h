@@ -16,6 +16,8 @@ constexpr int kMaxM = 1024;      // basis functions
 constexpr int kNeen = 23;        // e-e-n expansion terms per element (Sec. 2.1)
 constexpr int kNfree = 15;       // free e-e-n coefficients per element after the cusp conditions
 constexpr int kMaxElem = 16;
+constexpr int kMaxExc = 4;                   // reference-determinant tables: excitation degree
+constexpr int kTabStride = 2 + 2 * kMaxExc;  // per determinant: k, sign, S[kMaxExc], Q[kMaxExc]
 
 // e-e-n terms (p, k, l, m): p = 2..5, k = 0..p-1, l = 0..lmax with lmax = p-k (k != 0) or
 // p-k-2 (k = 0), kept when m = (p-k-l)/2 is an integer (Sec. 2.1, f_een).
@@ -44,6 +46,12 @@ struct SysHost {
   std::vector<int> det_loc[2];         // [U][n] index into occ_list[s]
   std::vector<int> det_ev[2];          // [U][n] eval index
   std::vector<int> det_glob[2];        // [U][n] global orbital id
+  // reference-determinant tables (usable when tab_ok): eval indices of the determinant
+  // orbitals outside the reference determinant u = 0, and per determinant [kTabStride]:
+  // k, sign, reference slots S[kMaxExc], positions in tab_x of the new orbitals Q[kMaxExc]
+  int tab_ok = 0;
+  std::vector<int> tab_x[2];
+  std::vector<int> tab_det[2];
   // determinant terms: unique (up, dn) pairs with merged coefficients C_k = sum_I c_I d_{I,k}
   std::vector<int> term_det;           // [nterm][2]
   std::vector<double> term_coef;       // [nterm]
@@ -102,6 +110,10 @@ struct SysDev {
   const int* occ_list[2];
   const int* det_loc[2];
   const int* det_ev[2];
+  int msd;                             // determinant part through the reference-determinant tables
+  int n_x[2];
+  const int* tab_x[2];
+  const int* tab_det[2];
   const int* term_det;
   const double* term_coef;
   const int* sterm_I;
@@ -136,6 +148,11 @@ struct SysDev {
   const float* jas_bf;                 // like jas_b
   const float* een_Bf;                 // like een_B
   float kappa_f, b1_anti_f, b1_par_f;
+  // float-float copies for the mixed form's e-n and e-e Jastrow values and Rbar (they set ln J)
+  const float* jas_a_ds;               // [n_elem][6][2]
+  const float* jas_b_ds;               // [6][2]
+  const float* een_c_ds;               // [n_elem][23][2] e-e-n coefficients
+  float kappa_ds[2], b1_anti_ds[2], b1_par_ds[2];
 };
 
 // Records the calling thread's error message (read by vbqmc_last_error) and returns 'code';

@@ -145,6 +145,28 @@ template <> __device__ __forceinline__ PadeT<double> ee_coef_t<double>(const Sys
 template <> __device__ __forceinline__ PadeT<float> ee_coef_t<float>(const SysDev& s, bool same) {
   return load_pade<float>(s.jas_bf, same ? s.b1_par_f : s.b1_anti_f);
 }
+// Value of the Pade + polynomial form f(r) = a1 R/(1 + a2 R) + sum_p q_p R^p, R = r/(1 + kappa r),
+// in float-float: the e-n and e-e terms of ln J, whose sum over all pairs sets ln|Psi| (the
+// mixed form's derivatives keep the float form).  p: [a1 a2 q0 q1 q2 q3] as (hi, lo) pairs
+// (a1 replaced by a1r when a1r is given).
+__device__ __forceinline__ dsf pade_value_ds(dsf r, const float* p, const float* a1r, const float* kap) {
+  const dsf k = {kap[0], kap[1]};
+  const dsf R = ds_div(r, ds_add_f(ds_mul(k, r), 1.0f));
+  const dsf a1 = a1r ? dsf{a1r[0], a1r[1]} : dsf{__ldg(p), __ldg(p + 1)};
+  const dsf a2 = {__ldg(p + 2), __ldg(p + 3)};
+  dsf poly = {__ldg(p + 10), __ldg(p + 11)};
+  poly = ds_add(ds_mul(poly, R), dsf{__ldg(p + 8), __ldg(p + 9)});
+  poly = ds_add(ds_mul(poly, R), dsf{__ldg(p + 6), __ldg(p + 7)});
+  poly = ds_add(ds_mul(poly, R), dsf{__ldg(p + 4), __ldg(p + 5)});
+  const dsf R2 = ds_mul(R, R);
+  return ds_add(ds_div(ds_mul(a1, R), ds_add_f(ds_mul(a2, R), 1.0f)), ds_mul(poly, R2));
+}
+// |a - b| for float-float 3-vectors
+__device__ __forceinline__ dsf ds_dist(const dsf* a, const dsf* b) {
+  const dsf dx = ds_sub(a[0], b[0]), dy = ds_sub(a[1], b[1]), dz = ds_sub(a[2], b[2]);
+  return ds_sqrt(ds_add(ds_add(ds_mul(dx, dx), ds_mul(dy, dy)), ds_mul(dz, dz)));
+}
+
 // 1/x in double (the determinant-ratio updates); see recip_dd.
 __device__ __forceinline__ double recip(double x) { return recip_dd(x); }
 
@@ -255,7 +277,7 @@ __device__ __forceinline__ void term_ratios(const SysDev& s, int lane, const dou
 //   Ssum [Nn][6] sum_i Rbar(r_ia)^q.
 // Returns this lane's share of the Coulomb potential V_ee + V_en.
 template <class Tb> struct GeoTables {
-  Tb *rEE, *uEE, *iEE, *eEE, *rEN, *eEN, *Stab, *Ssum;
+  Tb *rEE, *uEE, *iEE, *eEE, *rEN, *eEN, *Stab, *Ssum, *SsumLo;
   __device__ __forceinline__ GeoTables(Tb* geo, int N, int Nn) {
     rEE = geo;
     uEE = rEE + N * N;
@@ -265,10 +287,11 @@ template <class Tb> struct GeoTables {
     eEN = rEN + N * Nn;
     Stab = eEN + 3 * N * Nn;
     Ssum = Stab + 6 * N * Nn;
+    SsumLo = Ssum + 6 * Nn;
   }
 };
 template <class Tb> __host__ __device__ constexpr int geo_elems(int N, int Nn) {
-  return 6 * N * N + 4 * N * Nn + 6 * N * Nn + 6 * Nn;
+  return 6 * N * N + 4 * N * Nn + 6 * N * Nn + 12 * Nn;
 }
 
 // Electron coordinates of one walker as the kernels read them: double in the FP64 form;
@@ -307,10 +330,19 @@ template <class Tb> __device__ __forceinline__ Coords<Tb> load_coords(const doub
   return c;
 }
 
+// Rbar(r) = 1/(1 + kappa r).  The float form takes kappa as a float-float pair and rounds only
+// the result: kappa = 0.8 is not a float, and its rounding would shift every e-e-n term of
+// ln J the same way (a systematic error that grows with the number of terms).
+__device__ __forceinline__ double rbar(const SysDev& s, double r) { return 1.0 / (1.0 + s.kappa * r); }
+__device__ __forceinline__ float rbar(const SysDev& s, float r) {
+  const dsf d = ds_add_f(ds_mul(dsf{s.kappa_ds[0], s.kappa_ds[1]}, dsf{r, 0.0f}), 1.0f);
+  const float q = 1.0f / d.hi;
+  return fmaf(-q * q, d.lo, q);
+}
+
 template <class Tb>
 __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, const Coords<Tb>& C, const GeoTables<Tb>& g) {
   const int N = s.N, Nn = s.Nn;
-  const Tb kap = (Tb)s.kappa;
   Tb V_loc = 0;
   for (DivStep ij(lane, N); ij.hi < N; ij.next(N)) {
     const int i = ij.hi, j = ij.lo, p = i * N + j;
@@ -321,7 +353,7 @@ __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, cons
     }
     const Tb dx = C.ee(i, j, 0), dy = C.ee(i, j, 1), dz = C.ee(i, j, 2);
     const Tb r = vsqrt(dx * dx + dy * dy + dz * dz), ir = (Tb)1 / r;
-    g.rEE[p] = r; g.uEE[p] = (Tb)1 / ((Tb)1 + kap * r); g.iEE[p] = ir;
+    g.rEE[p] = r; g.uEE[p] = rbar(s, r); g.iEE[p] = ir;
     g.eEE[3 * p] = dx * ir; g.eEE[3 * p + 1] = dy * ir; g.eEE[3 * p + 2] = dz * ir;
     if (i < j) V_loc += ir;
   }
@@ -332,7 +364,7 @@ __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, cons
     g.rEN[p] = r;
     g.eEN[3 * p] = dx * ir; g.eEN[3 * p + 1] = dy * ir; g.eEN[3 * p + 2] = dz * ir;
     V_loc -= C.charge(s, a) * ir;
-    const Tb sv = (Tb)1 / ((Tb)1 + kap * r);
+    const Tb sv = rbar(s, r);
     Tb* St = g.Stab + (a * N + i) * 6;
     Tb pw = (Tb)1;
 #pragma unroll
@@ -341,9 +373,20 @@ __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, cons
   __syncwarp();
   for (int p = lane; p < Nn * 6; p += 32) {
     const int a = p / 6, q = p - 6 * a;
-    Tb t = 0;
-    for (int i = 0; i < N; ++i) t += g.Stab[(a * N + i) * 6 + q];
-    g.Ssum[p] = t;
+    // sum over all electrons of s^q, shared by every electron's k = 0 e-e-n terms (which take
+    // their own s^q off it): float-float in the float form, so that its rounding does not repeat
+    // coherently through every electron
+    if constexpr (kSameType<Tb, double>) {
+      Tb t = 0;
+      for (int i = 0; i < N; ++i) t += g.Stab[(a * N + i) * 6 + q];
+      g.Ssum[p] = t;
+      g.SsumLo[p] = 0;
+    } else {
+      dsf t = {0.0f, 0.0f};
+      for (int i = 0; i < N; ++i) t = ds_add_f(t, g.Stab[(a * N + i) * 6 + q]);
+      g.Ssum[p] = t.hi;
+      g.SsumLo[p] = t.lo;
+    }
   }
   __syncwarp();
   return (double)V_loc;

@@ -8,6 +8,7 @@
 
 #include <utility>
 
+#include "dsfloat.cuh"
 #include "vbqmc_internal.h"
 
 namespace vbq {
@@ -452,10 +453,10 @@ template <class T> struct EenSide {
 
 // Calls f(t, val, gx, gy, gz, lap) for every term t with k in [K0, K1] (k = 0 terms when
 // K0 == 1): val = s_i^A Y^{k,B}, (gx, gy, gz) = grad_i and lap = lap_i of the term's part
-// that involves electron i, as written above.  (ex, ey, ez) = (r_i - r_a)/r_ia; Ssum[q] = sum_j s_j^q.
+// that involves electron i, as written above.  (ex, ey, ez) = (r_i - r_a)/r_ia; Ssum[q] = sum_j s_j^q (SsumLo[q]: its low float part in the float form, 0 otherwise).
 template <class T, int K0, int K1, class F>
 __device__ __forceinline__ void een_terms(const EenAcc<T, K0, K1>& acc, const EenSide<T>& si, T ex, T ey, T ez,
-                                          const T* Ssum, F&& f) {
+                                          const T* Ssum, const T* SsumLo, F&& f) {
   een_for_each([&](auto tc) {
     constexpr int t = decltype(tc)::value;
     constexpr int k = een_klm(t).k, A = een_klm(t).l + een_klm(t).m, B = een_klm(t).m;
@@ -463,8 +464,13 @@ __device__ __forceinline__ void een_terms(const EenAcc<T, K0, K1>& acc, const Ee
     if (!mine) return;
     T Ya, Yb, Zax = 0, Zay = 0, Zaz = 0, Zbx = 0, Zby = 0, Zbz = 0, Qa = 0, Qb = 0;
     if (k == 0) {
-      Ya = Ssum[A] - si.S[A];
-      Yb = Ssum[B] - si.S[B];
+      if constexpr (sizeof(T) == 4) {  // float: the float-float sum minus own term, rounded once
+        Ya = ds_diff_f(dsf{Ssum[A], SsumLo[A]}, dsf{si.S[A], 0.0f});
+        Yb = ds_diff_f(dsf{Ssum[B], SsumLo[B]}, dsf{si.S[B], 0.0f});
+      } else {
+        Ya = Ssum[A] - si.S[A];
+        Yb = Ssum[B] - si.S[B];
+      }
     } else {
       constexpr int ca = EenK<K0, K1>::idx(k >= K0 ? k : K0, A <= 5 - k ? A : 0);
       constexpr int cb = EenK<K0, K1>::idx(k >= K0 ? k : K0, B <= 5 - k ? B : 0);

@@ -362,6 +362,73 @@ def small_open_shell(seed: int = 11, params: bool = True, een: bool = True) -> S
         kappa_kl=kap if params else np.zeros((0, 2), np.int32), step=0.4)
 
 
+def dmc48(seed: int = 20220728 + 3) -> SystemSpec:
+    """48-electron system for DMC at scale: 12 nuclei C2 N2 O2 H6 (sum Z = 48) at seeded positions
+    at least 1.8 bohr apart; per center 5 s, 3 p, 2 d Gaussians (M = 312), exponents per element
+    log-uniform in [0.1, 20].  24 electrons per spin occupy 20 inactive orbitals and 4 of 8
+    active orbitals (localised on the nuclei where the initial walkers start).  20 structures:
+    12 pair the 8 active orbitals into 4 distinct singlet pairs (16 determinants each), 8 use 3
+    distinct pairs and one doubly occupied active orbital (8 determinants each): 256
+    determinants, up to C(8,4) = 70 unique determinants per spin.  Jastrow e-n, e-e, e-e-n; no
+    optimisable parameters (the system is for DMC)."""
+    rng = np.random.default_rng(seed)
+    Z = np.array([6, 6, 7, 7, 8, 8, 1, 1, 1, 1, 1, 1], np.float64)
+    Nn = len(Z)
+    box = 1.8 * (Nn ** (1.0 / 3.0)) + 1.0
+    xyz = []
+    while len(xyz) < Nn:
+        p = rng.uniform(-box, box, 3)
+        if all(np.linalg.norm(p - q) >= 1.8 for q in xyz):
+            xyz.append(p)
+    xyz = np.array(xyz, np.float64)
+    elems = [1, 6, 7, 8]
+    elem = np.array([elems.index(int(z)) for z in Z], np.int32)
+    sc, sl, sz = _center_shells(rng, list(elem), [0] * 5 + [1] * 3 + [2] * 2)
+    M = int(sum(NCOMP[l] for l in sl))
+    lo, hi = _basis_ranges(sc, sl, Nn)
+    slots = []
+    for a, z in enumerate(Z):
+        slots += [a] * int(round(z))
+    n_inact, n_act = 20, 8
+    orbs, ocls, okind = [], [], []
+    for q in range(n_inact + n_act):
+        c = slots[(2 * q) % len(slots)] if q < n_inact else slots[(2 * n_inact + (q - n_inact)) % len(slots)]
+        orbs.append(_local_orbital(rng, M, lo, hi, sc, sl, c))
+        ocls.append(c)
+        okind.append(0 if q < n_inact else 1)
+    orb = np.stack(orbs)
+    inactive = list(range(n_inact))
+    act = list(range(n_inact, n_inact + n_act))
+    strs, seen = [], set()
+    while len(strs) < 12:                      # 4 distinct pairs
+        perm = [int(x) for x in rng.permutation(act)]
+        prs = tuple(sorted((min(perm[2 * q], perm[2 * q + 1]), max(perm[2 * q], perm[2 * q + 1])) for q in range(4)))
+        if prs not in seen:
+            seen.add(prs)
+            strs.append((inactive, list(prs), []))
+    while len(strs) < 20:                      # 3 distinct pairs + 1 doubly occupied active orbital
+        perm = [int(x) for x in rng.permutation(act)]
+        prs = [(min(perm[2 * q], perm[2 * q + 1]), max(perm[2 * q], perm[2 * q + 1])) for q in range(3)]
+        prs = tuple(sorted(prs + [(perm[6], perm[6])]))
+        if prs not in seen:
+            seen.add(prs)
+            strs.append((inactive, list(prs), []))
+    io, ina, po, prs_arr, uo, un = _structures(strs)
+    c_vb = np.concatenate([[1.0], rng.uniform(0.1, 0.6, len(strs) - 1)])
+    jas_a = np.zeros((len(elems), 6))
+    jas_a[:, 0] = -np.array(elems, np.float64)
+    jas_a[:, 1] = 1.0
+    jas_a[:, 2:] = rng.uniform(-0.05, 0.05, (len(elems), 4))
+    jas_b = np.zeros(6)
+    jas_b[1] = 1.0
+    jas_b[2:] = rng.uniform(-0.05, 0.05, 4)
+    return SystemSpec(
+        name="dmc48", nuc_xyz=xyz, nuc_Z=Z, nuc_elem=elem, n_elem=len(elems), sh_center=sc, sh_l=sl, sh_zeta=sz,
+        orb_coef=orb, orb_class=np.array(ocls, np.int32), orb_kind=np.array(okind, np.int32), n_up=24, n_dn=24,
+        c_vb=c_vb, inact_off=io, inact=ina, pair_off=po, pairs=prs_arr, unp_off=uo, unp=un, jas_a=jas_a,
+        jas_b=jas_b, een_on=True, een_theta=rng.uniform(-0.02, 0.02, (len(elems), EEN_NFREE)), step=0.3)
+
+
 def random_molecule(seed: int, max_electrons: int = 32) -> SystemSpec:
     """One system of the batched workload of many small uneven molecules: 2-10 nuclei with Z in
     {1, 3, 6, 7, 8, 9} at random positions at least 1.8 bohr apart, N = sum Z rounded up to
