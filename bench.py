@@ -26,6 +26,7 @@ sys.path.insert(0, ROOT)
 METRIC = "walker-steps/s (E_L + dlnPsi/dp + dE_L/dp), VMC sweep + evaluation"
 UNIT = "walker-steps/s"
 W_PER_GPU = 16384
+REFRESH = 10  # walker-steps between refactorisations of the Slater matrices
 SEED = 20220728 + 1
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per walker of the walker kernels
@@ -54,7 +55,9 @@ def workload_config(W, flush=True):
     return {"workload": "ethylene-shaped JVB VMC: 16 e (8/8), 6 nuclei, M=126 Gaussians, 6 structures / "
                         "24 determinants, e-n+e-e+e-e-n Jastrow, P=216, %d walkers per GPU" % W,
             "walkers_per_gpu": W, "electrons": 16, "determinants": 24, "params": 216,
-            "l2": "flushed between timed steps (256 MiB write)" if flush else "not flushed"}
+            "l2": "flushed between timed steps (256 MiB write)" if flush else "not flushed",
+            "refresh": "Slater matrices refactorised every %d walker-steps; in between the evaluation takes the "
+                       "inverses the sweep carries (Sherman-Morrison in double)" % REFRESH}
 
 
 # --------------------------------------------------------------------------------------
@@ -80,25 +83,26 @@ def work_model(spec, info):
     basis_full = S * 6 + 14 * sum(ncomp)        # + gradient and Laplacian per component
     npair = N * (N - 1) // 2
     een_terms = 23
-    # ---------------- sweep (N moves + one LU refresh) ----------------
-    sw64 = (N * (basis_val + 2 * nnz_det)                   # orbital values at all electrons (refresh)
-            + U * 2 * n ** 3                                 # LU + inverse
-            + N * (basis_val + 2 * nnz_det / 2)              # proposed orbital row (own spin's orbitals)
-            + N * (U / 2) * 2 * n                            # ratios
-            + N * 0.5 * (U / 2) * 4 * n * n)                 # Sherman-Morrison (acceptance ~ 1/2)
+    # ---------------- sweep (N moves from the carried inverses, no factorisation) ----------------
+    acc = info.get("acceptance", 0.7)
+    sw_row = N * (basis_val + 2 * nnz_det / 2)             # proposed orbital row (own spin's orbitals)
+    sw_ratio = N * (U / 2) * 2 * n                          # ratios
+    sw_sm = N * acc * (U / 2) * 4 * n * n                   # Sherman-Morrison on accepted moves
+    sw64 = sw_ratio + sw_sm
     sw32 = N * ((N - 1) * (30 + Nn * een_terms * 2 * 4) + Nn * 30)   # Jastrow change, old and new
     # ---------------- evaluation with derivatives ----------------
     ev_basis = N * basis_full
     ev_contr_val_det = 2 * N * nnz_det
     ev_contr_rest = 2 * N * (4 * nnz_ev + (nnz_ev - nnz_det))
-    ev_lu = U * (2 * n ** 3 + 2 * n * n + 6 * n * n)
+    # LU + inverse on the refactorising steps (one in REFRESH), the trace tr(A^-1 L) on every step
+    ev_lu = U * (2 * n ** 3 + 6 * n * n) / REFRESH + U * 2 * n * n
     ev_jas = npair * (2 * 30) + N * Nn * 30 + 2 * npair * Nn * een_terms * 12
     ev_jderiv = npair * Nn * een_terms * 45 + (npair + N * Nn) * 5 * 10
     ev_kappa = U * 2 * 2 * n * n * len(ev_orbs) + info["n_kappa_entries"] * 2 * n
     ev_orb = ev_basis + ev_contr_val_det + ev_contr_rest
     # per kernel and form: algorithmic flops per walker on the pipe each part runs on
     return {
-        "sweep": {"fp64": {"f64": sw64 + sw32, "f32": 0.0}, "mixed": {"f64": sw64, "f32": sw32}},
+        "sweep": {"fp64": {"f64": sw64 + sw32 + sw_row, "f32": 0.0}, "mixed": {"f64": sw64, "f32": sw32 + sw_row}},
         "jastrow": {"fp64": {"f64": ev_jas, "f32": 0.0}, "mixed": {"f64": 0.0, "f32": ev_jas}},
         "orbitals": {"fp64": {"f64": ev_orb, "f32": 0.0}, "mixed": {"f64": 0.0, "f32": ev_orb}},
         "det": {"fp64": {"f64": ev_lu + ev_kappa, "f32": 0.0}, "mixed": {"f64": ev_lu, "f32": ev_kappa}},
@@ -264,17 +268,16 @@ def run_ours(args, ws, rank, local):
     step_counter = [0]
 
     def step(prec, ev=None):
+        # one sweep + the evaluation with derivatives in one call; the evaluation takes the
+        # inverses the sweep carried and refactorises every REFRESH steps
         k = step_counter[0]
         step_counter[0] += 1
         if ev is not None:
             ev[0].record(stream)
-        ctx.vmc_steps(0, prec, R, 1, spec.step, SEED, step0=k, walker_offset=woff, refresh=0, state=state,
-                      state_valid=True, nacc=nacc)
+        ctx.vmc_steps(0, prec, R, 1, spec.step, SEED, step0=k, walker_offset=woff, refresh=REFRESH, state=state,
+                      state_valid=True, nacc=nacc, logpsi=lp, sign=sg, eloc=el, O=Ods[prec], dEL=dEs[prec])
         if ev is not None:
             ev[1].record(stream)
-        ctx.eval_walkers(0, prec, R, lp, sg, el, None, Ods[prec], dEs[prec], state_out=state)
-        if ev is not None:
-            ev[2].record(stream)
 
     # equilibration (untimed), then one evaluation to initialise the walker state
     ctx.vmc_steps(0, vbqmc.MIXED, R, 30, spec.step, SEED, step0=10 ** 6, walker_offset=woff, nacc=nacc)
@@ -286,7 +289,7 @@ def run_ours(args, ws, rank, local):
         for _ in range(args.warmup):
             step(prec)
         torch.cuda.synchronize()
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
         nacc.zero_()
         barrier(ws)
         torch.cuda.synchronize()
@@ -306,12 +309,13 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
         ctx.set_kernel_timing(False)
-        launches = 1 + ctx.last_launch_count()
+        launches = ctx.last_launch_count()
         barrier(ws)
         clocks = sampler.stop() if sampler else None
-        sweep_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
-        eval_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
-        tot_ms = allmax(sweep_ms + eval_ms, ws)
+        step_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
+        eval_ms = sum(ktimes.values())
+        sweep_ms = step_ms - eval_ms
+        tot_ms = allmax(step_ms, ws)
         kernel_ms = {"sweep": sweep_ms / steps}
         kernel_ms.update({key: v / steps for key, v in ktimes.items()})
         results[name] = {"steps": steps, "ms": tot_ms, "sweep_ms": sweep_ms / steps, "eval_ms": eval_ms / steps,
@@ -339,11 +343,12 @@ def run_ours(args, ws, rank, local):
     forces = force_timing(ctx, vbqmc, spec, info, R, args.force_steps, mhz) if args.force_steps > 0 else None
     dmc = dmc_timing(ctx, vbqmc, R, el, args.dmc_steps) if args.dmc_steps > 0 else None
     batched = batched_timing(vbqmc, dev, args.steps) if args.batch_steps > 0 else None
+    dmc48 = dmc48_timing(vbqmc, dev, args.steps) if args.dmc48_steps > 0 else None
     lin = lin_method_timing(ctx, vbqmc, dev, args.steps, args.lin_samples) if not args.no_lin else None
     barrier(ws)
     if rank != 0:
         return
-    model = work_model(spec, info)
+    model = work_model(spec, dict(info, acceptance=results["mixed"]["acc"]))
     m = results["mixed"]
     value = ws * W * m["steps"] / (m["ms"] * 1e-3)
     f64 = results["fp64"]
@@ -388,6 +393,7 @@ def run_ours(args, ws, rank, local):
         "nuclear_derivs": forces,
         "dmc": dmc,
         "batched": batched,
+        "dmc48": dmc48,
         "gpu_launches": m["launches_per_step"] * m["steps"],
         "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
                    "reasons": clocks.get("reasons", [])},
@@ -477,6 +483,60 @@ def dmc_timing(ctx, vbqmc, R, el, steps, tau=0.005):
             "launches_per_step": (ctx.last_launch_count() - 3) / steps}
 
 
+def dmc48_timing(vbqmc, dev, steps):
+    """The 48-electron system (256 determinants through the reference-determinant tables),
+    65536 walkers, mixed form: CUDA events around one evaluation (E_L, grad ln|Psi|) with the
+    per-kernel times, and around two DMC steps (tau = 0.005, capacity 1.5x, E_T at the median
+    E_L) from the unequilibrated initial walkers, restarted from the same walkers for each
+    repetition; walker-steps/s counts the walkers each step moved."""
+    import numpy as np
+    import torch
+    from paper_2207_14715_gb300 import systems as S
+    spec = S.dmc48()
+    W, cap, tau = 65536, 98304, 0.005
+    ctx = vbqmc.create(dev.index or 0)
+    ctx.set_system(0, spec)
+    R0 = torch.tensor(S.initial_walkers(spec, W, SEED + 48), device=dev)
+    lp, sg, el = (torch.zeros(W, dtype=torch.float64, device=dev) for _ in range(3))
+    g = torch.zeros_like(R0)
+    for _ in range(3):
+        ctx.eval_walkers(0, vbqmc.MIXED, R0, lp, sg, el, g)
+    torch.cuda.synchronize()
+    e_med = float(el.median().item())
+    n = max(3, steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.set_kernel_timing(True)
+    kt = {k: 0.0 for k in ctx.EVAL_KERNELS}
+    ev_ms = 0.0
+    for _ in range(n):
+        e0.record()
+        ctx.eval_walkers(0, vbqmc.MIXED, R0, lp, sg, el, g)
+        e1.record()
+        torch.cuda.synchronize()
+        ev_ms += e0.elapsed_time(e1)
+        for k, v in ctx.kernel_times().items():
+            kt[k] += v
+    ctx.set_kernel_timing(False)
+    buf = torch.zeros((cap, spec.N, 3), dtype=torch.float64, device=dev)
+    dmc_ms, moved, pops = 0.0, 0, None
+    for r in range(n):
+        buf[:W] = R0
+        torch.cuda.synchronize()
+        e0.record()
+        W1, _, hist = ctx.dmc_steps(0, vbqmc.MIXED, buf, W, 2, tau, e_med, W, SEED, step0=(1 << 24) + 2 * r)
+        e1.record()
+        torch.cuda.synchronize()
+        dmc_ms += e0.elapsed_time(e1)
+        moved += W + int(hist["pop"][0]) if len(hist["pop"]) > 1 else W
+        pops = [int(x) for x in hist["pop"]]
+    ctx.close()
+    return {"electrons": spec.N, "determinants": 256, "unique_per_spin": 70, "walkers": W,
+            "eval_ms": ev_ms / n, "eval_walkers_per_s": W / (ev_ms / n * 1e-3),
+            "eval_kernel_ms": {k: round(v / n, 4) for k, v in kt.items()},
+            "dmc_walker_steps_per_s": moved / (dmc_ms * 1e-3), "dmc_ms_per_call_of_2_steps": dmc_ms / n,
+            "population": pops, "tau": tau, "start": "unequilibrated walkers, E_T = median E_L"}
+
+
 def batched_timing(vbqmc, dev, steps):
     """The batched workload (64 random molecules of 2-32 electrons, 256-4096 walkers each) as
     one batch in the mixed form: tuned launch shapes, then steps of one sweep + evaluation with
@@ -559,6 +619,7 @@ def main():
     ap.add_argument("--dmc-steps", type=int, default=5, help="timed DMC steps (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3, help="batched-workload timing (0: skip)")
     ap.add_argument("--force-steps", type=int, default=3, help="nucleus-derivative timing (0: skip)")
+    ap.add_argument("--dmc48-steps", type=int, default=3, help="48-electron DMC system timing (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -122,7 +122,8 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc);
 int vbqmc_inspect_system(const vbqmc_system_desc* desc, int* info, int* terms, int max_terms, double* een_B);
 
 /* Per-walker persistent state: the inverse of every unique Slater matrix, its ln|det| and
- * sign, as written by the evaluation and read by the next VMC sweep so that a sweep starts
+ * sign, the ratio D_k/Phi of every determinant term, ln|Phi| and its sign, as written by the
+ * evaluation (or carried by the sweeps) and read by the next VMC sweep so that a sweep starts
  * without a fresh LU.  *ndoubles receives the number of doubles per walker; a state buffer
  * for W walkers holds W * ndoubles doubles, walker-major.  The layout is private to the
  * library and valid only together with the positions it was computed at. */
@@ -180,17 +181,21 @@ int vbqmc_weighted_colsum(vbqmc_ctx* ctx, int W, int K, int jtype, const double*
  * u_acc < |Psi(R')/Psi(R)|^2.  Determinant ratios and Sherman-Morrison updates of the
  * inverses are double in both precision modes (the mixed mode forms the proposed orbital row
  * in float).  The inverses at the start come from 'state' when state_valid != 0 (written by
- * a previous evaluation at the current R), else from a fresh double-precision LU; within the
- * call they are refreshed by LU every 'refresh' sweeps (0: never).
+ * a previous evaluation or sweep at the current R), else from a fresh double-precision LU;
+ * within the call they are refreshed by LU every 'refresh' sweeps (0: never).  The sweeps carry
+ * the inverses, the determinant-term ratios and ln|Phi| through their moves and, when state is
+ * given, write them back after the last sweep.
  * Random numbers: Philox4x32-10 keyed by seed, counter (walker_offset + w, step0 + sweep,
  * electron, (system_tag << 8) | purpose) with purpose 0 -> (u_x, u_y) and 1 -> (u_z, u_acc),
  * each uniform (x >> 11) * 2^-53 of one 64-bit half of the output.
  *   R     [W][N][3] device, in/out
- *   state [W][ndoubles] device or NULL, in (if state_valid) and out (if an evaluation runs)
+ *   state [W][ndoubles] device or NULL, in (if state_valid) and out
  *   nacc  [W] device int or NULL, out: accepted moves (accumulated over the sweeps)
  * After the last sweep, if logpsi/sign/eloc/O/dEL are non-NULL, the walkers are evaluated as
- * by vbqmc_eval_walkers and the state is rewritten (one walker-step = one sweep + that
- * evaluation). */
+ * by vbqmc_eval_walkers (one walker-step = one sweep + that evaluation).  With a state and
+ * nsweeps > 0 the evaluation takes the carried inverses instead of factorising the Slater
+ * matrices, except when step0 + nsweeps is a multiple of refresh (refresh > 0): then it
+ * factorises afresh and rewrites the state (refresh = 1: always). */
 int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R, int nsweeps, double step,
                     uint64_t seed, uint32_t step0, uint32_t system_tag, uint32_t walker_offset, int refresh,
                     double* state, int state_valid, int* nacc, double* logpsi, double* sign, double* eloc,

@@ -250,7 +250,10 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.ev_chunk_off = (const int*)(B + o_evco);
   d.det_chunk = (const int*)(B + o_dc);
   d.det_chunk_off = (const int*)(B + o_dco);
-  d.state_doubles = h.U[0] * h.n[0] * h.n[0] + h.U[1] * h.n[1] * h.n[1] + 2 * (h.U[0] + h.U[1]);
+  // walker state: inverses, ln|det| and signs per unique determinant, r_k = D_k/Phi per term,
+  // ln|Phi| and its sign
+  d.state_doubles = h.U[0] * h.n[0] * h.n[0] + h.U[1] * h.n[1] * h.n[1] + 2 * (h.U[0] + h.U[1]) +
+                    (int)h.term_coef.size() + 2;
   d.sh_zeta_ds = (const float*)(B + o_zds);
   d.sh_norm_ds = (const float*)(B + o_nds);
   d.orb_coef_ds = (const float*)(B + o_cds);
@@ -467,9 +470,9 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
   DeviceGuard g(ctx->device);
   int launches = 0;
   if (nsweeps > 0) {
-    cudaError_t e = vbq::launch_sweep(precision, s.dev, s.lay_sweep[precision], W, R, nsweeps, refresh,
-                                      state_valid ? state : nullptr, step, seed, step0, system_tag, walker_offset,
-                                      nacc, (cudaStream_t)stream);
+    cudaError_t e = vbq::launch_sweep(precision, s.dev, s.lay_sweep[precision], W, R, nsweeps, refresh, state,
+                                      state_valid, step, seed, step0, system_tag, walker_offset, nacc,
+                                      (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
     ++launches;
   }
@@ -479,8 +482,12 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
     rc = ensure_eval_ws(ctx, s, precision, W, (cudaStream_t)stream);
     if (rc) return rc;
     int nl = 0;
+    // the evaluation takes the inverses the sweeps carried, except at global step counts that are
+    // multiples of 'refresh', where it factorises afresh and rewrites the state
+    const bool carried = state && nsweeps > 0 && !(refresh > 0 && (step0 + (uint32_t)nsweeps) % (uint32_t)refresh == 0);
     cudaError_t e = vbq::launch_eval(precision, s.dev, s.lay_eval[precision], W, R, logpsi, sign, eloc, nullptr, O,
-                                     dEL, state, ctx->eval_work, (cudaStream_t)stream, &nl, timing_events(ctx));
+                                     dEL, carried ? nullptr : state, ctx->eval_work, (cudaStream_t)stream, &nl,
+                                     timing_events(ctx), nullptr, carried ? state : nullptr);
     launches += nl;
     if (e != cudaSuccess) {
       ctx->last_launches = launches;

@@ -75,7 +75,7 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
                                          double* __restrict__ sgn_out, double* __restrict__ eloc,
                                          double* __restrict__ vg_ws, double* __restrict__ grad, Tb* __restrict__ Og,
                                          Tb* __restrict__ dELg, double* __restrict__ state_out,
-                                         double* __restrict__ aux) {
+                                         double* __restrict__ aux, const double* __restrict__ carry) {
   const int lane = threadIdx.x & 31;
   double* vg = reinterpret_cast<double*>(base + L.vg);
   Tb* G = reinterpret_cast<Tb*>(base + L.G);
@@ -103,13 +103,13 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
   __syncwarp();
   for (int e = 0; e < N; ++e) {
     const Tb* ob = OB + ((size_t)w * N + e) * 5 * nev;
-    const double* od = OD + ((size_t)w * N + e) * nevd;
+    const double* od = carry ? nullptr : OD + ((size_t)w * N + e) * nevd;
     const Tb G0 = G[3 * e], G1 = G[3 * e + 1], G2 = G[3 * e + 2];
     for (int q = lane; q < nev; q += 32) {
       const Tb v = ob[q], x = ob[nev + q], y = ob[2 * nev + q], z = ob[3 * nev + q], lp = ob[4 * nev + q];
       Lphi[e * nev + q] = lp + (Tb)2 * (G0 * x + G1 * y + G2 * z);
       if (q < nevd) {
-        PhiD[e * nevd + q] = od[q];
+        if (!carry) PhiD[e * nevd + q] = od[q];
         Gphi[(e * nevd + q) * 3] = x;
         Gphi[(e * nevd + q) * 3 + 1] = y;
         Gphi[(e * nevd + q) * 3 + 2] = z;
@@ -120,21 +120,57 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
   __syncwarp();
 
   // ---- C. Slater matrices: LU, inverses, ln|det|, t_u = tr(A^-1 L) ----
-  double* st = state_out ? state_out + (size_t)w * s.state_doubles : nullptr;
+  // walker state: [Binv spin 0][Binv spin 1][ln|det| (Utot)][sign (Utot)][r_k (nterm)][ln|Phi|][sign]
   const int nb0 = s.U[0] * s.n[0] * s.n[0], nb1 = s.U[1] * s.n[1] * s.n[1];
-  lu_det_all<Tb>(s, 0, lane, PhiD, nevd, Lphi, nev, s.det_ev[0], L.G0, Bt[0], reinterpret_cast<double*>(scr), ldet,
-                 dsg, tdet, st);
-  lu_det_all<Tb>(s, 1, lane, PhiD, nevd, Lphi, nev, s.det_ev[1], L.G1, Bt[1], reinterpret_cast<double*>(scr),
-                 ldet + U0, dsg + U0, tdet + U0, st ? st + nb0 : nullptr);
   const int Utot = U0 + s.U[1];
-  if (st)
-    // walker state: [Binv spin 0][Binv spin 1][ln|det| (U0+U1)][sign (U0+U1)]
-    for (int q = lane; q < Utot; q += 32) {
-      st[nb0 + nb1 + q] = ldet[q];
-      st[nb0 + nb1 + Utot + q] = dsg[q];
-    }
   double lnPhi, sgnPhi;
-  term_ratios(s, lane, ldet, dsg, rk, lnPhi, sgnPhi);
+  if (carry) {
+    // inverses, term ratios and ln|Phi| carried by the sweep to these positions: no factorisation
+    const double* cs = carry + (size_t)w * s.state_doubles;
+    double* part = reinterpret_cast<double*>(scr);
+    for (int sp = 0; sp < 2; ++sp) {
+      const int n = s.n[sp], U = s.U[sp], e0 = sp ? Nup : 0, uo = sp ? U0 : 0;
+      const double* Bc = cs + (sp ? nb0 : 0);
+      for (int q = lane; q < U * n * n; q += 32) Bt[sp][q] = (Tb)Bc[q];
+      // t_u = tr(B_u L_u): partial sums per (u, slot o), then per u
+      for (int i = lane; i < U * n; i += 32) {
+        const int u = i / n, o = i - u * n, col = __ldg(s.det_ev[sp] + u * n + o);
+        const double* B = Bc + u * n * n + o * n;
+        double t = 0.0;
+        for (int e = 0; e < n; ++e) t = fma(B[e], (double)Lphi[(e0 + e) * nev + col], t);
+        part[i] = t;
+      }
+      __syncwarp();
+      for (int u = lane; u < U; u += 32) {
+        double t = 0.0;
+        for (int o = 0; o < n; ++o) t += part[u * n + o];
+        tdet[uo + u] = t;
+      }
+      __syncwarp();
+    }
+    for (int k = lane; k < s.nterm; k += 32) rk[k] = cs[nb0 + nb1 + 2 * Utot + k];
+    lnPhi = cs[nb0 + nb1 + 2 * Utot + s.nterm];
+    sgnPhi = cs[nb0 + nb1 + 2 * Utot + s.nterm + 1];
+    __syncwarp();
+  } else {
+    double* st = state_out ? state_out + (size_t)w * s.state_doubles : nullptr;
+    lu_det_all<Tb>(s, 0, lane, PhiD, nevd, Lphi, nev, s.det_ev[0], L.G0, Bt[0], reinterpret_cast<double*>(scr), ldet,
+                   dsg, tdet, st);
+    lu_det_all<Tb>(s, 1, lane, PhiD, nevd, Lphi, nev, s.det_ev[1], L.G1, Bt[1], reinterpret_cast<double*>(scr),
+                   ldet + U0, dsg + U0, tdet + U0, st ? st + nb0 : nullptr);
+    term_ratios(s, lane, ldet, dsg, rk, lnPhi, sgnPhi);
+    if (st) {
+      for (int q = lane; q < Utot; q += 32) {
+        st[nb0 + nb1 + q] = ldet[q];
+        st[nb0 + nb1 + Utot + q] = dsg[q];
+      }
+      for (int k = lane; k < s.nterm; k += 32) st[nb0 + nb1 + 2 * Utot + k] = rk[k];
+      if (lane == 0) {
+        st[nb0 + nb1 + 2 * Utot + s.nterm] = lnPhi;
+        st[nb0 + nb1 + 2 * Utot + s.nterm + 1] = sgnPhi;
+      }
+    }
+  }
   // K[Phi] and the marginal weights W_u = sum_{k contains u} w_k, T_u = sum_{k contains u} w_k t_k
   double kphi = 0.0;
   for (int k = lane; k < s.nterm; k += 32) {
@@ -278,13 +314,13 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
                const double* __restrict__ JS, const Tb* __restrict__ OB, const double* __restrict__ OD,
                double* __restrict__ logpsi, double* __restrict__ sgn_out, double* __restrict__ eloc,
                double* __restrict__ vg_ws, double* __restrict__ grad, Tb* __restrict__ Og, Tb* __restrict__ dELg,
-               double* __restrict__ state_out, double* __restrict__ aux) {
+               double* __restrict__ state_out, double* __restrict__ aux, const double* __restrict__ carry) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int wl = threadIdx.x >> 5;
   const int w = blockIdx.x * L.wpb + wl;
   if (w >= W) return;
   det_body<Tb>(s, L, w, smem + wl * L.warp_bytes, JG, JL, JS, OB, OD, logpsi, sgn_out, eloc, vg_ws, grad, Og, dELg,
-               state_out, aux);
+               state_out, aux, carry);
 }
 
 template <class Tb>
@@ -303,7 +339,7 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
     det_body<Tb>(b.dev, b.lay.det, item.first + wl, smem + wl * b.lay.det.warp_bytes, static_cast<const Tb*>(b.JG),
                  static_cast<const Tb*>(b.JL), b.JS, static_cast<const Tb*>(b.OB), b.OD, b.logpsi, b.sign, b.eloc, b.VG,
                  nullptr, d ? static_cast<Tb*>(b.O) : nullptr, d ? static_cast<Tb*>(b.dEL) : nullptr, b.state,
-                 nullptr);
+                 nullptr, nullptr);
   }
 }
 
@@ -339,6 +375,7 @@ int make_det_layout(const SysDev& s, int tb, int max_smem, DetLayout& L) {
     const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
     scr = std::max(scr, ng * (16 * n * n + 4 * n) + 16);  // LU: A, inverse, pivots per group
     scr = std::max(scr, 2 * n * s.n_ev * tb);              // excitations: X, Y
+    scr = std::max(scr, 8 * s.U[sp] * n);                  // carried state: trace partials
   }
   L.scratch = take(scr);
   L.kacc = take(8 * 2 * std::max(s.n_kappa, 1));
@@ -378,7 +415,7 @@ namespace {
 template <class Tb>
 cudaError_t launch_eval_t(const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi, double* sign,
                           double* eloc, double* grad, Tb* O, Tb* dEL, double* state_out, void* ws, cudaStream_t st,
-                          int* nlaunch, cudaEvent_t* ev, double* aux) {
+                          int* nlaunch, cudaEvent_t* ev, double* aux, const double* carry) {
   const EvalWs b = carve_eval_ws(s, (int)sizeof(Tb), W, ws);
   *nlaunch = 0;
   auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], st) : cudaSuccess; };
@@ -388,7 +425,7 @@ cudaError_t launch_eval_t(const SysDev& s, const EvalLayout& L, int W, const dou
   if (e != cudaSuccess) return e;
   ++*nlaunch;
   if ((e = mark(1)) != cudaSuccess) return e;
-  e = launch_orbitals<Tb>(s, L.orb, W, R, static_cast<Tb*>(b.OB), b.OD, st);
+  e = launch_orbitals<Tb>(s, L.orb, W, R, static_cast<Tb*>(b.OB), carry ? nullptr : b.OD, st);
   if (e != cudaSuccess) return e;
   ++*nlaunch;
   if ((e = mark(2)) != cudaSuccess) return e;
@@ -402,7 +439,7 @@ cudaError_t launch_eval_t(const SysDev& s, const EvalLayout& L, int W, const dou
     if (e != cudaSuccess) return e;
     det_kernel<Tb><<<(W + D.wpb - 1) / D.wpb, 32 * D.wpb, smem, st>>>(
         s, D, W, static_cast<const Tb*>(b.JG), static_cast<const Tb*>(b.JL), b.JS, static_cast<const Tb*>(b.OB), b.OD,
-        logpsi, sign, eloc, b.VG, grad, O, dEL, state_out, aux);
+        logpsi, sign, eloc, b.VG, grad, O, dEL, carry ? nullptr : state_out, aux, carry);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
@@ -449,12 +486,12 @@ size_t eval_workspace_bytes(const SysDev& s, int tb, int W) {
 
 cudaError_t launch_eval(int precision, const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
                         double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out, void* ws,
-                        cudaStream_t st, int* nlaunch, cudaEvent_t* ev, double* aux) {
+                        cudaStream_t st, int* nlaunch, cudaEvent_t* ev, double* aux, const double* carry) {
   if (precision == VBQMC_MIXED)
     return launch_eval_t<float>(s, L, W, R, logpsi, sign, eloc, grad, static_cast<float*>(O),
-                                static_cast<float*>(dEL), state_out, ws, st, nlaunch, ev, aux);
+                                static_cast<float*>(dEL), state_out, ws, st, nlaunch, ev, aux, carry);
   return launch_eval_t<double>(s, L, W, R, logpsi, sign, eloc, grad, static_cast<double*>(O),
-                               static_cast<double*>(dEL), state_out, ws, st, nlaunch, ev, aux);
+                               static_cast<double*>(dEL), state_out, ws, st, nlaunch, ev, aux, carry);
 }
 
 }  // namespace vbq

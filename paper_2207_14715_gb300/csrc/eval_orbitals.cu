@@ -40,7 +40,7 @@ __device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L
     // shared-memory load per function and coefficient), Laplacians after them
     const dsf r3[3] = {ds_from_double(r[0]), ds_from_double(r[1]), ds_from_double(r[2])};
     basis_at_f<true>(s, lane, r3, bv, bv + 1, bv + 2, bv + 3, bv + 4 * M, 4);
-    basis_values_ds(s, lane, r3, ctab, bds);
+    if (OD) basis_values_ds(s, lane, r3, ctab, bds);
   }
   __syncwarp();
   for (int c = lane; c < s.n_ev_chunk; c += 32) {
@@ -64,7 +64,7 @@ __device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L
     Tb* pp = part + 5 * c;
     pp[0] = v; pp[1] = gx; pp[2] = gy; pp[3] = gz; pp[4] = lp;
   }
-  if (!kSameType<Tb, double>)
+  if (!kSameType<Tb, double> && OD)
     for (int c = lane; c < s.n_det_chunk; c += 32) {
       const int4 ch = __ldg(reinterpret_cast<const int4*>(s.det_chunk) + c);
       const float2* cb = reinterpret_cast<const float2*>(s.orb_coef_ds) + ch.w;
@@ -84,7 +84,7 @@ __device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L
       const Tb* pp = part + 5 * c;
       v += pp[0]; gx += pp[1]; gy += pp[2]; gz += pp[3]; lp += pp[4];
     }
-    if (q < nevd) {
+    if (q < nevd && OD) {  // OD null: the determinant-orbital values in double are not needed
       double vd = 0.0;
       if (kSameType<Tb, double>) {
         vd = (double)v;

@@ -20,7 +20,7 @@ namespace vbq {
 template <class Tb>
 __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L, int w, unsigned char* base,
                                            double* __restrict__ Rg, int nsweeps, int refresh,
-                                           const double* __restrict__ state_in, double step, uint64_t seed,
+                                           double* __restrict__ state, int state_valid, double step, uint64_t seed,
                                            uint32_t step0, uint32_t tag, uint32_t woff, int* __restrict__ nacc) {
   const int lane = threadIdx.x & 31;
   double* R = reinterpret_cast<double*>(base + L.R);
@@ -77,22 +77,26 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
 #pragma unroll
     for (int q = 0; q < 6; ++q) { Stab[(a * N + i) * 6 + q] = pw; pw *= sv; }
   }
-  if (state_in) {
-    const double* st = state_in + (size_t)w * s.state_doubles;
-    const int nb0 = s.U[0] * s.n[0] * s.n[0], nb1 = s.U[1] * s.n[1] * s.n[1], Ut = U0 + s.U[1];
+  // walker state: [Binv spin 0][Binv spin 1][ln|det| (Ut)][sign (Ut)][r_k = D_k/Phi (nterm)]
+  // [ln|Phi|][sign Phi]; the sweep starts from the inverses and the term ratios and carries
+  // both (and ln|Phi|) through its moves
+  const int nb0 = s.U[0] * s.n[0] * s.n[0], nb1 = s.U[1] * s.n[1] * s.n[1], Ut = U0 + s.U[1];
+  double lnPhi = 0.0, sgnPhi = 1.0;
+  const bool from_state = state && state_valid;
+  if (from_state) {
+    const double* st = state + (size_t)w * s.state_doubles;
     for (int q = lane; q < nb0; q += 32) Binv[0][q] = st[q];
     for (int q = lane; q < nb1; q += 32) Binv[1][q] = st[nb0 + q];
-    for (int q = lane; q < Ut; q += 32) {
-      ldet[q] = st[nb0 + nb1 + q];
-      dsg[q] = st[nb0 + nb1 + Ut + q];
-    }
+    for (int k = lane; k < s.nterm; k += 32) wk[k] = st[nb0 + nb1 + 2 * Ut + k];
+    lnPhi = st[nb0 + nb1 + 2 * Ut + s.nterm];
+    sgnPhi = st[nb0 + nb1 + 2 * Ut + s.nterm + 1];
   }
   __syncwarp();
   int accepted = 0;
   const uint32_t wid = woff + (uint32_t)w;
 
   for (int sw = 0; sw < nsweeps; ++sw) {
-    const bool do_refresh = (sw == 0) ? (state_in == nullptr) : (refresh > 0 && sw % refresh == 0);
+    const bool do_refresh = (sw == 0) ? !from_state : (refresh > 0 && sw % refresh == 0);
     if (do_refresh) {
       // double-precision orbital values of every electron, then LU of every unique determinant
       for (int e = 0; e < N; ++e) {
@@ -120,10 +124,8 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
       lu_all(s, 1, lane, PhiO, ldo, (const double*)nullptr, 0, s.det_loc[1], L.G1, Binv[1], scr, ldet + U0, dsg + U0,
              nullptr);
     }
-    if (do_refresh || sw == 0) {
-      double lnPhi, sgnPhi;
-      term_ratios(s, lane, ldet, dsg, wk, lnPhi, sgnPhi);
-      for (int k = lane; k < s.nterm; k += 32) wk[k] *= __ldg(s.term_coef + k);  // w_k = C_k D_k / Phi
+    if (do_refresh) {
+      term_ratios(s, lane, ldet, dsg, wk, lnPhi, sgnPhi);  // wk: r_k = D_k / Phi
       __syncwarp();
     }
     const uint32_t st = step0 + (uint32_t)sw;
@@ -196,7 +198,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
       }
       __syncwarp();
       double rphi = 0.0;
-      for (int k = lane; k < s.nterm; k += 32) rphi += wk[k] * rho[__ldg(s.term_det + 2 * k + sp)];
+      for (int k = lane; k < s.nterm; k += 32) rphi += __ldg(s.term_coef + k) * wk[k] * rho[__ldg(s.term_det + 2 * k + sp)];
       rphi = warp_sum(rphi);
       // Jastrow change of the terms that involve electron e (Sec. 2.1): distances from the
       // proposed position, then items e-n (a), e-e (j) and e-e-n (a, k), the last through the
@@ -293,6 +295,8 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           __syncwarp();
         }
         const double irphi = __shfl_sync(kFull, lane == 0 ? recip(rphi) : 0.0, 0);
+        lnPhi += log(fabs(rphi));
+        if (rphi < 0.0) sgnPhi = -sgnPhi;
         for (int k = lane; k < s.nterm; k += 32) wk[k] *= rho[__ldg(s.term_det + 2 * k + sp)] * irphi;
         if (lane < 3) {
           R[3 * e + lane] = lane == 0 ? rn[0] : (lane == 1 ? rn[1] : rn[2]);
@@ -311,18 +315,29 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   }
   for (int i = lane; i < 3 * N; i += 32) Rg[(size_t)w * 3 * N + i] = R[i];
   if (nacc && lane == 0) nacc[w] += accepted;
+  if (state) {  // the carried inverses, term ratios and ln|Phi| at the final positions
+    double* st = state + (size_t)w * s.state_doubles;
+    for (int q = lane; q < nb0; q += 32) st[q] = Binv[0][q];
+    for (int q = lane; q < nb1; q += 32) st[nb0 + q] = Binv[1][q];
+    for (int k = lane; k < s.nterm; k += 32) st[nb0 + nb1 + 2 * Ut + k] = wk[k];
+    if (lane == 0) {
+      st[nb0 + nb1 + 2 * Ut + s.nterm] = lnPhi;
+      st[nb0 + nb1 + 2 * Ut + s.nterm + 1] = sgnPhi;
+    }
+  }
 }
 
 template <class Tb>
 __global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const SweepLayout L, int W, double* __restrict__ Rg,
-                                                    int nsweeps, int refresh, const double* __restrict__ state_in,
+                                                    int nsweeps, int refresh, double* __restrict__ state, int state_valid,
                                                     double step, uint64_t seed, uint32_t step0, uint32_t tag,
                                                     uint32_t woff, int* __restrict__ nacc) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int wl = threadIdx.x >> 5;
   const int w = blockIdx.x * L.wpb + wl;
   if (w >= W) return;
-  sweep_body<Tb>(s, L, w, smem + wl * L.warp_bytes, Rg, nsweeps, refresh, state_in, step, seed, step0, tag, woff, nacc);
+  sweep_body<Tb>(s, L, w, smem + wl * L.warp_bytes, Rg, nsweeps, refresh, state, state_valid, step, seed, step0, tag,
+                 woff, nacc);
 }
 
 // All systems of a batch: blocks loop over work items; warp wl takes walker first + wl.
@@ -339,7 +354,7 @@ __global__ void __launch_bounds__(512, 1) sweep_batch_kernel(const BatchSys* __r
     if (wl >= item.count) continue;
     const BatchSys& b = sys[item.sys];
     sweep_body<Tb>(b.dev, b.sweep, item.first + wl, smem + wl * b.sweep.warp_bytes, b.R, call->nsweeps, call->refresh,
-                   call->state_valid ? b.state : nullptr, call->step, call->seed, call->step0, b.tag, 0u, b.nacc);
+                   b.state, call->state_valid, call->step, call->seed, call->step0, b.tag, 0u, b.nacc);
   }
 }
 
@@ -389,13 +404,13 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
 
 template <class Tb>
 static cudaError_t launch_sweep_t(const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps, int refresh,
-                                  const double* state_in, double step, uint64_t seed, uint32_t step0, uint32_t tag,
+                                  double* state, int state_valid, double step, uint64_t seed, uint32_t step0, uint32_t tag,
                                   uint32_t woff, int* nacc, cudaStream_t st) {
   const int smem = L.wpb * L.warp_bytes;
   cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int blocks = (W + L.wpb - 1) / L.wpb;
-  sweep_kernel<Tb><<<blocks, 32 * L.wpb, smem, st>>>(s, L, W, R, nsweeps, refresh, state_in, step, seed, step0, tag,
+  sweep_kernel<Tb><<<blocks, 32 * L.wpb, smem, st>>>(s, L, W, R, nsweeps, refresh, state, state_valid, step, seed, step0, tag,
                                                      woff, nacc);
   return cudaGetLastError();
 }
@@ -427,11 +442,13 @@ template cudaError_t launch_sweep_batch<double>(const BatchSys*, const BatchItem
                                                 cudaStream_t);
 
 cudaError_t launch_sweep(int precision, const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps,
-                         int refresh, const double* state_in, double step, uint64_t seed, uint32_t step0, uint32_t tag,
+                         int refresh, double* state, int state_valid, double step, uint64_t seed, uint32_t step0, uint32_t tag,
                          uint32_t woff, int* nacc, cudaStream_t st) {
   if (precision == VBQMC_MIXED)
-    return launch_sweep_t<float>(s, L, W, R, nsweeps, refresh, state_in, step, seed, step0, tag, woff, nacc, st);
-  return launch_sweep_t<double>(s, L, W, R, nsweeps, refresh, state_in, step, seed, step0, tag, woff, nacc, st);
+    return launch_sweep_t<float>(s, L, W, R, nsweeps, refresh, state, state_valid, step, seed, step0, tag, woff, nacc,
+                                 st);
+  return launch_sweep_t<double>(s, L, W, R, nsweeps, refresh, state, state_valid, step, seed, step0, tag, woff, nacc,
+                                st);
 }
 
 }  // namespace vbq

@@ -97,9 +97,13 @@ EvalWs carve_eval_ws(const SysDev& s, int bulk_bytes, int W, void* ws);
 // marginal weights W_u and T_u of every unique determinant (both spins, U = U_up + U_dn)
 // and K[Phi]/Phi (see eval_det.cu), which the nucleus-derivative kernel reads.
 constexpr int kEvalKernels = 4;
+// If carry is not null (a walker state written by a sweep at R), the determinant kernel takes the
+// inverses, term ratios and ln|Phi| from it instead of factorising, and the orbital kernel skips
+// the double-accuracy determinant-orbital values that only the factorisation reads.
 cudaError_t launch_eval(int precision, const SysDev& s, const EvalLayout& L, int W, const double* R, double* logpsi,
                         double* sign, double* eloc, double* grad, void* O, void* dEL, double* state_out, void* ws,
-                        cudaStream_t st, int* nlaunch, cudaEvent_t* ev = nullptr, double* aux = nullptr);
+                        cudaStream_t st, int* nlaunch, cudaEvent_t* ev = nullptr, double* aux = nullptr,
+                        const double* carry = nullptr);
 // Evaluation followed by the nucleus-derivative kernel: logpsi, sign, eloc as launch_eval,
 // dlp [W][Nn][3] = d ln|Psi|/dR_a, dEL [W][Nn][3] = dE_L/dR_a (may be null).  ws: evaluation
 // workspace; fws: force_workspace_bytes(s, W) bytes (walker state and determinant weights).
@@ -112,9 +116,11 @@ cudaError_t launch_nuclear_derivs(int precision, const SysDev& s, const EvalLayo
 int colsum_slices(int W);
 cudaError_t launch_weighted_colsum(int W, int K, int jtype, const double* ga, const void* Ja, const double* gb,
                                    const void* Jb, double* out, double* part, cudaStream_t st);
+// VMC sweeps; state (may be null): read when state_valid, written after the last sweep with the
+// carried inverses, term ratios and ln|Phi| (its ln|det| entries are left as they were).
 cudaError_t launch_sweep(int precision, const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps,
-                         int refresh, const double* state_in, double step, uint64_t seed, uint32_t step0, uint32_t tag,
-                         uint32_t woff, int* nacc, cudaStream_t st);
+                         int refresh, double* state, int state_valid, double step, uint64_t seed, uint32_t step0,
+                         uint32_t tag, uint32_t woff, int* nacc, cudaStream_t st);
 
 // Per-kernel launchers of the evaluation (eval_jastrow.cu, eval_orbitals.cu, eval_det.cu).
 template <class Tb>

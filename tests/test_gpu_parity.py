@@ -144,8 +144,9 @@ def test_vmc_fp64_trajectory_matches_oracle(vb, orc, name, W, nsw):
 @pytest.mark.parametrize("name,W,nsw", [("small_open_shell", 19, 3), ("ethylene_vb", 3, 1)])
 def test_vmc_fp64_from_saved_state_matches_oracle(vb, orc, name, W, nsw):
     """Sweeps that start from the walker state written by an evaluation (no LU refresh inside
-    the call) follow the oracle's trajectory move for move, and the evaluation after them
-    rewrites a state equal to a fresh one."""
+    the call) follow the oracle's trajectory move for move; the evaluation after them (from the
+    carried inverses) matches the oracle, and sweeps continued from the carried state move
+    exactly as sweeps continued from a freshly factorised state."""
     mod, ctx = vb
     spec = SYSTEMS[name][0]()
     ctx.set_system(0, spec)
@@ -166,7 +167,59 @@ def test_vmc_fp64_from_saved_state_matches_oracle(vb, orc, name, W, nsw):
     np.testing.assert_allclose(Rt.cpu().numpy(), Ro, rtol=0, atol=1e-12)
     ref = orc.evaluate(spec, Ro)
     assert rel_err(el.cpu().numpy(), ref["eloc"]).max() < 1e-10
-    np.testing.assert_allclose(state.cpu().numpy(), state2.cpu().numpy(), rtol=1e-12, atol=1e-12)
+    assert rel_err(lp.cpu().numpy(), ref["logpsi"]).max() < 1e-10
+    Ra, Rb = Rt.clone(), Rt.clone()
+    na, nb = torch.zeros_like(nacc), torch.zeros_like(nacc)
+    ctx.vmc_steps(0, 0, Ra, 2, spec.step, 99, step0=50, refresh=0, state=state, state_valid=True, nacc=na)
+    ctx.vmc_steps(0, 0, Rb, 2, spec.step, 99, step0=50, refresh=0, state=state2, state_valid=True, nacc=nb)
+    torch.cuda.synchronize()
+    assert torch.equal(na, nb)
+    np.testing.assert_allclose(Ra.cpu().numpy(), Rb.cpu().numpy(), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name,refresh", [("ethylene_vb", 0), ("small_open_shell", 4)])
+def test_carried_evaluation_matches_fresh(vb, orc, name, refresh, precision):
+    """Ten walker-steps (one sweep + evaluation with derivatives each) that carry the inverses,
+    term ratios and ln|Phi| through the sweeps instead of factorising (refresh 0: never;
+    refresh 4: every fourth step) give the evaluation a fresh factorisation gives at the same
+    positions (FP64 1e-10 in ln|Psi| and E_L, 1e-8 in derivatives), and the mixed form stays
+    within its bounds of the oracle."""
+    mod, ctx = vb
+    spec = SYSTEMS[name][0]()
+    ctx.set_system(0, spec)
+    W, P = 48, spec.n_params
+    Rt = torch.tensor(S.initial_walkers(spec, W, 77), device="cuda")
+    dt = mod.deriv_dtype(precision)
+    z = lambda: torch.zeros(W, dtype=torch.float64, device="cuda")
+    lp, sg, el = z(), z(), z()
+    O = torch.zeros((W, P), dtype=dt, device="cuda")
+    dE = torch.zeros_like(O)
+    state = torch.zeros((W, ctx.walker_state_size(0)), dtype=torch.float64, device="cuda")
+    ctx.eval_walkers(0, precision, Rt, z(), z(), z(), state_out=state)
+    for k in range(10):
+        ctx.vmc_steps(0, precision, Rt, 1, spec.step, 31, step0=k, refresh=refresh, state=state, state_valid=True,
+                      logpsi=lp, sign=sg, eloc=el, O=O, dEL=dE)
+    lp2, sg2, el2 = z(), z(), z()
+    O2, dE2 = torch.zeros_like(O), torch.zeros_like(O)
+    ctx.eval_walkers(0, precision, Rt, lp2, sg2, el2, O=O2, dEL=dE2)
+    torch.cuda.synchronize()
+    a = {k: v.double().cpu().numpy() for k, v in dict(lp=lp, sg=sg, el=el, O=O, dE=dE).items()}
+    b = {k: v.double().cpu().numpy() for k, v in dict(lp=lp2, sg=sg2, el=el2, O=O2, dE=dE2).items()}
+    np.testing.assert_array_equal(a["sg"], b["sg"])
+    if precision == 0:
+        assert rel_err(a["lp"], b["lp"]).max() < 1e-10
+        assert rel_err(a["el"], b["el"]).max() < 1e-10
+        for key in ("O", "dE"):
+            assert np.abs(a[key] - b[key]).max() <= 1e-8 * max(1.0, np.abs(b[key]).max()), key
+    else:
+        ref = orc.evaluate(spec, Rt.cpu().numpy(), derivs=True)
+        dl = np.abs(a["lp"] - ref["logpsi"]).max()
+        de = rel_err(a["el"], ref["eloc"]).max()
+        print("%s carried mixed: worst |dlnPsi| %.2e, worst rel dE_L %.2e" % (name, dl, de))
+        assert dl <= 1e-5 and de <= 1e-4
+        for key, rk in (("O", "O"), ("dE", "dEL")):
+            assert np.abs(a[key] - ref[rk]).max() <= 2e-3 * max(1.0, np.abs(ref[rk]).max()), key
 
 
 def test_vmc_mixed_statistics_match_oracle(vb, orc):
