@@ -343,7 +343,7 @@ def run_ours(args, ws, rank, local):
     forces = force_timing(ctx, vbqmc, spec, info, R, args.force_steps, mhz) if args.force_steps > 0 else None
     dmc = dmc_timing(ctx, vbqmc, R, el, args.dmc_steps) if args.dmc_steps > 0 else None
     batched = batched_timing(vbqmc, dev, args.steps) if args.batch_steps > 0 else None
-    dmc48 = dmc48_timing(vbqmc, dev, args.steps) if args.dmc48_steps > 0 else None
+    dmc48 = dmc48_timing(vbqmc, dev, args.steps, args.dmc48_walkers) if args.dmc48_steps > 0 else None
     lin = lin_method_timing(ctx, vbqmc, dev, args.steps, args.lin_samples) if not args.no_lin else None
     barrier(ws)
     if rank != 0:
@@ -483,9 +483,9 @@ def dmc_timing(ctx, vbqmc, R, el, steps, tau=0.005):
             "launches_per_step": (ctx.last_launch_count() - 3) / steps}
 
 
-def dmc48_timing(vbqmc, dev, steps):
+def dmc48_timing(vbqmc, dev, steps, W=65536):
     """The 48-electron system (256 determinants through the reference-determinant tables),
-    65536 walkers, mixed form: CUDA events around one evaluation (E_L, grad ln|Psi|) with the
+    W (default 65536) walkers, mixed form: CUDA events around one evaluation (E_L, grad ln|Psi|) with the
     per-kernel times, and around two DMC steps (tau = 0.005, capacity 1.5x, E_T at the median
     E_L) from the unequilibrated initial walkers, restarted from the same walkers for each
     repetition; walker-steps/s counts the walkers each step moved."""
@@ -493,7 +493,7 @@ def dmc48_timing(vbqmc, dev, steps):
     import torch
     from paper_2207_14715_gb300 import systems as S
     spec = S.dmc48()
-    W, cap, tau = 65536, 98304, 0.005
+    cap, tau = W * 3 // 2, 0.005
     ctx = vbqmc.create(dev.index or 0)
     ctx.set_system(0, spec)
     R0 = torch.tensor(S.initial_walkers(spec, W, SEED + 48), device=dev)
@@ -620,6 +620,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=3, help="batched-workload timing (0: skip)")
     ap.add_argument("--force-steps", type=int, default=3, help="nucleus-derivative timing (0: skip)")
     ap.add_argument("--dmc48-steps", type=int, default=3, help="48-electron DMC system timing (0: skip)")
+    ap.add_argument("--dmc48-walkers", type=int, default=65536, help="walkers of the 48-electron timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -82,6 +82,10 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   // both (and ln|Phi|) through its moves
   const int nb0 = s.U[0] * s.n[0] * s.n[0], nb1 = s.U[1] * s.n[1] * s.n[1], Ut = U0 + s.U[1];
   double lnPhi = 0.0, sgnPhi = 1.0;
+  // product of the accepted moves' |Phi'/Phi| since ln|Phi| was last set, as a mantissa in
+  // [1, 2) and a binary exponent (bit operations; one logarithm per sweep instead of one per move)
+  double pm = 1.0;
+  int pe = 0;
   const bool from_state = state && state_valid;
   if (from_state) {
     const double* st = state + (size_t)w * s.state_doubles;
@@ -126,6 +130,8 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
     }
     if (do_refresh) {
       term_ratios(s, lane, ldet, dsg, wk, lnPhi, sgnPhi);  // wk: r_k = D_k / Phi
+      pm = 1.0;
+      pe = 0;
       __syncwarp();
     }
     const uint32_t st = step0 + (uint32_t)sw;
@@ -295,7 +301,11 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           __syncwarp();
         }
         const double irphi = __shfl_sync(kFull, lane == 0 ? recip(rphi) : 0.0, 0);
-        lnPhi += log(fabs(rphi));
+        {
+          const long long b = __double_as_longlong(fabs(rphi) * pm);
+          pe += (int)((b >> 52) & 0x7ff) - 1023;
+          pm = __longlong_as_double((b & 0x800fffffffffffffLL) | (1023LL << 52));
+        }
         if (rphi < 0.0) sgnPhi = -sgnPhi;
         for (int k = lane; k < s.nterm; k += 32) wk[k] *= rho[__ldg(s.term_det + 2 * k + sp)] * irphi;
         if (lane < 3) {
@@ -315,6 +325,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   }
   for (int i = lane; i < 3 * N; i += 32) Rg[(size_t)w * 3 * N + i] = R[i];
   if (nacc && lane == 0) nacc[w] += accepted;
+  lnPhi += log(pm) + (double)pe * 0.69314718055994530942;  // ln 2
   if (state) {  // the carried inverses, term ratios and ln|Phi| at the final positions
     double* st = state + (size_t)w * s.state_doubles;
     for (int q = lane; q < nb0; q += 32) st[q] = Binv[0][q];
