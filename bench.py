@@ -35,8 +35,8 @@ SEED = 20220728 + 1
 WALKER_KERNEL_SOURCES = ["kernels.cu", "eval_jastrow.cu", "eval_orbitals.cu", "eval_det.cu", "walker_common.cuh",
                          "kernels.h", "wf_device.cuh", "dsfloat.cuh", "vbqmc_internal.h"]
 PROFILED_TRAFFIC = {
-    "sources_sha256": "87b9e2b0697075269a8df2cefeca14afe6457ac7316ebbdc4e9c369d01d50464",
-    "bytes_per_walker": {"det": 24100.2, "sweep": 8960.6, "orbitals": 10555.0},
+    "sources_sha256": "350e17fbb39705f76065655024429fc6266816f1a6398f0605ae3bd9cfbfd94a",
+    "bytes_per_walker": {"sweep": 10794.9, "det": 26215.0, "orbitals": 9022.7},
 }
 
 

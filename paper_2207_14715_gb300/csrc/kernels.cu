@@ -39,12 +39,14 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   double* scr = reinterpret_cast<double*>(base + L.scratch);
   Tb* rEE = reinterpret_cast<Tb*>(base + L.geo);       // [N][N] r_ij
   Tb* rEN = rEE + s.N * s.N;                            // [N][Nn] r_ia
-  Tb* Stab = rEN + s.N * s.Nn;                          // [Nn][N][6] Rbar(r_ia)^q
-  Tb* rnE = Stab + 6 * s.N * s.Nn;                      // [N] r from the proposed position
+  // row strides padded by one so that lanes on different nuclei (powers) read different banks
+  const int SA = 6 * s.N + 1, UP = s.N + 1;
+  Tb* Stab = rEN + s.N * s.Nn;                          // [Nn][SA]: [a][j][q] = Rbar(r_ja)^q at a*SA + 6j + q
+  Tb* rnE = Stab + SA * s.Nn;                           // [N] r from the proposed position
   Tb* rnN = rnE + s.N;                                  // [Nn]
   Tb* Snew = rnN + s.Nn;                                // [Nn][6]
-  Tb* Upo = Snew + 6 * s.Nn;                            // [5][N] Rbar(r_ej)^k, current position of e
-  Tb* Upn = Upo + 5 * s.N;                              // [5][N] Rbar(r_ej)^k, proposed position
+  Tb* Upo = Snew + 6 * s.Nn;                            // [5][UP] Rbar(r_ej)^k, current position of e
+  Tb* Upn = Upo + 5 * UP;                               // [5][UP] Rbar(r_ej)^k, proposed position
 
   const int N = s.N, Nn = s.Nn, Nup = s.Nup, U0 = s.U[0], ldo = L.nocc_max;
   const Tb kap = (Tb)s.kappa;
@@ -75,7 +77,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
     const Tb sv = (Tb)1 / ((Tb)1 + kap * r);
     Tb pw = (Tb)1;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) { Stab[(a * N + i) * 6 + q] = pw; pw *= sv; }
+    for (int q = 0; q < 6; ++q) { Stab[a * SA + i * 6 + q] = pw; pw *= sv; }
   }
   // walker state: [Binv spin 0][Binv spin 1][ln|det| (Ut)][sign (Ut)][r_k = D_k/Phi (nterm)]
   // [ln|Phi|][sign Phi]; the sweep starts from the inverses and the term ratios and carries
@@ -217,8 +219,8 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         Tb po = (Tb)1, pn = (Tb)1;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-          Upo[k * N + j] = po;
-          Upn[k * N + j] = pn;
+          Upo[k * UP + j] = po;
+          Upn[k * UP + j] = pn;
           po *= uo;
           pn *= un;
         }
@@ -257,8 +259,8 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           for (int q = 0; q < 6; ++q) Yo[q] = Yn[q] = (Tb)0;
           for (int j = 0; j < N; ++j) {
             if (j == e) continue;
-            const Tb po = Upo[k * N + j], pn = Upn[k * N + j];
-            const Tb* Sj = Stab + (a * N + j) * 6;
+            const Tb po = Upo[k * UP + j], pn = Upn[k * UP + j];
+            const Tb* Sj = Stab + a * SA + j * 6;
 #pragma unroll
             for (int q = 0; q < 6; ++q)
               if (q <= 5 - k) {
@@ -266,7 +268,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
                 Yn[q] += pn * Sj[q];
               }
           }
-          const Tb* So = Stab + (a * N + e) * 6;
+          const Tb* So = Stab + a * SA + e * 6;
           const Tb* Sn = Snew + a * 6;
           const Tb* c = cE + kNeen * __ldg(s.nuc_elem + a);
           een_for_each([&](auto tc) {
@@ -316,7 +318,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         for (int a = lane; a < Nn; a += 32) {
           rEN[e * Nn + a] = rnN[a];
 #pragma unroll
-          for (int q = 0; q < 6; ++q) Stab[(a * N + e) * 6 + q] = Snew[a * 6 + q];
+          for (int q = 0; q < 6; ++q) Stab[a * SA + e * 6 + q] = Snew[a * 6 + q];
         }
         ++accepted;
       }
@@ -404,7 +406,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   }
   L.cvec = take(std::max(cv, 8));
   L.scratch = take(std::max(scr, 16));
-  L.geo = take(tb * (N * N + N * s.Nn + 6 * N * s.Nn + N + s.Nn + 6 * s.Nn + 10 * N));
+  L.geo = take(tb * (N * N + N * s.Nn + (6 * N + 1) * s.Nn + N + s.Nn + 6 * s.Nn + 10 * (N + 1)));
   L.warp_bytes = off;
   int wpb = max_smem / off;
   if (wpb > 16) wpb = 16;
