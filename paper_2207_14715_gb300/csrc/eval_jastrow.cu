@@ -33,21 +33,25 @@ template <> struct LnSum<float> {
 
 // lanes -> (electron i, group g); group g takes nuclei a = g, g + S, ... and partners
 // j = g, g + S, ...
-template <class Tb>
+// WIDE: the whole block works on walker w (warp rank r takes groups r Sg .. r Sg + Sg - 1 of
+// nuclei and partners), the per-walker tables are shared, and the per-electron sums of the
+// warps meet in shared memory; otherwise one warp per walker.
+template <class Tb, bool WIDE = false>
 __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L, int w, unsigned char* base,
                                              const double* __restrict__ Rg, Tb* __restrict__ JG, Tb* __restrict__ JL,
                                              double* __restrict__ JS) {
   const int lane = threadIdx.x & 31;
+  const int rank = WIDE ? (int)(threadIdx.x >> 5) : 0, nw = WIDE ? (int)(blockDim.x >> 5) : 1;
   const int N = s.N, Nn = s.Nn, Nup = s.Nup;
   const GeoTables<Tb> g(reinterpret_cast<Tb*>(base + L.geo), N, Nn);
   const Tb kap = (Tb)s.kappa;
-  const Coords<Tb> C = load_coords<Tb>(Rg + (size_t)w * 3 * N, N, lane, base + L.R);
-  const double V_loc = build_geometry<Tb>(s, lane, C, g);
+  const Coords<Tb> C = load_coords<Tb, WIDE>(Rg + (size_t)w * 3 * N, N, 32 * rank + lane, base + L.R, 32 * nw);
+  const double V_loc = build_geometry<Tb, WIDE>(s, 32 * rank + lane, C, g, 32 * nw);
   LnSum<Tb> lnJ_loc;
   const Tb* cE = een_coefs<Tb>(s);
-  const int Pp = L.jas_P, Sg = L.jas_S;
+  const int Pp = L.jas_P, Sg = L.jas_S * nw;
   for (int b0 = 0; b0 < N; b0 += Pp) {
-    const int i = b0 + (lane & (Pp - 1)), gr = lane >> (__ffs(Pp) - 1);
+    const int i = b0 + (lane & (Pp - 1)), gr = rank * L.jas_S + (lane >> (__ffs(Pp) - 1));
     const bool act = i < N;
     Tb g0 = 0, g1 = 0, g2 = 0, lap = 0;
     LnSum<Tb> lnj;
@@ -130,17 +134,48 @@ __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L
       g2 += __shfl_xor_sync(kFull, g2, o);
       lap += __shfl_xor_sync(kFull, lap, o);
     }
-    if (act && gr == 0) {
+    if constexpr (WIDE) {
+      Tb* red = reinterpret_cast<Tb*>(base + L.wred);  // [nw][Pp][4]
+      if (act && lane < Pp) {
+        Tb* r = red + (rank * Pp + lane) * 4;
+        r[0] = g0; r[1] = g1; r[2] = g2; r[3] = lap;
+      }
+      __syncthreads();
+      if (rank == 0 && act && lane < Pp) {
+        Tb a[4] = {0, 0, 0, 0};
+        for (int q = 0; q < nw; ++q)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) a[c] += red[(q * Pp + lane) * 4 + c];
+        Tb* Gw = JG + (size_t)w * 3 * N;
+        Gw[3 * i] = a[0]; Gw[3 * i + 1] = a[1]; Gw[3 * i + 2] = a[2];
+        JL[(size_t)w * N + i] = a[3];
+      }
+      __syncthreads();
+    } else if (act && gr == 0) {
       Tb* Gw = JG + (size_t)w * 3 * N;
       Gw[3 * i] = g0; Gw[3 * i + 1] = g1; Gw[3 * i + 2] = g2;
       JL[(size_t)w * N + i] = lap;
     }
   }
-  const double lnJ = warp_sum(lnJ_loc.value());
-  const double V = warp_sum(V_loc) + s.vnn;
-  if (lane == 0) {
+  double lnJ = warp_sum(lnJ_loc.value());
+  double V = warp_sum(V_loc);
+  if constexpr (WIDE) {
+    double* dred = reinterpret_cast<double*>(base + L.wred2);  // [nw][2]
+    if (lane == 0) {
+      dred[2 * rank] = lnJ;
+      dred[2 * rank + 1] = V;
+    }
+    __syncthreads();
+    lnJ = 0.0;
+    V = 0.0;
+    for (int q = 0; q < nw; ++q) {
+      lnJ += dred[2 * q];
+      V += dred[2 * q + 1];
+    }
+  }
+  if (lane == 0 && rank == 0) {
     JS[2 * (size_t)w] = lnJ;
-    JS[2 * (size_t)w + 1] = V;
+    JS[2 * (size_t)w + 1] = V + s.vnn;
   }
 }
 
@@ -153,6 +188,15 @@ __global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks)
   const int w = blockIdx.x * L.wpb + wl;
   if (w >= W) return;
   jastrow_body<Tb>(s, L, w, smem + wl * L.warp_bytes, Rg, JG, JL, JS);
+}
+
+// one block (L.nw warps) per walker, for systems whose per-walker tables leave few warps per SM
+template <class Tb>
+__global__ void __launch_bounds__(256, JasBounds<Tb>::min_blocks)
+    jastrow_wide_kernel(const SysDev s, const JasLayout L, const double* __restrict__ Rg, Tb* __restrict__ JG,
+                        Tb* __restrict__ JL, double* __restrict__ JS) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  jastrow_body<Tb, true>(s, L, blockIdx.x, smem, Rg, JG, JL, JS);
 }
 
 template <class Tb>
@@ -395,6 +439,16 @@ int make_jas_layout(const SysDev& s, int tb, int max_smem, JasLayout& L) {
   int wpb = std::min(8, max_smem / off);
   if (wpb < 1) return VBQMC_ERR_CAPACITY;
   L.wpb = wpb;
+  // few walkers per block: the Jastrow kernel runs one walker per block of eight warps that
+  // share its tables (the derivative kernel keeps one warp per walker)
+  L.nw = 1;
+  if (wpb < 4) {
+    const int nw = 8;
+    L.wred = take(tb * 4 * L.jas_P * nw);
+    L.wred2 = take(8 * 2 * nw);
+    L.wide_bytes = off;
+    if (off <= max_smem) L.nw = nw;
+  }
   return VBQMC_OK;
 }
 
@@ -406,6 +460,12 @@ static cudaError_t set_smem(K kernel, int smem) {
 template <class Tb>
 cudaError_t launch_jastrow(const SysDev& s, const JasLayout& L, int W, const double* R, Tb* JG, Tb* JL, double* JS,
                            cudaStream_t st) {
+  if (L.nw > 1) {
+    cudaError_t e = set_smem(jastrow_wide_kernel<Tb>, L.wide_bytes);
+    if (e != cudaSuccess) return e;
+    jastrow_wide_kernel<Tb><<<W, 32 * L.nw, L.wide_bytes, st>>>(s, L, R, JG, JL, JS);
+    return cudaGetLastError();
+  }
   const int smem = L.wpb * L.warp_bytes;
   cudaError_t e = set_smem(jastrow_kernel<Tb>, smem);
   if (e != cudaSuccess) return e;

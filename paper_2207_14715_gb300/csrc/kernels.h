@@ -19,6 +19,9 @@ struct JasLayout {
   int wpb = 0, warp_bytes = 0;
   int R, vg, red, geo;
   int jas_P, jas_S;  // lanes: electron = lane % jas_P, group = lane / jas_P (jas_S groups)
+  // nw > 1: the Jastrow kernel runs one walker per block of nw warps (wide_bytes of shared
+  // memory: the walker's tables, then the warps' partial sums at wred and wred2)
+  int nw = 1, wide_bytes = 0, wred = 0, wred2 = 0;
 };
 
 struct OrbLayout {

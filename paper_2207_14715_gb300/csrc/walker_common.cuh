@@ -315,18 +315,21 @@ template <> struct Coords<float> {
 };
 // Loads a walker's coordinates from global memory (double [N][3]) into the form of Coords<Tb>
 // at dst (shared memory, 3N doubles or 3N float pairs).
-template <class Tb> __device__ __forceinline__ Coords<Tb> load_coords(const double* Rg, int N, int lane, void* dst) {
+// (t, stride): this thread's index and the number of threads that share the walker (one warp,
+// or the whole block when WIDE).
+template <class Tb, bool WIDE = false>
+__device__ __forceinline__ Coords<Tb> load_coords(const double* Rg, int N, int t, void* dst, int stride = 32) {
   Coords<Tb> c;
   if constexpr (kSameType<Tb, double>) {
     double* R = static_cast<double*>(dst);
-    for (int i = lane; i < 3 * N; i += 32) R[i] = Rg[i];
+    for (int i = t; i < 3 * N; i += stride) R[i] = Rg[i];
     c.R = R;
   } else {
     dsf* R = static_cast<dsf*>(dst);
-    for (int i = lane; i < 3 * N; i += 32) R[i] = ds_from_double(Rg[i]);
+    for (int i = t; i < 3 * N; i += stride) R[i] = ds_from_double(Rg[i]);
     c.R = R;
   }
-  __syncwarp();
+  if constexpr (WIDE) __syncthreads(); else __syncwarp();
   return c;
 }
 
@@ -340,11 +343,12 @@ __device__ __forceinline__ float rbar(const SysDev& s, float r) {
   return fmaf(-q * q, d.lo, q);
 }
 
-template <class Tb>
-__device__ __forceinline__ double build_geometry(const SysDev& s, int lane, const Coords<Tb>& C, const GeoTables<Tb>& g) {
+template <class Tb, bool WIDE = false>
+__device__ __forceinline__ double build_geometry(const SysDev& s, int lane, const Coords<Tb>& C, const GeoTables<Tb>& g,
+                                                 int stride = 32) {
   const int N = s.N, Nn = s.Nn;
   Tb V_loc = 0;
-  for (DivStep ij(lane, N); ij.hi < N; ij.next(N)) {
+  for (DivStep ij(lane, N); ij.hi < N; ij.next(N, stride)) {
     const int i = ij.hi, j = ij.lo, p = i * N + j;
     if (i == j) {
       g.rEE[p] = (Tb)0; g.uEE[p] = (Tb)1; g.iEE[p] = (Tb)0;
@@ -357,7 +361,7 @@ __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, cons
     g.eEE[3 * p] = dx * ir; g.eEE[3 * p + 1] = dy * ir; g.eEE[3 * p + 2] = dz * ir;
     if (i < j) V_loc += ir;
   }
-  for (DivStep ia(lane, Nn); ia.hi < N; ia.next(Nn)) {
+  for (DivStep ia(lane, Nn); ia.hi < N; ia.next(Nn, stride)) {
     const int i = ia.hi, a = ia.lo, p = i * Nn + a;
     const Tb dx = C.en(s, i, a, 0), dy = C.en(s, i, a, 1), dz = C.en(s, i, a, 2);
     const Tb r = vsqrt(dx * dx + dy * dy + dz * dz), ir = (Tb)1 / r;
@@ -370,8 +374,8 @@ __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, cons
 #pragma unroll
     for (int q = 0; q < 6; ++q) { St[q] = pw; pw *= sv; }
   }
-  __syncwarp();
-  for (int p = lane; p < Nn * 6; p += 32) {
+  if constexpr (WIDE) __syncthreads(); else __syncwarp();
+  for (int p = lane; p < Nn * 6; p += stride) {
     const int a = p / 6, q = p - 6 * a;
     // sum over all electrons of s^q, shared by every electron's k = 0 e-e-n terms (which take
     // their own s^q off it): float-float in the float form, so that its rounding does not repeat
@@ -388,7 +392,7 @@ __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, cons
       g.SsumLo[p] = t.lo;
     }
   }
-  __syncwarp();
+  if constexpr (WIDE) __syncthreads(); else __syncwarp();
   return (double)V_loc;
 }
 

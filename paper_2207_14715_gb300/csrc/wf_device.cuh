@@ -25,8 +25,8 @@ struct DivStep {
   __device__ __forceinline__ DivStep(int q0, int d) : hi(0), lo(q0) {
     while (lo >= d) { lo -= d; ++hi; }
   }
-  __device__ __forceinline__ void next(int d) {
-    lo += 32;
+  __device__ __forceinline__ void next(int d, int stride = 32) {
+    lo += stride;
     while (lo >= d) { lo -= d; ++hi; }
   }
 };
