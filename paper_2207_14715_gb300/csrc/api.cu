@@ -161,8 +161,7 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
                o_sI = bb.add(h.sterm_I), o_sk = bb.add(h.sterm_k), o_sd = bb.add(h.sterm_d),
                o_cparam = bb.add(h.cparam), o_jas_a = bb.add(h.jas_a), o_jas_b = bb.add(h.jas_b),
                o_een_c = bb.add(h.een_c), o_een_cf = bb.add(een_cf), o_een_B = bb.add(h.een_B),
-               o_ko0 = bb.add(h.kap_off[0]), o_ko1 = bb.add(h.kap_off[1]), o_ke0 = bb.add(h.kap_ent[0]),
-               o_ke1 = bb.add(h.kap_ent[1]), o_oc0 = bb.add(h.occ_chunk[0]), o_oc1 = bb.add(h.occ_chunk[1]),
+               o_kx = bb.add(h.kap_x), o_oc0 = bb.add(h.occ_chunk[0]), o_oc1 = bb.add(h.occ_chunk[1]),
                o_oco0 = bb.add(h.occ_chunk_off[0]), o_oco1 = bb.add(h.occ_chunk_off[1]), o_evc = bb.add(h.ev_chunk),
                o_evco = bb.add(h.ev_chunk_off), o_dc = bb.add(h.det_chunk), o_dco = bb.add(h.det_chunk_off),
                o_zds = bb.add(zeta_ds), o_nds = bb.add(norm_ds), o_cds = bb.add(coef_ds), o_nucds = bb.add(nuc_ds),
@@ -235,10 +234,7 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.een_c = (const double*)(B + o_een_c);
   d.een_cf = (const float*)(B + o_een_cf);
   d.een_B = (const double*)(B + o_een_B);
-  d.kap_off[0] = (const int*)(B + o_ko0);
-  d.kap_off[1] = (const int*)(B + o_ko1);
-  d.kap_ent[0] = (const int*)(B + o_ke0);
-  d.kap_ent[1] = (const int*)(B + o_ke1);
+  d.kap_x = (const int*)(B + o_kx);
   for (int sp = 0; sp < 2; ++sp) d.n_occ_chunk[sp] = (int)(h.occ_chunk[sp].size() / 4);
   d.n_ev_chunk = (int)(h.ev_chunk.size() / 4);
   d.n_det_chunk = (int)(h.det_chunk.size() / 4);

@@ -92,7 +92,6 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
   double* Tdet = reinterpret_cast<double*>(base + L.Tdet);
   double* rk = reinterpret_cast<double*>(base + L.rk);
   unsigned char* scr = base + L.scratch;
-  Tb* kacc = reinterpret_cast<Tb*>(base + L.kacc);
 
   const int N = s.N, Nup = s.Nup, U0 = s.U[0];
   const int nev = s.n_ev, nevd = s.n_ev_det;
@@ -101,21 +100,18 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
   for (int q = lane; q < N; q += 32) LJ[q] = JL[(size_t)w * N + q];
   const double lnJ = JS[2 * (size_t)w], V = JS[2 * (size_t)w + 1];
   __syncwarp();
-  for (int e = 0; e < N; ++e) {
+  for (DivStep eq(lane, nev); eq.hi < N; eq.next(nev)) {
+    const int e = eq.hi, q = eq.lo;
     const Tb* ob = OB + ((size_t)w * N + e) * 5 * nev;
-    const double* od = carry ? nullptr : OD + ((size_t)w * N + e) * nevd;
-    const Tb G0 = G[3 * e], G1 = G[3 * e + 1], G2 = G[3 * e + 2];
-    for (int q = lane; q < nev; q += 32) {
-      const Tb v = ob[q], x = ob[nev + q], y = ob[2 * nev + q], z = ob[3 * nev + q], lp = ob[4 * nev + q];
-      Lphi[e * nev + q] = lp + (Tb)2 * (G0 * x + G1 * y + G2 * z);
-      if (q < nevd) {
-        if (!carry) PhiD[e * nevd + q] = od[q];
-        Gphi[(e * nevd + q) * 3] = x;
-        Gphi[(e * nevd + q) * 3 + 1] = y;
-        Gphi[(e * nevd + q) * 3 + 2] = z;
-      }
-      Phi[e * nev + q] = v;
+    const Tb v = ob[q], x = ob[nev + q], y = ob[2 * nev + q], z = ob[3 * nev + q], lp = ob[4 * nev + q];
+    Lphi[e * nev + q] = lp + (Tb)2 * (G[3 * e] * x + G[3 * e + 1] * y + G[3 * e + 2] * z);
+    if (q < nevd) {
+      if (!carry) PhiD[e * nevd + q] = OD[((size_t)w * N + e) * nevd + q];
+      Gphi[(e * nevd + q) * 3] = x;
+      Gphi[(e * nevd + q) * 3 + 1] = y;
+      Gphi[(e * nevd + q) * 3 + 2] = z;
     }
+    Phi[e * nev + q] = v;
   }
   __syncwarp();
 
@@ -197,32 +193,88 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
   }
   if (aux && lane == 0) aux[(size_t)w * (2 * Utot + 1) + 2 * Utot] = kphi;
   __syncwarp();
-  // grad_i ln|Psi| = grad_i lnJ + sum_u W_u sum_o Binv_u[o][i] grad phi_o(r_i), in the bulk type
-  // (it feeds the Jastrow-parameter derivatives and the drift, not E_L)
+  // Rows over the evaluation columns c < n_ev_det, one entry per electron of the spin:
+  //   Gam_c = sum over determinants u holding column c (at slot o) of W_u B_u[o],
+  // and, when orbital-excitation derivatives are wanted (D3 below),
+  //   Aux_c = sum over the same u of (T_u B_u - W_u B_u L_u B_u)[o],
+  // L_u the dressed Laplacians of u's own columns.
+  const bool kap = Og && s.n_kappa > 0;
+  Tb* Gam[2];
+  Tb* Aux[2];
+  Gam[0] = reinterpret_cast<Tb*>(scr);
+  Gam[1] = Gam[0] + nevd * s.n[0];
+  Aux[0] = Gam[1] + nevd * s.n[1];
+  Aux[1] = Aux[0] + nevd * s.n[0];
+  Tb* M = Aux[1] + nevd * s.n[1];
   double kin_loc = 0.0;
-  for (int e = lane; e < N; e += 32) {
-    const int sp = e >= Nup ? 1 : 0, ie = e - (sp ? Nup : 0), n = s.n[sp], uo = sp ? U0 : 0;
-    const Tb* Bs = Bt[sp];
-    Tb gx = 0, gy = 0, gz = 0;
-    for (int u = 0; u < s.U[sp]; ++u) {
-      const Tb* B = Bs + u * n * n;
-      Tb ax = 0, ay = 0, az = 0;
-      for (int o = 0; o < n; ++o) {
-        const Tb b = B[o * n + ie];
-        const Tb* gp = Gphi + (e * nevd + __ldg(s.det_ev[sp] + u * n + o)) * 3;
-        ax += b * gp[0];
-        ay += b * gp[1];
-        az += b * gp[2];
+  if (kap) {
+    for (int q = lane; q < 2 * nevd * N; q += 32) Gam[0][q] = (Tb)0;
+    __syncwarp();
+    for (int sp = 0; sp < 2; ++sp) {
+      const int n = s.n[sp], e0 = sp ? Nup : 0, uo = sp ? U0 : 0;
+      if (n == 0) continue;
+      const int* ev_u = s.det_ev[sp];
+      for (int u = 0; u < s.U[sp]; ++u) {
+        const Tb* B = Bt[sp] + u * n * n;
+        // M = B_u L_u
+        for (DivStep oc(lane, n); oc.hi < n; oc.next(n)) {
+          const int col = __ldg(ev_u + u * n + oc.lo);
+          const Tb* Br = B + oc.hi * n;
+          Tb m = 0;
+          for (int e = 0; e < n; ++e) m += Br[e] * Lphi[(e0 + e) * nev + col];
+          M[oc.hi * n + oc.lo] = m;
+        }
+        __syncwarp();
+        const Tb Wu = (Tb)Wdet[uo + u], Tu = (Tb)Tdet[uo + u];
+        for (DivStep oc(lane, n); oc.hi < n; oc.next(n)) {
+          const int o = oc.hi, e = oc.lo, r = __ldg(ev_u + u * n + o) * n + e;
+          const Tb b = B[o * n + e];
+          Tb z = 0;
+          for (int o2 = 0; o2 < n; ++o2) z += M[o * n + o2] * B[o2 * n + e];
+          Gam[sp][r] += Wu * b;
+          Aux[sp][r] += Tu * b - Wu * z;
+        }
+        __syncwarp();
       }
-      const Tb Wu = (Tb)Wdet[uo + u];
-      gx += Wu * ax;
-      gy += Wu * ay;
-      gz += Wu * az;
     }
+    // grad_i ln|Psi| = grad_i lnJ + sum_c Gam_c[i] grad phi_c(r_i), in the bulk type
+    for (int q = lane; q < 3 * N; q += 32) {
+      const int e = q / 3, x = q - 3 * e;
+      const int sp = e >= Nup ? 1 : 0, n = s.n[sp];
+      const Tb* g = Gam[sp] + (e - (sp ? Nup : 0));
+      const Tb* gp = Gphi + e * nevd * 3 + x;
+      Tb acc = 0;
+      for (int c = 0; c < nevd; ++c) acc += g[c * n] * gp[3 * c];
+      vg[q] = (double)G[q] + (double)acc;
+    }
+  } else {
+    // grad_i ln|Psi| = grad_i lnJ + sum_u W_u sum_o B_u[o][i] grad phi_o(r_i), in the bulk type
+    for (int e = lane; e < N; e += 32) {
+      const int sp = e >= Nup ? 1 : 0, ie = e - (sp ? Nup : 0), n = s.n[sp], uo = sp ? U0 : 0;
+      const Tb* Bs = Bt[sp];
+      Tb gx = 0, gy = 0, gz = 0;
+      for (int u = 0; u < s.U[sp]; ++u) {
+        const Tb* B = Bs + u * n * n;
+        Tb ax = 0, ay = 0, az = 0;
+        for (int o = 0; o < n; ++o) {
+          const Tb b = B[o * n + ie];
+          const Tb* gp = Gphi + (e * nevd + __ldg(s.det_ev[sp] + u * n + o)) * 3;
+          ax += b * gp[0];
+          ay += b * gp[1];
+          az += b * gp[2];
+        }
+        const Tb Wu = (Tb)Wdet[uo + u];
+        gx += Wu * ax;
+        gy += Wu * ay;
+        gz += Wu * az;
+      }
+      vg[3 * e] = (double)G[3 * e] + (double)gx;
+      vg[3 * e + 1] = (double)G[3 * e + 1] + (double)gy;
+      vg[3 * e + 2] = (double)G[3 * e + 2] + (double)gz;
+    }
+  }
+  for (int e = lane; e < N; e += 32) {
     const double G0 = (double)G[3 * e], G1 = (double)G[3 * e + 1], G2 = (double)G[3 * e + 2];
-    vg[3 * e] = G0 + (double)gx;
-    vg[3 * e + 1] = G1 + (double)gy;
-    vg[3 * e + 2] = G2 + (double)gz;
     kin_loc += (double)LJ[e] + G0 * G0 + G1 * G1 + G2 * G2;
   }
   const double kin = warp_sum(kin_loc) + kphi;
@@ -258,52 +310,32 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
     Ow[q] = (Tb)(o);
     if (Ew) Ew[q] = (Tb)(-0.5 * (kk - o * kphi));
   }
-  // D3. orbital excitations kappa_kl (Sec. 2.2): for determinant u with l at slot o_l and
-  //   k unoccupied, x_u = (A^-1 Phi)[o_l][k] = d ln D_u, y_u = (A^-1 L)[o_l][k] -
-  //   sum_o' (A^-1 L)[o_l][occ o'] (A^-1 Phi)[o'][k] = d t_u; O = sum_u W_u x_u,
-  //   K[Phi_kappa] = sum_u (T_u x_u + W_u y_u), E_L,kappa = -1/2 (K[Phi_kappa] - O K[Phi]).
-  if (s.n_kappa > 0) {
-    const int nk = s.n_kappa;
-    for (int q = lane; q < 2 * nk; q += 32) kacc[q] = (Tb)0;
-    __syncwarp();
-    Tb* X = reinterpret_cast<Tb*>(scr);
-    for (int sp = 0; sp < 2; ++sp) {
-      const int n = s.n[sp], e0 = sp ? Nup : 0, uo = sp ? U0 : 0;
-      if (n == 0) continue;
-      Tb* Y = X + n * nev;
-      for (int u = 0; u < s.U[sp]; ++u) {
-        const int eb = __ldg(s.kap_off[sp] + u), ee = __ldg(s.kap_off[sp] + u + 1);
-        if (eb == ee) continue;
-        const Tb* B = Bt[sp] + u * n * n;
-        for (DivStep oc(lane, nev); oc.hi < n; oc.next(nev)) {
-          const int o = oc.hi, c = oc.lo, q = o * nev + c;
-          Tb x = 0, y = 0;
-          for (int e = 0; e < n; ++e) {
-            const Tb b = B[o * n + e];
-            x += b * Phi[(e0 + e) * nev + c];
-            y += b * Lphi[(e0 + e) * nev + c];
-          }
-          X[q] = x;
-          Y[q] = y;
+  // D3. orbital excitations kappa_kl (Sec. 2.2), phi_l -> phi_l + kappa phi_k.  For determinant u
+  //   holding l at slot o (and not k): x_u = (B_u Phi)[o][k] = d ln D_u and
+  //   y_u = (B_u L)[o][k] - (B_u L_u B_u Phi)[o][k] = d t_u.  Both vanish identically when u
+  //   also holds k (B_u Phi has the unit vector there), so the sums over u factor through the
+  //   rows Gam_l and Aux_l built above:
+  //   O = sum_spin Gam_l . Phi_k,  K[Phi_kappa] = sum_u (T_u x_u + W_u y_u)
+  //     = sum_spin (Aux_l . Phi_k + Gam_l . L_k),  E_L,kappa = -1/2 (K[Phi_kappa] - O K[Phi]).
+  if (kap) {
+    for (int j = lane; j < s.n_kappa; j += 32) {
+      const int4 kx = __ldg(reinterpret_cast<const int4*>(s.kap_x) + j);
+      const int kc = kx.z;
+      Tb o = 0, kk = 0;
+      for (int sp = 0; sp < 2; ++sp) {
+        const int l = sp ? kx.y : kx.x;
+        if (l < 0) continue;
+        const int n = s.n[sp], e0 = sp ? Nup : 0;
+        const Tb* g = Gam[sp] + l * n;
+        const Tb* a = Aux[sp] + l * n;
+        for (int e = 0; e < n; ++e) {
+          const Tb ph = Phi[(e0 + e) * nev + kc], lph = Lphi[(e0 + e) * nev + kc];
+          o += g[e] * ph;
+          kk += a[e] * ph + g[e] * lph;
         }
-        __syncwarp();
-        const Tb Wu = (Tb)Wdet[uo + u], Tu = (Tb)Tdet[uo + u];
-        for (int t = eb + lane; t < ee; t += 32) {
-          const int j = __ldg(s.kap_ent[sp] + 4 * t), ol = __ldg(s.kap_ent[sp] + 4 * t + 1),
-                    kc = __ldg(s.kap_ent[sp] + 4 * t + 2);
-          const Tb x = X[ol * nev + kc];
-          Tb y = Y[ol * nev + kc];
-          for (int o2 = 0; o2 < n; ++o2) y -= Y[ol * nev + __ldg(s.det_ev[sp] + u * n + o2)] * X[o2 * nev + kc];
-          kacc[j] += Wu * x;
-          kacc[nk + j] += Tu * x + Wu * y;
-        }
-        __syncwarp();
       }
-    }
-    for (int j = lane; j < nk; j += 32) {
-      const Tb o = kacc[j];
       Ow[s.p_off_kappa + j] = o;
-      if (Ew) Ew[s.p_off_kappa + j] = (Tb)-0.5 * (kacc[nk + j] - o * (Tb)kphi);
+      if (Ew) Ew[s.p_off_kappa + j] = (Tb)-0.5 * (kk - o * (Tb)kphi);
     }
   }
 }
@@ -374,11 +406,11 @@ int make_det_layout(const SysDev& s, int tb, int max_smem, DetLayout& L) {
   for (int sp = 0; sp < 2; ++sp) {
     const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
     scr = std::max(scr, ng * (16 * n * n + 4 * n) + 16);  // LU: A, inverse, pivots per group
-    scr = std::max(scr, 2 * n * s.n_ev * tb);              // excitations: X, Y
     scr = std::max(scr, 8 * s.U[sp] * n);                  // carried state: trace partials
   }
+  // Gam and Aux rows of both spins, one product B_u L_u
+  scr = std::max(scr, tb * (2 * std::max(s.n_ev_det, 1) * N + std::max(s.n[0] * s.n[0], s.n[1] * s.n[1])));
   L.scratch = take(scr);
-  L.kacc = take(8 * 2 * std::max(s.n_kappa, 1));
   L.warp_bytes = off;
   int wpb = max_smem / off;
   const int cap = (tb == 8 ? EvalBounds<double>::threads : EvalBounds<float>::threads) / 32;

@@ -389,6 +389,16 @@ int build_system(const vbqmc_system_desc* d, SysHost& s, std::string& err) {
       s.kap_off[sp].push_back((int)(s.kap_ent[sp].size() / 4));
     }
   }
+  s.kap_x.assign(4 * (size_t)s.n_kappa, -1);
+  for (int j = 0; j < s.n_kappa; ++j) {
+    s.kap_x[4 * j + 2] = ev_of[d->kappa_kl[2 * j]];
+    s.kap_x[4 * j + 3] = 0;
+  }
+  for (int sp = 0; sp < 2; ++sp)
+    for (size_t t = 0; t < s.kap_ent[sp].size() / 4; ++t) {
+      const int j = s.kap_ent[sp][4 * t];
+      s.kap_x[4 * j + sp] = ev_of[d->kappa_kl[2 * j + 1]];
+    }
   // reference-determinant tables: determinant u of a spin is the reference (u = 0) with the
   // slots S_u replaced by the orbitals Q_u (k_u <= kMaxExc each, ascending, paired in order),
   // up to the parity of the column permutation from that replaced column list to u's own

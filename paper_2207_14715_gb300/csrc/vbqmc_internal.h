@@ -70,6 +70,9 @@ struct SysHost {
   int n_kappa = 0;
   std::vector<int> kap_off[2];         // [U_s + 1]
   std::vector<int> kap_ent[2];         // [n_ent][4]: j, slot of l, eval index of k, 0
+  // per excitation j: evaluation index of l for spin 0 and 1 (-1 where no determinant of the
+  // spin holds l without k), evaluation index of k, 0
+  std::vector<int> kap_x;
   // balanced work chunks of the orbital contraction phi_q = sum_mu lambda_{q,mu} chi_mu:
   // [n_chunk][4] = (orbital slot q, first mu, one-past-last mu, coefficient base so that the
   // coefficient of mu is orb_coef[base + mu]); chunk_off[q] .. chunk_off[q+1] are q's chunks.
@@ -125,8 +128,7 @@ struct SysDev {
   const double* een_c;
   const float* een_cf;
   const double* een_B;
-  const int* kap_off[2];
-  const int* kap_ent[2];               // [n_ent][4]: j, slot of l, eval index of k, 0
+  const int* kap_x;                    // [n_kappa][4]: eval index of l (spin 0, spin 1; -1: none), of k, 0
   int n_occ_chunk[2], n_ev_chunk, n_det_chunk;
   const int* occ_chunk[2];
   const int* occ_chunk_off[2];
