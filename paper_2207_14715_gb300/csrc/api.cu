@@ -131,6 +131,7 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   const vbq::SysHost& h = ls.host;
   BlobBuilder bb;
   std::vector<float> coef_f(h.orb_coef.begin(), h.orb_coef.end());
+  std::vector<float> evq_f(h.evq_coef.begin(), h.evq_coef.end());
   std::vector<float> een_cf(h.een_c.begin(), h.een_c.end());
   auto split = [](const std::vector<double>& v) {
     std::vector<float> o(2 * v.size());
@@ -162,8 +163,9 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
                o_cparam = bb.add(h.cparam), o_jas_a = bb.add(h.jas_a), o_jas_b = bb.add(h.jas_b),
                o_een_c = bb.add(h.een_c), o_een_cf = bb.add(een_cf), o_een_B = bb.add(h.een_B),
                o_kx = bb.add(h.kap_x), o_oc0 = bb.add(h.occ_chunk[0]), o_oc1 = bb.add(h.occ_chunk[1]),
-               o_oco0 = bb.add(h.occ_chunk_off[0]), o_oco1 = bb.add(h.occ_chunk_off[1]), o_evc = bb.add(h.ev_chunk),
-               o_evco = bb.add(h.ev_chunk_off), o_dc = bb.add(h.det_chunk), o_dco = bb.add(h.det_chunk_off),
+               o_oco0 = bb.add(h.occ_chunk_off[0]), o_oco1 = bb.add(h.occ_chunk_off[1]), o_evc = bb.add(h.evq_chunk),
+               o_evco = bb.add(h.evq_chunk_off), o_evs = bb.add(h.evq_slot), o_evq = bb.add(h.evq_coef),
+               o_evqf = bb.add(evq_f), o_dc = bb.add(h.det_chunk), o_dco = bb.add(h.det_chunk_off),
                o_zds = bb.add(zeta_ds), o_nds = bb.add(norm_ds), o_cds = bb.add(coef_ds), o_nucds = bb.add(nuc_ds),
                o_zf = bb.add(zeta_f), o_nf = bb.add(norm_f), o_jaf = bb.add(jas_af), o_jbf = bb.add(jas_bf),
                o_ebf = bb.add(een_Bf), o_nzf = bb.add(nuc_zf), o_nsh = bb.add(h.nuc_sh),
@@ -236,14 +238,17 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.een_B = (const double*)(B + o_een_B);
   d.kap_x = (const int*)(B + o_kx);
   for (int sp = 0; sp < 2; ++sp) d.n_occ_chunk[sp] = (int)(h.occ_chunk[sp].size() / 4);
-  d.n_ev_chunk = (int)(h.ev_chunk.size() / 4);
+  d.n_evq_chunk = (int)(h.evq_chunk.size() / 4);
   d.n_det_chunk = (int)(h.det_chunk.size() / 4);
   d.occ_chunk[0] = (const int*)(B + o_oc0);
   d.occ_chunk[1] = (const int*)(B + o_oc1);
   d.occ_chunk_off[0] = (const int*)(B + o_oco0);
   d.occ_chunk_off[1] = (const int*)(B + o_oco1);
-  d.ev_chunk = (const int*)(B + o_evc);
-  d.ev_chunk_off = (const int*)(B + o_evco);
+  d.evq_chunk = (const int*)(B + o_evc);
+  d.evq_chunk_off = (const int*)(B + o_evco);
+  d.evq_slot = (const int*)(B + o_evs);
+  d.evq_coef = (const double*)(B + o_evq);
+  d.evq_coef_f = (const float*)(B + o_evqf);
   d.det_chunk = (const int*)(B + o_dc);
   d.det_chunk_off = (const int*)(B + o_dco);
   // walker state: inverses, ln|det| and signs per unique determinant, r_k = D_k/Phi per term,

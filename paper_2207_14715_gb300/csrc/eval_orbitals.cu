@@ -1,6 +1,6 @@
 // Orbitals at every electron (arXiv:2207.14715, Sec. 2.1: phi_p = sum_mu lambda_{p mu} chi_mu):
 // basis functions with gradients and Laplacians, then the contraction in balanced chunks of
-// the nonzero coefficients.  One warp per (walker, electron), so that many warps share each
+// the nonzero coefficients, four orbitals of equal coefficient range at a time.  One warp per (walker, electron), so that many warps share each
 // SM; results go to the evaluation workspace:
 //   OB [W][N][5][n_ev] bulk type: phi, d/dx, d/dy, d/dz, lap phi of the evaluated orbitals
 //   OD [W][N][n_det_ev] double: values of the orbitals that enter determinants; in the mixed
@@ -43,26 +43,41 @@ __device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L
     if (OD) basis_values_ds(s, lane, r3, ctab, bds);
   }
   __syncwarp();
-  for (int c = lane; c < s.n_ev_chunk; c += 32) {
-    const int4 ch = __ldg(reinterpret_cast<const int4*>(s.ev_chunk) + c);
-    const Tb* cb = cf + ch.w;
-    Tb v = 0, gx = 0, gy = 0, gz = 0, lp = 0;
-    if constexpr (kSameType<Tb, double>) {
-      for (int mu = ch.y; mu < ch.z; ++mu) {
-        const Tb cm = __ldg(cb + mu);
-        v += cm * bv[mu]; gx += cm * bx[mu]; gy += cm * by[mu]; gz += cm * bz[mu]; lp += cm * bl[mu];
+  // contraction by quads of orbitals sharing a coefficient range: one basis-function load
+  // feeds four orbitals; partials component-major, part[(5 t + k) nch + chunk]
+  const int nch = s.n_evq_chunk;
+  const Tb* cq = kSameType<Tb, double> ? reinterpret_cast<const Tb*>(s.evq_coef)
+                                       : reinterpret_cast<const Tb*>(s.evq_coef_f);
+  for (int c = lane; c < nch; c += 32) {
+    const int4 ch = __ldg(reinterpret_cast<const int4*>(s.evq_chunk) + c);
+    Tb a[4][5];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) a[t][k] = (Tb)0;
+    for (int mu = ch.y; mu < ch.z; ++mu) {
+      Tb cm[4], b[5];
+      if constexpr (kSameType<Tb, double>) {
+        const double2 c01 = __ldg(reinterpret_cast<const double2*>(cq + ch.w + 4 * mu));
+        const double2 c23 = __ldg(reinterpret_cast<const double2*>(cq + ch.w + 4 * mu) + 1);
+        cm[0] = c01.x; cm[1] = c01.y; cm[2] = c23.x; cm[3] = c23.y;
+        b[0] = bv[mu]; b[1] = bx[mu]; b[2] = by[mu]; b[3] = bz[mu]; b[4] = bl[mu];
+      } else {
+        const float4 c4 = __ldg(reinterpret_cast<const float4*>(cq + ch.w + 4 * mu));
+        const float4 b4 = reinterpret_cast<const float4*>(bv)[mu];
+        cm[0] = c4.x; cm[1] = c4.y; cm[2] = c4.z; cm[3] = c4.w;
+        b[0] = b4.x; b[1] = b4.y; b[2] = b4.z; b[3] = b4.w;
+        b[4] = reinterpret_cast<const float*>(bv)[4 * M + mu];
       }
-    } else {
-      const float4* b4 = reinterpret_cast<const float4*>(bv);
-      const float* blf = reinterpret_cast<const float*>(bv) + 4 * M;
-      for (int mu = ch.y; mu < ch.z; ++mu) {
-        const float cm = __ldg(cb + mu);
-        const float4 b = b4[mu];
-        v += cm * b.x; gx += cm * b.y; gy += cm * b.z; gz += cm * b.w; lp += cm * blf[mu];
-      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) a[t][k] += cm[t] * b[k];
     }
-    Tb* pp = part + 5 * c;
-    pp[0] = v; pp[1] = gx; pp[2] = gy; pp[3] = gz; pp[4] = lp;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) part[(5 * t + k) * nch + c] = a[t][k];
   }
   if (!kSameType<Tb, double> && OD)
     for (int c = lane; c < s.n_det_chunk; c += 32) {
@@ -78,11 +93,12 @@ __device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L
   __syncwarp();
   Tb* out = OB + (size_t)gw * 5 * nev;
   for (int q = lane; q < nev; q += 32) {
-    const int c0 = __ldg(s.ev_chunk_off + q), c1 = __ldg(s.ev_chunk_off + q + 1);
+    const int qs = __ldg(s.evq_slot + q), qd = qs >> 2;
+    const int c0 = __ldg(s.evq_chunk_off + qd), c1 = __ldg(s.evq_chunk_off + qd + 1);
+    const Tb* pp = part + 5 * (qs & 3) * nch;
     Tb v = 0, gx = 0, gy = 0, gz = 0, lp = 0;
     for (int c = c0; c < c1; ++c) {
-      const Tb* pp = part + 5 * c;
-      v += pp[0]; gx += pp[1]; gy += pp[2]; gz += pp[3]; lp += pp[4];
+      v += pp[c]; gx += pp[nch + c]; gy += pp[2 * nch + c]; gz += pp[3 * nch + c]; lp += pp[4 * nch + c];
     }
     if (q < nevd && OD) {  // OD null: the determinant-orbital values in double are not needed
       double vd = 0.0;
@@ -145,7 +161,7 @@ int make_orb_layout(const SysDev& s, int tb, int max_smem, OrbLayout& L) {
   L.bas = take(5 * M * tb);
   L.bds = take(tb == 4 ? 8 * M : 16);
   L.ctab = take(tb == 4 ? 8 * 4 * s.Nn : 16);
-  L.part = take(5 * tb * std::max(s.n_ev_chunk, 1));
+  L.part = take(20 * tb * std::max(s.n_evq_chunk, 1));
   L.partd = take(tb == 4 ? 8 * std::max(s.n_det_chunk, 1) : 16);
   L.warp_bytes = off;
   L.wpb = kOrbWarps;

@@ -189,6 +189,65 @@ static void make_chunks(const SysHost& s, const std::vector<int>& orbs, std::vec
   }
 }
 
+// Groups the evaluated orbitals into quads of equal coefficient range (in order of first
+// appearance) and splits each quad's range into chunks with the critical-path model of
+// make_chunks (a quad's step costs about twice a single orbital's).
+static void make_quads(SysHost& s) {
+  const std::vector<int>& orbs = s.ev_orb;
+  std::vector<std::vector<int>> quads;
+  std::vector<std::pair<int, int>> open_rng;
+  std::vector<int> open_q;
+  s.evq_slot.assign(orbs.size(), 0);
+  for (size_t q = 0; q < orbs.size(); ++q) {
+    const std::pair<int, int> rng{s.orb_lo[orbs[q]], s.orb_hi[orbs[q]]};
+    size_t g = 0;
+    while (g < open_rng.size() && open_rng[g] != rng) ++g;
+    if (g == open_rng.size()) {
+      open_rng.push_back(rng);
+      open_q.push_back(-1);
+    }
+    if (open_q[g] < 0 || quads[open_q[g]].size() == 4) {
+      open_q[g] = (int)quads.size();
+      quads.emplace_back();
+    }
+    const int qd = open_q[g];
+    s.evq_slot[q] = 4 * qd + (int)quads[qd].size();
+    quads[qd].push_back((int)q);
+  }
+  int maxlen = 1;
+  for (auto& v : quads) maxlen = std::max(maxlen, s.orb_hi[orbs[v[0]]] - s.orb_lo[orbs[v[0]]]);
+  int bestL = maxlen;
+  long bestcost = -1;
+  for (int L = std::min(4, maxlen); L <= maxlen; ++L) {
+    long nch = 0, maxc = 1;
+    for (auto& v : quads) {
+      const long c = std::max(1, (s.orb_hi[orbs[v[0]]] - s.orb_lo[orbs[v[0]]] + L - 1) / L);
+      nch += c;
+      maxc = std::max(maxc, c);
+    }
+    const long cost = ((nch + 31) / 32) * (2 * L + 8) + (((long)orbs.size() + 31) / 32) * maxc;
+    if (bestcost < 0 || cost < bestcost) { bestcost = cost; bestL = L; }
+  }
+  s.evq_chunk.clear();
+  s.evq_coef.clear();
+  s.evq_chunk_off.assign(1, 0);
+  for (size_t qd = 0; qd < quads.size(); ++qd) {
+    const int k0 = orbs[quads[qd][0]], lo = s.orb_lo[k0], hi = s.orb_hi[k0], len = hi - lo;
+    const int qoff = (int)s.evq_coef.size();
+    s.evq_coef.resize(qoff + 4 * (size_t)len, 0.0);
+    for (size_t t = 0; t < quads[qd].size(); ++t) {
+      const int k = orbs[quads[qd][t]];
+      for (int mu = lo; mu < hi; ++mu) s.evq_coef[qoff + 4 * (mu - lo) + t] = s.orb_coef[s.orb_off[k] + mu - lo];
+    }
+    const int nc = std::max(1, (len + bestL - 1) / bestL);
+    for (int c = 0; c < nc; ++c) {
+      const int b = lo + (int)((long)len * c / nc), e = lo + (int)((long)len * (c + 1) / nc);
+      s.evq_chunk.insert(s.evq_chunk.end(), {(int)qd, b, e, qoff - 4 * lo});
+    }
+    s.evq_chunk_off.push_back((int)(s.evq_chunk.size() / 4));
+  }
+}
+
 #define VBQ_REQUIRE(cond, msg)                 \
   do {                                         \
     if (!(cond)) {                             \
@@ -451,7 +510,7 @@ int build_system(const vbqmc_system_desc* d, SysHost& s, std::string& err) {
   }
   // contraction work chunks
   for (int sp = 0; sp < 2; ++sp) make_chunks(s, s.occ_list[sp], s.occ_chunk[sp], s.occ_chunk_off[sp]);
-  make_chunks(s, s.ev_orb, s.ev_chunk, s.ev_chunk_off);
+  make_quads(s);
   make_chunks(s, std::vector<int>(s.ev_orb.begin(), s.ev_orb.begin() + s.n_ev_det), s.det_chunk, s.det_chunk_off);
   // Jastrow
   s.kappa = d->kappa;

@@ -77,7 +77,13 @@ struct SysHost {
   // [n_chunk][4] = (orbital slot q, first mu, one-past-last mu, coefficient base so that the
   // coefficient of mu is orb_coef[base + mu]); chunk_off[q] .. chunk_off[q+1] are q's chunks.
   std::vector<int> occ_chunk[2], occ_chunk_off[2];   // per spin, over occ_list[spin]
-  std::vector<int> ev_chunk, ev_chunk_off;            // over all evaluated orbitals
+  // quads of evaluated orbitals with the same nonzero coefficient range, contracted together
+  // (one basis-function load feeds four orbitals): evq_coef[qoff + 4 (mu - lo) + t] is the
+  // coefficient of mu in orbital t of the quad (0 for the padding of a short quad);
+  // evq_chunk [n][4] = (quad, first mu, one-past-last mu, qoff - 4 lo), evq_chunk_off[quad]
+  // .. [quad + 1] are the quad's chunks; evq_slot[q] = 4 quad + t of evaluated orbital q.
+  std::vector<int> evq_chunk, evq_chunk_off, evq_slot;
+  std::vector<double> evq_coef;
   std::vector<int> det_chunk, det_chunk_off;          // over the first n_ev_det evaluated orbitals
 };
 
@@ -129,11 +135,14 @@ struct SysDev {
   const float* een_cf;
   const double* een_B;
   const int* kap_x;                    // [n_kappa][4]: eval index of l (spin 0, spin 1; -1: none), of k, 0
-  int n_occ_chunk[2], n_ev_chunk, n_det_chunk;
+  int n_occ_chunk[2], n_evq_chunk, n_det_chunk;
   const int* occ_chunk[2];
   const int* occ_chunk_off[2];
-  const int* ev_chunk;
-  const int* ev_chunk_off;
+  const int* evq_chunk;
+  const int* evq_chunk_off;
+  const int* evq_slot;
+  const double* evq_coef;
+  const float* evq_coef_f;
   const int* det_chunk;
   const int* det_chunk_off;
   int state_doubles;                   // persistent walker state: inverses, ln|det|, signs
