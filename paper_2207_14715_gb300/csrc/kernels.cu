@@ -35,6 +35,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   Tb* part = reinterpret_cast<Tb*>(base + L.part);
   double* partd = reinterpret_cast<double*>(base + L.part);
   double* rho = reinterpret_cast<double*>(base + L.rho);
+  double* rinv = reinterpret_cast<double*>(base + L.rinv);
   double* cvec = reinterpret_cast<double*>(base + L.cvec);
   double* scr = reinterpret_cast<double*>(base + L.scratch);
   Tb* rEE = reinterpret_cast<Tb*>(base + L.geo);       // [N][N] r_ij
@@ -137,32 +138,34 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
       __syncwarp();
     }
     const uint32_t st = step0 + (uint32_t)sw;
-    // the sweep's random numbers, one electron per lane: displacement step (2u - 1) per
-    // coordinate and the acceptance uniform
+    // the sweep's random numbers, one electron per lane: the proposed position R_e + step
+    // (2u - 1) per coordinate (electron e has not moved yet in this sweep when its turn comes)
+    // and the acceptance uniform; in the mixed form also the float-float copy of the proposal
     double* rtab = reinterpret_cast<double*>(base + L.rtab);
+    dsf* rtds = reinterpret_cast<dsf*>(base + L.rtds);
     for (int e = lane; e < N; e += 32) {
-      double u0, u1, u2, ua;
-      uniforms2(seed, wid, st, (uint32_t)e, tag, 0, u0, u1);
-      uniforms2(seed, wid, st, (uint32_t)e, tag, 1, u2, ua);
-      rtab[4 * e] = __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u0), 1.0));
-      rtab[4 * e + 1] = __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u1), 1.0));
-      rtab[4 * e + 2] = __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u2), 1.0));
-      rtab[4 * e + 3] = ua;
+      double u[4];
+      uniforms2(seed, wid, st, (uint32_t)e, tag, 0, u[0], u[1]);
+      uniforms2(seed, wid, st, (uint32_t)e, tag, 1, u[2], u[3]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double x = __dadd_rn(R[3 * e + d], __dmul_rn(step, __dsub_rn(__dmul_rn(2.0, u[d]), 1.0)));
+        rtab[4 * e + d] = x;
+        if constexpr (!kSameType<Tb, double>) rtds[3 * e + d] = ds_from_double(x);
+      }
+      rtab[4 * e + 3] = u[3];
     }
     __syncwarp();
     for (int e = 0; e < N; ++e) {
       const int sp = e >= Nup ? 1 : 0, ie = e - (sp ? Nup : 0), n = s.n[sp], G = sp ? L.G1 : L.G0;
       const double uacc = rtab[4 * e + 3];
-      double rn[3];
-      rn[0] = __dadd_rn(R[3 * e], rtab[4 * e]);
-      rn[1] = __dadd_rn(R[3 * e + 1], rtab[4 * e + 1]);
-      rn[2] = __dadd_rn(R[3 * e + 2], rtab[4 * e + 2]);
+      const double rn[3] = {rtab[4 * e], rtab[4 * e + 1], rtab[4 * e + 2]};
       // the proposed position as the bulk-type arithmetic reads it
       dsf rnd[3];
       if constexpr (!kSameType<Tb, double>) {
-        rnd[0] = ds_from_double(rn[0]);
-        rnd[1] = ds_from_double(rn[1]);
-        rnd[2] = ds_from_double(rn[2]);
+        rnd[0] = rtds[3 * e];
+        rnd[1] = rtds[3 * e + 1];
+        rnd[2] = rtds[3 * e + 2];
       }
       auto dnew_e = [&](int j, int d) -> Tb {  // proposed position minus electron j
         if constexpr (kSameType<Tb, double>) return (Tb)(rn[d] - R[3 * j + d]);
@@ -282,6 +285,9 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
       const Tb dJ = warp_sum(dj);
       const double prob = rphi * rphi * (double)vexp((Tb)2 * dJ);
       if (uacc < prob) {
+        // the reciprocals 1/rho_u and 1/(Phi'/Phi), one per lane
+        for (int q = lane; q <= U; q += 32) rinv[q] = recip(q < U ? rho[q] : rphi);
+        __syncwarp();
         // Sherman-Morrison: Binv <- Binv - Binv[:, ie] (v^T Binv - e_ie^T) / rho
         for (int ub = 0; ub < U; ub += ng) {
           const int u = ub + g;
@@ -289,9 +295,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           double* B = Binv[sp] + (act ? u : 0) * n * n;
           double* cv = cvec + g * n;
           if (act && gl < n) cv[gl] = B[gl * n + ie];
-          // 1/rho_u once per determinant (lane 0 of the group), broadcast in the group
-          double irho = (act && gl == 0) ? recip(rho[u]) : 0.0;
-          irho = __shfl_sync(kFull, irho, lane & ~(G - 1));
+          const double irho = act ? rinv[u] : 0.0;
           __syncwarp();
           if (act && gl < n) {
             const int j = gl;
@@ -302,7 +306,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           }
           __syncwarp();
         }
-        const double irphi = __shfl_sync(kFull, lane == 0 ? recip(rphi) : 0.0, 0);
+        const double irphi = rinv[U];
         {
           const long long b = __double_as_longlong(fabs(rphi) * pm);
           pe += (int)((b >> 52) & 0x7ff) - 1023;
@@ -388,6 +392,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.R = take(8 * 3 * N);
   L.Rds = take(tb == 4 ? 8 * 3 * N : 16);
   L.rtab = take(8 * 4 * N);
+  L.rtds = take(tb == 4 ? 8 * 3 * N : 16);
   L.Binv0 = take(8 * s.U[0] * s.n[0] * s.n[0]);
   L.Binv1 = take(8 * s.U[1] * s.n[1] * s.n[1]);
   L.ldet = take(8 * Ut);
@@ -398,6 +403,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.vrow = take(8 * L.nocc_max);
   L.part = take(8 * std::max(std::max(s.n_occ_chunk[0], s.n_occ_chunk[1]), 1));
   L.rho = take(8 * std::max(s.U[0], s.U[1]));
+  L.rinv = take(8 * (std::max(s.U[0], s.U[1]) + 1));
   int cv = 0, scr = 0;
   for (int sp = 0; sp < 2; ++sp) {
     const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
