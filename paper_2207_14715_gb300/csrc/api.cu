@@ -159,7 +159,8 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
                o_ev_orb = bb.add(h.ev_orb), o_occ0 = bb.add(h.occ_list[0]), o_occ1 = bb.add(h.occ_list[1]),
                o_dl0 = bb.add(h.det_loc[0]), o_dl1 = bb.add(h.det_loc[1]), o_de0 = bb.add(h.det_ev[0]),
                o_de1 = bb.add(h.det_ev[1]), o_term_det = bb.add(h.term_det), o_term_coef = bb.add(h.term_coef),
-               o_sI = bb.add(h.sterm_I), o_sk = bb.add(h.sterm_k), o_sd = bb.add(h.sterm_d),
+               o_sI = bb.add(h.sterm_I), o_sk = bb.add(h.sterm_k), o_sd = bb.add(h.sterm_d), o_dto = bb.add(h.det_term_off), o_dt = bb.add(h.det_term),
+               o_cpo = bb.add(h.cpar_off), o_cps = bb.add(h.cpar_st),
                o_cparam = bb.add(h.cparam), o_jas_a = bb.add(h.jas_a), o_jas_b = bb.add(h.jas_b),
                o_een_c = bb.add(h.een_c), o_een_cf = bb.add(een_cf), o_een_B = bb.add(h.een_B),
                o_kx = bb.add(h.kap_x), o_oc0 = bb.add(h.occ_chunk[0]), o_oc1 = bb.add(h.occ_chunk[1]),
@@ -230,6 +231,10 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.sterm_I = (const int*)(B + o_sI);
   d.sterm_k = (const int*)(B + o_sk);
   d.sterm_d = (const double*)(B + o_sd);
+  d.det_term_off = (const int*)(B + o_dto);
+  d.det_term = (const int*)(B + o_dt);
+  d.cpar_off = (const int*)(B + o_cpo);
+  d.cpar_st = (const int*)(B + o_cps);
   d.cparam = (const int*)(B + o_cparam);
   d.jas_a = (const double*)(B + o_jas_a);
   d.jas_b = (const double*)(B + o_jas_b);
@@ -239,6 +244,7 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.kap_x = (const int*)(B + o_kx);
   for (int sp = 0; sp < 2; ++sp) d.n_occ_chunk[sp] = (int)(h.occ_chunk[sp].size() / 4);
   d.n_evq_chunk = (int)(h.evq_chunk.size() / 4);
+  d.evq_width = h.evq_width;
   d.n_det_chunk = (int)(h.det_chunk.size() / 4);
   d.occ_chunk[0] = (const int*)(B + o_oc0);
   d.occ_chunk[1] = (const int*)(B + o_oc1);

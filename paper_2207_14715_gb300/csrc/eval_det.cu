@@ -175,11 +175,10 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
   }
   kphi = warp_sum(kphi);
   for (int ud = lane; ud < Utot; ud += 32) {
-    const int sp = ud >= U0 ? 1 : 0, u = ud - (sp ? U0 : 0);
     double Wv = 0.0, Tv = 0.0;
-    for (int k = 0; k < s.nterm; ++k) {
+    for (int t = __ldg(s.det_term_off + ud); t < __ldg(s.det_term_off + ud + 1); ++t) {
+      const int k = __ldg(s.det_term + t);
       const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
-      if ((sp ? b : a) != u) continue;
       const double wk = __ldg(s.term_coef + k) * rk[k];
       Wv += wk;
       Tv += wk * (tdet[a] + tdet[U0 + b]);
@@ -297,11 +296,9 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
   Tb* Ew = dELg ? dELg + (size_t)w * P : nullptr;
   // D1. structure coefficients: O_I = Phi_I/Phi, E_L,I = -1/2 (K[Phi_I] - O_I K[Phi])
   for (int q = lane; q < s.n_cparam; q += 32) {
-    const int I = __ldg(s.cparam + q);
     double o = 0.0, kk = 0.0;
-    for (int t = 0; t < s.nsterm; ++t) {
-      if (__ldg(s.sterm_I + t) != I) continue;
-      const int k = __ldg(s.sterm_k + t);
+    for (int ts = __ldg(s.cpar_off + q); ts < __ldg(s.cpar_off + q + 1); ++ts) {
+      const int t = __ldg(s.cpar_st + ts), k = __ldg(s.sterm_k + t);
       const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
       const double r = __ldg(s.sterm_d + t) * rk[k];
       o += r;

@@ -222,11 +222,9 @@ __device__ __forceinline__ void dettab_body(const SysDev& s, const DetTabLayout&
   }
   kphi = warp_sum(kphi);
   for (int ud = lane; ud < Utot; ud += 32) {
-    const int sp = ud >= U0 ? 1 : 0, u = ud - (sp ? U0 : 0);
     double Wv = 0.0;
-    for (int k = 0; k < s.nterm; ++k) {
-      const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
-      if ((sp ? b : a) != u) continue;
+    for (int t = __ldg(s.det_term_off + ud); t < __ldg(s.det_term_off + ud + 1); ++t) {
+      const int k = __ldg(s.det_term + t);
       Wv += __ldg(s.term_coef + k) * rk[k];
     }
     Wdet[ud] = Wv;
@@ -317,11 +315,9 @@ __device__ __forceinline__ void dettab_body(const SysDev& s, const DetTabLayout&
   Tb* Ow = Og + (size_t)w * P;
   Tb* Ew = dELg ? dELg + (size_t)w * P : nullptr;
   for (int q = lane; q < s.n_cparam; q += 32) {
-    const int I = __ldg(s.cparam + q);
     double o = 0.0, kk = 0.0;
-    for (int t = 0; t < s.nsterm; ++t) {
-      if (__ldg(s.sterm_I + t) != I) continue;
-      const int k = __ldg(s.sterm_k + t);
+    for (int ts = __ldg(s.cpar_off + q); ts < __ldg(s.cpar_off + q + 1); ++ts) {
+      const int t = __ldg(s.cpar_st + ts), k = __ldg(s.sterm_k + t);
       const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
       const double r = __ldg(s.sterm_d + t) * rk[k];
       o += r;

@@ -15,6 +15,51 @@ namespace {
 
 constexpr int kOrbWarps = 8;
 
+// Chunks c = lane, lane + 32, ... of the contraction with groups of WD orbitals (coefficients
+// interleaved, stride WD): partial sums of phi, grad phi and lap phi over the chunk's basis
+// functions into part[(5 t + k) nch + c].  Basis layout as written by orbital_body.
+template <class Tb, int WD>
+__device__ __forceinline__ void contract_groups(const SysDev& s, int lane, int nch, const Tb* __restrict__ cq,
+                                                const Tb* bv, Tb* part) {
+  const int M = s.M;
+  for (int c = lane; c < nch; c += 32) {
+    const int4 ch = __ldg(reinterpret_cast<const int4*>(s.evq_chunk) + c);
+    Tb a[WD][5];
+#pragma unroll
+    for (int t = 0; t < WD; ++t)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) a[t][k] = (Tb)0;
+    for (int mu = ch.y; mu < ch.z; ++mu) {
+      Tb cm[WD], b[5];
+      if constexpr (WD == 4 && kSameType<Tb, double>) {
+        const double2 c01 = __ldg(reinterpret_cast<const double2*>(cq + ch.w + 4 * mu));
+        const double2 c23 = __ldg(reinterpret_cast<const double2*>(cq + ch.w + 4 * mu) + 1);
+        cm[0] = c01.x; cm[1] = c01.y; cm[2] = c23.x; cm[3] = c23.y;
+      } else if constexpr (WD == 4) {
+        const float4 c4 = __ldg(reinterpret_cast<const float4*>(cq + ch.w + 4 * mu));
+        cm[0] = c4.x; cm[1] = c4.y; cm[2] = c4.z; cm[3] = c4.w;
+      } else {
+        cm[0] = __ldg(cq + ch.w + mu);
+      }
+      if constexpr (kSameType<Tb, double>) {
+        b[0] = bv[mu]; b[1] = bv[M + mu]; b[2] = bv[2 * M + mu]; b[3] = bv[3 * M + mu]; b[4] = bv[4 * M + mu];
+      } else {
+        const float4 b4 = reinterpret_cast<const float4*>(bv)[mu];
+        b[0] = b4.x; b[1] = b4.y; b[2] = b4.z; b[3] = b4.w;
+        b[4] = reinterpret_cast<const float*>(bv)[4 * M + mu];
+      }
+#pragma unroll
+      for (int t = 0; t < WD; ++t)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) a[t][k] += cm[t] * b[k];
+    }
+#pragma unroll
+    for (int t = 0; t < WD; ++t)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) part[(5 * t + k) * nch + c] = a[t][k];
+  }
+}
+
 // One warp, (walker, electron) pair gw (walker gw / N, electron gw % N).
 template <class Tb>
 __device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L, long long gw, unsigned char* base,
@@ -43,42 +88,15 @@ __device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L
     if (OD) basis_values_ds(s, lane, r3, ctab, bds);
   }
   __syncwarp();
-  // contraction by quads of orbitals sharing a coefficient range: one basis-function load
-  // feeds four orbitals; partials component-major, part[(5 t + k) nch + chunk]
+  // contraction by groups of orbitals sharing a coefficient range (quads: one basis-function
+  // load feeds four orbitals); partials component-major, part[(5 t + k) nch + chunk]
   const int nch = s.n_evq_chunk;
   const Tb* cq = kSameType<Tb, double> ? reinterpret_cast<const Tb*>(s.evq_coef)
                                        : reinterpret_cast<const Tb*>(s.evq_coef_f);
-  for (int c = lane; c < nch; c += 32) {
-    const int4 ch = __ldg(reinterpret_cast<const int4*>(s.evq_chunk) + c);
-    Tb a[4][5];
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-#pragma unroll
-      for (int k = 0; k < 5; ++k) a[t][k] = (Tb)0;
-    for (int mu = ch.y; mu < ch.z; ++mu) {
-      Tb cm[4], b[5];
-      if constexpr (kSameType<Tb, double>) {
-        const double2 c01 = __ldg(reinterpret_cast<const double2*>(cq + ch.w + 4 * mu));
-        const double2 c23 = __ldg(reinterpret_cast<const double2*>(cq + ch.w + 4 * mu) + 1);
-        cm[0] = c01.x; cm[1] = c01.y; cm[2] = c23.x; cm[3] = c23.y;
-        b[0] = bv[mu]; b[1] = bx[mu]; b[2] = by[mu]; b[3] = bz[mu]; b[4] = bl[mu];
-      } else {
-        const float4 c4 = __ldg(reinterpret_cast<const float4*>(cq + ch.w + 4 * mu));
-        const float4 b4 = reinterpret_cast<const float4*>(bv)[mu];
-        cm[0] = c4.x; cm[1] = c4.y; cm[2] = c4.z; cm[3] = c4.w;
-        b[0] = b4.x; b[1] = b4.y; b[2] = b4.z; b[3] = b4.w;
-        b[4] = reinterpret_cast<const float*>(bv)[4 * M + mu];
-      }
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int k = 0; k < 5; ++k) a[t][k] += cm[t] * b[k];
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-#pragma unroll
-      for (int k = 0; k < 5; ++k) part[(5 * t + k) * nch + c] = a[t][k];
-  }
+  if (s.evq_width == 4)
+    contract_groups<Tb, 4>(s, lane, nch, cq, bv, part);
+  else
+    contract_groups<Tb, 1>(s, lane, nch, cq, bv, part);
   if (!kSameType<Tb, double> && OD)
     for (int c = lane; c < s.n_det_chunk; c += 32) {
       const int4 ch = __ldg(reinterpret_cast<const int4*>(s.det_chunk) + c);
@@ -161,7 +179,7 @@ int make_orb_layout(const SysDev& s, int tb, int max_smem, OrbLayout& L) {
   L.bas = take(5 * M * tb);
   L.bds = take(tb == 4 ? 8 * M : 16);
   L.ctab = take(tb == 4 ? 8 * 4 * s.Nn : 16);
-  L.part = take(20 * tb * std::max(s.n_evq_chunk, 1));
+  L.part = take(5 * s.evq_width * tb * std::max(s.n_evq_chunk, 1));
   L.partd = take(tb == 4 ? 8 * std::max(s.n_det_chunk, 1) : 16);
   L.warp_bytes = off;
   L.wpb = kOrbWarps;

@@ -299,9 +299,15 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           __syncwarp();
           if (act && gl < n) {
             const int j = gl;
-            double wj = (j == ie) ? -1.0 : 0.0;
-            for (int o = 0; o < n; ++o) wj = fma(vrowd[__ldg(dl + u * n + o)], B[o * n + j], wj);
-            const double f = wj * irho;
+            // two partial sums (even and odd o) halve the dependent chain
+            double w0 = (j == ie) ? -1.0 : 0.0, w1 = 0.0;
+            int o = 0;
+            for (; o + 1 < n; o += 2) {
+              w0 = fma(vrowd[__ldg(dl + u * n + o)], B[o * n + j], w0);
+              w1 = fma(vrowd[__ldg(dl + u * n + o + 1)], B[(o + 1) * n + j], w1);
+            }
+            if (o < n) w0 = fma(vrowd[__ldg(dl + u * n + o)], B[o * n + j], w0);
+            const double f = (w0 + w1) * irho;
             for (int o = 0; o < n; ++o) B[o * n + j] = fma(-cv[o], f, B[o * n + j]);
           }
           __syncwarp();

@@ -189,60 +189,75 @@ static void make_chunks(const SysHost& s, const std::vector<int>& orbs, std::vec
   }
 }
 
-// Groups the evaluated orbitals into quads of equal coefficient range (in order of first
-// appearance) and splits each quad's range into chunks with the critical-path model of
-// make_chunks (a quad's step costs about twice a single orbital's).
-static void make_quads(SysHost& s) {
+// Groups the evaluated orbitals for the contraction: width 1 (each orbital alone) or width 4
+// (quads of orbitals with equal coefficient range, in order of first appearance, so that one
+// basis-function load feeds four orbitals).  Each group's range is split into chunks of
+// length L; the modelled critical path of one warp is
+//   ceil(chunks / 32) * (c_mu L + 12)  [chunk loop; c_mu ~ instructions per mu: 8 or 23]
+//   + ceil(orbitals / 32) * 5 * max chunks of one group  [per-orbital sum of the partials],
+// and the width and L with the shorter path are taken.
+static long plan_groups(const SysHost& s, int width, std::vector<std::vector<int>>& groups, int& bestL) {
   const std::vector<int>& orbs = s.ev_orb;
-  std::vector<std::vector<int>> quads;
+  groups.clear();
   std::vector<std::pair<int, int>> open_rng;
-  std::vector<int> open_q;
-  s.evq_slot.assign(orbs.size(), 0);
+  std::vector<int> open_g;
   for (size_t q = 0; q < orbs.size(); ++q) {
     const std::pair<int, int> rng{s.orb_lo[orbs[q]], s.orb_hi[orbs[q]]};
     size_t g = 0;
     while (g < open_rng.size() && open_rng[g] != rng) ++g;
     if (g == open_rng.size()) {
       open_rng.push_back(rng);
-      open_q.push_back(-1);
+      open_g.push_back(-1);
     }
-    if (open_q[g] < 0 || quads[open_q[g]].size() == 4) {
-      open_q[g] = (int)quads.size();
-      quads.emplace_back();
+    if (open_g[g] < 0 || (int)groups[open_g[g]].size() == width) {
+      open_g[g] = (int)groups.size();
+      groups.emplace_back();
     }
-    const int qd = open_q[g];
-    s.evq_slot[q] = 4 * qd + (int)quads[qd].size();
-    quads[qd].push_back((int)q);
+    groups[open_g[g]].push_back((int)q);
   }
   int maxlen = 1;
-  for (auto& v : quads) maxlen = std::max(maxlen, s.orb_hi[orbs[v[0]]] - s.orb_lo[orbs[v[0]]]);
-  int bestL = maxlen;
+  for (auto& v : groups) maxlen = std::max(maxlen, s.orb_hi[orbs[v[0]]] - s.orb_lo[orbs[v[0]]]);
+  const long cmu = width == 4 ? 23 : 8;
   long bestcost = -1;
+  bestL = maxlen;
   for (int L = std::min(4, maxlen); L <= maxlen; ++L) {
     long nch = 0, maxc = 1;
-    for (auto& v : quads) {
+    for (auto& v : groups) {
       const long c = std::max(1, (s.orb_hi[orbs[v[0]]] - s.orb_lo[orbs[v[0]]] + L - 1) / L);
       nch += c;
       maxc = std::max(maxc, c);
     }
-    const long cost = ((nch + 31) / 32) * (2 * L + 8) + (((long)orbs.size() + 31) / 32) * maxc;
+    const long cost = ((nch + 31) / 32) * (cmu * L + 12) + (((long)orbs.size() + 31) / 32) * 5 * maxc;
     if (bestcost < 0 || cost < bestcost) { bestcost = cost; bestL = L; }
   }
+  return bestcost;
+}
+
+static void make_quads(SysHost& s) {
+  const std::vector<int>& orbs = s.ev_orb;
+  std::vector<std::vector<int>> g1, g4;
+  int L1 = 1, L4 = 1;
+  const long c1 = plan_groups(s, 1, g1, L1), c4 = plan_groups(s, 4, g4, L4);
+  const int width = c4 < c1 ? 4 : 1, bestL = width == 4 ? L4 : L1;
+  const std::vector<std::vector<int>>& groups = width == 4 ? g4 : g1;
+  s.evq_width = width;
+  s.evq_slot.assign(orbs.size(), 0);
   s.evq_chunk.clear();
   s.evq_coef.clear();
   s.evq_chunk_off.assign(1, 0);
-  for (size_t qd = 0; qd < quads.size(); ++qd) {
-    const int k0 = orbs[quads[qd][0]], lo = s.orb_lo[k0], hi = s.orb_hi[k0], len = hi - lo;
+  for (size_t qd = 0; qd < groups.size(); ++qd) {
+    const int k0 = orbs[groups[qd][0]], lo = s.orb_lo[k0], hi = s.orb_hi[k0], len = hi - lo;
     const int qoff = (int)s.evq_coef.size();
-    s.evq_coef.resize(qoff + 4 * (size_t)len, 0.0);
-    for (size_t t = 0; t < quads[qd].size(); ++t) {
-      const int k = orbs[quads[qd][t]];
-      for (int mu = lo; mu < hi; ++mu) s.evq_coef[qoff + 4 * (mu - lo) + t] = s.orb_coef[s.orb_off[k] + mu - lo];
+    s.evq_coef.resize(qoff + width * (size_t)len, 0.0);
+    for (size_t t = 0; t < groups[qd].size(); ++t) {
+      const int k = orbs[groups[qd][t]];
+      s.evq_slot[groups[qd][t]] = 4 * (int)qd + (int)t;
+      for (int mu = lo; mu < hi; ++mu) s.evq_coef[qoff + width * (mu - lo) + t] = s.orb_coef[s.orb_off[k] + mu - lo];
     }
     const int nc = std::max(1, (len + bestL - 1) / bestL);
     for (int c = 0; c < nc; ++c) {
       const int b = lo + (int)((long)len * c / nc), e = lo + (int)((long)len * (c + 1) / nc);
-      s.evq_chunk.insert(s.evq_chunk.end(), {(int)qd, b, e, qoff - 4 * lo});
+      s.evq_chunk.insert(s.evq_chunk.end(), {(int)qd, b, e, qoff - width * lo});
     }
     s.evq_chunk_off.push_back((int)(s.evq_chunk.size() / 4));
   }
@@ -533,6 +548,24 @@ int build_system(const vbqmc_system_desc* d, SysHost& s, std::string& err) {
   // parameters
   s.cparam.assign(d->cparam, d->cparam + d->n_cparam);
   for (int I : s.cparam) VBQ_REQUIRE(I >= 0 && I < s.Nvb, "bad structure parameter index");
+  s.cpar_off.assign(1, 0);
+  s.cpar_st.clear();
+  for (int I : s.cparam) {
+    for (size_t t = 0; t < s.sterm_I.size(); ++t)
+      if (s.sterm_I[t] == I) s.cpar_st.push_back((int)t);
+    s.cpar_off.push_back((int)s.cpar_st.size());
+  }
+  {
+    const int nterm = (int)s.term_coef.size();
+    s.det_term_off.assign(1, 0);
+    s.det_term.clear();
+    for (int sp = 0; sp < 2; ++sp)
+      for (int u = 0; u < s.U[sp]; ++u) {
+        for (int k = 0; k < nterm; ++k)
+          if (s.term_det[2 * k + sp] == u) s.det_term.push_back(k);
+        s.det_term_off.push_back((int)s.det_term.size());
+      }
+  }
   s.jas_param = d->jas_param ? 1 : 0;
   s.P = (int)s.cparam.size() + (s.jas_param ? 5 * s.n_elem + 5 + (s.een_on ? kNfree * s.n_elem : 0) : 0) +
         s.n_kappa;

@@ -58,6 +58,9 @@ struct SysHost {
   // structure terms (I, term, d) for the c_I derivatives
   std::vector<int> sterm_I, sterm_k;
   std::vector<double> sterm_d;
+  // the terms holding determinant ud (up u, then down U[0] + u): det_term[det_term_off[ud] ..
+  // det_term_off[ud + 1]]; the structure terms of parameter q: cpar_st[cpar_off[q] .. [q + 1]]
+  std::vector<int> det_term_off, det_term, cpar_off, cpar_st;
   // Jastrow
   double kappa = 0.8, b1_anti = 0.5, b1_par = 0.25, vnn = 0.0;
   int een_on = 0;
@@ -77,13 +80,15 @@ struct SysHost {
   // [n_chunk][4] = (orbital slot q, first mu, one-past-last mu, coefficient base so that the
   // coefficient of mu is orb_coef[base + mu]); chunk_off[q] .. chunk_off[q+1] are q's chunks.
   std::vector<int> occ_chunk[2], occ_chunk_off[2];   // per spin, over occ_list[spin]
-  // quads of evaluated orbitals with the same nonzero coefficient range, contracted together
-  // (one basis-function load feeds four orbitals): evq_coef[qoff + 4 (mu - lo) + t] is the
-  // coefficient of mu in orbital t of the quad (0 for the padding of a short quad);
-  // evq_chunk [n][4] = (quad, first mu, one-past-last mu, qoff - 4 lo), evq_chunk_off[quad]
-  // .. [quad + 1] are the quad's chunks; evq_slot[q] = 4 quad + t of evaluated orbital q.
+  // groups of evq_width (4 or 1) evaluated orbitals with the same nonzero coefficient range,
+  // contracted together (with width 4 one basis-function load feeds four orbitals):
+  // evq_coef[qoff + width (mu - lo) + t] is the coefficient of mu in orbital t of the group (0
+  // for the padding of a short group); evq_chunk [n][4] = (group, first mu, one-past-last mu,
+  // qoff - width lo), evq_chunk_off[group] .. [group + 1] are the group's chunks;
+  // evq_slot[q] = 4 group + t of evaluated orbital q.
   std::vector<int> evq_chunk, evq_chunk_off, evq_slot;
   std::vector<double> evq_coef;
+  int evq_width = 4;
   std::vector<int> det_chunk, det_chunk_off;          // over the first n_ev_det evaluated orbitals
 };
 
@@ -128,6 +133,10 @@ struct SysDev {
   const int* sterm_I;
   const int* sterm_k;
   const double* sterm_d;
+  const int* det_term_off;
+  const int* det_term;
+  const int* cpar_off;
+  const int* cpar_st;
   const int* cparam;
   const double* jas_a;
   const double* jas_b;
@@ -135,7 +144,7 @@ struct SysDev {
   const float* een_cf;
   const double* een_B;
   const int* kap_x;                    // [n_kappa][4]: eval index of l (spin 0, spin 1; -1: none), of k, 0
-  int n_occ_chunk[2], n_evq_chunk, n_det_chunk;
+  int n_occ_chunk[2], n_evq_chunk, n_det_chunk, evq_width;
   const int* occ_chunk[2];
   const int* occ_chunk_off[2];
   const int* evq_chunk;
