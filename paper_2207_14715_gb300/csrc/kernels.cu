@@ -239,15 +239,14 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
       }
       __syncwarp();
       Tb dj = 0;
-      const int nitem = Nn + N + (s.een_on ? 5 * Nn : 0);
-      for (int t = lane; t < nitem; t += 32) {
+      for (int t = lane; t < Nn + N; t += 32) {
         if (t < Nn) {
           const PadeT<Tb> c = en_coef_t<Tb>(s, t);
           Tb f1, f0, t0, t1;
           pade_eval<Tb, false>(c, rnN[t], kap, f1, t0, t1);
           pade_eval<Tb, false>(c, rEN[e * Nn + t], kap, f0, t0, t1);
           dj += f1 - f0;
-        } else if (t < Nn + N) {
+        } else {
           const int j = t - Nn;
           if (j == e) continue;
           const PadeT<Tb> c = ee_coef_t<Tb>(s, (e < Nup) == (j < Nup));
@@ -255,21 +254,35 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           pade_eval<Tb, false>(c, rnE[j], kap, f1, t0, t1);
           pade_eval<Tb, false>(c, rEE[e * N + j], kap, f0, t0, t1);
           dj += f1 - f0;
-        } else {
-          const int tt = t - Nn - N, a = tt / 5, k = tt % 5;
-          Tb Yo[6], Yn[6];
+        }
+      }
+      if (s.een_on) {
+        // e-e-n items (nucleus a, part of the partners j), every k in each: the pair sums
+        // are linear in the partners, so each part adds its own share of the change, and all
+        // lanes run the same code (no divergence over k)
+        const int np = max(1, 32 / Nn);
+        for (int t = lane; t < np * Nn; t += 32) {
+          const int a = t / np, part = t - np * a;
+          Tb Yo[5][6], Yn[5][6];
 #pragma unroll
-          for (int q = 0; q < 6; ++q) Yo[q] = Yn[q] = (Tb)0;
-          for (int j = 0; j < N; ++j) {
+          for (int k = 0; k < 5; ++k)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) Yo[k][q] = Yn[k][q] = (Tb)0;
+          for (int j = part * N / np; j < (part + 1) * N / np; ++j) {
             if (j == e) continue;
-            const Tb po = Upo[k * UP + j], pn = Upn[k * UP + j];
             const Tb* Sj = Stab + a * SA + j * 6;
+            Tb sj[6];
 #pragma unroll
-            for (int q = 0; q < 6; ++q)
-              if (q <= 5 - k) {
-                Yo[q] += po * Sj[q];
-                Yn[q] += pn * Sj[q];
+            for (int q = 0; q < 6; ++q) sj[q] = Sj[q];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+              const Tb po = Upo[k * UP + j], pn = Upn[k * UP + j];
+#pragma unroll
+              for (int q = 0; q <= 5 - k; ++q) {
+                Yo[k][q] += po * sj[q];
+                Yn[k][q] += pn * sj[q];
               }
+            }
           }
           const Tb* So = Stab + a * SA + e * 6;
           const Tb* Sn = Snew + a * 6;
@@ -277,8 +290,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           een_for_each([&](auto tc) {
             constexpr int q = decltype(tc)::value;
             constexpr int tk = een_klm(q).k, A = een_klm(q).l + een_klm(q).m, B = een_klm(q).m;
-            if (tk != k) return;
-            dj += c[q] * ((Sn[A] * Yn[B] + Sn[B] * Yn[A]) - (So[A] * Yo[B] + So[B] * Yo[A]));
+            dj += c[q] * ((Sn[A] * Yn[tk][B] + Sn[B] * Yn[tk][A]) - (So[A] * Yo[tk][B] + So[B] * Yo[tk][A]));
           });
         }
       }
