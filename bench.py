@@ -119,14 +119,60 @@ def peaks(sm_mhz):
 
 # --------------------------------------------------------------------------------------
 class ClockSampler:
-    """nvidia-smi samples during the timed region (read-only query)."""
+    """SM clock, its maximum and the clock-event reasons sampled every few milliseconds during
+    the timed region: read-only NVML queries (the library nvidia-smi reads) from a polling
+    thread, with nvidia-smi itself as the fallback where NVML cannot be loaded."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
 
     def __init__(self, index):
         self.index = index
+        self.samples = []
+        self.thread = None
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
 
+    def _nvml_handle(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None, None
+        h = ctypes.c_void_p()
+        rc = -1
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(self.index)
+            bus = "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+            rc = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h))
+        except Exception:
+            rc = -1
+        if rc != 0 and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+            return None, None
+        return lib, h
+
+    def _poll(self, lib, h, stop):
+        import ctypes
+        sm, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        get_rs = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        while not stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm)) == 0 and \
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                mask = rs.value if get_rs(h, ctypes.byref(rs)) == 0 else 0
+                self.samples.append((float(sm.value), float(mx.value), int(mask)))
+            time.sleep(0.005)
+
     def start(self):
+        import threading
+        try:
+            lib, h = self._nvml_handle()
+        except Exception:
+            lib, h = None, None
+        if lib is not None:
+            self.stop_flag = threading.Event()
+            self.thread = threading.Thread(target=self._poll, args=(lib, h, self.stop_flag), daemon=True)
+            self.thread.start()
+            return
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
@@ -141,6 +187,15 @@ class ClockSampler:
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=5)
+            if self.samples:
+                reasons = sorted({nm for _, _, m in self.samples for bit, nm in self.REASONS.items() if m & bit})
+                out = {"sm_mhz": statistics.median(x[0] for x in self.samples),
+                       "sm_max_mhz": max(x[1] for x in self.samples), "reasons": reasons,
+                       "samples": len(self.samples), "source": "NVML, every 5 ms in the timed region"}
+            return out
         if self.proc is None:
             return out
         self.proc.terminate()
@@ -165,7 +220,7 @@ class ClockSampler:
                     reasons.add(nm)
         if sm:
             out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                   "samples": len(sm)}
+                   "samples": len(sm), "source": "nvidia-smi, every 200 ms"}
         return out
 
 

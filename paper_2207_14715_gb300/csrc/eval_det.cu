@@ -104,9 +104,12 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
     const int e = eq.hi, q = eq.lo;
     const Tb* ob = OB + ((size_t)w * N + e) * 5 * nev;
     const Tb v = ob[q], x = ob[nev + q], y = ob[2 * nev + q], z = ob[3 * nev + q], lp = ob[4 * nev + q];
-    Lphi[e * nev + q] = lp + (Tb)2 * (G[3 * e] * x + G[3 * e + 1] * y + G[3 * e + 2] * z);
+    const Tb lq = lp + (Tb)2 * (G[3 * e] * x + G[3 * e + 1] * y + G[3 * e + 2] * z);
+    Lphi[e * nev + q] = lq;
     if (q < nevd) {
-      if (!carry) PhiD[e * nevd + q] = OD[((size_t)w * N + e) * nevd + q];
+      // PhiD: double orbital values for the LU, or with carried inverses (no LU) the dressed
+      // Laplacians of the determinant orbitals widened once for the traces t_u
+      PhiD[e * nevd + q] = carry ? (double)lq : OD[((size_t)w * N + e) * nevd + q];
       Gphi[(e * nevd + q) * 3] = x;
       Gphi[(e * nevd + q) * 3 + 1] = y;
       Gphi[(e * nevd + q) * 3 + 2] = z;
@@ -133,7 +136,7 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
         const int u = i / n, o = i - u * n, col = __ldg(s.det_ev[sp] + u * n + o);
         const double* B = Bc + u * n * n + o * n;
         double t = 0.0;
-        for (int e = 0; e < n; ++e) t = fma(B[e], (double)Lphi[(e0 + e) * nev + col], t);
+        for (int e = 0; e < n; ++e) t = fma(B[e], PhiD[(e0 + e) * nevd + col], t);
         part[i] = t;
       }
       __syncwarp();

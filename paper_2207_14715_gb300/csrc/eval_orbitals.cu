@@ -83,7 +83,11 @@ __device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L
   } else {
     // float form: value and gradient of a basis function interleaved as one float4 (one
     // shared-memory load per function and coefficient), Laplacians after them
-    const dsf r3[3] = {ds_from_double(r[0]), ds_from_double(r[1]), ds_from_double(r[2])};
+    // lane d < 3 converts coordinate d (the conversion runs on the double pipe), then a broadcast
+    const dsf rl = lane < 3 ? ds_from_double(r[lane]) : dsf{0.0f, 0.0f};
+    dsf r3[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) r3[d] = dsf{__shfl_sync(kFull, rl.hi, d), __shfl_sync(kFull, rl.lo, d)};
     basis_at_f<true>(s, lane, r3, bv, bv + 1, bv + 2, bv + 3, bv + 4 * M, 4);
     if (OD) basis_values_ds(s, lane, r3, ctab, bds);
   }
