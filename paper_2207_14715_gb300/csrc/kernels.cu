@@ -417,19 +417,23 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.dsg = take(8 * Ut);
   L.wk = take(8 * s.nterm);
   L.PhiO = take(8 * N * L.nocc_max);
-  L.bas = take(8 * s.M);
-  L.vrow = take(8 * L.nocc_max);
-  L.part = take(8 * std::max(std::max(s.n_occ_chunk[0], s.n_occ_chunk[1]), 1));
-  L.rho = take(8 * std::max(s.U[0], s.U[1]));
-  L.rinv = take(8 * (std::max(s.U[0], s.U[1]) + 1));
   int cv = 0, scr = 0;
   for (int sp = 0; sp < 2; ++sp) {
     const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
     cv = std::max(cv, 8 * ng * n);
     scr = std::max(scr, ng * (8 * n * n + 4 * n) + 16);
   }
+  // the LU scratch of a refactorisation shares its space with the buffers of the moves (the
+  // basis values and partial sums that build PhiO are consumed before the LU starts)
+  const int shared0 = off;
+  L.bas = take(8 * s.M);
+  L.vrow = take(8 * L.nocc_max);
+  L.part = take(8 * std::max(std::max(s.n_occ_chunk[0], s.n_occ_chunk[1]), 1));
+  L.rho = take(8 * std::max(s.U[0], s.U[1]));
+  L.rinv = take(8 * (std::max(s.U[0], s.U[1]) + 1));
   L.cvec = take(std::max(cv, 8));
-  L.scratch = take(std::max(scr, 16));
+  L.scratch = shared0;
+  off = std::max(off, align16(shared0 + std::max(scr, 16)));
   L.geo = take(tb * (N * N + N * s.Nn + (6 * N + 1) * s.Nn + N + s.Nn + 6 * s.Nn + 10 * (N + 1)));
   L.warp_bytes = off;
   int wpb = max_smem / off;
