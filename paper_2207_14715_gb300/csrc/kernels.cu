@@ -43,7 +43,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   // row strides padded by one so that lanes on different nuclei (powers) read different banks
   const int SA = 6 * s.N + 1, UP = s.N + 1;
   Tb* Stab = rEN + s.N * s.Nn;                          // [Nn][SA]: [a][j][q] = Rbar(r_ja)^q at a*SA + 6j + q
-  Tb* rnE = Stab + SA * s.Nn;                           // [N] r from the proposed position
+  Tb* rnE = reinterpret_cast<Tb*>(base + L.geom);       // [N] r from the proposed position
   Tb* rnN = rnE + s.N;                                  // [Nn]
   Tb* Snew = rnN + s.Nn;                                // [Nn][6]
   Tb* Upo = Snew + 6 * s.Nn;                            // [5][UP] Rbar(r_ej)^k, current position of e
@@ -409,14 +409,22 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.nocc_max = std::max(std::max(s.nocc[0], s.nocc[1]), 1);
   L.R = take(8 * 3 * N);
   L.Rds = take(tb == 4 ? 8 * 3 * N : 16);
-  L.rtab = take(8 * 4 * N);
-  L.rtds = take(tb == 4 ? 8 * 3 * N : 16);
   L.Binv0 = take(8 * s.U[0] * s.n[0] * s.n[0]);
   L.Binv1 = take(8 * s.U[1] * s.n[1] * s.n[1]);
+  L.wk = take(8 * s.nterm);
+  // a refactorisation's ln|det|, signs and orbital matrix overlay the sweep's proposals and
+  // the move-only geometry (the refactorisation runs before the proposals are formed, and its
+  // outputs are consumed by the term ratios before the moves start)
+  const int over0 = off;
+  L.rtab = take(8 * 4 * N);
+  L.rtds = take(tb == 4 ? 8 * 3 * N : 16);
+  L.geom = take(tb * (N + s.Nn + 6 * s.Nn + 10 * (N + 1)));
+  const int moves_end = off;
+  off = over0;
   L.ldet = take(8 * Ut);
   L.dsg = take(8 * Ut);
-  L.wk = take(8 * s.nterm);
   L.PhiO = take(8 * N * L.nocc_max);
+  off = std::max(off, moves_end);
   int cv = 0, scr = 0;
   for (int sp = 0; sp < 2; ++sp) {
     const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
@@ -434,7 +442,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.cvec = take(std::max(cv, 8));
   L.scratch = shared0;
   off = std::max(off, align16(shared0 + std::max(scr, 16)));
-  L.geo = take(tb * (N * N + N * s.Nn + (6 * N + 1) * s.Nn + N + s.Nn + 6 * s.Nn + 10 * (N + 1)));
+  L.geo = take(tb * (N * N + N * s.Nn + (6 * N + 1) * s.Nn));
   L.warp_bytes = off;
   int wpb = max_smem / off;
   if (wpb > 16) wpb = 16;
@@ -447,12 +455,26 @@ template <class Tb>
 static cudaError_t launch_sweep_t(const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps, int refresh,
                                   double* state, int state_valid, double step, uint64_t seed, uint32_t step0, uint32_t tag,
                                   uint32_t woff, int* nacc, cudaStream_t st) {
-  const int smem = L.wpb * L.warp_bytes;
+  // walkers per block: the most that fit, unless one or two fewer need no more waves of
+  // blocks over the SMs (a wave costs about 3 % more per extra warp on the SM, measured on the
+  // ethylene-shaped system; an idle part of the last wave costs its full share)
+  SweepLayout Lw = L;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
+                                               cudaSuccess && sms > 0 && W > 0) {
+    auto cost = [&](int p) {
+      const long waves = ((long)W + (long)p * sms - 1) / ((long)p * sms);
+      return waves * (100 + 3 * p);
+    };
+    for (int p = L.wpb - 1; p >= std::max(1, L.wpb - 2); --p)
+      if (cost(p) < cost(Lw.wpb)) Lw.wpb = p;
+  }
+  const int smem = Lw.wpb * Lw.warp_bytes;
   cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const int blocks = (W + L.wpb - 1) / L.wpb;
-  sweep_kernel<Tb><<<blocks, 32 * L.wpb, smem, st>>>(s, L, W, R, nsweeps, refresh, state, state_valid, step, seed, step0, tag,
-                                                     woff, nacc);
+  const int blocks = (W + Lw.wpb - 1) / Lw.wpb;
+  sweep_kernel<Tb><<<blocks, 32 * Lw.wpb, smem, st>>>(s, Lw, W, R, nsweeps, refresh, state, state_valid, step, seed, step0,
+                                                      tag, woff, nacc);
   return cudaGetLastError();
 }
 

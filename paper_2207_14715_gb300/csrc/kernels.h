@@ -50,7 +50,7 @@ struct EvalLayout {
 
 struct SweepLayout {
   int wpb = 0, warp_bytes = 0;
-  int R, Rds, rtab, rtds, Binv0, Binv1, ldet, dsg, wk, PhiO, bas, vrow, part, rho, rinv, cvec, scratch, geo;
+  int R, Rds, rtab, rtds, Binv0, Binv1, ldet, dsg, wk, PhiO, bas, vrow, part, rho, rinv, cvec, scratch, geo, geom;
   int nocc_max;
   int G0, G1;
 };
