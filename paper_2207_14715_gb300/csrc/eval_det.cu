@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(EvalBounds<Tb>::threads, 1)
 
 }  // namespace
 
-int make_det_layout(const SysDev& s, int tb, int max_smem, DetLayout& L) {
+int make_det_layout(const SysDev& s, int tb, int max_smem, DetLayout& L, bool carried) {
   int off = 0;
   auto take = [&](int bytes) {
     const int o = off;
@@ -405,7 +405,7 @@ int make_det_layout(const SysDev& s, int tb, int max_smem, DetLayout& L) {
   int scr = 16;
   for (int sp = 0; sp < 2; ++sp) {
     const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
-    scr = std::max(scr, ng * (16 * n * n + 4 * n) + 16);  // LU: A, inverse, pivots per group
+    if (!carried) scr = std::max(scr, ng * (16 * n * n + 4 * n) + 16);  // LU: A, inverse, pivots per group
     scr = std::max(scr, 8 * s.U[sp] * n);                  // carried state: trace partials
   }
   // Gam and Aux rows of both spins, one product B_u L_u
@@ -465,7 +465,7 @@ cudaError_t launch_eval_t(const SysDev& s, const EvalLayout& L, int W, const dou
     e = launch_dettab<Tb>(s, L.tab, W, static_cast<const Tb*>(b.JG), static_cast<const Tb*>(b.JL), b.JS,
                           static_cast<const Tb*>(b.OB), b.OD, logpsi, sign, eloc, b.VG, grad, O, dEL, st);
   } else {
-    const DetLayout& D = L.det;
+    const DetLayout& D = carry ? L.detc : L.det;
     const int smem = D.wpb * D.warp_bytes;
     e = cudaFuncSetAttribute(det_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -507,6 +507,7 @@ int make_eval_layout(const SysDev& s, int tb, int max_smem, EvalLayout& L) {
   if (rc == VBQMC_OK) rc = make_orb_layout(s, tb, max_smem, L.orb);
   if (rc == VBQMC_OK)
     rc = s.msd ? make_dettab_layout(s, tb, max_smem, L.tab) : make_det_layout(s, tb, max_smem, L.det);
+  if (rc == VBQMC_OK && !s.msd) rc = make_det_layout(s, tb, max_smem, L.detc, true);
   return rc;
 }
 

@@ -45,6 +45,7 @@ struct EvalLayout {
   JasLayout jas;
   OrbLayout orb;
   DetLayout det;
+  DetLayout detc;  // the same kernel from carried inverses: no LU scratch
   DetTabLayout tab;  // used instead of det when the system's msd flag is set
 };
 
@@ -70,7 +71,7 @@ struct ForceLayout {
 };
 
 int make_eval_layout(const SysDev& s, int bulk_bytes, int max_smem, EvalLayout& L);
-int make_det_layout(const SysDev& s, int bulk_bytes, int max_smem, DetLayout& L);
+int make_det_layout(const SysDev& s, int bulk_bytes, int max_smem, DetLayout& L, bool carried = false);
 int make_dettab_layout(const SysDev& s, int bulk_bytes, int max_smem, DetTabLayout& L);
 template <class Tb>
 cudaError_t launch_dettab(const SysDev& s, const DetTabLayout& L, int W, const Tb* JG, const Tb* JL, const double* JS,
