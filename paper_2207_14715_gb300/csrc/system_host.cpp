@@ -321,6 +321,10 @@ int build_system(const vbqmc_system_desc* d, SysHost& s, std::string& err) {
     }
     M += kNcomp[l];
   }
+  s.sh_by_l.clear();
+  for (int l = 0; l <= 2; ++l)
+    for (int i = 0; i < s.S; ++i)
+      if (s.sh_l[i] == l) s.sh_by_l.push_back(i);
   if (M > kMaxM) {
     err = "basis larger than 1024 functions";
     return VBQMC_ERR_CAPACITY;

@@ -30,6 +30,7 @@ struct SysHost {
   std::vector<double> nuc4;            // [Nn][4] x y z Z
   std::vector<int> nuc_elem;
   std::vector<int> sh_center, sh_l, sh_first;
+  std::vector<int> sh_by_l;            // shells in order of l (lanes of one round run one shell kind)
   std::vector<double> sh_zeta, sh_norm;  // norm [S][6]
   std::vector<int> nuc_sh;             // [Nn][4]: first shell, end shell, first and end basis function
   int max_nuc_mu = 0;                  // most basis functions on one nucleus
@@ -111,6 +112,7 @@ struct SysDev {
   const int* sh_center;
   const int* sh_l;
   const int* sh_first;
+  const int* sh_by_l;
   const int* nuc_sh;                   // [Nn][4], see SysHost
   int max_nuc_mu;
   const double* sh_zeta;

@@ -44,7 +44,8 @@ template <> __device__ __forceinline__ const float* een_coefs<float>(const SysDe
 template <class Tb, bool DERIV>
 __device__ __forceinline__ void basis_at(const SysDev& s, int lane, double x, double y, double z, Tb* bv, Tb* bx,
                                          Tb* by, Tb* bz, Tb* bl) {
-  for (int sh = lane; sh < s.S; sh += 32) {
+  for (int t = lane; t < s.S; t += 32) {
+    const int sh = __ldg(s.sh_by_l + t);
     const double* nu = s.nuc4 + 4 * __ldg(s.sh_center + sh);
     const int f = __ldg(s.sh_first + sh);
     gto_shell<Tb, DERIV>(__ldg(s.sh_l + sh), (Tb)__ldg(s.sh_zeta + sh), s.sh_norm + 6 * sh, (Tb)(x - __ldg(nu)),
@@ -63,7 +64,8 @@ __device__ __forceinline__ dsf nuc_coord_ds(const SysDev& s, int a, int d) {
 template <bool DERIV>
 __device__ __forceinline__ void basis_at_f(const SysDev& s, int lane, const dsf* r3, float* bv, float* bx, float* by,
                                            float* bz, float* bl, int cs = 1) {
-  for (int sh = lane; sh < s.S; sh += 32) {
+  for (int t = lane; t < s.S; t += 32) {
+    const int sh = __ldg(s.sh_by_l + t);
     const int c = __ldg(s.sh_center + sh);
     const int f = __ldg(s.sh_first + sh);
     const float dx = ds_diff_f(r3[0], nuc_coord_ds(s, c, 0)), dy = ds_diff_f(r3[1], nuc_coord_ds(s, c, 1)),
@@ -88,7 +90,8 @@ __device__ __forceinline__ void basis_values_ds(const SysDev& s, int lane, const
     ctab[4 * c + 3] = ds_add_nc(ds_add_nc(ds_mul(dx, dx), ds_mul(dy, dy)), ds_mul(dz, dz));
   }
   __syncwarp();
-  for (int sh = lane; sh < s.S; sh += 32) {
+  for (int t = lane; t < s.S; t += 32) {
+    const int sh = __ldg(s.sh_by_l + t);
     const int c = __ldg(s.sh_center + sh), l = __ldg(s.sh_l + sh), f = __ldg(s.sh_first + sh);
     const float2 zt = __ldg(reinterpret_cast<const float2*>(s.sh_zeta_ds) + sh);
     dsf e = {1.0f, 0.0f};
