@@ -35,8 +35,8 @@ SEED = 20220728 + 1
 WALKER_KERNEL_SOURCES = ["kernels.cu", "eval_jastrow.cu", "eval_orbitals.cu", "eval_det.cu", "walker_common.cuh",
                          "kernels.h", "wf_device.cuh", "dsfloat.cuh", "vbqmc_internal.h"]
 PROFILED_TRAFFIC = {
-    "sources_sha256": "c5f60e848db4eae0c2f57009884f13ca18f5c08eb5be9c226dd39eaa73ee8341",
-    "bytes_per_walker": {"sweep": 10784.6, "det": 26251.6, "orbitals": 8944.8},
+    "sources_sha256": "19686e597c7292a1144bb63cbb344fb18688d805da368d734d12f53462eb5d4f",
+    "bytes_per_walker": {"sweep": 10785.7, "det": 26172.2, "orbitals": 8943.9},
 }
 
 
