@@ -268,7 +268,8 @@ def cpu_baseline(spec, R_host, seconds_hint=15.0):
 
 
 def run_reference(args, ws, rank):
-    """Reference arm: the FP64 CPU oracle, timed on this machine's host cores."""
+    """Reference arm: the FP64 CPU oracle, timed on this machine's host cores, on the same workload
+    as the GPU arm (each step a bounded sample of its walkers, stated in cpu_baseline)."""
     if rank != 0:
         return
     from paper_2207_14715_gb300 import systems as S
@@ -288,7 +289,7 @@ def run_reference(args, ws, rank):
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic", "config": workload_config(0, flush=False),
+                      "data": "synthetic", "config": workload_config(args.walkers, flush=False),
                       "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                                   "d2h_bytes_per_step": 0}}), flush=True)
 
