@@ -73,7 +73,7 @@ __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L
       }
       for (int j = gr; j < N; j += Sg) {
         if (j == i) continue;
-        const int ij = i * N + j;
+        const int ij = g.ee(i, j);
         Tb f, df, d2f;
         pade_eval<Tb, true>(ee_coef_t<Tb>(s, (i < Nup) == (j < Nup)), g.rEE[ij], kap, f, df, d2f);
         if constexpr (kSameType<Tb, double>) {
@@ -108,7 +108,7 @@ __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L
             acc.zero();
             for (int j = 0; j < N; ++j)
               if (j != i) {
-                const int ij = i * N + j;
+                const int ij = g.ee(i, j);
                 acc.add(g.uEE[ij], g.iEE[ij], kap, g.eEE[3 * ij], g.eEE[3 * ij + 1], g.eEE[3 * ij + 2],
                         g.Stab + (a * N + j) * 6);
               }
@@ -119,7 +119,7 @@ __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L
             acc.zero();
             for (int j = 0; j < N; ++j)
               if (j != i) {
-                const int ij = i * N + j;
+                const int ij = g.ee(i, j);
                 acc.add(g.uEE[ij], g.iEE[ij], kap, g.eEE[3 * ij], g.eEE[3 * ij + 1], g.eEE[3 * ij + 2],
                         g.Stab + (a * N + j) * 6);
               }
@@ -292,7 +292,7 @@ __device__ __forceinline__ void jastrow_deriv_body(const SysDev& s, const JasLay
     for (int pp = lane; pp < npair; pp += 32) {
       int i = 0, rem = pp;
       while (rem >= N - 1 - i) { rem -= N - 1 - i; ++i; }
-      const int j = i + 1 + rem, ij = i * N + j;
+      const int j = i + 1 + rem, ij = g.ee(i, j);
       const Tb r = g.rEE[ij];
       const PadeT<Tb> c = ee_coef_t<Tb>(s, (i < Nup) == (j < Nup));
       const Tb cosv = g.eEE[3 * ij] * (vg[3 * i] - vg[3 * j]) + g.eEE[3 * ij + 1] * (vg[3 * i + 1] - vg[3 * j + 1]) +
@@ -343,7 +343,7 @@ __device__ __forceinline__ void jastrow_deriv_body(const SysDev& s, const JasLay
             acc.zero();
             for (int j = 0; j < N; ++j)
               if (j != i) {
-                const int ij = i * N + j;
+                const int ij = g.ee(i, j);
                 acc.add(g.uEE[ij], g.iEE[ij], kap, g.eEE[3 * ij], g.eEE[3 * ij + 1], g.eEE[3 * ij + 2],
                         g.Stab + (a * N + j) * 6);
               }
@@ -354,7 +354,7 @@ __device__ __forceinline__ void jastrow_deriv_body(const SysDev& s, const JasLay
             acc.zero();
             for (int j = 0; j < N; ++j)
               if (j != i) {
-                const int ij = i * N + j;
+                const int ij = g.ee(i, j);
                 acc.add(g.uEE[ij], g.iEE[ij], kap, g.eEE[3 * ij], g.eEE[3 * ij + 1], g.eEE[3 * ij + 2],
                         g.Stab + (a * N + j) * 6);
               }

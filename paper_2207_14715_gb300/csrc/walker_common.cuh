@@ -279,22 +279,28 @@ __device__ __forceinline__ void term_ratios(const SysDev& s, int lane, const dou
 //   rEN [N][Nn] r_ia, eEN [N][Nn][3] (r_i - r_a)/r_ia, Stab [Nn][N][6] Rbar(r_ia)^q,
 //   Ssum [Nn][6] sum_i Rbar(r_ia)^q.
 // Returns this lane's share of the Coulomb potential V_ee + V_en.
+// The electron-pair tables have rows of an odd length ld (N or N + 1), so that lanes on
+// consecutive electrons i reading entry (i, j) fall in different shared-memory banks; entry
+// (i, j) is at ee(i, j) (eEE: 3 ee(i, j) + component).
 template <class Tb> struct GeoTables {
   Tb *rEE, *uEE, *iEE, *eEE, *rEN, *eEN, *Stab, *Ssum, *SsumLo;
+  int ld;
   __device__ __forceinline__ GeoTables(Tb* geo, int N, int Nn) {
+    ld = N | 1;
     rEE = geo;
-    uEE = rEE + N * N;
-    iEE = uEE + N * N;
-    eEE = iEE + N * N;
-    rEN = eEE + 3 * N * N;
+    uEE = rEE + N * ld;
+    iEE = uEE + N * ld;
+    eEE = iEE + N * ld;
+    rEN = eEE + 3 * N * ld;
     eEN = rEN + N * Nn;
     Stab = eEN + 3 * N * Nn;
     Ssum = Stab + 6 * N * Nn;
     SsumLo = Ssum + 6 * Nn;
   }
+  __device__ __forceinline__ int ee(int i, int j) const { return i * ld + j; }
 };
 template <class Tb> __host__ __device__ constexpr int geo_elems(int N, int Nn) {
-  return 6 * N * N + 4 * N * Nn + 6 * N * Nn + 12 * Nn;
+  return 6 * N * (N | 1) + 4 * N * Nn + 6 * N * Nn + 12 * Nn;
 }
 
 // Electron coordinates of one walker as the kernels read them: double in the FP64 form;
@@ -352,7 +358,7 @@ __device__ __forceinline__ double build_geometry(const SysDev& s, int lane, cons
   const int N = s.N, Nn = s.Nn;
   Tb V_loc = 0;
   for (DivStep ij(lane, N); ij.hi < N; ij.next(N, stride)) {
-    const int i = ij.hi, j = ij.lo, p = i * N + j;
+    const int i = ij.hi, j = ij.lo, p = g.ee(i, j);
     if (i == j) {
       g.rEE[p] = (Tb)0; g.uEE[p] = (Tb)1; g.iEE[p] = (Tb)0;
       g.eEE[3 * p] = g.eEE[3 * p + 1] = g.eEE[3 * p + 2] = (Tb)0;
