@@ -35,8 +35,8 @@ SEED = 20220728 + 1
 WALKER_KERNEL_SOURCES = ["kernels.cu", "eval_jastrow.cu", "eval_orbitals.cu", "eval_det.cu", "walker_common.cuh",
                          "kernels.h", "wf_device.cuh", "dsfloat.cuh", "vbqmc_internal.h"]
 PROFILED_TRAFFIC = {
-    "sources_sha256": "19686e597c7292a1144bb63cbb344fb18688d805da368d734d12f53462eb5d4f",
-    "bytes_per_walker": {"sweep": 10785.7, "det": 26172.2, "orbitals": 8943.9},
+    "sources_sha256": "38ffab3c0fa0c96d1b86b9a2b2c2d4973f454b418bf64bd493aa18f0a67087fe",
+    "bytes_per_walker": {"sweep": 10813.3, "det": 26153.6, "orbitals": 8939.6},
 }
 
 
