@@ -132,6 +132,13 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   BlobBuilder bb;
   std::vector<float> coef_f(h.orb_coef.begin(), h.orb_coef.end());
   std::vector<float> evq_f(h.evq_coef.begin(), h.evq_coef.end());
+  std::vector<int> sh_pack;
+  for (int sh : h.sh_by_l) {
+    const float z = (float)h.sh_zeta[sh];
+    int zb;
+    std::memcpy(&zb, &z, sizeof(zb));
+    sh_pack.insert(sh_pack.end(), {h.sh_center[sh] | (h.sh_l[sh] << 16), h.sh_first[sh], sh, zb});
+  }
   std::vector<float> een_cf(h.een_c.begin(), h.een_c.end());
   auto split = [](const std::vector<double>& v) {
     std::vector<float> o(2 * v.size());
@@ -169,7 +176,7 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
                o_evqf = bb.add(evq_f), o_dc = bb.add(h.det_chunk), o_dco = bb.add(h.det_chunk_off),
                o_zds = bb.add(zeta_ds), o_nds = bb.add(norm_ds), o_cds = bb.add(coef_ds), o_nucds = bb.add(nuc_ds),
                o_zf = bb.add(zeta_f), o_nf = bb.add(norm_f), o_jaf = bb.add(jas_af), o_jbf = bb.add(jas_bf),
-               o_ebf = bb.add(een_Bf), o_nzf = bb.add(nuc_zf), o_nsh = bb.add(h.nuc_sh), o_sbl = bb.add(h.sh_by_l),
+               o_ebf = bb.add(een_Bf), o_nzf = bb.add(nuc_zf), o_nsh = bb.add(h.nuc_sh), o_sbl = bb.add(h.sh_by_l), o_shp = bb.add(sh_pack),
                o_jads = bb.add(split(h.jas_a)), o_jbds = bb.add(split(h.jas_b)), o_ecds = bb.add(split(h.een_c)), o_tx0 = bb.add(h.tab_x[0]),
                o_tx1 = bb.add(h.tab_x[1]), o_td0 = bb.add(h.tab_det[0]), o_td1 = bb.add(h.tab_det[1]);
   cudaError_t e = cudaMalloc(&ls.blob, bb.bytes.size());
@@ -206,6 +213,7 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.sh_first = (const int*)(B + o_sh_first);
   d.nuc_sh = (const int*)(B + o_nsh);
   d.sh_by_l = (const int*)(B + o_sbl);
+  d.sh_pack_f = (const int*)(B + o_shp);
   d.max_nuc_mu = h.max_nuc_mu;
   d.sh_zeta = (const double*)(B + o_sh_zeta);
   d.sh_norm = (const double*)(B + o_sh_norm);

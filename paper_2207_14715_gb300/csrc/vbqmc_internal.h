@@ -113,6 +113,7 @@ struct SysDev {
   const int* sh_l;
   const int* sh_first;
   const int* sh_by_l;
+  const int* sh_pack_f;                // [S][4] in the order of sh_by_l: center | l << 16, first function, shell, float bits of zeta
   const int* nuc_sh;                   // [Nn][4], see SysHost
   int max_nuc_mu;
   const double* sh_zeta;

@@ -65,12 +65,12 @@ template <bool DERIV>
 __device__ __forceinline__ void basis_at_f(const SysDev& s, int lane, const dsf* r3, float* bv, float* bx, float* by,
                                            float* bz, float* bl, int cs = 1) {
   for (int t = lane; t < s.S; t += 32) {
-    const int sh = __ldg(s.sh_by_l + t);
-    const int c = __ldg(s.sh_center + sh);
-    const int f = __ldg(s.sh_first + sh);
+    // one 16-byte record per shell, in the order of l
+    const int4 p = __ldg(reinterpret_cast<const int4*>(s.sh_pack_f) + t);
+    const int c = p.x & 0xffff, l = p.x >> 16, f = p.y, sh = p.z;
     const float dx = ds_diff_f(r3[0], nuc_coord_ds(s, c, 0)), dy = ds_diff_f(r3[1], nuc_coord_ds(s, c, 1)),
                 dz = ds_diff_f(r3[2], nuc_coord_ds(s, c, 2));
-    gto_shell<float, DERIV>(__ldg(s.sh_l + sh), __ldg(s.sh_zeta_f + sh), s.sh_norm_f + 6 * sh, dx, dy, dz,
+    gto_shell<float, DERIV>(l, __int_as_float(p.w), s.sh_norm_f + 6 * sh, dx, dy, dz,
                             bv + f * cs, DERIV ? bx + f * cs : nullptr, DERIV ? by + f * cs : nullptr,
                             DERIV ? bz + f * cs : nullptr, DERIV ? bl + f : nullptr, cs);
   }
