@@ -35,8 +35,8 @@ SEED = 20220728 + 1
 WALKER_KERNEL_SOURCES = ["kernels.cu", "eval_jastrow.cu", "eval_orbitals.cu", "eval_det.cu", "walker_common.cuh",
                          "kernels.h", "wf_device.cuh", "dsfloat.cuh", "vbqmc_internal.h"]
 PROFILED_TRAFFIC = {
-    "sources_sha256": "38ffab3c0fa0c96d1b86b9a2b2c2d4973f454b418bf64bd493aa18f0a67087fe",
-    "bytes_per_walker": {"sweep": 10813.3, "det": 26153.6, "orbitals": 8939.6},
+    "sources_sha256": "92956cc090a16ed8fbd11187cf970dff838bc380f672b9c8d7f4c9c6429d1054",
+    "bytes_per_walker": {"sweep": 10792.4, "det": 26175.8, "orbitals": 8967.0},
 }
 
 
