@@ -57,7 +57,7 @@ typedef struct vbqmc_ctx vbqmc_ctx;  /* opaque; owned by the library */
 /* System description: the inputs of Eqs. PsiJVBSCF, PhiI and PsiJVBp (Sec. 2.1-2.2).
  * Every pointer is a host array, read during vbqmc_set_system only. */
 typedef struct vbqmc_system_desc {
-  int Nn, n_elem;
+  int Nn, n_elem;          /* 1 <= Nn < 65536 */
   const double* nuc_xyz;   /* [Nn][3] bohr */
   const double* nuc_Z;     /* [Nn] */
   const int* nuc_elem;     /* [Nn] element index in [0, n_elem); Jastrow a and theta are per element */

@@ -276,6 +276,7 @@ static void make_quads(SysHost& s) {
 int build_system(const vbqmc_system_desc* d, SysHost& s, std::string& err) {
   VBQ_REQUIRE(d != nullptr, "null system description");
   VBQ_REQUIRE(d->Nn >= 1 && d->n_elem >= 1 && d->S >= 1 && d->Norb >= 1 && d->Nvb >= 1, "empty system");
+  VBQ_REQUIRE(d->Nn < 65536, "more than 65535 nuclei");
   VBQ_REQUIRE(d->n_elem <= kMaxElem, "too many elements");
   VBQ_REQUIRE(d->Nup >= 0 && d->Ndn >= 0 && d->Nup + d->Ndn >= 1, "bad electron counts");
   if (d->Nup > kMaxSpinN || d->Ndn > kMaxSpinN || d->Nup + d->Ndn > kMaxN) {
