@@ -97,6 +97,12 @@ def test_invalid_inputs_are_rejected(vb):
     bad.kappa_kl = np.array([[1, 1]], np.int32)
     with pytest.raises(vb.VbqmcError, match="excitation"):
         vb.inspect_system(bad)
+    # the packed shell records hold the center index in 16 bits
+    bad = S.h2_vb()
+    n = 65536
+    bad.nuc_xyz, bad.nuc_Z, bad.nuc_elem = np.zeros((n, 3)), np.ones(n), np.zeros(n, np.int32)
+    with pytest.raises(vb.VbqmcError, match="65535 nuclei"):
+        vb.inspect_system(bad)
 
 
 def test_binding_exposes_the_entry_points(vb):
