@@ -238,7 +238,7 @@ __device__ __forceinline__ void dettab_body(const SysDev& s, const DetTabLayout&
     if (n == 0) continue;
     const int* ref = s.det_ev[sp];
     const int* xl = s.tab_x[sp];
-    const double* B = Bd[sp];
+    double* B = Bd[sp];
     const double* T = TX[sp];
     // Gamma[x][o] = sum over determinants with o in S_u and x in Q_u of W_u (M_u^-1)[x][o]
     for (int i = lane; i < nx * n; i += 32) {
@@ -265,34 +265,37 @@ __device__ __forceinline__ void dettab_body(const SysDev& s, const DetTabLayout&
       Gam[i] = h;
     }
     __syncwarp();
+    // grad_i ln|Phi| = sum_o B[o][i] grad phi_o + sum_x h[x][i] (grad phi_x - sum_o T[o][x] grad phi_o)
+    //               = sum_o C[o][i] grad phi_o + sum_x h[x][i] grad phi_x,  C = B - T h
+    // (C in double, in place of B, which is not read again; the sums in the bulk type: the
+    // gradient feeds the drift and the Jastrow-parameter derivatives, not E_L)
+    for (int i = lane; i < n * n; i += 32) {
+      const int o = i / n, e = i - o * n;
+      double c = B[i];
+      for (int x = 0; x < nx; ++x) c = fma(-T[o * nx + x], Gam[x * n + e], c);
+      B[i] = c;
+    }
+    __syncwarp();
     for (int e = lane; e < n; e += 32) {
       const Tb* ob = OB + ((size_t)w * N + e0 + e) * 5 * nev;
-      double g[3] = {0.0, 0.0, 0.0};
+      Tb g[3] = {0, 0, 0};
       for (int o = 0; o < n; ++o) {
         const int col = __ldg(ref + o);
-        const double b = B[o * n + e];
+        const Tb c = (Tb)B[o * n + e];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) g[c] = fma(b, (double)ob[(1 + c) * nev + col], g[c]);
+        for (int d = 0; d < 3; ++d) g[d] += c * ob[(1 + d) * nev + col];
       }
       for (int x = 0; x < nx; ++x) {
-        const double h = Gam[x * n + e];
-        if (h == 0.0) continue;
+        const Tb h = (Tb)Gam[x * n + e];
         const int colx = __ldg(xl + x);
-        double cx[3] = {(double)ob[nev + colx], (double)ob[2 * nev + colx], (double)ob[3 * nev + colx]};
-        for (int o = 0; o < n; ++o) {
-          const double t = T[o * nx + x];
-          const int col = __ldg(ref + o);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) cx[c] = fma(-t, (double)ob[(1 + c) * nev + col], cx[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) g[c] = fma(h, cx[c], g[c]);
+        for (int d = 0; d < 3; ++d) g[d] += h * ob[(1 + d) * nev + colx];
       }
       const int i = e0 + e;
       const double G0 = (double)G[3 * i], G1 = (double)G[3 * i + 1], G2 = (double)G[3 * i + 2];
-      vg[3 * i] = G0 + g[0];
-      vg[3 * i + 1] = G1 + g[1];
-      vg[3 * i + 2] = G2 + g[2];
+      vg[3 * i] = G0 + (double)g[0];
+      vg[3 * i + 1] = G1 + (double)g[1];
+      vg[3 * i + 2] = G2 + (double)g[2];
       kin_loc += (double)JL[(size_t)w * N + i] + G0 * G0 + G1 * G1 + G2 * G2;
     }
     __syncwarp();
