@@ -264,6 +264,45 @@ def uniforms2(seed, walker, step, slot, system, purpose):
 # ----------------------------------------------------------------------------------
 # Linear method (Sec. 2.3.1), written term by term as Eqs. Hi0, H0j, Hij, Sij print them.
 # ----------------------------------------------------------------------------------
+def structure_ratios(spec, R, nthreads: int | None = None):
+    """Psi_I/Psi_0 = Phi_I/Phi of every VB structure I at R (W, N, 3) -> (W, Nvb) (Sec. 2.4; the
+    Jastrow factor cancels).  The c_I derivative of Eq. PsiJVBp is exactly this ratio, so the
+    evaluation of a copy of the system with every structure coefficient as a parameter (and no
+    Jastrow or orbital parameters) returns them as its first Nvb derivative columns."""
+    import dataclasses
+    nvb = len(spec.c_vb)
+    allc = dataclasses.replace(spec, cparam=np.arange(nvb, dtype=np.int32), jas_param=False,
+                               kappa_kl=np.zeros((0, 2), np.int32))
+    return evaluate(allc, R, derivs=True, nthreads=nthreads)["O"][:, :nvb]
+
+
+def structure_overlap(ratios, w=None):
+    """S_IJ = <(Psi_I/Psi_0)(Psi_J/Psi_0)> over the samples (Sec. 2.4, the VMC estimate), with
+    weights w (None: all 1), as the average of the products sample by sample."""
+    X = np.asarray(ratios, np.float64)
+    w = np.ones(X.shape[0]) if w is None else np.asarray(w, np.float64)
+    S = np.zeros((X.shape[1], X.shape[1]))
+    for m in range(X.shape[0]):
+        S += w[m] * np.outer(X[m], X[m])
+    return S / w.sum()
+
+
+def structure_weights(S, c):
+    """Chirgwin-Coulson and Loewdin weights of the JVB structures (Sec. 2.4) as defined there:
+    w_CC_I = sum_J c_I c_J S_IJ / <Psi_0|Psi_0>, and with cbar_K = sum_I c_I (S^1/2)_IK,
+    w_L_K = cbar_K^2 / sum_K cbar_K^2; S^1/2 by scipy.linalg.sqrtm."""
+    import scipy.linalg
+    S = np.asarray(S, np.float64)
+    c = np.asarray(c, np.float64)
+    n = len(c)
+    norm = sum(c[I] * c[J] * S[I, J] for I in range(n) for J in range(n))
+    w_cc = np.array([sum(c[I] * c[J] * S[I, J] for J in range(n)) for I in range(n)]) / norm
+    half = np.real(scipy.linalg.sqrtm(S))
+    cbar = np.array([sum(c[I] * half[I, K] for I in range(n)) for K in range(n)])
+    w_l = cbar ** 2 / np.sum(cbar ** 2)
+    return w_cc, w_l
+
+
 def lin_matrices(O, dEL, EL, w=None):
     """Sample estimates from O[M][P] = Psi_j/Psi_0, dEL[M][P] = E_L,j, EL[M] (weights w optional).
     Returns dict E0, gL, gR, H (P x P, nonsymmetric), S (P x P)."""

@@ -326,6 +326,80 @@ class Context:
                                                    _ptr(H), _stream(stream)))
         return {"E0": E0, "gL": gL, "gR": gR, "S": S, "H": H}
 
+    def structure_overlap(self, precision, O, cparam, c_vb, weights=None, stream=None):
+        """Overlap matrix of the JVB structures (Sec. 2.4), S_IJ = <(Psi_I/Psi_0)(Psi_J/Psi_0)>
+        over M samples, from derivative rows O [M, P] (the mode's bulk type, as the evaluation
+        writes them) whose first len(cparam) columns are Psi_I/Psi_0 = Phi_I/Phi for the
+        structures cparam (the c_I derivatives of Eq. PsiJVBp).  On the device: the column means
+        (vbqmc_weighted_colsum) and the centred products <Ot_I Ot_J> (the S output of
+        vbqmc_accumulate_lin_matrices); on the host, Nvb x Nvb: S = <Ot Ot> + <O><O>^T, and the
+        row of a structure missing from cparam (at most one) from sum_I c_I Psi_I/Psi_0 = 1,
+        which holds on every sample.  weights [M] float64 CUDA tensor or None (all 1).  The
+        centred products carry the linear-method kernel's accuracy (FP32-pipe products: about
+        2e-6 of the matrix scale with double rows).  Returns an [Nvb, Nvb] float64 numpy array."""
+        import torch
+        M, P = O.shape
+        cp = [int(I) for I in cparam]
+        if len(cp) > P:
+            raise VbqmcError("cparam longer than the derivative rows")
+        if not cp:  # a single structure: Psi_0 = c_0 Psi_1 everywhere
+            return assemble_structure_overlap(np.zeros(0), np.zeros((0, 0)), cp, c_vb)
+        dev = O.device
+        ones = torch.ones(M, dtype=torch.float64, device=dev)
+        ga = ones if weights is None else weights
+        wsum = float(M)
+        if weights is not None:
+            t = torch.empty(1, dtype=torch.float64, device=dev)
+            self.weighted_colsum(weights, ones.reshape(M, 1), t, stream=stream)
+            wsum = float(t.item())
+        n = len(cp)
+        Os = O[:, :n].contiguous()  # the structure columns alone (the products' scale is theirs)
+        total = torch.empty(n, dtype=torch.float64, device=dev)
+        self.weighted_colsum(ga, Os, total, stream=stream)
+        lin = self.accumulate_lin_matrices(precision, Os, Os, torch.zeros_like(ones), weights=weights, stream=stream)
+        return assemble_structure_overlap(total.cpu().numpy() / wsum, lin["S"].cpu().numpy(), cp, c_vb)
+
+
+def assemble_structure_overlap(mean, cov, cparam, c_vb):
+    """Host step of Context.structure_overlap: from the means <Psi_I/Psi_0> and the centred
+    products of the structures cparam, S_IJ = cov_IJ + mean_I mean_J; a structure I0 missing
+    from cparam gets <R_I0 R_J> = (<R_J> - sum_I c_I <R_I R_J>) / c_I0 and
+    <R_I0> = (1 - sum_I c_I <R_I>) / c_I0 (R_I = Psi_I/Psi_0, sum over I in cparam)."""
+    c = np.asarray(c_vb, np.float64)
+    nvb = len(c)
+    cp = [int(I) for I in cparam]
+    missing = [I for I in range(nvb) if I not in cp]
+    if len(missing) > 1 or len(set(cp)) != len(cp):
+        raise VbqmcError("structure overlap needs every structure but at most one in cparam")
+    mean = np.asarray(mean, np.float64)
+    cov = np.asarray(cov, np.float64)
+    Scp = 0.5 * (cov + cov.T) + np.outer(mean, mean)
+    S = np.zeros((nvb, nvb))
+    S[np.ix_(cp, cp)] = Scp
+    if missing:
+        i0 = missing[0]
+        cc = c[cp]
+        row = (mean - cc @ Scp) / c[i0]
+        S[i0, cp] = row
+        S[cp, i0] = row
+        S[i0, i0] = ((1.0 - cc @ mean) / c[i0] - cc @ row) / c[i0]
+    return S
+
+
+def structure_weights(S, c_vb):
+    """Chirgwin-Coulson and Loewdin weights of the JVB structures (Sec. 2.4) from their overlap
+    S [Nvb, Nvb]: w_CC = c * (S c) / (c^T S c); w_L = cbar^2 / |cbar|^2 with cbar = S^(1/2) c,
+    the square root through the eigendecomposition of S (eigenvalues of rounding size below 0
+    clipped).  Host routine on an Nvb x Nvb matrix.  Returns (w_CC, w_L)."""
+    S = 0.5 * (np.asarray(S, np.float64) + np.asarray(S, np.float64).T)
+    c = np.asarray(c_vb, np.float64)
+    Sc = S @ c
+    w_cc = c * Sc / (c @ Sc)
+    lam, U = np.linalg.eigh(S)
+    cbar = (U * np.sqrt(np.clip(lam, 0.0, None))) @ U.T @ c
+    w_l = cbar ** 2 / (cbar @ cbar)
+    return w_cc, w_l
+
 
 def accumulate_lin_matrices_noalloc(precision, O, dEL, eloc, weights, E0, gL, gR, S, H, stream=None):
     """vbqmc_accumulate_lin_matrices_noalloc: the linear-method estimators into caller-owned
