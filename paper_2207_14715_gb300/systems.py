@@ -109,6 +109,26 @@ def _structures(lst):
             np.array(uo, np.int32), np.array(un, np.int32))
 
 
+def structure_subset(spec: SystemSpec, keep) -> SystemSpec:
+    """The same system with only the VB structures `keep` (in that order, with their
+    coefficients): the wave function of a "diabatic" state restricted to a subset of Lewis
+    structures, whose VMC energy minus that of the full expansion is a resonance energy (Sec. 2.4,
+    Sec. 3).  Structure-coefficient parameters follow their structures (those of dropped
+    structures are removed)."""
+    keep = [int(I) for I in keep]
+    lst = []
+    for I in keep:
+        ina = spec.inact[spec.inact_off[I]:spec.inact_off[I + 1]]
+        prs = spec.pairs[spec.pair_off[I]:spec.pair_off[I + 1]]
+        un = spec.unp[spec.unp_off[I]:spec.unp_off[I + 1]]
+        lst.append((list(ina), [tuple(p) for p in prs], list(un)))
+    io, ina, po, prs, uo, un = _structures(lst)
+    new_index = {I: k for k, I in enumerate(keep)}
+    cparam = np.array([new_index[int(I)] for I in spec.cparam if int(I) in new_index], np.int32)
+    return dataclasses.replace(spec, name=spec.name + "_subset", c_vb=np.asarray(spec.c_vb, np.float64)[keep].copy(),
+                               inact_off=io, inact=ina, pair_off=po, pairs=prs, unp_off=uo, unp=un, cparam=cparam)
+
+
 def _center_shells(rng, elem_of_center, shell_ls, zeta_lo=0.1, zeta_hi=20.0):
     """Shells per center with exponents log-uniform in [zeta_lo, zeta_hi], drawn once per element."""
     zeta_elem = {}

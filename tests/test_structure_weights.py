@@ -1,6 +1,7 @@
 """Structure overlap and weights of the JVB structures (arXiv:2207.14715, Sec. 2.4): the oracle's
 ratios Psi_I/Psi_0 and both sides' host formulas against closed forms and identities.  (The GPU
 side of the overlap is in test_gpu_structure_weights.py.)"""
+import dataclasses
 import math
 
 import numpy as np
@@ -64,16 +65,16 @@ def test_oracle_ratios_resolve_the_wave_function(orc, maker, W):
     assert abs(c @ Sm @ c - 1) < 1e-10
 
 
-def test_oracle_single_structure():
+def test_oracle_single_structure(orc):
     """One structure: Psi_0 = c_0 Psi_1, so the ratio is 1/c_0 everywhere and the weight is 1."""
-    from oracle import oracle as orc
     spec = S.two_electron_product(2.0, 0.9)
     assert len(spec.c_vb) == 1
     R = S.initial_walkers(spec, 10, 3)
     X = orc.structure_ratios(spec, R)
     np.testing.assert_allclose(X, 1.0 / spec.c_vb[0], rtol=1e-13)
     w_cc, w_l = orc.structure_weights(orc.structure_overlap(X), spec.c_vb)
-    np.testing.assert_allclose(w_cc, [1.0]) and np.testing.assert_allclose(w_l, [1.0])
+    np.testing.assert_allclose(w_cc, [1.0])
+    np.testing.assert_allclose(w_l, [1.0])
 
 
 def test_host_assembly_recovers_the_missing_structure(orc):
@@ -97,3 +98,19 @@ def test_host_assembly_recovers_the_missing_structure(orc):
             np.testing.assert_allclose(got, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
     with pytest.raises(vbqmc.VbqmcError):
         vbqmc.assemble_structure_overlap(mean[:1], cov[:1, :1], [0], c)
+
+
+@pytest.mark.parametrize("maker, keep", [(S.h2_vb, [0]), (S.h2_vb, [1, 2]), (S.ethylene_vb, [0, 2, 5]),
+                                         (S.small_open_shell, [3, 1])])
+def test_structure_subset_is_the_expansion_with_the_others_removed(orc, maker, keep):
+    """A subset of structures (the wave function of a resonance-energy diabatic state) evaluates
+    like the full expansion with the other coefficients set to zero: same ln|Psi|, sign and E_L."""
+    spec = maker()
+    sub = S.structure_subset(spec, keep)
+    zeroed = dataclasses.replace(spec, c_vb=np.where(np.isin(np.arange(len(spec.c_vb)), keep), spec.c_vb, 0.0))
+    R = S.initial_walkers(spec, 8, 4)
+    a, b = orc.evaluate(sub, R), orc.evaluate(zeroed, R)
+    np.testing.assert_allclose(a["logpsi"], b["logpsi"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(a["sign"], b["sign"])
+    np.testing.assert_allclose(a["eloc"], b["eloc"], rtol=1e-10, atol=1e-10)
+    assert len(sub.c_vb) == len(keep)
