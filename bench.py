@@ -243,13 +243,9 @@ def barrier(ws):
 
 
 def allmax(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    """The slowest rank's time (ranks.max_over_ranks over NCCL)."""
+    from paper_2207_14715_gb300 import ranks
+    return x if ws == 1 else ranks.max_over_ranks(x, device="cuda")
 
 
 def cpu_baseline(spec, R_host, seconds_hint=15.0):
@@ -320,7 +316,8 @@ def run_ours(args, ws, rank, local):
     state = torch.zeros((W, ctx.walker_state_size(0)), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    woff = rank * W
+    from paper_2207_14715_gb300 import ranks
+    woff = ranks.walker_offset(rank, W)
     step_counter = [0]
 
     def step(prec, ev=None):
