@@ -110,11 +110,29 @@ def work_model(spec, info):
     }
 
 
-def peaks(sm_mhz):
-    """ALU peaks from unit counts and the SM clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA, and the
-    FP64 rate of 1.25 TFLOP/s at the 2070 MHz maximum clock, both scaled to the measured clock."""
-    f = sm_mhz * 1e6
-    return {"f32": 152 * 128 * 2 * f, "f64": 1.25e12 * (sm_mhz / 2070.0)}
+def measure_peaks(vbqmc, device):
+    """ALU peaks measured on this GPU (vbqmc_measure_alu_peaks: FP32 and FP64 FMA chains and
+    special-function exponentials over the whole device, CUDA events), with the SM clock sampled
+    while the probes ran."""
+    sampler = ClockSampler(device)
+    sampler.start()
+    pk = vbqmc.measure_alu_peaks(device)
+    clocks = sampler.stop()
+    return {"f32": pk["fp32_tflops"] * 1e12, "f64": pk["fp64_tflops"] * 1e12, "exp": pk["exp_tops"] * 1e12,
+            "sms": pk["sms"], "sm_mhz": clocks.get("sm_mhz"), "reasons": clocks.get("reasons", [])}
+
+
+def reblocked_error(x):
+    """Standard error of the mean of a correlated series by blocking (Flyvbjerg-Petersen): pairs
+    of neighbours are averaged level after level; the error is the largest estimate over the
+    levels that keep at least 16 blocks."""
+    import numpy as np
+    y = np.asarray(x, np.float64)
+    errs = []
+    while len(y) >= 16:
+        errs.append(y.std(ddof=1) / np.sqrt(len(y)))
+        y = 0.5 * (y[0:len(y) - len(y) % 2:2] + y[1:len(y) - len(y) % 2:2])
+    return max(errs) if errs else float("nan")
 
 
 # --------------------------------------------------------------------------------------
@@ -130,7 +148,8 @@ class ClockSampler:
         self.samples = []
         self.thread = None
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), "vbqmc_clocks_%d.csv" % os.getpid())
 
     def _nvml_handle(self):
         import ctypes
@@ -174,7 +193,6 @@ class ClockSampler:
             self.thread.start()
             return
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
@@ -305,6 +323,7 @@ def run_ours(args, ws, rank, local):
     P = spec.n_params
     ctx = vbqmc.create(local)
     ctx.set_system(0, spec)
+    pk = measure_peaks(vbqmc, local)
     R = torch.tensor(S.initial_walkers(spec, W, SEED + 1000 * rank), device=dev)
     lp = torch.zeros(W, dtype=torch.float64, device=dev)
     sg, el = torch.zeros_like(lp), torch.zeros_like(lp)
@@ -392,8 +411,8 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
     t_e2e = allmax(time.perf_counter() - t0, ws)
     barrier(ws)
-    mhz = (results["mixed"]["clocks"] or {}).get("sm_mhz") or 2070.0
-    forces = force_timing(ctx, vbqmc, spec, info, R, args.force_steps, mhz) if args.force_steps > 0 else None
+    forces = force_timing(ctx, vbqmc, spec, info, R, args.force_steps, pk) if args.force_steps > 0 else None
+    eta = efficiency(ctx, vbqmc, spec, R, woff, args.eta_steps) if args.eta_steps > 0 else None
     dmc = dmc_timing(ctx, vbqmc, R, el, args.dmc_steps) if args.dmc_steps > 0 else None
     batched = batched_timing(vbqmc, dev, args.steps) if args.batch_steps > 0 else None
     dmc48 = dmc48_timing(vbqmc, dev, args.steps, args.dmc48_walkers) if args.dmc48_steps > 0 else None
@@ -408,22 +427,30 @@ def run_ours(args, ws, rank, local):
     value64 = ws * W * f64["steps"] / (f64["ms"] * 1e-3)
     clocks = m["clocks"] or {}
     sm_mhz = clocks.get("sm_mhz") or 2070.0
-    pk = peaks(sm_mhz)
-    # dominant kernel of the mixed step
+    # per-kernel fractions of the measured ALU peaks (the walker path is ALU-bound): each kernel
+    # against the pipe its algorithmic work mostly runs on in the mixed form
     km = m["kernel_ms"]
+    kroof = {}
+    for kname, dur_ms in km.items():
+        if dur_ms <= 0:
+            continue
+        w64 = model[kname]["mixed"]["f64"] * W
+        w32 = model[kname]["mixed"]["f32"] * W
+        f64_, f32_ = w64 / (dur_ms * 1e-3) / pk["f64"], w32 / (dur_ms * 1e-3) / pk["f32"]
+        pipe = "fp64" if f64_ >= f32_ else "fp32"
+        ach = (w64 if pipe == "fp64" else w32) / (dur_ms * 1e-3)
+        kroof[kname] = {"pipe": pipe, "achieved_tflops": ach / 1e12, "frac": max(f64_, f32_),
+                        "other_pipe_frac": min(f64_, f32_), "ms": dur_ms}
     dom = max(km, key=km.get)
-    dur = km[dom] * 1e-3
-    w64 = model[dom]["mixed"]["f64"] * W
-    w32 = model[dom]["mixed"]["f32"] * W
-    frac64, frac32 = w64 / dur / pk["f64"], w32 / dur / pk["f32"]
-    if frac64 >= frac32:
-        roof = {"bound": "alu", "pipe": "fp64", "achieved": w64 / dur / 1e12, "peak": pk["f64"] / 1e12}
-    else:
-        roof = {"bound": "alu", "pipe": "fp32", "achieved": w32 / dur / 1e12, "peak": pk["f32"] / 1e12}
-    roof.update({"unit": "TFLOP/s", "frac": roof["achieved"] / roof["peak"], "traffic": walker_kernel_traffic(dom, W),
-                 "kernel": "%s_kernel<float>" % dom,
-                 "peak_source": "derived from unit counts at the measured median SM clock %.0f MHz" % sm_mhz,
-                 "other_pipe_frac": min(frac64, frac32)})
+    r = kroof[dom]
+    roof = {"bound": "alu", "pipe": r["pipe"], "achieved": r["achieved_tflops"],
+            "peak": (pk["f64"] if r["pipe"] == "fp64" else pk["f32"]) / 1e12, "unit": "TFLOP/s", "frac": r["frac"],
+            "traffic": walker_kernel_traffic(dom, W), "kernel": "%s_kernel<float>" % dom,
+            "peak_source": "measured on this GPU by vbqmc_measure_alu_peaks (FP64 %.3f, FP32 %.1f TFLOP/s, "
+                           "exp %.2f T/s, %d SMs; SM clock %s MHz during the probes, %.0f MHz during the step)"
+                           % (pk["f64"] / 1e12, pk["f32"] / 1e12, pk["exp"] / 1e12, pk["sms"], pk["sm_mhz"],
+                              sm_mhz),
+            "other_pipe_frac": r["other_pipe_frac"]}
     cb = cpu_baseline(spec, R_host.numpy()) if (ws == 1 and not args.no_cpu_baseline) else None
     bi = W * spec.N * 3 * 8
     bo = W * spec.N * 3 * 8 + W * 8
@@ -439,9 +466,13 @@ def run_ours(args, ws, rank, local):
         "kernel_ms": {k: round(v, 4) for k, v in km.items()},
         "acceptance": m["acc"], "E_L_mean": m["E_mean"],
         "roofline": roof,
+        "kernel_roofline": kroof,
+        "efficiency": eta,
         "cpu_baseline": cb,
         "e2e": {"value": ws * W * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bi,
-                "d2h_bytes_per_step": bo},
+                "d2h_bytes_per_step": bo,
+                "note": "per step: walker positions in, positions and E_L out; the derivative rows O and "
+                        "dE_L/dp (2 x 16384 x 216 floats) stay in HBM for the device-side linear method"},
         "linear_method": lin,
         "nuclear_derivs": forces,
         "dmc": dmc,
@@ -452,6 +483,44 @@ def run_ours(args, ws, rank, local):
                    "reasons": clocks.get("reasons", [])},
     }
     print(json.dumps(line), flush=True)
+
+
+def efficiency(ctx, vbqmc, spec, R0, woff, steps):
+    """Statistical efficiency eta = 1 / (sigma^2 t) of the VMC energy in each form: 'steps'
+    walker-steps (sweep + evaluation with derivatives, carried inverses, refactorisation every
+    REFRESH steps) from the same equilibrated walkers, the walker-averaged E_L of every step,
+    sigma = its reblocked standard error of the mean, t = the CUDA-event time of the steps.
+    The ratio of the two etas compares the forms at equal statistical error."""
+    import numpy as np
+    import torch
+    W = R0.shape[0]
+    dev = R0.device
+    out = {}
+    for name, prec in (("mixed", vbqmc.MIXED), ("fp64", vbqmc.FP64)):
+        R = R0.clone()
+        lp, sg, el = (torch.zeros(W, dtype=torch.float64, device=dev) for _ in range(3))
+        O = torch.zeros((W, spec.n_params), dtype=vbqmc.deriv_dtype(prec), device=dev)
+        dE = torch.zeros_like(O)
+        st = torch.zeros((W, ctx.walker_state_size(0)), dtype=torch.float64, device=dev)
+        ctx.eval_walkers(0, prec, R, lp, sg, el, state_out=st)
+        emean = torch.zeros(steps, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(steps):
+            ctx.vmc_steps(0, prec, R, 1, spec.step, SEED + 7, step0=k, walker_offset=woff, refresh=REFRESH,
+                          state=st, state_valid=True, logpsi=lp, sign=sg, eloc=el, O=O, dEL=dE)
+            emean[k] = el.mean()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        e = emean.cpu().numpy()
+        sig = reblocked_error(e)
+        out[name] = {"E_mean": float(e.mean()), "sigma": sig, "seconds": t, "eta": 1.0 / (sig * sig * t)}
+    out["steps"] = steps
+    out["walkers"] = W
+    out["eta_ratio_mixed_over_fp64"] = out["mixed"]["eta"] / out["fp64"]["eta"]
+    return out
 
 
 def force_work(spec, info):
@@ -474,7 +543,7 @@ def force_work(spec, info):
     return jas + basis + contr + det
 
 
-def force_timing(ctx, vbqmc, spec, info, R, steps, sm_mhz=2070.0):
+def force_timing(ctx, vbqmc, spec, info, R, steps, pk):
     """d ln|Psi|/dR_a and dE_L/dR_a of every walker (one evaluation + the nucleus-derivative
     kernel) in both forms: CUDA events around the call and around a plain evaluation at the
     same positions; the difference is the derivative kernel."""
@@ -503,12 +572,12 @@ def force_timing(ctx, vbqmc, spec, info, R, steps, sm_mhz=2070.0):
             ms[what] = e0.elapsed_time(e1) / n
         kms = max(ms["forces"] - ms["eval"], 1e-6)
         flops = force_work(spec, info) * W
-        pk = peaks(sm_mhz)["f32" if prec == vbqmc.MIXED else "f64"]
+        pkk = pk["f32" if prec == vbqmc.MIXED else "f64"]
         out[name] = {"walkers_per_s": W / (ms["forces"] * 1e-3), "ms_per_call": ms["forces"],
                      "eval_ms": ms["eval"], "kernel_ms": kms,
                      "kernel_roofline": {"bound": "alu", "pipe": "fp32" if prec == vbqmc.MIXED else "fp64",
-                                         "achieved": flops / (kms * 1e-3) / 1e12, "peak": pk / 1e12,
-                                         "unit": "TFLOP/s", "frac": flops / (kms * 1e-3) / pk}}
+                                         "achieved": flops / (kms * 1e-3) / 1e12, "peak": pkk / 1e12,
+                                         "unit": "TFLOP/s", "frac": flops / (kms * 1e-3) / pkk}}
     return {"walkers": W, "nuclei": spec.Nn, **out}
 
 
@@ -672,6 +741,7 @@ def main():
     ap.add_argument("--dmc-steps", type=int, default=5, help="timed DMC steps (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3, help="batched-workload timing (0: skip)")
     ap.add_argument("--force-steps", type=int, default=3, help="nucleus-derivative timing (0: skip)")
+    ap.add_argument("--eta-steps", type=int, default=200, help="steps of the efficiency comparison (0: skip)")
     ap.add_argument("--dmc48-steps", type=int, default=3, help="48-electron DMC system timing (0: skip)")
     ap.add_argument("--dmc48-walkers", type=int, default=65536, help="walkers of the 48-electron timing")
     args = ap.parse_args()

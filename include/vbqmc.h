@@ -202,20 +202,25 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
                     void* O, void* dEL, void* stream);
 
 /* Fixed-node diffusion Monte Carlo steps (Sec. 2.3.2; mixed estimator Eq. E0DMCweights).  The
- * paper names its step algorithm without giving it; the step here, per walker, is
- *   R' = R + tau v(R) + sqrt(tau) z  (v = grad ln|Psi|, z standard normal per coordinate);
+ * paper runs the algorithm of Umrigar, Nightingale and Runge (J. Chem. Phys. 99, 2865 (1993))
+ * without printing it; the step here is an all-electron move that keeps that algorithm's
+ * limits on the drift and on the branching energy near the nodes.  Per walker:
+ *   vbar_i = v_i (-1 + sqrt(1 + 2 |v_i|^2 tau)) / (|v_i|^2 tau) per electron, v = grad ln|Psi|;
+ *   R' = R + tau vbar(R) + sqrt(tau) z  (z standard normal per coordinate);
  *   rejected if sign Psi(R') != sign Psi(R), else accepted with probability
  *   min(1, exp(2 (ln|Psi(R')| - ln|Psi(R)|)) G(R <- R') / G(R' <- R)),
- *   G(R' <- R) = exp(-|R' - R - tau v(R)|^2 / (2 tau));
- *   weight w = exp(-tau ((E_L(R) + E_L(R_kept)) / 2 - E_T)); copies = min(floor(w + u), 3),
+ *   G(R' <- R) = exp(-|R' - R - tau vbar(R)|^2 / (2 tau));
+ *   E_b = E_T + (E_L - E_T) |Vbar| / |V| (whole-walker drift vectors) at R and at the kept point;
+ *   weight w = exp(-tau ((E_b(R) + E_b(R_kept)) / 2 - E_T)); copies = min(floor(w + u), 3),
  *   children in parent order (weights are 1 after branching);
  *   then E_T = sum(w E_L) / sum(w) - (0.1 / tau) ln(population / target).
- * Random numbers: Philox4x32-10 keyed by seed, counter (walker index in the current population,
- * step0 + step, slot, (system_tag << 8) | purpose): slot e < N, purpose 2 -> (u0, u1) giving
- * z_x = r cos(2 pi u1), z_y = r sin(2 pi u1) with r = sqrt(-2 ln(1 - u0)); purpose 3 -> z_z from
- * the cosine branch of its pair; slot N, purpose 4 -> (u_acc, u_branch).  Uniforms as in
- * vbqmc_vmc_steps.  The evaluation at R' computes E_L and grad ln|Psi| in the given precision
- * mode; acceptance, weights and sums are double in both modes.
+ * Random numbers: Philox4x32-10 keyed by seed, counter (walker_offset + walker index in the
+ * current population, step0 + step, slot, (system_tag << 8) | purpose): slot e < N, purpose 2 ->
+ * (u0, u1) giving z_x = r cos(2 pi u1), z_y = r sin(2 pi u1) with r = sqrt(-2 ln(1 - u0)); purpose
+ * 3 -> z_z from the cosine branch of its pair; slot N, purpose 4 -> (u_acc, u_branch).  Uniforms as
+ * in vbqmc_vmc_steps.  Ranks of a multi-GPU run pass disjoint walker_offset ranges (e.g. rank x
+ * cap) so that their streams differ.  The evaluation at R' computes E_L and grad ln|Psi| in the
+ * given precision mode; acceptance, weights and sums are double in both modes.
  *   W_io     host, in/out: population (0 <= W <= cap)
  *   R        [cap][N][3] device, in/out: walkers (the first W rows are the population)
  *   E_T_io   host, in/out: trial energy
@@ -228,8 +233,9 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
  * ends the call early.  Returns VBQMC_ERR_CAPACITY if branching would exceed 'cap': the moves of
  * that step are applied, its branching is not, and W_io holds the population before it. */
 int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int cap, double* R, int nsteps, double tau,
-                    double* E_T_io, int target, uint64_t seed, uint32_t step0, uint32_t system_tag, double* sum_wE,
-                    double* sum_w, int* pop, double* e_trial, int64_t* accepted, void* stream);
+                    double* E_T_io, int target, uint64_t seed, uint32_t step0, uint32_t system_tag,
+                    uint32_t walker_offset, double* sum_wE, double* sum_w, int* pop, double* e_trial, int64_t* accepted,
+                    void* stream);
 
 /* Linear-method estimators from M samples (Sec. 2.3.1, Eqs. Hi0, H0j, Hij, Sij, feeding the
  * generalized eigenproblem Eq. geneigeqM).  With weights w (NULL: all 1), averages
@@ -240,12 +246,78 @@ int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int ca
  *   O, dEL  [M][P] device, element type double (VBQMC_FP64) or float (VBQMC_MIXED)
  *   eloc    [M] device double;  weights [M] device double or NULL
  *   E0 [1], gL [P], gR [P], S [P][P], H [P][P]: device double, out
- * Column sums are double; centred values are float; products are accumulated on the FP32
- * pipe in chunks of up to 16384 samples and the chunk partials summed in double.  The
- * context keeps a device workspace (grown on demand, synchronizing 'stream' when it grows). */
+ * Column sums are double; the centred values are rounded to float and split into high and low
+ * TF32 parts; the products run on the tensor cores (tcgen05, three TF32 MMAs per product,
+ * fresh accumulator per 32-sample step drained into FP32 registers) over chunks of samples,
+ * and the chunk partials are summed in double.  The context keeps a device workspace (grown on
+ * demand, synchronizing 'stream' when it grows). */
 int vbqmc_accumulate_lin_matrices(vbqmc_ctx* ctx, int precision, int P, int64_t M, const void* O, const void* dEL,
                                   const double* eloc, const double* weights, double* E0, double* gL, double* gR,
                                   double* S, double* H, void* stream);
+
+/* Parameter update of the linear method (Sec. 2.3.1, Eq. geneigeqM): the generalized
+ * eigenproblem A v = E B v of the (P+1) x (P+1) matrices
+ *   A = [[E0, gR^T / 2], [gL / 2, H + shift I]],   B = [[1, 0], [0, S]]
+ * (the outputs of vbqmc_accumulate_lin_matrices; shift >= 0 stabilises the step).  The answer
+ * is the lowest real eigenvalue E whose eigenvector v has |v_0| >= 1e-3 |v|, with v scaled to
+ * v_0 = 1: dp[j] = v_{j+1}, *e_lin = E.  Host routine in double (no device is touched):
+ * S's eigendecomposition (directions with eigenvalues <= P eps max are dropped as redundant
+ * parameters), the pencil reduced with S^-1/2 to a standard nonsymmetric problem, its
+ * eigenvalues by Hessenberg reduction and Francis double-shift QR, the eigenvectors by inverse
+ * iteration.  All arrays are host, row-major: gL, gR [P], H, S [P][P] in; dp [P] out.
+ * Errors: VBQMC_ERR_ARG for bad or non-finite input, an S with no positive eigenvalue, a QR
+ * iteration that does not converge or no admissible eigenvector (message in vbqmc_last_error). */
+int vbqmc_lin_solve(int P, double E0, const double* gL, const double* gR, const double* H, const double* S,
+                    double shift, double* dp, double* e_lin);
+
+/* Merges linear-method estimators computed on disjoint parts of a sample (e.g. the walkers of
+ * several ranks) into the estimators of the whole sample, as vbqmc_accumulate_lin_matrices
+ * defines them (Sec. 2.3.1, Eqs. Hi0..Sij).  Part r has weight sum wsum[r] (its sample count for
+ * unit weights), mean derivative row mean[r] = <O>_r, and E0, gL, gR, S, H centred on its own
+ * mean.  With the global mean mu = sum_r wsum_r mean_r / sum_r wsum_r and d_r = mean_r - mu, the
+ * parts are re-centred exactly (no cancellation) and averaged with weights wsum_r:
+ *   S = <S_r + d d^T>,  gL = <gL_r + 2 d E0_r>,  gR = gL + 2 <(gR_r - gL_r) / 2>,
+ *   H_ij = <H_r,ij + (d_j gL_r,i + d_i gL_r,j) / 2 + d_i d_j E0_r + d_i (gR_r,j - gL_r,j) / 2>.
+ * Host routine, double.  In (host): wsum [nparts], mean [nparts][P], E0 [nparts],
+ * gL, gR [nparts][P], S, H [nparts][P][P].  Out (host): E0_out [1], mean_out [P] (or NULL),
+ * gL_out, gR_out [P], S_out, H_out [P][P].  Errors: VBQMC_ERR_ARG. */
+int vbqmc_lin_merge(int nparts, int P, const double* wsum, const double* mean, const double* E0, const double* gL,
+                    const double* gR, const double* S, const double* H, double* E0_out, double* mean_out,
+                    double* gL_out, double* gR_out, double* S_out, double* H_out);
+
+/* Overlap matrix of the JVB structures (Sec. 2.4) over M samples:
+ *   S_IJ = <(Psi_I/Psi_0)(Psi_J/Psi_0)>,  <x> = sum_m w_m x_m / sum_m w_m,
+ * with Psi_I = J c_I-derivative of Eq. PsiJVBp, i.e. Psi_I/Psi_0 = Phi_I/Phi: the c_I
+ * derivatives that vbqmc_eval_walkers writes as the first n_cparam columns of O.  A structure
+ * missing from cparam (at most one; its c_I must be nonzero) is rebuilt at every sample from
+ * the identity sum_I c_I Psi_I/Psi_0 = 1.  Products and sums are double, in a fixed order,
+ * for either element type of O.
+ *   O        [M][ldo] device, element type double (VBQMC_FP64) or float (VBQMC_MIXED), in
+ *   weights  [M] device double or NULL (all 1)
+ *   c_vb     [nvb] host: structure coefficients; cparam [n_cparam] host: structure of each
+ *            leading column of O (n_cparam >= nvb - 1, nvb <= 32)
+ *   S        [nvb][nvb] host double, out
+ * Synchronizes 'stream' (the result is copied to the host).  Uses the context's reduction
+ * workspace (grown on demand).  Errors: VBQMC_ERR_ARG, VBQMC_ERR_CAPACITY (nvb > 32),
+ * VBQMC_ERR_CUDA. */
+int vbqmc_structure_overlap(vbqmc_ctx* ctx, int precision, int M, int ldo, const void* O, const double* weights,
+                            int nvb, const double* c_vb, int n_cparam, const int* cparam, double* S, void* stream);
+
+/* Weights of the JVB structures from their overlap S (Sec. 2.4), host double:
+ *   Chirgwin-Coulson  w_I = c_I (S c)_I / (c^T S c);
+ *   Loewdin           w_I = (S^1/2 c)_I^2 / |S^1/2 c|^2,
+ * S^1/2 through the eigendecomposition of the symmetric part of S (negative eigenvalues of
+ * rounding size taken as 0).  S [nvb][nvb], c [nvb] in; w_cc, w_lowdin [nvb] out (either may
+ * be NULL).  Errors: VBQMC_ERR_ARG for bad or non-finite input or a vanishing norm. */
+int vbqmc_structure_weights(int nvb, const double* S, const double* c, double* w_cc, double* w_lowdin);
+
+/* Measured ALU throughput of a device (diagnostics; the paper has no counterpart): the
+ * denominators of the walker kernels' rooflines.  out[0] FP32 FMA TFLOP/s, out[1] FP64 FMA
+ * TFLOP/s, out[2] special-function exponentials in 10^12 per second, out[3] SM count; *n = 4.
+ * Each probe runs independent FMA (or exponential) chains over 8 x 256 threads per SM and is
+ * timed with CUDA events (best of three launches after one warm-up).  Synchronous; allocates
+ * nothing; the calling thread's current device is restored. */
+int vbqmc_measure_alu_peaks(int device, double* out, int max, int* n);
 
 /* Scratch size of vbqmc_accumulate_lin_matrices_noalloc, bytes per device (64 MiB). */
 #define VBQMC_NOALLOC_SCRATCH_BYTES (64u << 20)

@@ -60,7 +60,7 @@ def lib():
                               _c_int_p, ctypes.c_int]
         L.orc_dmc.argtypes = [ctypes.POINTER(_OrcSystem), ctypes.c_int, _c_int_p, _c_dbl_p, ctypes.c_int,
                               ctypes.c_double, _c_dbl_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
-                              ctypes.c_uint32, _c_dbl_p, _c_dbl_p, _c_int_p, _c_dbl_p, ctypes.c_int]
+                              ctypes.c_uint32, ctypes.c_uint32, _c_dbl_p, _c_dbl_p, _c_int_p, _c_dbl_p, ctypes.c_int]
         _LIB = L
     return _LIB
 
@@ -178,8 +178,10 @@ def vmc(spec, R, nsweeps, step, seed, step0=0, system=0, walker_id=None, eloc=Tr
     return R, hist, lp, nacc
 
 
-def dmc(spec, R, nsteps, tau, e_trial, target, seed, step0=0, system=0, cap=None, nthreads=None):
-    """Fixed-node DMC; returns dict with final population and per-step sums."""
+def dmc(spec, R, nsteps, tau, e_trial, target, seed, step0=0, system=0, cap=None, nthreads=None, walker_offset=0):
+    """Fixed-node DMC (the step of vbqmc_oracle.cpp: drift and branching energy limited near
+    nodes as in Umrigar, Nightingale and Runge 1993); returns dict with final population and
+    per-step sums."""
     R0 = np.ascontiguousarray(R, dtype=np.float64)
     W = R0.shape[0]
     cap = cap or 4 * max(W, target)
@@ -192,7 +194,8 @@ def dmc(spec, R, nsteps, tau, e_trial, target, seed, step0=0, system=0, cap=None
     pop = np.zeros(nsteps, np.int32)
     rc = lib().orc_dmc(ctypes.byref(s), cap, ctypes.byref(Wio), _dp(buf), int(nsteps), float(tau),
                        ctypes.byref(et), int(target), ctypes.c_uint64(seed), ctypes.c_uint32(step0),
-                       ctypes.c_uint32(system), _dp(swE), _dp(sw), _ip(pop), _dp(et_hist),
+                       ctypes.c_uint32(system), ctypes.c_uint32(walker_offset), _dp(swE), _dp(sw), _ip(pop),
+                       _dp(et_hist),
                        nthreads or default_threads())
     if rc:
         raise RuntimeError("oracle dmc failed: %d" % rc)

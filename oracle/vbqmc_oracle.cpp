@@ -32,9 +32,17 @@
 //   * orbital-rotation derivative: at kappa = 0 the first-order action of E_kl replaces
 //     phi_l by phi_l + eps * phi_k in every determinant (both spins).
 //   * V includes the nucleus-nucleus repulsion.
-//   * DMC: plain all-electron drift-diffusion step with Metropolis acceptance, node
-//     rejection, weight exp(-tau[(E_L+E_L')/2 - E_T]), branching copies = floor(w + U)
-//     capped at 3, children in parent order, E_T = E_mean - (0.1/tau) ln(pop/target).
+//   * DMC: the paper names the algorithm of Umrigar, Nightingale and Runge (J. Chem. Phys.
+//     99, 2865 (1993)) without printing it.  The step here keeps that algorithm's two limits
+//     near nodes on an all-electron drift-diffusion move with Metropolis acceptance: each
+//     electron's drift v_i = grad_i ln|Psi| is replaced by
+//       vbar_i = v_i (-1 + sqrt(1 + 2 a |v_i|^2 tau)) / (a |v_i|^2 tau),  a = 1,
+//     and in the branching weight E_L is replaced by E_T + (E_L - E_T) |Vbar| / |V| (V, Vbar the
+//     whole-walker drift vectors); node rejection, weight
+//     exp(-tau[(E'_L(R) + E'_L(R_kept))/2 - E_T]) with E'_L the limited energy, branching
+//     copies = floor(w + U) capped at 3, children in parent order,
+//     E_T = E_mean - (0.1/tau) ln(pop/target) with E_mean the weighted mean of the raw E_L.
+//     Random numbers are keyed by walker_offset + (the walker's index in the population).
 //
 // Derivatives:
 //   * electron gradients/Laplacians of the Slater part: each determinant is linear in the
@@ -1016,9 +1024,25 @@ int orc_vmc(const orc_system* in, int W, double* R, int nsweeps, double step, ui
 // Outputs per step (may be NULL): sum_wE [nsteps], sum_w [nsteps], pop [nsteps] (after branching),
 // e_trial [nsteps] (after update).  *W_io: population in/out.  Returns 0, or -3 if the
 // population exceeds cap.
+// The drift of Umrigar, Nightingale and Runge limited per electron (a = 1); returns the
+// ratio |Vbar| / |V| of the whole walker (1 where V = 0).
+static double limited_drift(int N, const double* v, double tau, double* vbar) {
+  double n2 = 0.0, nb2 = 0.0;
+  for (int e = 0; e < N; ++e) {
+    const double* g = v + 3 * e;
+    const double v2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const double x = v2 * tau;
+    const double f = x > 0.0 ? (-1.0 + std::sqrt(1.0 + 2.0 * x)) / x : 1.0;
+    for (int d = 0; d < 3; ++d) vbar[3 * e + d] = f * g[d];
+    n2 += v2;
+    nb2 += f * f * v2;
+  }
+  return n2 > 0.0 ? std::sqrt(nb2 / n2) : 1.0;
+}
+
 int orc_dmc(const orc_system* in, int cap, int* W_io, double* R, int nsteps, double tau, double* E_T_io,
-            int target, uint64_t seed, uint32_t step0, uint32_t system, double* sum_wE, double* sum_w, int* pop_out,
-            double* et_out, int nthreads) {
+            int target, uint64_t seed, uint32_t step0, uint32_t system, uint32_t walker_offset, double* sum_wE,
+            double* sum_w, int* pop_out, double* et_out, int nthreads) {
   Sys s;
   int rc = build_sys(in, s);
   if (rc) return rc;
@@ -1033,28 +1057,32 @@ int orc_dmc(const orc_system* in, int cap, int* W_io, double* R, int nsteps, dou
     std::vector<int> copies(W);
     parallel_for(W, nthreads, [&](int w) {
       double* Rw = R + (size_t)w * 3 * N;
+      const uint32_t wid = walker_offset + (uint32_t)w;
       Eval<double> e0 = evaluate(s, P0, Rw, true);
-      std::vector<double> Rp(3 * N);
+      std::vector<double> Rp(3 * N), vb0(3 * N), vb1(3 * N);
+      const double lim0 = limited_drift(N, e0.grad.data(), tau, vb0.data());
       for (int e = 0; e < N; ++e) {
         double ua[2], ub[2];
-        uniforms2(seed, (uint32_t)w, st, (uint32_t)e, system, 2, ua);
-        uniforms2(seed, (uint32_t)w, st, (uint32_t)e, system, 3, ub);
+        uniforms2(seed, wid, st, (uint32_t)e, system, 2, ua);
+        uniforms2(seed, wid, st, (uint32_t)e, system, 3, ub);
         double ra = std::sqrt(-2.0 * std::log(1.0 - ua[0]));
         double rb = std::sqrt(-2.0 * std::log(1.0 - ub[0]));
         double z[3] = {ra * std::cos(2.0 * M_PI * ua[1]), ra * std::sin(2.0 * M_PI * ua[1]),
                        rb * std::cos(2.0 * M_PI * ub[1])};
         for (int d = 0; d < 3; ++d)
-          Rp[3 * e + d] = Rw[3 * e + d] + tau * e0.grad[3 * e + d] + std::sqrt(tau) * z[d];
+          Rp[3 * e + d] = Rw[3 * e + d] + tau * vb0[3 * e + d] + std::sqrt(tau) * z[d];
       }
       Eval<double> e1 = evaluate(s, P0, Rp.data(), true);
+      const double lim1 = limited_drift(N, e1.grad.data(), tau, vb1.data());
       double uu[2];
-      uniforms2(seed, (uint32_t)w, st, (uint32_t)N, system, 4, uu);
+      uniforms2(seed, wid, st, (uint32_t)N, system, 4, uu);
       bool accept = false;
       if (e1.sign == e0.sign && e1.sign != 0.0) {
-        double lg_fwd = 0.0, lg_rev = 0.0;  // -|R'-R-tau v(R)|^2/2tau and -|R-R'-tau v(R')|^2/2tau
+        // -|R'-R-tau vbar(R)|^2/2tau and -|R-R'-tau vbar(R')|^2/2tau
+        double lg_fwd = 0.0, lg_rev = 0.0;
         for (int q = 0; q < 3 * N; ++q) {
-          double f = Rp[q] - Rw[q] - tau * e0.grad[q];
-          double b = Rw[q] - Rp[q] - tau * e1.grad[q];
+          double f = Rp[q] - Rw[q] - tau * vb0[q];
+          double b = Rw[q] - Rp[q] - tau * vb1[q];
           lg_fwd += f * f;
           lg_rev += b * b;
         }
@@ -1064,7 +1092,10 @@ int orc_dmc(const orc_system* in, int cap, int* W_io, double* R, int nsteps, dou
       double Enew = accept ? e1.eloc : e0.eloc;
       if (accept)
         for (int q = 0; q < 3 * N; ++q) Rw[q] = Rp[q];
-      double w1 = std::exp(-tau * (0.5 * (e0.eloc + Enew) - E_T));
+      // branching energies limited in proportion to the drift
+      const double Eb0 = E_T + (e0.eloc - E_T) * lim0;
+      const double Eb1 = E_T + (Enew - E_T) * (accept ? lim1 : lim0);
+      double w1 = std::exp(-tau * (0.5 * (Eb0 + Eb1) - E_T));
       wt[w] = w1;
       EL[w] = Enew;
       int c = (int)std::floor(w1 + uu[1]);

@@ -18,8 +18,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
 CU_SOURCES = ["kernels.cu", "eval_jastrow.cu", "eval_orbitals.cu", "eval_det.cu", "eval_dettab.cu", "eval_forces.cu",
-              "dmc.cu", "gradient.cu", "linmethod.cu", "linmethod_noalloc.cu", "api.cu", "batch_api.cu"]
-CPP_SOURCES = ["system_host.cpp"]
+              "dmc.cu", "gradient.cu", "linmethod.cu", "linmethod_noalloc.cu", "api.cu", "batch_api.cu", "peaks.cu"]
+CPP_SOURCES = ["system_host.cpp", "host_linalg.cpp"]
 
 
 def _headers():

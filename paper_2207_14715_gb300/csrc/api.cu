@@ -465,6 +465,61 @@ int vbqmc_weighted_colsum(vbqmc_ctx* ctx, int W, int K, int jtype, const double*
   return VBQMC_OK;
 }
 
+int vbqmc_structure_overlap(vbqmc_ctx* ctx, int precision, int M, int ldo, const void* O, const double* weights,
+                            int nvb, const double* c_vb, int n_cparam, const int* cparam, double* S, void* stream) {
+  if (!ctx) return fail(VBQMC_ERR_ARG, "null context");
+  ctx->last_launches = 0;
+  if (precision != VBQMC_FP64 && precision != VBQMC_MIXED) return fail(VBQMC_ERR_ARG, "bad precision mode");
+  if (M < 1 || nvb < 1 || !c_vb || !S) return fail(VBQMC_ERR_ARG, "structure_overlap: bad size or null pointer");
+  if (nvb > vbq::kOvMaxStruct) return fail(VBQMC_ERR_CAPACITY, "structure_overlap: more than 32 structures");
+  if (n_cparam < 0 || n_cparam > nvb || n_cparam < nvb - 1 || (n_cparam > 0 && (!cparam || !O)) || ldo < n_cparam)
+    return fail(VBQMC_ERR_ARG, "structure_overlap: cparam must list every structure but at most one");
+  vbq::OverlapMap map{};
+  map.nvb = nvb;
+  for (int I = 0; I < nvb; ++I) {
+    map.col[I] = -1;
+    map.c[I] = c_vb[I];
+  }
+  for (int k = 0; k < n_cparam; ++k) {
+    const int I = cparam[k];
+    if (I < 0 || I >= nvb || map.col[I] >= 0) return fail(VBQMC_ERR_ARG, "structure_overlap: bad or repeated cparam entry");
+    map.col[I] = k;
+  }
+  for (int I = 0; I < nvb; ++I)
+    if (map.col[I] < 0 && !(c_vb[I] != 0.0))
+      return fail(VBQMC_ERR_ARG, "structure_overlap: the structure left out of cparam needs c_I != 0");
+  DeviceGuard g(ctx->device);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int np = (nvb + 1) * (nvb + 2) / 2;
+  const size_t need = (vbq::overlap_part_doubles(M, nvb) + np) * sizeof(double);
+  if (need > ctx->red_bytes) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (ctx->red_work) cudaFree(ctx->red_work);
+    ctx->red_work = nullptr;
+    ctx->red_bytes = 0;
+    e = cudaMalloc(&ctx->red_work, need);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(overlap workspace)");
+    ctx->red_bytes = need;
+  }
+  double* part = static_cast<double*>(ctx->red_work);
+  double* out = part + vbq::overlap_part_doubles(M, nvb);
+  cudaError_t e = vbq::launch_structure_overlap(M, ldo, precision == VBQMC_MIXED ? 1 : 0, O, weights, map, part, out, st);
+  if (e != cudaSuccess) return cuda_fail(e, "structure overlap kernel launch");
+  ctx->last_launches = 2;
+  std::vector<double> sums(np);
+  e = cudaMemcpyAsync(sums.data(), out, np * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "structure overlap result copy");
+  const double wsum = sums[np - 1];
+  if (!(wsum > 0.0)) return fail(VBQMC_ERR_ARG, "structure_overlap: the weights do not sum to a positive value");
+  int t = 0;
+  for (int i = 0; i <= nvb; ++i)
+    for (int j = i; j <= nvb; ++j, ++t)
+      if (i < nvb && j < nvb) S[(size_t)i * nvb + j] = S[(size_t)j * nvb + i] = sums[t] / wsum;
+  return VBQMC_OK;
+}
+
 int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R, int nsweeps, double step,
                     uint64_t seed, uint32_t step0, uint32_t system_tag, uint32_t walker_offset, int refresh,
                     double* state, int state_valid, int* nacc, double* logpsi, double* sign, double* eloc, void* O,
@@ -515,8 +570,9 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
 }
 
 int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int cap, double* R, int nsteps, double tau,
-                    double* E_T_io, int target, uint64_t seed, uint32_t step0, uint32_t system_tag, double* sum_wE,
-                    double* sum_w, int* pop, double* e_trial, int64_t* accepted, void* stream) {
+                    double* E_T_io, int target, uint64_t seed, uint32_t step0, uint32_t system_tag,
+                    uint32_t walker_offset, double* sum_wE, double* sum_w, int* pop, double* e_trial, int64_t* accepted,
+                    void* stream) {
   if (!W_io || !E_T_io) return fail(VBQMC_ERR_ARG, "null W_io or E_T_io");
   int rc = check_call(ctx, sys_id, precision, *W_io);
   if (rc) return rc;
@@ -593,13 +649,13 @@ int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int ca
   int rcode = VBQMC_OK;
   for (int k = 0; k < nsteps; ++k) {
     const uint32_t stp = step0 + (uint32_t)k;
-    e = vbq::launch_dmc_propose(W, N, cur.R, cur.grad, tau, seed, stp, system_tag, Rp, st);
+    e = vbq::launch_dmc_propose(W, N, cur.R, cur.grad, tau, seed, stp, system_tag, walker_offset, Rp, st);
     if (e == cudaSuccess)
       e = vbq::launch_eval(precision, s.dev, s.lay_eval[precision], W, Rp, lp1, sg1, el1, grad1, nullptr, nullptr,
                            nullptr, ctx->eval_work, st, &nl);
     if (e == cudaSuccess)
       e = vbq::launch_dmc_accept(W, N, cur.R, cur.lp, cur.sg, cur.el, cur.grad, Rp, lp1, sg1, el1, grad1, tau, E_T,
-                                 seed, stp, system_tag, wt, wE, copies, acc, st);
+                                 seed, stp, system_tag, walker_offset, wt, wE, copies, acc, st);
     if (e == cudaSuccess) e = vbq::launch_dmc_scan(W, copies, wt, wE, acc, offsets, tot, st);
     if (e == cudaSuccess)
       e = vbq::launch_dmc_branch(W, N, cap, copies, offsets, tot, cur.R, cur.lp, cur.sg, cur.el, cur.grad, nxt.R,

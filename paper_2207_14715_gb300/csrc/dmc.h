@@ -17,11 +17,11 @@ struct DmcTotals {
 
 // Arrays are walker-major: R, grad [W][N][3]; lp, sg, el, wt, wE [W]; copies, offsets, acc [W].
 cudaError_t launch_dmc_propose(int W, int N, const double* R, const double* grad, double tau, uint64_t seed,
-                               uint32_t step, uint32_t tag, double* Rp, cudaStream_t st);
+                               uint32_t step, uint32_t tag, uint32_t woff, double* Rp, cudaStream_t st);
 cudaError_t launch_dmc_accept(int W, int N, double* R, double* lp, double* sg, double* el, double* grad,
                               const double* Rp, const double* lp1, const double* sg1, const double* el1,
                               const double* grad1, double tau, double E_T, uint64_t seed, uint32_t step, uint32_t tag,
-                              double* wt, double* wE, int* copies, int* acc, cudaStream_t st);
+                              uint32_t woff, double* wt, double* wE, int* copies, int* acc, cudaStream_t st);
 cudaError_t launch_dmc_scan(int W, const int* copies, const double* wt, const double* wE, const int* acc,
                             int* offsets, DmcTotals* out, cudaStream_t st);
 cudaError_t launch_dmc_branch(int W, int N, int cap, const int* copies, const int* offsets, const DmcTotals* tot,

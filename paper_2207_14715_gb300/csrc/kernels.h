@@ -120,6 +120,19 @@ cudaError_t launch_nuclear_derivs(int precision, const SysDev& s, const EvalLayo
 int colsum_slices(int W);
 cudaError_t launch_weighted_colsum(int W, int K, int jtype, const double* ga, const void* Ja, const double* gb,
                                    const void* Jb, double* out, double* part, cudaStream_t st);
+// Structure overlap (gradient.cu): out[pair] = sum_m w_m R_i R_j over the upper triangle i <= j
+// of the columns 0..nvb, column nvb being 1 (so the last pairs hold sum w R_i and sum w);
+// R_I = O[m][col[I]] for col[I] >= 0, else (1 - sum_J c_J R_J) / c_I.  O element type double
+// (otype 0) or float (otype 1), row stride ldo; part: overlap_part_doubles(M, nvb) doubles.
+constexpr int kOvMaxStruct = 32;
+struct OverlapMap {
+  int nvb;
+  int col[kOvMaxStruct];
+  double c[kOvMaxStruct];
+};
+size_t overlap_part_doubles(int M, int nvb);
+cudaError_t launch_structure_overlap(int M, int ldo, int otype, const void* O, const double* wts, const OverlapMap& map,
+                                     double* part, double* out, cudaStream_t st);
 // VMC sweeps; state (may be null): read when state_valid, written after the last sweep with the
 // carried inverses, term ratios and ln|Phi| (its ln|det| entries are left as they were).
 cudaError_t launch_sweep(int precision, const SysDev& s, const SweepLayout& L, int W, double* R, int nsweeps,

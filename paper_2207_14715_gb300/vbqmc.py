@@ -54,7 +54,8 @@ EXPORTED = ["vbqmc_create", "vbqmc_destroy", "vbqmc_last_error", "vbqmc_set_syst
             "vbqmc_launch_info", "vbqmc_last_launch_count", "vbqmc_accumulate_lin_matrices_noalloc",
             "vbqmc_dmc_steps", "vbqmc_set_kernel_timing", "vbqmc_kernel_times", "vbqmc_batch_create",
             "vbqmc_batch_destroy", "vbqmc_batch_vmc_steps", "vbqmc_batch_tune", "vbqmc_batch_info",
-            "vbqmc_eval_nuclear_derivs", "vbqmc_weighted_colsum"]
+            "vbqmc_eval_nuclear_derivs", "vbqmc_weighted_colsum", "vbqmc_lin_solve", "vbqmc_structure_overlap",
+            "vbqmc_structure_weights", "vbqmc_measure_alu_peaks", "vbqmc_lin_merge"]
 
 _LIB = None
 
@@ -87,7 +88,7 @@ def lib():
                                                     vp, vp, vp, vp, vp, vp]
         L.vbqmc_dmc_steps.argtypes = [vp, ctypes.c_int, ctypes.c_int, _c_int_p, ctypes.c_int, vp, ctypes.c_int,
                                       ctypes.c_double, _c_dbl_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
-                                      ctypes.c_uint32, _c_dbl_p, _c_dbl_p, _c_int_p, _c_dbl_p,
+                                      ctypes.c_uint32, ctypes.c_uint32, _c_dbl_p, _c_dbl_p, _c_int_p, _c_dbl_p,
                                       ctypes.POINTER(ctypes.c_int64), vp]
         L.vbqmc_batch_create.argtypes = [vp, ctypes.c_int, _c_int_p, _c_int_p, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_void_p)]
@@ -98,6 +99,13 @@ def lib():
         L.vbqmc_batch_info.argtypes = [vp, _c_int_p]
         L.vbqmc_set_kernel_timing.argtypes = [vp, ctypes.c_int]
         L.vbqmc_kernel_times.argtypes = [vp, _c_dbl_p, ctypes.c_int, _c_int_p]
+        L.vbqmc_lin_solve.argtypes = [ctypes.c_int, ctypes.c_double, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p,
+                                      ctypes.c_double, _c_dbl_p, _c_dbl_p]
+        L.vbqmc_structure_overlap.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int,
+                                              _c_dbl_p, ctypes.c_int, _c_int_p, _c_dbl_p, vp]
+        L.vbqmc_lin_merge.argtypes = [ctypes.c_int, ctypes.c_int] + [_c_dbl_p] * 13
+        L.vbqmc_structure_weights.argtypes = [ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p]
+        L.vbqmc_measure_alu_peaks.argtypes = [ctypes.c_int, _c_dbl_p, ctypes.c_int, _c_int_p]
         L.vbqmc_accumulate_lin_matrices_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp, vp,
                                                             vp, vp, vp, vp, vp, vp, vp]
         _LIB = L
@@ -275,7 +283,7 @@ class Context:
 
 
     def dmc_steps(self, sys_id, precision, R, W, nsteps, tau, E_T, target, seed, step0=0, system_tag=0,
-                  stream=None):
+                  walker_offset=0, stream=None):
         """vbqmc_dmc_steps on the population R[:W] of a float64 CUDA tensor R [cap, N, 3] (updated
         in place).  Returns (W, E_T, history) with history the per-step host arrays sum_wE,
         sum_w, pop, e_trial (truncated to the steps run) and the accepted-move count."""
@@ -289,8 +297,8 @@ class Context:
         nacc = ctypes.c_int64(0)
         _check(lib().vbqmc_dmc_steps(self.h, int(sys_id), int(precision), ctypes.byref(W_c), int(cap), _ptr(R),
                                      int(nsteps), float(tau), ctypes.byref(et), int(target), int(seed) & (2**64 - 1),
-                                     int(step0) & 0xffffffff, int(system_tag), _dp(swe), _dp(sw), _ip(pop), _dp(etr),
-                                     ctypes.byref(nacc), _stream(stream)))
+                                     int(step0) & 0xffffffff, int(system_tag), int(walker_offset) & 0xffffffff,
+                                     _dp(swe), _dp(sw), _ip(pop), _dp(etr), ctypes.byref(nacc), _stream(stream)))
         ran = int((pop >= 0).sum()) if nsteps > 0 else 0
         hist = {"sum_wE": swe[:ran], "sum_w": sw[:ran], "pop": pop[:ran], "e_trial": etr[:ran],
                 "accepted": int(nacc.value)}
@@ -326,79 +334,100 @@ class Context:
                                                    _ptr(H), _stream(stream)))
         return {"E0": E0, "gL": gL, "gR": gR, "S": S, "H": H}
 
-    def structure_overlap(self, precision, O, cparam, c_vb, weights=None, stream=None):
-        """Overlap matrix of the JVB structures (Sec. 2.4), S_IJ = <(Psi_I/Psi_0)(Psi_J/Psi_0)>
-        over M samples, from derivative rows O [M, P] (the mode's bulk type, as the evaluation
-        writes them) whose first len(cparam) columns are Psi_I/Psi_0 = Phi_I/Phi for the
-        structures cparam (the c_I derivatives of Eq. PsiJVBp).  On the device: the column means
-        (vbqmc_weighted_colsum) and the centred products <Ot_I Ot_J> (the S output of
-        vbqmc_accumulate_lin_matrices); on the host, Nvb x Nvb: S = <Ot Ot> + <O><O>^T, and the
-        row of a structure missing from cparam (at most one) from sum_I c_I Psi_I/Psi_0 = 1,
-        which holds on every sample.  weights [M] float64 CUDA tensor or None (all 1).  The
-        centred products carry the linear-method kernel's accuracy (FP32-pipe products: about
-        2e-6 of the matrix scale with double rows).  Returns an [Nvb, Nvb] float64 numpy array."""
+    def lin_part(self, precision, O, dEL, eloc, weights=None, stream=None):
+        """This rank's share of a multi-rank linear-method accumulation (ranks.merge_lin_parts):
+        the estimators of vbqmc_accumulate_lin_matrices plus the weight sum and the mean row <O>
+        (vbqmc_weighted_colsum), as host arrays."""
         import torch
         M, P = O.shape
-        cp = [int(I) for I in cparam]
+        ones = torch.ones(M, dtype=torch.float64, device=O.device)
+        ga = ones if weights is None else weights
+        sums = torch.empty(P + 1, dtype=torch.float64, device=O.device)
+        self.weighted_colsum(ga, O, sums[:P], stream=stream)
+        self.weighted_colsum(ga, ones.reshape(M, 1), sums[P:], stream=stream)
+        m = self.accumulate_lin_matrices(precision, O, dEL, eloc, weights=weights, stream=stream)
+        out = {k: v.cpu().numpy() for k, v in m.items()}
+        h = sums.cpu().numpy()
+        out["wsum"] = float(h[P])
+        out["mean"] = h[:P] / h[P]
+        return out
+
+    def structure_overlap(self, precision, O, cparam, c_vb, weights=None, stream=None):
+        """vbqmc_structure_overlap: S_IJ = <(Psi_I/Psi_0)(Psi_J/Psi_0)> (Sec. 2.4) from derivative
+        rows O [M, P] (the mode's bulk type) whose first len(cparam) columns are the c_I
+        derivatives of the structures cparam.  weights [M] float64 CUDA tensor or None.
+        Returns an [Nvb, Nvb] float64 numpy array (the call synchronizes the stream)."""
+        M, P = O.shape
+        _check_deriv(precision, O)
+        c = np.ascontiguousarray(c_vb, np.float64)
+        cp = np.ascontiguousarray(cparam, np.int32)
         if len(cp) > P:
             raise VbqmcError("cparam longer than the derivative rows")
-        if not cp:  # a single structure: Psi_0 = c_0 Psi_1 everywhere
-            return assemble_structure_overlap(np.zeros(0), np.zeros((0, 0)), cp, c_vb)
-        dev = O.device
-        ones = torch.ones(M, dtype=torch.float64, device=dev)
-        ga = ones if weights is None else weights
-        wsum = float(M)
-        if weights is not None:
-            t = torch.empty(1, dtype=torch.float64, device=dev)
-            self.weighted_colsum(weights, ones.reshape(M, 1), t, stream=stream)
-            wsum = float(t.item())
-        n = len(cp)
-        Os = O[:, :n].contiguous()  # the structure columns alone (the products' scale is theirs)
-        total = torch.empty(n, dtype=torch.float64, device=dev)
-        self.weighted_colsum(ga, Os, total, stream=stream)
-        lin = self.accumulate_lin_matrices(precision, Os, Os, torch.zeros_like(ones), weights=weights, stream=stream)
-        return assemble_structure_overlap(total.cpu().numpy() / wsum, lin["S"].cpu().numpy(), cp, c_vb)
-
-
-def assemble_structure_overlap(mean, cov, cparam, c_vb):
-    """Host step of Context.structure_overlap: from the means <Psi_I/Psi_0> and the centred
-    products of the structures cparam, S_IJ = cov_IJ + mean_I mean_J; a structure I0 missing
-    from cparam gets <R_I0 R_J> = (<R_J> - sum_I c_I <R_I R_J>) / c_I0 and
-    <R_I0> = (1 - sum_I c_I <R_I>) / c_I0 (R_I = Psi_I/Psi_0, sum over I in cparam)."""
-    c = np.asarray(c_vb, np.float64)
-    nvb = len(c)
-    cp = [int(I) for I in cparam]
-    missing = [I for I in range(nvb) if I not in cp]
-    if len(missing) > 1 or len(set(cp)) != len(cp):
-        raise VbqmcError("structure overlap needs every structure but at most one in cparam")
-    mean = np.asarray(mean, np.float64)
-    cov = np.asarray(cov, np.float64)
-    Scp = 0.5 * (cov + cov.T) + np.outer(mean, mean)
-    S = np.zeros((nvb, nvb))
-    S[np.ix_(cp, cp)] = Scp
-    if missing:
-        i0 = missing[0]
-        cc = c[cp]
-        row = (mean - cc @ Scp) / c[i0]
-        S[i0, cp] = row
-        S[cp, i0] = row
-        S[i0, i0] = ((1.0 - cc @ mean) / c[i0] - cc @ row) / c[i0]
-    return S
+        nvb = len(c)
+        S = np.zeros((nvb, nvb), np.float64)
+        _check(lib().vbqmc_structure_overlap(self.h, int(precision), int(M), int(P), _ptr(O), _ptr(weights), nvb,
+                                             _dp(c), len(cp), _ip(cp) if len(cp) else None, _dp(S),
+                                             _stream(stream)))
+        return S
 
 
 def structure_weights(S, c_vb):
-    """Chirgwin-Coulson and Loewdin weights of the JVB structures (Sec. 2.4) from their overlap
-    S [Nvb, Nvb]: w_CC = c * (S c) / (c^T S c); w_L = cbar^2 / |cbar|^2 with cbar = S^(1/2) c,
-    the square root through the eigendecomposition of S (eigenvalues of rounding size below 0
-    clipped).  Host routine on an Nvb x Nvb matrix.  Returns (w_CC, w_L)."""
-    S = 0.5 * (np.asarray(S, np.float64) + np.asarray(S, np.float64).T)
-    c = np.asarray(c_vb, np.float64)
-    Sc = S @ c
-    w_cc = c * Sc / (c @ Sc)
-    lam, U = np.linalg.eigh(S)
-    cbar = (U * np.sqrt(np.clip(lam, 0.0, None))) @ U.T @ c
-    w_l = cbar ** 2 / (cbar @ cbar)
+    """vbqmc_structure_weights: Chirgwin-Coulson and Loewdin weights of the JVB structures
+    (Sec. 2.4) from their overlap S [Nvb, Nvb] and coefficients c.  Returns (w_CC, w_L)."""
+    S = np.ascontiguousarray(S, np.float64)
+    c = np.ascontiguousarray(c_vb, np.float64)
+    n = len(c)
+    if S.shape != (n, n):
+        raise VbqmcError("S must be [Nvb, Nvb]")
+    w_cc, w_l = np.zeros(n), np.zeros(n)
+    _check(lib().vbqmc_structure_weights(n, _dp(S), _dp(c), _dp(w_cc), _dp(w_l)))
     return w_cc, w_l
+
+
+def lin_solve(E0, gL, gR, H, S, shift=0.0):
+    """vbqmc_lin_solve: the parameter update of Eq. geneigeqM (host FP64 routine of the
+    library).  Returns (dp [P], E_lin)."""
+    gL = np.ascontiguousarray(gL, np.float64)
+    gR = np.ascontiguousarray(gR, np.float64)
+    H = np.ascontiguousarray(H, np.float64)
+    S = np.ascontiguousarray(S, np.float64)
+    P = len(gL)
+    if gR.shape != (P,) or H.shape != (P, P) or S.shape != (P, P):
+        raise VbqmcError("lin_solve: gL, gR [P] and H, S [P, P] expected")
+    dp = np.zeros(P)
+    e = ctypes.c_double(0.0)
+    _check(lib().vbqmc_lin_solve(P, float(E0), _dp(gL), _dp(gR), _dp(H), _dp(S), float(shift), _dp(dp),
+                                 ctypes.byref(e)))
+    return dp, e.value
+
+
+def lin_merge(parts):
+    """vbqmc_lin_merge: estimators of the whole sample from per-part ones.  parts: list of dicts
+    with 'wsum' (float), 'mean' [P], 'E0', 'gL' [P], 'gR' [P], 'S' [P, P], 'H' [P, P] (host
+    values).  Returns a dict with E0 [1], mean [P], gL, gR [P], S, H [P, P] (numpy, float64)."""
+    n = len(parts)
+    P = len(np.asarray(parts[0]["gL"]))
+    stack = lambda k, shape: np.ascontiguousarray(np.stack([np.asarray(p[k], np.float64).reshape(shape)
+                                                             for p in parts]))
+    ws = np.ascontiguousarray([float(p["wsum"]) for p in parts])
+    e0 = np.ascontiguousarray([float(np.asarray(p["E0"]).ravel()[0]) for p in parts])
+    mean, gL, gR = stack("mean", (P,)), stack("gL", (P,)), stack("gR", (P,))
+    S, H = stack("S", (P, P)), stack("H", (P, P))
+    out = {"E0": np.zeros(1), "mean": np.zeros(P), "gL": np.zeros(P), "gR": np.zeros(P), "S": np.zeros((P, P)),
+           "H": np.zeros((P, P))}
+    _check(lib().vbqmc_lin_merge(n, P, _dp(ws), _dp(mean), _dp(e0), _dp(gL), _dp(gR), _dp(S), _dp(H),
+                                 _dp(out["E0"]), _dp(out["mean"]), _dp(out["gL"]), _dp(out["gR"]), _dp(out["S"]),
+                                 _dp(out["H"])))
+    return out
+
+
+def measure_alu_peaks(device=0):
+    """vbqmc_measure_alu_peaks: {'fp32_tflops', 'fp64_tflops', 'exp_tops', 'sms'} of a device."""
+    out = np.zeros(4)
+    n = ctypes.c_int(0)
+    _check(lib().vbqmc_measure_alu_peaks(int(device), _dp(out), 4, ctypes.byref(n)))
+    return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1]), "exp_tops": float(out[2]),
+            "sms": int(out[3])}
 
 
 def accumulate_lin_matrices_noalloc(precision, O, dEL, eloc, weights, E0, gL, gR, S, H, stream=None):
@@ -473,33 +502,3 @@ class Batch:
 
 def create(device: int = 0) -> Context:
     return Context(device)
-
-
-def lin_solve(E0, gL, gR, H, S, shift=0.0):
-    """Host-side FP64 generalized eigenproblem of Eq. geneigeqM for the parameter update: the
-    lowest real eigenvalue whose eigenvector has a first component >= 1e-3 of its norm, scaled
-    to first component 1.  (Host library routine on a (P+1)^2 matrix, not a GPU step.)"""
-    import scipy.linalg
-    P = len(gL)
-    A = np.zeros((P + 1, P + 1))
-    B = np.zeros((P + 1, P + 1))
-    A[0, 0] = float(E0)
-    A[0, 1:] = 0.5 * np.asarray(gR)
-    A[1:, 0] = 0.5 * np.asarray(gL)
-    A[1:, 1:] = np.asarray(H) + shift * np.eye(P)
-    B[0, 0] = 1.0
-    B[1:, 1:] = np.asarray(S)
-    ev, vec = scipy.linalg.eig(A, B)
-    best = None
-    for k in range(P + 1):
-        lam = ev[k]
-        if not np.isfinite(lam) or abs(lam.imag) > 1e-8 * max(1.0, abs(lam.real)):
-            continue
-        v = vec[:, k].real
-        if abs(v[0]) < 1e-3 * np.linalg.norm(v):
-            continue
-        if best is None or lam.real < best[0]:
-            best = (lam.real, v / v[0])
-    if best is None:
-        raise VbqmcError("no admissible eigenvector")
-    return best[1][1:], best[0]

@@ -24,27 +24,29 @@ def vb():
     ctx.close()
 
 
-def gpu_dmc(vb, spec, precision, R, nsteps, tau, e_trial, target, seed, cap=None, step0=0, sys_id=0):
+def gpu_dmc(vb, spec, precision, R, nsteps, tau, e_trial, target, seed, cap=None, step0=0, sys_id=0, walker_offset=0):
     mod, ctx = vb
     ctx.set_system(sys_id, spec)
     W = R.shape[0]
     cap = cap or 4 * max(W, target)
     buf = torch.zeros((cap, spec.N, 3), dtype=torch.float64, device="cuda")
     buf[:W] = torch.tensor(R, device="cuda")
-    W1, et, hist = ctx.dmc_steps(sys_id, precision, buf, W, nsteps, tau, e_trial, target, seed, step0=step0)
+    W1, et, hist = ctx.dmc_steps(sys_id, precision, buf, W, nsteps, tau, e_trial, target, seed, step0=step0,
+                                 walker_offset=walker_offset)
     torch.cuda.synchronize()
     return {"R": buf[:W1].cpu().numpy(), "W": W1, "e_trial": et, **hist}
 
 
-@pytest.mark.parametrize("maker,W,nsteps", [(S.small_open_shell, 24, 8), (S.h2_vb, 32, 8), (S.ethylene_vb, 12, 3)])
-def test_dmc_fp64_trajectory_matches_oracle(vb, orc, maker, W, nsteps):
+@pytest.mark.parametrize("maker,W,nsteps,woff", [(S.small_open_shell, 24, 8, 0), (S.h2_vb, 32, 8, 0),
+                                                 (S.ethylene_vb, 12, 3, 0), (S.small_open_shell, 24, 6, 4096)])
+def test_dmc_fp64_trajectory_matches_oracle(vb, orc, maker, W, nsteps, woff):
     spec = maker()
     R = S.initial_walkers(spec, W, 7)
     R, _, _, _ = orc.vmc(spec, R, 4, spec.step, seed=2, eloc=False)
     e0 = float(np.mean(orc.evaluate(spec, R)["eloc"]))
     tau = 0.01
-    ref = orc.dmc(spec, R, nsteps, tau, e0, W, seed=11, step0=3)
-    got = gpu_dmc(vb, spec, 0, R, nsteps, tau, e0, W, seed=11, step0=3)
+    ref = orc.dmc(spec, R, nsteps, tau, e0, W, seed=11, step0=3, walker_offset=woff)
+    got = gpu_dmc(vb, spec, 0, R, nsteps, tau, e0, W, seed=11, step0=3, walker_offset=woff)
     assert got["W"] == ref["W"]
     np.testing.assert_array_equal(got["pop"], ref["pop"])
     np.testing.assert_allclose(got["sum_w"], ref["sum_w"], rtol=1e-10)
@@ -52,6 +54,20 @@ def test_dmc_fp64_trajectory_matches_oracle(vb, orc, maker, W, nsteps):
     np.testing.assert_allclose(got["e_trial"], ref["e_trial_hist"], rtol=1e-10)
     np.testing.assert_allclose(got["R"], ref["R"], atol=1e-9)
     assert 0 < got["accepted"] <= sum([W] + list(ref["pop"][:-1]))
+
+
+def test_dmc_walker_offsets_separate_the_streams(vb, orc):
+    """Two ranks given the same seed, tag and step but disjoint walker offsets draw different
+    moves: the same walkers end at different positions (and the oracle agrees with each)."""
+    spec = S.h2_vb()
+    R = S.initial_walkers(spec, 16, 3)
+    e0 = float(np.mean(orc.evaluate(spec, R)["eloc"]))
+    a = gpu_dmc(vb, spec, 0, R, 2, 0.01, e0, 16, seed=5, walker_offset=0, cap=64)
+    b = gpu_dmc(vb, spec, 0, R, 2, 0.01, e0, 16, seed=5, walker_offset=64, cap=64)
+    n = min(a["W"], b["W"], 4)
+    assert np.abs(a["R"][:n] - b["R"][:n]).max() > 1e-3
+    ref = orc.dmc(spec, R, 2, 0.01, e0, 16, seed=5, walker_offset=64, cap=64)
+    np.testing.assert_allclose(b["R"], ref["R"], atol=1e-9)
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -126,7 +126,52 @@ def test_linear_method_update_matches_oracle(vb, orc):
     shift = 0.5
     dp, E = mod.lin_solve(m["E0"][0], m["gL"], m["gR"], m["H"], m["S"], shift=shift)
     dpo, Eo = orc.lin_solve(ref["E0"], ref["gL"], ref["gR"], ref["H"], ref["S"], shift=shift)
-    # the solve amplifies the float-product rounding of the matrices (1e-6 of their scale) by the
-    # conditioning of S (near-redundant parameters): compare against the update's own scale
-    np.testing.assert_allclose(dp, dpo, rtol=0, atol=1e-5 * max(1.0, np.abs(dpo).max()))
+    # S is ill-conditioned here (near-redundant parameters: eigenvalues down to 1e-11), so the
+    # update's components along near-null directions of S are not determined by the data; the
+    # wave-function change is: compare the updates in the S-norm, and the energies
+    sn = lambda v: np.sqrt(max(v @ ref["S"] @ v, 0.0))
+    assert sn(dp - dpo) <= 1e-4 * sn(dpo), (sn(dp - dpo), sn(dpo))
     assert E == pytest.approx(Eo, rel=1e-6)
+
+
+@pytest.mark.parametrize("P", [37, 130, 400])
+def test_library_solve_on_gpu_matrices(vb, orc, P):
+    """vbqmc_lin_solve (the library's host solve) on matrices accumulated on the GPU, against the
+    oracle's generalized eigensolver on the same matrices, up to the P = 400 of the linear-method
+    workload; and against the oracle's solve of the oracle's own matrices, within what the
+    accumulation's rounding (1e-5 of the matrix scale for float inputs) allows through S's
+    conditioning."""
+    mod, ctx = vb
+    M = 8 * P + 500
+    O, dE, E, _ = synthetic(M, P, 1000 + P)
+    O, dE = O.astype(np.float32).astype(np.float64), dE.astype(np.float32).astype(np.float64)
+    got = run_gpu(vb, 1, O, dE, E, None)
+    dp, e = mod.lin_solve(got["E0"][0], got["gL"], got["gR"], got["H"], got["S"], shift=0.1)
+    dpo, eo = orc.lin_solve(got["E0"][0], got["gL"], got["gR"], got["H"], got["S"], shift=0.1)
+    assert e == pytest.approx(eo, rel=1e-11)
+    sn = lambda v: np.sqrt(max(v @ got["S"] @ v, 0.0))
+    assert sn(dp - dpo) <= 1e-9 * sn(dpo)
+    ref = orc.lin_matrices(O, dE, E)
+    dpr, er = orc.lin_solve(ref["E0"], ref["gL"], ref["gR"], ref["H"], ref["S"], shift=0.1)
+    lam = np.linalg.eigvalsh(ref["S"])
+    amp = max(1.0, np.abs(ref["H"]).max()) / lam.min()
+    assert e == pytest.approx(er, rel=1e-5 * amp)
+    np.testing.assert_allclose(dp, dpr, rtol=0, atol=1e-4 * amp * max(1.0, np.abs(dpr).max()))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_parts_on_gpu_merge_to_the_whole(vb, orc, precision):
+    """The multi-rank path on one GPU: the estimators of two parts of a sample (Context.lin_part:
+    the accumulation kernels plus the weighted column sums) merged by vbqmc_lin_merge equal the
+    oracle's estimators of the whole sample, within the accumulation's tolerance."""
+    mod, ctx = vb
+    M, P = 6000, 40
+    O, dE, E, w = synthetic(M, P, 77, weights=True)
+    if precision == 1:
+        O, dE = O.astype(np.float32).astype(np.float64), dE.astype(np.float32).astype(np.float64)
+    dt = mod.deriv_dtype(precision)
+    t = lambda x, d=torch.float64: torch.tensor(x, dtype=d, device="cuda")
+    parts = [ctx.lin_part(precision, t(O[a:b], dt), t(dE[a:b], dt), t(E[a:b]), t(w[a:b]))
+             for a, b in ((0, 1700), (1700, M))]
+    got = mod.lin_merge(parts)
+    check(got, orc.lin_matrices(O, dE, E, w), 2e-6 if precision == 0 else 1e-5)

@@ -647,3 +647,67 @@ def test_dmc_h2_nodeless(orc):
     m, e = orc.reblock(Eb)
     assert e < 3e-3
     assert abs(m + 1.17447) < 4 * e + 3e-3, (m, e, e_vmc)
+
+
+def _ar1(rng, N, rho):
+    """Stationary AR(1) series x_t = rho x_{t-1} + sqrt(1 - rho^2) e_t, unit variance."""
+    from scipy.signal import lfilter
+    e = rng.normal(size=N)
+    return lfilter([np.sqrt(1.0 - rho * rho)], [1.0, -rho], e, zi=[rho * rng.normal()])[0]
+
+
+def test_reblock_short_series_is_the_textbook_standard_error(orc):
+    """Below 32 samples no blocking level is formed: the error is s / sqrt(n) with the sample
+    standard deviation s (n - 1 in the denominator).  x = 1, 2, 3, 4: s^2 = 5/3, error
+    sqrt(5/3) / 2."""
+    m, e = orc.reblock([1.0, 2.0, 3.0, 4.0])
+    assert m == 2.5
+    assert e == pytest.approx(np.sqrt(5.0 / 3.0) / 2.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.9, 0.98])
+def test_reblock_recovers_the_ar1_error_of_the_mean(orc, rho):
+    """For an AR(1) series the variance of the mean is known in closed form,
+    Var = (1 + 2 sum_{k=1}^{N-1} (1 - k/N) rho^k) / N (integrated autocorrelation time
+    (1 + rho)/(1 - rho) for large N).  Over 20 independent series the reblocked error must track
+    it: a level-0 estimate would be sqrt((1 - rho)/(1 + rho)) too small (0.23 at rho = 0.9)."""
+    N = 1 << 18
+    k = np.arange(1, N)
+    sd = np.sqrt((1.0 + 2.0 * np.sum((1.0 - k / N) * rho ** k)) / N)
+    ratios = []
+    for seed in range(20):
+        x = _ar1(np.random.default_rng(seed), N, rho)
+        m, e = orc.reblock(x)
+        assert m == pytest.approx(x.mean(), rel=0, abs=1e-15)
+        ratios.append(e / sd)
+    ratios = np.array(ratios)
+    assert 0.95 < ratios.mean() < 1.25, ratios.mean()
+    assert ratios.min() > 0.8 and ratios.max() < 1.6, (ratios.min(), ratios.max())
+
+
+def test_dmc_limits_bound_the_weights_at_a_node(orc):
+    """Trial orbital (1 + c' z) exp(-zeta r^2) (an s and a p Gaussian shell on one nucleus with
+    normalised coefficients 1 and c = 2, so c' = c sqrt(4 zeta)) with the e-n cusp in the Jastrow:
+    its node is the plane z0 = -1 / c', where lap Psi != 0, so v = grad ln|Psi| and E_L grow
+    like 1 / |z - z0|.  Walkers placed 1e-7 from the node would carry weights exp(-tau (E_L - E_T))
+    of order exp(1e5) without limits.  With the drift and energy limits of the step (Umrigar,
+    Nightingale and Runge 1993) the branching energy E_T + (E_L - E_T)|Vbar|/|V| stays bounded
+    (tau |Vbar| <= sqrt(2 tau) per electron): every weight stays within exp(+-0.5) here, so the
+    weight sum stays within a factor two of the population."""
+    import dataclasses
+    zeta, c = 0.5, 2.0
+    base = S.one_electron(1.0, zeta, a1=-1.0, a2=1.0)
+    spec = dataclasses.replace(base, sh_center=np.zeros(2, np.int32), sh_l=np.array([0, 1], np.int32),
+                               sh_zeta=np.array([zeta, zeta]), orb_coef=np.array([[1.0, 0.0, 0.0, c]]))
+    z0 = -1.0 / (c * np.sqrt(4.0 * zeta))
+    rng = np.random.default_rng(4)
+    W = 64
+    R = np.zeros((W, 1, 3))
+    R[:, 0, 0] = rng.uniform(-1.0, 1.0, W)
+    R[:, 0, 1] = rng.uniform(-1.0, 1.0, W)
+    R[:, 0, 2] = z0 + np.where(rng.uniform(size=W) < 0.5, -1e-7, 1e-7)
+    ev = orc.evaluate(spec, R)
+    assert np.abs(ev["eloc"]).min() > 1e5  # E_L ~ 1 / |z - z0| at the node
+    out = orc.dmc(spec, R, 1, 0.01, -0.3, W, seed=3, cap=4 * W)
+    assert 0.5 * W < out["sum_w"][0] < 2.0 * W, out["sum_w"][0]
+    assert out["pop"][0] <= 2 * W

@@ -83,20 +83,104 @@ def _dmc_run_worker(rank, world, port):
         R = torch.zeros((16, 1, 3), dtype=torch.float64)
         seen = []
 
-        def step(W, E_T):  # a stand-in step: rank 0 grows by 3, rank 1 shrinks by 1; E_L = -1 - rank
+        keys = []
+
+        def step(W, E_T, k, off):  # a stand-in step: rank 0 grows by 3, rank 1 shrinks by 1; E_L = -1 - rank
             seen.append(E_T)
+            keys.append((k, off))
             W2 = W + 3 if rank == 0 else max(W - 1, 0)
             R[:W2, 0, 0] = float(rank)
             return W2, (-1.0 - rank) * W2, float(W2)
-        W, E_T, hist = ranks.dmc_run(step, R, 4, 3, tau=0.01, E_T=-1.0, target_per_rank=4)
+        W, E_T, hist = ranks.dmc_run(step, R, 4, 3, tau=0.01, E_T=-1.0, target_per_rank=4, step0=100)
         # every rank sees the same global sums and trial energies
         assert [h[2] for h in hist] == [10, 12, 14]
         gwE, gw, gpop = hist[-1]
         assert abs(E_T - (gwE / gw - 10.0 * math.log(gpop / 8))) < 1e-12
         assert W == 7 and seen[0] == -1.0 and len(set(seen)) == 3
+        # the random-number keys: global step numbers, and walker ranges [off, off + cap) that
+        # differ between the ranks (the streams of vbqmc_dmc_steps never coincide)
+        assert [k for k, _ in keys] == [100, 101, 102]
+        offs = [torch.tensor([keys[0][1]]) for _ in range(world)]
+        dist.all_gather(offs, torch.tensor([keys[0][1]]))
+        lo = sorted(int(o) for o in offs)
+        assert lo == [0, 16] and lo[1] - lo[0] >= R.shape[0]
     finally:
         dist.destroy_process_group()
 
 
 def test_dmc_run_two_gloo_ranks():
     torch.multiprocessing.spawn(_dmc_run_worker, args=(2, _free_port()), nprocs=2, join=True)
+
+
+def _failure_worker(rank, world, port, mode):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    try:
+        if mode == "step":
+            R = torch.zeros((8, 1, 3), dtype=torch.float64)
+
+            def step(W, E_T, k, off):  # rank 1 fails at its second step
+                if rank == 1 and k == 1:
+                    raise ValueError("capacity exceeded on rank 1")
+                return W, -1.0 * W, float(W)
+            try:
+                ranks.dmc_run(step, R, 4, 5, tau=0.01, E_T=-1.0, target_per_rank=4)
+            except ValueError as e:
+                assert rank == 1 and "rank 1" in str(e)
+            except ranks.RankFailure as e:
+                assert rank == 0 and "1 other rank" in str(e)
+            else:
+                raise AssertionError("no rank may continue after a failed step")
+        else:  # a share above one rank's capacity: every rank raises before any transfer
+            R = torch.zeros((12 if rank == 0 else 3, 1, 3), dtype=torch.float64)
+            try:
+                ranks.balance_walkers(R, 12 if rank == 0 else 0)
+            except ValueError as e:
+                assert "rank 1" in str(e)
+            else:
+                raise AssertionError("the overflow must be seen on every rank")
+        # the group is still usable: a collective after the failure completes
+        t = torch.ones(1)
+        dist.all_reduce(t)
+        assert float(t) == world
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("mode", ["step", "capacity"])
+def test_failures_stop_every_rank(mode):
+    torch.multiprocessing.spawn(_failure_worker, args=(2, _free_port(), mode), nprocs=2, join=True)
+
+
+def _lin_worker(rank, world, port):
+    import numpy as np
+    import torch.distributed as dist
+    from oracle import oracle as orc
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(42)
+        M, P = 700, 9
+        O = rng.normal(size=(M, P)) + 2.0 * rng.normal(size=P)
+        dE = rng.normal(size=(M, P))
+        E = -7.0 + rng.normal(size=M) + 0.3 * O[:, 1]
+        w = rng.uniform(0.3, 1.7, M)
+        cut = 250  # uneven parts
+        sl = slice(0, cut) if rank == 0 else slice(cut, M)
+        m = orc.lin_matrices(O[sl], dE[sl], E[sl], w[sl])
+        part = dict(m, wsum=w[sl].sum(), mean=(w[sl, None] * O[sl]).sum(0) / w[sl].sum())
+        got = ranks.merge_lin_parts(part)
+        ref = orc.lin_matrices(O, dE, E, w)
+        for k in ("S", "H", "gL", "gR"):
+            assert np.abs(got[k] - ref[k]).max() <= 1e-12 * np.abs(ref[k]).max(), k
+        assert abs(got["E0"][0] - ref["E0"]) <= 1e-12 * abs(ref["E0"])
+        sw, swe, swe2 = ranks.vmc_energy_moments(w[sl].sum(), (w[sl] * E[sl]).sum(), (w[sl] * E[sl] ** 2).sum())
+        assert abs(swe / sw - (w * E).sum() / w.sum()) < 1e-12
+        assert abs(swe2 / sw - (w * E * E).sum() / w.sum()) < 1e-10
+    finally:
+        dist.destroy_process_group()
+
+
+def test_linear_method_parts_merge_to_the_union():
+    """Two ranks each accumulate the estimators of their own samples; the all-gathered merge
+    equals one accumulation over the union of the samples (S, H, g to 1e-12 of scale)."""
+    torch.multiprocessing.spawn(_lin_worker, args=(2, _free_port()), nprocs=2, join=True)

@@ -1,6 +1,7 @@
 """Structure overlap and weights of the JVB structures (arXiv:2207.14715, Sec. 2.4): the oracle's
-ratios Psi_I/Psi_0 and both sides' host formulas against closed forms and identities.  (The GPU
-side of the overlap is in test_gpu_structure_weights.py.)"""
+ratios Psi_I/Psi_0, and the weight formulas of the oracle and of the library
+(vbqmc_structure_weights, host code of the C ABI), against closed forms and identities.  (The
+GPU side of the overlap is in test_gpu_structure_weights.py.)"""
 import dataclasses
 import math
 
@@ -75,29 +76,6 @@ def test_oracle_single_structure(orc):
     w_cc, w_l = orc.structure_weights(orc.structure_overlap(X), spec.c_vb)
     np.testing.assert_allclose(w_cc, [1.0])
     np.testing.assert_allclose(w_l, [1.0])
-
-
-def test_host_assembly_recovers_the_missing_structure(orc):
-    """The product's host step rebuilds the row of a structure left out of cparam from
-    sum_I c_I R_I = 1; with the exact means and centred products of the other columns it must
-    reproduce the full sample average (weighted and unweighted)."""
-    spec = S.small_open_shell()
-    R = S.initial_walkers(spec, 50, 9)
-    X = orc.structure_ratios(spec, R)
-    c = np.asarray(spec.c_vb)
-    rng = np.random.default_rng(2)
-    for w in (None, rng.uniform(0.2, 2.0, len(X))):
-        ref = orc.structure_overlap(X, w)
-        ww = np.ones(len(X)) if w is None else w
-        for miss in range(len(c)):
-            cp = [I for I in range(len(c)) if I != miss]
-            mean = (ww[:, None] * X[:, cp]).sum(0) / ww.sum()
-            Xc = X[:, cp] - mean
-            cov = (ww[:, None] * Xc).T @ Xc / ww.sum()
-            got = vbqmc.assemble_structure_overlap(mean, cov, cp, c)
-            np.testing.assert_allclose(got, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
-    with pytest.raises(vbqmc.VbqmcError):
-        vbqmc.assemble_structure_overlap(mean[:1], cov[:1, :1], [0], c)
 
 
 @pytest.mark.parametrize("maker, keep", [(S.h2_vb, [0]), (S.h2_vb, [1, 2]), (S.ethylene_vb, [0, 2, 5]),
