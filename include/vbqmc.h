@@ -15,9 +15,11 @@
  *
  * Conventions
  *   - Electrons 0..n_up-1 are spin up, n_up..N-1 spin down (spins fixed, Sec. 2.3.1).
- *   - Basis: uncontracted normalised cartesian Gaussians; a shell of angular momentum l
- *     (0, 1, 2) contributes 1, 3, 6 functions in the order s; x y z; xx yy zz xy xz yz.
- *     zeta = 0 denotes the constant function 1.
+ *   - Basis: uncontracted normalised cartesian Gaussians N x^a y^b z^c e^{-zeta r^2} or, per
+ *     shell (sh_kind), Slater functions N x^a y^b z^c e^{-zeta r} (the paper's all-electron
+ *     basis, Sec. 2.1, whose 1s shells carry the nuclear cusp so that a_1 = 0); a shell of
+ *     angular momentum l (0, 1, 2) contributes 1, 3, 6 functions in the order s; x y z;
+ *     xx yy zz xy xz yz.  A Gaussian zeta = 0 denotes the constant function 1.
  *   - Walker positions R are walker-major: R[w][i][d] (double), w < W, i < N, d < 3.
  *     Per-walker outputs are [W]; parameter derivatives are [W][P] (double).
  *   - Parameters p, in this order: c_I for I in cparam; if jas_param: a_2..a_6 per
@@ -87,6 +89,8 @@ typedef struct vbqmc_system_desc {
   int jas_param;           /* nonzero: Jastrow parameters are parameters */
   int n_kappa;
   const int* kappa_kl;     /* [n_kappa][2] orbital excitations (k, l): phi_l -> phi_l + kappa phi_k */
+  const int* sh_kind;      /* [S] 0 Gaussian, 1 Slater (N x^a y^b z^c e^{-zeta r}, zeta > 0), or NULL:
+                              all Gaussian */
 } vbqmc_system_desc;
 
 /* Creates a context on CUDA device 'device' (the calling thread's current device is
@@ -158,7 +162,8 @@ int vbqmc_eval_walkers(vbqmc_ctx* ctx, int sys_id, int precision, int W, const d
  *   dEL_dR      [W][Nn][3] device double or NULL, out: dE_L / dR_a
  * precision: VBQMC_FP64, or VBQMC_MIXED (bulk arithmetic in float as in the evaluation, the
  * sums over determinants and the potential term in double).  W may be 0.  Errors:
- * VBQMC_ERR_CAPACITY if the per-walker tables do not fit in shared memory. */
+ * VBQMC_ERR_CAPACITY if the per-walker tables do not fit in shared memory;
+ * VBQMC_ERR_UNSUPPORTED for systems with Slater shells or on reference-determinant tables. */
 int vbqmc_eval_nuclear_derivs(vbqmc_ctx* ctx, int sys_id, int precision, int W, const double* R, double* logpsi,
                               double* sign, double* eloc, double* dlogpsi_dR, double* dEL_dR, void* stream);
 
@@ -195,7 +200,10 @@ int vbqmc_weighted_colsum(vbqmc_ctx* ctx, int W, int K, int jtype, const double*
  * by vbqmc_eval_walkers (one walker-step = one sweep + that evaluation).  With a state and
  * nsweeps > 0 the evaluation takes the carried inverses instead of factorising the Slater
  * matrices, except when step0 + nsweeps is a multiple of refresh (refresh > 0): then it
- * factorises afresh and rewrites the state (refresh = 1: always). */
+ * factorises afresh and rewrites the state (refresh = 1: always).  Systems on the
+ * reference-determinant tables (vbqmc_use_tables) carry the reference inverse, the tables and
+ * the minors through the moves instead (Sherman-Morrison on the reference, a rank-1 update of
+ * the tables), refreshed the same way; they keep no state (state must be NULL). */
 int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R, int nsweeps, double step,
                     uint64_t seed, uint32_t step0, uint32_t system_tag, uint32_t walker_offset, int refresh,
                     double* state, int state_valid, int* nacc, double* logpsi, double* sign, double* eloc,
@@ -395,6 +403,18 @@ int vbqmc_kernel_times(vbqmc_ctx* ctx, double* ms, int max, int* n);
  * thread block and shared-memory bytes per walker of the evaluation's determinant kernel, then
  * the same two numbers for the sweep kernel, for the given precision mode. */
 int vbqmc_launch_info(vbqmc_ctx* ctx, int sys_id, int precision, int* out);
+
+/* Chooses how the determinant part of a loaded system is carried (Sec. 2.1: the determinants
+ * of a spin share the inactive orbitals and differ from the first one by a few active
+ * columns).  on = 0: every unique determinant's inverse (walker state, orbital-excitation and
+ * nucleus derivatives available); on = 1: the first determinant of each spin as reference, its
+ * inverse B and the tables T = B Phi_X, every other determinant as a k x k minor (k <= 4):
+ * VMC sweeps and evaluations keep no walker state, orbital-excitation and nucleus derivatives
+ * are refused.  vbqmc_set_system takes the tables only when the per-determinant inverses of one
+ * walker do not fit in shared memory.  Errors: VBQMC_ERR_NOSYS, VBQMC_ERR_UNSUPPORTED (a
+ * determinant differs from the reference in more than 4 columns), VBQMC_ERR_CAPACITY (on = 0
+ * but the inverses do not fit). */
+int vbqmc_use_tables(vbqmc_ctx* ctx, int sys_id, int on);
 
 /* Number of kernel launches enqueued by the last successful call on this context. */
 int vbqmc_last_launch_count(vbqmc_ctx* ctx);

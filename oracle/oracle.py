@@ -39,6 +39,7 @@ class _OrcSystem(ctypes.Structure):
         ("n_cparam", ctypes.c_int), ("cparam", _c_int_p),
         ("jas_param", ctypes.c_int),
         ("n_kappa", ctypes.c_int), ("kappa_kl", _c_int_p),
+        ("sh_kind", _c_int_p),
     ]
 
 
@@ -106,6 +107,7 @@ def _pack(spec):
     s.n_cparam, s.cparam = len(spec.cparam), i(spec.cparam)
     s.jas_param = int(spec.jas_param)
     s.n_kappa, s.kappa_kl = len(spec.kappa_kl), i(spec.kappa_kl)
+    s.sh_kind = i(spec.sh_kind) if getattr(spec, "sh_kind", None) is not None else None
     return s, keep
 
 

@@ -22,7 +22,9 @@
 //
 // Readings where the paper is silent (each is listed in the design notes of the repo):
 //   * basis: uncontracted, normalised cartesian Gaussians, d shells with 6 components;
-//     zeta = 0 denotes the constant function 1 (normalisation taken as 1).
+//     zeta = 0 denotes the constant function 1 (normalisation taken as 1).  Shells may instead
+//     be Slater-type (the paper's all-electron basis, Sec. 2.1): N x^a y^b z^c exp(-zeta r)
+//     with n = l + 1, zeta > 0, normalised to 1.
 //   * i = j self-pairs: the factor 2 of Sec. 2.1 is dropped (structures are unnormalised).
 //   * determinant columns: orbitals in creation-string order after moving all up-spin
 //     operators in front of all down-spin ones; the permutation parity is the sign d_{I,k}.
@@ -241,6 +243,7 @@ typedef struct orc_system {
   int jas_param;          // 1: a2..a6 per element, b2..b6, theta per element are parameters
   int n_kappa;
   const int* kappa_kl;    // [n_kappa][2] = (k, l): excitation from l to k
+  const int* sh_kind;     // [S] 0 Gaussian, 1 Slater (NULL: all Gaussian)
 } orc_system;
 }
 
@@ -341,6 +344,7 @@ struct Sys {
   std::vector<int> nuc_elem;
   std::vector<int> sh_center, sh_l, sh_first;
   std::vector<double> sh_zeta, sh_norm;  // norm per component: [S][6]
+  std::vector<int> sh_kind;              // 0 Gaussian, 1 Slater
   std::vector<double> lam;               // [Norb][M]
   std::vector<double> c_vb;
   std::vector<DetTerm> terms;
@@ -423,6 +427,8 @@ static int build_sys(const orc_system* in, Sys& s) {
   s.sh_center.assign(in->sh_center, in->sh_center + s.S);
   s.sh_l.assign(in->sh_l, in->sh_l + s.S);
   s.sh_zeta.assign(in->sh_zeta, in->sh_zeta + s.S);
+  s.sh_kind.assign(s.S, 0);
+  if (in->sh_kind) s.sh_kind.assign(in->sh_kind, in->sh_kind + s.S);
   s.sh_first.resize(s.S);
   s.sh_norm.assign((size_t)s.S * 6, 0.0);
   int M = 0;
@@ -434,7 +440,16 @@ static int build_sys(const orc_system* in, Sys& s) {
     for (int c = 0; c < NCOMP[l]; ++c) {
       const int* e = CART[CART_OFF[l] + c];
       double nrm;
-      if (z == 0.0) nrm = 1.0;  // constant function
+      if (s.sh_kind[i] == 1) {
+        // Slater: int x^2a y^2b z^2c e^{-2 z r} d^3r = [4 pi (2a-1)!!(2b-1)!!(2c-1)!! / (2l+1)!!]
+        //         x (2l+2)! / (2z)^(2l+3)
+        if (!(z > 0.0)) return -1;
+        double fact = 1.0;
+        for (int k = 2; k <= 2 * l + 2; ++k) fact *= k;
+        const double integral = 4.0 * M_PI * dfact(2 * e[0] - 1) * dfact(2 * e[1] - 1) * dfact(2 * e[2] - 1) /
+                                dfact(2 * l + 1) * fact / std::pow(2.0 * z, 2 * l + 3);
+        nrm = 1.0 / std::sqrt(integral);
+      } else if (z == 0.0) nrm = 1.0;  // constant function
       else
         nrm = std::pow(2.0 * z / M_PI, 0.75) * std::pow(4.0 * z, 0.5 * l) /
               std::sqrt(dfact(2 * e[0] - 1) * dfact(2 * e[1] - 1) * dfact(2 * e[2] - 1));
@@ -537,6 +552,8 @@ template <class T> static Params<T> make_params(const Sys& s, int dir) {
 // Cartesian Gaussian values, gradients and Laplacians at point r (closed form):
 // chi = N P(x) e^{-z r^2};  grad chi = N e (grad P - 2 z x P);
 // lap chi = N e (lap P + P (4 z^2 r^2 - 6 z - 4 z l)).
+// Slater shells: chi = N P(x) e^{-z r};  grad chi = N e (grad P - z x P / r);
+// lap chi = N e (lap P + P (z^2 - 2 z (l + 1) / r))  (grad P . x = l P for the degree-l monomial).
 // The centres are nuc (type T, so that a tangent on a nucleus position carries through).
 template <class T>
 static void basis_at(const Sys& s, const std::vector<T>& nuc, const double* r, T* chi, T* dchi, T* lchi) {
@@ -545,7 +562,9 @@ static void basis_at(const Sys& s, const std::vector<T>& nuc, const double* r, T
     T x[3] = {r[0] - nuc[3 * c], r[1] - nuc[3 * c + 1], r[2] - nuc[3 * c + 2]};
     T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     double z = s.sh_zeta[sh];
-    T e = vexp(r2 * (-z));
+    const bool slater = s.sh_kind[sh] == 1;
+    T rr = slater ? vsqrt(r2) : T(0.0);
+    T e = slater ? vexp(rr * (-z)) : vexp(r2 * (-z));
     for (int q = 0; q < NCOMP[l]; ++q) {
       const int* ex = CART[CART_OFF[l] + q];
       double nrm = s.sh_norm[(size_t)sh * 6 + q];
@@ -561,7 +580,8 @@ static void basis_at(const Sys& s, const std::vector<T>& nuc, const double* r, T
             for (int o = 0; o < 3; ++o)
               if (o != d) dP = dP * ipow(x[o], ex[o]);
           }
-          dchi[3 * mu + d] = e * (dP - x[d] * P * (2.0 * z)) * nrm;
+          if (slater) dchi[3 * mu + d] = e * (dP - x[d] * P * z / rr) * nrm;
+          else dchi[3 * mu + d] = e * (dP - x[d] * P * (2.0 * z)) * nrm;
         }
         T lapP(0.0);
         for (int d = 0; d < 3; ++d)
@@ -571,7 +591,8 @@ static void basis_at(const Sys& s, const std::vector<T>& nuc, const double* r, T
               if (o != d) t = t * ipow(x[o], ex[o]);
             lapP = lapP + t;
           }
-        lchi[mu] = e * (lapP + P * (r2 * (4.0 * z * z) - (6.0 * z + 4.0 * z * l))) * nrm;
+        if (slater) lchi[mu] = e * (lapP + P * (z * z - (2.0 * z * (l + 1)) / rr)) * nrm;
+        else lchi[mu] = e * (lapP + P * (r2 * (4.0 * z * z) - (6.0 * z + 4.0 * z * l))) * nrm;
       }
     }
   }

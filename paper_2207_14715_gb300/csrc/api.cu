@@ -48,6 +48,15 @@ int set_error(int code, const std::string& msg) { return fail(code, msg); }
 int set_cuda_error(int cuda_error, const char* what) { return cuda_fail((cudaError_t)cuda_error, what); }
 }  // namespace vbq
 
+static void make_layouts(const vbqmc_ctx* ctx, LoadedSystem& ls) {
+  for (int p = 0; p < 2; ++p) {
+    const int tb = p == VBQMC_MIXED ? 4 : 8;
+    ls.lay_rc_eval[p] = vbq::make_eval_layout(ls.dev, tb, ctx->max_smem, ls.lay_eval[p]);
+    ls.lay_rc_sweep[p] = vbq::make_sweep_layout(ls.dev, tb, ctx->max_smem, ls.lay_sweep[p]);
+    ls.lay_rc_force[p] = vbq::make_force_layout(ls.dev, tb, ctx->max_smem, ls.lay_force[p]);
+  }
+}
+
 static void free_system(LoadedSystem& s) {
   if (s.blob) cudaFree(s.blob);
   s = LoadedSystem();
@@ -178,7 +187,8 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
                o_zf = bb.add(zeta_f), o_nf = bb.add(norm_f), o_jaf = bb.add(jas_af), o_jbf = bb.add(jas_bf),
                o_ebf = bb.add(een_Bf), o_nzf = bb.add(nuc_zf), o_nsh = bb.add(h.nuc_sh), o_sbl = bb.add(h.sh_by_l), o_shp = bb.add(sh_pack),
                o_jads = bb.add(split(h.jas_a)), o_jbds = bb.add(split(h.jas_b)), o_ecds = bb.add(split(h.een_c)), o_tx0 = bb.add(h.tab_x[0]),
-               o_tx1 = bb.add(h.tab_x[1]), o_td0 = bb.add(h.tab_det[0]), o_td1 = bb.add(h.tab_det[1]);
+               o_tx1 = bb.add(h.tab_x[1]), o_td0 = bb.add(h.tab_det[0]), o_td1 = bb.add(h.tab_det[1]),
+               o_txl0 = bb.add(h.tab_xl[0]), o_txl1 = bb.add(h.tab_xl[1]);
   cudaError_t e = cudaMalloc(&ls.blob, bb.bytes.size());
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(system tables)");
   ls.blob_bytes = bb.bytes.size();
@@ -233,6 +243,8 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.tab_x[1] = (const int*)(B + o_tx1);
   d.tab_det[0] = (const int*)(B + o_td0);
   d.tab_det[1] = (const int*)(B + o_td1);
+  d.tab_xl[0] = (const int*)(B + o_txl0);
+  d.tab_xl[1] = (const int*)(B + o_txl1);
   d.n_x[0] = (int)h.tab_x[0].size();
   d.n_x[1] = (int)h.tab_x[1].size();
   d.term_det = (const int*)(B + o_term_det);
@@ -299,12 +311,7 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
     vbq::DetLayout probe;
     if (h.tab_ok && vbq::make_det_layout(d, 8, ctx->max_smem, probe) != VBQMC_OK) d.msd = 1;
   }
-  for (int p = 0; p < 2; ++p) {
-    const int tb = p == VBQMC_MIXED ? 4 : 8;
-    ls.lay_rc_eval[p] = vbq::make_eval_layout(d, tb, ctx->max_smem, ls.lay_eval[p]);
-    ls.lay_rc_sweep[p] = vbq::make_sweep_layout(d, tb, ctx->max_smem, ls.lay_sweep[p]);
-    ls.lay_rc_force[p] = vbq::make_force_layout(d, tb, ctx->max_smem, ls.lay_force[p]);
-  }
+  make_layouts(ctx, ls);
   ls.loaded = true;
   free_system(ctx->sys[sys_id]);
   ctx->sys[sys_id] = ls;
@@ -312,6 +319,25 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
 }
 
 int vbqmc_last_launch_count(vbqmc_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+int vbqmc_use_tables(vbqmc_ctx* ctx, int sys_id, int on) {
+  if (!ctx) return fail(VBQMC_ERR_ARG, "null context");
+  if (sys_id < 0 || sys_id >= VBQMC_MAX_SYSTEMS || !ctx->sys[sys_id].loaded)
+    return fail(VBQMC_ERR_NOSYS, "no system loaded under this id");
+  LoadedSystem& ls = ctx->sys[sys_id];
+  if (on) {
+    if (!ls.host.tab_ok)
+      return fail(VBQMC_ERR_UNSUPPORTED, "a determinant differs from the reference by more than 4 orbitals");
+    ls.dev.msd = 1;
+  } else {
+    vbq::DetLayout probe;
+    if (vbq::make_det_layout(ls.dev, 8, ctx->max_smem, probe) != VBQMC_OK)
+      return fail(VBQMC_ERR_CAPACITY, "per-determinant inverses of one walker exceed shared memory");
+    ls.dev.msd = 0;
+  }
+  make_layouts(ctx, ls);
+  return VBQMC_OK;
+}
 
 int vbqmc_launch_info(vbqmc_ctx* ctx, int sys_id, int precision, int* out) {
   if (!ctx || !out) return fail(VBQMC_ERR_ARG, "null argument");
@@ -405,6 +431,7 @@ int vbqmc_eval_nuclear_derivs(vbqmc_ctx* ctx, int sys_id, int precision, int W, 
   LoadedSystem& s = ctx->sys[sys_id];
   if (s.lay_rc_eval[precision]) return fail(s.lay_rc_eval[precision], "per-walker state exceeds shared memory");
   if (s.dev.msd) return fail(VBQMC_ERR_UNSUPPORTED, "nucleus derivatives with reference-determinant tables");
+  if (s.host.has_slater) return fail(VBQMC_ERR_UNSUPPORTED, "nucleus derivatives of Slater shells");
   if (s.lay_rc_force[precision])
     return fail(s.lay_rc_force[precision], "nucleus-derivative tables exceed shared memory");
   DeviceGuard g(ctx->device);
@@ -533,7 +560,8 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
   if (W == 0) return VBQMC_OK;
   if (!R) return fail(VBQMC_ERR_ARG, "null R");
   LoadedSystem& s = ctx->sys[sys_id];
-  if (s.dev.msd) return fail(VBQMC_ERR_UNSUPPORTED, "VMC sweeps need per-determinant inverses (use DMC steps)");
+  if (s.dev.msd && (state || state_valid))
+    return fail(VBQMC_ERR_UNSUPPORTED, "systems on reference-determinant tables keep no walker state (pass NULL)");
   if (s.lay_rc_sweep[precision]) return fail(s.lay_rc_sweep[precision], "per-walker state exceeds shared memory");
   const bool do_eval = logpsi || sign || eloc || O || dEL;
   if (do_eval && (!logpsi || !sign || !eloc)) return fail(VBQMC_ERR_ARG, "evaluation needs logpsi, sign and eloc");

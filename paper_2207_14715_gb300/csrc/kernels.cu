@@ -9,15 +9,74 @@
 
 namespace vbq {
 
+// q_u = D_u / D_0 of a determinant u given by the reference-determinant tables: sign_u times
+// the k x k determinant of T[S_u, Q_u] + b[S_u] c[Q_u]^T (k <= 4; b = null: T alone), by
+// elimination with partial pivoting.  T [n][nx] row-major; td = the determinant's table row.
+__device__ __forceinline__ double tab_ratio(const double* T, int nx, const int* __restrict__ td, const double* b,
+                                            const double* c) {
+  const int k = __ldg(td);
+  double M[kMaxExc][kMaxExc];
+#pragma unroll
+  for (int i = 0; i < kMaxExc; ++i)
+#pragma unroll
+    for (int j = 0; j < kMaxExc; ++j) {
+      double v = (i == j) ? 1.0 : 0.0;
+      if (i < k && j < k) {
+        const int si = __ldg(td + 2 + i), qj = __ldg(td + 2 + kMaxExc + j);
+        v = T[si * nx + qj];
+        if (b) v = fma(b[si], c[qj], v);
+      }
+      M[i][j] = v;
+    }
+  double det = (double)__ldg(td + 1);
+#pragma unroll
+  for (int col = 0; col < kMaxExc; ++col) {
+#pragma unroll
+    for (int r = col + 1; r < kMaxExc; ++r)
+      if (fabs(M[r][col]) > fabs(M[col][col])) {
+#pragma unroll
+        for (int j = 0; j < kMaxExc; ++j) {
+          const double t = M[col][j];
+          M[col][j] = M[r][j];
+          M[r][j] = t;
+        }
+        det = -det;
+      }
+    const double p = M[col][col];
+    det *= p;
+    if (p == 0.0) return 0.0;
+    const double ip = 1.0 / p;
+#pragma unroll
+    for (int r = col + 1; r < kMaxExc; ++r) {
+      const double f = M[r][col] * ip;
+#pragma unroll
+      for (int j = col + 1; j < kMaxExc; ++j) M[r][j] = fma(-f, M[col][j], M[r][j]);
+    }
+  }
+  return det;
+}
+
 // =====================================================================================
 // VMC sweep kernel
 // =====================================================================================
+// Two ways of carrying the determinants through the moves (template parameter TAB):
+//  - per-determinant inverses (TAB = false): every unique determinant's inverse is updated by
+//    Sherman-Morrison on an accepted move (Sec. 2.3.1); the ratio of determinant u is
+//    rho_u = sum_o v_o Binv_u[o][i].
+//  - reference-determinant tables (TAB = true; systems whose per-determinant inverses do not
+//    fit in shared memory): each spin carries the inverse B of its reference determinant
+//    (u = 0), T = B Phi_X over the orbitals X outside the reference, and q_u = D_u / D_0 =
+//    sgn_u det T[S_u, Q_u].  Moving electron i to a point with orbital row v gives
+//      rho_0 = sum_o v_o B[o][i],  c_x = v_x - sum_o v_o T[o][x],  b = B[:, i] / rho_0,
+//      T' = T + b c^T,  q'_u = sgn_u det T'[S_u, Q_u],
+//    and Phi'/Phi = rho_0 Sigma' / Sigma with Sigma = sum_k C_k q_up(k) q_dn(k); an accepted move
+//    updates B by Sherman-Morrison, T to T' and q to q'.
 // Each sweep moves every electron once (Sec. 2.3.1).  The determinant inverses come from
 // the walker state written by the evaluation at the same positions, or from a fresh LU of
 // double-precision orbital values (first sweep without state, and every 'refresh' sweeps).
 // The proposed orbital row uses the bulk type; ratios and Sherman-Morrison updates are double.
 // One warp, walker w, shared-memory region 'base' of L.warp_bytes bytes.
-template <class Tb>
+template <class Tb, bool TAB>
 __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L, int w, unsigned char* base,
                                            double* __restrict__ Rg, int nsweeps, int refresh,
                                            double* __restrict__ state, int state_valid, double step, uint64_t seed,
@@ -89,7 +148,13 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   // [1, 2) and a binary exponent (bit operations; one logarithm per sweep instead of one per move)
   double pm = 1.0;
   int pe = 0;
-  const bool from_state = state && state_valid;
+  // reference-determinant tables (TAB): T per spin, q_u of both spins in wk, proposed q_u,
+  // the move's c_x, and Sigma = sum_k C_k q_up q_dn
+  double* Tt[2] = {reinterpret_cast<double*>(base + L.T0), reinterpret_cast<double*>(base + L.T1)};
+  double* qn = reinterpret_cast<double*>(base + L.qn);
+  double* cxv = reinterpret_cast<double*>(base + L.cx);
+  double Sig = 1.0;
+  const bool from_state = !TAB && state && state_valid;
   if (from_state) {
     const double* st = state + (size_t)w * s.state_doubles;
     for (int q = lane; q < nb0; q += 32) Binv[0][q] = st[q];
@@ -127,11 +192,52 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         }
         __syncwarp();
       }
-      lu_all(s, 0, lane, PhiO, ldo, (const double*)nullptr, 0, s.det_loc[0], L.G0, Binv[0], scr, ldet, dsg, nullptr);
-      lu_all(s, 1, lane, PhiO, ldo, (const double*)nullptr, 0, s.det_loc[1], L.G1, Binv[1], scr, ldet + U0, dsg + U0,
-             nullptr);
+      if constexpr (TAB) {
+        // per spin: LU of the reference determinant, T = B Phi_X, every q_u
+        for (int sp = 0; sp < 2; ++sp) {
+          const int n = s.n[sp], e0 = sp ? Nup : 0, nx = s.n_x[sp], U = s.U[sp], uo = sp ? U0 : 0;
+          if (n == 0) {
+            for (int u = lane; u < U; u += 32) wk[uo + u] = 1.0;
+            __syncwarp();
+            continue;
+          }
+          int G = 1;
+          while (G < n) G <<= 1;
+          const LaneGroup lg(lane, G);
+          const bool act = lg.g == 0;
+          double* A = scr;
+          int* perm = reinterpret_cast<int*>(scr + n * n);
+          if (act && lg.gl < n) {
+            const int col = __ldg(s.det_loc[sp] + lg.gl);
+            for (int e = 0; e < n; ++e) A[e * n + lg.gl] = PhiO[(e0 + e) * ldo + col];
+          }
+          __syncwarp();
+          double lgd, sgd;
+          group_lu_inverse(A, Binv[sp], perm, n, lg.gl, G, act, lgd, sgd);
+          const double* B = Binv[sp];
+          for (int t = lane; t < n * nx; t += 32) {
+            const int o = t / nx, x = t - o * nx, col = __ldg(s.tab_xl[sp] + x);
+            double v = 0.0;
+            for (int e = 0; e < n; ++e) v = fma(B[o * n + e], PhiO[(e0 + e) * ldo + col], v);
+            Tt[sp][t] = v;
+          }
+          __syncwarp();
+          for (int u = lane; u < U; u += 32)
+            wk[uo + u] = tab_ratio(Tt[sp], nx, s.tab_det[sp] + u * kTabStride, nullptr, nullptr);
+          __syncwarp();
+        }
+        double sg = 0.0;
+        for (int k = lane; k < s.nterm; k += 32)
+          sg = fma(__ldg(s.term_coef + k), wk[__ldg(s.term_det + 2 * k)] * wk[U0 + __ldg(s.term_det + 2 * k + 1)], sg);
+        Sig = warp_sum(sg);
+      } else {
+        lu_all(s, 0, lane, PhiO, ldo, (const double*)nullptr, 0, s.det_loc[0], L.G0, Binv[0], scr, ldet, dsg,
+               nullptr);
+        lu_all(s, 1, lane, PhiO, ldo, (const double*)nullptr, 0, s.det_loc[1], L.G1, Binv[1], scr, ldet + U0,
+               dsg + U0, nullptr);
+      }
     }
-    if (do_refresh) {
+    if (!TAB && do_refresh) {
       term_ratios(s, lane, ldet, dsg, wk, lnPhi, sgnPhi);  // wk: r_k = D_k / Phi
       pm = 1.0;
       pe = 0;
@@ -196,21 +302,51 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         vrowd[q] = (double)v;
       }
       __syncwarp();
-      // determinant ratios rho_u = sum_o v_occ(o) Binv_u[o][ie]
       const LaneGroup lgp(lane, G);
       const int U = s.U[sp], ng = lgp.ng, g = lgp.g, gl = lgp.gl;
       const int* dl = s.det_loc[sp];
-      for (int ub = 0; ub < U; ub += ng) {
-        const int u = ub + g;
-        double r = 0.0;
-        if (u < U && gl < n) r = vrowd[__ldg(dl + u * n + gl)] * Binv[sp][u * n * n + gl * n + ie];
-        r = group_sum(r, G);
-        if (u < U && gl == 0) rho[u] = r;
+      double rphi = 0.0, r0 = 0.0, Sig_new = 0.0;
+      if constexpr (TAB) {
+        // rho_0, c_x, b = B[:, i] / rho_0 (in cvec), the proposed q_u and Sigma'
+        const int nx = s.n_x[sp], uo = sp ? U0 : 0;
+        const double* B = Binv[sp];
+        const double* T = Tt[sp];
+        if (lane < n) r0 = vrowd[__ldg(dl + lane)] * B[lane * n + ie];
+        r0 = warp_sum(r0);
+        for (int x = lane; x < nx; x += 32) {
+          double cc = vrowd[__ldg(s.tab_xl[sp] + x)];
+          for (int o = 0; o < n; ++o) cc = fma(-vrowd[__ldg(dl + o)], T[o * nx + x], cc);
+          cxv[x] = cc;
+        }
+        const double ir0 = r0 != 0.0 ? 1.0 / r0 : 0.0;
+        if (lane < n) cvec[lane] = B[lane * n + ie] * ir0;
+        __syncwarp();
+        for (int u = lane; u < U; u += 32) qn[u] = tab_ratio(T, nx, s.tab_det[sp] + u * kTabStride, cvec, cxv);
+        __syncwarp();
+        double sg = 0.0;
+        for (int k = lane; k < s.nterm; k += 32) {
+          const int a = __ldg(s.term_det + 2 * k), b = __ldg(s.term_det + 2 * k + 1);
+          const double qa = sp == 0 ? qn[a] : wk[a], qb = sp == 1 ? qn[b] : wk[U0 + b];
+          sg = fma(__ldg(s.term_coef + k), qa * qb, sg);
+        }
+        Sig_new = warp_sum(sg);
+        rphi = (r0 != 0.0 && Sig != 0.0) ? r0 * Sig_new / Sig : 0.0;
+        if (!isfinite(rphi)) rphi = 0.0;  // an overflowing ratio is rejected (the tables are refreshed)
+        (void)uo;
+      } else {
+        // determinant ratios rho_u = sum_o v_occ(o) Binv_u[o][ie]
+        for (int ub = 0; ub < U; ub += ng) {
+          const int u = ub + g;
+          double r = 0.0;
+          if (u < U && gl < n) r = vrowd[__ldg(dl + u * n + gl)] * Binv[sp][u * n * n + gl * n + ie];
+          r = group_sum(r, G);
+          if (u < U && gl == 0) rho[u] = r;
+        }
+        __syncwarp();
+        for (int k = lane; k < s.nterm; k += 32)
+          rphi += __ldg(s.term_coef + k) * wk[k] * rho[__ldg(s.term_det + 2 * k + sp)];
+        rphi = warp_sum(rphi);
       }
-      __syncwarp();
-      double rphi = 0.0;
-      for (int k = lane; k < s.nterm; k += 32) rphi += __ldg(s.term_coef + k) * wk[k] * rho[__ldg(s.term_det + 2 * k + sp)];
-      rphi = warp_sum(rphi);
       // Jastrow change of the terms that involve electron e (Sec. 2.1): distances from the
       // proposed position, then items e-n (a), e-e (j) and e-e-n (a, k), the last through the
       // pair sums Y^{k,q} = sum_{j != e} u_ej^k s_j^q (the terms of e are s_e^A Y^{k,B} + s_e^B Y^{k,A}).
@@ -296,7 +432,36 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
       }
       const Tb dJ = warp_sum(dj);
       const double prob = rphi * rphi * (double)vexp((Tb)2 * dJ);
-      if (uacc < prob) {
+      if (TAB && uacc < prob) {
+        // T <- T + b c^T; B <- B - b (v^T B - e_i^T) (b = B[:, i] / rho_0, lane j owns column j:
+        // it reads only its own column before writing it); q <- q'
+        const int nx = s.n_x[sp], uo = sp ? U0 : 0;
+        double* T = Tt[sp];
+        double* B = Binv[sp];
+        for (int t = lane; t < n * nx; t += 32) {
+          const int o = t / nx, x = t - o * nx;
+          T[t] = fma(cvec[o], cxv[x], T[t]);
+        }
+        if (lane < n) {
+          const int j = lane;
+          double w = (j == ie) ? -1.0 : 0.0;
+          for (int o = 0; o < n; ++o) w = fma(vrowd[__ldg(dl + o)], B[o * n + j], w);
+          for (int o = 0; o < n; ++o) B[o * n + j] = fma(-cvec[o], w, B[o * n + j]);
+        }
+        for (int u = lane; u < U; u += 32) wk[uo + u] = qn[u];
+        Sig = Sig_new;
+        if (lane < 3) {
+          R[3 * e + lane] = lane == 0 ? rn[0] : (lane == 1 ? rn[1] : rn[2]);
+          if constexpr (!kSameType<Tb, double>) Rds[3 * e + lane] = lane == 0 ? rnd[0] : (lane == 1 ? rnd[1] : rnd[2]);
+        }
+        for (int j = lane; j < N; j += 32) rEE[e * N + j] = rEE[j * N + e] = rnE[j];
+        for (int a = lane; a < Nn; a += 32) {
+          rEN[e * Nn + a] = rnN[a];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) Stab[a * SA + e * 6 + q] = Snew[a * 6 + q];
+        }
+        ++accepted;
+      } else if (!TAB && uacc < prob) {
         // the reciprocals 1/rho_u and 1/(Phi'/Phi), one per lane
         for (int q = lane; q <= U; q += 32) rinv[q] = recip(q < U ? rho[q] : rphi);
         __syncwarp();
@@ -350,7 +515,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   for (int i = lane; i < 3 * N; i += 32) Rg[(size_t)w * 3 * N + i] = R[i];
   if (nacc && lane == 0) nacc[w] += accepted;
   lnPhi += log(pm) + (double)pe * 0.69314718055994530942;  // ln 2
-  if (state) {  // the carried inverses, term ratios and ln|Phi| at the final positions
+  if (!TAB && state) {  // the carried inverses, term ratios and ln|Phi| at the final positions
     double* st = state + (size_t)w * s.state_doubles;
     for (int q = lane; q < nb0; q += 32) st[q] = Binv[0][q];
     for (int q = lane; q < nb1; q += 32) st[nb0 + q] = Binv[1][q];
@@ -362,7 +527,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   }
 }
 
-template <class Tb>
+template <class Tb, bool TAB>
 __global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const SweepLayout L, int W, double* __restrict__ Rg,
                                                     int nsweeps, int refresh, double* __restrict__ state, int state_valid,
                                                     double step, uint64_t seed, uint32_t step0, uint32_t tag,
@@ -371,8 +536,8 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SysDev s, const Swe
   const int wl = threadIdx.x >> 5;
   const int w = blockIdx.x * L.wpb + wl;
   if (w >= W) return;
-  sweep_body<Tb>(s, L, w, smem + wl * L.warp_bytes, Rg, nsweeps, refresh, state, state_valid, step, seed, step0, tag,
-                 woff, nacc);
+  sweep_body<Tb, TAB>(s, L, w, smem + wl * L.warp_bytes, Rg, nsweeps, refresh, state, state_valid, step, seed, step0,
+                      tag, woff, nacc);
 }
 
 // All systems of a batch: blocks loop over work items; warp wl takes walker first + wl.
@@ -388,7 +553,8 @@ __global__ void __launch_bounds__(512, 1) sweep_batch_kernel(const BatchSys* __r
     const BatchItem item = items[it];
     if (wl >= item.count) continue;
     const BatchSys& b = sys[item.sys];
-    sweep_body<Tb>(b.dev, b.sweep, item.first + wl, smem + wl * b.sweep.warp_bytes, b.R, call->nsweeps, call->refresh,
+    sweep_body<Tb, false>(b.dev, b.sweep, item.first + wl, smem + wl * b.sweep.warp_bytes, b.R, call->nsweeps,
+                          call->refresh,
                    b.state, call->state_valid, call->step, call->seed, call->step0, b.tag, 0u, b.nacc);
   }
 }
@@ -404,14 +570,25 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
     return o;
   };
   const int N = s.N, Ut = s.U[0] + s.U[1];
+  L.tab = s.msd ? 1 : 0;
   L.G0 = group_size(s.n[0]);
   L.G1 = group_size(s.n[1]);
   L.nocc_max = std::max(std::max(s.nocc[0], s.nocc[1]), 1);
   L.R = take(8 * 3 * N);
   L.Rds = take(tb == 4 ? 8 * 3 * N : 16);
-  L.Binv0 = take(8 * s.U[0] * s.n[0] * s.n[0]);
-  L.Binv1 = take(8 * s.U[1] * s.n[1] * s.n[1]);
-  L.wk = take(8 * s.nterm);
+  if (L.tab) {  // reference inverse and tables per spin, q_u of both spins, proposed q_u, c_x
+    L.Binv0 = take(8 * s.n[0] * s.n[0]);
+    L.Binv1 = take(8 * s.n[1] * s.n[1]);
+    L.T0 = take(8 * std::max(s.n[0] * s.n_x[0], 1));
+    L.T1 = take(8 * std::max(s.n[1] * s.n_x[1], 1));
+    L.wk = take(8 * std::max(Ut, 1));
+    L.qn = take(8 * std::max(std::max(s.U[0], s.U[1]), 1));
+    L.cx = take(8 * std::max(std::max(s.n_x[0], s.n_x[1]), 1));
+  } else {
+    L.Binv0 = take(8 * s.U[0] * s.n[0] * s.n[0]);
+    L.Binv1 = take(8 * s.U[1] * s.n[1] * s.n[1]);
+    L.wk = take(8 * s.nterm);
+  }
   // a refactorisation's ln|det|, signs and orbital matrix overlay the sweep's proposals and
   // the move-only geometry (the refactorisation runs before the proposals are formed, and its
   // outputs are consumed by the term ratios before the moves start)
@@ -427,7 +604,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   off = std::max(off, moves_end);
   int cv = 0, scr = 0;
   for (int sp = 0; sp < 2; ++sp) {
-    const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = 32 / G;
+    const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = L.tab ? 1 : 32 / G;
     cv = std::max(cv, 8 * ng * n);
     scr = std::max(scr, ng * (8 * n * n + 4 * n) + 16);
   }
@@ -470,11 +647,16 @@ static cudaError_t launch_sweep_t(const SysDev& s, const SweepLayout& L, int W, 
       if (cost(p) < cost(Lw.wpb)) Lw.wpb = p;
   }
   const int smem = Lw.wpb * Lw.warp_bytes;
-  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Tb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const void* fn = Lw.tab ? (const void*)sweep_kernel<Tb, true> : (const void*)sweep_kernel<Tb, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int blocks = (W + Lw.wpb - 1) / Lw.wpb;
-  sweep_kernel<Tb><<<blocks, 32 * Lw.wpb, smem, st>>>(s, Lw, W, R, nsweeps, refresh, state, state_valid, step, seed, step0,
-                                                      tag, woff, nacc);
+  if (Lw.tab)
+    sweep_kernel<Tb, true><<<blocks, 32 * Lw.wpb, smem, st>>>(s, Lw, W, R, nsweeps, refresh, nullptr, 0, step, seed,
+                                                              step0, tag, woff, nacc);
+  else
+    sweep_kernel<Tb, false><<<blocks, 32 * Lw.wpb, smem, st>>>(s, Lw, W, R, nsweeps, refresh, state, state_valid, step,
+                                                               seed, step0, tag, woff, nacc);
   return cudaGetLastError();
 }
 

@@ -49,9 +49,17 @@ struct EvalLayout {
   DetTabLayout tab;  // used instead of det when the system's msd flag is set
 };
 
+// VMC sweep, warp per walker.  With per-determinant inverses (tab = 0): Binv0/Binv1 hold the
+// inverse of every unique determinant of each spin, wk the term ratios D_k/Phi.  With the
+// reference-determinant tables (tab = 1, systems whose per-determinant inverses do not fit):
+// Binv0/Binv1 hold the reference inverse B of each spin, T0/T1 the tables T = B Phi_X
+// [n][n_x], wk the replacement determinants q_u = D_u/D_0 of both spins [U0 + U1], qn the
+// proposed q_u of the moving electron's spin, cx the vector c_x of the move.
 struct SweepLayout {
   int wpb = 0, warp_bytes = 0;
   int R, Rds, rtab, rtds, Binv0, Binv1, ldet, dsg, wk, PhiO, bas, vrow, part, rho, rinv, cvec, scratch, geo, geom;
+  int T0 = 0, T1 = 0, qn = 0, cx = 0;
+  int tab = 0;
   int nocc_max;
   int G0, G1;
 };

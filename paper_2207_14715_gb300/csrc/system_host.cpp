@@ -309,16 +309,31 @@ int build_system(const vbqmc_system_desc* d, SysHost& s, std::string& err) {
     VBQ_REQUIRE(l >= 0 && l <= 2, "shell " << i << ": l must be 0, 1 or 2");
     VBQ_REQUIRE(s.sh_center[i] >= 0 && s.sh_center[i] < s.Nn, "shell " << i << ": bad center");
     VBQ_REQUIRE(s.sh_zeta[i] >= 0.0 && std::isfinite(s.sh_zeta[i]), "shell " << i << ": bad exponent");
+    const int kind = d->sh_kind ? d->sh_kind[i] : 0;
+    VBQ_REQUIRE(kind == 0 || kind == 1, "shell " << i << ": kind must be 0 (Gaussian) or 1 (Slater)");
+    VBQ_REQUIRE(kind == 0 || s.sh_zeta[i] > 0.0, "shell " << i << ": a Slater shell needs zeta > 0");
     s.sh_first[i] = M;
     const double z = s.sh_zeta[i];
     for (int c = 0; c < kNcomp[l]; ++c) {
       const int* e = kCart[kCartOff[l] + c];
+      const double dfc = double_factorial(2 * e[0] - 1) * double_factorial(2 * e[1] - 1) *
+                         double_factorial(2 * e[2] - 1);
       double nrm = 1.0;
-      if (z > 0.0)
-        nrm = std::pow(2.0 * z / M_PI, 0.75) * std::pow(4.0 * z, 0.5 * l) /
-              std::sqrt(double_factorial(2 * e[0] - 1) * double_factorial(2 * e[1] - 1) *
-                        double_factorial(2 * e[2] - 1));
+      if (kind == 1) {
+        // N^2 = (2 zeta)^(2l+3) (2l+1)!! / (4 pi (2l+2)! (2a-1)!!(2b-1)!!(2c-1)!!): the
+        // monomial's angular integral times the radial integral of r^(2l+2) e^{-2 zeta r}
+        double f = 1.0;
+        for (int k = 2; k <= 2 * l + 2; ++k) f *= k;
+        nrm = std::sqrt(std::pow(2.0 * z, 2 * l + 3) * double_factorial(2 * l + 1) / (4.0 * M_PI * f * dfc));
+      } else if (z > 0.0) {
+        nrm = std::pow(2.0 * z / M_PI, 0.75) * std::pow(4.0 * z, 0.5 * l) / std::sqrt(dfc);
+      }
       s.sh_norm[(size_t)6 * i + c] = nrm;
+    }
+    // device encoding: a Slater shell carries its exponent negated (the kernels branch on the sign)
+    if (kind == 1) {
+      s.sh_zeta[i] = -z;
+      s.has_slater = 1;
     }
     M += kNcomp[l];
   }
@@ -499,6 +514,13 @@ int build_system(const vbqmc_system_desc* d, SysHost& s, std::string& err) {
       }
     for (size_t q = 0; q < xpos.size(); ++q)
       if (xpos[q] == 0) { xpos[q] = (int)s.tab_x[sp].size(); s.tab_x[sp].push_back((int)q); }
+    s.tab_xl[sp].clear();
+    for (int q : s.tab_x[sp]) {
+      const int g = s.ev_orb[q];
+      const int pos = (int)(std::find(s.occ_list[sp].begin(), s.occ_list[sp].end(), g) - s.occ_list[sp].begin());
+      if (pos >= (int)s.occ_list[sp].size()) s.tab_ok = 0;  // every determinant orbital is in occ_list
+      s.tab_xl[sp].push_back(pos);
+    }
     for (int u = 0; u < U; ++u) {
       const int* cols = s.det_ev[sp].data() + (size_t)u * n;
       std::vector<char> in_u(s.ev_orb.size(), 0);

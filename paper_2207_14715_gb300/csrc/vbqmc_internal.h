@@ -31,7 +31,8 @@ struct SysHost {
   std::vector<int> nuc_elem;
   std::vector<int> sh_center, sh_l, sh_first;
   std::vector<int> sh_by_l;            // shells in order of l (lanes of one round run one shell kind)
-  std::vector<double> sh_zeta, sh_norm;  // norm [S][6]
+  std::vector<double> sh_zeta, sh_norm;  // norm [S][6]; zeta < 0: Slater shell with exponent -zeta
+  int has_slater = 0;
   std::vector<int> nuc_sh;             // [Nn][4]: first shell, end shell, first and end basis function
   int max_nuc_mu = 0;                  // most basis functions on one nucleus
   // orbitals: nonzero range [lo, hi) per orbital, coefficients packed
@@ -53,6 +54,7 @@ struct SysHost {
   int tab_ok = 0;
   std::vector<int> tab_x[2];
   std::vector<int> tab_det[2];
+  std::vector<int> tab_xl[2];          // [n_x] position of each tab_x orbital in occ_list[spin]
   // determinant terms: unique (up, dn) pairs with merged coefficients C_k = sum_I c_I d_{I,k}
   std::vector<int> term_det;           // [nterm][2]
   std::vector<double> term_coef;       // [nterm]
@@ -131,6 +133,7 @@ struct SysDev {
   int n_x[2];
   const int* tab_x[2];
   const int* tab_det[2];
+  const int* tab_xl[2];
   const int* term_det;
   const double* term_coef;
   const int* sterm_I;

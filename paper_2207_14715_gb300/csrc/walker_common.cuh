@@ -95,7 +95,10 @@ __device__ __forceinline__ void basis_values_ds(const SysDev& s, int lane, const
     const int c = __ldg(s.sh_center + sh), l = __ldg(s.sh_l + sh), f = __ldg(s.sh_first + sh);
     const float2 zt = __ldg(reinterpret_cast<const float2*>(s.sh_zeta_ds) + sh);
     dsf e = {1.0f, 0.0f};
-    if (zt.x != 0.0f) e = ds_exp_neg(ds_mul(ctab[4 * c + 3], dsf{zt.x, zt.y}));
+    if (zt.x < 0.0f)  // Slater shell: exp(-zeta r), zeta = -z
+      e = ds_exp_neg(ds_mul(ds_sqrt(ctab[4 * c + 3]), dsf{-zt.x, -zt.y}));
+    else if (zt.x != 0.0f)
+      e = ds_exp_neg(ds_mul(ctab[4 * c + 3], dsf{zt.x, zt.y}));
     const float2* nr = reinterpret_cast<const float2*>(s.sh_norm_ds) + 6 * sh;
     if (l == 0) {
       const float2 n0 = __ldg(nr);

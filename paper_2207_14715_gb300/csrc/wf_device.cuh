@@ -214,19 +214,32 @@ __device__ __forceinline__ float vsqrt(float x) { return sqrtf(x); }
 template <class T> __device__ __forceinline__ T tload(const double* p) { return (T)__ldg(p); }
 
 // ------------------------------------------------------------------------------------
-// Cartesian Gaussian shell at displacement d = r - center: for every component
-//   chi = N P e^{-z r^2},  grad chi = N e (grad P - 2 z d P),
-//   lap chi = N e (lap P + P (4 z^2 r^2 - 6 z - 4 z l)),
-// P the cartesian monomial (s; x y z; xx yy zz xy xz yz).  Writes value (and if out_d is
-// non-null gradient and Laplacian) for component c at out[c * stride].
+// Cartesian shell at displacement d = r - center: for every component, with P the cartesian
+// monomial (s; x y z; xx yy zz xy xz yz) of degree l,
+//   Gaussian (z >= 0):   chi = N P e^{-z r^2},  grad chi = N e (grad P - 2 z d P),
+//                        lap chi = N e (lap P + P (4 z^2 r^2 - 6 z - 4 z l));
+//   Slater (z = -zeta < 0): chi = N P e^{-zeta r},  grad chi = N e (grad P - (zeta / r) d P),
+//                        lap chi = N e (lap P + P (zeta^2 - 2 zeta (l + 1) / r))
+// (grad P . d = l P).  Both have the form N e (grad P - t d P) and N e (lap P + P base), so only
+// e, t and base depend on the kind.  Writes value (and if out_d is non-null gradient and
+// Laplacian) for component c at out[c * stride].
 // ------------------------------------------------------------------------------------
 template <class T, bool DERIV, class NT>
 __device__ __forceinline__ void gto_shell(int l, T z, const NT* nrm, T dx, T dy, T dz, T* val, T* gx, T* gy, T* gz,
                                           T* lap, int cs = 1) {
   const T r2 = dx * dx + dy * dy + dz * dz;
-  const T e = (z == (T)0) ? (T)1 : vexp(-z * r2);
-  const T tz = (T)2 * z;
-  const T base = (T)4 * z * z * r2 - (T)6 * z - (T)4 * z * (T)l;
+  T e, tz, base;
+  if (z < (T)0) {
+    const T zeta = -z, r = vsqrt(r2);
+    const T ir = r > (T)0 ? (T)1 / r : (T)0;
+    e = vexp(-zeta * r);
+    tz = zeta * ir;
+    base = zeta * zeta - (T)2 * zeta * (T)(l + 1) * ir;
+  } else {
+    e = (z == (T)0) ? (T)1 : vexp(-z * r2);
+    tz = (T)2 * z;
+    base = (T)4 * z * z * r2 - (T)6 * z - (T)4 * z * (T)l;
+  }
   if (l == 0) {
     const T ne = (T)nrm[0] * e;
     val[0] = ne;

@@ -60,6 +60,7 @@ class SystemSpec:
     jas_param: bool = False
     kappa_kl: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 2), np.int32))
     step: float = 0.3        # VMC step size (bohr)
+    sh_kind: np.ndarray | None = None  # (S,) int32: 0 Gaussian, 1 Slater (None: all Gaussian)
 
     @property
     def N(self) -> int:
@@ -185,6 +186,48 @@ def one_electron(Z: float, zeta: float, a1: float = 0.0, a2: float = 0.0, name: 
         orb_coef=np.ones((1, 1)), orb_class=np.zeros(1, np.int32), orb_kind=np.ones(1, np.int32),
         n_up=1, n_dn=0, c_vb=np.ones(1), inact_off=io, inact=ina, pair_off=po, pairs=prs, unp_off=uo, unp=un,
         jas_a=np.array([[a1, a2, 0, 0, 0, 0]], np.float64), jas_b=np.zeros(6), b1_anti=0.0, b1_par=0.0)
+
+
+def slater_1s(Z: float, zeta: float) -> SystemSpec:
+    """One nucleus of charge Z, one electron in a 1s Slater orbital exp(-zeta r), no Jastrow
+    (a1 = 0, the paper's choice with cusp-correct orbitals).  zeta = Z is the exact ground
+    state: E_L = -Z^2/2 everywhere."""
+    io, ina, po, prs, uo, un = _structures([([], [], [0])])
+    return SystemSpec(
+        name="slater_1s", nuc_xyz=np.zeros((1, 3)), nuc_Z=np.array([float(Z)]), nuc_elem=np.zeros(1, np.int32),
+        n_elem=1, sh_center=np.zeros(1, np.int32), sh_l=np.zeros(1, np.int32), sh_zeta=np.array([float(zeta)]),
+        orb_coef=np.ones((1, 1)), orb_class=np.zeros(1, np.int32), orb_kind=np.ones(1, np.int32),
+        n_up=1, n_dn=0, c_vb=np.ones(1), inact_off=io, inact=ina, pair_off=po, pairs=prs, unp_off=uo, unp=un,
+        jas_a=np.zeros((1, 6)), jas_b=np.zeros(6), b1_anti=0.0, b1_par=0.0, sh_kind=np.ones(1, np.int32))
+
+
+def slater_h2(seed: int = 20220728 + 7) -> SystemSpec:
+    """H2 at R = 1.4 bohr on Slater shells (the paper's all-electron practice, Sec. 2.1): per
+    center a 1s (zeta 1.0), a 2s-like s (zeta 0.6), a p and a d Slater shell, Heitler-London and
+    two ionic structures, e-n Jastrow a1 = 0 (the 1s shells carry the nuclear cusp), e-e Pade,
+    e-e-n terms; c_2, c_3 and the Jastrow parameters are parameters."""
+    rng = np.random.default_rng(seed)
+    xyz = np.array([[0.0, 0.0, -0.7], [0.0, 0.0, 0.7]])
+    sc, sl, sz = [], [], []
+    for c in range(2):
+        for l, z in ((0, 1.0), (0, 0.6), (1, 0.9), (2, 1.3)):
+            sc.append(c), sl.append(l), sz.append(z)
+    sc, sl, sz = np.array(sc, np.int32), np.array(sl, np.int32), np.array(sz)
+    M = int(sum(NCOMP[l] for l in sl))
+    orb = np.zeros((2, M))
+    half = M // 2
+    for c in range(2):
+        orb[c, c * half:(c + 1) * half] = rng.uniform(-0.3, 0.3, half)
+        orb[c, c * half] = 1.0                      # the 1s shell carries the cusp
+    io, ina, po, prs, uo, un = _structures([([], [(0, 1)], []), ([], [(0, 0)], []), ([], [(1, 1)], [])])
+    jas_a = np.array([[0.0, 1.0, 0.02, -0.01, 0.0, 0.0]])
+    return SystemSpec(
+        name="slater_h2", nuc_xyz=xyz, nuc_Z=np.ones(2), nuc_elem=np.zeros(2, np.int32), n_elem=1, sh_center=sc,
+        sh_l=sl, sh_zeta=sz, orb_coef=orb, orb_class=np.array([0, 1], np.int32), orb_kind=np.ones(2, np.int32),
+        n_up=1, n_dn=1, c_vb=np.array([1.0, 0.3, 0.3]), inact_off=io, inact=ina, pair_off=po, pairs=prs,
+        unp_off=uo, unp=un, jas_a=jas_a, jas_b=np.array([0.0, 1.0, 0.01, 0.0, 0.0, 0.0]), een_on=True,
+        een_theta=rng.uniform(-0.02, 0.02, (1, EEN_NFREE)), cparam=np.array([1, 2], np.int32), jas_param=True,
+        sh_kind=np.ones(len(sl), np.int32))
 
 
 def two_electron_product(Z: float, zeta: float) -> SystemSpec:
@@ -337,6 +380,56 @@ def ethylene_vb(seed: int = 20220728 + 1, n_virt_center: int = 15, n_virt_deloc:
         jas_a=jas_a, jas_b=jas_b, een_on=True, een_theta=theta,
         cparam=np.arange(1, 6, dtype=np.int32) if params else np.zeros(0, np.int32),
         jas_param=params, kappa_kl=kap, step=0.3)
+
+
+def bovb(spec: SystemSpec, eps: float = 0.05, seed: int = 20220728 + 9) -> SystemSpec:
+    """Breathing-orbital VB form of a VBSCF system (Sec. 2.2, Eq. PsiJBOVB): every structure
+    gets its own copy of the orbitals it uses (inactive, paired and unpaired), so that each
+    structure's orbitals can relax on their own.  The original orbitals stay in the list first
+    (no structure uses them: they are excitation targets); structure I's copies follow in a
+    block.  Each copy's nonzero coefficients are scaled by (1 + eps u), u ~ U(-1, 1) seeded (eps = 0:
+    exact copies, the wave function is the VBSCF one).  Every VBSCF orbital excitation (k, l)
+    becomes one excitation per structure I that uses l: (k_I, l_I) with k_I = I's copy of k when
+    I uses k, else the original k."""
+    rng = np.random.default_rng(seed)
+    nvb = spec.Nvb
+    orbs = [spec.orb_coef[q] for q in range(spec.Norb)]
+    cls = list(spec.orb_class)
+    kind = list(spec.orb_kind)
+    copy = []                                        # per structure: original -> copy index
+    strs = []
+    for I in range(nvb):
+        ina = [int(x) for x in spec.inact[spec.inact_off[I]:spec.inact_off[I + 1]]]
+        prs = [tuple(int(v) for v in p) for p in spec.pairs[spec.pair_off[I]:spec.pair_off[I + 1]]]
+        unp = [int(x) for x in spec.unp[spec.unp_off[I]:spec.unp_off[I + 1]]]
+        used = sorted(set(ina) | {v for p in prs for v in p} | set(unp))
+        m = {}
+        for q in used:
+            v = spec.orb_coef[q].copy()
+            nz = v != 0.0
+            v[nz] *= 1.0 + eps * rng.uniform(-1.0, 1.0, int(nz.sum()))
+            m[q] = len(orbs)
+            orbs.append(v)
+            cls.append(spec.orb_class[q])
+            kind.append(spec.orb_kind[q])
+        copy.append(m)
+        strs.append(([m[q] for q in ina], [(m[a], m[b]) for a, b in prs], [m[q] for q in unp]))
+    io, ina, po, prs, uo, un = _structures(strs)
+    kap = []
+    for k, l in spec.kappa_kl:
+        for I in range(nvb):
+            if int(l) in copy[I]:
+                kap.append((copy[I].get(int(k), int(k)), copy[I][int(l)]))
+    return dataclasses.replace(
+        spec, name=spec.name + "_bovb", orb_coef=np.stack(orbs), orb_class=np.array(cls, np.int32),
+        orb_kind=np.array(kind, np.int32), inact_off=io, inact=ina, pair_off=po, pairs=prs, unp_off=uo, unp=un,
+        kappa_kl=np.array(kap, np.int32).reshape(-1, 2))
+
+
+def ethylene_bovb(eps: float = 0.05) -> SystemSpec:
+    """The ethylene-shaped workload in breathing-orbital form: six structures with their own
+    10 orbitals each (24 determinants, none shared between structures)."""
+    return bovb(ethylene_vb(), eps=eps)
 
 
 def ethylene_vb_p400(seed: int = 20220728 + 4) -> SystemSpec:

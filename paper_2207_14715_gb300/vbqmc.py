@@ -46,6 +46,7 @@ class _Desc(ctypes.Structure):
         ("n_cparam", ctypes.c_int), ("cparam", _c_int_p),
         ("jas_param", ctypes.c_int),
         ("n_kappa", ctypes.c_int), ("kappa_kl", _c_int_p),
+        ("sh_kind", _c_int_p),
     ]
 
 
@@ -55,7 +56,7 @@ EXPORTED = ["vbqmc_create", "vbqmc_destroy", "vbqmc_last_error", "vbqmc_set_syst
             "vbqmc_dmc_steps", "vbqmc_set_kernel_timing", "vbqmc_kernel_times", "vbqmc_batch_create",
             "vbqmc_batch_destroy", "vbqmc_batch_vmc_steps", "vbqmc_batch_tune", "vbqmc_batch_info",
             "vbqmc_eval_nuclear_derivs", "vbqmc_weighted_colsum", "vbqmc_lin_solve", "vbqmc_structure_overlap",
-            "vbqmc_structure_weights", "vbqmc_measure_alu_peaks", "vbqmc_lin_merge"]
+            "vbqmc_structure_weights", "vbqmc_measure_alu_peaks", "vbqmc_lin_merge", "vbqmc_use_tables"]
 
 _LIB = None
 
@@ -103,6 +104,7 @@ def lib():
                                       ctypes.c_double, _c_dbl_p, _c_dbl_p]
         L.vbqmc_structure_overlap.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int,
                                               _c_dbl_p, ctypes.c_int, _c_int_p, _c_dbl_p, vp]
+        L.vbqmc_use_tables.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.vbqmc_lin_merge.argtypes = [ctypes.c_int, ctypes.c_int] + [_c_dbl_p] * 13
         L.vbqmc_structure_weights.argtypes = [ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p]
         L.vbqmc_measure_alu_peaks.argtypes = [ctypes.c_int, _c_dbl_p, ctypes.c_int, _c_int_p]
@@ -149,6 +151,7 @@ def _desc(spec: SystemSpec):
     s.n_cparam, s.cparam = len(spec.cparam), i(spec.cparam)
     s.jas_param = int(spec.jas_param)
     s.n_kappa, s.kappa_kl = len(spec.kappa_kl), i(spec.kappa_kl)
+    s.sh_kind = i(spec.sh_kind) if getattr(spec, "sh_kind", None) is not None else None
     return s, keep
 
 
@@ -225,6 +228,11 @@ class Context:
         s, keep = _desc(spec)
         _check(lib().vbqmc_set_system(self.h, int(sys_id), ctypes.byref(s)))
         self.specs[sys_id] = spec
+
+    def use_tables(self, sys_id: int, on: bool = True):
+        """vbqmc_use_tables: carry the system's determinants through reference tables (on) or
+        per-determinant inverses (off)."""
+        _check(lib().vbqmc_use_tables(self.h, int(sys_id), 1 if on else 0))
 
     def last_launch_count(self) -> int:
         return int(lib().vbqmc_last_launch_count(self.h))

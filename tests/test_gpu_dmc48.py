@@ -49,7 +49,9 @@ def _rel(a, b):
 
 
 def test_table_mode_limits(vb, spec):
-    """The tables carry no per-determinant inverses: walker state and VMC sweeps are refused."""
+    """The tables carry no per-determinant inverses: a walker state is refused (evaluation and
+    sweeps), sweeps without one run (test_gpu_tables.py checks them against the oracle), and
+    the system cannot be switched to per-determinant inverses (they do not fit)."""
     mod, ctx = vb
     ctx.set_system(0, spec)
     assert ctx.launch_info(0, 0)["eval_walkers_per_block"] >= 1
@@ -58,8 +60,11 @@ def test_table_mode_limits(vb, spec):
     st = torch.zeros((2, 8), dtype=torch.float64, device="cuda")
     with pytest.raises(mod.VbqmcError, match="reference"):
         ctx.eval_walkers(0, 0, R, z, z, z, state_out=st)
-    with pytest.raises(mod.VbqmcError):
-        ctx.vmc_steps(0, 0, R, 1, 0.3, 1)
+    with pytest.raises(mod.VbqmcError, match="state"):
+        ctx.vmc_steps(0, 0, R, 1, 0.3, 1, state=st)
+    ctx.vmc_steps(0, 0, R, 1, 0.3, 1)
+    with pytest.raises(mod.VbqmcError, match="shared memory"):
+        ctx.use_tables(0, False)
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -114,3 +114,20 @@ def test_binding_exposes_the_entry_points(vb):
         assert callable(getattr(vb, name)), name
     for sym in vb.EXPORTED:
         assert hasattr(vb.lib(), sym)
+
+
+def test_slater_shells_in_the_host_setup(vb):
+    """Slater shells are accepted (zeta > 0) and counted like Gaussian shells; a bad kind or a
+    Slater zeta of 0 is refused."""
+    from paper_2207_14715_gb300 import systems as S
+    spec = S.slater_h2()
+    info, _, _ = vb.inspect_system(spec)
+    assert info["M"] == spec.M
+    bad = S.slater_h2()
+    bad.sh_kind = np.full(len(bad.sh_l), 2, np.int32)
+    with pytest.raises(vb.VbqmcError, match="kind"):
+        vb.inspect_system(bad)
+    bad = S.slater_1s(1.0, 1.0)
+    bad.sh_zeta = np.zeros(1)
+    with pytest.raises(vb.VbqmcError, match="zeta"):
+        vb.inspect_system(bad)

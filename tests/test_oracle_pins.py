@@ -711,3 +711,159 @@ def test_dmc_limits_bound_the_weights_at_a_node(orc):
     out = orc.dmc(spec, R, 1, 0.01, -0.3, W, seed=3, cap=4 * W)
     assert 0.5 * W < out["sum_w"][0] < 2.0 * W, out["sum_w"][0]
     assert out["pop"][0] <= 2 * W
+
+
+# ----------------------------------------------------------------------------- Slater shells
+@pytest.mark.parametrize("Z", list(range(1, 10)))
+def test_slater_1s_exact_without_jastrow(orc, Z):
+    """A 1s Slater orbital exp(-Z r) carries the exact nuclear cusp itself (the paper's a1 = 0,
+    Sec. 2.1): E_L = -Z^2/2 at every point, no Jastrow factor."""
+    spec = S.slater_1s(float(Z), float(Z))
+    R = np.random.default_rng(Z).normal(scale=1.0 / Z, size=(20, 1, 3))
+    out = orc.evaluate(spec, R)
+    np.testing.assert_allclose(out["eloc"], -0.5 * Z * Z, rtol=1e-12)
+
+
+def test_slater_normalisation_quadrature():
+    """Every Slater component N x^a y^b z^c exp(-zeta r) of the library's normalisation integrates
+    to 1: Gauss-Laguerre in r times Gauss-Legendre in cos(theta) and the trapezoid rule in phi
+    (exact for these polynomial-times-exponential integrands)."""
+    from oracle import oracle as orc
+    spec = S.slater_h2()
+    xr, wr = np.polynomial.laguerre.laggauss(40)
+    xc, wc = np.polynomial.legendre.leggauss(12)
+    nphi = 16
+    phi = 2 * np.pi * np.arange(nphi) / nphi
+    mu = 0
+    for sh in range(2 * 4):
+        c, l, zt = spec.sh_center[sh], int(spec.sh_l[sh]), spec.sh_zeta[sh]
+        for (a, b, cc) in _basis_exponents(l):
+            r0 = spec.nuc_xyz[c] + np.array([0.31, -0.22, 0.17])
+            chi, _, _ = orc.basis_eval(spec, r0)
+            d = r0 - spec.nuc_xyz[c]
+            N = chi[mu] / (d[0] ** a * d[1] ** b * d[2] ** cc * math.exp(-zt * np.linalg.norm(d)))
+            # int r^(2l+2) e^{-2 zt r} dr with r = x / (2 zt), and the angular integral of the monomial
+            rad = np.sum(wr * (xr / (2 * zt)) ** (2 * l + 2)) / (2 * zt)
+            st = np.sqrt(1 - xc ** 2)
+            ang = 0.0
+            for p in phi:
+                ux, uy, uz = st * np.cos(p), st * np.sin(p), xc
+                ang += np.sum(wc * ux ** (2 * a) * uy ** (2 * b) * uz ** (2 * cc)) * (2 * np.pi / nphi)
+            assert N * N * rad * ang == pytest.approx(1.0, rel=1e-12)
+            mu += 1
+
+
+def test_slater_gradient_laplacian_finite_difference(orc):
+    spec = S.slater_h2()
+    rng = np.random.default_rng(13)
+    h = 1e-3
+    for _ in range(6):
+        r = spec.nuc_xyz[rng.integers(spec.Nn)] + rng.normal(scale=0.8, size=3)
+        chi, dchi, lchi = orc.basis_eval(spec, r)
+        g_fd = np.zeros_like(dchi)
+        lap_fd = np.zeros_like(lchi)
+        for d in range(3):
+            e = np.zeros(3)
+            e[d] = 1
+
+            def f(hh):
+                return orc.basis_eval(spec, r + hh * e)[0]
+            d1 = (f(h) - f(-h)) / (2 * h)
+            d2 = (f(h / 2) - f(-h / 2)) / h
+            g_fd[:, d] = (4 * d2 - d1) / 3
+            s1 = (f(h) - 2 * chi + f(-h)) / h ** 2
+            s2 = (f(h / 2) - 2 * chi + f(-h / 2)) / (h / 2) ** 2
+            lap_fd += (4 * s2 - s1) / 3
+        scale = np.abs(chi).max() + np.abs(dchi).max()
+        np.testing.assert_allclose(dchi, g_fd, rtol=1e-8, atol=1e-9 * scale)
+        np.testing.assert_allclose(lchi, lap_fd, rtol=1e-6, atol=1e-6 * scale)
+
+
+@pytest.mark.parametrize("Z, zeta", [(2.0, 2.0), (2.0, 1.6875), (3.0, 2.4)])
+def test_slater_two_electron_closed_form(orc, Z, zeta):
+    """He-like singlet in one 1s Slater orbital, no Jastrow: Psi = exp(-zeta (r1 + r2)) and
+    E_L = -zeta^2 + (zeta - Z)(1/r1 + 1/r2) + 1/r12 pointwise; with zeta = Z the nuclear cusp is
+    exact and E_L stays bounded as an electron reaches the nucleus."""
+    spec = S.slater_1s(Z, zeta)
+    spec.n_dn = 1
+    spec.inact_off, spec.inact = np.array([0, 1], np.int32), np.array([0], np.int32)
+    spec.unp_off, spec.unp = np.array([0, 0], np.int32), np.zeros(0, np.int32)
+    R = np.random.default_rng(int(10 * zeta)).normal(scale=0.8, size=(12, 2, 3))
+    out = orc.evaluate(spec, R)
+    r1, r2 = np.linalg.norm(R[:, 0], axis=1), np.linalg.norm(R[:, 1], axis=1)
+    r12 = np.linalg.norm(R[:, 0] - R[:, 1], axis=1)
+    ref = -zeta ** 2 + (zeta - Z) * (1 / r1 + 1 / r2) + 1 / r12
+    np.testing.assert_allclose(out["eloc"], ref, rtol=1e-12)
+    v = _cusp_series(orc, spec, R[:1], 0, np.zeros(3), np.array([0.6, -0.48, 0.64]))
+    if zeta == Z:
+        assert np.abs(np.diff(v))[-1] < 1e-3, v
+    else:
+        assert abs(v[-1] - v[-2]) > 100.0 * abs(zeta - Z), v
+
+
+def test_slater_parameter_and_nuclear_derivatives_finite_difference(orc):
+    spec = S.slater_h2()
+    R = S.initial_walkers(spec, 3, 8)
+    out = orc.evaluate(spec, R, derivs=True)
+    P = out["O"].shape[1]
+    O_fd, E_fd = _fd_params(orc, spec, R, range(P))
+    np.testing.assert_allclose(out["O"], O_fd, rtol=1e-7, atol=1e-8)
+    np.testing.assert_allclose(out["dEL"], E_fd, rtol=1e-6, atol=1e-7 * (1.0 + np.abs(out["eloc"]).max()))
+    nd = orc.nuclear_derivs(spec, R)
+    L_fd, EN_fd = _fd_nuclei(orc, spec, R, range(3 * spec.Nn))
+    np.testing.assert_allclose(nd["dlogpsi"].reshape(3, -1), L_fd, rtol=1e-7, atol=1e-8)
+    np.testing.assert_allclose(nd["dEL"].reshape(3, -1), EN_fd, rtol=1e-6, atol=1e-7 * (1.0 + np.abs(EN_fd).max()))
+
+
+# ----------------------------------------------------------------------------- BOVB
+def _bovb_groups(spec):
+    """For every VBSCF excitation j, the indices of the BOVB excitations made from it (one per
+    structure that uses its orbital l), in the order systems.bovb emits them."""
+    groups, q = [], 0
+    for k, l in spec.kappa_kl:
+        n = 0
+        for I in range(spec.Nvb):
+            used = set(spec.inact[spec.inact_off[I]:spec.inact_off[I + 1]]) | set(
+                spec.pairs[spec.pair_off[I]:spec.pair_off[I + 1]].ravel()) | set(spec.unp[spec.unp_off[I]:spec.unp_off[I + 1]])
+            n += int(l) in used
+        groups.append(list(range(q, q + n)))
+        q += n
+    return groups
+
+
+@pytest.mark.parametrize("maker", [S.small_open_shell, S.h2_vb])
+def test_bovb_with_identical_orbitals_reduces_to_vbscf(orc, maker):
+    """BOVB (Sec. 2.2) whose per-structure orbitals are exact copies of the shared ones is the
+    VBSCF wave function: same ln|Psi|, sign, E_L, structure-coefficient and Jastrow derivatives;
+    and a shared orbital's excitation acts in every structure, so its derivative is the sum of
+    the per-structure excitations' derivatives (first-order variations add)."""
+    spec = maker()
+    if len(spec.kappa_kl) == 0:
+        spec.kappa_kl = np.array([[1, 0], [0, 1]], np.int32)
+    bo = S.bovb(spec, eps=0.0)
+    R = S.initial_walkers(spec, 5, 13)
+    a, b = orc.evaluate(spec, R, derivs=True), orc.evaluate(bo, R, derivs=True)
+    np.testing.assert_allclose(b["logpsi"], a["logpsi"], rtol=1e-13, atol=1e-13)
+    np.testing.assert_array_equal(b["sign"], a["sign"])
+    np.testing.assert_allclose(b["eloc"], a["eloc"], rtol=1e-12, atol=1e-12)
+    nk = len(spec.kappa_kl)
+    n0 = spec.n_params - nk
+    np.testing.assert_allclose(b["O"][:, :n0], a["O"][:, :n0], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(b["dEL"][:, :n0], a["dEL"][:, :n0], rtol=1e-10, atol=1e-10)
+    for j, grp in enumerate(_bovb_groups(spec)):
+        cols = [n0 + q for q in grp]
+        np.testing.assert_allclose(b["O"][:, cols].sum(1), a["O"][:, n0 + j], rtol=1e-11, atol=1e-11)
+        np.testing.assert_allclose(b["dEL"][:, cols].sum(1), a["dEL"][:, n0 + j], rtol=1e-9, atol=1e-9)
+
+
+def test_bovb_derivatives_finite_difference(orc):
+    """Breathing orbitals (eps = 0.1): the per-structure excitation derivatives against
+    Richardson differences of the oracle (a subset of the parameters)."""
+    bo = S.bovb(S.small_open_shell(), eps=0.1)
+    R = S.initial_walkers(bo, 3, 6)
+    out = orc.evaluate(bo, R, derivs=True)
+    P = bo.n_params
+    js = list(range(0, 4)) + list(range(P - 12, P))
+    O_fd, E_fd = _fd_params(orc, bo, R, js)
+    np.testing.assert_allclose(out["O"][:, js], O_fd, rtol=1e-7, atol=1e-8)
+    np.testing.assert_allclose(out["dEL"][:, js], E_fd, rtol=1e-6, atol=1e-7 * (1.0 + np.abs(out["eloc"]).max()))
