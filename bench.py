@@ -415,7 +415,7 @@ def run_ours(args, ws, rank, local):
     eta = efficiency(ctx, vbqmc, spec, R, woff, args.eta_steps) if args.eta_steps > 0 else None
     dmc = dmc_timing(ctx, vbqmc, R, el, args.dmc_steps) if args.dmc_steps > 0 else None
     batched = batched_timing(vbqmc, dev, args.steps) if args.batch_steps > 0 else None
-    dmc48 = dmc48_timing(vbqmc, dev, args.steps, args.dmc48_walkers) if args.dmc48_steps > 0 else None
+    dmc48 = dmc48_timing(vbqmc, dev, args.dmc48_steps, args.dmc48_walkers) if args.dmc48_steps > 0 else None
     lin = lin_method_timing(ctx, vbqmc, dev, args.steps, args.lin_samples) if not args.no_lin else None
     barrier(ws)
     if rank != 0:
@@ -605,30 +605,42 @@ def dmc_timing(ctx, vbqmc, R, el, steps, tau=0.005):
             "launches_per_step": (ctx.last_launch_count() - 3) / steps}
 
 
-def dmc48_timing(vbqmc, dev, steps, W=65536):
-    """The 48-electron system (256 determinants through the reference-determinant tables),
-    W (default 65536) walkers, mixed form: CUDA events around one evaluation (E_L, grad ln|Psi|) with the
-    per-kernel times, and around two DMC steps (tau = 0.005, capacity 1.5x, E_T at the median
-    E_L) from the unequilibrated initial walkers, restarted from the same walkers for each
-    repetition; walker-steps/s counts the walkers each step moved."""
+def dmc48_timing(vbqmc, dev, steps, W=65536, equil_sweeps=100, warm_steps=20, tau=0.005):
+    """The 48-electron system (256 determinants through the reference-determinant tables), W
+    (default 65536) walkers, mixed form.  CUDA events around one evaluation (E_L, grad ln|Psi|)
+    with the per-kernel times and around one VMC sweep (table sweep).  Then the DMC run of the
+    workload: the walkers equilibrated by VMC sweeps (refactorised every 10), E_T = their mean
+    E_L, warm_steps untimed DMC steps (tau = 0.005, capacity 1.5x the target), then 'steps' timed
+    steps; the population and E_T history of the timed steps and whether the population stayed
+    within +-20 % of the target.  walker-steps/s counts the walkers each step moved."""
     import numpy as np
     import torch
     from paper_2207_14715_gb300 import systems as S
     spec = S.dmc48()
-    cap, tau = W * 3 // 2, 0.005
+    cap = W * 3 // 2
     ctx = vbqmc.create(dev.index or 0)
     ctx.set_system(0, spec)
-    R0 = torch.tensor(S.initial_walkers(spec, W, SEED + 48), device=dev)
+    buf = torch.zeros((cap, spec.N, 3), dtype=torch.float64, device=dev)
+    buf[:W] = torch.tensor(S.initial_walkers(spec, W, SEED + 48), device=dev)
+    R0 = buf[:W]
     lp, sg, el = (torch.zeros(W, dtype=torch.float64, device=dev) for _ in range(3))
     g = torch.zeros_like(R0)
-    for _ in range(3):
-        ctx.eval_walkers(0, vbqmc.MIXED, R0, lp, sg, el, g)
-    torch.cuda.synchronize()
-    e_med = float(el.median().item())
-    n = max(3, steps)
+    nacc = torch.zeros(W, dtype=torch.int32, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ctx.vmc_steps(0, vbqmc.MIXED, R0, equil_sweeps, spec.step, SEED, step0=1 << 25, refresh=10, nacc=nacc)
+    torch.cuda.synchronize()
+    t_equil = time.perf_counter() - t0
+    acc = float(nacc.double().sum().item()) / (equil_sweeps * W * spec.N)
+    # one table sweep, timed
+    e0.record()
+    ctx.vmc_steps(0, vbqmc.MIXED, R0, 1, spec.step, SEED, step0=(1 << 25) + equil_sweeps, refresh=1)
+    e1.record()
+    torch.cuda.synchronize()
+    sweep_ms = e0.elapsed_time(e1)
     ctx.set_kernel_timing(True)
     kt = {k: 0.0 for k in ctx.EVAL_KERNELS}
+    n = 3
     ev_ms = 0.0
     for _ in range(n):
         e0.record()
@@ -639,24 +651,32 @@ def dmc48_timing(vbqmc, dev, steps, W=65536):
         for k, v in ctx.kernel_times().items():
             kt[k] += v
     ctx.set_kernel_timing(False)
-    buf = torch.zeros((cap, spec.N, 3), dtype=torch.float64, device=dev)
-    dmc_ms, moved, pops = 0.0, 0, None
-    for r in range(n):
-        buf[:W] = R0
-        torch.cuda.synchronize()
-        e0.record()
-        W1, _, hist = ctx.dmc_steps(0, vbqmc.MIXED, buf, W, 2, tau, e_med, W, SEED, step0=(1 << 24) + 2 * r)
-        e1.record()
-        torch.cuda.synchronize()
-        dmc_ms += e0.elapsed_time(e1)
-        moved += W + int(hist["pop"][0]) if len(hist["pop"]) > 1 else W
-        pops = [int(x) for x in hist["pop"]]
+    e_vmc = float(el.mean().item())
+    Wc, e_t, hist0 = ctx.dmc_steps(0, vbqmc.MIXED, buf, W, warm_steps, tau, e_vmc, W, SEED, step0=1 << 24)
+    torch.cuda.synchronize()
+    e0.record()
+    W1, e_t1, hist = ctx.dmc_steps(0, vbqmc.MIXED, buf, Wc, steps, tau, e_t, W, SEED, step0=(1 << 24) + warm_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    dmc_ms = e0.elapsed_time(e1)
+    pops = np.asarray(hist["pop"], np.int64)
+    moved = Wc + int(pops[:-1].sum())
+    est = hist["sum_wE"] / hist["sum_w"]
     ctx.close()
     return {"electrons": spec.N, "determinants": 256, "unique_per_spin": 70, "walkers": W,
+            "vmc_equilibration": {"sweeps": equil_sweeps, "seconds": t_equil, "acceptance": acc,
+                                  "E_L_mean_after": e_vmc},
+            "sweep_ms": sweep_ms, "sweep_walker_sweeps_per_s": W / (sweep_ms * 1e-3),
             "eval_ms": ev_ms / n, "eval_walkers_per_s": W / (ev_ms / n * 1e-3),
             "eval_kernel_ms": {k: round(v / n, 4) for k, v in kt.items()},
-            "dmc_walker_steps_per_s": moved / (dmc_ms * 1e-3), "dmc_ms_per_call_of_2_steps": dmc_ms / n,
-            "population": pops, "tau": tau, "start": "unequilibrated walkers, E_T = median E_L"}
+            "dmc_walker_steps_per_s": moved / (dmc_ms * 1e-3), "dmc_ms_per_step": dmc_ms / max(len(pops), 1),
+            "tau": tau, "target": W, "warm_steps": warm_steps, "timed_steps": int(len(pops)),
+            "population_min_max": [int(pops.min()), int(pops.max())] if len(pops) else None,
+            "population_within_20pct": bool(len(pops) and np.all(np.abs(pops / W - 1.0) <= 0.2)),
+            "population_every_10": [int(x) for x in pops[::10]],
+            "e_trial_every_10": [round(float(x), 4) for x in hist["e_trial"][::10]],
+            "estimator_last_10_mean": float(np.mean(est[-10:])) if len(est) else None,
+            "acceptance": hist["accepted"] / max(moved, 1)}
 
 
 def batched_timing(vbqmc, dev, steps):
@@ -693,12 +713,18 @@ def batched_timing(vbqmc, dev, steps):
     ms = e0.elapsed_time(e1) / n
     launches = ctx.last_launch_count()
     info = batch.info()
+    tables = sum(ctx.launch_info(k, vbqmc.MIXED)["tables"] for k in range(len(specs)))
     batch.close()
     ctx.close()
+    # per-electron-pair normalisation: walker-steps/s x mean N^2, comparable across system sizes
+    n2 = sum(w * sp.N * sp.N for sp, w in zip(specs, W)) / sum(W)
     return {"systems": len(specs), "walkers": int(sum(W)), "electrons": [min(sp.N for sp in specs),
                                                                        max(sp.N for sp in specs)],
+            "systems_on_tables": int(tables), "mean_N2_per_walker": n2,
             "walker_steps_per_s": sum(W) / (ms * 1e-3), "ms_per_step": ms, "launches_per_step": launches,
-            "launch_shapes": {k: [v["grid"], v["warps"], v["persist"], v["cap"]] for k, v in info.items()}}
+            "one_launch": info["one_launch"], "tuned_eval_us": info["tuned_eval_us"],
+            "launch_shapes": {k: [info[k]["grid"], info[k]["warps"], info[k]["persist"], info[k]["cap"]]
+                              for k in vbqmc.Batch.KINDS}}
 
 
 def lin_method_timing(ctx, vbqmc, dev, steps, M=1 << 20):
@@ -742,7 +768,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=3, help="batched-workload timing (0: skip)")
     ap.add_argument("--force-steps", type=int, default=3, help="nucleus-derivative timing (0: skip)")
     ap.add_argument("--eta-steps", type=int, default=200, help="steps of the efficiency comparison (0: skip)")
-    ap.add_argument("--dmc48-steps", type=int, default=3, help="48-electron DMC system timing (0: skip)")
+    ap.add_argument("--dmc48-steps", type=int, default=100, help="timed DMC steps of the 48-electron system (0: skip)")
+    ap.add_argument("--only-dmc48", action="store_true", help="run only the 48-electron DMC leg (long runs)")
     ap.add_argument("--dmc48-walkers", type=int, default=65536, help="walkers of the 48-electron timing")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -753,6 +780,16 @@ def main():
         run_reference(args, ws, rank)
         return
     ws, rank, local = dist_setup()
+    if args.only_dmc48:
+        import torch
+        from paper_2207_14715_gb300 import vbqmc
+        torch.cuda.set_device(local)
+        sampler = ClockSampler(local)
+        sampler.start()
+        out = dmc48_timing(vbqmc, torch.device("cuda", local), args.dmc48_steps, args.dmc48_walkers)
+        out["clocks"] = sampler.stop()
+        print(json.dumps({"dmc48": out}), flush=True)
+        return
     run_ours(args, ws, rank, local)
     if ws > 1:
         import torch.distributed as dist

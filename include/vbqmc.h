@@ -218,10 +218,14 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
  *   rejected if sign Psi(R') != sign Psi(R), else accepted with probability
  *   min(1, exp(2 (ln|Psi(R')| - ln|Psi(R)|)) G(R <- R') / G(R' <- R)),
  *   G(R' <- R) = exp(-|R' - R - tau vbar(R)|^2 / (2 tau));
- *   E_b = E_T + (E_L - E_T) |Vbar| / |V| (whole-walker drift vectors) at R and at the kept point;
+ *   E_b = E_T + clamp((E_L - E_T) |Vbar| / |V|, -E_cut, E_cut) at R and at the kept point (V, Vbar
+ *   the whole-walker drift vectors; E_cut = 0.2 sqrt(N / tau), the energy cutoff of Zen, Sorella,
+ *   Gillan, Michaelides and Alfe, Phys. Rev. B 93, 241118(R) (2016));
  *   weight w = exp(-tau ((E_b(R) + E_b(R_kept)) / 2 - E_T)); copies = min(floor(w + u), 3),
  *   children in parent order (weights are 1 after branching);
- *   then E_T = sum(w E_L) / sum(w) - (0.1 / tau) ln(population / target).
+ *   then E_T = sum(w E_b) / sum(w) - (0.1 / tau) ln(population / target), E_b at the kept points
+ *   (the energies that set the weights, so that the population settles at the target; the
+ *   estimator returned in sum_wE / sum_w uses the raw E_L).
  * Random numbers: Philox4x32-10 keyed by seed, counter (walker_offset + walker index in the
  * current population, step0 + step, slot, (system_tag << 8) | purpose): slot e < N, purpose 2 ->
  * (u0, u1) giving z_x = r cos(2 pi u1), z_y = r sin(2 pi u1) with r = sqrt(-2 ln(1 - u0)); purpose
@@ -232,8 +236,9 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
  *   W_io     host, in/out: population (0 <= W <= cap)
  *   R        [cap][N][3] device, in/out: walkers (the first W rows are the population)
  *   E_T_io   host, in/out: trial energy
- *   sum_wE, sum_w [nsteps] host double or NULL: per step, sums of the pre-branching weights
- *            times E_L and of the weights (the estimator is sum_wE / sum_w)
+ *   sum_wE, sum_w, sum_wEb [nsteps] host double or NULL: per step, sums of the pre-branching
+ *            weights times E_L, of the weights (the estimator is sum_wE / sum_w) and of the weights
+ *            times E_b (what the trial-energy update averages)
  *   pop [nsteps] host int or NULL: population after branching; e_trial [nsteps] host or NULL:
  *            E_T after its update;  accepted: host or NULL, accepted moves over the call.
  * The call synchronizes 'stream' once per step (to read the population and the sums) and keeps
@@ -242,8 +247,8 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
  * that step are applied, its branching is not, and W_io holds the population before it. */
 int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int cap, double* R, int nsteps, double tau,
                     double* E_T_io, int target, uint64_t seed, uint32_t step0, uint32_t system_tag,
-                    uint32_t walker_offset, double* sum_wE, double* sum_w, int* pop, double* e_trial, int64_t* accepted,
-                    void* stream);
+                    uint32_t walker_offset, double* sum_wE, double* sum_w, double* sum_wEb, int* pop, double* e_trial,
+                    int64_t* accepted, void* stream);
 
 /* Linear-method estimators from M samples (Sec. 2.3.1, Eqs. Hi0, H0j, Hij, Sij, feeding the
  * generalized eigenproblem Eq. geneigeqM).  With weights w (NULL: all 1), averages
@@ -254,11 +259,13 @@ int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int ca
  *   O, dEL  [M][P] device, element type double (VBQMC_FP64) or float (VBQMC_MIXED)
  *   eloc    [M] device double;  weights [M] device double or NULL
  *   E0 [1], gL [P], gR [P], S [P][P], H [P][P]: device double, out
- * Column sums are double; the centred values are rounded to float and split into high and low
- * TF32 parts; the products run on the tensor cores (tcgen05, three TF32 MMAs per product,
- * fresh accumulator per 32-sample step drained into FP32 registers) over chunks of samples,
- * and the chunk partials are summed in double.  The context keeps a device workspace (grown on
- * demand, synchronizing 'stream' when it grows). */
+ * Column sums are double (fixed-order block partials); the centred values, times sqrt(w) and a
+ * power-of-two scale per parameter that bounds them by 2^14, are split into high and low FP16
+ * halves (22 significant bits); the products run on the tensor cores (tcgen05 kind::f16,
+ * three MMAs per product: hi*hi + hi*lo + lo*hi, FP32 accumulators in TMEM drained every 64
+ * samples into FP32 registers) over chunks of samples, and the chunk partials are summed in
+ * double and unscaled.  The context keeps a device workspace (grown on demand, synchronizing
+ * 'stream' when it grows). */
 int vbqmc_accumulate_lin_matrices(vbqmc_ctx* ctx, int precision, int P, int64_t M, const void* O, const void* dEL,
                                   const double* eloc, const double* weights, double* E0, double* gL, double* gR,
                                   double* S, double* H, void* stream);
@@ -351,12 +358,14 @@ int vbqmc_accumulate_lin_matrices_noalloc(int precision, int P, int64_t M, const
                                           const double* eloc, const double* weights, double* E0, double* gL,
                                           double* gR, double* S, double* H, void* stream);
 
-/* ---- Batched systems (many small molecules of uneven size in one set of launches) ----
+/* ---- Batched systems (many small molecules of uneven size in one launch per step) ----
  * A batch holds several systems already loaded in the context (each with its own walker
- * count W[k]) in one precision mode.  Every kernel type runs once per step for all systems,
- * through a table of (system, walker range) work items ordered by estimated cost; the
- * launches of a step are captured in a CUDA graph on first use (per call shape: with or
- * without sweeps, evaluation and derivatives) and replayed.  Results equal those of the
+ * count W[k]) in one precision mode.  A step is one persistent launch: its blocks take
+ * (system, tile of walkers) work items, ordered by estimated cost, from a device queue and run
+ * the sweep and every evaluation phase on each tile (the tuner may instead pick one launch per
+ * kernel type over per-kind work items, when that measures faster); the step is captured in a
+ * CUDA graph on first use (per call shape: with or without sweeps, evaluation and derivatives)
+ * and replayed.  Results equal those of the
  * per-system calls with system_tag = the system id and walker_offset = 0.  A batch keeps a
  * copy of the systems' tables: recreate it after reloading one of its systems.  The paper has
  * no counterpart (it runs one molecule per calculation); this serves many small systems at
@@ -376,15 +385,20 @@ int vbqmc_batch_vmc_steps(vbqmc_batch* batch, double* const* R, int nsweeps, dou
                           uint32_t step0, int refresh, double* const* state, int state_valid, int* const* nacc,
                           double* const* logpsi, double* const* sign, double* const* eloc, void* const* O,
                           void* const* dEL, void* stream);
-/* Launch-shape tuner: times the evaluation kernels of the batch on the walkers R (outputs
- * written to logpsi/sign/eloc) for one-block-per-item and persistent grids, with and without a
- * cap on walkers per block, keeps the fastest for each kernel and drops captured graphs.
+/* Launch-shape tuner: times the evaluation on the walkers R (outputs written to
+ * logpsi/sign/eloc), for the per-kind kernels with one-block-per-item and persistent grids and
+ * with and without a cap on walkers per block, and for the one-launch step over tile shapes
+ * (8, 12 or 16 warps per block, tiles capped at 4 walkers or not, 1 or 2 x the resident blocks);
+ * keeps the fastest shapes and the faster launch style, and drops captured graphs.
  * Synchronizes 'stream'. */
 int vbqmc_batch_tune(vbqmc_batch* batch, double* const* R, double* const* logpsi, double* const* sign,
                      double* const* eloc, void* stream);
 /* Launch shapes: out[5 k + 0..4] = work items, grid, warps per block, persistence (0: one
  * block per item, p: p x resident blocks), walkers-per-block cap (0: none) for kernel k in
- * the order sweep, Jastrow, Jastrow derivatives, orbitals, determinants. */
+ * the order sweep, Jastrow, Jastrow derivatives, orbitals, determinants, then k = 5 the
+ * one-launch step; out[30] = 1 when steps run as one launch, out[31] and out[32] the tuner's
+ * evaluation times in microseconds of the per-kind launches and of the one-launch step
+ * (0 before tuning).  out holds 33 ints. */
 int vbqmc_batch_info(vbqmc_batch* batch, int* out);
 
 /* Per-kernel timing of the evaluation (diagnostics; the paper has no counterpart).  With
@@ -401,7 +415,8 @@ int vbqmc_kernel_times(vbqmc_ctx* ctx, double* ms, int max, int* n);
 
 /* Launch shape of the walker kernels for a loaded system: out[0..3] = walkers (warps) per
  * thread block and shared-memory bytes per walker of the evaluation's determinant kernel, then
- * the same two numbers for the sweep kernel, for the given precision mode. */
+ * the same two numbers for the sweep kernel, for the given precision mode; out[4] = 1 when the
+ * system is on reference-determinant tables (vbqmc_use_tables).  out holds 5 ints. */
 int vbqmc_launch_info(vbqmc_ctx* ctx, int sys_id, int precision, int* out);
 
 /* Chooses how the determinant part of a loaded system is carried (Sec. 2.1: the determinants

@@ -40,10 +40,15 @@
 //     electron's drift v_i = grad_i ln|Psi| is replaced by
 //       vbar_i = v_i (-1 + sqrt(1 + 2 a |v_i|^2 tau)) / (a |v_i|^2 tau),  a = 1,
 //     and in the branching weight E_L is replaced by E_T + (E_L - E_T) |Vbar| / |V| (V, Vbar the
-//     whole-walker drift vectors); node rejection, weight
+//     whole-walker drift vectors), the difference E_L - E_T being further cut off at
+//     +-0.2 sqrt(N / tau) (the cutoff of Zen, Sorella, Gillan, Michaelides and Alfe, Phys. Rev. B
+//     93, 241118(R) (2016), which keeps a walker far from any node but at a huge |E_L| from
+//     multiplying without bound); node rejection, weight
 //     exp(-tau[(E'_L(R) + E'_L(R_kept))/2 - E_T]) with E'_L the limited energy, branching
 //     copies = floor(w + U) capped at 3, children in parent order,
-//     E_T = E_mean - (0.1/tau) ln(pop/target) with E_mean the weighted mean of the raw E_L.
+//     E_T = E_b,mean - (0.1/tau) ln(pop/target) with E_b,mean the weighted mean of the limited
+//     energies at the kept positions (the energies that set the weights, so that the population
+//     settles at the target); the reported estimator stays the weighted mean of the raw E_L.
 //     Random numbers are keyed by walker_offset + (the walker's index in the population).
 //
 // Derivatives:
@@ -1074,7 +1079,7 @@ int orc_dmc(const orc_system* in, int cap, int* W_io, double* R, int nsteps, dou
   std::vector<double> Rnext;
   for (int k = 0; k < nsteps; ++k) {
     uint32_t st = step0 + (uint32_t)k;
-    std::vector<double> wt(W), EL(W);
+    std::vector<double> wt(W), EL(W), EB(W);
     std::vector<int> copies(W);
     parallel_for(W, nthreads, [&](int w) {
       double* Rw = R + (size_t)w * 3 * N;
@@ -1113,17 +1118,19 @@ int orc_dmc(const orc_system* in, int cap, int* W_io, double* R, int nsteps, dou
       double Enew = accept ? e1.eloc : e0.eloc;
       if (accept)
         for (int q = 0; q < 3 * N; ++q) Rw[q] = Rp[q];
-      // branching energies limited in proportion to the drift
-      const double Eb0 = E_T + (e0.eloc - E_T) * lim0;
-      const double Eb1 = E_T + (Enew - E_T) * (accept ? lim1 : lim0);
+      // branching energies limited in proportion to the drift, then cut off
+      const double ecut = 0.2 * std::sqrt((double)N / tau);
+      const double Eb0 = E_T + std::max(-ecut, std::min(ecut, (e0.eloc - E_T) * lim0));
+      const double Eb1 = E_T + std::max(-ecut, std::min(ecut, (Enew - E_T) * (accept ? lim1 : lim0)));
       double w1 = std::exp(-tau * (0.5 * (Eb0 + Eb1) - E_T));
       wt[w] = w1;
       EL[w] = Enew;
+      EB[w] = Eb1;
       int c = (int)std::floor(w1 + uu[1]);
       copies[w] = std::min(c, 3);
     });
-    double swE = 0.0, sw = 0.0;
-    for (int w = 0; w < W; ++w) { swE += wt[w] * EL[w]; sw += wt[w]; }
+    double swE = 0.0, sw = 0.0, swEb = 0.0;
+    for (int w = 0; w < W; ++w) { swE += wt[w] * EL[w]; sw += wt[w]; swEb += wt[w] * EB[w]; }
     int total = 0;
     for (int w = 0; w < W; ++w) total += copies[w];
     if (total > cap) return -3;
@@ -1134,8 +1141,8 @@ int orc_dmc(const orc_system* in, int cap, int* W_io, double* R, int nsteps, dou
         std::copy(R + (size_t)w * 3 * N, R + (size_t)(w + 1) * 3 * N, Rnext.begin() + (size_t)pos * 3 * N);
     std::copy(Rnext.begin(), Rnext.end(), R);
     W = total;
-    double Emean = sw > 0 ? swE / sw : E_T;
-    if (W > 0) E_T = Emean - (0.1 / tau) * std::log((double)W / (double)target);
+    double Ebmean = sw > 0 ? swEb / sw : E_T;
+    if (W > 0) E_T = Ebmean - (0.1 / tau) * std::log((double)W / (double)target);
     if (sum_wE) sum_wE[k] = swE;
     if (sum_w) sum_w[k] = sw;
     if (pop_out) pop_out[k] = W;

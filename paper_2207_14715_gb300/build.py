@@ -18,7 +18,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
 CU_SOURCES = ["kernels.cu", "eval_jastrow.cu", "eval_orbitals.cu", "eval_det.cu", "eval_dettab.cu", "eval_forces.cu",
-              "dmc.cu", "gradient.cu", "linmethod.cu", "linmethod_noalloc.cu", "api.cu", "batch_api.cu", "peaks.cu"]
+              "dmc.cu", "gradient.cu", "linmethod.cu", "linmethod_noalloc.cu", "api.cu", "batch_api.cu", "peaks.cu", "batch_fused.cu"]
 CPP_SOURCES = ["system_host.cpp", "host_linalg.cpp"]
 
 

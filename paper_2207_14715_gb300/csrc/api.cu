@@ -349,6 +349,7 @@ int vbqmc_launch_info(vbqmc_ctx* ctx, int sys_id, int precision, int* out) {
   out[1] = s.dev.msd ? s.lay_eval[precision].tab.warp_bytes : s.lay_eval[precision].det.warp_bytes;
   out[2] = s.lay_sweep[precision].wpb;
   out[3] = s.lay_sweep[precision].warp_bytes;
+  out[4] = s.dev.msd ? 1 : 0;
   return VBQMC_OK;
 }
 
@@ -599,8 +600,8 @@ int vbqmc_vmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int W, double* R,
 
 int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int cap, double* R, int nsteps, double tau,
                     double* E_T_io, int target, uint64_t seed, uint32_t step0, uint32_t system_tag,
-                    uint32_t walker_offset, double* sum_wE, double* sum_w, int* pop, double* e_trial, int64_t* accepted,
-                    void* stream) {
+                    uint32_t walker_offset, double* sum_wE, double* sum_w, double* sum_wEb, int* pop, double* e_trial,
+                    int64_t* accepted, void* stream) {
   if (!W_io || !E_T_io) return fail(VBQMC_ERR_ARG, "null W_io or E_T_io");
   int rc = check_call(ctx, sys_id, precision, *W_io);
   if (rc) return rc;
@@ -621,7 +622,7 @@ int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int ca
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t vec = al(sizeof(double) * (size_t)cap * n3), sca = al(sizeof(double) * (size_t)cap),
                ints = al(sizeof(int) * (size_t)cap);
-  const size_t need = 5 * vec + 11 * sca + 3 * ints + al(sizeof(vbq::DmcTotals));
+  const size_t need = 5 * vec + 12 * sca + 3 * ints + al(sizeof(vbq::DmcTotals));
   if (need > ctx->dmc_bytes) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
@@ -659,6 +660,7 @@ int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int ca
   double* el1 = reinterpret_cast<double*>(take(sca));
   double* wt = reinterpret_cast<double*>(take(sca));
   double* wE = reinterpret_cast<double*>(take(sca));
+  double* wEb = reinterpret_cast<double*>(take(sca));
   int* copies = reinterpret_cast<int*>(take(ints));
   int* offsets = reinterpret_cast<int*>(take(ints));
   int* acc = reinterpret_cast<int*>(take(ints));
@@ -683,8 +685,8 @@ int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int ca
                            nullptr, ctx->eval_work, st, &nl);
     if (e == cudaSuccess)
       e = vbq::launch_dmc_accept(W, N, cur.R, cur.lp, cur.sg, cur.el, cur.grad, Rp, lp1, sg1, el1, grad1, tau, E_T,
-                                 seed, stp, system_tag, walker_offset, wt, wE, copies, acc, st);
-    if (e == cudaSuccess) e = vbq::launch_dmc_scan(W, copies, wt, wE, acc, offsets, tot, st);
+                                 seed, stp, system_tag, walker_offset, wt, wE, wEb, copies, acc, st);
+    if (e == cudaSuccess) e = vbq::launch_dmc_scan(W, copies, wt, wE, wEb, acc, offsets, tot, st);
     if (e == cudaSuccess)
       e = vbq::launch_dmc_branch(W, N, cap, copies, offsets, tot, cur.R, cur.lp, cur.sg, cur.el, cur.grad, nxt.R,
                                  nxt.lp, nxt.sg, nxt.el, nxt.grad, st);
@@ -705,10 +707,11 @@ int vbqmc_dmc_steps(vbqmc_ctx* ctx, int sys_id, int precision, int* W_io, int ca
     }
     std::swap(cur, nxt);
     W = (int)h.total;
-    const double Emean = h.sum_w > 0.0 ? h.sum_wE / h.sum_w : E_T;
-    if (W > 0) E_T = Emean - (0.1 / tau) * std::log((double)W / (double)target);
+    const double Ebmean = h.sum_w > 0.0 ? h.sum_wEb / h.sum_w : E_T;
+    if (W > 0) E_T = Ebmean - (0.1 / tau) * std::log((double)W / (double)target);
     if (sum_wE) sum_wE[k] = h.sum_wE;
     if (sum_w) sum_w[k] = h.sum_w;
+    if (sum_wEb) sum_wEb[k] = h.sum_wEb;
     if (pop) pop[k] = W;
     if (e_trial) e_trial[k] = E_T;
     if (W == 0) break;

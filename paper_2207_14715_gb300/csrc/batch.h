@@ -60,6 +60,15 @@ cudaError_t launch_orbitals_batch(const BatchSys* sys, const BatchItem* items, i
 template <class Tb>
 cudaError_t launch_det_batch(const BatchSys* sys, const BatchItem* items, int nitems, const BatchCall* call, int grid,
                              int warps, int smem, cudaStream_t st);
+// The whole step in one persistent launch (batch_fused.cu): blocks take items (system, tile of
+// walkers) from the device counter *queue (zero before the launch) and run the sweep (if sweep),
+// the evaluation kernels' bodies (if eval) and the Jastrow-parameter derivatives (if derivs) on
+// each tile in turn.  Every item's count fits the block's warps and, for every phase, the
+// shared memory smem.
+cudaError_t launch_batch_fused(int is_float, const BatchSys* sys, const BatchItem* items, int nitems,
+                               const BatchCall* call, int* queue, bool sweep, bool eval, bool derivs, int grid,
+                               int warps, int smem, cudaStream_t st);
+int batch_fused_grid(int is_float, int warps, int smem, int persist);
 // Grid of each batched kernel for nitems items: one block per item (persist = 0), or
 // persist x the blocks that fit on all SMs at once (persistent blocks looping over items);
 // -1 on a CUDA error.  Also sets the kernel's dynamic shared-memory limit, so call these

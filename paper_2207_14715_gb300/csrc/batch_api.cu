@@ -1,8 +1,10 @@
-// Batched VMC steps over many loaded systems (C ABI in include/vbqmc.h): one launch per
-// kernel type covers every system through a table of (system, walker range) work items;
-// the launches of a step are captured once in a CUDA graph and replayed, and the launch
-// shapes (walkers per block, persistent or one-block-per-item grids) are chosen by timing
-// the candidates on the batch itself.
+// Batched VMC steps over many loaded systems (C ABI in include/vbqmc.h).  A step is one
+// persistent launch (batch_fused.cu) over a device queue of (system, walker tile) work items
+// that runs every phase of the step on each tile; the launch (with the reset of the queue
+// counter and the staging copies) is captured once per call shape in a CUDA graph and replayed.
+// The tile shape (warps per block, walkers per tile) and the persistence of the grid are chosen
+// by timing the candidates on the batch itself.  One launch per kernel type over per-kind
+// work items remains as the alternative the tuner compares against.
 #include <algorithm>
 #include <numeric>
 #include <string>
@@ -19,6 +21,7 @@ namespace {
 
 constexpr int kKinds = 5;  // 0 sweep, 1 Jastrow, 2 Jastrow derivatives, 3 orbitals, 4 determinants
 const char* const kKindName[kKinds] = {"sweep", "jastrow", "jastrow_deriv", "orbitals", "det"};
+constexpr int kFused = kKinds;  // plan index of the one-launch step
 
 struct KernelPlan {
   int persist = 1;  // 0: one block per item; k: k x the blocks resident at once
@@ -34,7 +37,10 @@ struct vbqmc_batch {
   int precision = 0, n = 0;
   std::vector<int> ids, W;
   std::vector<BatchSys> sys;  // host template (tables, layouts, workspace pointers)
-  KernelPlan plan[kKinds];
+  KernelPlan plan[kKinds + 1];  // per kind, then the one-launch step
+  bool fused = true;             // steps as one launch (else one launch per kind)
+  bool tables = false;           // a system on reference-determinant tables: one-launch steps only
+  int* d_queue = nullptr;        // work-queue counter of the one-launch step
   BatchSys* d_sys = nullptr;
   BatchCall* d_call = nullptr;
   BatchSys* h_sys = nullptr;  // pinned staging copied by the graph
@@ -44,6 +50,7 @@ struct vbqmc_batch {
   cudaGraphExec_t graph[8] = {};
   cudaEvent_t staged = nullptr;  // the last graph launch has read the staging buffers
   bool tuned = false;
+  float tune_ms[2] = {0.0f, 0.0f};  // evaluation per launch style at the tuned shapes
 };
 
 namespace {
@@ -139,6 +146,58 @@ int build_plan(vbqmc_batch* b, int kind) {
   return VBQMC_OK;
 }
 
+// Work items and shape of the one-launch step: with p.warps warps per block (p.cap > 0 caps the
+// walkers per tile), system s takes tiles of c_s walkers, c_s = the most that fit the warps and,
+// for the phase with the largest per-walker region, the opt-in shared memory; the orbital phase
+// uses every warp of the block.
+int build_fused_plan(vbqmc_batch* b) {
+  KernelPlan& p = b->plan[kFused];
+  const bool f = b->precision == VBQMC_MIXED;
+  const int smax = b->ctx->max_smem;
+  const int warps = std::max(1, std::min(p.warps, 16));
+  int smem = 0;
+  std::vector<int> per(b->n);
+  for (int k = 0; k < b->n; ++k) {
+    const BatchSys& s = b->sys[k];
+    const int mb = std::max(std::max(s.sweep.warp_bytes, s.lay.jas.warp_bytes),
+                            s.dev.msd ? s.lay.tab.warp_bytes : s.lay.det.warp_bytes);
+    int c = std::max(1, std::min(warps, smax / std::max(mb, 1)));
+    if (p.cap > 0) c = std::min(c, p.cap);
+    if (warps * s.lay.orb.warp_bytes > smax) return fail(VBQMC_ERR_CAPACITY, "orbital tables of a batched system");
+    per[k] = c;
+    smem = std::max(smem, std::max(c * mb, warps * s.lay.orb.warp_bytes));
+  }
+  struct It {
+    BatchItem item;
+    double cost;
+  };
+  std::vector<It> its;
+  for (int k = 0; k < b->n; ++k) {
+    const double c = walker_cost(b->sys[k].dev);
+    for (int f0 = 0; f0 < b->sys[k].W; f0 += per[k]) {
+      It t;
+      t.item = BatchItem{k, f0, std::min(per[k], b->sys[k].W - f0), 0};
+      t.cost = c * t.item.count;
+      its.push_back(t);
+    }
+  }
+  std::stable_sort(its.begin(), its.end(), [](const It& a, const It& c) { return a.cost > c.cost; });
+  std::vector<BatchItem> items(its.size());
+  for (size_t i = 0; i < its.size(); ++i) items[i] = its[i].item;
+  if (p.d_items) cudaFree(p.d_items);
+  p.d_items = nullptr;
+  cudaError_t e = cudaMalloc(&p.d_items, sizeof(BatchItem) * std::max<size_t>(items.size(), 1));
+  if (e == cudaSuccess) e = cudaMemcpy(p.d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "batch items");
+  p.nitems = (int)items.size();
+  p.warps = warps;
+  p.smem = smem;
+  const int g = vbq::batch_fused_grid(f, warps, smem, std::max(p.persist, 1));
+  if (g < 0) return fail(VBQMC_ERR_CUDA, "launch setup of the one-launch batched step");
+  p.grid = std::min(g, std::max(p.nitems, 1));
+  return VBQMC_OK;
+}
+
 cudaError_t launch_kind(vbqmc_batch* b, int kind, cudaStream_t st) {
   const KernelPlan& p = b->plan[kind];
   if (p.nitems == 0) return cudaSuccess;
@@ -162,10 +221,21 @@ cudaError_t launch_kind(vbqmc_batch* b, int kind, cudaStream_t st) {
   }
 }
 
-// The launches of one call shape: staging copy, then sweep and/or evaluation kernels.
+cudaError_t launch_fused(vbqmc_batch* b, bool sweep, bool eval, bool derivs, cudaStream_t st) {
+  const KernelPlan& p = b->plan[kFused];
+  if (p.nitems == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  return vbq::launch_batch_fused(b->precision == VBQMC_MIXED, b->d_sys, p.d_items, p.nitems, b->d_call, b->d_queue,
+                                 sweep, eval, derivs, p.grid, p.warps, p.smem, st);
+}
+
+// The launches of one call shape: staging copy, then the one-launch step or the sweep and/or
+// evaluation kernels.
 cudaError_t record_step(vbqmc_batch* b, bool sweep, bool eval, bool derivs, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(b->d_sys, b->h_sys, sizeof(BatchSys) * b->n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_call, b->h_call, sizeof(BatchCall), cudaMemcpyHostToDevice, st);
+  if (b->fused) return e == cudaSuccess ? launch_fused(b, sweep, eval, derivs, st) : e;
   if (e == cudaSuccess && sweep) e = launch_kind(b, 0, st);
   if (e == cudaSuccess && eval) e = launch_kind(b, 1, st);
   if (e == cudaSuccess && eval) e = launch_kind(b, 3, st);
@@ -175,6 +245,7 @@ cudaError_t record_step(vbqmc_batch* b, bool sweep, bool eval, bool derivs, cuda
 }
 
 int launch_count(const vbqmc_batch* b, bool sweep, bool eval, bool derivs) {
+  if (b->fused) return (sweep || eval) && b->plan[kFused].nitems ? 1 : 0;
   int n = 0;
   if (sweep && b->plan[0].nitems) ++n;
   if (eval) n += (b->plan[1].nitems ? 1 : 0) + (b->plan[3].nitems ? 1 : 0) + (b->plan[4].nitems ? 1 : 0);
@@ -221,6 +292,7 @@ void free_batch(vbqmc_batch* b) {
   if (b->h_sys) cudaFreeHost(b->h_sys);
   if (b->h_call) cudaFreeHost(b->h_call);
   if (b->ws) cudaFree(b->ws);
+  if (b->d_queue) cudaFree(b->d_queue);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->staged) cudaEventDestroy(b->staged);
   delete b;
@@ -240,8 +312,6 @@ int vbqmc_batch_create(vbqmc_ctx* ctx, int nsys, const int* sys_ids, const int* 
     if (id < 0 || id >= VBQMC_MAX_SYSTEMS || !ctx->sys[id].loaded)
       return fail(VBQMC_ERR_NOSYS, "no system loaded under id " + std::to_string(id));
     if (W[k] < 1) return fail(VBQMC_ERR_ARG, "every system needs at least one walker");
-    if (ctx->sys[id].dev.msd)
-      return fail(VBQMC_ERR_UNSUPPORTED, "system " + std::to_string(id) + " needs reference-determinant tables");
     if (ctx->sys[id].lay_rc_eval[precision] || ctx->sys[id].lay_rc_sweep[precision])
       return fail(VBQMC_ERR_CAPACITY, "per-walker state of system " + std::to_string(id) + " exceeds shared memory");
     for (int q = 0; q < k; ++q)
@@ -262,6 +332,7 @@ int vbqmc_batch_create(vbqmc_ctx* ctx, int nsys, const int* sys_ids, const int* 
   cudaError_t e = cudaMalloc(&b->ws, std::max<size_t>(off[nsys], 256));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_sys, sizeof(BatchSys) * nsys);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_call, sizeof(BatchCall));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_sys, sizeof(BatchSys) * nsys);
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_call, sizeof(BatchCall));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
@@ -295,12 +366,19 @@ int vbqmc_batch_create(vbqmc_ctx* ctx, int nsys, const int* sys_ids, const int* 
     s.VG = reinterpret_cast<double*>(take(Wz * 3 * N * 8));
     b->sys[k] = s;
   }
-  for (int kind = 0; kind < kKinds; ++kind) {
+  for (int k = 0; k < nsys; ++k) b->tables = b->tables || ctx->sys[sys_ids[k]].dev.msd;
+  for (int kind = 0; kind < kKinds && !b->tables; ++kind) {  // the per-kind kernels have no table forms
     const int rc = build_plan(b, kind);
     if (rc) {
       free_batch(b);
       return rc;
     }
+  }
+  b->plan[kFused].warps = 16;
+  const int rcf = build_fused_plan(b);
+  if (rcf) {
+    free_batch(b);
+    return rcf;
   }
   *out = b;
   return VBQMC_OK;
@@ -373,7 +451,7 @@ int vbqmc_batch_tune(vbqmc_batch* b, double* const* R, double* const* logpsi, do
   // evaluation kernels in order (each reads what the previous one wrote); for each, try
   // one-block-per-item and persistent grids with and without a cap on walkers per block
   const int kinds[3] = {1, 3, 4};
-  for (int kk = 0; kk < 3 && e == cudaSuccess && rc == VBQMC_OK; ++kk) {
+  for (int kk = 0; kk < 3 && e == cudaSuccess && rc == VBQMC_OK && !b->tables; ++kk) {
     const int kind = kinds[kk];
     KernelPlan& p = b->plan[kind];
     int best_persist = p.persist, best_cap = p.cap;
@@ -407,11 +485,64 @@ int vbqmc_batch_tune(vbqmc_batch* b, double* const* R, double* const* logpsi, do
     if (rc == VBQMC_OK && e == cudaSuccess) rc = build_plan(b, kind);
   }
   // the sweep and the Jastrow derivatives follow the determinant kernel's grid choice
-  if (rc == VBQMC_OK && e == cudaSuccess) {
+  if (rc == VBQMC_OK && e == cudaSuccess && !b->tables) {
     b->plan[0].persist = b->plan[2].persist = b->plan[4].persist;
     rc = build_plan(b, 0);
     if (rc == VBQMC_OK) rc = build_plan(b, 2);
   }
+  // the per-kind evaluation at its best shapes, then the one-launch step over tile shapes
+  // (warps per block, walkers per tile) and grid persistence
+  float best_kinds = 1e30f;
+  if (rc == VBQMC_OK && e == cudaSuccess && !b->tables) {
+    b->fused = false;
+    auto run = [&]() {
+      cudaError_t r = cudaSuccess;
+      for (int kind : {1, 3, 4})
+        if (r == cudaSuccess) r = launch_kind(b, kind, st);
+      return r;
+    };
+    e = run();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = run();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&best_kinds, e0, e1);
+  }
+  float best_fused = 1e30f;
+  if (rc == VBQMC_OK && e == cudaSuccess) {
+    KernelPlan& p = b->plan[kFused];
+    int bw = p.warps, bc = p.cap, bp = p.persist;
+    for (int warps : {8, 12, 16})
+      for (int cap : {0, 4})
+        for (int persist : {1, 2}) {
+          if (rc != VBQMC_OK || e != cudaSuccess) break;
+          p.warps = warps;
+          p.cap = cap;
+          p.persist = persist;
+          rc = build_fused_plan(b);
+          if (rc) break;
+          e = launch_fused(b, false, true, false, st);
+          if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+          for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_fused(b, false, true, false, st);
+          if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          float ms = 0.0f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+          if (e == cudaSuccess && ms < best_fused) {
+            best_fused = ms;
+            bw = warps;
+            bc = cap;
+            bp = persist;
+          }
+        }
+    p.warps = bw;
+    p.cap = bc;
+    p.persist = bp;
+    if (rc == VBQMC_OK && e == cudaSuccess) rc = build_fused_plan(b);
+    b->fused = best_fused <= best_kinds;
+  }
+  b->tune_ms[0] = best_kinds / 3.0f;
+  b->tune_ms[1] = best_fused / 3.0f;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return cuda_fail(e, "batch tuning");
@@ -423,13 +554,16 @@ int vbqmc_batch_tune(vbqmc_batch* b, double* const* R, double* const* logpsi, do
 
 int vbqmc_batch_info(vbqmc_batch* b, int* out) {
   if (!b || !out) return fail(VBQMC_ERR_ARG, "null argument");
-  for (int k = 0; k < kKinds; ++k) {
+  for (int k = 0; k <= kKinds; ++k) {
     out[5 * k] = b->plan[k].nitems;
     out[5 * k + 1] = b->plan[k].grid;
     out[5 * k + 2] = b->plan[k].warps;
     out[5 * k + 3] = b->plan[k].persist;
     out[5 * k + 4] = b->plan[k].cap;
   }
+  out[5 * (kKinds + 1)] = b->fused ? 1 : 0;
+  out[5 * (kKinds + 1) + 1] = (int)(1000.0f * b->tune_ms[0]);
+  out[5 * (kKinds + 1) + 2] = (int)(1000.0f * b->tune_ms[1]);
   return VBQMC_OK;
 }
 

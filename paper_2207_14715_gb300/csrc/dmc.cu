@@ -8,10 +8,15 @@
 //   R' = R + tau vbar(R) + sqrt(tau) z,   z ~ N(0, 1) per coordinate;
 //   rejected when sign Psi(R') != sign Psi(R) (fixed node), else accepted with probability
 //   min(1, Psi(R')^2 G(R <- R') / (Psi(R)^2 G(R' <- R))), G(R' <- R) = exp(-|R' - R - tau vbar(R)|^2 / 2 tau);
-//   branching energy E_b = E_T + (E_L - E_T) |Vbar| / |V| (whole-walker drift vectors);
+//   branching energy E_b = E_T + clamp((E_L - E_T) |Vbar| / |V|, -E_cut, E_cut) (whole-walker drift
+//   vectors), E_cut = 0.2 sqrt(N / tau): the energy cutoff of Zen, Sorella, Gillan, Michaelides and
+//   Alfe (Phys. Rev. B 93, 241118(R) (2016)), which keeps walkers at a huge |E_L| away from any
+//   node from multiplying without bound;
 //   weight w = exp(-tau [ (E_b(R) + E_b(R_new)) / 2 - E_T ]) with R_new the position kept;
 //   copies = min(floor(w + u), 3), children stored in parent order (exclusive prefix sum);
-//   E_T <- sum w E_L / sum w - (0.1 / tau) ln(population / target) after branching.
+//   E_T <- sum w E_b / sum w - (0.1 / tau) ln(population / target) after branching, E_b at the kept
+//   positions (the energies that set the weights: the population settles at the target); the
+//   reported estimator is sum w E_L / sum w with the raw E_L.
 // Random numbers: Philox4x32-10 with counter (walker_offset + walker index in the current
 // population, step, slot, (system << 8) | purpose): slot e < N, purposes 2 and 3 -> Box-Muller
 // normals of electron e (purpose 2: z_x, z_y from the cosine and sine branches; purpose 3: z_z
@@ -64,7 +69,8 @@ __global__ void dmc_accept_kernel(int W, int N, double* __restrict__ R, double* 
                                   const double* __restrict__ sg1, const double* __restrict__ el1,
                                   const double* __restrict__ grad1, double tau, double E_T, uint64_t seed,
                                   uint32_t step, uint32_t tag, uint32_t woff, double* __restrict__ wt,
-                                  double* __restrict__ wE, int* __restrict__ copies, int* __restrict__ acc) {
+                                  double* __restrict__ wE, double* __restrict__ wEb, int* __restrict__ copies,
+                                  int* __restrict__ acc) {
   const int w = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   const int lane = lane_id();
   if (w >= W) return;
@@ -117,12 +123,15 @@ __global__ void dmc_accept_kernel(int W, int N, double* __restrict__ R, double* 
     const double en = accept ? el1[w] : e0;
     // branching energies limited in proportion to the drift, |Vbar| / |V| at each point
     const double q0 = n0 > 0.0 ? sqrt(nb0 / n0) : 1.0, q1 = n1 > 0.0 ? sqrt(nb1 / n1) : 1.0;
-    const double eb0 = E_T + (e0 - E_T) * q0, eb1 = E_T + (en - E_T) * (accept ? q1 : q0);
+    const double ecut = 0.2 * sqrt((double)N / tau);
+    const double eb0 = E_T + fmin(ecut, fmax(-ecut, (e0 - E_T) * q0));
+    const double eb1 = E_T + fmin(ecut, fmax(-ecut, (en - E_T) * (accept ? q1 : q0)));
     const double ww = exp(-tau * (0.5 * (eb0 + eb1) - E_T));
     const double x = ww + ubr;
     const int c = (x >= 3.0) ? 3 : (x >= 0.0 ? (int)floor(x) : 0);  // NaN weights die
     wt[w] = ww;
     wE[w] = ww * en;
+    wEb[w] = ww * eb1;
     copies[w] = c;
     acc[w] = accept;
     if (accept) {
@@ -147,14 +156,15 @@ constexpr int kScanThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads) dmc_scan_kernel(int W, const int* __restrict__ copies,
                                                                 const double* __restrict__ wt,
                                                                 const double* __restrict__ wE,
+                                                                const double* __restrict__ wEb,
                                                                 const int* __restrict__ acc,
                                                                 int* __restrict__ offsets, DmcTotals* out) {
   __shared__ int wsum[32];
-  __shared__ double rs[2][32];
+  __shared__ double rs[3][32];
   __shared__ int ra[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   long long running = 0;
-  double sw = 0.0, swe = 0.0;
+  double sw = 0.0, swe = 0.0, sweb = 0.0;
   int na = 0;
   for (int base = 0; base < W; base += kScanThreads) {
     const int i = base + tid;
@@ -162,6 +172,7 @@ __global__ void __launch_bounds__(kScanThreads) dmc_scan_kernel(int W, const int
     if (i < W) {
       sw += wt[i];
       swe += wE[i];
+      sweb += wEb[i];
       na += acc[i];
     }
     int incl = c;
@@ -189,23 +200,27 @@ __global__ void __launch_bounds__(kScanThreads) dmc_scan_kernel(int W, const int
   }
   sw = warp_sum(sw);
   swe = warp_sum(swe);
+  sweb = warp_sum(sweb);
   na = warp_sum(na);
   if (lane == 0) {
     rs[0][wid] = sw;
     rs[1][wid] = swe;
+    rs[2][wid] = sweb;
     ra[wid] = na;
   }
   __syncthreads();
   if (wid == 0) {
-    double a = rs[0][lane], e = rs[1][lane];
+    double a = rs[0][lane], e = rs[1][lane], eb = rs[2][lane];
     int n = ra[lane];
     a = warp_sum(a);
     e = warp_sum(e);
+    eb = warp_sum(eb);
     n = warp_sum(n);
     if (lane == 0) {
       out->total = running;
       out->sum_w = a;
       out->sum_wE = e;
+      out->sum_wEb = eb;
       out->accepted = n;
     }
   }
@@ -250,17 +265,18 @@ cudaError_t launch_dmc_propose(int W, int N, const double* R, const double* grad
 cudaError_t launch_dmc_accept(int W, int N, double* R, double* lp, double* sg, double* el, double* grad,
                               const double* Rp, const double* lp1, const double* sg1, const double* el1,
                               const double* grad1, double tau, double E_T, uint64_t seed, uint32_t step, uint32_t tag,
-                              uint32_t woff, double* wt, double* wE, int* copies, int* acc, cudaStream_t st) {
+                              uint32_t woff, double* wt, double* wE, double* wEb, int* copies, int* acc,
+                              cudaStream_t st) {
   const long long threads = (long long)W * 32;
   dmc_accept_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(W, N, R, lp, sg, el, grad, Rp, lp1, sg1, el1,
                                                                         grad1, tau, E_T, seed, step, tag, woff, wt, wE,
-                                                                        copies, acc);
+                                                                        wEb, copies, acc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dmc_scan(int W, const int* copies, const double* wt, const double* wE, const int* acc,
-                            int* offsets, DmcTotals* out, cudaStream_t st) {
-  dmc_scan_kernel<<<1, kScanThreads, 0, st>>>(W, copies, wt, wE, acc, offsets, out);
+cudaError_t launch_dmc_scan(int W, const int* copies, const double* wt, const double* wE, const double* wEb,
+                            const int* acc, int* offsets, DmcTotals* out, cudaStream_t st) {
+  dmc_scan_kernel<<<1, kScanThreads, 0, st>>>(W, copies, wt, wE, wEb, acc, offsets, out);
   return cudaGetLastError();
 }
 

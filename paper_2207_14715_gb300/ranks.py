@@ -38,27 +38,38 @@ def max_over_ranks(x: float, device=None) -> float:
     return float(t.item())
 
 
-def dmc_global_sums(sum_wE: float, sum_w: float, population: int, device=None, failed=None):
-    """Sums over the ranks of one DMC step's weighted local energies, weights and populations.
-    With failed given (this rank's step raised, True/False), the count of failed ranks travels
-    in the same reduction and is returned as a fourth value."""
+def dmc_global_sums(sum_wE: float, sum_w: float, population: int, device=None, failed=None, sum_wEb=None):
+    """Sums over the ranks of one DMC step's weighted local energies, weights and populations
+    (and, if given, of the weighted branching energies, appended to the result).  With failed
+    given (this rank's step raised, True/False), the count of failed ranks travels in the same
+    reduction and is returned last."""
     d = _dist()
     nf = 1 if failed else 0
-    if d is None:
-        out = (float(sum_wE), float(sum_w), int(population))
-        return out if failed is None else out + (nf,)
-    import torch
-    t = torch.tensor([float(sum_wE), float(sum_w), float(population), float(nf)], dtype=torch.float64,
-                     device=device)
-    d.all_reduce(t, op=d.ReduceOp.SUM)
-    out = (float(t[0]), float(t[1]), int(round(float(t[2]))))
-    return out if failed is None else out + (int(round(float(t[3]))),)
+    vals = [float(sum_wE), float(sum_w), float(population)]
+    if sum_wEb is not None:
+        vals.append(float(sum_wEb))
+    if failed is not None:
+        vals.append(float(nf))
+    if d is not None:
+        import torch
+        t = torch.tensor(vals, dtype=torch.float64, device=device)
+        d.all_reduce(t, op=d.ReduceOp.SUM)
+        vals = [float(x) for x in t]
+    out = (vals[0], vals[1], int(round(vals[2])))
+    k = 3
+    if sum_wEb is not None:
+        out += (vals[k],)
+        k += 1
+    if failed is not None:
+        out += (int(round(vals[k])),)
+    return out
 
 
-def trial_energy(sum_wE: float, sum_w: float, population: int, target: int, tau: float) -> float:
+def trial_energy(sum_wEb: float, sum_w: float, population: int, target: int, tau: float) -> float:
     """The trial-energy update of the DMC step (the one vbqmc_dmc_steps applies to its own
-    population), from global sums: E_T = sum w E_L / sum w - (0.1 / tau) ln(population / target)."""
-    return sum_wE / sum_w - (0.1 / tau) * math.log(population / target)
+    population), from global sums of the weights and of the weights times the limited branching
+    energies: E_T = sum w E_b / sum w - (0.1 / tau) ln(population / target)."""
+    return sum_wEb / sum_w - (0.1 / tau) * math.log(population / target)
 
 
 def balance_plan(pops):
@@ -139,7 +150,7 @@ def dmc_run(dmc_step, R, W: int, nsteps: int, tau: float, E_T: float, target_per
             balance_every: int = 1, device=None, step0: int = 0):
     """nsteps DMC steps of this rank's population under one global trial energy.
     dmc_step(W, E_T, step, walker_offset) advances the population in R by one step at trial
-    energy E_T and returns (W', sum of pre-branching w E_L, sum of w), e.g.
+    energy E_T and returns (W', sum of pre-branching w E_L, sum of w, sum of w E_b), e.g.
         lambda W, E_T, step, off: Context.dmc_steps(sys, prec, R, W, 1, tau, E_T, target, seed,
                                                     step0=step, walker_offset=off) (+ its sums);
     'step' is the global step number step0 + k and 'walker_offset' = rank x capacity, so the
@@ -157,10 +168,10 @@ def dmc_run(dmc_step, R, W: int, nsteps: int, tau: float, E_T: float, target_per
     for k in range(nsteps):
         err = None
         try:
-            W, swE, sw = dmc_step(W, E_T, step0 + k, offset)
+            W, swE, sw, swEb = dmc_step(W, E_T, step0 + k, offset)
         except Exception as e:  # decided as a group below
-            err, swE, sw = e, 0.0, 0.0
-        gwE, gw, gpop, nfail = dmc_global_sums(swE, sw, W, device, failed=err is not None)
+            err, swE, sw, swEb = e, 0.0, 0.0, 0.0
+        gwE, gw, gpop, gwEb, nfail = dmc_global_sums(swE, sw, W, device, failed=err is not None, sum_wEb=swEb)
         if nfail:
             if err is not None:
                 raise err
@@ -168,7 +179,7 @@ def dmc_run(dmc_step, R, W: int, nsteps: int, tau: float, E_T: float, target_per
         hist.append((gwE, gw, gpop))
         if gpop == 0:
             break
-        E_T = trial_energy(gwE, gw, gpop, target, tau)
+        E_T = trial_energy(gwEb, gw, gpop, target, tau)
         if balance_every and (k + 1) % balance_every == 0:
             W = balance_walkers(R, W)
     return W, E_T, hist

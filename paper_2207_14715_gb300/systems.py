@@ -171,6 +171,27 @@ def _local_orbital(rng, M, lo, hi, sh_center, sh_l, center, s_positive=True, sca
     return v * scale
 
 
+def _shaped_orbital(rng, M, sh_center, sh_l, center, k, admix=0.15):
+    """The k-th orbital placed on a centre, with a distinct angular character per k so that the
+    orbitals sharing a centre are far from linearly dependent: k = 0 s-like (every s shell
+    positive), k = 1..3 the x, y, z components of the p shells, k >= 4 the (k - 4)-th d
+    component; every other function of the centre gets a seeded admixture of size 'admix'."""
+    v = np.zeros(M)
+    mu = 0
+    for c, l in zip(sh_center, sh_l):
+        n = NCOMP[int(l)]
+        if c == center:
+            v[mu:mu + n] = admix * rng.uniform(-1.0, 1.0, n)
+            if k == 0 and l == 0:
+                v[mu] = rng.uniform(0.5, 1.0)
+            elif 1 <= k <= 3 and l == 1:
+                v[mu + k - 1] = rng.uniform(0.5, 1.0)
+            elif k >= 4 and l == 2:
+                v[mu + (k - 4) % 6] = rng.uniform(0.5, 1.0)
+        mu += n
+    return v
+
+
 # ----------------------------------------------------------------------------------
 # Tiny systems with closed-form answers (used by the physics pins of the oracle).
 # ----------------------------------------------------------------------------------
@@ -479,7 +500,9 @@ def dmc48(seed: int = 20220728 + 3) -> SystemSpec:
     """48-electron system for DMC at scale: 12 nuclei C2 N2 O2 H6 (sum Z = 48) at seeded positions
     at least 1.8 bohr apart; per center 5 s, 3 p, 2 d Gaussians (M = 312), exponents per element
     log-uniform in [0.1, 20].  24 electrons per spin occupy 20 inactive orbitals and 4 of 8
-    active orbitals (localised on the nuclei where the initial walkers start).  20 structures:
+    active orbitals (localised on the nuclei where the initial walkers start; the orbitals of
+    one centre take s, p_x, p_y, p_z and d characters in turn, so that they stay well apart).
+    20 structures:
     12 pair the 8 active orbitals into 4 distinct singlet pairs (16 determinants each), 8 use 3
     distinct pairs and one doubly occupied active orbital (8 determinants each): 256
     determinants, up to C(8,4) = 70 unique determinants per spin.  Jastrow e-n, e-e, e-e-n; no
@@ -504,9 +527,12 @@ def dmc48(seed: int = 20220728 + 3) -> SystemSpec:
         slots += [a] * int(round(z))
     n_inact, n_act = 20, 8
     orbs, ocls, okind = [], [], []
+    per_center = {}
     for q in range(n_inact + n_act):
         c = slots[(2 * q) % len(slots)] if q < n_inact else slots[(2 * n_inact + (q - n_inact)) % len(slots)]
-        orbs.append(_local_orbital(rng, M, lo, hi, sc, sl, c))
+        k = per_center.get(c, 0)
+        per_center[c] = k + 1
+        orbs.append(_shaped_orbital(rng, M, sc, sl, c, k))
         ocls.append(c)
         okind.append(0 if q < n_inact else 1)
     orb = np.stack(orbs)
@@ -548,8 +574,8 @@ def random_molecule(seed: int, max_electrons: int = 32) -> SystemSpec:
     even and clamped to [2, max_electrons] (resampled while sum Z > max_electrons + 2), Sz = 0.
     Per center 4-12 Gaussian shells split s:p:d about 5:3:2 (at least one s), exponents per
     element log-uniform in [0.1, 20].  Orbitals: N/2 - k doubly occupied and 2k active
-    localised orbitals, placed on the nuclei in proportion to their charges, k = 0..4 distinct pairs per structure (fewer for
-    large N so that the unique determinants per spin stay within C(2k, k) <= 20 at n > 8);
+    localised orbitals, placed on the nuclei in proportion to their charges, k = 0..4 distinct pairs per structure
+    (at most n);
     2-16 structures drawn as random pairings of the active orbitals (covalent or ionic, duplicates
     removed).  Jastrow e-n, e-e and e-e-n with small random polynomial parts; parameters: the
     structure coefficients after the first and the Jastrow."""
@@ -589,10 +615,9 @@ def random_molecule(seed: int, max_electrons: int = 32) -> SystemSpec:
     sc, sl, sz = np.array(sc, np.int32), np.array(sl, np.int32), np.array(sz, np.float64)
     M = int(sum(NCOMP[l] for l in sl))
     lo, hi = _basis_ranges(sc, sl, Nn)
-    # pairs per structure, limited by the size of the unique-determinant set
-    k = int(rng.integers(0, 5))
-    while k > 0 and (math.comb(2 * k, k) > (70 if n <= 8 else 20) or k > n):
-        k -= 1
+    # distinct pairs per structure (up to 4: 16 determinants); systems whose unique determinants
+    # do not fit the per-determinant kernels run on reference-determinant tables
+    k = min(int(rng.integers(0, 5)), n)
     n_inact = n - k
     # orbital q sits on the nucleus that initial_walkers() places electrons 2q and 2q + 1 near
     # (nuclei listed round(Z) times each), so that starting configurations are well conditioned

@@ -89,8 +89,8 @@ def lib():
                                                     vp, vp, vp, vp, vp, vp]
         L.vbqmc_dmc_steps.argtypes = [vp, ctypes.c_int, ctypes.c_int, _c_int_p, ctypes.c_int, vp, ctypes.c_int,
                                       ctypes.c_double, _c_dbl_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
-                                      ctypes.c_uint32, ctypes.c_uint32, _c_dbl_p, _c_dbl_p, _c_int_p, _c_dbl_p,
-                                      ctypes.POINTER(ctypes.c_int64), vp]
+                                      ctypes.c_uint32, ctypes.c_uint32, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_int_p,
+                                      _c_dbl_p, ctypes.POINTER(ctypes.c_int64), vp]
         L.vbqmc_batch_create.argtypes = [vp, ctypes.c_int, _c_int_p, _c_int_p, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_void_p)]
         L.vbqmc_batch_destroy.argtypes = [vp]
@@ -238,10 +238,11 @@ class Context:
         return int(lib().vbqmc_last_launch_count(self.h))
 
     def launch_info(self, sys_id, precision) -> dict:
-        out = np.zeros(4, np.int32)
+        out = np.zeros(5, np.int32)
         _check(lib().vbqmc_launch_info(self.h, int(sys_id), int(precision), out.ctypes.data_as(_c_int_p)))
         return {"eval_walkers_per_block": int(out[0]), "eval_smem_per_walker": int(out[1]),
-                "sweep_walkers_per_block": int(out[2]), "sweep_smem_per_walker": int(out[3])}
+                "sweep_walkers_per_block": int(out[2]), "sweep_smem_per_walker": int(out[3]),
+                "tables": bool(out[4])}
 
     def walker_state_size(self, sys_id) -> int:
         n = ctypes.c_int(0)
@@ -294,22 +295,24 @@ class Context:
                   walker_offset=0, stream=None):
         """vbqmc_dmc_steps on the population R[:W] of a float64 CUDA tensor R [cap, N, 3] (updated
         in place).  Returns (W, E_T, history) with history the per-step host arrays sum_wE,
-        sum_w, pop, e_trial (truncated to the steps run) and the accepted-move count."""
+        sum_w, sum_wEb, pop, e_trial (truncated to the steps run) and the accepted-move count."""
         cap = R.shape[0]
         W_c = ctypes.c_int(int(W))
         et = ctypes.c_double(float(E_T))
         swe = np.zeros(max(nsteps, 1))
         sw = np.zeros(max(nsteps, 1))
+        sweb = np.zeros(max(nsteps, 1))
         pop = np.full(max(nsteps, 1), -1, np.int32)
         etr = np.zeros(max(nsteps, 1))
         nacc = ctypes.c_int64(0)
         _check(lib().vbqmc_dmc_steps(self.h, int(sys_id), int(precision), ctypes.byref(W_c), int(cap), _ptr(R),
                                      int(nsteps), float(tau), ctypes.byref(et), int(target), int(seed) & (2**64 - 1),
                                      int(step0) & 0xffffffff, int(system_tag), int(walker_offset) & 0xffffffff,
-                                     _dp(swe), _dp(sw), _ip(pop), _dp(etr), ctypes.byref(nacc), _stream(stream)))
+                                     _dp(swe), _dp(sw), _dp(sweb), _ip(pop), _dp(etr), ctypes.byref(nacc),
+                                     _stream(stream)))
         ran = int((pop >= 0).sum()) if nsteps > 0 else 0
-        hist = {"sum_wE": swe[:ran], "sum_w": sw[:ran], "pop": pop[:ran], "e_trial": etr[:ran],
-                "accepted": int(nacc.value)}
+        hist = {"sum_wE": swe[:ran], "sum_w": sw[:ran], "sum_wEb": sweb[:ran], "pop": pop[:ran],
+                "e_trial": etr[:ran], "accepted": int(nacc.value)}
         return W_c.value, et.value, hist
 
     EVAL_KERNELS = ("jastrow", "orbitals", "det", "jastrow_deriv")
@@ -467,7 +470,7 @@ class Batch:
     """Several loaded systems run as one set of launches (vbqmc_batch_*).  Per-system arguments
     are lists of CUDA tensors in the order of sys_ids."""
 
-    KINDS = ("sweep", "jastrow", "jastrow_deriv", "orbitals", "det")
+    KINDS = ("sweep", "jastrow", "jastrow_deriv", "orbitals", "det", "fused")
 
     def __init__(self, ctx: "Context", sys_ids, walkers, precision):
         self.ctx = ctx
@@ -502,10 +505,13 @@ class Batch:
         _check(lib().vbqmc_batch_tune(self.h, keep[0], keep[1], keep[2], keep[3], _stream(stream)))
 
     def info(self):
-        out = np.zeros(25, np.int32)
+        out = np.zeros(33, np.int32)
         _check(lib().vbqmc_batch_info(self.h, _ip(out)))
-        return {k: dict(zip(("items", "grid", "warps", "persist", "cap"), out[5 * i:5 * i + 5].tolist()))
-                for i, k in enumerate(self.KINDS)}
+        d = {k: dict(zip(("items", "grid", "warps", "persist", "cap"), out[5 * i:5 * i + 5].tolist()))
+             for i, k in enumerate(self.KINDS)}
+        d["one_launch"] = bool(out[30])
+        d["tuned_eval_us"] = {"per_kind": int(out[31]), "one_launch": int(out[32])}
+        return d
 
 
 def create(device: int = 0) -> Context:

@@ -1,4 +1,4 @@
-"""Batched systems: many small molecules of uneven size in one set of launches.
+"""Batched systems: many small molecules of uneven size in one persistent launch per step.
 
 The batch runs the per-system kernels' arithmetic on every system through work-item tables,
 so a batched step must reproduce the per-system calls (same Philox streams with the system id
@@ -53,15 +53,19 @@ def test_batch_matches_per_system_calls(vb, precision):
     W = [32 + 16 * k for k in range(len(specs))]
     a = buffers(mod, ctx, specs, W, precision, 5)
     b = buffers(mod, ctx, specs, W, precision, 5)
+    # systems on reference-determinant tables (structures of many determinants) keep no state
+    tables = [ctx.launch_info(k, precision)["tables"] for k in ids]
     for step in range(2):
         for k in ids:
+            st = None if tables[k] else a["st"][k]
             ctx.vmc_steps(k, precision, a["R"][k], 2, specs[k].step, 77, step0=10 * step, system_tag=k, refresh=1,
-                          state=a["st"][k], state_valid=step > 0, nacc=a["na"][k], logpsi=a["lp"][k],
+                          state=st, state_valid=step > 0 and st is not None, nacc=a["na"][k], logpsi=a["lp"][k],
                           sign=a["sg"][k], eloc=a["el"][k], O=a["O"][k], dEL=a["dE"][k])
     batch = mod.Batch(ctx, ids, W, precision)
     for step in range(2):
         batch.vmc_steps(b["R"], 2, 0.3, 77, step0=10 * step, refresh=1, state=b["st"], state_valid=step > 0,
                         nacc=b["na"], logpsi=b["lp"], sign=b["sg"], eloc=b["el"], O=b["O"], dEL=b["dE"])
+        assert ctx.last_launch_count() == 1  # the whole step (sweeps and evaluation) in one launch
     torch.cuda.synchronize()
     assert all(sp.step == 0.3 for sp in specs)
     # positions and acceptances: identical (the same moves from the same random numbers);
@@ -95,7 +99,12 @@ def test_batch_tune_and_replay(vb):
     batch = mod.Batch(ctx, ids, W, 1)
     batch.tune(b["R"], b["lp"], b["sg"], b["el"])
     info = batch.info()
-    assert all(info[k]["items"] > 0 for k in info)
+    tables = any(ctx.launch_info(k, 1)["tables"] for k in ids)
+    # systems on reference-determinant tables have one-launch steps only (no per-kind plans)
+    kinds = ["fused"] if tables else mod.Batch.KINDS
+    assert all(info[k]["items"] > 0 for k in kinds)
+    assert info["one_launch"] or not tables
+    print("batch tune: one launch %s, evaluation us %s" % (info["one_launch"], info["tuned_eval_us"]))
     for step in range(3):
         batch.vmc_steps(b["R"], 1, 0.3, 5, step0=step, logpsi=b["lp"], sign=b["sg"], eloc=b["el"])
     torch.cuda.synchronize()
@@ -134,8 +143,10 @@ def test_random_molecules_match_oracle(vb, orc):
 
 
 def test_full_batched_workload(vb):
-    """64 random molecules with 256-4096 walkers each, mixed form, one batch: a tuned step with
-    derivatives gives finite results and reproduces a per-system evaluation on a sample."""
+    """64 random molecules with 256-4096 walkers each (structures of up to 16 determinants at any
+    size; the largest run on reference-determinant tables), mixed form, one batch: a tuned step
+    with derivatives is one launch, gives finite results and reproduces a per-system evaluation
+    on a sample."""
     mod, ctx = vb
     specs, W = S.batched_workload(64)
     ids = load(vb, specs)
@@ -145,6 +156,9 @@ def test_full_batched_workload(vb):
     batch.vmc_steps(b["R"], 1, 0.3, 11, logpsi=b["lp"], sign=b["sg"], eloc=b["el"], O=b["O"], dEL=b["dE"],
                     state=b["st"])
     torch.cuda.synchronize()
+    assert ctx.last_launch_count() == 1
+    tables = sum(ctx.launch_info(k, 1)["tables"] for k in ids)
+    print("full batch: %d systems, %d on tables, one launch %s" % (len(ids), tables, batch.info()["one_launch"]))
     for k in ids:
         assert torch.isfinite(b["el"][k]).all() and torch.isfinite(b["O"][k]).all(), k
     for k in (0, 17, 63):

@@ -139,3 +139,34 @@ def test_dmc48_full_population(vb, orc, spec):
     got = gpu_eval(vb, spec, R, 1)
     assert np.abs(got["logpsi"] - ref["logpsi"]).max() <= 1e-5
     assert _rel(got["eloc"], ref["eloc"]).max() <= 1e-4
+
+
+def test_dmc48_reduced_population_220_steps(vb, spec):
+    """The DMC workload at a reduced population: 1024 walkers equilibrated by VMC sweeps (table
+    sweeps, mixed form), then 220 DMC steps at tau = 0.005 in each form, four independent
+    replicas per form.  The population stays within +-20 % of the target in every step after
+    the first 20, and the two forms' estimates (mean over steps 20..219 of sum w E_L / sum w)
+    agree within 2 sigma (sigma from the replicas' spread).  The FP64 form's first steps match
+    the oracle's step by step (test_dmc48_fp64_trajectory_matches_oracle)."""
+    mod, ctx = vb
+    ctx.set_system(0, spec)
+    W, tau, steps, skip = 1024, 0.005, 220, 20
+    R = torch.tensor(S.initial_walkers(spec, W, 6), device="cuda")
+    ctx.vmc_steps(0, 1, R, 60, spec.step, 3, step0=0, refresh=10)
+    lp, sg, el = (torch.zeros(W, dtype=torch.float64, device="cuda") for _ in range(3))
+    ctx.eval_walkers(0, 1, R, lp, sg, el)
+    e0 = float(el.mean())
+    est = {0: [], 1: []}
+    for prec in (1, 0):
+        for rep in range(4):
+            buf = torch.zeros((W * 3 // 2, spec.N, 3), dtype=torch.float64, device="cuda")
+            buf[:W] = R
+            _, _, h = ctx.dmc_steps(0, prec, buf, W, steps, tau, e0, W, 1000 + rep, step0=0)
+            pop = np.asarray(h["pop"])
+            assert len(pop) == steps, len(pop)
+            assert np.all(np.abs(pop[skip:] / W - 1.0) <= 0.2), (pop.min(), pop.max())
+            est[prec].append(float(np.mean(h["sum_wE"][skip:] / h["sum_w"][skip:])))
+    m = {p: np.mean(v) for p, v in est.items()}
+    s = {p: np.std(v, ddof=1) / np.sqrt(len(v)) for p, v in est.items()}
+    print("dmc48 reduced: E_VMC %.3f, DMC mixed %.3f +- %.3f, fp64 %.3f +- %.3f" % (e0, m[1], s[1], m[0], s[0]))
+    assert abs(m[1] - m[0]) < 2 * np.hypot(s[0], s[1]), (m, s)

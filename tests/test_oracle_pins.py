@@ -713,6 +713,20 @@ def test_dmc_limits_bound_the_weights_at_a_node(orc):
     assert out["pop"][0] <= 2 * W
 
 
+def test_dmc_energy_cutoff_bounds_every_weight(orc):
+    """Far from any node a walker can still have a huge |E_L| (here: E_T set 1e4 Ha away from the
+    exact energy of the 1s trial, every walker's E_L - E_T = -1e4).  The cutoff
+    |E_b - E_T| <= 0.2 sqrt(N / tau) (Zen et al. 2016) bounds each weight to
+    exp(tau 0.2 sqrt(N / tau)): with N = 1, tau = 0.01 that is exp(0.02) per walker, so the
+    weight sum is exactly W exp(0.02) (without the cutoff it would be W exp(100))."""
+    Z = 2.0
+    spec = S.one_electron(Z, 0.0, a1=-Z, a2=-0.8)
+    W, tau = 32, 0.01
+    R = np.random.default_rng(3).normal(scale=0.6, size=(W, 1, 3))
+    out = orc.dmc(spec, R, 1, tau, -0.5 * Z * Z + 1e4, W, seed=2, cap=8 * W)
+    np.testing.assert_allclose(out["sum_w"][0], W * np.exp(tau * 0.2 * np.sqrt(1.0 / tau)), rtol=1e-12)
+
+
 # ----------------------------------------------------------------------------- Slater shells
 @pytest.mark.parametrize("Z", list(range(1, 10)))
 def test_slater_1s_exact_without_jastrow(orc, Z):

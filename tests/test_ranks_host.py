@@ -30,6 +30,7 @@ def test_single_rank_calls_return_their_input():
     assert ranks.world() == (0, 1)
     assert ranks.max_over_ranks(2.5) == 2.5
     assert ranks.dmc_global_sums(1.0, 2.0, 3) == (1.0, 2.0, 3)
+    assert ranks.dmc_global_sums(1.0, 2.0, 3, sum_wEb=4.0, failed=False) == (1.0, 2.0, 3, 4.0, 0)
     assert ranks.walker_offset(3, 1024) == 3072
     R = torch.zeros((4, 2, 3))
     assert ranks.balance_walkers(R, 3) == 3
@@ -83,19 +84,23 @@ def _dmc_run_worker(rank, world, port):
         R = torch.zeros((16, 1, 3), dtype=torch.float64)
         seen = []
 
-        keys = []
+        keys, last_ret = [], []
 
         def step(W, E_T, k, off):  # a stand-in step: rank 0 grows by 3, rank 1 shrinks by 1; E_L = -1 - rank
             seen.append(E_T)
             keys.append((k, off))
             W2 = W + 3 if rank == 0 else max(W - 1, 0)
             R[:W2, 0, 0] = float(rank)
-            return W2, (-1.0 - rank) * W2, float(W2)
+            last_ret.append((W2, (-1.0 - rank) * W2, float(W2), (-1.5 - rank) * W2))
+            return last_ret[-1]
         W, E_T, hist = ranks.dmc_run(step, R, 4, 3, tau=0.01, E_T=-1.0, target_per_rank=4, step0=100)
         # every rank sees the same global sums and trial energies
         assert [h[2] for h in hist] == [10, 12, 14]
         gwE, gw, gpop = hist[-1]
-        assert abs(E_T - (gwE / gw - 10.0 * math.log(gpop / 8))) < 1e-12
+        # E_T follows the global sum of w E_b of the last step (the fourth value each rank returned)
+        last = torch.tensor([last_ret[-1][3]], dtype=torch.float64)
+        dist.all_reduce(last)
+        assert abs(E_T - (float(last) / gw - 10.0 * math.log(gpop / 8))) < 1e-12
         assert W == 7 and seen[0] == -1.0 and len(set(seen)) == 3
         # the random-number keys: global step numbers, and walker ranges [off, off + cap) that
         # differ between the ranks (the streams of vbqmc_dmc_steps never coincide)
@@ -122,7 +127,7 @@ def _failure_worker(rank, world, port, mode):
             def step(W, E_T, k, off):  # rank 1 fails at its second step
                 if rank == 1 and k == 1:
                     raise ValueError("capacity exceeded on rank 1")
-                return W, -1.0 * W, float(W)
+                return W, -1.0 * W, float(W), -1.0 * W
             try:
                 ranks.dmc_run(step, R, 4, 5, tau=0.01, E_T=-1.0, target_per_rank=4)
             except ValueError as e:
