@@ -713,7 +713,22 @@ def batched_timing(vbqmc, dev, steps):
     ms = e0.elapsed_time(e1) / n
     launches = ctx.last_launch_count()
     info = batch.info()
-    tables = sum(ctx.launch_info(k, vbqmc.MIXED)["tables"] for k in range(len(specs)))
+    on_tab = [ctx.launch_info(k, vbqmc.MIXED)["tables"] for k in range(len(specs))]
+    tables = sum(on_tab)
+    # the same step system by system through the single-system call (what the batch replaces)
+    def per_system(step0):
+        for k in range(len(specs)):
+            ctx.vmc_steps(k, vbqmc.MIXED, R[k], 1, 0.3, SEED, step0=step0, refresh=0,
+                          state=None if on_tab[k] else st[k], state_valid=True, logpsi=lp[k], sign=sg[k],
+                          eloc=el[k], O=O[k], dEL=dE[k])
+    per_system((1 << 24))
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(n):
+        per_system((1 << 24) + 1 + k)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_sep = e0.elapsed_time(e1) / n
     batch.close()
     ctx.close()
     # per-electron-pair normalisation: walker-steps/s x mean N^2, comparable across system sizes
@@ -722,6 +737,7 @@ def batched_timing(vbqmc, dev, steps):
                                                                        max(sp.N for sp in specs)],
             "systems_on_tables": int(tables), "mean_N2_per_walker": n2,
             "walker_steps_per_s": sum(W) / (ms * 1e-3), "ms_per_step": ms, "launches_per_step": launches,
+            "per_system_calls_ms_per_step": ms_sep, "speedup_over_per_system_calls": ms_sep / ms,
             "one_launch": info["one_launch"], "tuned_eval_us": info["tuned_eval_us"],
             "launch_shapes": {k: [info[k]["grid"], info[k]["warps"], info[k]["persist"], info[k]["cap"]]
                               for k in vbqmc.Batch.KINDS}}

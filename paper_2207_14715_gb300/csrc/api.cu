@@ -761,7 +761,8 @@ int vbqmc_accumulate_lin_matrices(vbqmc_ctx* ctx, int precision, int P, int64_t 
   if (!O || !dEL || !eloc || !E0 || !gL || !gR || !S || !H) return fail(VBQMC_ERR_ARG, "null required pointer");
   DeviceGuard g(ctx->device);
   ctx->last_launches = 0;
-  const size_t need = vbq::lin_workspace_bytes(P, M);
+  const int nsm = vbq::lin_sms();
+  const size_t need = vbq::lin_workspace_bytes(P, M, nsm);
   if (need > ctx->work_bytes) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
@@ -773,8 +774,8 @@ int vbqmc_accumulate_lin_matrices(vbqmc_ctx* ctx, int precision, int P, int64_t 
     ctx->work_bytes = need;
   }
   int nl = 0;
-  cudaError_t e = vbq::launch_lin(precision == VBQMC_MIXED, P, (long long)M, O, dEL, eloc, weights, ctx->work, E0, gL,
-                                  gR, S, H, (cudaStream_t)stream, &nl);
+  cudaError_t e = vbq::launch_lin(precision == VBQMC_MIXED, P, (long long)M, O, dEL, eloc, weights, ctx->work,
+                                  ctx->work_bytes, nsm, E0, gL, gR, S, H, (cudaStream_t)stream, &nl);
   if (e != cudaSuccess) return cuda_fail(e, "linear-method kernels");
   ctx->last_launches = nl;
   return VBQMC_OK;

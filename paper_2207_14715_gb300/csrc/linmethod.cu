@@ -18,9 +18,10 @@
 //      the accuracy of a float to 2^-22) and transposed to parameter-major rows; the same pass
 //      forms sum w Ot E from the centred values (block partials, fixed-order sum);
 //  (3) the products on the tensor cores (tcgen05, kind::f16, FP32 accumulators in tensor
-//      memory): per output tile of 128 parameters j x 112 parameters i and chunk of samples,
-//      D_S[j][i] = sum_s X_sj X_si and D_H[j][i] = sum_s Y_sj X_si, each product formed as
-//      hi*lo + lo*hi + hi*hi (the lo*lo term is below the float accuracy);
+//      memory): per output tile of 128 parameters i x 112 parameters j and chunk of samples,
+//      D_S[i][j] = sum_s X_si X_sj and D_H[i][j] = sum_s X_si Y_sj in one MMA of N = 224 whose B
+//      operand stacks the j rows of X and of Y, each product formed as hi*lo + lo*hi + hi*hi
+//      (the lo*lo term is below the float accuracy);
 //  (4) the chunk partials added in double in a fixed order, unscaled and divided by sum w.
 // The half-precision split runs the tensor cores at twice the rate of the TF32 split with the
 // same accuracy, because the per-parameter scales keep every value in the normal half range;
@@ -37,20 +38,24 @@ namespace vbq {
 
 namespace {
 
-constexpr int kTj = 128;          // output tile rows j (MMA M, tensor-memory lanes)
-constexpr int kTi = 112;          // output tile columns i (MMA N, a multiple of 16)
+constexpr int kTa = 128;          // output tile rows i (MMA M, tensor-memory lanes): A = X_i
+constexpr int kTb = 112;          // output tile columns j of S and of H: B = [X_j; Y_j], N = 224
 constexpr int kColBlock = 256;    // threads of a column-sum block (and samples per sub-tile)
 constexpr int kColTiles = 1;      // sub-tiles per column-sum block
 constexpr int kCenTiles = 8;      // 64-sample tiles per centring block: 512 samples
 constexpr float kScaleTop = 16384.0f;  // scaled values stay below 2^14 (half precision max 65504)
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
-__host__ __device__ inline int rows_j(int P) { return round_up(P, kTj); }
-__host__ __device__ inline int rows_i(int P) { return round_up(P, kTi); }
-// rows of the transposed arrays: both tile kinds, rounded to the centring kernel's 64-row blocks
-__host__ __device__ inline int rows_t(int P) { return round_up(rows_j(P) > rows_i(P) ? rows_j(P) : rows_i(P), 64); }
+__host__ __device__ inline int rows_a(int P) { return round_up(P, kTa); }
+__host__ __device__ inline int rows_b(int P) { return round_up(P, kTb); }
+// stored rows of the transposed arrays: P rounded to the centring kernel's 64-row blocks, at
+// least one 128-row tile (the tensor-core pass reads the rows from max(P, 128) up to its tile
+// edges as zeros, filled by the copy engine, not from memory)
+__host__ __device__ inline int rows_t(int P) { return round_up(P > kTa ? P : kTa, 64); }
+// rows the tensor maps cover (never fewer than a box)
+__host__ __device__ inline int rows_m(int P) { return P > kTa ? P : kTa; }
 
-// (1) Block partials: row b = [sum w, sum w E, sum w O (P), sum w dE (P)] over the block's 2048
+// (1) Block partials: row b = [sum w, sum w E, sum w O (P), sum w dE (P)] over the block's 256
 // samples (the O and dE sums in the input type per thread, stored in double); maxima as float
 // bits (non-negative floats order like unsigned): mx[0] = max w, mx[1] = max |E|,
 // mx[2 + c] = max |O_c|, mx[2 + P + c] = max |dE_c|.
@@ -103,6 +108,7 @@ __global__ void __launch_bounds__(kColBlock) lin_colsum_kernel(int P, long long 
           tot_we = fma(sw[k], se[k], tot_we);
         }
       if (c < P)
+#pragma unroll 8
         for (int k = 0; k < n; ++k) {
           const Tin o = O[(s0 + k) * P + c], d = dEL[(s0 + k) * P + c];
           const Tin ws = (Tin)sw[k];
@@ -125,18 +131,37 @@ __global__ void __launch_bounds__(kColBlock) lin_colsum_kernel(int P, long long 
   }
 }
 
-// Block partials added in a fixed order: acc[q] = sum over k of (sum of part1[b][q] for the
-// blocks b = k mod 8, in block order), eight independent chains for memory-level parallelism.
-__global__ void lin_colsum_reduce(int L1, int nb, const double* __restrict__ part1, double* __restrict__ acc) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= L1) return;
-  double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  int b = 0;
-  for (; b + 8 <= nb; b += 8)
+// Block partials added in a fixed order, in two levels so that the whole machine takes part:
+// (a) grid (columns / 32, kSeg): block (x, g) sums for its 32 columns the partial rows of
+//     segment g (rows [g nb / kSeg, (g + 1) nb / kSeg)), warp w the rows w, w + 8, ... of the
+//     segment, the 8 warp sums added in warp order: seg[g][q];
+// (b) acc[q] = sum over g of seg[g][q] in segment order.
+constexpr int kSeg = 64;
+__global__ void __launch_bounds__(256) lin_seg_reduce(int L, int nb, const double* __restrict__ part,
+                                                      double* __restrict__ seg) {
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int q = blockIdx.x * 32 + lane, g = blockIdx.y;
+  const int b0 = (int)((long long)g * nb / kSeg), b1 = (int)((long long)(g + 1) * nb / kSeg);
+  double s = 0.0;
+  if (q < L)
+#pragma unroll 4
+    for (int b = b0 + wp; b < b1; b += 8) s += part[(size_t)b * L + q];
+  red[wp][lane] = s;
+  __syncthreads();
+  if (wp == 0 && q < L) {
+    double t = red[0][lane];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) s[k] += part1[(size_t)(b + k) * L1 + q];
-  for (int k = 0; b + k < nb; ++k) s[k] += part1[(size_t)(b + k) * L1 + q];
-  acc[q] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+    for (int k = 1; k < 8; ++k) t += red[k][lane];
+    seg[(size_t)g * L + q] = t;
+  }
+}
+__global__ void lin_final_reduce(int L, const double* __restrict__ seg, double* __restrict__ acc) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= L) return;
+  double s = 0.0;
+  for (int g = 0; g < kSeg; ++g) s += seg[(size_t)g * L + q];
+  acc[q] = s;
 }
 
 // Per-sample float copies for the centring pass: sqrt(w_s) and E_s.
@@ -180,17 +205,20 @@ __device__ __forceinline__ void split_half(float v, __half& hi, __half& lo) {
   lo = __float2half_rn(v - __half2float(hi));
 }
 
-// (2b) Scaled, split and transposed values: rows c < Pr of Xh/Xl/Yh/Yl [Pr][Mp] hold the samples
-// of parameter c (zero rows c >= P).  A block transposes 64 samples x 64 parameters through
+// (2b) Scaled, split and transposed values in sample groups: group g (samples 32 g .. 32 g + 31)
+// of XI and YI is a [Pr][64] block of halves whose row c holds parameter c's 32 high halves
+// followed by its 32 low halves (one 128-byte row); zero rows c >= P and zero samples
+// M <= s < Mp.  A tile of the tensor-core pass (rows r0 .. r0 + 127 of one group) is then one
+// contiguous 16 KB block.  A block of this kernel transposes 64 samples x 64 parameters through
 // shared memory: reads along parameters and writes along samples are both coalesced.
 template <class Tin>
 __global__ void __launch_bounds__(256) lin_center_kernel(int P, long long M, long long Mp, const Tin* __restrict__ O,
                                                          const Tin* __restrict__ dEL, const double* __restrict__ E,
                                                          const double* __restrict__ w, const float* __restrict__ rwf,
                                                          const float* __restrict__ Ef, const double* __restrict__ acc,
-                                                         const float* __restrict__ scl, int Pr, __half* __restrict__ Xh,
-                                                         __half* __restrict__ Xl, __half* __restrict__ Yh,
-                                                         __half* __restrict__ Yl, double* __restrict__ part2) {
+                                                         const float* __restrict__ scl, int Pr,
+                                                         __half* __restrict__ XI, __half* __restrict__ YI,
+                                                         double* __restrict__ part2) {
   // [array][parameter][sample]: rows of 72 halves (144 bytes) keep the 16-byte chunks aligned
   __shared__ __align__(16) __half t[4][64][72];
   __shared__ double red[4][64];
@@ -201,21 +229,30 @@ __global__ void __launch_bounds__(256) lin_center_kernel(int P, long long M, lon
   const Tin mo = c < P ? (Tin)(acc[2 + c] * isw) : (Tin)0;
   const float sx = scl[c], sy = scl[Pr + c];
   double sxe = 0.0;  // sum over this thread's samples of w Ot E (16-sample partials in Tin)
-  __half* const dst[4] = {Xh, Xl, Yh, Yl};
   for (int tt = 0; tt < kCenTiles; ++tt) {
     const long long s0 = ((long long)blockIdx.x * kCenTiles + tt) * 64;
     if (s0 >= M) break;
     __syncthreads();
     Tin part = 0;
+    // all 32 loads of the tile first (memory-level parallelism), then the arithmetic
+    Tin ov[16], dv[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const long long sm = s0 + sq + 4 * k;
+      const bool in = sm < M && c < P;
+      ov[k] = in ? O[sm * P + c] : (Tin)0;
+      dv[k] = in ? dEL[sm * P + c] : (Tin)0;
+    }
+#pragma unroll
     for (int k = 0; k < 16; ++k) {
       const int sl = sq + 4 * k;
       const long long sm = s0 + sl;
       float xv = 0.0f, yv = 0.0f;
       if (sm < M && c < P) {
-        const Tin x = O[sm * P + c] - mo;
+        const Tin x = ov[k] - mo;
         const Tin e = std::is_same<Tin, double>::value ? (Tin)E[sm] : (Tin)Ef[sm];
         const Tin ex = e * x;
-        const Tin y = ex + dEL[sm * P + c];
+        const Tin y = ex + dv[k];
         const float rw = rwf[sm];
         xv = (float)x * rw * sx;
         yv = (float)y * rw * sy;
@@ -226,18 +263,16 @@ __global__ void __launch_bounds__(256) lin_center_kernel(int P, long long M, lon
     }
     sxe += (double)part;
     __syncthreads();
-    // 16-byte stores: per array 64 rows x 8 chunks of 8 samples
-    for (int q = threadIdx.x; q < 4 * 64 * 8; q += 256) {
-      const int a = q >> 9, rr = (q >> 3) & 63, ch = q & 7;
-      const long long sm = s0 + 8 * ch;
-      if (sm >= M) continue;
-      const uint4 v = *reinterpret_cast<const uint4*>(&t[a][rr][8 * ch]);
-      if (sm + 8 <= M) {
-        *reinterpret_cast<uint4*>(dst[a] + (size_t)(c0 + rr) * Mp + sm) = v;
-      } else {  // the ragged end of the samples
-        const __half* hv = reinterpret_cast<const __half*>(&v);
-        for (int u = 0; u < (int)(M - sm); ++u) dst[a][(size_t)(c0 + rr) * Mp + sm + u] = hv[u];
-      }
+    // 16-byte stores: per array (X, Y), group g of the tile's two and row, the 128-byte row
+    // [hi 0-31 | lo 0-31] in 8 chunks of 8 halves; groups that start at or past Mp are not stored
+    for (int q = threadIdx.x; q < 2 * 64 * 16; q += 256) {
+      const int a = q >> 10, rr = (q >> 4) & 63, ch = q & 15;
+      const int g = ch >> 3, part = (ch >> 2) & 1, sub = ch & 3;
+      if (s0 + 32 * g >= Mp) continue;
+      const uint4 v = *reinterpret_cast<const uint4*>(&t[2 * a + part][rr][32 * g + 8 * sub]);
+      __half* const dst = a == 0 ? XI : YI;
+      const size_t grp = (size_t)(s0 / 32 + g);
+      *reinterpret_cast<uint4*>(dst + (grp * Pr + c0 + rr) * 64 + 32 * part + 8 * sub) = v;
     }
   }
   red[sq][cl] = sxe;
@@ -248,184 +283,232 @@ __global__ void __launch_bounds__(256) lin_center_kernel(int P, long long M, lon
 }
 
 // (3) Partial tiles, one CTA per (128 x 112 output tile, chunk of samples):
-//   part[chunk][0][j][i] = sum_{s in chunk} X_sj X_si,   part[chunk][1][j][i] = sum Y_sj X_si
-// (scaled values).  Per stage of 32 samples, TMA brings the tiles Xj hi/lo, Yj hi/lo (128 rows)
-// and Xi hi/lo (112 rows), 64-byte rows K-major with the 64-byte swizzle (the layout the MMA
-// reads), four stages in flight.  One thread issues per 16-sample slice the MMAs
-// Xj_hi Xi_lo, Xj_lo Xi_hi, Xj_hi Xi_hi into D_S and the same with Yj into D_H (correction
-// products first, while the accumulator is small).  The tensor core's accumulation rounds at
-// the accumulator's magnitude, so an accumulator covers 64 samples (two stages) and is then
-// moved to registers and summed there in FP32 (round to nearest); two tensor-memory sets
-// alternate so that draining overlaps the next MMAs.  Barrier waits are bounded (about a
-// second); on a timeout the CTA raises *err and stops.
-constexpr int kTcThreads = 256;
-constexpr int kK = 32;                                     // samples per stage (64 bytes of f16)
-constexpr int kStages = 4;
-constexpr int kJBytes = kTj * kK * 2;                      // 8 KB
-constexpr int kIBytes = kTi * kK * 2;                      // 7 KB
-constexpr int kStageBytes = 4 * kJBytes + 2 * kIBytes;     // Xj hi, Xj lo, Yj hi, Yj lo, Xi hi, Xi lo
-constexpr int kTcSmem = kStages * kStageBytes + 1024 + 128;
+//   part[chunk][0][i][j] = sum_{s in chunk} X_si X_sj,   part[chunk][1][i][j] = sum X_si Y_sj
+// (scaled values).  Per stage of 32 samples (one group), TMA brings the A tile X_i (128 rows) and
+// the B tile [X_j; Y_j] (2 x 112 rows), each row 128 bytes [32 high halves | 32 low halves],
+// K-major with the 128-byte swizzle (the layout the MMA reads: the high and low operands of a
+// 16-sample slice start 32 bytes apart within the swizzled rows, at +32 kk and +64 + 32 kk).  Warp roles: warp 8 issues the copies into a ring of stages;
+// warp 9 owns the tensor memory and issues per 16-sample slice the MMAs A_hi B_lo, A_lo B_hi,
+// A_hi B_hi (M = 128, N = 224: columns 0-111 accumulate S, 112-223 H; the correction
+// products first, while the accumulator is small); warps 0-7 drain the accumulators.  The
+// tensor core's accumulation rounds at the accumulator's magnitude, so an accumulator covers 64
+// samples (two stages) and is then moved to registers and summed there in FP32 (round to
+// nearest); two tensor-memory sets alternate so that draining overlaps the next MMAs.  The
+// roles meet only on shared-memory barriers: stage full (copies landed), stage empty (its MMAs
+// done), set full (a pair's MMAs done), set empty (all eight drain warps read it).  Every wait
+// is bounded (about a second); a timeout sets a shared abort flag that the other roles check
+// before each wait, copies and MMAs in flight still get a bounded wait before the shared and
+// tensor memory are released, and the CTA raises *err instead of writing its partials.
+constexpr int kTcWarps = 10;                               // 8 drain warps, copy warp, MMA warp
+constexpr int kTcThreads = 32 * kTcWarps;
+constexpr int kCopyWarp = 8, kMmaWarp = 9;
+constexpr int kK = 32;                                     // samples per stage
+constexpr int kRow = 2 * kK * 2;                           // 128-byte rows: high and low halves
+constexpr int kStages = 5;
+constexpr int kN = 2 * kTb;                                // MMA N: the j rows of X and of Y
+constexpr int kABytes = kTa * kRow;                        // 16 KB
+constexpr int kHBytes = kTb * kRow;                        // 14 KB: the X_j (or Y_j) half of B
+constexpr int kBBytes = 2 * kHBytes;                       // 28 KB
+constexpr int kStageBytes = kABytes + kBBytes;             // A, B
+constexpr int kNumBars = 2 * kStages + 5;                  // full, empty, set full x2, set empty x2, done
+constexpr int kTcSmem = kStages * kStageBytes + 1024 + 8 * kNumBars + 64;
 constexpr int kSetCols = 256;                              // tensor-memory columns per accumulator set
 constexpr uint64_t kWaitNs = 1000000000ull;
-static_assert(kIBytes % 512 == 0 && kJBytes % 512 == 0, "swizzled tiles stay 512-byte aligned");
+static_assert(kHBytes % 1024 == 0 && kABytes % 1024 == 0, "128-byte swizzled tiles stay 1024-byte aligned");
+static_assert(kN % 16 == 0 && kN <= 256 && kN <= kSetCols, "MMA shape M = 128 needs N a multiple of 16, <= 256");
+static_assert(kTcSmem <= 232448, "shared memory of one CTA");
 
-// adds this thread's 112 accumulator columns of set 'set' (warp w: lanes 32 (w % 4) + lane;
-// warps 0-3 the S tile, warps 4-7 the H tile)
-// (the loads go out four and three at a time, each group behind one wait)
-__device__ __forceinline__ void drain(uint32_t tmem, int set, int warp, float acc[kTi]) {
-  const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(kSetCols * set) +
-                        (warp < 4 ? 0u : (uint32_t)kTi);
-  uint32_t v[4][16];
+// adds this warp's 112 accumulator columns (lanes 32 (warp % 4) + lane; warps 0-3 the S half
+// of the set, warps 4-7 the H half) starting at tensor-memory address 'base'; the loads go out
+// two at a time behind one wait
+__device__ __forceinline__ void drain(uint32_t base, float acc[kTb]) {
+  uint32_t v[2][16];
 #pragma unroll
-  for (int g = 0; g < 4; ++g) tmem_ld16_async(base + 16 * g, v[g]);
-  tmem_wait_ld();
+  for (int g = 0; g < kTb / 16; g += 2) {
+    tmem_ld16_async(base + 16 * g, v[0]);
+    if (g + 1 < kTb / 16) tmem_ld16_async(base + 16 * (g + 1), v[1]);
+    tmem_wait_ld();
 #pragma unroll
-  for (int g = 0; g < 4; ++g)
+    for (int q = 0; q < 16; ++q) acc[16 * g + q] += __uint_as_float(v[0][q]);
+    if (g + 1 < kTb / 16)
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[16 * g + q] += __uint_as_float(v[g][q]);
-#pragma unroll
-  for (int g = 0; g < 3; ++g) tmem_ld16_async(base + 64 + 16 * g, v[g]);
-  tmem_wait_ld();
-#pragma unroll
-  for (int g = 0; g < 3; ++g)
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[64 + 16 * g + q] += __uint_as_float(v[g][q]);
+      for (int q = 0; q < 16; ++q) acc[16 * (g + 1) + q] += __uint_as_float(v[1][q]);
+  }
+}
+
+// Pacing of the CTAs that share a chunk (they read the same X and Y rows, through L2): the copy
+// thread publishes its step every kProgEvery steps and, while a started peer is more than
+// kLead steps behind, waits for it, at most kPaceNs per check.  The wait is a hint for L2
+// reuse only: it never fails, and a peer that has not started (-1) or has finished is not
+// waited for.
+constexpr int kProgEvery = 16;
+constexpr int kLead = 32;
+constexpr uint64_t kPaceNs = 20000;
+__device__ __forceinline__ void pace(int* peers, int me, int n, int ks) {
+  __stcg(peers + me, ks);
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    int lo = ks;
+    for (int t = 0; t < n; ++t) {  // independent L2 reads (not cached in L1)
+      const int p = __ldcv(peers + t);
+      if (p >= 0 && p < lo) lo = p;
+    }
+    if (ks - lo <= kLead || global_ns() - t0 > kPaceNs) return;
+    __nanosleep(256);
+  }
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
-    lin_tc_kernel(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUtensorMap tXl,
-                  const __grid_constant__ CUtensorMap tYh, const __grid_constant__ CUtensorMap tYl,
-                  const __grid_constant__ CUtensorMap tXhi, const __grid_constant__ CUtensorMap tXli, int Pj, int Pi,
-                  long long M, long long chunk, double* __restrict__ part, int* __restrict__ err) {
+    lin_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tBX,
+                  const __grid_constant__ CUtensorMap tBY, int Pa, int Pb, long long M, long long chunk,
+                  double* __restrict__ part, int* __restrict__ prog, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kStages * kStageBytes);  // [kStages] TMA arrivals
-  uint64_t* done = full + kStages;                                            // [kStages] MMA completions
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + kStages);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int nti = Pi / kTi;
-  const int tj = blockIdx.x / nti, ti = blockIdx.x % nti;
-  const int j0 = tj * kTj, i0 = ti * kTi;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kStages * kStageBytes);  // [kStages] copies landed
+  uint64_t* empty = full + kStages;                                           // [kStages] MMAs of the stage done
+  uint64_t* sfull = empty + kStages;                                          // [2] a pair's MMAs done
+  uint64_t* sempty = sfull + 2;                                               // [2] drained by 8 warps
+  uint64_t* mdone = sempty + 2;                                               // every MMA issued done
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mdone + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntb = Pb / kTb;
+  const int ta = blockIdx.x / ntb, tb = blockIdx.x % ntb;
+  const int i0 = ta * kTa, j0 = tb * kTb;
   const long long s0 = (long long)blockIdx.y * chunk, s1 = min(M, s0 + chunk);
-  const int nsteps = (int)((s1 - s0 + kK - 1) / kK);
-  // tiles of a stage: 0 Xj_hi, 1 Xj_lo, 2 Yj_hi, 3 Yj_lo, 4 Xi_hi, 5 Xi_lo
-  auto tile = [&](int st, int t) {
-    return sm + st * kStageBytes + (t < 4 ? t * kJBytes : 4 * kJBytes + (t - 4) * kIBytes);
-  };
-  int loaded = 0;  // (thread 0) steps whose TMA was issued
-  auto load = [&](int ks) {
-    const int st = ks % kStages, x = (int)(s0 + (long long)ks * kK);
-    loaded = ks + 1;
-    mbar_arrive_expect_tx(&full[st], kStageBytes);
-    tma_load_2d(tile(st, 0), &tXh, x, j0, &full[st]);
-    tma_load_2d(tile(st, 1), &tXl, x, j0, &full[st]);
-    tma_load_2d(tile(st, 2), &tYh, x, j0, &full[st]);
-    tma_load_2d(tile(st, 3), &tYl, x, j0, &full[st]);
-    tma_load_2d(tile(st, 4), &tXhi, x, i0, &full[st]);  // 112-row boxes
-    tma_load_2d(tile(st, 5), &tXli, x, i0, &full[st]);
-  };
+  const int nsteps = s1 > s0 ? (int)((s1 - s0 + kK - 1) / kK) : 0;
+  const int npairs = (nsteps + 1) / 2;
+  // stage layout: A = X_i rows, B = [X_j rows; Y_j rows]
+  auto a_tile = [&](int st) { return sm + st * kStageBytes; };
+  auto b_tile = [&](int st) { return sm + st * kStageBytes + kABytes; };
 
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     for (int b = 0; b < kStages; ++b) {
       mbar_init(&full[b], 1);
-      mbar_init(&done[b], 1);
+      mbar_init(&empty[b], 1);
     }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sfull[b], 1);
+      mbar_init(&sempty[b], 8);
+    }
+    mbar_init(mdone, 1);
+    *abort_flag = 0;
     fence_async_smem();
   }
-  if (warp == 0) tmem_alloc(tmem_holder, 512);  // set b at columns 256 b: S (+0), H (+112)
+  if (warp == kMmaWarp) tmem_alloc(tmem_holder, 512);  // set b at columns 256 b: S (+0), H (+112)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
-  if (tid == 0)
-    for (int ks = 0; ks < kStages && ks < nsteps; ++ks) load(ks);
-  constexpr uint32_t idesc = idesc_f16(kTj, kTi);
-  float acc[kTi];
-#pragma unroll
-  for (int c = 0; c < kTi; ++c) acc[c] = 0.0f;
-  bool ok = true;
-  int issued = 0, drained = 0;
+  float acc[kTb];
 
-  for (int ks = 0; ks < nsteps; ++ks) {
-    // steps 2p and 2p + 1 accumulate into tensor-memory set p & 1
-    const int st = ks % kStages, set = (ks >> 1) & 1;
-    if (tid == 0) {
-      const bool arrived = mbar_wait(&full[st], (uint32_t)((ks / kStages) & 1), kWaitNs);
-      if (arrived) {
+  if (warp == kCopyWarp) {
+    if (lane == 0) {
+      int* const peers = prog + (size_t)blockIdx.y * gridDim.x;  // the chunk's CTAs, one per tile
+      int loaded = 0;
+      for (int ks = 0; ks < nsteps; ++ks) {
+        const int st = ks % kStages;
+        if ((ks & (kProgEvery - 1)) == 0) pace(peers, (int)blockIdx.x, (int)gridDim.x, ks);
+        if (ks >= kStages) {  // the stage's previous MMAs must be done
+          if (*abort_flag) break;
+          if (!mbar_wait(&empty[st], (uint32_t)((ks / kStages - 1) & 1), kWaitNs)) {
+            *abort_flag = 1;
+            break;
+          }
+        }
+        const int g = (int)(s0 / kK) + ks;  // sample group
+        mbar_arrive_expect_tx(&full[st], kStageBytes);
+        tma_load_3d(a_tile(st), &tA, 0, i0, g, &full[st]);
+        tma_load_3d(b_tile(st), &tBX, 0, j0, g, &full[st]);
+        tma_load_3d(b_tile(st) + kHBytes, &tBY, 0, j0, g, &full[st]);
+        loaded = ks + 1;
+      }
+      __stcg(peers + blockIdx.x, nsteps);  // done: never hold a peer back
+      // after an abort, the copies that may still be in flight land before the CTA ends
+      if (*abort_flag)
+        for (int ks = max(0, loaded - kStages); ks < loaded; ++ks)
+          mbar_wait(&full[ks % kStages], (uint32_t)((ks / kStages) & 1), kWaitNs);
+    }
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f16(kTa, kN);
+      int issued = 0;
+      for (int ks = 0; ks < nsteps; ++ks) {
+        const int st = ks % kStages, p = ks >> 1, set = p & 1;
+        if (*abort_flag) break;
+        if ((ks & 1) == 0 && p >= 2 &&
+            !mbar_wait(&sempty[set], (uint32_t)(((p >> 1) - 1) & 1), kWaitNs)) {  // set drained
+          *abort_flag = 1;
+          break;
+        }
+        if (!mbar_wait(&full[st], (uint32_t)((ks / kStages) & 1), kWaitNs)) {
+          *abort_flag = 1;
+          break;
+        }
         tc_fence_after();
-        const uint32_t xjh = smem_addr(tile(st, 0)), xjl = smem_addr(tile(st, 1));
-        const uint32_t yjh = smem_addr(tile(st, 2)), yjl = smem_addr(tile(st, 3));
-        const uint32_t xih = smem_addr(tile(st, 4)), xil = smem_addr(tile(st, 5));
-        const uint32_t dS = tmem + kSetCols * set, dH = dS + kTi;
+        const uint32_t a = smem_addr(a_tile(st)), b = smem_addr(b_tile(st));
+        const uint32_t d = tmem + kSetCols * set;
         const bool fresh = (ks & 1) == 0;
+        // slice kk (16 samples = 32 bytes): high halves at +32 kk, low halves at +64 + 32 kk
 #pragma unroll
         for (int kk = 0; kk < kK / 16; ++kk) {
-          const uint32_t ko = kk * 32;  // 16 halves = 32 bytes along the swizzled row
-          const uint32_t a0 = (fresh && kk == 0) ? 0u : 1u;
-          mma_f16(dS, smem_desc_k64(xjh + ko), smem_desc_k64(xil + ko), idesc, a0);
-          mma_f16(dS, smem_desc_k64(xjl + ko), smem_desc_k64(xih + ko), idesc, 1u);
-          mma_f16(dH, smem_desc_k64(yjh + ko), smem_desc_k64(xil + ko), idesc, a0);
-          mma_f16(dH, smem_desc_k64(yjl + ko), smem_desc_k64(xih + ko), idesc, 1u);
+          const uint32_t hi = 32 * kk, lo = 64 + 32 * kk;
+          mma_f16(d, smem_desc_k128(a + hi), smem_desc_k128(b + lo), idesc, (fresh && kk == 0) ? 0u : 1u);
+          mma_f16(d, smem_desc_k128(a + lo), smem_desc_k128(b + hi), idesc, 1u);
         }
 #pragma unroll
         for (int kk = 0; kk < kK / 16; ++kk) {
-          const uint32_t ko = kk * 32;
-          mma_f16(dS, smem_desc_k64(xjh + ko), smem_desc_k64(xih + ko), idesc, 1u);
-          mma_f16(dH, smem_desc_k64(yjh + ko), smem_desc_k64(xih + ko), idesc, 1u);
+          const uint32_t hi = 32 * kk;
+          mma_f16(d, smem_desc_k128(a + hi), smem_desc_k128(b + hi), idesc, 1u);
         }
-        mma_commit(&done[st]);
+        mma_commit(&empty[st]);
+        if ((ks & 1) || ks == nsteps - 1) mma_commit(&sfull[set]);
+        issued = ks + 1;
       }
-      ok = arrived;
-    }
-    ok = __syncthreads_and(ok) != 0;
-    if (!ok) break;
-    issued = ks + 1;
-    if (ks >= 1) {
-      // MMAs of step ks-1 done: refill its stage with step ks+3; after the second step of a
-      // pair, drain the pair's accumulators
-      const int pk = ks - 1, pst = pk % kStages;
-      ok = __syncthreads_and(mbar_wait(&done[pst], (uint32_t)((pk / kStages) & 1), kWaitNs)) != 0;
-      if (!ok) break;
-      if (tid == 0 && pk + kStages < nsteps) load(pk + kStages);
-      if (pk & 1) {
-        tc_fence_after();
-        drain(tmem, (pk >> 1) & 1, warp, acc);
-        drained = pk + 1;
-        tc_fence_before();
+      // every MMA issued has completed before the tensor memory is released
+      if (issued > 0) {
+        mma_commit(mdone);
+        if (!mbar_wait(mdone, 0u, kWaitNs)) *abort_flag = 1;
       }
     }
-  }
-  // the steps not yet drained (the last pair): wait for the last MMAs and drain; on a
-  // timeout, still give the copies and MMAs in flight a bounded wait before the shared and
-  // tensor memory are released
-  if (issued > 0 && drained < issued) {
-    const int ks = issued - 1;
-    const bool d = mbar_wait(&done[ks % kStages], (uint32_t)((ks / kStages) & 1), kWaitNs);
-    ok = __syncthreads_and(ok && d) != 0;
-    if (ok) {
+    __syncwarp();
+  } else {
+#pragma unroll
+    for (int c = 0; c < kTb; ++c) acc[c] = 0.0f;
+    const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (warp < 4 ? 0u : (uint32_t)kTb);
+    for (int p = 0; p < npairs; ++p) {
+      const int set = p & 1;
+      int ok = 0;
+      if (lane == 0) ok = !*abort_flag && mbar_wait(&sfull[set], (uint32_t)((p >> 1) & 1), kWaitNs);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) *abort_flag = 1;
+        break;
+      }
       tc_fence_after();
-      drain(tmem, (ks >> 1) & 1, warp, acc);
-      drained = issued;
+      drain(base + kSetCols * set, acc);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sempty[set]);
     }
   }
-  if (!ok && tid == 0)
-    for (int ks = issued; ks < loaded; ++ks) mbar_wait(&full[ks % kStages], (uint32_t)((ks / kStages) & 1), kWaitNs);
-  if (ok && drained == nsteps) {
-    const int row = j0 + 32 * (warp & 3) + (tid & 31);
-    double* out = part + ((size_t)blockIdx.y * 2 + (warp < 4 ? 0 : 1)) * Pj * Pi + (size_t)row * Pi + i0;
-#pragma unroll
-    for (int c = 0; c < kTi; ++c) out[c] = (double)acc[c];
-  } else if (tid == 0) {
-    atomicExch(err, 1);
-  }
-  tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 512);
+  const bool good = *abort_flag == 0;  // every role has finished: the flag is final
+  if (warp < 8 && good) {
+    const int row = i0 + 32 * (warp & 3) + lane;
+    double* out = part + ((size_t)blockIdx.y * 2 + (warp < 4 ? 0 : 1)) * Pa * Pb + (size_t)row * Pb + j0;
+#pragma unroll
+    for (int c = 0; c < kTb; ++c) out[c] = (double)acc[c];
+  }
+  if (threadIdx.x == 0 && !good) atomicExch(err, 1);
+  tc_fence_after();
+  if (warp == kMmaWarp) tmem_dealloc(tmem, 512);
 }
 
-// (4) thread (j, i): S[i][j] and H[i][j] from the chunk partials [chunk][2][Pj][Pi] (stored as
-// [j][i]), unscaled; gL, gR, E0 from the column sums.
-__global__ void lin_reduce_kernel(int P, int Pj, int Pi, int Pr, int nchunk, const double* __restrict__ part,
+// (4) thread (i, j): S[i][j] and H[i][j] from the chunk partials [chunk][2][Pa][Pb], unscaled;
+// gL, gR, E0 from the column sums.
+__global__ void lin_reduce_kernel(int P, int Pa, int Pb, int Pr, int nchunk, const double* __restrict__ part,
                                   const double* __restrict__ acc, const double* __restrict__ sxe,
                                   const float* __restrict__ scl, double* E0,
                                   double* gL, double* gR, double* S, double* H, const int* __restrict__ err) {
@@ -433,12 +516,12 @@ __global__ void lin_reduce_kernel(int P, int Pj, int Pi, int Pr, int nchunk, con
   const double isw = *err ? __longlong_as_double(0x7ff8000000000000ll) : 1.0 / acc[0];
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q < (long long)P * P) {
-    const int j = (int)(q / P), i = (int)(q % P);
-    const size_t o = (size_t)j * Pi + i;
+    const int i = (int)(q / P), j = (int)(q % P);
+    const size_t o = (size_t)i * Pb + j, plane = (size_t)Pa * Pb;
     double s = 0.0, h = 0.0;
     for (int c = 0; c < nchunk; ++c) {
-      s += part[(size_t)c * 2 * Pj * Pi + o];
-      h += part[(size_t)c * 2 * Pj * Pi + (size_t)Pj * Pi + o];
+      s += part[(size_t)c * 2 * plane + o];
+      h += part[(size_t)c * 2 * plane + plane + o];
     }
     const double sxi = scl[i], sxj = scl[j], syj = scl[Pr + j];
     S[(size_t)i * P + j] = s / (sxi * sxj) * isw;
@@ -454,28 +537,43 @@ __global__ void lin_reduce_kernel(int P, int Pj, int Pi, int Pr, int nchunk, con
 
 }  // namespace
 
-long long lin_chunk(long long M) {
-  // enough chunks to fill the machine with the tile grid, at least 2048 samples per chunk
-  long long c = 32768;
-  while (c > 2048 && (M + c - 1) / c < 32) c /= 2;
-  return c;
+int lin_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      n < 1)
+    return 1;
+  return n;
+}
+
+LinGrid lin_grid(int P, long long M, int nsm) {
+  // one CTA per SM (the stages take most of the shared memory) and one wave: as many chunks as
+  // the SMs hold for every tile at once (the CTAs of a chunk then run side by side and share
+  // its tiles through L2), at least kMinChunk samples per chunk
+  constexpr long long kMinChunk = 2048;
+  const int ntile = (rows_a(P) / kTa) * (rows_b(P) / kTb);
+  const long long maxc = std::max<long long>(1, (M + kMinChunk - 1) / kMinChunk);
+  const long long n = std::min(maxc, std::max<long long>(1, (long long)std::max(nsm, 1) / ntile));
+  LinGrid g;
+  g.chunk = std::max<long long>(kK, ((M + n - 1) / n + kK - 1) / kK * kK);
+  g.nchunk = (int)((M + g.chunk - 1) / g.chunk);
+  return g;
 }
 
 namespace {
 struct LinWs {
-  double *part1, *acc, *part2, *sxe, *part;
+  double *part1, *acc, *part2, *sxe, *seg, *part;
   unsigned* mx;
   float *scl, *rw, *Ef;
-  __half *Xh, *Xl, *Yh, *Yl;
+  __half *XI, *YI;
   int* err;
+  int* prog;
   size_t bytes;
 };
-LinWs carve(void* ws, int P, long long M) {
-  const int L1 = 2 * P + 2, Pj = rows_j(P), Pi = rows_i(P), Pr = rows_t(P);
+LinWs carve(void* ws, int P, long long M, int nchunk) {
+  const int L1 = 2 * P + 2, Pa = rows_a(P), Pb = rows_b(P), Pr = rows_t(P);
   const long long nb1 = (M + kColBlock * kColTiles - 1) / (kColBlock * kColTiles),
                   nb2 = (M + 64 * kCenTiles - 1) / (64 * kCenTiles);
   const long long Mp = (M + 31) / 32 * 32;
-  const long long chunk = lin_chunk(M), nchunk = (M + chunk - 1) / chunk;
   unsigned char* p = static_cast<unsigned char*>(ws);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -488,32 +586,32 @@ LinWs carve(void* ws, int P, long long M) {
   w.acc = reinterpret_cast<double*>(take(sizeof(double) * (size_t)L1));
   w.part2 = reinterpret_cast<double*>(take(sizeof(double) * (size_t)nb2 * Pr));
   w.sxe = reinterpret_cast<double*>(take(sizeof(double) * (size_t)Pr));
+  w.seg = reinterpret_cast<double*>(take(sizeof(double) * (size_t)kSeg * std::max(L1, Pr)));
   w.mx = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * (2 + 2 * (size_t)P)));
   w.scl = reinterpret_cast<float*>(take(sizeof(float) * 2 * (size_t)Pr));
   w.rw = reinterpret_cast<float*>(take(sizeof(float) * (size_t)M));
   w.Ef = reinterpret_cast<float*>(take(sizeof(float) * (size_t)M));
-  w.Xh = reinterpret_cast<__half*>(take(sizeof(__half) * (size_t)Pr * Mp));
-  w.Xl = reinterpret_cast<__half*>(take(sizeof(__half) * (size_t)Pr * Mp));
-  w.Yh = reinterpret_cast<__half*>(take(sizeof(__half) * (size_t)Pr * Mp));
-  w.Yl = reinterpret_cast<__half*>(take(sizeof(__half) * (size_t)Pr * Mp));
-  w.part = reinterpret_cast<double*>(take(sizeof(double) * (size_t)nchunk * 2 * Pj * Pi));
+  w.XI = reinterpret_cast<__half*>(take(sizeof(__half) * (size_t)Pr * 2 * Mp));
+  w.YI = reinterpret_cast<__half*>(take(sizeof(__half) * (size_t)Pr * 2 * Mp));
+  w.part = reinterpret_cast<double*>(take(sizeof(double) * (size_t)nchunk * 2 * Pa * Pb));
   w.err = reinterpret_cast<int*>(take(sizeof(int)));
+  w.prog = reinterpret_cast<int*>(take(sizeof(int) * (size_t)nchunk * (rows_a(P) / kTa) * (rows_b(P) / kTb)));
   w.bytes = off;
   return w;
 }
 }  // namespace
 
-size_t lin_workspace_bytes(int P, long long M) { return carve(nullptr, P, M).bytes; }
+size_t lin_workspace_bytes(int P, long long M, int nsm) { return carve(nullptr, P, M, lin_grid(P, M, nsm).nchunk).bytes; }
 
-// Tensor map of a [rows][Mp] half array read as M samples per row in 32-sample x box_rows
-// boxes with the 64-byte swizzle (samples past M read as zero).  The encoder comes from the
-// driver through the runtime, so the library does not link the driver library itself.
+// Tensor map of a grouped [Mp / 32][Pr][64] half array read in boxes of box_rows rows of one
+// group (box_rows x 128 contiguous bytes) with the 128-byte swizzle; rows max(P, 128) and above
+// lie outside the map and read as zeros.  The encoder comes from the driver through the runtime,
+// so the library does not link the driver library itself.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-static cudaError_t encode_tile_map(CUtensorMap* map, const __half* base, int rows, long long M, long long Mp,
-                                   int box_rows) {
+static cudaError_t encode_tile_map(CUtensorMap* map, const __half* base, int P, int Pr, long long Mp, int box_rows) {
   static EncodeTiledFn encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -523,69 +621,68 @@ static cudaError_t encode_tile_map(CUtensorMap* map, const __half* base, int row
     if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorSymbolNotFound;
     encode = reinterpret_cast<EncodeTiledFn>(fn);
   }
-  const cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)Mp * sizeof(__half)};
-  const cuuint32_t box[2] = {(cuuint32_t)kK, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  static_assert(kK * 2 == 64, "the tile rows are 64 bytes (64-byte swizzle)");
-  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(base), dims, strides, box,
-                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * kK), (cuuint64_t)rows_m(P), (cuuint64_t)(Mp / kK)};
+  const cuuint64_t strides[2] = {(cuuint64_t)kRow, (cuuint64_t)kRow * Pr};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * kK), (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  static_assert(kRow == 128, "the tile rows are 128 bytes (128-byte swizzle)");
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<__half*>(base), dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <class Tin>
 static cudaError_t launch_lin_t(int P, long long M, const Tin* O, const Tin* dEL, const double* E, const double* w,
-                                void* ws, double* E0, double* gL, double* gR, double* S, double* H, cudaStream_t st,
-                                int* nlaunch) {
-  const int L1 = 2 * P + 2, Pj = rows_j(P), Pi = rows_i(P), Pr = rows_t(P);
+                                void* ws, size_t ws_bytes, int nsm, double* E0, double* gL, double* gR, double* S,
+                                double* H, cudaStream_t st, int* nlaunch) {
+  const int L1 = 2 * P + 2, Pa = rows_a(P), Pb = rows_b(P), Pr = rows_t(P);
   const long long Mp = (M + 31) / 32 * 32;
   const int nb2 = (int)((M + 64 * kCenTiles - 1) / (64 * kCenTiles));
-  const long long chunk = lin_chunk(M);
-  const int nchunk = (int)((M + chunk - 1) / chunk);
+  const LinGrid G = lin_grid(P, M, nsm);
   const int nb1 = (int)((M + kColBlock * kColTiles - 1) / (kColBlock * kColTiles));
-  const LinWs L = carve(ws, P, M);
+  const LinWs L = carve(ws, P, M, G.nchunk);
+  if (L.bytes > ws_bytes) return cudaErrorInvalidValue;  // workspace sized for another grid
   cudaError_t e = cudaMemsetAsync(L.mx, 0, sizeof(unsigned) * (2 + 2 * (size_t)P), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(L.err, 0, sizeof(int), st);
+  if (e == cudaSuccess)  // -1: not started
+    e = cudaMemsetAsync(L.prog, 0xff, sizeof(int) * (size_t)G.nchunk * (Pa / kTa) * (Pb / kTb), st);
   if (e != cudaSuccess) return e;
   lin_colsum_kernel<Tin><<<nb1, kColBlock, 0, st>>>(P, M, O, dEL, E, w, L.part1, L.mx);
-  lin_colsum_reduce<<<(L1 + 255) / 256, 256, 0, st>>>(L1, nb1, L.part1, L.acc);
+  lin_seg_reduce<<<dim3((L1 + 31) / 32, kSeg), 256, 0, st>>>(L1, nb1, L.part1, L.seg);
+  lin_final_reduce<<<(L1 + 255) / 256, 256, 0, st>>>(L1, L.seg, L.acc);
   lin_scale_kernel<<<(Pr + 255) / 256, 256, 0, st>>>(P, Pr, L.acc, L.mx, L.scl);
   lin_sample_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, E, w, L.rw, L.Ef);
   lin_center_kernel<Tin><<<dim3((unsigned)nb2, Pr / 64), 256, 0, st>>>(
-      P, M, Mp, O, dEL, E, w, L.rw, L.Ef, L.acc, L.scl, Pr, L.Xh, L.Xl, L.Yh, L.Yl, L.part2);
-  lin_colsum_reduce<<<(Pr + 255) / 256, 256, 0, st>>>(Pr, nb2, L.part2, L.sxe);
-  CUtensorMap mXh, mXl, mYh, mYl;
-  e = encode_tile_map(&mXh, L.Xh, Pr, M, Mp, kTj);
-  if (e == cudaSuccess) e = encode_tile_map(&mXl, L.Xl, Pr, M, Mp, kTj);
-  if (e == cudaSuccess) e = encode_tile_map(&mYh, L.Yh, Pr, M, Mp, kTj);
-  if (e == cudaSuccess) e = encode_tile_map(&mYl, L.Yl, Pr, M, Mp, kTj);
-  if (e != cudaSuccess) return e;
-  // the i tiles are 112 rows: maps of the same arrays with 112-row boxes
-  CUtensorMap mXhi, mXli;
-  e = encode_tile_map(&mXhi, L.Xh, Pr, M, Mp, kTi);
-  if (e == cudaSuccess) e = encode_tile_map(&mXli, L.Xl, Pr, M, Mp, kTi);
+      P, M, Mp, O, dEL, E, w, L.rw, L.Ef, L.acc, L.scl, Pr, L.XI, L.YI, L.part2);
+  lin_seg_reduce<<<dim3((Pr + 31) / 32, kSeg), 256, 0, st>>>(Pr, nb2, L.part2, L.seg);
+  lin_final_reduce<<<(Pr + 255) / 256, 256, 0, st>>>(Pr, L.seg, L.sxe);
+  // A tiles: 128 rows of X; B tiles: 112 rows of X and of Y
+  CUtensorMap mA, mBX, mBY;
+  e = encode_tile_map(&mA, L.XI, P, Pr, Mp, kTa);
+  if (e == cudaSuccess) e = encode_tile_map(&mBX, L.XI, P, Pr, Mp, kTb);
+  if (e == cudaSuccess) e = encode_tile_map(&mBY, L.YI, P, Pr, Mp, kTb);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(lin_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   if (e != cudaSuccess) return e;
-  const int ntile = (Pj / kTj) * (Pi / kTi);
-  lin_tc_kernel<<<dim3(ntile, nchunk), kTcThreads, kTcSmem, st>>>(mXh, mXl, mYh, mYl, mXhi, mXli, Pj, Pi, M, chunk,
-                                                                   L.part, L.err);
+  const int ntile = (Pa / kTa) * (Pb / kTb);
+  lin_tc_kernel<<<dim3(ntile, G.nchunk), kTcThreads, kTcSmem, st>>>(mA, mBX, mBY, Pa, Pb, M, G.chunk, L.part,
+                                                                     L.prog, L.err);
   const long long nq = std::max<long long>((long long)P * P, 1);
-  lin_reduce_kernel<<<(int)((nq + 255) / 256), 256, 0, st>>>(P, Pj, Pi, Pr, nchunk, L.part, L.acc, L.sxe, L.scl, E0,
-                                                              gL, gR, S, H, L.err);
-  *nlaunch = 8;
+  lin_reduce_kernel<<<(int)((nq + 255) / 256), 256, 0, st>>>(P, Pa, Pb, Pr, G.nchunk, L.part, L.acc, L.sxe, L.scl,
+                                                              E0, gL, gR, S, H, L.err);
+  *nlaunch = 11;
   return cudaGetLastError();
 }
 
 cudaError_t launch_lin(int in_float, int P, long long M, const void* O, const void* dEL, const double* E,
-                       const double* w, void* ws, double* E0, double* gL, double* gR, double* S, double* H,
-                       cudaStream_t st, int* nlaunch) {
+                       const double* w, void* ws, size_t ws_bytes, int nsm, double* E0, double* gL, double* gR,
+                       double* S, double* H, cudaStream_t st, int* nlaunch) {
   if (in_float)
-    return launch_lin_t<float>(P, M, static_cast<const float*>(O), static_cast<const float*>(dEL), E, w, ws, E0, gL,
-                               gR, S, H, st, nlaunch);
-  return launch_lin_t<double>(P, M, static_cast<const double*>(O), static_cast<const double*>(dEL), E, w, ws, E0, gL,
-                              gR, S, H, st, nlaunch);
+    return launch_lin_t<float>(P, M, static_cast<const float*>(O), static_cast<const float*>(dEL), E, w, ws, ws_bytes,
+                               nsm, E0, gL, gR, S, H, st, nlaunch);
+  return launch_lin_t<double>(P, M, static_cast<const double*>(O), static_cast<const double*>(dEL), E, w, ws,
+                              ws_bytes, nsm, E0, gL, gR, S, H, st, nlaunch);
 }
 
 }  // namespace vbq

@@ -62,7 +62,9 @@ extern "C" int vbqmc_accumulate_lin_matrices_noalloc(int precision, int P, int64
   // Every sample takes at least 8 bytes and the P x P partial tiles at least 16 P^2, so these
   // bounds only keep the size arithmetic below far from overflow.
   const size_t cap = (size_t)VBQMC_NOALLOC_SCRATCH_BYTES;
-  const size_t need = (P <= 2048 && (uint64_t)M <= cap / 8) ? vbq::lin_workspace_bytes(P, (long long)M) : cap + 1;
+  const int nsm = vbq::lin_sms();
+  const size_t need =
+      (P <= 2048 && (uint64_t)M <= cap / 8) ? vbq::lin_workspace_bytes(P, (long long)M, nsm) : cap + 1;
   if (need > cap)
     return vbq::set_error(VBQMC_ERR_CAPACITY,
                           "allocation-free linear-method accumulation: P=" + std::to_string(P) + ", M=" +
@@ -78,8 +80,8 @@ extern "C" int vbqmc_accumulate_lin_matrices_noalloc(int precision, int P, int64
   e = scratch_address(dev, &ws);
   if (e != cudaSuccess) return vbq::set_cuda_error((int)e, "cudaGetSymbolAddress(linear-method scratch)");
   int nl = 0;
-  e = vbq::launch_lin(precision == VBQMC_MIXED, P, (long long)M, O, dEL, eloc, weights, ws, E0, gL, gR, S, H,
-                      (cudaStream_t)stream, &nl);
+  e = vbq::launch_lin(precision == VBQMC_MIXED, P, (long long)M, O, dEL, eloc, weights, ws, cap, nsm, E0, gL, gR, S,
+                      H, (cudaStream_t)stream, &nl);
   if (e != cudaSuccess) return vbq::set_cuda_error((int)e, "linear-method kernels");
   return VBQMC_OK;
 }
