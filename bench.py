@@ -122,6 +122,19 @@ def measure_peaks(vbqmc, device):
             "sms": pk["sms"], "sm_mhz": clocks.get("sm_mhz"), "reasons": clocks.get("reasons", [])}
 
 
+def file_peaks():
+    """HBM copy bandwidth (GB/s) and BF16 GEMM rate (TFLOP/s) measured on this machine's GPUs by the
+    environment (MEASURED_PEAKS.json beside this script); the recipe's earlier GB300 figures where
+    the file is missing."""
+    import json
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
 def reblocked_error(x):
     """Standard error of the mean of a correlated series by blocking (Flyvbjerg-Petersen): pairs
     of neighbours are averaged level after level; the error is the largest estimate over the
@@ -416,7 +429,7 @@ def run_ours(args, ws, rank, local):
     dmc = dmc_timing(ctx, vbqmc, R, el, args.dmc_steps) if args.dmc_steps > 0 else None
     batched = batched_timing(vbqmc, dev, args.steps) if args.batch_steps > 0 else None
     dmc48 = dmc48_timing(vbqmc, dev, args.dmc48_steps, args.dmc48_walkers) if args.dmc48_steps > 0 else None
-    lin = lin_method_timing(ctx, vbqmc, dev, args.steps, args.lin_samples) if not args.no_lin else None
+    lin = lin_method_timing(ctx, vbqmc, dev, args.steps, file_peaks(), args.lin_samples) if not args.no_lin else None
     barrier(ws)
     if rank != 0:
         return
@@ -743,10 +756,13 @@ def batched_timing(vbqmc, dev, steps):
                               for k in vbqmc.Batch.KINDS}}
 
 
-def lin_method_timing(ctx, vbqmc, dev, steps, M=1 << 20):
+def lin_method_timing(ctx, vbqmc, dev, steps, pk, M=1 << 20):
     """Linear-method estimators for M (default 2^20) samples x 400 parameters (mixed form,
     float inputs): time per accumulation with CUDA events, inputs resident in HBM (larger than
-    L2)."""
+    L2); then one timed call split into its four phases (column sums, centring, tensor-core
+    products, reduction) with the roofline of each: HBM bytes for the streaming phases, tensor
+    flops for the products (algorithmic: 2 x 2 M P^2; issued: three half-precision products per
+    pair over the padded 128 x 112 tiles)."""
     import torch
     P = 400
     g = torch.Generator(device=dev)
@@ -764,9 +780,30 @@ def lin_method_timing(ctx, vbqmc, dev, steps, M=1 << 20):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / n
+    ctx.set_kernel_timing(True)
+    ctx.accumulate_lin_matrices(vbqmc.MIXED, O, dE, E)
+    ph = list(ctx.kernel_times().values())
+    ctx.set_kernel_timing(False)
     flops = 2 * 2.0 * M * P * P  # S and H products
-    return {"samples": M, "params": P, "ms": ms, "tflops_fp32_products": flops / (ms * 1e-3) / 1e12,
-            "input_bytes": 2 * M * P * 4 + M * 8}
+    Pa, Pb, Pr = -(-P // 128) * 128, -(-P // 112) * 112, max(-(-P // 64) * 64, 128)
+    mma = 3 * 2.0 * M * Pa * (2 * Pb)
+    in_bytes = 2 * M * P * 4
+    xy_bytes = 2 * Pr * M * 2 * 2  # X and Y, high and low halves
+    hbm, bf16 = pk["hbm_gbs"], pk["bf16_tflops"]
+    return {"samples": M, "params": P, "ms": ms, "algorithmic_tflops": flops / (ms * 1e-3) / 1e12,
+            "input_bytes": in_bytes + M * 8,
+            "phases_ms": {"column_sums": ph[0], "centring": ph[1], "tensor_products": ph[2], "reduction": ph[3]},
+            "roofline": {
+                "column_sums": {"bound": "hbm", "achieved_gbs": in_bytes / (ph[0] * 1e-3) / 1e9,
+                                "frac": in_bytes / (ph[0] * 1e-3) / 1e9 / hbm},
+                "centring": {"bound": "hbm", "achieved_gbs": (in_bytes + xy_bytes) / (ph[1] * 1e-3) / 1e9,
+                             "frac": (in_bytes + xy_bytes) / (ph[1] * 1e-3) / 1e9 / hbm},
+                "tensor_products": {"bound": "tensor", "issued_tflops": mma / (ph[2] * 1e-3) / 1e12,
+                                    "frac_issued": mma / (ph[2] * 1e-3) / 1e12 / bf16,
+                                    "algorithmic_tflops": flops / (ph[2] * 1e-3) / 1e12,
+                                    "frac_algorithmic": flops / (ph[2] * 1e-3) / 1e12 / bf16,
+                                    "peak": bf16, "peak_note": "%s BF16 burst (f16 runs at the BF16 rate)" % pk["source"]},
+                "hbm_peak_gbs": hbm}}
 
 
 def main():

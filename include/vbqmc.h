@@ -406,11 +406,13 @@ int vbqmc_batch_info(vbqmc_batch* batch, int* out);
  * vbqmc_vmc_steps) records CUDA events on its stream around each of its kernels; the
  * evaluation runs as four kernels in this order: Jastrow factor, orbitals, determinants
  * (with E_L, structure and excitation derivatives), Jastrow-parameter derivatives (skipped
- * when no derivatives are asked for: time 0). */
+ * when no derivatives are asked for: time 0).  vbqmc_accumulate_lin_matrices records the same
+ * four intervals around its phases: column sums (with the scales), centring and splitting,
+ * tensor-core products, final reduction. */
 int vbqmc_set_kernel_timing(vbqmc_ctx* ctx, int on);
-/* Durations in ms of the four evaluation kernels of the last timed evaluation, in the order
- * above: ms[0..min(max, 4) - 1]; *n = 4.  Waits for that evaluation to finish.  Error if no
- * timed evaluation has been recorded since timing was switched on. */
+/* Durations in ms of the four intervals of the last timed call (evaluation or linear-method
+ * accumulation), in the order above: ms[0..min(max, 4) - 1]; *n = 4.  Waits for that call to
+ * finish.  Error if no timed call has been recorded since timing was switched on. */
 int vbqmc_kernel_times(vbqmc_ctx* ctx, double* ms, int max, int* n);
 
 /* Launch shape of the walker kernels for a loaded system: out[0..3] = walkers (warps) per

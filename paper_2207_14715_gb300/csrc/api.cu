@@ -305,13 +305,23 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
     d.b1_par_ds[0] = sc[4]; d.b1_par_ds[1] = sc[5];
   }
   // determinants through the reference-determinant tables when the per-determinant inverses of
-  // one walker do not fit in shared memory
+  // one walker do not fit in shared memory, or when they hold so much of it that few walkers
+  // share an SM: a sweep region above 48 KB, or above 32 KB with 16 or more unique
+  // determinants of a spin (the measured crossover on molecules of 2-32 electrons; systems with
+  // orbital-excitation parameters keep the per-determinant form, whose derivatives they need)
   d.msd = 0;
   {
     vbq::DetLayout probe;
     if (h.tab_ok && vbq::make_det_layout(d, 8, ctx->max_smem, probe) != VBQMC_OK) d.msd = 1;
   }
   make_layouts(ctx, ls);
+  if (!d.msd && h.tab_ok && d.n_kappa == 0 && ls.lay_rc_sweep[VBQMC_MIXED] == VBQMC_OK) {
+    const int bytes = ls.lay_sweep[VBQMC_MIXED].warp_bytes, U = std::max(d.U[0], d.U[1]);
+    if (bytes > 48 * 1024 || (bytes > 32 * 1024 && U >= 16)) {
+      d.msd = 1;
+      make_layouts(ctx, ls);
+    }
+  }
   ls.loaded = true;
   free_system(ctx->sys[sys_id]);
   ctx->sys[sys_id] = ls;
@@ -775,7 +785,8 @@ int vbqmc_accumulate_lin_matrices(vbqmc_ctx* ctx, int precision, int P, int64_t 
   }
   int nl = 0;
   cudaError_t e = vbq::launch_lin(precision == VBQMC_MIXED, P, (long long)M, O, dEL, eloc, weights, ctx->work,
-                                  ctx->work_bytes, nsm, E0, gL, gR, S, H, (cudaStream_t)stream, &nl);
+                                  ctx->work_bytes, nsm, E0, gL, gR, S, H, (cudaStream_t)stream, &nl,
+                                  timing_events(ctx));
   if (e != cudaSuccess) return cuda_fail(e, "linear-method kernels");
   ctx->last_launches = nl;
   return VBQMC_OK;

@@ -41,6 +41,7 @@ struct BatchSys {
   double* JS;
   double* OD;
   double* VG;
+  int cw[3];  // one-launch step: walkers run at once in the sweep, Jastrow and determinant phases
 };
 
 // Launchers: 'warps' warps per block, 'smem' dynamic shared memory, 'grid' blocks, each
@@ -63,8 +64,10 @@ cudaError_t launch_det_batch(const BatchSys* sys, const BatchItem* items, int ni
 // The whole step in one persistent launch (batch_fused.cu): blocks take items (system, tile of
 // walkers) from the device counter *queue (zero before the launch) and run the sweep (if sweep),
 // the evaluation kernels' bodies (if eval) and the Jastrow-parameter derivatives (if derivs) on
-// each tile in turn.  Every item's count fits the block's warps and, for every phase, the
-// shared memory smem.
+// each tile in turn.  Every item's count fits the block's warps; in the per-walker phases of
+// system s, warps 0 .. s.cw[phase] - 1 take the tile's walkers in turn (cw[phase] regions of
+// that phase fit the shared memory smem), and the orbital phase spreads the tile's (walker,
+// electron) pairs over all warps.
 cudaError_t launch_batch_fused(int is_float, const BatchSys* sys, const BatchItem* items, int nitems,
                                const BatchCall* call, int* queue, bool sweep, bool eval, bool derivs, int grid,
                                int warps, int smem, cudaStream_t st);

@@ -146,26 +146,28 @@ int build_plan(vbqmc_batch* b, int kind) {
   return VBQMC_OK;
 }
 
-// Work items and shape of the one-launch step: with p.warps warps per block (p.cap > 0 caps the
-// walkers per tile), system s takes tiles of c_s walkers, c_s = the most that fit the warps and,
-// for the phase with the largest per-walker region, the opt-in shared memory; the orbital phase
-// uses every warp of the block.
+// Work items and shape of the one-launch step: with p.warps warps per block, tiles of T = p.warps
+// walkers (p.cap > 0: at most p.cap); one block per SM holds the opt-in shared memory, and in each
+// per-walker phase of system s as many walkers run at once as that phase's per-walker regions
+// fit it (cw, at most T); the orbital phase gives every warp its own region.
 int build_fused_plan(vbqmc_batch* b) {
   KernelPlan& p = b->plan[kFused];
   const bool f = b->precision == VBQMC_MIXED;
   const int smax = b->ctx->max_smem;
   const int warps = std::max(1, std::min(p.warps, 16));
-  int smem = 0;
+  const int T = p.cap > 0 ? std::max(1, std::min(warps, p.cap)) : warps;
+  const int smem = smax - 128;  // the kernel's static shared memory (the item index) takes the rest
   std::vector<int> per(b->n);
   for (int k = 0; k < b->n; ++k) {
-    const BatchSys& s = b->sys[k];
-    const int mb = std::max(std::max(s.sweep.warp_bytes, s.lay.jas.warp_bytes),
-                            s.dev.msd ? s.lay.tab.warp_bytes : s.lay.det.warp_bytes);
-    int c = std::max(1, std::min(warps, smax / std::max(mb, 1)));
-    if (p.cap > 0) c = std::min(c, p.cap);
-    if (warps * s.lay.orb.warp_bytes > smax) return fail(VBQMC_ERR_CAPACITY, "orbital tables of a batched system");
-    per[k] = c;
-    smem = std::max(smem, std::max(c * mb, warps * s.lay.orb.warp_bytes));
+    BatchSys& s = b->sys[k];
+    const int bytes[3] = {s.sweep.warp_bytes, s.lay.jas.warp_bytes,
+                          s.dev.msd ? s.lay.tab.warp_bytes : s.lay.det.warp_bytes};
+    for (int q = 0; q < 3; ++q) {
+      if (bytes[q] > smem) return fail(VBQMC_ERR_CAPACITY, "per-walker region of a batched system");
+      s.cw[q] = std::max(1, std::min(T, smem / std::max(bytes[q], 1)));
+    }
+    if (warps * s.lay.orb.warp_bytes > smem) return fail(VBQMC_ERR_CAPACITY, "orbital tables of a batched system");
+    per[k] = T;
   }
   struct It {
     BatchItem item;
@@ -513,8 +515,8 @@ int vbqmc_batch_tune(vbqmc_batch* b, double* const* R, double* const* logpsi, do
     KernelPlan& p = b->plan[kFused];
     int bw = p.warps, bc = p.cap, bp = p.persist;
     for (int warps : {8, 12, 16})
-      for (int cap : {0, 4})
-        for (int persist : {1, 2}) {
+      for (int cap : {0})
+        for (int persist : {1}) {
           if (rc != VBQMC_OK || e != cudaSuccess) break;
           p.warps = warps;
           p.cap = cap;

@@ -20,7 +20,7 @@ namespace vbq {
 namespace {
 
 // MAXT: the block size the registers are allocated for (256: up to 255 registers per thread,
-// 512: 128).
+// 384: 168, 512: 128).
 template <class Tb, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) batch_fused_kernel(const BatchSys* __restrict__ sys,
                                                           const BatchItem* __restrict__ items, int nitems,
@@ -37,23 +37,27 @@ __global__ void __launch_bounds__(MAXT, 1) batch_fused_kernel(const BatchSys* __
     if (it >= nitems) break;
     const BatchItem item = items[it];
     const BatchSys& b = sys[item.sys];
-    const bool act = wl < item.count;
-    const int w = item.first + wl;
+    // per-walker phases: warp wl < c takes walkers wl, wl + c, ... of the tile
+    const int cs = b.cw[0], cj = b.cw[1], cd = b.cw[2];
     // systems on reference-determinant tables (many determinants per structure) carry the
     // reference inverse and tables through their moves and keep no walker state
-    if (sweep && act) {
-      if (b.dev.msd)
-        sweep_body<Tb, true>(b.dev, b.sweep, w, smem + wl * b.sweep.warp_bytes, b.R, call->nsweeps, call->refresh,
-                             nullptr, 0, call->step, call->seed, call->step0, b.tag, 0u, b.nacc);
-      else
-        sweep_body<Tb, false>(b.dev, b.sweep, w, smem + wl * b.sweep.warp_bytes, b.R, call->nsweeps, call->refresh,
-                              b.state, call->state_valid, call->step, call->seed, call->step0, b.tag, 0u, b.nacc);
-    }
+    if (sweep && wl < cs)
+      for (int r = wl; r < item.count; r += cs) {
+        const int w = item.first + r;
+        if (b.dev.msd)
+          sweep_body<Tb, true>(b.dev, b.sweep, w, smem + wl * b.sweep.warp_bytes, b.R, call->nsweeps, call->refresh,
+                               nullptr, 0, call->step, call->seed, call->step0, b.tag, 0u, b.nacc);
+        else
+          sweep_body<Tb, false>(b.dev, b.sweep, w, smem + wl * b.sweep.warp_bytes, b.R, call->nsweeps,
+                                call->refresh, b.state, call->state_valid, call->step, call->seed, call->step0, b.tag,
+                                0u, b.nacc);
+      }
     if (!eval) continue;
     __syncthreads();
-    if (act)
-      jastrow_body<Tb>(b.dev, b.lay.jas, w, smem + wl * b.lay.jas.warp_bytes, b.R, static_cast<Tb*>(b.JG),
-                       static_cast<Tb*>(b.JL), b.JS);
+    if (wl < cj)
+      for (int r = wl; r < item.count; r += cj)
+        jastrow_body<Tb>(b.dev, b.lay.jas, item.first + r, smem + wl * b.lay.jas.warp_bytes, b.R,
+                         static_cast<Tb*>(b.JG), static_cast<Tb*>(b.JL), b.JS);
     __syncthreads();
     const int npair = item.count * b.dev.N;
     for (int p = wl; p < npair; p += nw)
@@ -61,23 +65,26 @@ __global__ void __launch_bounds__(MAXT, 1) batch_fused_kernel(const BatchSys* __
                        static_cast<Tb*>(b.OB), b.OD);
     __syncthreads();
     const bool d = derivs && b.O && b.dev.P > 0;
-    if (act) {
-      if (b.dev.msd)
-        dettab_body<Tb>(b.dev, b.lay.tab, w, smem + wl * b.lay.tab.warp_bytes, static_cast<const Tb*>(b.JG),
-                        static_cast<const Tb*>(b.JL), b.JS, static_cast<const Tb*>(b.OB), b.OD, b.logpsi, b.sign,
-                        b.eloc, b.VG, nullptr, d ? static_cast<Tb*>(b.O) : nullptr,
-                        d ? static_cast<Tb*>(b.dEL) : nullptr);
-      else
-        det_body<Tb>(b.dev, b.lay.det, w, smem + wl * b.lay.det.warp_bytes, static_cast<const Tb*>(b.JG),
-                     static_cast<const Tb*>(b.JL), b.JS, static_cast<const Tb*>(b.OB), b.OD, b.logpsi, b.sign, b.eloc,
-                     b.VG, nullptr, d ? static_cast<Tb*>(b.O) : nullptr, d ? static_cast<Tb*>(b.dEL) : nullptr,
-                     b.state, nullptr, nullptr);
-    }
+    if (wl < cd)
+      for (int r = wl; r < item.count; r += cd) {
+        const int w = item.first + r;
+        if (b.dev.msd)
+          dettab_body<Tb>(b.dev, b.lay.tab, w, smem + wl * b.lay.tab.warp_bytes, static_cast<const Tb*>(b.JG),
+                          static_cast<const Tb*>(b.JL), b.JS, static_cast<const Tb*>(b.OB), b.OD, b.logpsi, b.sign,
+                          b.eloc, b.VG, nullptr, d ? static_cast<Tb*>(b.O) : nullptr,
+                          d ? static_cast<Tb*>(b.dEL) : nullptr);
+        else
+          det_body<Tb>(b.dev, b.lay.det, w, smem + wl * b.lay.det.warp_bytes, static_cast<const Tb*>(b.JG),
+                       static_cast<const Tb*>(b.JL), b.JS, static_cast<const Tb*>(b.OB), b.OD, b.logpsi, b.sign,
+                       b.eloc, b.VG, nullptr, d ? static_cast<Tb*>(b.O) : nullptr,
+                       d ? static_cast<Tb*>(b.dEL) : nullptr, b.state, nullptr, nullptr);
+      }
     if (d && b.dev.jas_param) {
       __syncthreads();
-      if (act)
-        jastrow_deriv_body<Tb>(b.dev, b.lay.jas, w, smem + wl * b.lay.jas.warp_bytes, b.R, b.VG,
-                               static_cast<Tb*>(b.O), static_cast<Tb*>(b.dEL));
+      if (wl < cj)
+        for (int r = wl; r < item.count; r += cj)
+          jastrow_deriv_body<Tb>(b.dev, b.lay.jas, item.first + r, smem + wl * b.lay.jas.warp_bytes, b.R, b.VG,
+                                 static_cast<Tb*>(b.O), static_cast<Tb*>(b.dEL));
     }
   }
 }
@@ -87,29 +94,29 @@ __global__ void __launch_bounds__(MAXT, 1) batch_fused_kernel(const BatchSys* __
 cudaError_t launch_batch_fused(int is_float, const BatchSys* sys, const BatchItem* items, int nitems,
                                const BatchCall* call, int* queue, bool sweep, bool eval, bool derivs, int grid,
                                int warps, int smem, cudaStream_t st) {
+#define VBQ_FUSED(T, MT) \
+  batch_fused_kernel<T, MT><<<grid, 32 * warps, smem, st>>>(sys, items, nitems, call, queue, sweep, eval, derivs)
   if (warps <= 8) {
-    if (is_float)
-      batch_fused_kernel<float, 256><<<grid, 32 * warps, smem, st>>>(sys, items, nitems, call, queue, sweep, eval,
-                                                                    derivs);
-    else
-      batch_fused_kernel<double, 256><<<grid, 32 * warps, smem, st>>>(sys, items, nitems, call, queue, sweep, eval,
-                                                                     derivs);
+    if (is_float) VBQ_FUSED(float, 256);
+    else VBQ_FUSED(double, 256);
+  } else if (warps <= 12) {
+    if (is_float) VBQ_FUSED(float, 384);
+    else VBQ_FUSED(double, 384);
   } else {
-    if (is_float)
-      batch_fused_kernel<float, 512><<<grid, 32 * warps, smem, st>>>(sys, items, nitems, call, queue, sweep, eval,
-                                                                    derivs);
-    else
-      batch_fused_kernel<double, 512><<<grid, 32 * warps, smem, st>>>(sys, items, nitems, call, queue, sweep, eval,
-                                                                     derivs);
+    if (is_float) VBQ_FUSED(float, 512);
+    else VBQ_FUSED(double, 512);
   }
+#undef VBQ_FUSED
   return cudaGetLastError();
 }
 
 int batch_fused_grid(int is_float, int warps, int smem, int persist) {
-  const void* fn = warps <= 8 ? (is_float ? (const void*)batch_fused_kernel<float, 256>
-                                          : (const void*)batch_fused_kernel<double, 256>)
-                              : (is_float ? (const void*)batch_fused_kernel<float, 512>
-                                          : (const void*)batch_fused_kernel<double, 512>);
+  const void* fn = warps <= 8    ? (is_float ? (const void*)batch_fused_kernel<float, 256>
+                                             : (const void*)batch_fused_kernel<double, 256>)
+                   : warps <= 12 ? (is_float ? (const void*)batch_fused_kernel<float, 384>
+                                             : (const void*)batch_fused_kernel<double, 384>)
+                                 : (is_float ? (const void*)batch_fused_kernel<float, 512>
+                                             : (const void*)batch_fused_kernel<double, 512>);
   return batch_grid(fn, 1 << 30, warps, smem, persist);
 }
 

@@ -41,7 +41,6 @@ namespace {
 constexpr int kTa = 128;          // output tile rows i (MMA M, tensor-memory lanes): A = X_i
 constexpr int kTb = 112;          // output tile columns j of S and of H: B = [X_j; Y_j], N = 224
 constexpr int kColBlock = 256;    // threads of a column-sum block (and samples per sub-tile)
-constexpr int kColTiles = 1;      // sub-tiles per column-sum block
 constexpr int kCenTiles = 8;      // 64-sample tiles per centring block: 512 samples
 constexpr float kScaleTop = 16384.0f;  // scaled values stay below 2^14 (half precision max 65504)
 
@@ -55,79 +54,129 @@ __host__ __device__ inline int rows_t(int P) { return round_up(P > kTa ? P : kTa
 // rows the tensor maps cover (never fewer than a box)
 __host__ __device__ inline int rows_m(int P) { return P > kTa ? P : kTa; }
 
-// (1) Block partials: row b = [sum w, sum w E, sum w O (P), sum w dE (P)] over the block's 256
-// samples (the O and dE sums in the input type per thread, stored in double); maxima as float
-// bits (non-negative floats order like unsigned): mx[0] = max w, mx[1] = max |E|,
-// mx[2 + c] = max |O_c|, mx[2 + P + c] = max |dE_c|.
-template <class Tin>
+// Four consecutive columns c .. c + 3 of one sample row (zero past P): 16-byte loads when VEC
+// (P a multiple of 4 and 16-byte aligned arrays), else one element at a time.
+template <class Tin, bool VEC>
+__device__ __forceinline__ void load4(const Tin* __restrict__ row, int c, int P, Tin v[4]) {
+  if (VEC) {
+    if (std::is_same<Tin, float>::value) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(row + c));
+      v[0] = (Tin)t.x; v[1] = (Tin)t.y; v[2] = (Tin)t.z; v[3] = (Tin)t.w;
+    } else {
+      const double2 a = __ldg(reinterpret_cast<const double2*>(row + c));
+      const double2 b = __ldg(reinterpret_cast<const double2*>(row + c + 2));
+      v[0] = (Tin)a.x; v[1] = (Tin)a.y; v[2] = (Tin)b.x; v[3] = (Tin)b.y;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = c + u < P ? row[c + u] : (Tin)0;
+  }
+}
+
+// (1) Block partials: row b = [sum w, sum w E, sum w O (P), sum w dE (P)] over samples
+// [256 b, 256 b + 256) (the O and dE sums in the input type per thread, added in a fixed order,
+// stored in double); maxima as float bits (non-negative floats order like unsigned):
+// mx[0] = max w, mx[1] = max |E|, mx[2 + c] = max |O_c|, mx[2 + P + c] = max |dE_c|.
+// Block (b, g) takes columns [64 g, 64 g + 64): thread (r, q) = (tid / 16, tid % 16) columns
+// 64 g + 4 q .. + 3 of samples 256 b + r, + 16, ...; the 16 row partials are added in row order.
+template <class Tin, bool VEC>
 __global__ void __launch_bounds__(kColBlock) lin_colsum_kernel(int P, long long M, const Tin* __restrict__ O,
                                                                const Tin* __restrict__ dEL,
                                                                const double* __restrict__ E,
                                                                const double* __restrict__ w,
                                                                double* __restrict__ part1, unsigned* __restrict__ mx) {
-  __shared__ double sw[kColBlock], se[kColBlock];
+  __shared__ double sw[kColBlock];
+  __shared__ Tin red_o[16][64], red_d[16][64];
+  __shared__ float red_mo[16][64], red_md[16][64];
+  __shared__ double red_w[8][2];
   const int L1 = 2 * P + 2;
   double* row = part1 + (size_t)blockIdx.x * L1;
-  // each thread keeps its columns' sums over the block's sub-tiles (at most ceil(P / 256)
-  // columns per thread; the loop below handles the rest in passes)
-  double tot_w = 0.0, tot_we = 0.0;
-  for (int c0 = 0; c0 < max(P, 1); c0 += kColBlock) {
-    const int c = c0 + threadIdx.x;
-    Tin so = 0, sd = 0;
-    float mo = 0.0f, md = 0.0f;
-    for (int t = 0; t < kColTiles; ++t) {
-      const long long s0 = ((long long)blockIdx.x * kColTiles + t) * kColBlock, s1 = min(M, s0 + kColBlock);
-      if (s0 >= M) break;
-      __syncthreads();
-      {
-        const long long s = s0 + threadIdx.x;
-        double ws = 0.0, e = 0.0;
-        if (s < s1) {
-          ws = w ? w[s] : 1.0;
-          e = E[s];
-        }
-        sw[threadIdx.x] = ws;
-        se[threadIdx.x] = e;
-        if (c0 == 0) {
-          float mw = (float)ws, me = fabsf((float)e);
-          for (int o = 16; o > 0; o >>= 1) {
-            mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
-            me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, o));
-          }
-          if ((threadIdx.x & 31) == 0) {
-            atomicMax(mx, __float_as_uint(mw));
-            atomicMax(mx + 1, __float_as_uint(me));
-          }
-        }
-      }
-      __syncthreads();
-      const int n = (int)(s1 - s0);
-      if (c0 == 0 && threadIdx.x == 0)
-        for (int k = 0; k < n; ++k) {
-          tot_w += sw[k];
-          tot_we = fma(sw[k], se[k], tot_we);
-        }
-      if (c < P)
-#pragma unroll 8
-        for (int k = 0; k < n; ++k) {
-          const Tin o = O[(s0 + k) * P + c], d = dEL[(s0 + k) * P + c];
-          const Tin ws = (Tin)sw[k];
-          so += ws * o;
-          sd += ws * d;
-          mo = fmaxf(mo, fabsf((float)o));
-          md = fmaxf(md, fabsf((float)d));
-        }
+  const long long s0 = (long long)blockIdx.x * kColBlock;
+  const int tid = threadIdx.x, r = tid >> 4, q = tid & 15;
+  {
+    const long long s = s0 + tid;
+    double ws = 0.0, e = 0.0;
+    if (s < M) {
+      ws = w ? w[s] : 1.0;
+      e = E[s];
     }
-    if (c < P) {
-      row[2 + c] = (double)so;
-      row[2 + P + c] = (double)sd;
-      atomicMax(mx + 2 + c, __float_as_uint(mo));
-      atomicMax(mx + 2 + P + c, __float_as_uint(md));
+    sw[tid] = ws;
+    if (blockIdx.y == 0) {  // sum w, sum w E in a fixed order, and the maxima of w and |E|
+      double a = ws, b = ws * e;
+      float mw = (float)ws, me = fabsf((float)e);
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+        me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, o));
+      }
+      if ((tid & 31) == 0) {
+        red_w[tid >> 5][0] = a;
+        red_w[tid >> 5][1] = b;
+        atomicMax(mx, __float_as_uint(mw));
+        atomicMax(mx + 1, __float_as_uint(me));
+      }
     }
   }
-  if (threadIdx.x == 0) {
-    row[0] = tot_w;
-    row[1] = tot_we;
+  __syncthreads();
+  if (blockIdx.y == 0 && tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < 8; ++k) {
+      a += red_w[k][0];
+      b += red_w[k][1];
+    }
+    row[0] = a;
+    row[1] = b;
+  }
+  const int c = blockIdx.y * 64 + 4 * q;
+  Tin so[4] = {0, 0, 0, 0}, sd[4] = {0, 0, 0, 0};
+  float mo[4] = {0.0f, 0.0f, 0.0f, 0.0f}, md[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  auto take = [&](int sl) {
+    Tin o[4], d[4];
+    load4<Tin, VEC>(O + (s0 + sl) * P, c, P, o);
+    load4<Tin, VEC>(dEL + (s0 + sl) * P, c, P, d);
+    const Tin ws = (Tin)sw[sl];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      so[u] += ws * o[u];
+      sd[u] += ws * d[u];
+      mo[u] = fmaxf(mo[u], fabsf((float)o[u]));
+      md[u] = fmaxf(md[u], fabsf((float)d[u]));
+    }
+  };
+  if (c < P) {
+    if (s0 + kColBlock <= M) {  // a full block: no per-sample test, so the loads batch
+#pragma unroll 4
+      for (int k = 0; k < kColBlock / 16; ++k) take(r + 16 * k);
+    } else {
+      for (int k = 0; k < kColBlock / 16; ++k)
+        if (s0 + r + 16 * k < M) take(r + 16 * k);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    red_o[r][4 * q + u] = so[u];
+    red_d[r][4 * q + u] = sd[u];
+    red_mo[r][4 * q + u] = mo[u];
+    red_md[r][4 * q + u] = md[u];
+  }
+  __syncthreads();
+  if (tid < 64) {
+    const int cc = blockIdx.y * 64 + tid;
+    if (cc < P) {
+      Tin a = red_o[0][tid], b = red_d[0][tid];
+      float ma = red_mo[0][tid], mb = red_md[0][tid];
+      for (int k = 1; k < 16; ++k) {
+        a += red_o[k][tid];
+        b += red_d[k][tid];
+        ma = fmaxf(ma, red_mo[k][tid]);
+        mb = fmaxf(mb, red_md[k][tid]);
+      }
+      row[2 + cc] = (double)a;
+      row[2 + P + cc] = (double)b;
+      atomicMax(mx + 2 + cc, __float_as_uint(ma));
+      atomicMax(mx + 2 + P + cc, __float_as_uint(mb));
+    }
   }
 }
 
@@ -211,8 +260,8 @@ __device__ __forceinline__ void split_half(float v, __half& hi, __half& lo) {
 // M <= s < Mp.  A tile of the tensor-core pass (rows r0 .. r0 + 127 of one group) is then one
 // contiguous 16 KB block.  A block of this kernel transposes 64 samples x 64 parameters through
 // shared memory: reads along parameters and writes along samples are both coalesced.
-template <class Tin>
-__global__ void __launch_bounds__(256) lin_center_kernel(int P, long long M, long long Mp, const Tin* __restrict__ O,
+template <class Tin, bool VEC>
+__global__ void __launch_bounds__(256, 3) lin_center_kernel(int P, long long M, long long Mp, const Tin* __restrict__ O,
                                                          const Tin* __restrict__ dEL, const double* __restrict__ E,
                                                          const double* __restrict__ w, const float* __restrict__ rwf,
                                                          const float* __restrict__ Ef, const double* __restrict__ acc,
@@ -221,65 +270,85 @@ __global__ void __launch_bounds__(256) lin_center_kernel(int P, long long M, lon
                                                          double* __restrict__ part2) {
   // [array][parameter][sample]: rows of 72 halves (144 bytes) keep the 16-byte chunks aligned
   __shared__ __align__(16) __half t[4][64][72];
-  __shared__ double red[4][64];
+  __shared__ double red[16][64];
   const int c0 = blockIdx.y * 64;
   const double isw = 1.0 / acc[0];
-  const int cl = threadIdx.x & 63, sq = threadIdx.x >> 6;
-  const int c = c0 + cl;
-  const Tin mo = c < P ? (Tin)(acc[2 + c] * isw) : (Tin)0;
-  const float sx = scl[c], sy = scl[Pr + c];
-  double sxe = 0.0;  // sum over this thread's samples of w Ot E (16-sample partials in Tin)
+  // thread (r, q) = (tid % 16, tid / 16): parameters c0 + 4 q .. + 3 of samples s0 + r + 16 k
+  const int r = threadIdx.x & 15, q = threadIdx.x >> 4;
+  const int c = c0 + 4 * q;
+  Tin mo[4];
+  float sx[4], sy[4];
+  double sxe[4] = {0.0, 0.0, 0.0, 0.0};  // sums of w Ot E over this thread's samples (4-sample partials in Tin)
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    mo[u] = c + u < P ? (Tin)(acc[2 + c + u] * isw) : (Tin)0;
+    sx[u] = scl[c + u];
+    sy[u] = scl[Pr + c + u];
+  }
   for (int tt = 0; tt < kCenTiles; ++tt) {
     const long long s0 = ((long long)blockIdx.x * kCenTiles + tt) * 64;
     if (s0 >= M) break;
     __syncthreads();
-    Tin part = 0;
-    // all 32 loads of the tile first (memory-level parallelism), then the arithmetic
-    Tin ov[16], dv[16];
+    // the tile's 8 loads of 4 values first (memory-level parallelism), then the arithmetic
+    Tin ov[4][4], dv[4][4];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const long long sm = s0 + sq + 4 * k;
-      const bool in = sm < M && c < P;
-      ov[k] = in ? O[sm * P + c] : (Tin)0;
-      dv[k] = in ? dEL[sm * P + c] : (Tin)0;
-    }
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int sl = sq + 4 * k;
-      const long long sm = s0 + sl;
-      float xv = 0.0f, yv = 0.0f;
+    for (int k = 0; k < 4; ++k) {
+      const long long sm = s0 + r + 16 * k;
       if (sm < M && c < P) {
-        const Tin x = ov[k] - mo;
-        const Tin e = std::is_same<Tin, double>::value ? (Tin)E[sm] : (Tin)Ef[sm];
-        const Tin ex = e * x;
-        const Tin y = ex + dv[k];
-        const float rw = rwf[sm];
-        xv = (float)x * rw * sx;
-        yv = (float)y * rw * sy;
-        part += (w ? (Tin)w[sm] : (Tin)1) * ex;
+        load4<Tin, VEC>(O + sm * P, c, P, ov[k]);
+        load4<Tin, VEC>(dEL + sm * P, c, P, dv[k]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ov[k][u] = dv[k][u] = (Tin)0;
       }
-      split_half(xv, t[0][cl][sl], t[1][cl][sl]);
-      split_half(yv, t[2][cl][sl], t[3][cl][sl]);
     }
-    sxe += (double)part;
+    Tin part[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int sl = r + 16 * k;
+      const long long sm = s0 + sl;
+      const bool in = sm < M;
+      const Tin e = in ? (std::is_same<Tin, double>::value ? (Tin)E[sm] : (Tin)Ef[sm]) : (Tin)0;
+      const float rw = in ? rwf[sm] : 0.0f;
+      const Tin ws = in ? (w ? (Tin)w[sm] : (Tin)1) : (Tin)0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float xv = 0.0f, yv = 0.0f;
+        if (in && c + u < P) {
+          const Tin x = ov[k][u] - mo[u];
+          const Tin ex = e * x;
+          const Tin y = ex + dv[k][u];
+          xv = (float)x * rw * sx[u];
+          yv = (float)y * rw * sy[u];
+          part[u] += ws * ex;
+        }
+        split_half(xv, t[0][4 * q + u][sl], t[1][4 * q + u][sl]);
+        split_half(yv, t[2][4 * q + u][sl], t[3][4 * q + u][sl]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sxe[u] += (double)part[u];
     __syncthreads();
     // 16-byte stores: per array (X, Y), group g of the tile's two and row, the 128-byte row
     // [hi 0-31 | lo 0-31] in 8 chunks of 8 halves; groups that start at or past Mp are not stored
-    for (int q = threadIdx.x; q < 2 * 64 * 16; q += 256) {
-      const int a = q >> 10, rr = (q >> 4) & 63, ch = q & 15;
-      const int g = ch >> 3, part = (ch >> 2) & 1, sub = ch & 3;
+    for (int qq = threadIdx.x; qq < 2 * 64 * 16; qq += 256) {
+      const int a = qq >> 10, rr = (qq >> 4) & 63, ch = qq & 15;
+      const int g = ch >> 3, half = (ch >> 2) & 1, sub = ch & 3;
       if (s0 + 32 * g >= Mp) continue;
-      const uint4 v = *reinterpret_cast<const uint4*>(&t[2 * a + part][rr][32 * g + 8 * sub]);
+      const uint4 v = *reinterpret_cast<const uint4*>(&t[2 * a + half][rr][32 * g + 8 * sub]);
       __half* const dst = a == 0 ? XI : YI;
       const size_t grp = (size_t)(s0 / 32 + g);
-      *reinterpret_cast<uint4*>(dst + (grp * Pr + c0 + rr) * 64 + 32 * part + 8 * sub) = v;
+      *reinterpret_cast<uint4*>(dst + (grp * Pr + c0 + rr) * 64 + 32 * half + 8 * sub) = v;
     }
   }
-  red[sq][cl] = sxe;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) red[r][4 * q + u] = sxe[u];
   __syncthreads();
-  if (threadIdx.x < 64)  // block partial of sum w Ot E, in sample-quarter order
-    part2[(size_t)blockIdx.x * Pr + c0 + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x] +
-                                                       red[2][threadIdx.x] + red[3][threadIdx.x];
+  if (threadIdx.x < 64) {  // block partial of sum w Ot E, the 16 sample offsets in order
+    double v = red[0][threadIdx.x];
+    for (int k = 1; k < 16; ++k) v += red[k][threadIdx.x];
+    part2[(size_t)blockIdx.x * Pr + c0 + threadIdx.x] = v;
+  }
 }
 
 // (3) Partial tiles, one CTA per (128 x 112 output tile, chunk of samples):
@@ -571,7 +640,7 @@ struct LinWs {
 };
 LinWs carve(void* ws, int P, long long M, int nchunk) {
   const int L1 = 2 * P + 2, Pa = rows_a(P), Pb = rows_b(P), Pr = rows_t(P);
-  const long long nb1 = (M + kColBlock * kColTiles - 1) / (kColBlock * kColTiles),
+  const long long nb1 = (M + kColBlock - 1) / kColBlock,
                   nb2 = (M + 64 * kCenTiles - 1) / (64 * kCenTiles);
   const long long Mp = (M + 31) / 32 * 32;
   unsigned char* p = static_cast<unsigned char*>(ws);
@@ -635,12 +704,15 @@ static cudaError_t encode_tile_map(CUtensorMap* map, const __half* base, int P, 
 template <class Tin>
 static cudaError_t launch_lin_t(int P, long long M, const Tin* O, const Tin* dEL, const double* E, const double* w,
                                 void* ws, size_t ws_bytes, int nsm, double* E0, double* gL, double* gR, double* S,
-                                double* H, cudaStream_t st, int* nlaunch) {
+                                double* H, cudaStream_t st, int* nlaunch, cudaEvent_t* ev) {
+  auto mark = [&](int k) {
+    if (ev) cudaEventRecord(ev[k], st);
+  };
   const int L1 = 2 * P + 2, Pa = rows_a(P), Pb = rows_b(P), Pr = rows_t(P);
   const long long Mp = (M + 31) / 32 * 32;
   const int nb2 = (int)((M + 64 * kCenTiles - 1) / (64 * kCenTiles));
   const LinGrid G = lin_grid(P, M, nsm);
-  const int nb1 = (int)((M + kColBlock * kColTiles - 1) / (kColBlock * kColTiles));
+  const int nb1 = (int)((M + kColBlock - 1) / kColBlock);
   const LinWs L = carve(ws, P, M, G.nchunk);
   if (L.bytes > ws_bytes) return cudaErrorInvalidValue;  // workspace sized for another grid
   cudaError_t e = cudaMemsetAsync(L.mx, 0, sizeof(unsigned) * (2 + 2 * (size_t)P), st);
@@ -648,15 +720,28 @@ static cudaError_t launch_lin_t(int P, long long M, const Tin* O, const Tin* dEL
   if (e == cudaSuccess)  // -1: not started
     e = cudaMemsetAsync(L.prog, 0xff, sizeof(int) * (size_t)G.nchunk * (Pa / kTa) * (Pb / kTb), st);
   if (e != cudaSuccess) return e;
-  lin_colsum_kernel<Tin><<<nb1, kColBlock, 0, st>>>(P, M, O, dEL, E, w, L.part1, L.mx);
+  mark(0);
+  // 16-byte loads of the [M][P] inputs when every row starts on a 16-byte boundary
+  const bool vec = P % 4 == 0 && reinterpret_cast<uintptr_t>(O) % 16 == 0 && reinterpret_cast<uintptr_t>(dEL) % 16 == 0;
+  const dim3 gcol((unsigned)nb1, (unsigned)((P + 63) / 64));
+  if (vec)
+    lin_colsum_kernel<Tin, true><<<gcol, kColBlock, 0, st>>>(P, M, O, dEL, E, w, L.part1, L.mx);
+  else
+    lin_colsum_kernel<Tin, false><<<gcol, kColBlock, 0, st>>>(P, M, O, dEL, E, w, L.part1, L.mx);
   lin_seg_reduce<<<dim3((L1 + 31) / 32, kSeg), 256, 0, st>>>(L1, nb1, L.part1, L.seg);
   lin_final_reduce<<<(L1 + 255) / 256, 256, 0, st>>>(L1, L.seg, L.acc);
   lin_scale_kernel<<<(Pr + 255) / 256, 256, 0, st>>>(P, Pr, L.acc, L.mx, L.scl);
   lin_sample_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, E, w, L.rw, L.Ef);
-  lin_center_kernel<Tin><<<dim3((unsigned)nb2, Pr / 64), 256, 0, st>>>(
-      P, M, Mp, O, dEL, E, w, L.rw, L.Ef, L.acc, L.scl, Pr, L.XI, L.YI, L.part2);
+  mark(1);
+  if (vec)
+    lin_center_kernel<Tin, true><<<dim3((unsigned)nb2, Pr / 64), 256, 0, st>>>(
+        P, M, Mp, O, dEL, E, w, L.rw, L.Ef, L.acc, L.scl, Pr, L.XI, L.YI, L.part2);
+  else
+    lin_center_kernel<Tin, false><<<dim3((unsigned)nb2, Pr / 64), 256, 0, st>>>(
+        P, M, Mp, O, dEL, E, w, L.rw, L.Ef, L.acc, L.scl, Pr, L.XI, L.YI, L.part2);
   lin_seg_reduce<<<dim3((Pr + 31) / 32, kSeg), 256, 0, st>>>(Pr, nb2, L.part2, L.seg);
   lin_final_reduce<<<(Pr + 255) / 256, 256, 0, st>>>(Pr, L.seg, L.sxe);
+  mark(2);
   // A tiles: 128 rows of X; B tiles: 112 rows of X and of Y
   CUtensorMap mA, mBX, mBY;
   e = encode_tile_map(&mA, L.XI, P, Pr, Mp, kTa);
@@ -668,21 +753,23 @@ static cudaError_t launch_lin_t(int P, long long M, const Tin* O, const Tin* dEL
   const int ntile = (Pa / kTa) * (Pb / kTb);
   lin_tc_kernel<<<dim3(ntile, G.nchunk), kTcThreads, kTcSmem, st>>>(mA, mBX, mBY, Pa, Pb, M, G.chunk, L.part,
                                                                      L.prog, L.err);
+  mark(3);
   const long long nq = std::max<long long>((long long)P * P, 1);
   lin_reduce_kernel<<<(int)((nq + 255) / 256), 256, 0, st>>>(P, Pa, Pb, Pr, G.nchunk, L.part, L.acc, L.sxe, L.scl,
                                                               E0, gL, gR, S, H, L.err);
+  mark(4);
   *nlaunch = 11;
   return cudaGetLastError();
 }
 
 cudaError_t launch_lin(int in_float, int P, long long M, const void* O, const void* dEL, const double* E,
                        const double* w, void* ws, size_t ws_bytes, int nsm, double* E0, double* gL, double* gR,
-                       double* S, double* H, cudaStream_t st, int* nlaunch) {
+                       double* S, double* H, cudaStream_t st, int* nlaunch, cudaEvent_t* ev) {
   if (in_float)
     return launch_lin_t<float>(P, M, static_cast<const float*>(O), static_cast<const float*>(dEL), E, w, ws, ws_bytes,
-                               nsm, E0, gL, gR, S, H, st, nlaunch);
+                               nsm, E0, gL, gR, S, H, st, nlaunch, ev);
   return launch_lin_t<double>(P, M, static_cast<const double*>(O), static_cast<const double*>(dEL), E, w, ws,
-                              ws_bytes, nsm, E0, gL, gR, S, H, st, nlaunch);
+                              ws_bytes, nsm, E0, gL, gR, S, H, st, nlaunch, ev);
 }
 
 }  // namespace vbq
