@@ -732,7 +732,7 @@ def batched_timing(vbqmc, dev, steps):
     def per_system(step0):
         for k in range(len(specs)):
             ctx.vmc_steps(k, vbqmc.MIXED, R[k], 1, 0.3, SEED, step0=step0, refresh=0,
-                          state=None if on_tab[k] else st[k], state_valid=True, logpsi=lp[k], sign=sg[k],
+                          state=None if on_tab[k] else st[k], state_valid=not on_tab[k], logpsi=lp[k], sign=sg[k],
                           eloc=el[k], O=O[k], dEL=dE[k])
     per_system((1 << 24))
     torch.cuda.synchronize()
@@ -823,6 +823,8 @@ def main():
     ap.add_argument("--eta-steps", type=int, default=200, help="steps of the efficiency comparison (0: skip)")
     ap.add_argument("--dmc48-steps", type=int, default=100, help="timed DMC steps of the 48-electron system (0: skip)")
     ap.add_argument("--only-dmc48", action="store_true", help="run only the 48-electron DMC leg (long runs)")
+    ap.add_argument("--only-lin", action="store_true", help="run only the linear-method leg (profiling)")
+    ap.add_argument("--only-batch", action="store_true", help="run only the batched-workload leg (profiling)")
     ap.add_argument("--dmc48-walkers", type=int, default=65536, help="walkers of the 48-electron timing")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -842,6 +844,19 @@ def main():
         out = dmc48_timing(vbqmc, torch.device("cuda", local), args.dmc48_steps, args.dmc48_walkers)
         out["clocks"] = sampler.stop()
         print(json.dumps({"dmc48": out}), flush=True)
+        return
+    if args.only_lin or args.only_batch:
+        import torch
+        from paper_2207_14715_gb300 import vbqmc
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        if args.only_lin:
+            ctx = vbqmc.create(local)
+            out = {"linear_method": lin_method_timing(ctx, vbqmc, dev, args.steps, file_peaks(), args.lin_samples)}
+            ctx.close()
+        else:
+            out = {"batched": batched_timing(vbqmc, dev, args.steps)}
+        print(json.dumps(out), flush=True)
         return
     run_ours(args, ws, rank, local)
     if ws > 1:
