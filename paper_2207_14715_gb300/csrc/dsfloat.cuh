@@ -92,48 +92,6 @@ __device__ __forceinline__ dsf ds_from_double(double x) {
 }
 __device__ __forceinline__ double ds_to_double(dsf a) { return (double)a.hi + (double)a.lo; }
 
-// Conversions between double and float-float through integer operations on the IEEE bit
-// patterns, so that they take no FP64-pipe slot (the two-way conversion instructions between
-// float and double issue on that pipe).
-// float -> double, exact; subnormal floats flush to a signed zero, infinities stay infinite.
-__device__ __forceinline__ double f2d_bits(float x) {
-  const unsigned b = __float_as_uint(x);
-  const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
-  const unsigned e = (b >> 23) & 0xffu;
-  if (e == 0u) return __longlong_as_double((long long)sgn);
-  const unsigned long long E = e == 0xffu ? 0x7ffull : (unsigned long long)(e - 127u + 1023u);
-  return __longlong_as_double((long long)(sgn | (E << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
-}
-// double -> float-float: hi = x with its significand rounded to 24 bits, lo = the remainder
-// (below 2^-24 |x|) rounded to float; |x| beyond the float range gives +-inf, below the
-// normal float range a signed zero.
-__device__ __forceinline__ dsf ds_split_bits(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sgn = (unsigned)(b >> 63) << 31;
-  const int e = (int)((b >> 52) & 0x7ffu) - 1023;
-  if (e < -126) return {__uint_as_float(sgn), 0.0f};
-  if (e > 127) return {__uint_as_float(sgn | 0x7f800000u), 0.0f};
-  const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);  // 53-bit significand
-  unsigned long long Mh = (M + (1ull << 28)) >> 29;                      // rounded to 24 bits
-  int eh = e, sh = 29;
-  if (Mh >> 24) {  // the rounding carried into a 25th bit
-    Mh >>= 1;
-    ++eh;
-    ++sh;
-  }
-  if (eh > 127) return {__uint_as_float(sgn | 0x7f800000u), 0.0f};
-  const float hi = __uint_as_float(sgn | ((unsigned)(eh + 127) << 23) | ((unsigned)Mh & 0x7fffffu));
-  const int r = (int)((long long)M - (long long)(Mh << sh));  // |r| <= 2^29: the remainder in units of 2^(e-52)
-  float lo = (float)r;
-  // lo * 2^(e - 52) in two exact power-of-two steps (e - 52 >= -178)
-  const int k = e - 52, k1 = k < -100 ? -100 : k, k2 = k - k1;
-  lo *= __int_as_float((k1 + 127) << 23);
-  lo *= __int_as_float((k2 + 127) << 23);
-  return {hi, sgn ? -lo : lo};
-}
-// float-float -> double (hi and lo exactly, one double addition)
-__device__ __forceinline__ double ds_to_double_bits(dsf a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
-
 // exp(-x) for x >= 0 given in float-float, relative error ~1e-14.
 // Reduction (Cody and Waite): n = round(x / ln 2), r = x - n ln 2 with ln 2 split into three
 // floats L1 + L2 + L3 (L1 has 15 significant bits, so n L1 and x_hi - n L1 are exact for the

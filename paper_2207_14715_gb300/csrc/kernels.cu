@@ -97,8 +97,6 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.part = take(8 * std::max(std::max(s.n_occ_chunk[0], s.n_occ_chunk[1]), 1));
   L.rho = take(8 * std::max(s.U[0], s.U[1]));
   L.rinv = take(8 * (std::max(s.U[0], s.U[1]) + 1));
-  L.vrowf = take(4 * L.nocc_max);
-  L.rhos = take(8 * std::max(s.U[0], s.U[1]));
   L.cvec = take(std::max(cv, 8));
   L.scratch = shared0;
   off = std::max(off, align16(shared0 + std::max(scr, 16)));

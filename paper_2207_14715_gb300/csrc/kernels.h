@@ -59,7 +59,6 @@ struct SweepLayout {
   int wpb = 0, warp_bytes = 0;
   int R, Rds, rtab, rtds, Binv0, Binv1, ldet, dsg, wk, PhiO, bas, vrow, part, rho, rinv, cvec, scratch, geo, geom;
   int T0 = 0, T1 = 0, qn = 0, cx = 0;
-  int vrowf = 0, rhos = 0;  // mixed form: float orbital row, float-float ratios
   int tab = 0;
   int nocc_max;
   int G0, G1;

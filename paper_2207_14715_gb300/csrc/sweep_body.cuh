@@ -142,7 +142,6 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   // [ln|Phi|][sign Phi]; the sweep starts from the inverses and the term ratios and carries
   // both (and ln|Phi|) through its moves
   const int nb0 = s.U[0] * s.n[0] * s.n[0], nb1 = s.U[1] * s.n[1] * s.n[1], Ut = U0 + s.U[1];
-  const int nb0_ds = TAB ? 0 : nb0, nb1_ds = TAB ? 0 : nb1;
   double lnPhi = 0.0, sgnPhi = 1.0;
   // product of the accepted moves' |Phi'/Phi| since ln|Phi| was last set, as a mantissa in
   // [1, 2) and a binary exponent (bit operations; one logarithm per sweep instead of one per move)
@@ -151,21 +150,6 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   // reference-determinant tables (TAB): T per spin, q_u of both spins in wk, proposed q_u,
   // the move's c_x, and Sigma = sum_k C_k q_up q_dn
   double* Tt[2] = {reinterpret_cast<double*>(base + L.T0), reinterpret_cast<double*>(base + L.T1)};
-  // mixed form with per-determinant inverses: the inverses, the determinant ratios, their
-  // reciprocals and the Sherman-Morrison columns in float-float (on the FP32 pipe; the FP64
-  // pipe of this part is ~74x slower), the orbital row in float; the structure sum stays in
-  // double.  The inverses are split from double after every factorisation and joined back to
-  // double for the walker state.
-  constexpr bool kDS = !TAB && !kSameType<Tb, double>;
-  dsf* BS[2] = {reinterpret_cast<dsf*>(Binv[0]), reinterpret_cast<dsf*>(Binv[1])};
-  dsf* rhos = reinterpret_cast<dsf*>(base + L.rhos);
-  dsf* rinvS = reinterpret_cast<dsf*>(rinv);  // [0, U) float-float 1/rho_u; rinv[U] stays double
-  dsf* cvS = reinterpret_cast<dsf*>(cvec);
-  float* vrowf = reinterpret_cast<float*>(base + L.vrowf);
-  auto split_inverses = [&]() {  // double -> float-float in place, each lane its own elements
-    for (int q = lane; q < nb0_ds; q += 32) BS[0][q] = ds_split_bits(Binv[0][q]);
-    for (int q = lane; q < nb1_ds; q += 32) BS[1][q] = ds_split_bits(Binv[1][q]);
-  };
   double* qn = reinterpret_cast<double*>(base + L.qn);
   double* cxv = reinterpret_cast<double*>(base + L.cx);
   double Sig = 1.0;
@@ -177,7 +161,6 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
     for (int k = lane; k < s.nterm; k += 32) wk[k] = st[nb0 + nb1 + 2 * Ut + k];
     lnPhi = st[nb0 + nb1 + 2 * Ut + s.nterm];
     sgnPhi = st[nb0 + nb1 + 2 * Ut + s.nterm + 1];
-    if constexpr (kDS) split_inverses();
   }
   __syncwarp();
   int accepted = 0;
@@ -251,10 +234,6 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
                nullptr);
         lu_all(s, 1, lane, PhiO, ldo, (const double*)nullptr, 0, s.det_loc[1], L.G1, Binv[1], scr, ldet + U0,
                dsg + U0, nullptr);
-        if constexpr (kDS) {
-          __syncwarp();
-          split_inverses();
-        }
       }
     }
     if (!TAB && do_refresh) {
@@ -319,8 +298,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         const int c0 = __ldg(s.occ_chunk_off[sp] + q), c1 = __ldg(s.occ_chunk_off[sp] + q + 1);
         Tb v = 0;
         for (int c = c0; c < c1; ++c) v += part[c];
-        if constexpr (kDS) vrowf[q] = (float)v;
-        else vrowd[q] = (double)v;
+        vrowd[q] = (double)v;
       }
       __syncwarp();
       const LaneGroup lgp(lane, G);
@@ -354,29 +332,6 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         rphi = (r0 != 0.0 && Sig != 0.0) ? r0 * Sig_new / Sig : 0.0;
         if (!isfinite(rphi)) rphi = 0.0;  // an overflowing ratio is rejected (the tables are refreshed)
         (void)uo;
-      } else if constexpr (kDS) {
-        // determinant ratios rho_u = sum_o v_occ(o) Binv_u[o][ie] in float-float (group sums
-        // by shuffles), and in double for the structure sum
-        for (int ub = 0; ub < U; ub += ng) {
-          const int u = ub + g;
-          dsf r = {0.0f, 0.0f};
-          if (u < U && gl < n) {
-            const float v = vrowf[__ldg(dl + u * n + gl)];
-            const dsf bb = BS[sp][u * n * n + gl * n + ie];
-            r = ds_two_prod(v, bb.hi);
-            r.lo = fmaf(v, bb.lo, r.lo);
-          }
-          for (int o = G >> 1; o > 0; o >>= 1)
-            r = ds_add(r, dsf{__shfl_xor_sync(kFull, r.hi, o), __shfl_xor_sync(kFull, r.lo, o)});
-          if (u < U && gl == 0) {
-            rhos[u] = r;
-            rho[u] = ds_to_double_bits(r);
-          }
-        }
-        __syncwarp();
-        for (int k = lane; k < s.nterm; k += 32)
-          rphi += __ldg(s.term_coef + k) * wk[k] * rho[__ldg(s.term_det + 2 * k + sp)];
-        rphi = warp_sum(rphi);
       } else {
         // determinant ratios rho_u = sum_o v_occ(o) Binv_u[o][ie]
         for (int ub = 0; ub < U; ub += ng) {
@@ -506,41 +461,6 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         }
         ++accepted;
       } else if (!TAB && uacc < prob) {
-        if constexpr (kDS) {
-          // 1/rho_u in float-float, 1/(Phi'/Phi) in double
-          for (int q = lane; q <= U; q += 32) {
-            if (q < U) rinvS[q] = ds_recip(rhos[q]);
-            else rinv[U] = recip(rphi);
-          }
-          __syncwarp();
-          // Sherman-Morrison in float-float: B <- B - B[:, ie] f^T with
-          // f_j = (sum_o v_o B[o][j] - [j = ie]) / rho, the sum compensated (the errors of the
-          // products and of the running sum collected in one float)
-          for (int ub = 0; ub < U; ub += ng) {
-            const int u = ub + g;
-            const bool act = u < U;
-            dsf* B = BS[sp] + (act ? u : 0) * n * n;
-            dsf* cv = cvS + g * n;
-            if (act && gl < n) cv[gl] = B[gl * n + ie];
-            const dsf irho = act ? rinvS[u] : dsf{0.0f, 0.0f};
-            __syncwarp();
-            if (act && gl < n) {
-              const int j = gl;
-              float sm = (j == ie) ? -1.0f : 0.0f, cm = 0.0f;
-              for (int o = 0; o < n; ++o) {
-                const float v = vrowf[__ldg(dl + u * n + o)];
-                const dsf bb = B[o * n + j];
-                const dsf p = ds_two_prod(v, bb.hi);
-                const dsf t = ds_two_sum(sm, p.hi);
-                sm = t.hi;
-                cm += t.lo + fmaf(v, bb.lo, p.lo);
-              }
-              const dsf f = ds_mul(ds_two_sum(sm, cm), irho);
-              for (int o = 0; o < n; ++o) B[o * n + j] = ds_sub(B[o * n + j], ds_mul(cv[o], f));
-            }
-            __syncwarp();
-          }
-        } else {
         // the reciprocals 1/rho_u and 1/(Phi'/Phi), one per lane
         for (int q = lane; q <= U; q += 32) rinv[q] = recip(q < U ? rho[q] : rphi);
         __syncwarp();
@@ -567,7 +487,6 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
             for (int o = 0; o < n; ++o) B[o * n + j] = fma(-cv[o], f, B[o * n + j]);
           }
           __syncwarp();
-        }
         }
         const double irphi = rinv[U];
         {
@@ -596,10 +515,6 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   if (nacc && lane == 0) nacc[w] += accepted;
   lnPhi += log(pm) + (double)pe * 0.69314718055994530942;  // ln 2
   if (!TAB && state) {  // the carried inverses, term ratios and ln|Phi| at the final positions
-    if constexpr (kDS) {  // float-float -> double in place, each lane its own elements
-      for (int q = lane; q < nb0; q += 32) Binv[0][q] = ds_to_double_bits(BS[0][q]);
-      for (int q = lane; q < nb1; q += 32) Binv[1][q] = ds_to_double_bits(BS[1][q]);
-    }
     double* st = state + (size_t)w * s.state_doubles;
     for (int q = lane; q < nb0; q += 32) st[q] = Binv[0][q];
     for (int q = lane; q < nb1; q += 32) st[nb0 + q] = Binv[1][q];
