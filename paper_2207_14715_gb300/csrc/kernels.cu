@@ -100,7 +100,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.cvec = take(std::max(cv, 8));
   L.scratch = shared0;
   off = std::max(off, align16(shared0 + std::max(scr, 16)));
-  L.geo = take(tb * (N * N + N * s.Nn + (6 * N + 1) * s.Nn));
+  L.geo = take(tb * (N * N + N * s.Nn + (N + 1) * s.Nn));
   L.warp_bytes = off;
   int wpb = max_smem / off;
   if (wpb > 16) wpb = 16;

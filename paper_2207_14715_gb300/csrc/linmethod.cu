@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kColBlock) lin_colsum_kernel(int P, long long 
                                                                const double* __restrict__ E,
                                                                const double* __restrict__ w,
                                                                double* __restrict__ part1, unsigned* __restrict__ mx) {
-  __shared__ double sw[kColBlock];
+  __shared__ Tin sw[kColBlock];  // the block's weights in the input type (converted once per sample)
   __shared__ Tin red_o[16][64], red_d[16][64];
   __shared__ float red_mo[16][64], red_md[16][64];
   __shared__ double red_w[8][2];
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kColBlock) lin_colsum_kernel(int P, long long 
       ws = w ? w[s] : 1.0;
       e = E[s];
     }
-    sw[tid] = ws;
+    sw[tid] = (Tin)ws;
     if (blockIdx.y == 0) {  // sum w, sum w E in a fixed order, and the maxima of w and |E|
       double a = ws, b = ws * e;
       float mw = (float)ws, me = fabsf((float)e);
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kColBlock) lin_colsum_kernel(int P, long long 
     Tin o[4], d[4];
     load4<Tin, VEC>(O + (s0 + sl) * P, c, P, o);
     load4<Tin, VEC>(dEL + (s0 + sl) * P, c, P, d);
-    const Tin ws = (Tin)sw[sl];
+    const Tin ws = sw[sl];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       so[u] += ws * o[u];
@@ -278,7 +278,8 @@ __global__ void __launch_bounds__(256, 3) lin_center_kernel(int P, long long M, 
   const int c = c0 + 4 * q;
   Tin mo[4];
   float sx[4], sy[4];
-  double sxe[4] = {0.0, 0.0, 0.0, 0.0};  // sums of w Ot E over this thread's samples (4-sample partials in Tin)
+  double sxe[4] = {0.0, 0.0, 0.0, 0.0};  // sums of w Ot E over this thread's samples (16-sample partials in Tin)
+  Tin part[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     mo[u] = c + u < P ? (Tin)(acc[2 + c + u] * isw) : (Tin)0;
@@ -302,7 +303,6 @@ __global__ void __launch_bounds__(256, 3) lin_center_kernel(int P, long long M, 
         for (int u = 0; u < 4; ++u) ov[k][u] = dv[k][u] = (Tin)0;
       }
     }
-    Tin part[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int sl = r + 16 * k;
@@ -326,8 +326,13 @@ __global__ void __launch_bounds__(256, 3) lin_center_kernel(int P, long long M, 
         split_half(yv, t[2][4 * q + u][sl], t[3][4 * q + u][sl]);
       }
     }
+    if ((tt & 3) == 3) {  // every 4 tiles (16 samples of this thread) into double
 #pragma unroll
-    for (int u = 0; u < 4; ++u) sxe[u] += (double)part[u];
+      for (int u = 0; u < 4; ++u) {
+        sxe[u] += (double)part[u];
+        part[u] = (Tin)0;
+      }
+    }
     __syncthreads();
     // 16-byte stores: per array (X, Y), group g of the tile's two and row, the 128-byte row
     // [hi 0-31 | lo 0-31] in 8 chunks of 8 halves; groups that start at or past Mp are not stored
@@ -342,7 +347,7 @@ __global__ void __launch_bounds__(256, 3) lin_center_kernel(int P, long long M, 
     }
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) red[r][4 * q + u] = sxe[u];
+  for (int u = 0; u < 4; ++u) red[r][4 * q + u] = sxe[u] + (double)part[u];
   __syncthreads();
   if (threadIdx.x < 64) {  // block partial of sum w Ot E, the 16 sample offsets in order
     double v = red[0][threadIdx.x];

@@ -99,8 +99,8 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   Tb* rEE = reinterpret_cast<Tb*>(base + L.geo);       // [N][N] r_ij
   Tb* rEN = rEE + s.N * s.N;                            // [N][Nn] r_ia
   // row strides padded by one so that lanes on different nuclei (powers) read different banks
-  const int SA = 6 * s.N + 1, UP = s.N + 1;
-  Tb* Stab = rEN + s.N * s.Nn;                          // [Nn][SA]: [a][j][q] = Rbar(r_ja)^q at a*SA + 6j + q
+  const int SA = s.N + 1, UP = s.N + 1;
+  Tb* Sv = rEN + s.N * s.Nn;                            // [Nn][SA]: Rbar(r_ja) at a*SA + j (its powers formed where used)
   Tb* rnE = reinterpret_cast<Tb*>(base + L.geom);       // [N] r from the proposed position
   Tb* rnN = rnE + s.N;                                  // [Nn]
   Tb* Snew = rnN + s.Nn;                                // [Nn][6]
@@ -133,10 +133,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
     const Tb dx = C.en(s, i, a, 0), dy = C.en(s, i, a, 1), dz = C.en(s, i, a, 2);
     const Tb r = vsqrt(dx * dx + dy * dy + dz * dz);
     rEN[p] = r;
-    const Tb sv = (Tb)1 / ((Tb)1 + kap * r);
-    Tb pw = (Tb)1;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) { Stab[a * SA + i * 6 + q] = pw; pw *= sv; }
+    Sv[a * SA + i] = (Tb)1 / ((Tb)1 + kap * r);
   }
   // walker state: [Binv spin 0][Binv spin 1][ln|det| (Ut)][sign (Ut)][r_k = D_k/Phi (nterm)]
   // [ln|Phi|][sign Phi]; the sweep starts from the inverses and the term ratios and carries
@@ -405,10 +402,11 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
             for (int q = 0; q < 6; ++q) Yo[k][q] = Yn[k][q] = (Tb)0;
           for (int j = part * N / np; j < (part + 1) * N / np; ++j) {
             if (j == e) continue;
-            const Tb* Sj = Stab + a * SA + j * 6;
+            const Tb svj = Sv[a * SA + j];
             Tb sj[6];
+            sj[0] = (Tb)1;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) sj[q] = Sj[q];
+            for (int q = 1; q < 6; ++q) sj[q] = sj[q - 1] * svj;
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
               const Tb po = Upo[k * UP + j], pn = Upn[k * UP + j];
@@ -419,7 +417,13 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
               }
             }
           }
-          const Tb* So = Stab + a * SA + e * 6;
+          Tb So[6];
+          So[0] = (Tb)1;
+          {
+            const Tb sve = Sv[a * SA + e];
+#pragma unroll
+            for (int q = 1; q < 6; ++q) So[q] = So[q - 1] * sve;
+          }
           const Tb* Sn = Snew + a * 6;
           const Tb* c = cE + kNeen * __ldg(s.nuc_elem + a);
           een_for_each([&](auto tc) {
@@ -456,8 +460,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         for (int j = lane; j < N; j += 32) rEE[e * N + j] = rEE[j * N + e] = rnE[j];
         for (int a = lane; a < Nn; a += 32) {
           rEN[e * Nn + a] = rnN[a];
-#pragma unroll
-          for (int q = 0; q < 6; ++q) Stab[a * SA + e * 6 + q] = Snew[a * 6 + q];
+          Sv[a * SA + e] = Snew[a * 6 + 1];
         }
         ++accepted;
       } else if (!TAB && uacc < prob) {
@@ -503,8 +506,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         for (int j = lane; j < N; j += 32) rEE[e * N + j] = rEE[j * N + e] = rnE[j];
         for (int a = lane; a < Nn; a += 32) {
           rEN[e * Nn + a] = rnN[a];
-#pragma unroll
-          for (int q = 0; q < 6; ++q) Stab[a * SA + e * 6 + q] = Snew[a * 6 + q];
+          Sv[a * SA + e] = Snew[a * 6 + 1];
         }
         ++accepted;
       }
