@@ -770,7 +770,8 @@ def lin_method_timing(ctx, vbqmc, dev, steps, pk, M=1 << 20):
     O = torch.randn((M, P), generator=g, device=dev, dtype=torch.float32)
     dE = 0.3 * torch.randn((M, P), generator=g, device=dev, dtype=torch.float32)
     E = -10.0 + torch.randn(M, generator=g, device=dev, dtype=torch.float64)
-    ctx.accumulate_lin_matrices(vbqmc.MIXED, O, dE, E)
+    for _ in range(3):  # warm-up (workspace, clocks)
+        ctx.accumulate_lin_matrices(vbqmc.MIXED, O, dE, E)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n = max(3, steps)

@@ -77,105 +77,112 @@ __device__ __forceinline__ void load4(const Tin* __restrict__ row, int c, int P,
 // [256 b, 256 b + 256) (the O and dE sums in the input type per thread, added in a fixed order,
 // stored in double); maxima as float bits (non-negative floats order like unsigned):
 // mx[0] = max w, mx[1] = max |E|, mx[2 + c] = max |O_c|, mx[2 + P + c] = max |dE_c|.
-// Block (b, g) takes columns [64 g, 64 g + 64): thread (r, q) = (tid / 16, tid % 16) columns
-// 64 g + 4 q .. + 3 of samples 256 b + r, + 16, ...; the 16 row partials are added in row order.
+// Block (g, b) (column group fastest, so that the blocks sharing a sample range run together
+// and a 128-byte line that straddles two column groups comes from DRAM once) takes columns
+// [64 g, 64 g + 64): thread (r, q) = (tid / 16, tid % 16) columns 64 g + 4 q .. + 3 of samples
+// 256 b + r, + 16, ...; the 16 row partials are added in row order.
 template <class Tin, bool VEC>
 __global__ void __launch_bounds__(kColBlock) lin_colsum_kernel(int P, long long M, const Tin* __restrict__ O,
                                                                const Tin* __restrict__ dEL,
                                                                const double* __restrict__ E,
                                                                const double* __restrict__ w,
-                                                               double* __restrict__ part1, unsigned* __restrict__ mx) {
+                                                               double* __restrict__ part1, unsigned* __restrict__ mx,
+                                                               long long nb) {
   __shared__ Tin sw[kColBlock];  // the block's weights in the input type (converted once per sample)
   __shared__ Tin red_o[16][64], red_d[16][64];
   __shared__ float red_mo[16][64], red_md[16][64];
   __shared__ double red_w[8][2];
   const int L1 = 2 * P + 2;
-  double* row = part1 + (size_t)blockIdx.x * L1;
-  const long long s0 = (long long)blockIdx.x * kColBlock;
   const int tid = threadIdx.x, r = tid >> 4, q = tid & 15;
-  {
-    const long long s = s0 + tid;
-    double ws = 0.0, e = 0.0;
-    if (s < M) {
-      ws = w ? w[s] : 1.0;
-      e = E[s];
-    }
-    sw[tid] = (Tin)ws;
-    if (blockIdx.y == 0) {  // sum w, sum w E in a fixed order, and the maxima of w and |E|
-      double a = ws, b = ws * e;
-      float mw = (float)ws, me = fabsf((float)e);
-      for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
-        me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, o));
+  // sample blocks blockIdx.y, + gridDim.y, ... (the grid's y extent is limited)
+  for (long long sb = blockIdx.y; sb < nb; sb += gridDim.y) {
+    __syncthreads();  // the previous sample block is done with the shared arrays
+    double* row = part1 + (size_t)sb * L1;
+    const long long s0 = sb * kColBlock;
+    {
+      const long long s = s0 + tid;
+      double ws = 0.0, e = 0.0;
+      if (s < M) {
+        ws = w ? w[s] : 1.0;
+        e = E[s];
       }
-      if ((tid & 31) == 0) {
-        red_w[tid >> 5][0] = a;
-        red_w[tid >> 5][1] = b;
-        atomicMax(mx, __float_as_uint(mw));
-        atomicMax(mx + 1, __float_as_uint(me));
+      sw[tid] = (Tin)ws;
+      if (blockIdx.x == 0) {  // sum w, sum w E in a fixed order, and the maxima of w and |E|
+        double a = ws, b = ws * e;
+        float mw = (float)ws, me = fabsf((float)e);
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+          me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, o));
+        }
+        if ((tid & 31) == 0) {
+          red_w[tid >> 5][0] = a;
+          red_w[tid >> 5][1] = b;
+          atomicMax(mx, __float_as_uint(mw));
+          atomicMax(mx + 1, __float_as_uint(me));
+        }
       }
     }
-  }
-  __syncthreads();
-  if (blockIdx.y == 0 && tid == 0) {
-    double a = 0.0, b = 0.0;
-    for (int k = 0; k < 8; ++k) {
-      a += red_w[k][0];
-      b += red_w[k][1];
+    __syncthreads();
+    if (blockIdx.x == 0 && tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int k = 0; k < 8; ++k) {
+        a += red_w[k][0];
+        b += red_w[k][1];
+      }
+      row[0] = a;
+      row[1] = b;
     }
-    row[0] = a;
-    row[1] = b;
-  }
-  const int c = blockIdx.y * 64 + 4 * q;
-  Tin so[4] = {0, 0, 0, 0}, sd[4] = {0, 0, 0, 0};
-  float mo[4] = {0.0f, 0.0f, 0.0f, 0.0f}, md[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  auto take = [&](int sl) {
-    Tin o[4], d[4];
-    load4<Tin, VEC>(O + (s0 + sl) * P, c, P, o);
-    load4<Tin, VEC>(dEL + (s0 + sl) * P, c, P, d);
-    const Tin ws = sw[sl];
+    const int c = blockIdx.x * 64 + 4 * q;
+    Tin so[4] = {0, 0, 0, 0}, sd[4] = {0, 0, 0, 0};
+    float mo[4] = {0.0f, 0.0f, 0.0f, 0.0f}, md[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    auto take = [&](int sl) {
+      Tin o[4], d[4];
+      load4<Tin, VEC>(O + (s0 + sl) * P, c, P, o);
+      load4<Tin, VEC>(dEL + (s0 + sl) * P, c, P, d);
+      const Tin ws = sw[sl];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        so[u] += ws * o[u];
+        sd[u] += ws * d[u];
+        mo[u] = fmaxf(mo[u], fabsf((float)o[u]));
+        md[u] = fmaxf(md[u], fabsf((float)d[u]));
+      }
+    };
+    if (c < P) {
+      if (s0 + kColBlock <= M) {  // a full block: no per-sample test, so the loads batch
+#pragma unroll 4
+        for (int k = 0; k < kColBlock / 16; ++k) take(r + 16 * k);
+      } else {
+        for (int k = 0; k < kColBlock / 16; ++k)
+          if (s0 + r + 16 * k < M) take(r + 16 * k);
+      }
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      so[u] += ws * o[u];
-      sd[u] += ws * d[u];
-      mo[u] = fmaxf(mo[u], fabsf((float)o[u]));
-      md[u] = fmaxf(md[u], fabsf((float)d[u]));
+      red_o[r][4 * q + u] = so[u];
+      red_d[r][4 * q + u] = sd[u];
+      red_mo[r][4 * q + u] = mo[u];
+      red_md[r][4 * q + u] = md[u];
     }
-  };
-  if (c < P) {
-    if (s0 + kColBlock <= M) {  // a full block: no per-sample test, so the loads batch
-#pragma unroll 4
-      for (int k = 0; k < kColBlock / 16; ++k) take(r + 16 * k);
-    } else {
-      for (int k = 0; k < kColBlock / 16; ++k)
-        if (s0 + r + 16 * k < M) take(r + 16 * k);
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    red_o[r][4 * q + u] = so[u];
-    red_d[r][4 * q + u] = sd[u];
-    red_mo[r][4 * q + u] = mo[u];
-    red_md[r][4 * q + u] = md[u];
-  }
-  __syncthreads();
-  if (tid < 64) {
-    const int cc = blockIdx.y * 64 + tid;
-    if (cc < P) {
-      Tin a = red_o[0][tid], b = red_d[0][tid];
-      float ma = red_mo[0][tid], mb = red_md[0][tid];
-      for (int k = 1; k < 16; ++k) {
-        a += red_o[k][tid];
-        b += red_d[k][tid];
-        ma = fmaxf(ma, red_mo[k][tid]);
-        mb = fmaxf(mb, red_md[k][tid]);
+    __syncthreads();
+    if (tid < 64) {
+      const int cc = blockIdx.x * 64 + tid;
+      if (cc < P) {
+        Tin a = red_o[0][tid], b = red_d[0][tid];
+        float ma = red_mo[0][tid], mb = red_md[0][tid];
+        for (int k = 1; k < 16; ++k) {
+          a += red_o[k][tid];
+          b += red_d[k][tid];
+          ma = fmaxf(ma, red_mo[k][tid]);
+          mb = fmaxf(mb, red_md[k][tid]);
+        }
+        row[2 + cc] = (double)a;
+        row[2 + P + cc] = (double)b;
+        atomicMax(mx + 2 + cc, __float_as_uint(ma));
+        atomicMax(mx + 2 + P + cc, __float_as_uint(mb));
       }
-      row[2 + cc] = (double)a;
-      row[2 + P + cc] = (double)b;
-      atomicMax(mx + 2 + cc, __float_as_uint(ma));
-      atomicMax(mx + 2 + P + cc, __float_as_uint(mb));
     }
   }
 }
@@ -249,9 +256,16 @@ __global__ void lin_scale_kernel(int P, int Pr, const double* __restrict__ acc, 
   scl[Pr + c] = sy;
 }
 
-__device__ __forceinline__ void split_half(float v, __half& hi, __half& lo) {
-  hi = __float2half_rn(v);
-  lo = __float2half_rn(v - __half2float(hi));
+// x and y split into high and low halves (v = hi + lo, hi = half(v), lo = half(v - hi)), the
+// two values converted together (one packed conversion each way)
+__device__ __forceinline__ void split_half2(float x, float y, __half& xh, __half& xl, __half& yh, __half& yl) {
+  const __half2 h = __floats2half2_rn(x, y);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(x - hf.x, y - hf.y);
+  xh = __low2half(h);
+  yh = __high2half(h);
+  xl = __low2half(l);
+  yl = __high2half(l);
 }
 
 // (2b) Scaled, split and transposed values in sample groups: group g (samples 32 g .. 32 g + 31)
@@ -267,92 +281,95 @@ __global__ void __launch_bounds__(256, 3) lin_center_kernel(int P, long long M, 
                                                          const float* __restrict__ Ef, const double* __restrict__ acc,
                                                          const float* __restrict__ scl, int Pr,
                                                          __half* __restrict__ XI, __half* __restrict__ YI,
-                                                         double* __restrict__ part2) {
+                                                         double* __restrict__ part2, long long nb) {
   // [array][parameter][sample]: rows of 72 halves (144 bytes) keep the 16-byte chunks aligned
   __shared__ __align__(16) __half t[4][64][72];
   __shared__ double red[16][64];
-  const int c0 = blockIdx.y * 64;
+  const int c0 = blockIdx.x * 64;
   const double isw = 1.0 / acc[0];
   // thread (r, q) = (tid % 16, tid / 16): parameters c0 + 4 q .. + 3 of samples s0 + r + 16 k
   const int r = threadIdx.x & 15, q = threadIdx.x >> 4;
   const int c = c0 + 4 * q;
   Tin mo[4];
   float sx[4], sy[4];
-  double sxe[4] = {0.0, 0.0, 0.0, 0.0};  // sums of w Ot E over this thread's samples (16-sample partials in Tin)
-  Tin part[4] = {0, 0, 0, 0};
+  // sample blocks blockIdx.y, + gridDim.y, ... (the grid's y extent is limited)
+  for (long long sb = blockIdx.y; sb < nb; sb += gridDim.y) {
+    double sxe[4] = {0.0, 0.0, 0.0, 0.0};  // sums of w Ot E over this thread's samples (16-sample partials in Tin)
+    Tin part[4] = {0, 0, 0, 0};
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    mo[u] = c + u < P ? (Tin)(acc[2 + c + u] * isw) : (Tin)0;
-    sx[u] = scl[c + u];
-    sy[u] = scl[Pr + c + u];
-  }
-  for (int tt = 0; tt < kCenTiles; ++tt) {
-    const long long s0 = ((long long)blockIdx.x * kCenTiles + tt) * 64;
-    if (s0 >= M) break;
-    __syncthreads();
-    // the tile's 8 loads of 4 values first (memory-level parallelism), then the arithmetic
-    Tin ov[4][4], dv[4][4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const long long sm = s0 + r + 16 * k;
-      if (sm < M && c < P) {
-        load4<Tin, VEC>(O + sm * P, c, P, ov[k]);
-        load4<Tin, VEC>(dEL + sm * P, c, P, dv[k]);
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) ov[k][u] = dv[k][u] = (Tin)0;
-      }
+    for (int u = 0; u < 4; ++u) {
+      mo[u] = c + u < P ? (Tin)(acc[2 + c + u] * isw) : (Tin)0;
+      sx[u] = scl[c + u];
+      sy[u] = scl[Pr + c + u];
     }
+    for (int tt = 0; tt < kCenTiles; ++tt) {
+      const long long s0 = (sb * kCenTiles + tt) * 64;
+      if (s0 >= M) break;
+      __syncthreads();  // the previous tile's stores have read t
+      // the tile's 8 loads of 4 values first (memory-level parallelism), then the arithmetic
+      Tin ov[4][4], dv[4][4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int sl = r + 16 * k;
-      const long long sm = s0 + sl;
-      const bool in = sm < M;
-      const Tin e = in ? (std::is_same<Tin, double>::value ? (Tin)E[sm] : (Tin)Ef[sm]) : (Tin)0;
-      const float rw = in ? rwf[sm] : 0.0f;
-      const Tin ws = in ? (w ? (Tin)w[sm] : (Tin)1) : (Tin)0;
+      for (int k = 0; k < 4; ++k) {
+        const long long sm = s0 + r + 16 * k;
+        if (sm < M && c < P) {
+          load4<Tin, VEC>(O + sm * P, c, P, ov[k]);
+          load4<Tin, VEC>(dEL + sm * P, c, P, dv[k]);
+        } else {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float xv = 0.0f, yv = 0.0f;
-        if (in && c + u < P) {
-          const Tin x = ov[k][u] - mo[u];
-          const Tin ex = e * x;
-          const Tin y = ex + dv[k][u];
-          xv = (float)x * rw * sx[u];
-          yv = (float)y * rw * sy[u];
-          part[u] += ws * ex;
+          for (int u = 0; u < 4; ++u) ov[k][u] = dv[k][u] = (Tin)0;
         }
-        split_half(xv, t[0][4 * q + u][sl], t[1][4 * q + u][sl]);
-        split_half(yv, t[2][4 * q + u][sl], t[3][4 * q + u][sl]);
       }
-    }
-    if ((tt & 3) == 3) {  // every 4 tiles (16 samples of this thread) into double
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        sxe[u] += (double)part[u];
-        part[u] = (Tin)0;
+      for (int k = 0; k < 4; ++k) {
+        const int sl = r + 16 * k;
+        const long long sm = s0 + sl;
+        const bool in = sm < M;
+        const Tin e = in ? (std::is_same<Tin, double>::value ? (Tin)E[sm] : (Tin)Ef[sm]) : (Tin)0;
+        const float rw = in ? rwf[sm] : 0.0f;
+        const Tin ws = in ? (w ? (Tin)w[sm] : (Tin)1) : (Tin)0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float xv = 0.0f, yv = 0.0f;
+          if (in && c + u < P) {
+            const Tin x = ov[k][u] - mo[u];
+            const Tin ex = e * x;
+            const Tin y = ex + dv[k][u];
+            xv = (float)x * rw * sx[u];
+            yv = (float)y * rw * sy[u];
+            part[u] += ws * ex;
+          }
+          split_half2(xv, yv, t[0][4 * q + u][sl], t[1][4 * q + u][sl], t[2][4 * q + u][sl], t[3][4 * q + u][sl]);
+        }
+      }
+      if ((tt & 3) == 3) {  // every 4 tiles (16 samples of this thread) into double
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          sxe[u] += (double)part[u];
+          part[u] = (Tin)0;
+        }
+      }
+      __syncthreads();
+      // 16-byte stores: per array (X, Y), group g of the tile's two and row, the 128-byte row
+      // [hi 0-31 | lo 0-31] in 8 chunks of 8 halves; groups that start at or past Mp are not stored
+      for (int qq = threadIdx.x; qq < 2 * 64 * 16; qq += 256) {
+        const int a = qq >> 10, rr = (qq >> 4) & 63, ch = qq & 15;
+        const int g = ch >> 3, half = (ch >> 2) & 1, sub = ch & 3;
+        if (s0 + 32 * g >= Mp) continue;
+        const uint4 v = *reinterpret_cast<const uint4*>(&t[2 * a + half][rr][32 * g + 8 * sub]);
+        __half* const dst = a == 0 ? XI : YI;
+        const size_t grp = (size_t)(s0 / 32 + g);
+        *reinterpret_cast<uint4*>(dst + (grp * Pr + c0 + rr) * 64 + 32 * half + 8 * sub) = v;
       }
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) red[r][4 * q + u] = sxe[u] + (double)part[u];
     __syncthreads();
-    // 16-byte stores: per array (X, Y), group g of the tile's two and row, the 128-byte row
-    // [hi 0-31 | lo 0-31] in 8 chunks of 8 halves; groups that start at or past Mp are not stored
-    for (int qq = threadIdx.x; qq < 2 * 64 * 16; qq += 256) {
-      const int a = qq >> 10, rr = (qq >> 4) & 63, ch = qq & 15;
-      const int g = ch >> 3, half = (ch >> 2) & 1, sub = ch & 3;
-      if (s0 + 32 * g >= Mp) continue;
-      const uint4 v = *reinterpret_cast<const uint4*>(&t[2 * a + half][rr][32 * g + 8 * sub]);
-      __half* const dst = a == 0 ? XI : YI;
-      const size_t grp = (size_t)(s0 / 32 + g);
-      *reinterpret_cast<uint4*>(dst + (grp * Pr + c0 + rr) * 64 + 32 * half + 8 * sub) = v;
+    if (threadIdx.x < 64) {  // block partial of sum w Ot E, the 16 sample offsets in order
+      double v = red[0][threadIdx.x];
+      for (int k = 1; k < 16; ++k) v += red[k][threadIdx.x];
+      part2[(size_t)sb * Pr + c0 + threadIdx.x] = v;
     }
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) red[r][4 * q + u] = sxe[u] + (double)part[u];
-  __syncthreads();
-  if (threadIdx.x < 64) {  // block partial of sum w Ot E, the 16 sample offsets in order
-    double v = red[0][threadIdx.x];
-    for (int k = 1; k < 16; ++k) v += red[k][threadIdx.x];
-    part2[(size_t)blockIdx.x * Pr + c0 + threadIdx.x] = v;
+    __syncthreads();  // red is read before the next sample block writes it
   }
 }
 
@@ -728,22 +745,22 @@ static cudaError_t launch_lin_t(int P, long long M, const Tin* O, const Tin* dEL
   mark(0);
   // 16-byte loads of the [M][P] inputs when every row starts on a 16-byte boundary
   const bool vec = P % 4 == 0 && reinterpret_cast<uintptr_t>(O) % 16 == 0 && reinterpret_cast<uintptr_t>(dEL) % 16 == 0;
-  const dim3 gcol((unsigned)nb1, (unsigned)((P + 63) / 64));
+  const dim3 gcol((unsigned)((P + 63) / 64), (unsigned)std::min(nb1, 65535));
   if (vec)
-    lin_colsum_kernel<Tin, true><<<gcol, kColBlock, 0, st>>>(P, M, O, dEL, E, w, L.part1, L.mx);
+    lin_colsum_kernel<Tin, true><<<gcol, kColBlock, 0, st>>>(P, M, O, dEL, E, w, L.part1, L.mx, nb1);
   else
-    lin_colsum_kernel<Tin, false><<<gcol, kColBlock, 0, st>>>(P, M, O, dEL, E, w, L.part1, L.mx);
+    lin_colsum_kernel<Tin, false><<<gcol, kColBlock, 0, st>>>(P, M, O, dEL, E, w, L.part1, L.mx, nb1);
   lin_seg_reduce<<<dim3((L1 + 31) / 32, kSeg), 256, 0, st>>>(L1, nb1, L.part1, L.seg);
   lin_final_reduce<<<(L1 + 255) / 256, 256, 0, st>>>(L1, L.seg, L.acc);
   lin_scale_kernel<<<(Pr + 255) / 256, 256, 0, st>>>(P, Pr, L.acc, L.mx, L.scl);
   lin_sample_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, E, w, L.rw, L.Ef);
   mark(1);
   if (vec)
-    lin_center_kernel<Tin, true><<<dim3((unsigned)nb2, Pr / 64), 256, 0, st>>>(
-        P, M, Mp, O, dEL, E, w, L.rw, L.Ef, L.acc, L.scl, Pr, L.XI, L.YI, L.part2);
+    lin_center_kernel<Tin, true><<<dim3(Pr / 64, (unsigned)std::min(nb2, 65535)), 256, 0, st>>>(
+        P, M, Mp, O, dEL, E, w, L.rw, L.Ef, L.acc, L.scl, Pr, L.XI, L.YI, L.part2, nb2);
   else
-    lin_center_kernel<Tin, false><<<dim3((unsigned)nb2, Pr / 64), 256, 0, st>>>(
-        P, M, Mp, O, dEL, E, w, L.rw, L.Ef, L.acc, L.scl, Pr, L.XI, L.YI, L.part2);
+    lin_center_kernel<Tin, false><<<dim3(Pr / 64, (unsigned)std::min(nb2, 65535)), 256, 0, st>>>(
+        P, M, Mp, O, dEL, E, w, L.rw, L.Ef, L.acc, L.scl, Pr, L.XI, L.YI, L.part2, nb2);
   lin_seg_reduce<<<dim3((Pr + 31) / 32, kSeg), 256, 0, st>>>(Pr, nb2, L.part2, L.seg);
   lin_final_reduce<<<(Pr + 255) / 256, 256, 0, st>>>(Pr, L.seg, L.sxe);
   mark(2);
