@@ -76,7 +76,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   const int over0 = off;
   L.rtab = take(8 * 4 * N);
   L.rtds = take(tb == 4 ? 8 * 3 * N : 16);
-  L.geom = take(tb * (N + s.Nn + 6 * s.Nn + 10 * (N + 1)));
+  L.geom = take(tb * (2 * N + s.Nn + 6 * s.Nn + 10 * (N + 1)));
   const int moves_end = off;
   off = over0;
   L.ldet = take(8 * Ut);
@@ -100,7 +100,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.cvec = take(std::max(cv, 8));
   L.scratch = shared0;
   off = std::max(off, align16(shared0 + std::max(scr, 16)));
-  L.geo = take(tb * (N * N + N * s.Nn + (N + 1) * s.Nn));
+  L.geo = take(tb * (N * s.Nn + (N + 1) * s.Nn));
   L.warp_bytes = off;
   int wpb = max_smem / off;
   if (wpb > 16) wpb = 16;

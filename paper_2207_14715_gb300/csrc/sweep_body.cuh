@@ -96,13 +96,15 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   double* rinv = reinterpret_cast<double*>(base + L.rinv);
   double* cvec = reinterpret_cast<double*>(base + L.cvec);
   double* scr = reinterpret_cast<double*>(base + L.scratch);
-  Tb* rEE = reinterpret_cast<Tb*>(base + L.geo);       // [N][N] r_ij
-  Tb* rEN = rEE + s.N * s.N;                            // [N][Nn] r_ia
+  // the pair distances r_ij are formed where a move needs them (the distances of the moving
+  // electron, from the same coordinate differences the tables would hold)
+  Tb* rEN = reinterpret_cast<Tb*>(base + L.geo);       // [N][Nn] r_ia
   // row strides padded by one so that lanes on different nuclei (powers) read different banks
   const int SA = s.N + 1, UP = s.N + 1;
   Tb* Sv = rEN + s.N * s.Nn;                            // [Nn][SA]: Rbar(r_ja) at a*SA + j (its powers formed where used)
   Tb* rnE = reinterpret_cast<Tb*>(base + L.geom);       // [N] r from the proposed position
-  Tb* rnN = rnE + s.N;                                  // [Nn]
+  Tb* roE = rnE + s.N;                                  // [N] r from the current position
+  Tb* rnN = roE + s.N;                                  // [Nn]
   Tb* Snew = rnN + s.Nn;                                // [Nn][6]
   Tb* Upo = Snew + 6 * s.Nn;                            // [5][UP] Rbar(r_ej)^k, current position of e
   Tb* Upn = Upo + 5 * UP;                               // [5][UP] Rbar(r_ej)^k, proposed position
@@ -123,11 +125,6 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   }
   __syncwarp();
   // geometry tables
-  for (DivStep ij(lane, N); ij.hi < N; ij.next(N)) {
-    const int i = ij.hi, j = ij.lo, p = i * N + j;
-    const Tb dx = C.ee(i, j, 0), dy = C.ee(i, j, 1), dz = C.ee(i, j, 2);
-    rEE[p] = i == j ? (Tb)0 : vsqrt(dx * dx + dy * dy + dz * dz);
-  }
   for (DivStep ia(lane, Nn); ia.hi < N; ia.next(Nn)) {
     const int i = ia.hi, a = ia.lo, p = i * Nn + a;
     const Tb dx = C.en(s, i, a, 0), dy = C.en(s, i, a, 1), dz = C.en(s, i, a, 2);
@@ -349,8 +346,11 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
       for (int j = lane; j < N; j += 32) {
         const Tb dx = dnew_e(j, 0), dy = dnew_e(j, 1), dz = dnew_e(j, 2);
         const Tb rnew = j == e ? (Tb)0 : vsqrt(dx * dx + dy * dy + dz * dz);
+        const Tb ox = C.ee(e, j, 0), oy = C.ee(e, j, 1), oz = C.ee(e, j, 2);
+        const Tb rold = j == e ? (Tb)0 : vsqrt(ox * ox + oy * oy + oz * oz);
         rnE[j] = rnew;
-        const Tb uo = (Tb)1 / ((Tb)1 + kap * rEE[e * N + j]), un = (Tb)1 / ((Tb)1 + kap * rnew);
+        roE[j] = rold;
+        const Tb uo = (Tb)1 / ((Tb)1 + kap * rold), un = (Tb)1 / ((Tb)1 + kap * rnew);
         Tb po = (Tb)1, pn = (Tb)1;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -384,7 +384,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           const PadeT<Tb> c = ee_coef_t<Tb>(s, (e < Nup) == (j < Nup));
           Tb f1, f0, t0, t1;
           pade_eval<Tb, false>(c, rnE[j], kap, f1, t0, t1);
-          pade_eval<Tb, false>(c, rEE[e * N + j], kap, f0, t0, t1);
+          pade_eval<Tb, false>(c, roE[j], kap, f0, t0, t1);
           dj += f1 - f0;
         }
       }
@@ -457,7 +457,6 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           R[3 * e + lane] = lane == 0 ? rn[0] : (lane == 1 ? rn[1] : rn[2]);
           if constexpr (!kSameType<Tb, double>) Rds[3 * e + lane] = lane == 0 ? rnd[0] : (lane == 1 ? rnd[1] : rnd[2]);
         }
-        for (int j = lane; j < N; j += 32) rEE[e * N + j] = rEE[j * N + e] = rnE[j];
         for (int a = lane; a < Nn; a += 32) {
           rEN[e * Nn + a] = rnN[a];
           Sv[a * SA + e] = Snew[a * 6 + 1];
@@ -503,7 +502,6 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           R[3 * e + lane] = lane == 0 ? rn[0] : (lane == 1 ? rn[1] : rn[2]);
           if constexpr (!kSameType<Tb, double>) Rds[3 * e + lane] = lane == 0 ? rnd[0] : (lane == 1 ? rnd[1] : rnd[2]);
         }
-        for (int j = lane; j < N; j += 32) rEE[e * N + j] = rEE[j * N + e] = rnE[j];
         for (int a = lane; a < Nn; a += 32) {
           rEN[e * Nn + a] = rnN[a];
           Sv[a * SA + e] = Snew[a * 6 + 1];
