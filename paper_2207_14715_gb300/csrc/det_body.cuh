@@ -79,7 +79,6 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
   double* vg = reinterpret_cast<double*>(base + L.vg);
   Tb* G = reinterpret_cast<Tb*>(base + L.G);
   Tb* LJ = reinterpret_cast<Tb*>(base + L.LJ);
-  Tb* Phi = reinterpret_cast<Tb*>(base + L.Phi);
   double* PhiD = reinterpret_cast<double*>(base + L.PhiD);
   Tb* Lphi = reinterpret_cast<Tb*>(base + L.Lphi);
   Tb* Gphi = reinterpret_cast<Tb*>(base + L.Gphi);
@@ -102,7 +101,7 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
   for (DivStep eq(lane, nev); eq.hi < N; eq.next(nev)) {
     const int e = eq.hi, q = eq.lo;
     const Tb* ob = OB + ((size_t)w * N + e) * 5 * nev;
-    const Tb v = ob[q], x = ob[nev + q], y = ob[2 * nev + q], z = ob[3 * nev + q], lp = ob[4 * nev + q];
+    const Tb x = ob[nev + q], y = ob[2 * nev + q], z = ob[3 * nev + q], lp = ob[4 * nev + q];
     const Tb lq = lp + (Tb)2 * (G[3 * e] * x + G[3 * e + 1] * y + G[3 * e + 2] * z);
     Lphi[e * nev + q] = lq;
     if (q < nevd) {
@@ -113,7 +112,6 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
       Gphi[(e * nevd + q) * 3 + 1] = y;
       Gphi[(e * nevd + q) * 3 + 2] = z;
     }
-    Phi[e * nev + q] = v;
   }
   __syncwarp();
 
@@ -327,8 +325,11 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
         const int n = s.n[sp], e0 = sp ? Nup : 0;
         const Tb* g = Gam[sp] + l * n;
         const Tb* a = Aux[sp] + l * n;
+        // orbital values from the workspace (not staged in shared memory: the walker region
+        // then fits 16 walkers per SM)
+        const Tb* pv = OB + ((size_t)w * N + e0) * 5 * nev + kc;
         for (int e = 0; e < n; ++e) {
-          const Tb ph = Phi[(e0 + e) * nev + kc], lph = Lphi[(e0 + e) * nev + kc];
+          const Tb ph = pv[(size_t)e * 5 * nev], lph = Lphi[(e0 + e) * nev + kc];
           o += g[e] * ph;
           kk += a[e] * ph + g[e] * lph;
         }

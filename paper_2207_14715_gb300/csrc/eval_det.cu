@@ -61,7 +61,6 @@ int make_det_layout(const SysDev& s, int tb, int max_smem, DetLayout& L, bool ca
   L.vg = take(8 * 3 * N);
   L.G = take(tb * 3 * N);
   L.LJ = take(tb * N);
-  L.Phi = take(tb * N * s.n_ev);
   L.PhiD = take(8 * N * std::max(s.n_ev_det, 1));
   L.Lphi = take(tb * N * s.n_ev);
   L.Gphi = take(tb * N * s.n_ev_det * 3);

@@ -31,7 +31,7 @@ struct OrbLayout {
 
 struct DetLayout {
   int wpb = 0, warp_bytes = 0;
-  int vg, G, LJ, Phi, PhiD, Lphi, Gphi, Bt0, Bt1, ldet, dsg, tdet, Wdet, Tdet, rk, scratch;
+  int vg, G, LJ, PhiD, Lphi, Gphi, Bt0, Bt1, ldet, dsg, tdet, Wdet, Tdet, rk, scratch;
   int G0, G1;  // lane-group size per spin for the LU
 };
 
