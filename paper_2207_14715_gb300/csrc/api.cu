@@ -243,6 +243,12 @@ int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc) 
   d.tab_x[1] = (const int*)(B + o_tx1);
   d.tab_det[0] = (const int*)(B + o_td0);
   d.tab_det[1] = (const int*)(B + o_td1);
+  d.tab_ksq = 0;
+  for (int sp = 0; sp < 2; ++sp)
+    for (size_t u = 0; u * vbq::kTabStride < h.tab_det[sp].size(); ++u) {
+      const int k = h.tab_det[sp][u * vbq::kTabStride];
+      d.tab_ksq += k * k;
+    }
   d.tab_xl[0] = (const int*)(B + o_txl0);
   d.tab_xl[1] = (const int*)(B + o_txl1);
   d.n_x[0] = (int)h.tab_x[0].size();

@@ -84,7 +84,7 @@ __device__ __forceinline__ void dettab_body(const SysDev& s, const DetTabLayout&
   double* tdet = reinterpret_cast<double*>(base + L.tdet);
   double* Wdet = reinterpret_cast<double*>(base + L.Wdet);
   double* rk = reinterpret_cast<double*>(base + L.rk);
-  double* Minv = reinterpret_cast<double*>(base + L.Minv);  // [Utot][16]
+  double* Minv = reinterpret_cast<double*>(base + L.Minv);  // per determinant its k x k minor inverse, packed
   double* Gam = reinterpret_cast<double*>(base + L.Gam);    // [n_x][n] of one spin: h = Gamma B
   Tb* G = reinterpret_cast<Tb*>(base + L.G);
 
@@ -93,7 +93,10 @@ __device__ __forceinline__ void dettab_body(const SysDev& s, const DetTabLayout&
   __syncwarp();
 
   // ---- per spin: reference LU, tables, every determinant's ratio and trace ----
+  int moff_spin = 0;  // start of the spin's packed minor inverses
+  int mstart[2] = {0, 0};
   for (int sp = 0; sp < 2; ++sp) {
+    mstart[sp] = moff_spin;
     const int n = s.n[sp], e0 = sp ? Nup : 0, nx = s.n_x[sp], uo = sp ? U0 : 0;
     if (n == 0) {
       for (int u = lane; u < s.U[sp]; u += 32) {
@@ -124,12 +127,10 @@ __device__ __forceinline__ void dettab_body(const SysDev& s, const DetTabLayout&
     }
     __syncwarp();
     double lg0 = 0.0, sg0 = 1.0;
-    group_lu_inverse(A, Bs, perm, n, lg.gl, Gs, act, lg0, sg0);
+    double* B = Bd[sp];
+    group_lu_inverse(A, B, perm, n, lg.gl, Gs, act, lg0, sg0);
     lg0 = __shfl_sync(kFull, lg0, 0);
     sg0 = __shfl_sync(kFull, sg0, 0);
-    __syncwarp();
-    double* B = Bd[sp];
-    for (int i = lane; i < n * n; i += 32) B[i] = Bs[i];
     __syncwarp();
     // Y0 = B L_0 (into A), t0 = tr Y0
     for (int i = lane; i < n * n; i += 32) {
@@ -166,10 +167,22 @@ __device__ __forceinline__ void dettab_body(const SysDev& s, const DetTabLayout&
     __syncwarp();
     for (int i = lane; i < n * nx; i += 32) Yh[i] = Bs[i];
     __syncwarp();
-    // every determinant of the spin: lanes over determinants
-    for (int u = lane; u < s.U[sp]; u += 32) {
-      const int* tab = s.tab_det[sp] + u * kTabStride;
-      const int k = __ldg(tab);
+    // every determinant of the spin: lanes over determinants; the packed minor inverses start
+    // at the running sum of k^2 (a scan over each round of 32 determinants)
+    int mbase = moff_spin;
+    for (int ub = 0; ub < s.U[sp]; ub += 32) {
+      const int u = ub + lane;
+      const int* tab = s.tab_det[sp] + (u < s.U[sp] ? u : 0) * kTabStride;
+      const int k = u < s.U[sp] ? __ldg(tab) : 0;
+      int incl = k * k;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int moff = mbase + incl - k * k;
+      mbase += __shfl_sync(kFull, incl, 31);
+      if (u >= s.U[sp]) continue;
       const double sgu = (double)__ldg(tab + 1);
       int S[kMaxExc], Q[kMaxExc];
 #pragma unroll
@@ -193,12 +206,14 @@ __device__ __forceinline__ void dettab_body(const SysDev& s, const DetTabLayout&
       ldet[uo + u] = ok ? lg0 + log(fabs(dm)) : -INFINITY;
       dsg[uo + u] = ok ? sg0 * sgu * (dm > 0.0 ? 1.0 : -1.0) : 0.0;
       tdet[uo + u] = ok ? t0 + tr : 0.0;
-      double* mo = Minv + (size_t)(uo + u) * 16;
+      double* mo = Minv + moff;
 #pragma unroll
       for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int jp = 0; jp < 4; ++jp) mo[4 * j + jp] = ok ? Mi[j][jp] : 0.0;
+        for (int jp = 0; jp < 4; ++jp)
+          if (j < k && jp < k) mo[k * j + jp] = ok ? Mi[j][jp] : 0.0;
     }
+    moff_spin = mbase;
     __syncwarp();
   }
 
@@ -234,6 +249,8 @@ __device__ __forceinline__ void dettab_body(const SysDev& s, const DetTabLayout&
     for (int i = lane; i < nx * n; i += 32) {
       const int x = i / n, o = i - x * n;
       double gsum = 0.0;
+      const int k0 = __ldg(s.tab_det[sp]);
+      int mo = mstart[sp] + k0 * k0;  // packed minor inverse of determinant u
       for (int u = 1; u < s.U[sp]; ++u) {
         const int* tab = s.tab_det[sp] + u * kTabStride;
         const int k = __ldg(tab);
@@ -242,7 +259,8 @@ __device__ __forceinline__ void dettab_body(const SysDev& s, const DetTabLayout&
           if (__ldg(tab + 2 + j) == o) jo = j;
           if (__ldg(tab + 2 + kMaxExc + j) == x) jx = j;
         }
-        if (jo >= 0 && jx >= 0) gsum = fma(Wdet[uo + u], Minv[(size_t)(uo + u) * 16 + 4 * jx + jo], gsum);
+        if (jo >= 0 && jx >= 0) gsum = fma(Wdet[uo + u], Minv[mo + k * jx + jo], gsum);
+        mo += k * k;
       }
       A[i] = gsum;
     }

@@ -52,7 +52,7 @@ int make_dettab_layout(const SysDev& s, int tb, int max_smem, DetTabLayout& L) {
   L.Y0 = take(8 * std::max(s.n[0] * s.n_x[0], 1));
   L.Y1 = take(8 * std::max(s.n[1] * s.n_x[1], 1));
   L.A = take(8 * std::max(nmax * nmax, nxmax * nmax));
-  L.Bs = take(8 * std::max(nmax * nmax, nxmax * nmax));
+  L.Bs = take(8 * nxmax * nmax);
   L.perm = take(4 * nmax);
   L.Ls = take(8 * nmax * nevd);
   L.ldet = take(8 * Ut);
@@ -60,7 +60,7 @@ int make_dettab_layout(const SysDev& s, int tb, int max_smem, DetTabLayout& L) {
   L.tdet = take(8 * Ut);
   L.Wdet = take(8 * Ut);
   L.rk = take(8 * std::max(s.nterm, 1));
-  L.Minv = take(8 * 16 * Ut);
+  L.Minv = take(8 * std::max(s.tab_ksq, 1));  // the k_u x k_u minor inverses, packed
   L.Gam = take(8 * nxmax * nmax);
   L.warp_bytes = off;
   int wpb = max_smem / off;

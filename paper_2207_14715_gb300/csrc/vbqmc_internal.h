@@ -133,6 +133,7 @@ struct SysDev {
   int n_x[2];
   const int* tab_x[2];
   const int* tab_det[2];
+  int tab_ksq;                         // sum over the determinants of both spins of k_u^2
   const int* tab_xl[2];
   const int* term_det;
   const double* term_coef;
