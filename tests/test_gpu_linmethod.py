@@ -1,8 +1,9 @@
 """Linear-method estimators on the GPU (Sec. 2.3.1, Eqs. Hi0, H0j, Hij, Sij) against the oracle.
 
-Tolerance: products of float-rounded centred values accumulated in float over chunks of at
-most 16384 samples and summed in double: each entry within 1e-5 of the matrix scale
-(max |entry|) for float inputs and 2e-6 for double inputs."""
+Tolerance: centred values rounded to float and split into high and low halves, products
+accumulated on the tensor cores in FP32 over 64 samples at a time, then in FP32 registers over
+a chunk and in double over the chunks: each entry within 1e-5 of the matrix scale (max |entry|)
+for float inputs and 2e-6 for double inputs."""
 import numpy as np
 import pytest
 
@@ -50,7 +51,10 @@ def check(got, ref, tol):
     assert abs(got["E0"][0] - ref["E0"]) < 1e-12 * max(1.0, abs(ref["E0"]))
 
 
-@pytest.mark.parametrize("M,P,weights", [(1, 1, False), (300, 7, False), (5000, 37, True), (40000, 130, False)])
+# P = 64 and 400: 16-byte loads of the inputs (P a multiple of 4); P = 1501: 168 output tiles,
+# more than one wave of CTAs, ragged tiles and columns
+@pytest.mark.parametrize("M,P,weights", [(1, 1, False), (300, 7, False), (5000, 37, True), (40000, 130, False),
+                                         (20000, 64, True), (600, 1501, False)])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_lin_matrices_match_oracle(vb, orc, M, P, weights, precision):
     O, dE, E, w = synthetic(M, P, M + P, weights)
