@@ -53,16 +53,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 }
 
 // ---- TMA ---------------------------------------------------------------------------
-// 2-D tile load global -> shared through a tensor map; completion counted on 'bar'.
-// x is the innermost coordinate (its byte offset must be a multiple of 16).
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-          "r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
-      : "memory");
-}
-
 // 3-D tile load (x innermost, its byte offset a multiple of 16; y, z free)
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
   asm volatile(
@@ -88,20 +78,6 @@ __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
-// whole warp: 16 consecutive 32-bit columns of TMEM lanes (lane base of taddr) + warp lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // whole warp: issue the load of 16 consecutive columns without waiting (registers valid only
 // after tmem_wait_ld)
 __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t r[16]) {
@@ -124,17 +100,6 @@ __device__ __forceinline__ uint64_t smem_desc_k128(uint32_t saddr) {
   d |= (uint64_t)(1024 >> 4) << 32;               // stride-dimension byte offset: 8 rows
   d |= (uint64_t)1 << 46;                         // descriptor version
   d |= (uint64_t)2 << 61;                         // 128-byte swizzle
-  return d;
-}
-// The same for rows of 64 bytes with the 64-byte swizzle: 8-row groups 512 bytes apart (tile
-// base 512-byte aligned).
-__device__ __forceinline__ uint64_t smem_desc_k64(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);         // start address
-  d |= (uint64_t)1 << 16;                         // leading-dimension byte offset (unused here)
-  d |= (uint64_t)(512 >> 4) << 32;                // stride-dimension byte offset: 8 rows
-  d |= (uint64_t)1 << 46;                         // descriptor version
-  d |= (uint64_t)4 << 61;                         // 64-byte swizzle
   return d;
 }
 // Instruction descriptor: D f32, A and B f16, both K-major, M x N (M = 128: N a multiple of 16).
