@@ -110,9 +110,10 @@ const char* vbqmc_last_error(void);
  * Host-side set-up (Sec. 2.1-2.2): validates the description, expands every structure into
  * signed determinants (Eq. PhiI and the expansion after it: 2^Npairs terms, self pairs
  * i = j give one term), merges identical determinants, derives the cusp-preserving e-e-n
- * coefficients c = B theta (the coefficients fixed "in order not to alter the cusp
- * conditions", Sec. 2.1), builds the orbital-excitation tables (Sec. 2.2) and uploads
- * everything to the device.  Synchronous.  Errors: VBQMC_ERR_ARG for inconsistent input,
+ * coefficients c = B theta (the coefficients held fixed so that the cusp conditions
+ * still hold, Sec. 2.1), builds the orbital-excitation tables (Sec. 2.2), chooses per-
+ * determinant inverses or reference-determinant tables for the determinant part (see
+ * vbqmc_use_tables) and uploads everything to the device.  Synchronous.  Errors: VBQMC_ERR_ARG for inconsistent input,
  * VBQMC_ERR_CAPACITY if a size exceeds the kernels' limits (N <= 64, n_up <= 32, M <= 1024). */
 int vbqmc_set_system(vbqmc_ctx* ctx, int sys_id, const vbqmc_system_desc* desc);
 
@@ -427,8 +428,11 @@ int vbqmc_launch_info(vbqmc_ctx* ctx, int sys_id, int precision, int* out);
  * nucleus derivatives available); on = 1: the first determinant of each spin as reference, its
  * inverse B and the tables T = B Phi_X, every other determinant as a k x k minor (k <= 4):
  * VMC sweeps and evaluations keep no walker state, orbital-excitation and nucleus derivatives
- * are refused.  vbqmc_set_system takes the tables only when the per-determinant inverses of one
- * walker do not fit in shared memory.  Errors: VBQMC_ERR_NOSYS, VBQMC_ERR_UNSUPPORTED (a
+ * are refused.  vbqmc_set_system takes the tables when the per-determinant inverses of one
+ * walker do not fit in shared memory, and, for systems without orbital-excitation parameters,
+ * when the per-determinant sweep region of a walker exceeds 48 KB, or 32 KB with 16 or more
+ * unique determinants of a spin (few walkers per SM: the measured crossover on molecules of
+ * 2-32 electrons).  Errors: VBQMC_ERR_NOSYS, VBQMC_ERR_UNSUPPORTED (a
  * determinant differs from the reference in more than 4 columns), VBQMC_ERR_CAPACITY (on = 0
  * but the inverses do not fit). */
 int vbqmc_use_tables(vbqmc_ctx* ctx, int sys_id, int on);
