@@ -275,7 +275,7 @@ __device__ __forceinline__ void split_half2(float x, float y, __half& xh, __half
 // contiguous 16 KB block.  A block of this kernel transposes 64 samples x 64 parameters through
 // shared memory: reads along parameters and writes along samples are both coalesced.
 template <class Tin, bool VEC>
-__global__ void __launch_bounds__(256, 3) lin_center_kernel(int P, long long M, long long Mp, const Tin* __restrict__ O,
+__global__ void __launch_bounds__(256, 4) lin_center_kernel(int P, long long M, long long Mp, const Tin* __restrict__ O,
                                                          const Tin* __restrict__ dEL, const double* __restrict__ E,
                                                          const double* __restrict__ w, const float* __restrict__ rwf,
                                                          const float* __restrict__ Ef, const double* __restrict__ acc,
