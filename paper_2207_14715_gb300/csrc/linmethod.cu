@@ -427,32 +427,10 @@ __device__ __forceinline__ void drain(uint32_t base, float acc[kTb]) {
   }
 }
 
-// Pacing of the CTAs that share a chunk (they read the same X and Y rows, through L2): the copy
-// thread publishes its step every kProgEvery steps and, while a started peer is more than
-// kLead steps behind, waits for it, at most kPaceNs per check.  The wait is a hint for L2
-// reuse only: it never fails, and a peer that has not started (-1) or has finished is not
-// waited for.
-constexpr int kProgEvery = 16;
-constexpr int kLead = 32;
-constexpr uint64_t kPaceNs = 20000;
-__device__ __forceinline__ void pace(int* peers, int me, int n, int ks) {
-  __stcg(peers + me, ks);
-  const uint64_t t0 = global_ns();
-  for (;;) {
-    int lo = ks;
-    for (int t = 0; t < n; ++t) {  // independent L2 reads (not cached in L1)
-      const int p = __ldcv(peers + t);
-      if (p >= 0 && p < lo) lo = p;
-    }
-    if (ks - lo <= kLead || global_ns() - t0 > kPaceNs) return;
-    __nanosleep(256);
-  }
-}
-
 __global__ void __launch_bounds__(kTcThreads, 1)
     lin_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tBX,
                   const __grid_constant__ CUtensorMap tBY, int Pa, int Pb, long long M, long long chunk,
-                  double* __restrict__ part, int* __restrict__ prog, int* __restrict__ err) {
+                  double* __restrict__ part, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + kStages * kStageBytes);  // [kStages] copies landed
@@ -495,11 +473,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (warp == kCopyWarp) {
     if (lane == 0) {
-      int* const peers = prog + (size_t)blockIdx.y * gridDim.x;  // the chunk's CTAs, one per tile
       int loaded = 0;
       for (int ks = 0; ks < nsteps; ++ks) {
         const int st = ks % kStages;
-        if ((ks & (kProgEvery - 1)) == 0) pace(peers, (int)blockIdx.x, (int)gridDim.x, ks);
         if (ks >= kStages) {  // the stage's previous MMAs must be done
           if (*abort_flag) break;
           if (!mbar_wait(&empty[st], (uint32_t)((ks / kStages - 1) & 1), kWaitNs)) {
@@ -514,7 +490,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tma_load_3d(b_tile(st) + kHBytes, &tBY, 0, j0, g, &full[st]);
         loaded = ks + 1;
       }
-      __stcg(peers + blockIdx.x, nsteps);  // done: never hold a peer back
       // after an abort, the copies that may still be in flight land before the CTA ends
       if (*abort_flag)
         for (int ks = max(0, loaded - kStages); ks < loaded; ++ks)
@@ -657,7 +632,6 @@ struct LinWs {
   float *scl, *rw, *Ef;
   __half *XI, *YI;
   int* err;
-  int* prog;
   size_t bytes;
 };
 LinWs carve(void* ws, int P, long long M, int nchunk) {
@@ -686,7 +660,6 @@ LinWs carve(void* ws, int P, long long M, int nchunk) {
   w.YI = reinterpret_cast<__half*>(take(sizeof(__half) * (size_t)Pr * 2 * Mp));
   w.part = reinterpret_cast<double*>(take(sizeof(double) * (size_t)nchunk * 2 * Pa * Pb));
   w.err = reinterpret_cast<int*>(take(sizeof(int)));
-  w.prog = reinterpret_cast<int*>(take(sizeof(int) * (size_t)nchunk * (rows_a(P) / kTa) * (rows_b(P) / kTb)));
   w.bytes = off;
   return w;
 }
@@ -739,8 +712,6 @@ static cudaError_t launch_lin_t(int P, long long M, const Tin* O, const Tin* dEL
   if (L.bytes > ws_bytes) return cudaErrorInvalidValue;  // workspace sized for another grid
   cudaError_t e = cudaMemsetAsync(L.mx, 0, sizeof(unsigned) * (2 + 2 * (size_t)P), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(L.err, 0, sizeof(int), st);
-  if (e == cudaSuccess)  // -1: not started
-    e = cudaMemsetAsync(L.prog, 0xff, sizeof(int) * (size_t)G.nchunk * (Pa / kTa) * (Pb / kTb), st);
   if (e != cudaSuccess) return e;
   mark(0);
   // 16-byte loads of the [M][P] inputs when every row starts on a 16-byte boundary
@@ -774,7 +745,7 @@ static cudaError_t launch_lin_t(int P, long long M, const Tin* O, const Tin* dEL
   if (e != cudaSuccess) return e;
   const int ntile = (Pa / kTa) * (Pb / kTb);
   lin_tc_kernel<<<dim3(ntile, G.nchunk), kTcThreads, kTcSmem, st>>>(mA, mBX, mBY, Pa, Pb, M, G.chunk, L.part,
-                                                                     L.prog, L.err);
+                                                                     L.err);
   mark(3);
   const long long nq = std::max<long long>((long long)P * P, 1);
   lin_reduce_kernel<<<(int)((nq + 255) / 256), 256, 0, st>>>(P, Pa, Pb, Pr, G.nchunk, L.part, L.acc, L.sxe, L.scl,
