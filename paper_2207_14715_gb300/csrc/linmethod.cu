@@ -350,11 +350,12 @@ __global__ void __launch_bounds__(256, 4) lin_center_kernel(int P, long long M, 
       }
       __syncthreads();
       // 16-byte stores: per array (X, Y), group g of the tile's two and row, the 128-byte row
-      // [hi 0-31 | lo 0-31] in 8 chunks of 8 halves; groups that start at or past Mp are not stored
+      // [hi 0-31 | lo 0-31] in 8 chunks of 8 halves; groups that start at or past Mp, and rows
+      // past the tensor maps' extent (read as zeros by the copy engine), are not stored
       for (int qq = threadIdx.x; qq < 2 * 64 * 16; qq += 256) {
         const int a = qq >> 10, rr = (qq >> 4) & 63, ch = qq & 15;
         const int g = ch >> 3, half = (ch >> 2) & 1, sub = ch & 3;
-        if (s0 + 32 * g >= Mp) continue;
+        if (s0 + 32 * g >= Mp || c0 + rr >= rows_m(P)) continue;
         const uint4 v = *reinterpret_cast<const uint4*>(&t[2 * a + half][rr][32 * g + 8 * sub]);
         __half* const dst = a == 0 ? XI : YI;
         const size_t grp = (size_t)(s0 / 32 + g);

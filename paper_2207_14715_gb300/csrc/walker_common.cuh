@@ -64,15 +64,35 @@ __device__ __forceinline__ dsf nuc_coord_ds(const SysDev& s, int a, int d) {
 template <bool DERIV>
 __device__ __forceinline__ void basis_at_f(const SysDev& s, int lane, const dsf* r3, float* bv, float* bx, float* by,
                                            float* bz, float* bl, int cs = 1) {
-  for (int t = lane; t < s.S; t += 32) {
+  // the displacement from each nucleus once (lane a: nucleus a), shared by shuffles with the
+  // lanes of that nucleus's shells (more than 32 nuclei: each shell forms its own)
+  const bool shuf = s.Nn <= 32;
+  float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+  if (shuf && lane < s.Nn) {
+    cx = ds_diff_f(r3[0], nuc_coord_ds(s, lane, 0));
+    cy = ds_diff_f(r3[1], nuc_coord_ds(s, lane, 1));
+    cz = ds_diff_f(r3[2], nuc_coord_ds(s, lane, 2));
+  }
+  for (int t0 = 0; t0 < s.S; t0 += 32) {  // every lane takes part in each round (the shuffles)
+    const int t = t0 + lane;
+    const bool act = t < s.S;
     // one 16-byte record per shell, in the order of l
-    const int4 p = __ldg(reinterpret_cast<const int4*>(s.sh_pack_f) + t);
+    const int4 p = act ? __ldg(reinterpret_cast<const int4*>(s.sh_pack_f) + t) : make_int4(0, 0, 0, 0);
     const int c = p.x & 0xffff, l = p.x >> 16, f = p.y, sh = p.z;
-    const float dx = ds_diff_f(r3[0], nuc_coord_ds(s, c, 0)), dy = ds_diff_f(r3[1], nuc_coord_ds(s, c, 1)),
-                dz = ds_diff_f(r3[2], nuc_coord_ds(s, c, 2));
-    gto_shell<float, DERIV>(l, __int_as_float(p.w), s.sh_norm_f + 6 * sh, dx, dy, dz,
-                            bv + f * cs, DERIV ? bx + f * cs : nullptr, DERIV ? by + f * cs : nullptr,
-                            DERIV ? bz + f * cs : nullptr, DERIV ? bl + f : nullptr, cs);
+    float dx, dy, dz;
+    if (shuf) {
+      dx = __shfl_sync(kFull, cx, c);
+      dy = __shfl_sync(kFull, cy, c);
+      dz = __shfl_sync(kFull, cz, c);
+    } else {
+      dx = ds_diff_f(r3[0], nuc_coord_ds(s, c, 0));
+      dy = ds_diff_f(r3[1], nuc_coord_ds(s, c, 1));
+      dz = ds_diff_f(r3[2], nuc_coord_ds(s, c, 2));
+    }
+    if (act)
+      gto_shell<float, DERIV>(l, __int_as_float(p.w), s.sh_norm_f + 6 * sh, dx, dy, dz,
+                              bv + f * cs, DERIV ? bx + f * cs : nullptr, DERIV ? by + f * cs : nullptr,
+                              DERIV ? bz + f * cs : nullptr, DERIV ? bl + f : nullptr, cs);
   }
 }
 
