@@ -786,10 +786,10 @@ def lin_method_timing(ctx, vbqmc, dev, steps, pk, M=1 << 20):
     ph = list(ctx.kernel_times().values())
     ctx.set_kernel_timing(False)
     flops = 2 * 2.0 * M * P * P  # S and H products
-    Pa, Pb, Pr = -(-P // 128) * 128, -(-P // 112) * 112, max(-(-P // 64) * 64, 128)
+    Pa, Pb, Pm = -(-P // 128) * 128, -(-P // 112) * 112, max(P, 128)
     mma = 3 * 2.0 * M * Pa * (2 * Pb)
     in_bytes = 2 * M * P * 4
-    xy_bytes = 2 * Pr * M * 2 * 2  # X and Y, high and low halves
+    xy_bytes = 2 * Pm * M * 2 * 2  # X and Y, high and low halves, the rows the tensor maps cover
     hbm, bf16 = pk["hbm_gbs"], pk["bf16_tflops"]
     return {"samples": M, "params": P, "ms": ms, "algorithmic_tflops": flops / (ms * 1e-3) / 1e12,
             "input_bytes": in_bytes + M * 8,
