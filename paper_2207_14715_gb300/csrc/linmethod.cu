@@ -15,8 +15,9 @@
 //  (2) per parameter a power-of-two scale for X = sqrt(w) Ot and Y = sqrt(w) (E Ot + dE) that
 //      bounds the scaled values by 2^14, then X and Y scaled, split into high and low half
 //      precision parts (v = hi + lo with hi = half(v), lo = half(v - hi): 22 significant bits,
-//      the accuracy of a float to 2^-22) and transposed to parameter-major rows; the same pass
-//      forms sum w Ot E from the centred values (block partials, fixed-order sum);
+//      the accuracy of a float to 2^-22) and transposed into 32-sample groups of parameter
+//      rows (each row 32 high halves then 32 low halves); the same pass forms sum w Ot E from
+//      the centred values (block partials, fixed-order sum);
 //  (3) the products on the tensor cores (tcgen05, kind::f16, FP32 accumulators in tensor
 //      memory): per output tile of 128 parameters i x 112 parameters j and chunk of samples,
 //      D_S[i][j] = sum_s X_si X_sj and D_H[i][j] = sum_s X_si Y_sj in one MMA of N = 224 whose B
@@ -25,7 +26,7 @@
 //  (4) the chunk partials added in double in a fixed order, unscaled and divided by sum w.
 // The half-precision split runs the tensor cores at twice the rate of the TF32 split with the
 // same accuracy, because the per-parameter scales keep every value in the normal half range;
-// 112-wide i tiles cover 400 parameters with 448 columns instead of 512.
+// 112-wide j tiles cover 400 parameters with 448 columns instead of 512.
 #include <cuda_fp16.h>
 
 #include <algorithm>
