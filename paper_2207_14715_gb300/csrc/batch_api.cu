@@ -437,6 +437,17 @@ int vbqmc_batch_vmc_steps(vbqmc_batch* b, double* const* R, int nsweeps, double 
   return VBQMC_OK;
 }
 
+// The per-phase walker counts of a new one-launch plan into the staged and device copies of the
+// system table (the tuner launches from the copy staged at its start), after the previous
+// launches have read it.
+static cudaError_t refresh_walker_counts(vbqmc_batch* b, cudaStream_t st) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < b->n; ++k)
+    for (int q = 0; q < 3; ++q) b->h_sys[k].cw[q] = b->sys[k].cw[q];
+  return cudaMemcpyAsync(b->d_sys, b->h_sys, sizeof(BatchSys) * b->n, cudaMemcpyHostToDevice, st);
+}
+
 int vbqmc_batch_tune(vbqmc_batch* b, double* const* R, double* const* logpsi, double* const* sign, double* const* eloc,
                      void* stream) {
   if (!b || !R || !logpsi || !sign || !eloc) return fail(VBQMC_ERR_ARG, "null argument");
@@ -523,7 +534,8 @@ int vbqmc_batch_tune(vbqmc_batch* b, double* const* R, double* const* logpsi, do
           p.persist = persist;
           rc = build_fused_plan(b);
           if (rc) break;
-          e = launch_fused(b, false, true, false, st);
+          e = refresh_walker_counts(b, st);
+          if (e == cudaSuccess) e = launch_fused(b, false, true, false, st);
           if (e == cudaSuccess) e = cudaEventRecord(e0, st);
           for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_fused(b, false, true, false, st);
           if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -541,6 +553,7 @@ int vbqmc_batch_tune(vbqmc_batch* b, double* const* R, double* const* logpsi, do
     p.cap = bc;
     p.persist = bp;
     if (rc == VBQMC_OK && e == cudaSuccess) rc = build_fused_plan(b);
+    if (rc == VBQMC_OK && e == cudaSuccess) e = refresh_walker_counts(b, st);
     b->fused = best_fused <= best_kinds;
   }
   b->tune_ms[0] = best_kinds / 3.0f;

@@ -29,6 +29,9 @@ __global__ void __launch_bounds__(MAXT, 1) batch_fused_kernel(const BatchSys* __
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   const int wl = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned dsmem;  // this launch's dynamic shared memory: no warp's region may pass its end
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsmem));
+  auto fit = [&](int c, int bytes) { return min(c, (int)(dsmem / (unsigned)max(bytes, 1))); };
   for (;;) {
     __syncthreads();  // every warp is done with the previous item's shared memory
     if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
@@ -38,7 +41,9 @@ __global__ void __launch_bounds__(MAXT, 1) batch_fused_kernel(const BatchSys* __
     const BatchItem item = items[it];
     const BatchSys& b = sys[item.sys];
     // per-walker phases: warp wl < c takes walkers wl, wl + c, ... of the tile
-    const int cs = b.cw[0], cj = b.cw[1], cd = b.cw[2];
+    const int cs = fit(b.cw[0], b.sweep.warp_bytes), cj = fit(b.cw[1], b.lay.jas.warp_bytes),
+              cd = fit(b.cw[2], b.dev.msd ? b.lay.tab.warp_bytes : b.lay.det.warp_bytes),
+              co = fit(nw, b.lay.orb.warp_bytes);
     // systems on reference-determinant tables (many determinants per structure) carry the
     // reference inverse and tables through their moves and keep no walker state
     if (sweep && wl < cs)
@@ -60,9 +65,10 @@ __global__ void __launch_bounds__(MAXT, 1) batch_fused_kernel(const BatchSys* __
                          static_cast<Tb*>(b.JG), static_cast<Tb*>(b.JL), b.JS);
     __syncthreads();
     const int npair = item.count * b.dev.N;
-    for (int p = wl; p < npair; p += nw)
-      orbital_body<Tb>(b.dev, b.lay.orb, (long long)item.first * b.dev.N + p, smem + wl * b.lay.orb.warp_bytes, b.R,
-                       static_cast<Tb*>(b.OB), b.OD);
+    if (wl < co)
+      for (int p = wl; p < npair; p += co)
+        orbital_body<Tb>(b.dev, b.lay.orb, (long long)item.first * b.dev.N + p, smem + wl * b.lay.orb.warp_bytes,
+                         b.R, static_cast<Tb*>(b.OB), b.OD);
     __syncthreads();
     const bool d = derivs && b.O && b.dev.P > 0;
     if (wl < cd)
