@@ -54,6 +54,22 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   L.tab = s.msd ? 1 : 0;
   L.G0 = group_size(s.n[0]);
   L.G1 = group_size(s.n[1]);
+  // a double instruction costs the same whatever the number of active lanes: the ratios take
+  // the lane-group size with the fewest double instructions per move (passes over the
+  // determinants times the products per lane plus the reduction levels)
+  auto ratio_group = [](int n, int U, int G) {
+    int best = G, bc = 1 << 30;
+    for (int g = 1, lg = 0; g <= G; g <<= 1, ++lg) {
+      const int per = 32 / g, c = ((U + per - 1) / per) * ((n + g - 1) / g + lg);
+      if (c < bc) {
+        bc = c;
+        best = g;
+      }
+    }
+    return best;
+  };
+  L.RG0 = ratio_group(s.n[0], s.U[0], L.G0);
+  L.RG1 = ratio_group(s.n[1], s.U[1], L.G1);
   L.nocc_max = std::max(std::max(s.nocc[0], s.nocc[1]), 1);
   L.R = take(8 * 3 * N);
   L.Rds = take(tb == 4 ? 8 * 3 * N : 16);

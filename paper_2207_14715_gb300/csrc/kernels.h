@@ -61,7 +61,8 @@ struct SweepLayout {
   int T0 = 0, T1 = 0, qn = 0, cx = 0;
   int tab = 0;
   int nocc_max;
-  int G0, G1;
+  int G0, G1;    // lanes per determinant of the LU and Sherman-Morrison (power of two >= n)
+  int RG0, RG1;  // lanes per determinant of the move's ratios (power of two <= G)
 };
 
 // Nucleus-derivative kernel (eval_forces.cu), one block per walker with one warp per nucleus.

@@ -327,13 +327,19 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         if (!isfinite(rphi)) rphi = 0.0;  // an overflowing ratio is rejected (the tables are refreshed)
         (void)uo;
       } else {
-        // determinant ratios rho_u = sum_o v_occ(o) Binv_u[o][ie]
-        for (int ub = 0; ub < U; ub += ng) {
-          const int u = ub + g;
+        // determinant ratios rho_u = sum_o v_occ(o) Binv_u[o][ie], RG lanes per determinant
+        const int RG = sp ? L.RG1 : L.RG0;
+        const LaneGroup lgr(lane, RG);
+        for (int ub = 0; ub < U; ub += lgr.ng) {
+          const int u = ub + lgr.g;
           double r = 0.0;
-          if (u < U && gl < n) r = vrowd[__ldg(dl + u * n + gl)] * Binv[sp][u * n * n + gl * n + ie];
-          r = group_sum(r, G);
-          if (u < U && gl == 0) rho[u] = r;
+          if (u < U) {
+            const double* Bu = Binv[sp] + u * n * n + ie;
+            const int* du = dl + u * n;
+            for (int o = lgr.gl; o < n; o += RG) r = fma(vrowd[__ldg(du + o)], Bu[o * n], r);
+          }
+          r = group_sum(r, RG);
+          if (u < U && lgr.gl == 0) rho[u] = r;
         }
         __syncwarp();
         for (int k = lane; k < s.nterm; k += 32)
@@ -477,15 +483,10 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           __syncwarp();
           if (act && gl < n) {
             const int j = gl;
-            // two partial sums (even and odd o) halve the dependent chain
-            double w0 = (j == ie) ? -1.0 : 0.0, w1 = 0.0;
-            int o = 0;
-            for (; o + 1 < n; o += 2) {
-              w0 = fma(vrowd[__ldg(dl + u * n + o)], B[o * n + j], w0);
-              w1 = fma(vrowd[__ldg(dl + u * n + o + 1)], B[(o + 1) * n + j], w1);
-            }
-            if (o < n) w0 = fma(vrowd[__ldg(dl + u * n + o)], B[o * n + j], w0);
-            const double f = (w0 + w1) * irho;
+            // one chain: the double pipe, not the chain's latency, bounds this loop
+            double w = (j == ie) ? -1.0 : 0.0;
+            for (int o = 0; o < n; ++o) w = fma(vrowd[__ldg(dl + u * n + o)], B[o * n + j], w);
+            const double f = w * irho;
             for (int o = 0; o < n; ++o) B[o * n + j] = fma(-cv[o], f, B[o * n + j]);
           }
           __syncwarp();

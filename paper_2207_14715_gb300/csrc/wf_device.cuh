@@ -87,19 +87,27 @@ template <class T> __device__ __forceinline__ T group_sum(T v, int G) {
   return v;
 }
 
-// 1/x in double, a few FP64 instructions instead of a division: x = m 2^k with m in [1, 2)
-// (read from the bit pattern), the float reciprocal of m refined by two Newton steps (each
-// doubles the correct bits: 2^-23 -> 2^-46 -> below double rounding), scaled by 2^-k.  Zero,
-// subnormal, huge and non-finite x take the division.
+// 1/x in double, four FP64 instructions instead of a division: x = m 2^k with |m| in [1, 2)
+// (read from the bit pattern); the float reciprocal of m truncated to 24 bits (a float
+// built from the bits, no conversion instruction: conversions to and from double run at the
+// double rate) refined by two Newton steps (each doubles the correct bits: 2^-22 -> 2^-44 ->
+// below double rounding), then 2^-k added to the exponent field.  Zero, subnormal, huge and
+// non-finite x take the division.
 __device__ __forceinline__ double recip_dd(double x) {
   const long long b = __double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7ff);
   if (e <= 1 || e >= 2045) return 1.0 / x;
   const double m = __longlong_as_double((b & (long long)0x800fffffffffffffull) | 0x3ff0000000000000ll);
-  double y = (double)__frcp_rn((float)m);
+  const unsigned sgn = (unsigned)((unsigned long long)b >> 32) & 0x80000000u;
+  const float mf = __uint_as_float(sgn | 0x3f800000u | (unsigned)((b >> 29) & 0x7fffff));
+  const unsigned yb = __float_as_uint(__frcp_rn(mf));  // |1/mf| in (0.5, 1]: a normal float
+  // the same value as a double: exponent rebased from 127 to 1023, mantissa moved up 29 bits
+  double y = __longlong_as_double(
+      (long long)((((unsigned long long)(yb & 0x7fffffffu) << 29) + (896ull << 52)) | ((unsigned long long)sgn << 32)));
   y = y * fma(-m, y, 2.0);
   y = y * fma(-m, y, 2.0);
-  return y * __longlong_as_double((long long)(2046 - e) << 52);
+  // |y| in [0.5, 1]: the result's exponent field stays in 1..2044 over the fast branch's range
+  return __longlong_as_double(__double_as_longlong(y) + (long long)(1023 - e) * (1LL << 52));
 }
 
 // ------------------------------------------------------------------------------------
