@@ -292,7 +292,8 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         const int c0 = __ldg(s.occ_chunk_off[sp] + q), c1 = __ldg(s.occ_chunk_off[sp] + q + 1);
         Tb v = 0;
         for (int c = c0; c < c1; ++c) v += part[c];
-        vrowd[q] = (double)v;
+        if constexpr (kSameType<Tb, double>) vrowd[q] = v;
+        else vrowd[q] = f2d_bits(v);
       }
       __syncwarp();
       const LaneGroup lgp(lane, G);
@@ -440,8 +441,12 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         }
       }
       const Tb dJ = warp_sum(dj);
-      const double prob = rphi * rphi * (double)vexp((Tb)2 * dJ);
-      if (TAB && uacc < prob) {
+      double ej;
+      if constexpr (kSameType<Tb, double>) ej = vexp(2.0 * dJ);
+      else ej = f2d_bits(vexp(2.0f * dJ));
+      const double prob = rphi * rphi * ej;
+      const bool acc = less_nonneg(uacc, prob);  // uacc in [0, 1), prob >= 0 or NaN
+      if (TAB && acc) {
         // T <- T + b c^T; B <- B - b (v^T B - e_i^T) (b = B[:, i] / rho_0, lane j owns column j:
         // it reads only its own column before writing it); q <- q'
         const int nx = s.n_x[sp], uo = sp ? U0 : 0;
@@ -468,7 +473,7 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           Sv[a * SA + e] = Snew[a * 6 + 1];
         }
         ++accepted;
-      } else if (!TAB && uacc < prob) {
+      } else if (!TAB && acc) {
         // the reciprocals 1/rho_u and 1/(Phi'/Phi), one per lane
         for (int q = lane; q <= U; q += 32) rinv[q] = recip(q < U ? rho[q] : rphi);
         __syncwarp();
@@ -497,7 +502,9 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           pe += (int)((b >> 52) & 0x7ff) - 1023;
           pm = __longlong_as_double((b & 0x800fffffffffffffLL) | (1023LL << 52));
         }
-        if (rphi < 0.0) sgnPhi = -sgnPhi;
+        // an accepted rphi is nonzero: its sign bit is its sign; flip sgnPhi's sign bit
+        if (__double_as_longlong(rphi) < 0)
+          sgnPhi = __longlong_as_double(__double_as_longlong(sgnPhi) ^ (long long)0x8000000000000000ull);
         for (int k = lane; k < s.nterm; k += 32) wk[k] *= rho[__ldg(s.term_det + 2 * k + sp)] * irphi;
         if (lane < 3) {
           R[3 * e + lane] = lane == 0 ? rn[0] : (lane == 1 ? rn[1] : rn[2]);

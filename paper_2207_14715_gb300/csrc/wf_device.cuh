@@ -110,6 +110,23 @@ __device__ __forceinline__ double recip_dd(double x) {
   return __longlong_as_double(__double_as_longlong(y) + (long long)(1023 - e) * (1LL << 52));
 }
 
+// float -> double by moving the bits (exact, as the conversion): a conversion to or from
+// double runs at the double rate, integer operations at the full rate.  Zero, subnormal and
+// non-finite values take the conversion (a branch no lane takes costs nothing).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f), ex = (u >> 23) & 0xffu;
+  if (ex == 0u || ex == 0xffu) return (double)f;
+  return __longlong_as_double((long long)((((unsigned long long)(u & 0x7fffffffu) << 29) + (896ull << 52)) |
+                                          ((unsigned long long)(u & 0x80000000u) << 32)));
+}
+
+// a < b for a >= 0 and b >= 0 or NaN (false for NaN), on the bit patterns: for non-negative
+// doubles their order is the order of the patterns as integers
+__device__ __forceinline__ bool less_nonneg(double a, double b) {
+  const long long ib = __double_as_longlong(b);
+  return __double_as_longlong(a) < ib && ib <= 0x7ff0000000000000ll;
+}
+
 // ------------------------------------------------------------------------------------
 // Lane-group LU with partial pivoting and explicit inverse.
 // A (n x n, row-major, rows = electrons, columns = orbital slots) is overwritten with its
