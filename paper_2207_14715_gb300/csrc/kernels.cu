@@ -102,7 +102,7 @@ int make_sweep_layout(const SysDev& s, int tb, int max_smem, SweepLayout& L) {
   int cv = 0, scr = 0;
   for (int sp = 0; sp < 2; ++sp) {
     const int n = s.n[sp], G = sp ? L.G1 : L.G0, ng = L.tab ? 1 : 32 / G;
-    cv = std::max(cv, 8 * ng * n);
+    cv = std::max(cv, 8 * (L.tab ? 1 : 2) * ng * n);  // Sherman-Morrison stages two passes' columns
     scr = std::max(scr, ng * (8 * n * n + 4 * n) + 16);
   }
   // the LU scratch of a refactorisation shares its space with the buffers of the moves (the

@@ -345,7 +345,8 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         __syncwarp();
         for (int k = lane; k < s.nterm; k += 32)
           rphi += __ldg(s.term_coef + k) * wk[k] * rho[__ldg(s.term_det + 2 * k + sp)];
-        rphi = warp_sum(rphi);
+        // the lanes' partial sums are reduced after the Jastrow change, together with its sum:
+        // the double reduction's latency then overlaps the float work
       }
       // Jastrow change of the terms that involve electron e (Sec. 2.1): distances from the
       // proposed position, then items e-n (a), e-e (j) and e-e-n (a, k), the last through the
@@ -440,7 +441,17 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
           });
         }
       }
-      const Tb dJ = warp_sum(dj);
+      Tb dJ;
+      if constexpr (TAB) {
+        dJ = warp_sum(dj);
+      } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          rphi += __shfl_xor_sync(kFull, rphi, o);
+          dj += __shfl_xor_sync(kFull, dj, o);
+        }
+        dJ = dj;
+      }
       double ej;
       if constexpr (kSameType<Tb, double>) ej = vexp(2.0 * dJ);
       else ej = f2d_bits(vexp(2.0f * dJ));
@@ -477,22 +488,38 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         // the reciprocals 1/rho_u and 1/(Phi'/Phi), one per lane
         for (int q = lane; q <= U; q += 32) rinv[q] = recip(q < U ? rho[q] : rphi);
         __syncwarp();
-        // Sherman-Morrison: Binv <- Binv - Binv[:, ie] (v^T Binv - e_ie^T) / rho
-        for (int ub = 0; ub < U; ub += ng) {
-          const int u = ub + g;
-          const bool act = u < U;
-          double* B = Binv[sp] + (act ? u : 0) * n * n;
-          double* cv = cvec + g * n;
-          if (act && gl < n) cv[gl] = B[gl * n + ie];
-          const double irho = act ? rinv[u] : 0.0;
+        // Sherman-Morrison: Binv <- Binv - Binv[:, ie] (v^T Binv - e_ie^T) / rho, two lane-group
+        // passes at a time (determinants u and u + ng): their row products are independent
+        // chains, so each hides the other's latency without extra double instructions
+        for (int ub = 0; ub < U; ub += 2 * ng) {
+          const int ua = ub + g, uc = ub + ng + g;
+          const bool aa = ua < U, ac = uc < U, two = ub + ng < U;  // ac implies aa; two: warp-uniform
+          double* Ba = Binv[sp] + (aa ? ua : 0) * n * n;
+          double* Bc = Binv[sp] + (ac ? uc : 0) * n * n;
+          double* cva = cvec + g * n;
+          double* cvc = cvec + (ng + g) * n;
+          if (aa && gl < n) cva[gl] = Ba[gl * n + ie];
+          if (ac && gl < n) cvc[gl] = Bc[gl * n + ie];
+          const double ira = aa ? rinv[ua] : 0.0, irc = ac ? rinv[uc] : 0.0;
           __syncwarp();
-          if (act && gl < n) {
+          if (aa && gl < n) {
             const int j = gl;
-            // one chain: the double pipe, not the chain's latency, bounds this loop
-            double w = (j == ie) ? -1.0 : 0.0;
-            for (int o = 0; o < n; ++o) w = fma(vrowd[__ldg(dl + u * n + o)], B[o * n + j], w);
-            const double f = w * irho;
-            for (int o = 0; o < n; ++o) B[o * n + j] = fma(-cv[o], f, B[o * n + j]);
+            const int* da = dl + ua * n;
+            const int* dc = dl + (ac ? uc : ua) * n;
+            double wa = (j == ie) ? -1.0 : 0.0, wc = wa;
+            if (two) {
+              for (int o = 0; o < n; ++o) {
+                wa = fma(vrowd[__ldg(da + o)], Ba[o * n + j], wa);
+                if (ac) wc = fma(vrowd[__ldg(dc + o)], Bc[o * n + j], wc);
+              }
+            } else {
+              for (int o = 0; o < n; ++o) wa = fma(vrowd[__ldg(da + o)], Ba[o * n + j], wa);
+            }
+            const double fa = wa * ira, fc = wc * irc;
+            for (int o = 0; o < n; ++o) {
+              Ba[o * n + j] = fma(-cva[o], fa, Ba[o * n + j]);
+              if (ac) Bc[o * n + j] = fma(-cvc[o], fc, Bc[o * n + j]);
+            }
           }
           __syncwarp();
         }
