@@ -15,8 +15,10 @@ namespace {
 template <class Tb> struct JasBounds { static constexpr int min_blocks = 2; };
 template <> struct JasBounds<double> { static constexpr int min_blocks = 1; };
 
-// Per-lane sum of ln J terms: double in the FP64 form, float-float in the mixed form (the
-// value enters ln|Psi|, so it keeps about double accuracy without double instructions).
+// Per-lane sum of ln J terms: double in the FP64 form; in the mixed form a compensated float
+// sum (the value enters ln|Psi|, so it keeps about double accuracy without double
+// instructions): the running sum s and, in c, the rounding error of every addition (TwoSum)
+// and of every coefficient product (TwoProduct), added to s once at the end.
 template <class Tb> struct LnSum {
   double v = 0.0;
   __device__ __forceinline__ void add(double x) { v += x; }
@@ -24,11 +26,28 @@ template <class Tb> struct LnSum {
   __device__ __forceinline__ double value() const { return v; }
 };
 template <> struct LnSum<float> {
-  dsf v = {0.0f, 0.0f};
-  __device__ __forceinline__ void add(float x) { v = ds_add_f(v, x); }
-  __device__ __forceinline__ void add(dsf x) { v = ds_add(v, x); }
-  __device__ __forceinline__ void add(const LnSum& o) { v = ds_add(v, o.v); }
-  __device__ __forceinline__ double value() const { return ds_to_double(v); }
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void acc(float x) {
+    const dsf t = ds_two_sum(s, x);
+    s = t.hi;
+    c += t.lo;
+  }
+  __device__ __forceinline__ void add(float x) { acc(x); }
+  __device__ __forceinline__ void add(dsf x) {
+    acc(x.hi);
+    c += x.lo;
+  }
+  // (chi + clo) val, the coefficient a float-float pair
+  __device__ __forceinline__ void add_prod(float chi, float clo, float val) {
+    const float p = chi * val;
+    c += fmaf(clo, val, fmaf(chi, val, -p));
+    acc(p);
+  }
+  __device__ __forceinline__ void add(const LnSum& o) {
+    acc(o.s);
+    c += o.c;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
 // lanes -> (electron i, group g); group g takes nuclei a = g, g + S, ... and partners
@@ -99,7 +118,7 @@ __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L
             if constexpr (kSameType<Tb, double>)
               lnj.add(ct * val);
             else  // coefficient as a float-float pair: its rounding would shift every triple alike
-              lnj.add(ds_mul(dsf{__ldg(cds + 2 * t), __ldg(cds + 2 * t + 1)}, dsf{val, 0.0f}));
+              lnj.add_prod(__ldg(cds + 2 * t), __ldg(cds + 2 * t + 1), val);
             g0 += ct * gx; g1 += ct * gy; g2 += ct * gz;
             lap += ct * lp;
           };

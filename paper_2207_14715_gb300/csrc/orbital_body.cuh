@@ -85,7 +85,7 @@ __device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L
     dsf r3[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) r3[d] = dsf{__shfl_sync(kFull, rl.hi, d), __shfl_sync(kFull, rl.lo, d)};
-    basis_at_f<true>(s, lane, r3, bv, bv + 1, bv + 2, bv + 3, bv + 4 * M, 4);
+    basis_at_f<true, true>(s, lane, r3, bv, nullptr, nullptr, nullptr, bv + 4 * M);
     if (OD) basis_values_ds(s, lane, r3, ctab, bds);
   }
   __syncwarp();

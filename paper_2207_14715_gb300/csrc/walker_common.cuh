@@ -61,7 +61,9 @@ __device__ __forceinline__ dsf nuc_coord_ds(const SysDev& s, int a, int d) {
   const float2 v = __ldg(reinterpret_cast<const float2*>(s.nuc_ds) + 3 * a + d);
   return dsf{v.x, v.y};
 }
-template <bool DERIV>
+// PACK4 (with DERIV): value and gradient of function mu as the float4 bv[4 mu .. 4 mu + 3],
+// Laplacian at bl[mu] (bx, by, bz and cs unused).
+template <bool DERIV, bool PACK4 = false>
 __device__ __forceinline__ void basis_at_f(const SysDev& s, int lane, const dsf* r3, float* bv, float* bx, float* by,
                                            float* bz, float* bl, int cs = 1) {
   // the displacement from each nucleus once (lane a: nucleus a), shared by shuffles with the
@@ -89,10 +91,18 @@ __device__ __forceinline__ void basis_at_f(const SysDev& s, int lane, const dsf*
       dy = ds_diff_f(r3[1], nuc_coord_ds(s, c, 1));
       dz = ds_diff_f(r3[2], nuc_coord_ds(s, c, 2));
     }
-    if (act)
-      gto_shell<float, DERIV>(l, __int_as_float(p.w), s.sh_norm_f + 6 * sh, dx, dy, dz,
-                              bv + f * cs, DERIV ? bx + f * cs : nullptr, DERIV ? by + f * cs : nullptr,
-                              DERIV ? bz + f * cs : nullptr, DERIV ? bl + f : nullptr, cs);
+    if (act) {
+      if constexpr (PACK4)  // value and gradient of function f + c as one 16-byte store
+        gto_shell_emit<float, true>(l, __int_as_float(p.w), s.sh_norm_f + 6 * sh, dx, dy, dz,
+                                    [&](int c, float v, float x, float y, float w, float lp) {
+                                      reinterpret_cast<float4*>(bv)[f + c] = make_float4(v, x, y, w);
+                                      bl[f + c] = lp;
+                                    });
+      else
+        gto_shell<float, DERIV>(l, __int_as_float(p.w), s.sh_norm_f + 6 * sh, dx, dy, dz,
+                                bv + f * cs, DERIV ? bx + f * cs : nullptr, DERIV ? by + f * cs : nullptr,
+                                DERIV ? bz + f * cs : nullptr, DERIV ? bl + f : nullptr, cs);
+    }
   }
 }
 

@@ -249,9 +249,8 @@ template <class T> __device__ __forceinline__ T tload(const double* p) { return 
 // e, t and base depend on the kind.  Writes value (and if out_d is non-null gradient and
 // Laplacian) for component c at out[c * stride].
 // ------------------------------------------------------------------------------------
-template <class T, bool DERIV, class NT>
-__device__ __forceinline__ void gto_shell(int l, T z, const NT* nrm, T dx, T dy, T dz, T* val, T* gx, T* gy, T* gz,
-                                          T* lap, int cs = 1) {
+template <class T, bool DERIV, class NT, class Emit>
+__device__ __forceinline__ void gto_shell_emit(int l, T z, const NT* nrm, T dx, T dy, T dz, Emit&& emit) {
   const T r2 = dx * dx + dy * dy + dz * dz;
   T e, tz, base;
   if (z < (T)0) {
@@ -267,24 +266,19 @@ __device__ __forceinline__ void gto_shell(int l, T z, const NT* nrm, T dx, T dy,
   }
   if (l == 0) {
     const T ne = (T)nrm[0] * e;
-    val[0] = ne;
-    if (DERIV) {
-      gx[0] = -tz * dx * ne; gy[0] = -tz * dy * ne; gz[0] = -tz * dz * ne;
-      lap[0] = base * ne;
-    }
+    if (DERIV) emit(0, ne, -tz * dx * ne, -tz * dy * ne, -tz * dz * ne, base * ne);
+    else emit(0, ne, (T)0, (T)0, (T)0, (T)0);
   } else if (l == 1) {
     const T d[3] = {dx, dy, dz};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const T ne = (T)nrm[c] * e;
       const T P = d[c];
-      val[c * cs] = ne * P;
-      if (DERIV) {
-        gx[c * cs] = ne * ((c == 0 ? (T)1 : (T)0) - tz * dx * P);
-        gy[c * cs] = ne * ((c == 1 ? (T)1 : (T)0) - tz * dy * P);
-        gz[c * cs] = ne * ((c == 2 ? (T)1 : (T)0) - tz * dz * P);
-        lap[c] = ne * P * base;
-      }
+      if (DERIV)
+        emit(c, ne * P, ne * ((c == 0 ? (T)1 : (T)0) - tz * dx * P), ne * ((c == 1 ? (T)1 : (T)0) - tz * dy * P),
+             ne * ((c == 2 ? (T)1 : (T)0) - tz * dz * P), ne * P * base);
+      else
+        emit(c, ne * P, (T)0, (T)0, (T)0, (T)0);
     }
   } else {
     // xx yy zz xy xz yz
@@ -295,7 +289,6 @@ __device__ __forceinline__ void gto_shell(int l, T z, const NT* nrm, T dx, T dy,
     for (int c = 0; c < 6; ++c) {
       const T ne = (T)nrm[c] * e;
       const T P = d[ia[c]] * d[ib[c]];
-      val[c * cs] = ne * P;
       if (DERIV) {
         T g[3];
 #pragma unroll
@@ -305,12 +298,27 @@ __device__ __forceinline__ void gto_shell(int l, T z, const NT* nrm, T dx, T dy,
           if (ib[c] == q) dP += d[ia[c]];
           g[q] = ne * (dP - tz * d[q] * P);
         }
-        gx[c * cs] = g[0]; gy[c * cs] = g[1]; gz[c * cs] = g[2];
         const T lapP = (c < 3) ? (T)2 : (T)0;
-        lap[c] = ne * (lapP + P * base);
+        emit(c, ne * P, g[0], g[1], g[2], ne * (lapP + P * base));
+      } else {
+        emit(c, ne * P, (T)0, (T)0, (T)0, (T)0);
       }
     }
   }
+}
+
+template <class T, bool DERIV, class NT>
+__device__ __forceinline__ void gto_shell(int l, T z, const NT* nrm, T dx, T dy, T dz, T* val, T* gx, T* gy, T* gz,
+                                          T* lap, int cs = 1) {
+  gto_shell_emit<T, DERIV>(l, z, nrm, dx, dy, dz, [&](int c, T v, T x, T y, T w, T lp) {
+    val[c * cs] = v;
+    if (DERIV) {
+      gx[c * cs] = x;
+      gy[c * cs] = y;
+      gz[c * cs] = w;
+      lap[c] = lp;
+    }
+  });
 }
 
 // ------------------------------------------------------------------------------------
