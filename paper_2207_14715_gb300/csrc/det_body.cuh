@@ -98,19 +98,38 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
   for (int q = lane; q < N; q += 32) LJ[q] = JL[(size_t)w * N + q];
   const double lnJ = JS[2 * (size_t)w], V = JS[2 * (size_t)w + 1];
   __syncwarp();
-  for (DivStep eq(lane, nev); eq.hi < N; eq.next(nev)) {
-    const int e = eq.hi, q = eq.lo;
-    const Tb* ob = OB + ((size_t)w * N + e) * 5 * nev;
-    const Tb x = ob[nev + q], y = ob[2 * nev + q], z = ob[3 * nev + q], lp = ob[4 * nev + q];
-    const Tb lq = lp + (Tb)2 * (G[3 * e] * x + G[3 * e + 1] * y + G[3 * e + 2] * z);
-    Lphi[e * nev + q] = lq;
-    if (q < nevd) {
-      // PhiD: double orbital values for the LU, or with carried inverses (no LU) the dressed
-      // Laplacians of the determinant orbitals widened once for the traces t_u
-      PhiD[e * nevd + q] = carry ? (double)lq : OD[((size_t)w * N + e) * nevd + q];
-      Gphi[(e * nevd + q) * 3] = x;
-      Gphi[(e * nevd + q) * 3 + 1] = y;
-      Gphi[(e * nevd + q) * 3 + 2] = z;
+  // four (electron, orbital) entries per lane requested before the first is used (the
+  // workspace comes from memory: one latency per four entries)
+  for (DivStep eq(lane, nev); eq.hi < N;) {
+    int ee[4], qq[4];
+    Tb x[4], y[4], z[4], lp[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ee[k] = eq.hi;
+      qq[k] = eq.lo;
+      if (eq.hi < N) {
+        const Tb* ob = OB + ((size_t)w * N + eq.hi) * 5 * nev + eq.lo;
+        x[k] = ob[nev];
+        y[k] = ob[2 * nev];
+        z[k] = ob[3 * nev];
+        lp[k] = ob[4 * nev];
+        eq.next(nev);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = ee[k], q = qq[k];
+      if (e >= N) break;
+      const Tb lq = lp[k] + (Tb)2 * (G[3 * e] * x[k] + G[3 * e + 1] * y[k] + G[3 * e + 2] * z[k]);
+      Lphi[e * nev + q] = lq;
+      if (q < nevd) {
+        // PhiD: double orbital values for the LU, or with carried inverses (no LU) the dressed
+        // Laplacians of the determinant orbitals widened once for the traces t_u
+        PhiD[e * nevd + q] = carry ? (double)lq : OD[((size_t)w * N + e) * nevd + q];
+        Gphi[(e * nevd + q) * 3] = x[k];
+        Gphi[(e * nevd + q) * 3 + 1] = y[k];
+        Gphi[(e * nevd + q) * 3 + 2] = z[k];
+      }
     }
   }
   __syncwarp();
@@ -328,10 +347,20 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
         // orbital values from the workspace (not staged in shared memory: the walker region
         // then fits 16 walkers per SM)
         const Tb* pv = OB + ((size_t)w * N + e0) * 5 * nev + kc;
-        for (int e = 0; e < n; ++e) {
-          const Tb ph = pv[(size_t)e * 5 * nev], lph = Lphi[(e0 + e) * nev + kc];
-          o += g[e] * ph;
-          kk += a[e] * ph + g[e] * lph;
+        // eight electrons' values requested before the first is used (the workspace rows are
+        // mostly not cached by now: one memory latency per eight loads instead of per load)
+        for (int eb = 0; eb < n; eb += 8) {
+          Tb ph[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) ph[t] = eb + t < n ? pv[(size_t)(eb + t) * 5 * nev] : (Tb)0;
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            if (eb + t < n) {
+              const int e = eb + t;
+              const Tb lph = Lphi[(e0 + e) * nev + kc];
+              o += g[e] * ph[t];
+              kk += a[e] * ph[t] + g[e] * lph;
+            }
         }
       }
       Ow[s.p_off_kappa + j] = o;
