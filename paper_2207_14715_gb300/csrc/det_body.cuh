@@ -68,13 +68,12 @@ __device__ __forceinline__ void lu_det_all(const SysDev& s, int sp, int lane, co
 
 template <class Tb>
 __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, int w, unsigned char* base,
-                                         const Tb* __restrict__ JG, const Tb* __restrict__ JL,
-                                         const double* __restrict__ JS, const Tb* __restrict__ OB,
-                                         const double* __restrict__ OD, double* __restrict__ logpsi,
+                                         const Tb* JG, const Tb* JL, const double* JS, const Tb* OB,
+                                         const double* OD, double* __restrict__ logpsi,
                                          double* __restrict__ sgn_out, double* __restrict__ eloc,
                                          double* __restrict__ vg_ws, double* __restrict__ grad, Tb* __restrict__ Og,
                                          Tb* __restrict__ dELg, double* __restrict__ state_out,
-                                         double* __restrict__ aux, const double* __restrict__ carry) {
+                                         double* __restrict__ aux, const double* carry) {
   const int lane = threadIdx.x & 31;
   double* vg = reinterpret_cast<double*>(base + L.vg);
   Tb* G = reinterpret_cast<Tb*>(base + L.G);
@@ -146,7 +145,7 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
     for (int sp = 0; sp < 2; ++sp) {
       const int n = s.n[sp], U = s.U[sp], e0 = sp ? Nup : 0, uo = sp ? U0 : 0;
       const double* Bc = cs + (sp ? nb0 : 0);
-      for (int q = lane; q < U * n * n; q += 32) Bt[sp][q] = (Tb)Bc[q];
+      warp_copy(Bt[sp], Bc, U * n * n, lane);
       // t_u = tr(B_u L_u): partial sums per (u, slot o), then per u
       for (int i = lane; i < U * n; i += 32) {
         const int u = i / n, o = i - u * n, col = __ldg(s.det_ev[sp] + u * n + o);

@@ -62,9 +62,8 @@ __device__ __forceinline__ double small_inverse(double M[4][4], double Mi[4][4],
 
 template <class Tb>
 __device__ __forceinline__ void dettab_body(const SysDev& s, const DetTabLayout& L, int w, unsigned char* base,
-                                            const Tb* __restrict__ JG, const Tb* __restrict__ JL,
-                                            const double* __restrict__ JS, const Tb* __restrict__ OB,
-                                            const double* __restrict__ OD, double* __restrict__ logpsi,
+                                            const Tb* JG, const Tb* JL, const double* JS, const Tb* OB,
+                                            const double* OD, double* __restrict__ logpsi,
                                             double* __restrict__ sgn_out, double* __restrict__ eloc,
                                             double* __restrict__ vg_ws, double* __restrict__ grad,
                                             Tb* __restrict__ Og, Tb* __restrict__ dELg) {

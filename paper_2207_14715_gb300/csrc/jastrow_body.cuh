@@ -57,7 +57,7 @@ template <> struct LnSum<float> {
 // warps meet in shared memory; otherwise one warp per walker.
 template <class Tb, bool WIDE = false>
 __device__ __forceinline__ void jastrow_body(const SysDev& s, const JasLayout& L, int w, unsigned char* base,
-                                             const double* __restrict__ Rg, Tb* __restrict__ JG, Tb* __restrict__ JL,
+                                             const double* Rg, Tb* __restrict__ JG, Tb* __restrict__ JL,
                                              double* __restrict__ JS) {
   const int lane = threadIdx.x & 31;
   const int rank = WIDE ? (int)(threadIdx.x >> 5) : 0, nw = WIDE ? (int)(blockDim.x >> 5) : 1;
@@ -228,7 +228,7 @@ __device__ __forceinline__ void pade_param_derivs(Tb r, Tb kap, Tb a1, Tb a2, Tb
 
 template <class Tb>
 __device__ __forceinline__ void jastrow_deriv_body(const SysDev& s, const JasLayout& L, int w, unsigned char* base,
-                                                   const double* __restrict__ Rg, const double* __restrict__ vgg,
+                                                   const double* Rg, const double* vgg,
                                                    Tb* __restrict__ Og, Tb* __restrict__ dELg) {
   const int lane = threadIdx.x & 31;
   Tb* vg = reinterpret_cast<Tb*>(base + L.vg);  // grad ln|Psi| in the bulk type

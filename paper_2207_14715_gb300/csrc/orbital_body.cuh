@@ -60,7 +60,7 @@ __device__ __forceinline__ void contract_groups(const SysDev& s, int lane, int n
 // One warp, (walker, electron) pair gw (walker gw / N, electron gw % N).
 template <class Tb>
 __device__ __forceinline__ void orbital_body(const SysDev& s, const OrbLayout& L, long long gw, unsigned char* base,
-                                             const double* __restrict__ Rg, Tb* __restrict__ OB,
+                                             const double* Rg, Tb* __restrict__ OB,
                                              double* __restrict__ OD) {
   const int lane = threadIdx.x & 31;
   const int nev = s.n_ev, nevd = s.n_ev_det, M = s.M;

@@ -150,9 +150,9 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
   const bool from_state = !TAB && state && state_valid;
   if (from_state) {
     const double* st = state + (size_t)w * s.state_doubles;
-    for (int q = lane; q < nb0; q += 32) Binv[0][q] = st[q];
-    for (int q = lane; q < nb1; q += 32) Binv[1][q] = st[nb0 + q];
-    for (int k = lane; k < s.nterm; k += 32) wk[k] = st[nb0 + nb1 + 2 * Ut + k];
+    warp_copy(Binv[0], st, nb0, lane);
+    warp_copy(Binv[1], st + nb0, nb1, lane);
+    warp_copy(wk, st + nb0 + nb1 + 2 * Ut, s.nterm, lane);
     lnPhi = st[nb0 + nb1 + 2 * Ut + s.nterm];
     sgnPhi = st[nb0 + nb1 + 2 * Ut + s.nterm + 1];
   }

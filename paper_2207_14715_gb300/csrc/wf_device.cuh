@@ -30,6 +30,23 @@ struct DivStep {
     while (lo >= d) { lo -= d; ++hi; }
   }
 };
+// dst[i] = (TD)src[i] for i = lane, lane + 32, ... < n by one warp: eight loads issued before
+// the first store (the compiler may not move a global load above a store through another
+// pointer, so a plain loop waits one memory latency per element).  src is not declared
+// __restrict__: in the one-launch batched step it can hold data written earlier in the same
+// launch, which the read-only data path may not return.
+template <class TD, class TS>
+__device__ __forceinline__ void warp_copy(TD* dst, const TS* src, int n, int lane) {
+  for (int i0 = lane; i0 < n; i0 += 256) {
+    TS v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (i0 + 32 * k < n) v[k] = src[i0 + 32 * k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (i0 + 32 * k < n) dst[i0 + 32 * k] = (TD)v[k];
+  }
+}
 // lane-group coordinates for a power-of-two group size G
 struct LaneGroup {
   int ng, g, gl;
