@@ -327,26 +327,35 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
         rphi = (r0 != 0.0 && Sig != 0.0) ? r0 * Sig_new / Sig : 0.0;
         if (!isfinite(rphi)) rphi = 0.0;  // an overflowing ratio is rejected (the tables are refreshed)
         (void)uo;
-      } else {
-        // determinant ratios rho_u = sum_o v_occ(o) Binv_u[o][ie], RG lanes per determinant
-        const int RG = sp ? L.RG1 : L.RG0;
-        const LaneGroup lgr(lane, RG);
-        for (int ub = 0; ub < U; ub += lgr.ng) {
-          const int u = ub + lgr.g;
-          double r = 0.0;
-          if (u < U) {
-            const double* Bu = Binv[sp] + u * n * n + ie;
-            const int* du = dl + u * n;
-            for (int o = lgr.gl; o < n; o += RG) r = fma(vrowd[__ldg(du + o)], Bu[o * n], r);
+      }
+      // determinant ratios rho_u = sum_o v_occ(o) Binv_u[o][ie], RG lanes per determinant.  With
+      // one pass over the determinants (the usual case) the lanes' products are formed here and
+      // reduced after the Jastrow distances below, whose float work then covers their latency.
+      const int RG = sp ? L.RG1 : L.RG0;
+      const LaneGroup lgr(lane, RG);
+      const bool one_pass = U <= lgr.ng;
+      const int ur = lgr.g;
+      double rpart = 0.0;
+      if constexpr (!TAB) {
+        if (one_pass) {
+          if (ur < U) {
+            const double* Bu = Binv[sp] + ur * n * n + ie;
+            const int* du = dl + ur * n;
+            for (int o = lgr.gl; o < n; o += RG) rpart = fma(vrowd[__ldg(du + o)], Bu[o * n], rpart);
           }
-          r = group_sum(r, RG);
-          if (u < U && lgr.gl == 0) rho[u] = r;
+        } else {
+          for (int ub = 0; ub < U; ub += lgr.ng) {
+            const int u = ub + lgr.g;
+            double r = 0.0;
+            if (u < U) {
+              const double* Bu = Binv[sp] + u * n * n + ie;
+              const int* du = dl + u * n;
+              for (int o = lgr.gl; o < n; o += RG) r = fma(vrowd[__ldg(du + o)], Bu[o * n], r);
+            }
+            r = group_sum(r, RG);
+            if (u < U && lgr.gl == 0) rho[u] = r;
+          }
         }
-        __syncwarp();
-        for (int k = lane; k < s.nterm; k += 32)
-          rphi += __ldg(s.term_coef + k) * wk[k] * rho[__ldg(s.term_det + 2 * k + sp)];
-        // the lanes' partial sums are reduced after the Jastrow change, together with its sum:
-        // the double reduction's latency then overlaps the float work
       }
       // Jastrow change of the terms that involve electron e (Sec. 2.1): distances from the
       // proposed position, then items e-n (a), e-e (j) and e-e-n (a, k), the last through the
@@ -377,7 +386,19 @@ __device__ __forceinline__ void sweep_body(const SysDev& s, const SweepLayout& L
 #pragma unroll
         for (int q = 0; q < 6; ++q) { Snew[a * 6 + q] = pw; pw *= sv; }
       }
+      if constexpr (!TAB) {
+        if (one_pass) {
+          rpart = group_sum(rpart, RG);
+          if (ur < U && lgr.gl == 0) rho[ur] = rpart;
+        }
+      }
       __syncwarp();
+      if constexpr (!TAB) {
+        // the structure sum's per-lane parts; they are reduced after the Jastrow change,
+        // together with its sum: the double reduction's latency then overlaps the float work
+        for (int k = lane; k < s.nterm; k += 32)
+          rphi += __ldg(s.term_coef + k) * wk[k] * rho[__ldg(s.term_det + 2 * k + sp)];
+      }
       Tb dj = 0;
       for (int t = lane; t < Nn + N; t += 32) {
         if (t < Nn) {
