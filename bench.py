@@ -33,10 +33,11 @@ SEED = 20220728 + 1
 # from one ncu capture (8192 walkers of the same workload; traffic scales with walkers), valid
 # only while the kernel sources hash to the recorded value (else the bench reports null).
 WALKER_KERNEL_SOURCES = ["kernels.cu", "eval_jastrow.cu", "eval_orbitals.cu", "eval_det.cu", "walker_common.cuh",
-                         "kernels.h", "wf_device.cuh", "dsfloat.cuh", "vbqmc_internal.h"]
+                         "kernels.h", "wf_device.cuh", "dsfloat.cuh", "vbqmc_internal.h", "sweep_body.cuh",
+                         "jastrow_body.cuh", "orbital_body.cuh", "det_body.cuh"]
 PROFILED_TRAFFIC = {
-    "sources_sha256": "92956cc090a16ed8fbd11187cf970dff838bc380f672b9c8d7f4c9c6429d1054",
-    "bytes_per_walker": {"sweep": 10792.4, "det": 26175.8, "orbitals": 8967.0},
+    "sources_sha256": "691ae3d12a32f737a716a7d8350bc6d5433f6073be043f1c99fae71a10a331f8",
+    "bytes_per_walker": {"sweep": 10862.5, "det": 26410.8, "orbitals": 9004.3, "jastrow": 392.2},
 }
 
 
