@@ -30,26 +30,31 @@ REFRESH = 10  # walker-steps between refactorisations of the Slater matrices
 SEED = 20220728 + 1
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per walker of the walker kernels
-# from one ncu capture (8192 walkers of the same workload; traffic scales with walkers), valid
-# only while the kernel sources hash to the recorded value (else the bench reports null).
-WALKER_KERNEL_SOURCES = ["kernels.cu", "eval_jastrow.cu", "eval_orbitals.cu", "eval_det.cu", "walker_common.cuh",
-                         "kernels.h", "wf_device.cuh", "dsfloat.cuh", "vbqmc_internal.h", "sweep_body.cuh",
-                         "jastrow_body.cuh", "orbital_body.cuh", "det_body.cuh"]
+# from one ncu capture (8192 walkers of the same workload; traffic scales with walkers), each
+# valid only while that kernel's sources hash to the recorded value (else the bench reports null).
+_COMMON_SOURCES = ["walker_common.cuh", "wf_device.cuh", "dsfloat.cuh", "kernels.h", "vbqmc_internal.h"]
+WALKER_KERNEL_SOURCES = {"sweep": ["kernels.cu", "sweep_body.cuh"] + _COMMON_SOURCES,
+                         "det": ["eval_det.cu", "det_body.cuh"] + _COMMON_SOURCES,
+                         "orbitals": ["eval_orbitals.cu", "orbital_body.cuh"] + _COMMON_SOURCES,
+                         "jastrow": ["eval_jastrow.cu", "jastrow_body.cuh"] + _COMMON_SOURCES}
 PROFILED_TRAFFIC = {
-    "sources_sha256": "691ae3d12a32f737a716a7d8350bc6d5433f6073be043f1c99fae71a10a331f8",
-    "bytes_per_walker": {"sweep": 10862.5, "det": 26410.8, "orbitals": 9004.3, "jastrow": 392.2},
+    "sweep": ("282f97f15ec056b95ca54391cd230c827fe9b4dc3b04783db99c8ca6c38daa7d", 10862.5),
+    "det": ("2b71d97144b4651efed3caca6ec526642a0828cb1e515851c6e4a118689f42e1", 26410.8),
+    "orbitals": ("d68d06277ae1b8dbf8f9209074e417fc21ce06de2e3cdacab233c41ca3dd13dd", 9004.3),
+    "jastrow": ("9bb53d641580f851d7480ef8d5c101d8363dfc188579676e4813c39251a35a10", 392.2),
 }
 
 
 def walker_kernel_traffic(kernel, W):
     import hashlib
+    if kernel not in PROFILED_TRAFFIC:
+        return None
     h = hashlib.sha256()
-    for f in WALKER_KERNEL_SOURCES:
+    for f in WALKER_KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2207_14715_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != PROFILED_TRAFFIC["sources_sha256"] or kernel not in PROFILED_TRAFFIC["bytes_per_walker"]:
-        return None
-    return PROFILED_TRAFFIC["bytes_per_walker"][kernel] * W
+    sha, per_walker = PROFILED_TRAFFIC[kernel]
+    return per_walker * W if h.hexdigest() == sha else None
 
 
 def workload_config(W, flush=True):

@@ -201,8 +201,10 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
       Wv += wk;
       Tv += wk * (tdet[a] + tdet[U0 + b]);
     }
-    Wdet[ud] = Wv;
-    Tdet[ud] = Tv;
+    // the rows below read W_u and T_u in the bulk type: converted here once per determinant
+    // (a conversion costs a double instruction) instead of once per use by the whole warp
+    reinterpret_cast<Tb*>(Wdet)[ud] = (Tb)Wv;
+    reinterpret_cast<Tb*>(Tdet)[ud] = (Tb)Tv;
     if (aux) {
       aux[(size_t)w * (2 * Utot + 1) + ud] = Wv;
       aux[(size_t)w * (2 * Utot + 1) + Utot + ud] = Tv;
@@ -242,7 +244,7 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
           M[oc.hi * n + oc.lo] = m;
         }
         __syncwarp();
-        const Tb Wu = (Tb)Wdet[uo + u], Tu = (Tb)Tdet[uo + u];
+        const Tb Wu = reinterpret_cast<const Tb*>(Wdet)[uo + u], Tu = reinterpret_cast<const Tb*>(Tdet)[uo + u];
         for (DivStep oc(lane, n); oc.hi < n; oc.next(n)) {
           const int o = oc.hi, e = oc.lo, r = __ldg(ev_u + u * n + o) * n + e;
           const Tb b = B[o * n + e];
@@ -280,7 +282,7 @@ __device__ __forceinline__ void det_body(const SysDev& s, const DetLayout& L, in
           ay += b * gp[1];
           az += b * gp[2];
         }
-        const Tb Wu = (Tb)Wdet[uo + u];
+        const Tb Wu = reinterpret_cast<const Tb*>(Wdet)[uo + u];
         gx += Wu * ax;
         gy += Wu * ay;
         gz += Wu * az;
